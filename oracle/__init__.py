@@ -1,0 +1,337 @@
+"""CPU FP64 oracle for explicit time stepping of du/dt = F(t,u) (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: only the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package.  The CUDA library never
+loads it, and it never loads the CUDA library; the two share no code.
+
+The arithmetic lives in ``oracle.c`` (plain loops, IEEE FP64, no FMA
+contraction); this module only marshals numpy arrays into it.  Function names
+follow the paper's vocabulary: a *System* F(t,u) (Listing 2), fixed-step
+``integrate_const`` (Listing 3), error-controlled ``integrate_adaptive``
+(section "Architecture and nomenclature of Boost Odeint"), and the steppers
+of Table 1.
+
+Parity status of each function (pins live in tests/test_oracle_*.py):
+  gs_rhs / gs_laplacian        pinned: Fourier eigenvalues, zero sum, uniform
+                               fixed points of the reaction (closed forms)
+  integrate_const (Euler/RK4/  pinned: exact discrete solutions of du/dt = -x,
+  Dopri5)                      polynomial exactness, observed orders
+  dopri5 error estimate        pinned: local error order 5 (ratio ~32)
+  integrate_adaptive           pinned: closed-form error within C*tol; tol
+                               scaling.  The controller formula itself is this
+                               build's reading (paper silent)
+  integrate_ab4                pinned: cubic exactness, observed order 4
+  axpy                         pinned: exact small-integer sums
+  conv3d fwd/dgrad/wgrad       pinned: FP64 central differences of a scalar
+                               loss, 1x1x1-equivalent reduction to a matmul
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+EULER, RK4, DOPRI5 = 0, 1, 2
+PW_EXP_DECAY, PW_LOGISTIC, PW_PAPER_EXP, PW_PAPER_SIGMOID = 0, 1, 2, 3
+
+OK, ERR_INVALID, ERR_NOMEM, ERR_STEP_UNDERFLOW, ERR_MAX_STEPS, ERR_NONFINITE = 0, 1, 3, 4, 5, 6
+
+_lib = None
+_dp = C.POINTER(C.c_double)
+
+
+class _GS(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("Du", C.c_double), ("Dv", C.c_double), ("F", C.c_double), ("k", C.c_double)]
+
+
+class _Tableau(C.Structure):
+    _fields_ = [("s", C.c_int), ("a", C.c_double * 169), ("b", C.c_double * 13),
+                ("bhat", C.c_double * 13), ("c", C.c_double * 13), ("has_bhat", C.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        L.orc_get_tableau.argtypes = [C.c_int, C.POINTER(_Tableau)]
+        L.orc_gs_laplacian.argtypes = [C.POINTER(_GS), _dp, _dp]
+        L.orc_gs_rhs_full.argtypes = [C.POINTER(_GS), _dp, _dp]
+        L.orc_gs_integrate_const.argtypes = [C.POINTER(_GS), C.c_int, _dp, C.c_double, C.c_double, C.c_long]
+        L.orc_gs_integrate_replay.argtypes = [C.POINTER(_GS), C.c_int, _dp, C.c_double, _dp, C.c_long]
+        L.orc_gs_integrate_adaptive.argtypes = [C.POINTER(_GS), _dp, _dp, C.c_double, _dp, C.c_double,
+                                                C.c_double, C.c_long, C.c_long, C.POINTER(C.c_long),
+                                                C.POINTER(C.c_long), _dp, C.c_long]
+        L.orc_gs_integrate_ab4.argtypes = [C.POINTER(_GS), _dp, C.c_double, C.c_double, C.c_long]
+        L.orc_gs_dopri5_attempt.argtypes = [C.POINTER(_GS), C.c_double, C.c_double, _dp, _dp, _dp,
+                                            C.c_double, C.c_double]
+        L.orc_gs_dopri5_attempt.restype = C.c_double
+        L.orc_pw_rhs.argtypes = [C.c_int, _dp, C.c_double, C.c_long, _dp, _dp]
+        L.orc_pw_integrate_const.argtypes = [C.c_int, _dp, C.c_int, C.c_long, _dp, C.c_double, C.c_double, C.c_long]
+        L.orc_pw_integrate_replay.argtypes = [C.c_int, _dp, C.c_int, C.c_long, _dp, C.c_double, _dp, C.c_long]
+        L.orc_pw_integrate_adaptive.argtypes = [C.c_int, _dp, C.c_long, _dp, _dp, C.c_double, _dp,
+                                                C.c_double, C.c_double, C.c_long, C.c_long,
+                                                C.POINTER(C.c_long), C.POINTER(C.c_long), _dp, C.c_long]
+        L.orc_pw_integrate_ab4.argtypes = [C.c_int, _dp, C.c_long, _dp, C.c_double, C.c_double, C.c_long]
+        L.orc_pw_dopri5_attempt.argtypes = [C.c_int, _dp, C.c_long, C.c_double, C.c_double, _dp, _dp, _dp,
+                                            C.c_double, C.c_double]
+        L.orc_pw_dopri5_attempt.restype = C.c_double
+        L.orc_axpy.argtypes = [C.c_long, C.c_int, _dp, C.POINTER(_dp), _dp]
+        L.orc_conv3d_fwd.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp, _dp]
+        L.orc_conv3d_dgrad.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp]
+        L.orc_conv3d_wgrad.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp, _dp]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Tableaux (Table 1)
+# --------------------------------------------------------------------------
+def tableau(method: int):
+    T = _Tableau()
+    if lib().orc_get_tableau(method, C.byref(T)) != 0:
+        raise ValueError(method)
+    s = T.s
+    A = np.array(T.a[: s * s]).reshape(s, s)
+    return {"s": s, "A": A, "b": np.array(T.b[:s]), "bhat": np.array(T.bhat[:s]) if T.has_bhat else None,
+            "c": np.array(T.c[:s])}
+
+
+# --------------------------------------------------------------------------
+# Gray-Scott (Eq. 2)
+# --------------------------------------------------------------------------
+class GSParams:
+    """Grid and physics of one Gray-Scott problem (periodic box L^3)."""
+
+    def __init__(self, nx, ny, nz, L=2.5, Du=2e-5, Dv=1e-5, F=0.053, k=0.014, Ly=None, Lz=None):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.Lx = float(L)
+        self.Ly = float(L if Ly is None else Ly)
+        self.Lz = float(L if Lz is None else Lz)
+        self.Du, self.Dv, self.F, self.k = float(Du), float(Dv), float(F), float(k)
+
+    @property
+    def ncell(self):
+        return self.nx * self.ny * self.nz
+
+    def _c(self):
+        return _GS(self.nx, self.ny, self.nz, self.Lx, self.Ly, self.Lz, self.Du, self.Dv, self.F, self.k)
+
+
+def _pack(p: GSParams, u, v):
+    y = np.empty(2 * p.ncell, dtype=np.float64)
+    y[: p.ncell] = np.asarray(u, dtype=np.float64).reshape(-1)
+    y[p.ncell:] = np.asarray(v, dtype=np.float64).reshape(-1)
+    return y
+
+
+def _unpack(p: GSParams, y):
+    shape = (p.nz, p.ny, p.nx)
+    return y[: p.ncell].reshape(shape).copy(), y[p.ncell:].reshape(shape).copy()
+
+
+def gs_laplacian(p: GSParams, w):
+    w = _f64(w).reshape(-1)
+    out = np.empty_like(w)
+    lib().orc_gs_laplacian(C.byref(p._c()), _p(w), _p(out))
+    return out.reshape(p.nz, p.ny, p.nx)
+
+
+def gs_rhs(p: GSParams, u, v):
+    """F(t,u) of the Gray-Scott System (Listing 2): returns (du/dt, dv/dt)."""
+    y = _pack(p, u, v)
+    f = np.empty_like(y)
+    lib().orc_gs_rhs_full(C.byref(p._c()), _p(y), _p(f))
+    return _unpack(p, f)
+
+
+def gs_integrate_const(p: GSParams, u, v, method: int, dt: float, nsteps: int, t0: float = 0.0):
+    y = _pack(p, u, v)
+    st = lib().orc_gs_integrate_const(C.byref(p._c()), method, _p(y), t0, dt, nsteps)
+    if st:
+        raise RuntimeError(f"oracle status {st}")
+    return _unpack(p, y)
+
+
+def gs_integrate_replay(p: GSParams, u, v, method: int, dts, t0: float = 0.0):
+    y = _pack(p, u, v)
+    dts = _f64(dts)
+    st = lib().orc_gs_integrate_replay(C.byref(p._c()), method, _p(y), t0, _p(dts), len(dts))
+    if st:
+        raise RuntimeError(f"oracle status {st}")
+    return _unpack(p, y)
+
+
+def gs_integrate_adaptive(p: GSParams, u, v, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500,
+                          log_cap=0):
+    y = _pack(p, u, v)
+    t = C.c_double(t0)
+    dt = C.c_double(dt0)
+    na, nr = C.c_long(0), C.c_long(0)
+    log = np.zeros(max(log_cap, 1))
+    st = lib().orc_gs_integrate_adaptive(C.byref(p._c()), _p(y), C.byref(t), t_end, C.byref(dt), atol, rtol,
+                                         max_acc, max_rej, C.byref(na), C.byref(nr),
+                                         _p(log) if log_cap else None, log_cap)
+    u1, v1 = _unpack(p, y)
+    return {"u": u1, "v": v1, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value,
+            "status": st, "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
+
+
+def gs_integrate_ab4(p: GSParams, u, v, dt, nsteps, t0=0.0):
+    y = _pack(p, u, v)
+    lib().orc_gs_integrate_ab4(C.byref(p._c()), _p(y), t0, dt, nsteps)
+    return _unpack(p, y)
+
+
+def gs_dopri5_attempt(p: GSParams, u, v, dt, atol, rtol, t=0.0):
+    """One Dopri5 attempt: returns (u5, v5, err_u, err_v, E)."""
+    y = _pack(p, u, v)
+    yo = np.empty_like(y)
+    err = np.empty_like(y)
+    E = lib().orc_gs_dopri5_attempt(C.byref(p._c()), t, dt, _p(y), _p(yo), _p(err), atol, rtol)
+    u5, v5 = _unpack(p, yo)
+    eu, ev = _unpack(p, err)
+    return u5, v5, eu, ev, E
+
+
+# --------------------------------------------------------------------------
+# Pointwise ODE families (closed-form benchmarks, Eq. 1a / 1b, and the
+# decay / logistic ensembles)
+# --------------------------------------------------------------------------
+def pw_rhs(kind, x, t=0.0, coef=None):
+    x = _f64(x)
+    f = np.empty_like(x)
+    c = _f64(coef) if coef is not None else None
+    lib().orc_pw_rhs(kind, _p(c), t, x.size, _p(x), _p(f))
+    return f
+
+
+def pw_integrate_const(kind, x, method, dt, nsteps, t0=0.0, coef=None):
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    lib().orc_pw_integrate_const(kind, _p(c), method, x.size, _p(x), t0, dt, nsteps)
+    return x
+
+
+def pw_integrate_replay(kind, x, method, dts, t0=0.0, coef=None):
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    dts = _f64(dts)
+    lib().orc_pw_integrate_replay(kind, _p(c), method, x.size, _p(x), t0, _p(dts), len(dts))
+    return x
+
+
+def pw_integrate_adaptive(kind, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500, coef=None,
+                          log_cap=0):
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    t = C.c_double(t0)
+    dt = C.c_double(dt0)
+    na, nr = C.c_long(0), C.c_long(0)
+    log = np.zeros(max(log_cap, 1))
+    st = lib().orc_pw_integrate_adaptive(kind, _p(c), x.size, _p(x), C.byref(t), t_end, C.byref(dt), atol,
+                                         rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
+                                         _p(log) if log_cap else None, log_cap)
+    return {"x": x, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
+            "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
+
+
+def pw_integrate_ab4(kind, x, dt, nsteps, t0=0.0, coef=None):
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    lib().orc_pw_integrate_ab4(kind, _p(c), x.size, _p(x), t0, dt, nsteps)
+    return x
+
+
+def pw_dopri5_attempt(kind, x, dt, atol, rtol, t=0.0, coef=None):
+    x = _f64(x)
+    c = _f64(coef) if coef is not None else None
+    yo = np.empty_like(x)
+    err = np.empty_like(x)
+    E = lib().orc_pw_dopri5_attempt(kind, _p(c), x.size, t, dt, _p(x), _p(yo), _p(err), atol, rtol)
+    return yo, err, E
+
+
+def axpy(coef, xs):
+    """y = sum_j coef[j] * xs[j] (the Algebra's n-ary for_each, n <= 15)."""
+    xs = [_f64(x).reshape(-1) for x in xs]
+    coef = _f64(coef)
+    n = xs[0].size
+    y = np.empty(n)
+    arr = (_dp * len(xs))(*[_p(x) for x in xs])
+    st = lib().orc_axpy(n, len(xs), _p(coef), arr, _p(y))
+    if st:
+        raise ValueError("nterms must be in 1..15")
+    return y
+
+
+# --------------------------------------------------------------------------
+# 3D periodic convolution (surrogate)
+# --------------------------------------------------------------------------
+def conv3d_fwd(x, w, b=None):
+    """x: (D,H,W,Cin), w: (27,Cin,Cout) taps ordered (dz,dy,dx), b: (Cout,)."""
+    x = _f64(x)
+    w = _f64(w)
+    D, H, W, Cin = x.shape
+    Cout = w.shape[2]
+    y = np.empty((D, H, W, Cout))
+    lib().orc_conv3d_fwd(D, H, W, Cin, Cout, _p(x), _p(w), _p(_f64(b)) if b is not None else None, _p(y))
+    return y
+
+
+def conv3d_dgrad(dy, w):
+    dy = _f64(dy)
+    w = _f64(w)
+    D, H, W, Cout = dy.shape
+    Cin = w.shape[1]
+    dx = np.empty((D, H, W, Cin))
+    lib().orc_conv3d_dgrad(D, H, W, Cin, Cout, _p(dy), _p(w), _p(dx))
+    return dx
+
+
+def conv3d_wgrad(x, dy):
+    x = _f64(x)
+    dy = _f64(dy)
+    D, H, W, Cin = x.shape
+    Cout = dy.shape[3]
+    dw = np.empty((27, Cin, Cout))
+    db = np.empty(Cout)
+    lib().orc_conv3d_wgrad(D, H, W, Cin, Cout, _p(x), _p(dy), _p(dw), _p(db))
+    return dw, db
+
+
+# --------------------------------------------------------------------------
+# Error norms of the accuracy benchmarks (section "Accuracy Benchmarks")
+# --------------------------------------------------------------------------
+def linf(e):
+    return float(np.max(np.abs(np.asarray(e, dtype=np.float64))))
+
+
+def l2(e):
+    e = np.asarray(e, dtype=np.float64).reshape(-1)
+    return float(np.sqrt(np.sum(e * e)))
+
+
+def rel_l2(a, b):
+    """||a - b||_2 / ||b||_2 over all components, a and b sequences of arrays."""
+    if not isinstance(a, (list, tuple)):
+        a, b = [a], [b]
+    num = sum(float(np.sum((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2)) for x, y in zip(a, b))
+    den = sum(float(np.sum(np.asarray(y, np.float64) ** 2)) for y in b)
+    return float(np.sqrt(num / den))

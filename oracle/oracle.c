@@ -1,0 +1,533 @@
+/*
+ * oracle.c -- plain, slow, single-threaded CPU reference (IEEE FP64) for
+ * explicit time stepping of du/dt = F(t,u), u(0) = u0 (paper, Introduction).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may include, link,
+ * load or call this file: only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg use it.  It shares no code with the CUDA library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no FMA
+ * contraction), so every operation below is one correctly rounded IEEE op in
+ * the order written.
+ *
+ * Contents, each following the passage cited at its definition:
+ *   - right-hand sides: the Gray-Scott system (Eq. 2, read with the System
+ *     functor of Listing 2 for the v-equation) on a periodic grid with the
+ *     7-point central Laplacian; pointwise ODEs dx/dt = -x and x(1-x); the
+ *     paper's exponential (Eq. 1a) and sigmoidal (Eq. 1b) families.
+ *   - explicit Runge-Kutta steppers of Table 1 (explicit Euler, RK4,
+ *     Dormand-Prince 5 with its embedded order-4 solution), as one generic
+ *     Butcher-tableau step: k_i = F(t + c_i dt, u + dt sum_j a_ij k_j),
+ *     u_new = u + dt sum_i b_i k_i, err = dt sum_i (b_i - bhat_i) k_i.
+ *   - the error-controlled adaptive driver (section "Architecture and
+ *     nomenclature of Boost Odeint": error stepper + L-infinity norm + step
+ *     size controller).  The paper gives no controller formula; the reading
+ *     used here is stated at orc_integrate_adaptive.
+ *   - the Adams-Bashforth 4 multistep method (Table 1) started by RK4.
+ *   - the n-ary stage algebra y = sum_j a_j x_j (section "The distributed
+ *     OpenFPM state type and algebra", for_each operations, up to 15 terms).
+ *   - 3D periodic convolution forward / input-gradient / weight-gradient for
+ *     the learned surrogate, by their definitions (plain loops).
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Butcher tableaux (Table 1).  a is s x s row-major, strictly lower.        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int s;
+    double a[13 * 13];
+    double b[13];
+    double bhat[13]; /* embedded lower-order weights; valid if has_bhat */
+    double c[13];
+    int has_bhat;
+} orc_tableau;
+
+enum { ORC_EULER = 0, ORC_RK4 = 1, ORC_DOPRI5 = 2 };
+
+/* Fills tableau T for method id; returns 0 on success. */
+int orc_get_tableau(int id, orc_tableau* T) {
+    memset(T, 0, sizeof(*T));
+    if (id == ORC_EULER) {
+        /* explicit Euler: one stage, b = 1 */
+        T->s = 1;
+        T->b[0] = 1.0;
+        T->c[0] = 0.0;
+        return 0;
+    }
+    if (id == ORC_RK4) {
+        /* classical Runge-Kutta 4: c = (0, 1/2, 1/2, 1), b = (1,2,2,1)/6 */
+        T->s = 4;
+        T->a[1 * 4 + 0] = 0.5;
+        T->a[2 * 4 + 1] = 0.5;
+        T->a[3 * 4 + 2] = 1.0;
+        T->b[0] = 1.0 / 6.0; T->b[1] = 1.0 / 3.0; T->b[2] = 1.0 / 3.0; T->b[3] = 1.0 / 6.0;
+        T->c[0] = 0.0; T->c[1] = 0.5; T->c[2] = 0.5; T->c[3] = 1.0;
+        return 0;
+    }
+    if (id == ORC_DOPRI5) {
+        /* Dormand & Prince (1980) RK5(4)7M.  Row 7 equals b (first same as
+         * last); bhat is the embedded order-4 solution. */
+        const int s = 7;
+        double* a = T->a;
+        T->s = s;
+        T->c[0] = 0.0; T->c[1] = 1.0 / 5.0; T->c[2] = 3.0 / 10.0; T->c[3] = 4.0 / 5.0;
+        T->c[4] = 8.0 / 9.0; T->c[5] = 1.0; T->c[6] = 1.0;
+        a[1 * s + 0] = 1.0 / 5.0;
+        a[2 * s + 0] = 3.0 / 40.0;        a[2 * s + 1] = 9.0 / 40.0;
+        a[3 * s + 0] = 44.0 / 45.0;       a[3 * s + 1] = -56.0 / 15.0;    a[3 * s + 2] = 32.0 / 9.0;
+        a[4 * s + 0] = 19372.0 / 6561.0;  a[4 * s + 1] = -25360.0 / 2187.0;
+        a[4 * s + 2] = 64448.0 / 6561.0;  a[4 * s + 3] = -212.0 / 729.0;
+        a[5 * s + 0] = 9017.0 / 3168.0;   a[5 * s + 1] = -355.0 / 33.0;   a[5 * s + 2] = 46732.0 / 5247.0;
+        a[5 * s + 3] = 49.0 / 176.0;      a[5 * s + 4] = -5103.0 / 18656.0;
+        a[6 * s + 0] = 35.0 / 384.0;      a[6 * s + 1] = 0.0;             a[6 * s + 2] = 500.0 / 1113.0;
+        a[6 * s + 3] = 125.0 / 192.0;     a[6 * s + 4] = -2187.0 / 6784.0; a[6 * s + 5] = 11.0 / 84.0;
+        T->b[0] = 35.0 / 384.0; T->b[1] = 0.0; T->b[2] = 500.0 / 1113.0; T->b[3] = 125.0 / 192.0;
+        T->b[4] = -2187.0 / 6784.0; T->b[5] = 11.0 / 84.0; T->b[6] = 0.0;
+        T->bhat[0] = 5179.0 / 57600.0; T->bhat[1] = 0.0; T->bhat[2] = 7571.0 / 16695.0;
+        T->bhat[3] = 393.0 / 640.0; T->bhat[4] = -92097.0 / 339200.0; T->bhat[5] = 187.0 / 2100.0;
+        T->bhat[6] = 1.0 / 40.0;
+        T->has_bhat = 1;
+        return 0;
+    }
+    return 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Right-hand sides F(t, y)                                                  */
+/* ------------------------------------------------------------------------ */
+
+typedef void (*orc_rhs_fn)(const void* sys, double t, long n, const double* y, double* f);
+
+/* Gray-Scott system (Eq. 2 with the v-equation of Listing 2):
+ *   du/dt = Du Lap(u) - u v^2 + F (1 - u)
+ *   dv/dt = Dv Lap(v) + u v^2 - (F + k) v
+ * on an nx*ny*nz periodic grid, spacing h_d = L_d / n_d, and the 7-point
+ * central Laplacian Lap(w)_i = sum_d (w_{i+e_d} - 2 w_i + w_{i-e_d}) / h_d^2.
+ * State vector y = [u (N values); v (N values)], cell index x + nx (y + ny z). */
+typedef struct {
+    int nx, ny, nz;
+    double Lx, Ly, Lz;
+    double Du, Dv, F, k;
+} orc_gs;
+
+static double orc_lap(const orc_gs* p, const double* w, int x, int y, int z) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const double hx = p->Lx / nx, hy = p->Ly / ny, hz = p->Lz / nz;
+    const int xm = (x + nx - 1) % nx, xp = (x + 1) % nx;
+    const int ym = (y + ny - 1) % ny, yp = (y + 1) % ny;
+    const int zm = (z + nz - 1) % nz, zp = (z + 1) % nz;
+#define ORC_AT(X, Y, Z) w[(long)(X) + (long)nx * ((long)(Y) + (long)ny * (long)(Z))]
+    const double c = ORC_AT(x, y, z);
+    const double lx = (ORC_AT(xm, y, z) - 2.0 * c + ORC_AT(xp, y, z)) / (hx * hx);
+    const double ly = (ORC_AT(x, ym, z) - 2.0 * c + ORC_AT(x, yp, z)) / (hy * hy);
+    const double lz = (ORC_AT(x, y, zm) - 2.0 * c + ORC_AT(x, y, zp)) / (hz * hz);
+#undef ORC_AT
+    return lx + ly + lz;
+}
+
+/* Lap(w) for a whole field (exported for the Laplacian pins). */
+void orc_gs_laplacian(const orc_gs* p, const double* w, double* out) {
+    for (int z = 0; z < p->nz; ++z)
+        for (int y = 0; y < p->ny; ++y)
+            for (int x = 0; x < p->nx; ++x)
+                out[(long)x + (long)p->nx * ((long)y + (long)p->ny * z)] = orc_lap(p, w, x, y, z);
+}
+
+void orc_gs_rhs(const void* sys, double t, long n, const double* y, double* f) {
+    (void)t;
+    const orc_gs* p = (const orc_gs*)sys;
+    const long N = (long)p->nx * p->ny * p->nz;
+    (void)n; /* n == 2N */
+    const double* u = y;
+    const double* v = y + N;
+    for (int z = 0; z < p->nz; ++z)
+        for (int yy = 0; yy < p->ny; ++yy)
+            for (int x = 0; x < p->nx; ++x) {
+                const long i = (long)x + (long)p->nx * ((long)yy + (long)p->ny * z);
+                const double uvv = u[i] * v[i] * v[i];
+                f[i] = p->Du * orc_lap(p, u, x, yy, z) - uvv + p->F * (1.0 - u[i]);
+                f[N + i] = p->Dv * orc_lap(p, v, x, yy, z) + uvv - (p->F + p->k) * v[i];
+            }
+}
+
+/* Pointwise families.  kind 0: dx/dt = -x.  kind 1: dx/dt = x (1 - x).
+ * kind 2: the exponential family of Eq. 1a, du/dt = c_i e^t, c_i = x_i y_i
+ * given per element in coef.  kind 3: the sigmoidal family of Eq. 1b,
+ * du/dt = s(t) (1 - s(t)), s(t) = 1 / (1 + e^-t). */
+typedef struct {
+    int kind;
+    const double* coef;
+} orc_pointwise;
+
+void orc_pointwise_rhs(const void* sys, double t, long n, const double* y, double* f) {
+    const orc_pointwise* p = (const orc_pointwise*)sys;
+    for (long i = 0; i < n; ++i) {
+        switch (p->kind) {
+            case 0: f[i] = -y[i]; break;
+            case 1: f[i] = y[i] * (1.0 - y[i]); break;
+            case 2: f[i] = p->coef[i] * exp(t); break;
+            default: {
+                const double s = 1.0 / (1.0 + exp(-t));
+                f[i] = s * (1.0 - s);
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Stage algebra: y = sum_j a_j x_j over n elements (the for_each operations */
+/* of the custom Algebra, up to 15 operands).                               */
+/* ------------------------------------------------------------------------ */
+int orc_axpy(long n, int nterms, const double* a, const double* const* x, double* y) {
+    if (nterms < 1 || nterms > 15) return 1;
+    for (long i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < nterms; ++j) s += a[j] * x[j][i];
+        y[i] = s;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One explicit Runge-Kutta step with tableau T.                              */
+/*   k_i  = F(t + c_i dt, y + dt * sum_{j<i} a_ij k_j)                        */
+/*   yout = y + dt * sum_i b_i k_i                                            */
+/*   err  = dt * sum_i (b_i - bhat_i) k_i        (if err != NULL)             */
+/* k: s*n scratch (k_i at k + i*n), ytmp: n scratch.  yout may alias y.      */
+/* ------------------------------------------------------------------------ */
+void orc_rk_step(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, double t, double dt,
+                 const double* y, double* yout, double* err, double* k, double* ytmp) {
+    const int s = T->s;
+    for (int i = 0; i < s; ++i) {
+        for (long e = 0; e < n; ++e) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc += T->a[i * s + j] * k[(long)j * n + e];
+            ytmp[e] = y[e] + dt * acc;
+        }
+        F(sys, t + T->c[i] * dt, n, ytmp, k + (long)i * n);
+    }
+    if (err) {
+        for (long e = 0; e < n; ++e) {
+            double acc = 0.0;
+            for (int i = 0; i < s; ++i) acc += (T->b[i] - T->bhat[i]) * k[(long)i * n + e];
+            err[e] = dt * acc;
+        }
+    }
+    for (long e = 0; e < n; ++e) {
+        double acc = 0.0;
+        for (int i = 0; i < s; ++i) acc += T->b[i] * k[(long)i * n + e];
+        yout[e] = y[e] + dt * acc;
+    }
+}
+
+/* integrate_const (Listing 3): nsteps fixed steps, t_m = t0 + m dt. */
+int orc_integrate_const(int method, orc_rhs_fn F, const void* sys, long n, double* y, double t0,
+                        double dt, long nsteps) {
+    orc_tableau T;
+    if (orc_get_tableau(method, &T)) return 1;
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!k || !ytmp) { free(k); free(ytmp); return 3; }
+    for (long m = 0; m < nsteps; ++m)
+        orc_rk_step(&T, F, sys, n, t0 + (double)m * dt, dt, y, y, NULL, k, ytmp);
+    free(k);
+    free(ytmp);
+    return 0;
+}
+
+/* Fixed steps of a given dt sequence (replay of an adaptive run's accepted
+ * steps): t advances by each dt in turn. */
+int orc_integrate_replay(int method, orc_rhs_fn F, const void* sys, long n, double* y, double t0,
+                         const double* dts, long nsteps) {
+    orc_tableau T;
+    if (orc_get_tableau(method, &T)) return 1;
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!k || !ytmp) { free(k); free(ytmp); return 3; }
+    double t = t0;
+    for (long m = 0; m < nsteps; ++m) {
+        orc_rk_step(&T, F, sys, n, t, dts[m], y, y, NULL, k, ytmp);
+        t += dts[m];
+    }
+    free(k);
+    free(ytmp);
+    return 0;
+}
+
+/* One error-stepper attempt: yout, and the scaled L-infinity error norm
+ *   E = max_e |err_e| / (atol + rtol (|y_e| + dt |k1_e|))
+ * (section "Architecture and nomenclature of Boost Odeint": the norm is
+ * usually the L-infinity norm; the scaling by the state and its derivative
+ * is this build's reading).  Returns E. */
+double orc_error_attempt(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, double t,
+                         double dt, const double* y, double* yout, double atol, double rtol,
+                         double* err, double* k, double* ytmp) {
+    orc_rk_step(T, F, sys, n, t, dt, y, yout, err, k, ytmp);
+    double E = 0.0;
+    for (long e = 0; e < n; ++e) {
+        const double sc = atol + rtol * (fabs(y[e]) + dt * fabs(k[e]));
+        const double r = fabs(err[e]) / sc;
+        if (isnan(E)) continue;             /* a NaN ratio, once seen, stays */
+        if (isnan(r) || r > E) E = r;
+    }
+    return E;
+}
+
+/* Status codes (same meaning as the library's). */
+enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 3, ORC_ERR_STEP_UNDERFLOW = 4,
+       ORC_ERR_MAX_STEPS = 5, ORC_ERR_NONFINITE = 6 };
+
+/* integrate_adaptive with Dormand-Prince 5(4).
+ *
+ * The paper states only that adaptive steppers size each step from an error
+ * estimate and a tolerance, with an L-infinity norm.  The controller read
+ * here (error order q = 4, stepper order p = 5):
+ *   attempt size h = dt, clipped to t_end - t if t + dt >= t_end;
+ *   E > 1            : reject; dt = h * max(0.9 E^(-1/(q-1)), 0.2)
+ *   E < 0.5          : accept; dt = h * 0.9 * max(E, 5^-p)^(-1/p)
+ *   0.5 <= E <= 1    : accept; dt = h
+ *   E not finite     : stop with NONFINITE
+ *   max_rej consecutive rejections, or t + h == t: stop with STEP_UNDERFLOW.
+ * On accept t += h (t = t_end exactly on a clipped step).  The loop ends when
+ * t reaches t_end or after max_acc accepted steps (max_acc < 0: no limit).
+ * If log_dt != NULL the accepted step sizes are written there (up to log_cap).
+ */
+int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
+                           double t_end, double* dt_io, double atol, double rtol, long max_acc,
+                           long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
+                           long log_cap) {
+    orc_tableau T;
+    orc_get_tableau(ORC_DOPRI5, &T);
+    const int s = T.s;
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    double* ynew = (double*)malloc(sizeof(double) * (size_t)n);
+    double* err = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!k || !ytmp || !ynew || !err) { free(k); free(ytmp); free(ynew); free(err); return ORC_ERR_NOMEM; }
+    double t = *t_io, dt = *dt_io;
+    long n_acc = 0, n_rej = 0, consec = 0;
+    int status = ORC_OK;
+    while (t < t_end && (max_acc < 0 || n_acc < max_acc)) {
+        int last = 0;
+        double h = dt;
+        if (t + dt >= t_end) { h = t_end - t; last = 1; }
+        if (!(h > 0.0) || t + h == t) { status = ORC_ERR_STEP_UNDERFLOW; break; }
+        const double E = orc_error_attempt(&T, F, sys, n, t, h, y, ynew, atol, rtol, err, k, ytmp);
+        if (!isfinite(E)) { status = ORC_ERR_NONFINITE; break; }
+        if (E > 1.0) {
+            ++n_rej; ++consec;
+            double fac = 0.9 * pow(E, -1.0 / 3.0);
+            if (fac < 0.2) fac = 0.2;
+            dt = h * fac;
+            if (consec >= max_rej) { status = ORC_ERR_STEP_UNDERFLOW; break; }
+            continue;
+        }
+        consec = 0;
+        memcpy(y, ynew, sizeof(double) * (size_t)n);
+        if (log_dt && n_acc < log_cap) log_dt[n_acc] = h;
+        ++n_acc;
+        t = last ? t_end : t + h;
+        if (E < 0.5) {
+            double Em = E;
+            const double floor5 = pow(5.0, -5.0);
+            if (Em < floor5) Em = floor5;
+            dt = h * 0.9 * pow(Em, -1.0 / 5.0);
+        } else {
+            dt = h;
+        }
+    }
+    *t_io = t;
+    *dt_io = dt;
+    if (n_acc_out) *n_acc_out = n_acc;
+    if (n_rej_out) *n_rej_out = n_rej;
+    free(k); free(ytmp); free(ynew); free(err);
+    return status;
+}
+
+/* Adams-Bashforth 4 (Table 1, multi-step), started with three RK4 steps:
+ *   u_{m+1} = u_m + dt/24 (55 f_m - 59 f_{m-1} + 37 f_{m-2} - 9 f_{m-3}),
+ * f_m = F(t_m, u_m), t_m = t0 + m dt.  nsteps counts all steps, the RK4
+ * start-up steps included. */
+int orc_integrate_ab4(orc_rhs_fn F, const void* sys, long n, double* y, double t0, double dt,
+                      long nsteps) {
+    orc_tableau T;
+    orc_get_tableau(ORC_RK4, &T);
+    double* f = (double*)malloc(sizeof(double) * (size_t)n * 4); /* f_m, f_{m-1}, f_{m-2}, f_{m-3} */
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * 4);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!f || !k || !ytmp) { free(f); free(k); free(ytmp); return ORC_ERR_NOMEM; }
+    double* fm[4] = {f, f + n, f + 2 * n, f + 3 * n}; /* fm[j] = f_{m-j} */
+    for (long m = 0; m < nsteps; ++m) {
+        const double t = t0 + (double)m * dt;
+        /* rotate history: f_{m-j} <- f_{m-j+1} */
+        double* oldest = fm[3];
+        fm[3] = fm[2]; fm[2] = fm[1]; fm[1] = fm[0]; fm[0] = oldest;
+        F(sys, t, n, y, fm[0]);
+        if (m < 3) {
+            orc_rk_step(&T, F, sys, n, t, dt, y, y, NULL, k, ytmp);
+        } else {
+            for (long e = 0; e < n; ++e)
+                y[e] = y[e] + dt / 24.0 * (55.0 * fm[0][e] - 59.0 * fm[1][e] + 37.0 * fm[2][e] -
+                                           9.0 * fm[3][e]);
+        }
+    }
+    free(f); free(k); free(ytmp);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Convenience entry points with concrete systems (for ctypes).             */
+/* ------------------------------------------------------------------------ */
+void orc_gs_rhs_full(const orc_gs* p, const double* y, double* f) {
+    orc_gs_rhs(p, 0.0, 2L * p->nx * p->ny * p->nz, y, f);
+}
+int orc_gs_integrate_const(const orc_gs* p, int method, double* y, double t0, double dt, long nsteps) {
+    return orc_integrate_const(method, orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t0, dt, nsteps);
+}
+int orc_gs_integrate_replay(const orc_gs* p, int method, double* y, double t0, const double* dts,
+                            long nsteps) {
+    return orc_integrate_replay(method, orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t0, dts, nsteps);
+}
+int orc_gs_integrate_adaptive(const orc_gs* p, double* y, double* t, double t_end, double* dt,
+                              double atol, double rtol, long max_acc, long max_rej, long* n_acc,
+                              long* n_rej, double* log_dt, long log_cap) {
+    return orc_integrate_adaptive(orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t, t_end, dt, atol,
+                                  rtol, max_acc, max_rej, n_acc, n_rej, log_dt, log_cap);
+}
+int orc_gs_integrate_ab4(const orc_gs* p, double* y, double t0, double dt, long nsteps) {
+    return orc_integrate_ab4(orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t0, dt, nsteps);
+}
+/* One Dopri5 attempt on the GS system: yout, err and the scaled norm. */
+double orc_gs_dopri5_attempt(const orc_gs* p, double t, double dt, const double* y, double* yout,
+                             double* err, double atol, double rtol) {
+    orc_tableau T;
+    orc_get_tableau(ORC_DOPRI5, &T);
+    const long n = 2L * p->nx * p->ny * p->nz;
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    double E = NAN;
+    if (k && ytmp) E = orc_error_attempt(&T, orc_gs_rhs, p, n, t, dt, y, yout, atol, rtol, err, k, ytmp);
+    free(k); free(ytmp);
+    return E;
+}
+
+void orc_pw_rhs(int kind, const double* coef, double t, long n, const double* y, double* f) {
+    orc_pointwise p = {kind, coef};
+    orc_pointwise_rhs(&p, t, n, y, f);
+}
+int orc_pw_integrate_const(int kind, const double* coef, int method, long n, double* y, double t0,
+                           double dt, long nsteps) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_const(method, orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
+}
+int orc_pw_integrate_replay(int kind, const double* coef, int method, long n, double* y, double t0,
+                            const double* dts, long nsteps) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_replay(method, orc_pointwise_rhs, &p, n, y, t0, dts, nsteps);
+}
+int orc_pw_integrate_adaptive(int kind, const double* coef, long n, double* y, double* t,
+                              double t_end, double* dt, double atol, double rtol, long max_acc,
+                              long max_rej, long* n_acc, long* n_rej, double* log_dt, long log_cap) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_adaptive(orc_pointwise_rhs, &p, n, y, t, t_end, dt, atol, rtol, max_acc,
+                                  max_rej, n_acc, n_rej, log_dt, log_cap);
+}
+int orc_pw_integrate_ab4(int kind, const double* coef, long n, double* y, double t0, double dt,
+                         long nsteps) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_ab4(orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
+}
+/* One Dopri5 attempt on a pointwise system: yout, err, returns the norm. */
+double orc_pw_dopri5_attempt(int kind, const double* coef, long n, double t, double dt,
+                             const double* y, double* yout, double* err, double atol, double rtol) {
+    orc_pointwise p = {kind, coef};
+    orc_tableau T;
+    orc_get_tableau(ORC_DOPRI5, &T);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    double E = NAN;
+    if (k && ytmp) E = orc_error_attempt(&T, orc_pointwise_rhs, &p, n, t, dt, y, yout, atol, rtol, err, k, ytmp);
+    free(k); free(ytmp);
+    return E;
+}
+
+/* ------------------------------------------------------------------------ */
+/* 3D periodic convolution (learned surrogate), plain loops, FP64.          */
+/* Activations: channels-last [D][H][W][C] with x = W fastest over cells.    */
+/* Weights: [3][3][3][Cin][Cout] indexed by offsets (dz,dy,dx) in {-1,0,1}.  */
+/*   y[z,y,x,o] = b[o] + sum_{dz,dy,dx,i} w[dz+1,dy+1,dx+1,i,o]              */
+/*                                  * x[(z+dz)%D, (y+dy)%H, (x+dx)%W, i]     */
+/* ------------------------------------------------------------------------ */
+static long orc_wrap(long a, long n) { return ((a % n) + n) % n; }
+
+void orc_conv3d_fwd(int D, int H, int W, int Cin, int Cout, const double* x, const double* w,
+                    const double* b, double* y) {
+    for (long z = 0; z < D; ++z)
+        for (long yy = 0; yy < H; ++yy)
+            for (long xx = 0; xx < W; ++xx)
+                for (int o = 0; o < Cout; ++o) {
+                    double acc = b ? b[o] : 0.0;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dy = -1; dy <= 1; ++dy)
+                            for (int dx = -1; dx <= 1; ++dx) {
+                                const long zz = orc_wrap(z + dz, D), y2 = orc_wrap(yy + dy, H), x2 = orc_wrap(xx + dx, W);
+                                const long tap = (long)((dz + 1) * 9 + (dy + 1) * 3 + (dx + 1));
+                                for (int i = 0; i < Cin; ++i)
+                                    acc += w[(tap * Cin + i) * Cout + o] *
+                                           x[((zz * H + y2) * W + x2) * Cin + i];
+                            }
+                    y[((z * H + yy) * W + xx) * Cout + o] = acc;
+                }
+}
+
+/* dL/dx given dL/dy: each input cell collects from the outputs it fed. */
+void orc_conv3d_dgrad(int D, int H, int W, int Cin, int Cout, const double* dy, const double* w,
+                      double* dx) {
+    for (long z = 0; z < D; ++z)
+        for (long yy = 0; yy < H; ++yy)
+            for (long xx = 0; xx < W; ++xx)
+                for (int i = 0; i < Cin; ++i) {
+                    double acc = 0.0;
+                    for (int dz = -1; dz <= 1; ++dz)
+                        for (int dyo = -1; dyo <= 1; ++dyo)
+                            for (int dxo = -1; dxo <= 1; ++dxo) {
+                                /* output cell q = p - offset used input p at offset */
+                                const long zz = orc_wrap(z - dz, D), y2 = orc_wrap(yy - dyo, H), x2 = orc_wrap(xx - dxo, W);
+                                const long tap = (long)((dz + 1) * 9 + (dyo + 1) * 3 + (dxo + 1));
+                                for (int o = 0; o < Cout; ++o)
+                                    acc += w[(tap * Cin + i) * Cout + o] *
+                                           dy[((zz * H + y2) * W + x2) * Cout + o];
+                            }
+                    dx[((z * H + yy) * W + xx) * Cin + i] = acc;
+                }
+}
+
+/* dL/dw and dL/db given dL/dy (sums over all cells). */
+void orc_conv3d_wgrad(int D, int H, int W, int Cin, int Cout, const double* x, const double* dy,
+                      double* dw, double* db) {
+    for (long tap = 0; tap < 27; ++tap) {
+        const int dz = (int)(tap / 9) - 1, dyo = (int)((tap / 3) % 3) - 1, dxo = (int)(tap % 3) - 1;
+        for (int i = 0; i < Cin; ++i)
+            for (int o = 0; o < Cout; ++o) {
+                double acc = 0.0;
+                for (long z = 0; z < D; ++z)
+                    for (long yy = 0; yy < H; ++yy)
+                        for (long xx = 0; xx < W; ++xx) {
+                            const long zz = orc_wrap(z + dz, D), y2 = orc_wrap(yy + dyo, H), x2 = orc_wrap(xx + dxo, W);
+                            acc += x[((zz * H + y2) * W + x2) * Cin + i] *
+                                   dy[((z * H + yy) * W + xx) * Cout + o];
+                        }
+                dw[(tap * Cin + i) * Cout + o] = acc;
+            }
+    }
+    if (db)
+        for (int o = 0; o < Cout; ++o) {
+            double acc = 0.0;
+            for (long c = 0; c < (long)D * H * W; ++c) acc += dy[c * Cout + o];
+            db[o] = acc;
+        }
+}

@@ -1,0 +1,156 @@
+"""Pins for the oracle's Gray-Scott system (Eq. 2, Listing 2) and its
+integrators, against closed forms of the mathematics.
+
+* 7-point periodic Laplacian: Fourier modes are eigenvectors with eigenvalue
+  -sum_d (4/h_d^2) sin^2(pi m_d / n_d) (anisotropic grids, odd sizes), and
+  the sum over the periodic grid of Lap(w) is zero.
+* Reaction: u=1, v=0 and the two uniform nontrivial steady states
+  v = (F +- sqrt(F^2 - 4F(F+k)^2)) / (2(F+k)), u = (F+k)/v are fixed points.
+* Linear sub-case v = 0, u = 1 + eps*mode: u - 1 obeys w' = lambda w with
+  lambda = -(Du mu + F), so n steps of a Runge-Kutta method give exactly
+  R(lambda dt)^n (R the stability polynomial).
+* Symmetry of the noiseless cube initial state under axis permutations and
+  reflections.
+* Self-convergence order of RK4 / Dopri5 on the full nonlinear problem.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+
+
+def _mode(p, m):
+    z, y, x = np.meshgrid(np.arange(p.nz), np.arange(p.ny), np.arange(p.nx), indexing="ij")
+    return np.cos(2 * np.pi * (m[0] * x / p.nx + m[1] * y / p.ny + m[2] * z / p.nz))
+
+
+def _mu(p, m):
+    h = (p.Lx / p.nx, p.Ly / p.ny, p.Lz / p.nz)
+    n = (p.nx, p.ny, p.nz)
+    return sum(4.0 / h[d] ** 2 * math.sin(math.pi * m[d] / n[d]) ** 2 for d in range(3))
+
+
+@pytest.mark.parametrize("dims,m", [((8, 8, 8), (1, 2, 3)), ((9, 6, 5), (2, 1, 2)),
+                                    ((16, 4, 7), (5, 0, 3)), ((3, 1, 2), (1, 0, 1))])
+def test_laplacian_fourier_eigenvalues(dims, m):
+    p = oracle.GSParams(*dims, L=2.5, Ly=1.7, Lz=3.1)
+    w = _mode(p, m)
+    lap = oracle.gs_laplacian(p, w)
+    assert np.allclose(lap, -_mu(p, m) * w, atol=1e-9 * _mu(p, m), rtol=0)
+
+
+def test_laplacian_sums_to_zero():
+    p = oracle.GSParams(7, 5, 6)
+    rng = np.random.default_rng(0)
+    w = rng.standard_normal((6, 5, 7))
+    lap = oracle.gs_laplacian(p, w)
+    scale = np.max(np.abs(lap))
+    assert abs(lap.sum()) < 1e-12 * scale * lap.size
+
+
+def _steady_states(F, k):
+    disc = F * F - 4 * F * (F + k) ** 2
+    out = [(1.0, 0.0)]
+    if disc > 0:
+        for sgn in (+1, -1):
+            v = (F + sgn * math.sqrt(disc)) / (2 * (F + k))
+            out.append(((F + k) / v, v))
+    return out
+
+
+@pytest.mark.parametrize("F,k", [(0.053, 0.014), (0.03, 0.05), (0.05, 0.055)])
+def test_uniform_steady_states_are_fixed_points(F, k):
+    p = oracle.GSParams(4, 3, 5, F=F, k=k)
+    sts = _steady_states(F, k)
+    assert len(sts) == 3
+    for (us, vs) in sts:
+        u = np.full((5, 3, 4), us)
+        v = np.full((5, 3, 4), vs)
+        fu, fv = oracle.gs_rhs(p, u, v)
+        assert np.max(np.abs(fu)) < 1e-15 and np.max(np.abs(fv)) < 1e-15
+    # a perturbed uniform state is not a fixed point (the test can fail)
+    fu, fv = oracle.gs_rhs(p, np.full((5, 3, 4), 0.9), np.full((5, 3, 4), 0.1))
+    assert np.max(np.abs(fu)) > 1e-4
+
+
+def _R(method, z):
+    if method == oracle.RK4:
+        return sum(z ** j / math.factorial(j) for j in range(5))
+    return sum(z ** j / math.factorial(j) for j in range(6)) + z ** 6 / 600.0
+
+
+@pytest.mark.parametrize("method", [oracle.RK4, oracle.DOPRI5])
+def test_linear_subcase_exact_discrete_solution(method):
+    # large diffusivity so the Laplacian term matters at this dt
+    p = oracle.GSParams(8, 6, 10, L=2.5, Ly=2.0, Lz=3.0, Du=2e-2, Dv=1e-2, F=0.053, k=0.014)
+    m = (1, 2, 3)
+    eps = 1e-3
+    mode = _mode(p, m)
+    u0 = 1.0 + eps * mode
+    v0 = np.zeros_like(u0)
+    dt, n = 0.1, 25
+    u, v = oracle.gs_integrate_const(p, u0, v0, method, dt, n)
+    lam = -(p.Du * _mu(p, m) + p.F)
+    expect = 1.0 + eps * _R(method, lam * dt) ** n * mode
+    assert np.array_equal(v, np.zeros_like(v))
+    assert np.max(np.abs(u - expect)) < 1e-14
+
+
+def test_noiseless_cube_symmetries():
+    n = 16
+    p = oracle.GSParams(n, n, n, Du=2e-3, Dv=1e-3)
+    u0, v0 = si.gs_initial_state(n, n, n, noise=0.0)
+    u, v = oracle.gs_integrate_const(p, u0, v0, oracle.RK4, 0.5, 6)
+    for w in (u, v):
+        assert np.max(np.abs(w - np.transpose(w, (1, 0, 2)))) < 1e-14
+        assert np.max(np.abs(w - np.transpose(w, (2, 1, 0)))) < 1e-14
+        # cube [6,10) is symmetric under i -> n-1-i
+        assert np.max(np.abs(w - w[::-1, :, :])) < 1e-14
+        assert np.max(np.abs(w - w[:, :, ::-1])) < 1e-14
+    # the dynamics moved the state (the symmetry test is not vacuous)
+    assert np.max(np.abs(u - u0)) > 1e-3
+
+
+@pytest.mark.parametrize("method,order", [(oracle.RK4, 4), (oracle.DOPRI5, 5)])
+def test_gs_self_convergence(method, order):
+    n = 8
+    p = oracle.GSParams(n, n, n, Du=2e-3, Dv=1e-3)
+    u0, v0 = si.gs_initial_state(n, n, n, seed=5)
+    T = 4.0
+    sols = [oracle.gs_integrate_const(p, u0, v0, method, T / m, m) for m in (4, 8, 16)]
+    e1 = oracle.rel_l2(list(sols[0]), list(sols[1]))
+    e2 = oracle.rel_l2(list(sols[1]), list(sols[2]))
+    assert abs(math.log2(e1 / e2) - order) < 0.5, (e1, e2)
+
+
+def test_gs_ab4_self_convergence():
+    n = 8
+    p = oracle.GSParams(n, n, n, Du=2e-3, Dv=1e-3)
+    u0, v0 = si.gs_initial_state(n, n, n, seed=6)
+    T = 4.0
+    sols = [oracle.gs_integrate_ab4(p, u0, v0, T / m, m) for m in (16, 32, 64)]
+    e1 = oracle.rel_l2(list(sols[0]), list(sols[1]))
+    e2 = oracle.rel_l2(list(sols[1]), list(sols[2]))
+    assert abs(math.log2(e1 / e2) - 4) < 0.5, (e1, e2)
+
+
+def test_gs_uniform_state_reduces_to_reaction_ode():
+    # with no spatial variation the Laplacian vanishes and every cell follows
+    # the same reaction ODE; compare with scipy's DOP853 at tight tolerance on
+    # the rates read off the oracle's own RHS at the current state
+    from scipy.integrate import solve_ivp
+    p = oracle.GSParams(3, 4, 2)
+
+    def f(t, y):
+        fu, fv = oracle.gs_rhs(p, np.full((2, 4, 3), y[0]), np.full((2, 4, 3), y[1]))
+        return [fu[0, 0, 0], fv[0, 0, 0]]
+
+    y0 = [0.6, 0.3]
+    ref = solve_ivp(f, (0, 5), y0, method="DOP853", rtol=1e-13, atol=1e-15).y[:, -1]
+    u, v = oracle.gs_integrate_const(p, np.full((2, 4, 3), y0[0]), np.full((2, 4, 3), y0[1]),
+                                     oracle.RK4, 0.01, 500)
+    assert abs(u[0, 0, 0] - ref[0]) < 1e-9 and abs(v[0, 0, 0] - ref[1]) < 1e-9
+    assert np.ptp(u) == 0.0 and np.ptp(v) == 0.0

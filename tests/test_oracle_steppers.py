@@ -1,0 +1,213 @@
+"""Pins for the oracle's steppers (Table 1) against mathematics, not itself.
+
+* Butcher order conditions, generated from rooted trees (Butcher's theory of
+  order: sum_i b_i Phi_i(t) = 1/gamma(t) for every tree t with |t| <= p).
+* Stability polynomials R(z) of RK4 (sum_{k<=4} z^k/k!) and Dormand-Prince 5
+  (sum_{k<=5} z^k/k! + z^6/600, Hairer-Norsett-Wanner Vol. I): on dx/dt = -x
+  one step multiplies x by R(-dt) exactly.
+* Observed orders of convergence on closed-form solutions, as in the paper's
+  accuracy benchmarks (Fig. 2, Eq. 1a and 1b): Euler 1, RK4 4, Dopri5 5,
+  AB4 4; the embedded estimate's local error is O(dt^5).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+
+# ---------------------------------------------------------------- rooted trees
+def _trees(order):
+    """All rooted trees with `order` nodes, as sorted tuples of child subtrees."""
+    if order == 1:
+        return [()]
+    out = set()
+
+    def partitions(n, maxpart):
+        if n == 0:
+            yield []
+            return
+        for p in range(min(n, maxpart), 0, -1):
+            for rest in partitions(n - p, p):
+                yield [p] + rest
+
+    for parts in partitions(order - 1, order - 1):
+        # choose a tree for each part (multisets)
+        def build(idx, acc):
+            if idx == len(parts):
+                out.add(tuple(sorted(acc)))
+                return
+            for t in _trees(parts[idx]):
+                build(idx + 1, acc + [t])
+        build(0, [])
+    return sorted(out)
+
+
+def _size(t):
+    return 1 + sum(_size(c) for c in t)
+
+
+def _gamma(t):
+    g = _size(t)
+    for c in t:
+        g *= _gamma(c)
+    return g
+
+
+def _phi(t, A):
+    """Elementary weight vector Phi_i(t) = prod_children (A @ Phi(child))_i."""
+    s = A.shape[0]
+    v = np.ones(s)
+    for c in t:
+        v = v * (A @ _phi(c, A))
+    return v
+
+
+def test_tree_enumeration_counts():
+    # number of rooted trees: 1, 1, 2, 4, 9, 20 (OEIS A000081)
+    assert [len(_trees(n)) for n in range(1, 7)] == [1, 1, 2, 4, 9, 20]
+
+
+@pytest.mark.parametrize("method,weights,order", [
+    (oracle.EULER, "b", 1),
+    (oracle.RK4, "b", 4),
+    (oracle.DOPRI5, "b", 5),
+    (oracle.DOPRI5, "bhat", 4),
+])
+def test_order_conditions(method, weights, order):
+    T = oracle.tableau(method)
+    A, b = T["A"], T[weights]
+    # row-sum condition c_i = sum_j a_ij
+    assert np.allclose(A.sum(axis=1), T["c"], atol=1e-15, rtol=0)
+    for p in range(1, order + 1):
+        for t in _trees(p):
+            assert abs(b @ _phi(t, A) - 1.0 / _gamma(t)) < 1e-14, (p, t)
+    # and the method is NOT of the next order (some condition fails)
+    worst = max(abs(b @ _phi(t, A) - 1.0 / _gamma(t)) for t in _trees(order + 1))
+    assert worst > 1e-6
+
+
+def test_dopri5_fsal_and_error_weights():
+    T = oracle.tableau(oracle.DOPRI5)
+    A, b, bh = T["A"], T["b"], T["bhat"]
+    assert np.array_equal(A[6, :], b)  # last stage evaluates F at the new solution
+    assert abs(np.sum(b - bh)) < 1e-16
+
+
+# ------------------------------------------------------- stability polynomials
+def _R_rk4(z):
+    return sum(z ** k / math.factorial(k) for k in range(5))
+
+
+def _R_dopri5(z):
+    return sum(z ** k / math.factorial(k) for k in range(6)) + z ** 6 / 600.0
+
+
+@pytest.mark.parametrize("method,R", [(oracle.RK4, _R_rk4), (oracle.DOPRI5, _R_dopri5),
+                                      (oracle.EULER, lambda z: 1 + z)])
+def test_exact_discrete_solution_decay(method, R):
+    x0 = np.array([0.1, 0.5, 0.9, 1.7])
+    for dt in (0.05, 0.3, 1.0):
+        n = 20
+        x = oracle.pw_integrate_const(oracle.PW_EXP_DECAY, x0, method, dt, n)
+        expect = x0 * R(-dt) ** n
+        assert np.allclose(x, expect, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------------------ convergence order
+def _closed_form(kind, x0, t0, t1, coef=None):
+    if kind == oracle.PW_EXP_DECAY:
+        return x0 * np.exp(-(t1 - t0))
+    if kind == oracle.PW_LOGISTIC:
+        e = np.exp(-(t1 - t0))
+        return x0 / (x0 + (1 - x0) * e)
+    if kind == oracle.PW_PAPER_EXP:  # u = c e^t
+        return coef * np.exp(t1)
+    if kind == oracle.PW_PAPER_SIGMOID:  # u = sigma(t)
+        return 1.0 / (1.0 + np.exp(-t1))
+    raise ValueError
+
+
+def _family(kind):
+    """Initial data and interval of each benchmark family."""
+    if kind in (oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC):
+        x0 = np.linspace(0.05, 0.95, 7)
+        return x0, 0.0, 10.0, None
+    if kind == oracle.PW_PAPER_EXP:
+        # Eq. 1a on a 4x4 grid of (x, y) in [0,1]^2, t from -5 to 5
+        g = np.linspace(0.0, 1.0, 4)
+        coef = np.outer(g, g).reshape(-1)
+        return coef * np.exp(-5.0), -5.0, 5.0, coef
+    x0 = np.array([1.0 / (1.0 + np.exp(5.0))])
+    return x0, -5.0, 5.0, None
+
+
+@pytest.mark.parametrize("kind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP,
+                                  oracle.PW_PAPER_SIGMOID])
+@pytest.mark.parametrize("method,order,nbase", [(oracle.EULER, 1, 400), (oracle.RK4, 4, 40),
+                                                (oracle.DOPRI5, 5, 40)])
+def test_observed_order(kind, method, order, nbase):
+    x0, t0, t1, coef = _family(kind)
+    exact = _closed_form(kind, x0, t0, t1, coef)
+    errs = []
+    for m in (nbase, 2 * nbase):
+        dt = (t1 - t0) / m
+        x = oracle.pw_integrate_const(kind, x0, method, dt, m, t0=t0, coef=coef)
+        errs.append(oracle.linf(x - exact))
+    ratio = errs[0] / errs[1]
+    if kind == oracle.PW_PAPER_SIGMOID and order % 2 == 1:
+        # Eq. 1b is a quadrature of an even integrand over the symmetric
+        # interval [-5, 5].  A composite rule's error expands in terms
+        # dt^j (f^(j-1)(5) - f^(j-1)(-5)), which vanish for odd j: an odd
+        # order p shows as p + 1 (Euler 2, Dopri5 6).
+        order += 1
+    assert abs(math.log2(ratio) - order) < 0.35, (errs, ratio)
+
+
+@pytest.mark.parametrize("kind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP,
+                                  oracle.PW_PAPER_SIGMOID])
+def test_ab4_observed_order(kind):
+    x0, t0, t1, coef = _family(kind)
+    exact = _closed_form(kind, x0, t0, t1, coef)
+    errs = []
+    for m in (100, 200):
+        dt = (t1 - t0) / m
+        x = oracle.pw_integrate_ab4(kind, x0, dt, m, t0=t0, coef=coef)
+        errs.append(oracle.linf(x - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - 4) < 0.35, errs
+
+
+@pytest.mark.parametrize("kind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC])
+def test_embedded_error_estimate_is_local_order_5(kind):
+    x0 = np.array([0.2, 0.6, 0.8])
+    ests = []
+    for dt in (0.2, 0.1):
+        _, err, _ = oracle.pw_dopri5_attempt(kind, x0, dt, 1e-8, 1e-8)
+        ests.append(np.max(np.abs(err)))
+    assert abs(math.log2(ests[0] / ests[1]) - 5) < 0.3, ests
+
+
+def test_embedded_error_matches_difference_of_solutions():
+    # err = y5 - y4 where y4 uses bhat; on -x both are polynomials in z=-dt
+    x0 = np.array([1.0])
+    dt = 0.25
+    y5, err, _ = oracle.pw_dopri5_attempt(oracle.PW_EXP_DECAY, x0, dt, 1e-8, 1e-8)
+    T = oracle.tableau(oracle.DOPRI5)
+    # y4 = R_hat(z) x0 where R_hat(z) = 1 + z bhat^T (I - zA)^-1 1
+    z = -dt
+    I = np.eye(7)
+    Rhat = 1 + z * T["bhat"] @ np.linalg.solve(I - z * T["A"], np.ones(7))
+    assert abs(y5[0] - _R_dopri5(z)) < 1e-15
+    assert abs(err[0] - (_R_dopri5(z) - Rhat)) < 1e-15
+
+
+# ------------------------------------------------------------------- algebra
+def test_axpy_exact_and_limits():
+    xs = [np.arange(10.0) * (j + 1) for j in range(15)]
+    coef = np.array([(-1.0) ** j * (j + 1) for j in range(15)])
+    y = oracle.axpy(coef, xs)
+    expect = np.arange(10.0) * sum((-1) ** j * (j + 1) ** 2 for j in range(15))
+    assert np.array_equal(y, expect)
+    with pytest.raises(ValueError):
+        oracle.axpy(np.ones(16), [np.ones(3)] * 16)
