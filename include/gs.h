@@ -1,0 +1,216 @@
+/*
+ * gs.h -- C ABI of the B300 explicit time-stepping library (libgs_b300.so).
+ *
+ * The library integrates du/dt = F(t,u), u(0) = u0 (paper, Introduction) with
+ * the explicit steppers of Table 1 that are in scope here: fixed-step
+ * explicit Euler, Runge-Kutta 4 and Dormand-Prince 5, error-controlled
+ * Dormand-Prince 5(4), and Adams-Bashforth 4.  F is either the 3D Gray-Scott
+ * reaction-diffusion system (Eq. 2, with the v-equation as in the System
+ * functor of Listing 2) on a periodic grid with the 7-point central
+ * Laplacian, or a pointwise ODE applied to every element of a vector.
+ *
+ * Conventions shared by every entry point
+ *   - Device arrays are owned by the caller (e.g. PyTorch tensors); the
+ *     library never frees them.  Pointers named *_dev / state pointers are
+ *     device pointers; pointers named *_host are host pointers.
+ *   - Gray-Scott state: two arrays u and v (structure of arrays), each of
+ *     nx*ny*nz elements of the context's precision, cell (x,y,z) at index
+ *     x + nx*(y + ny*z) (x fastest), 16-byte aligned.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued on it; calls that return host-side results (t, dt, step
+ *     counts, norms) synchronise that stream before returning.
+ *   - Every call returns a gs_status and never aborts.  On GS_ERR_CUDA the
+ *     CUDA error text is available from gs_last_error(ctx) (or
+ *     gs_last_global_error() for context-free calls).
+ *   - Time t and step sizes are FP64 on the host and on the device in every
+ *     precision; only the bulk stencil / stage arithmetic follows the
+ *     context precision.
+ *   - The library has no CPU fallback: without a usable CUDA device every
+ *     compute call fails with GS_ERR_CUDA.
+ */
+#ifndef GS_B300_H
+#define GS_B300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GS_OK = 0,
+    GS_ERR_INVALID = 1,        /* bad argument: null pointer, size, enum, unbound state */
+    GS_ERR_CUDA = 2,           /* a CUDA runtime call failed (see gs_last_error) */
+    GS_ERR_NOMEM = 3,          /* device or pinned host allocation failed */
+    GS_ERR_STEP_UNDERFLOW = 4, /* adaptive control: 500 consecutive rejections, or t + dt == t */
+    GS_ERR_MAX_STEPS = 5,      /* adaptive control: attempt limit reached before t_end */
+    GS_ERR_NONFINITE = 6       /* adaptive control: error norm is NaN or infinite */
+} gs_status;
+
+typedef enum { GS_FP64 = 0, GS_FP32 = 1 } gs_precision;
+
+/* Steppers of Table 1 available through gs_step / ode_integrate_const. */
+typedef enum {
+    GS_RK4 = 0,    /* classical Runge-Kutta 4, fixed step */
+    GS_DOPRI5 = 1, /* Dormand-Prince 5 (its 5th-order solution), fixed step */
+    GS_AB4 = 2,    /* Adams-Bashforth 4; the first 3 steps of each call by RK4 */
+    GS_EULER = 3   /* explicit Euler */
+} gs_method;
+
+/* Gray-Scott problem (Eq. 2): periodic box [0,Lx)x[0,Ly)x[0,Lz), nx*ny*nz
+ * cells, spacing h_d = L_d / n_d, diffusivities Du, Dv, feed rate F and kill
+ * rate k:  du/dt = Du Lap(u) - u v^2 + F (1 - u),
+ *          dv/dt = Dv Lap(v) + u v^2 - (F + k) v.
+ * prec is a gs_precision. */
+typedef struct {
+    int nx, ny, nz;
+    double Lx, Ly, Lz;
+    double Du, Dv, F, k;
+    int prec;
+} gs_params;
+
+typedef struct gs_ctx gs_ctx; /* opaque; owns the stage scratch (the state type's
+                                 temporaries of the section "Architecture and
+                                 nomenclature of Boost Odeint") */
+
+/* Creates a context for one Gray-Scott problem on the current device.  Stage
+ * scratch (8 fields x 2 components) and a small control block are allocated
+ * here (the Algebra's resize, section "The distributed OpenFPM state type and
+ * algebra").  Requires 1 <= n_d <= 65535, L_d > 0.
+ * stream: where all work of this context is enqueued.
+ * Errors: INVALID (p/out NULL, bad sizes), NOMEM, CUDA. */
+gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out);
+
+/* Frees the context's scratch and graphs (not the bound state).  NULL is a no-op. */
+gs_status gs_destroy(gs_ctx* ctx);
+
+/* Binds the caller-owned device arrays u and v (nx*ny*nz elements each, of
+ * the context precision).  All integrators update them in place (section
+ * "Reuse potential": the state is updated in-place).  INVALID if NULL or not
+ * 16-byte aligned. */
+gs_status gs_bind_state(gs_ctx* ctx, void* u_dev, void* v_dev);
+
+/* Copies host arrays into the bound state (stream-ordered; returns once the
+ * copies are enqueued; host buffers must stay valid until the stream passes
+ * them -- pinned memory gives asynchronous copies). */
+gs_status gs_upload_state(gs_ctx* ctx, const void* u_host, const void* v_host);
+
+/* Copies the bound state to host arrays and synchronises the stream. */
+gs_status gs_download_state(gs_ctx* ctx, void* u_host, void* v_host);
+
+/* One evaluation of the System F(t, (u,v)) (Listing 2):
+ * (fu, fv) = F(t, (u, v)).  All four are device arrays of nx*ny*nz elements;
+ * outputs must not alias inputs.  Enqueued on the context stream. */
+gs_status gs_rhs(gs_ctx* ctx, double t, const void* u_dev, const void* v_dev, void* fu_dev,
+                 void* fv_dev);
+
+/* integrate_const / do_step (Listing 3): nsteps fixed steps of size dt from
+ * *t on the bound state.  Step m is taken at time *t + m*dt; on return
+ * *t = *t + nsteps*dt.  nsteps = 0 is a no-op.  Synchronises the stream. */
+gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps);
+
+/* integrate_adaptive (section "Architecture and nomenclature of Boost
+ * Odeint"): error-controlled Dormand-Prince 5(4) on the bound state from *t
+ * towards t_end with initial step *dt and tolerances atol, rtol.
+ * Error norm: E = max over cells and both components of
+ *   |err_i| / (atol + rtol (|u_i| + dt |k1_i|)),   err = dt sum_j (b_j - bhat_j) k_j.
+ * Step-size controller (paper silent; this library's reading):
+ *   E > 1 reject, dt *= max(0.9 E^(-1/3), 0.2);
+ *   E < 0.5 accept, dt *= 0.9 max(E, 5^-5)^(-1/5);  otherwise accept, dt kept.
+ * The last step is clipped to land exactly on t_end.  Integration stops at
+ * t_end or after max_accepted accepted steps (max_accepted < 0: no limit;
+ * t_end may be +inf then).  On return *t, *dt (the next proposed step),
+ * *n_accepted, *n_rejected are set (the latter two may be NULL).
+ * Statuses: STEP_UNDERFLOW, NONFINITE, MAX_STEPS (more than 10^7 attempts).
+ * In FP32 contexts the per-cell scaled errors are formed in FP32 from the
+ * FP32 stage values; the max-reduction, controller, dt and t are FP64.
+ * Synchronises the stream. */
+gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t, double t_end,
+                                double* dt, long max_accepted, long* n_accepted,
+                                long* n_rejected);
+
+/* Enables (capacity > 0) or disables (0) recording of the accepted step
+ * sizes of later gs_integrate_adaptive calls into a device buffer of
+ * `capacity` doubles. */
+gs_status gs_set_step_log(gs_ctx* ctx, long capacity);
+
+/* Copies up to `capacity` recorded step sizes to dts_host; *count receives
+ * the number recorded by the last call (may exceed capacity). Synchronises. */
+gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* count);
+
+/* Tile shape of the stencil kernels: ty rows of 30 interior cells per CTA
+ * (CTA = 32 x (ty+2) threads), marching over zc planes.  ty in {2,4,6,8,14},
+ * 1 <= zc <= 1024.  Takes effect at the next integrator call. */
+gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);
+gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
+
+/* Times each candidate tile shape on one Dormand-Prince step from the bound
+ * state (outputs go to the context's scratch only; the bound state is not
+ * modified), selects the fastest, and returns it.  best_ms may be NULL. */
+gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
+
+/* Text of the last CUDA error seen by ctx ("" if none). */
+const char* gs_last_error(const gs_ctx* ctx);
+/* Text of the last CUDA error seen by a context-free entry point. */
+const char* gs_last_global_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Stage algebra (section "The distributed OpenFPM state type and algebra":  */
+/* for_each operations over up to 15 states)                                 */
+/* ------------------------------------------------------------------------ */
+
+/* y[i] = sum_{j<nterms} coef[j] * x_j[i] for i < n.  coef: host array of
+ * nterms doubles (cast to the precision of the data).  x: host array of
+ * nterms device pointers (each n elements of precision prec, 16-byte
+ * aligned); y may alias one of them.  1 <= nterms <= 15, n >= 0.  Enqueued
+ * on stream. */
+gs_status ode_axpy_stage(long n, gs_precision prec, int nterms, const double* coef,
+                         const void* const* x, void* y, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Pointwise ODE ensembles: dx_i/dt = f(x_i) on n independent FP64 elements */
+/* (autonomous forms of the benchmark families of "Accuracy Benchmarks")    */
+/* ------------------------------------------------------------------------ */
+typedef enum {
+    ODE_EXP_DECAY = 0, /* f(x) = -x,        x(t) = x0 e^-t */
+    ODE_LOGISTIC = 1   /* f(x) = x (1 - x), x(t) = x0 / (x0 + (1 - x0) e^-t) */
+} ode_rhs;
+
+/* Workspace bytes needed by ode_integrate_adaptive for n elements. */
+size_t ode_workspace_size(long n);
+
+/* Error-controlled Dormand-Prince 5(4) on x (n FP64 device values) with ONE
+ * global step size (a single state vector with a global norm, section
+ * "Architecture and nomenclature of Boost Odeint"); same norm, controller
+ * and clipping as gs_integrate_adaptive.  workspace: device buffer of at
+ * least ode_workspace_size(n) bytes, 256-byte aligned, owned by the caller.
+ * dt_log: optional device array (may be NULL) receiving the accepted step
+ * sizes, up to log_cap entries.  max_steps bounds accepted steps (< 0: none).
+ * Synchronises the stream. */
+gs_status ode_integrate_adaptive(ode_rhs rhs, long n, double* x_dev, double* t, double t_end,
+                                 double* dt, double atol, double rtol, long max_steps,
+                                 long* n_acc, long* n_rej, void* workspace,
+                                 size_t workspace_bytes, double* dt_log, long log_cap,
+                                 void* stream);
+
+/* Adams-Bashforth 4 (Table 1) for nsteps steps of size dt from t0; the first
+ * three steps by RK4.  All steps of an element run in registers in one
+ * kernel (no global synchronisation is needed between fixed steps).
+ * Enqueued on stream. */
+gs_status ode_integrate_ab4(ode_rhs rhs, long n, double* x_dev, double t0, double dt, long nsteps,
+                            void* stream);
+
+/* Fixed-step Euler / RK4 / Dopri5 (Table 1), nsteps steps of dt, in
+ * registers, one kernel.  Enqueued on stream. */
+gs_status ode_integrate_const(ode_rhs rhs, gs_method method, long n, double* x_dev, double t0,
+                              double dt, long nsteps, void* stream);
+
+/* Measures this device's FP64 fused-multiply-add throughput (TFLOP/s,
+ * 2 flops per FMA) with independent dependent-chains; used as the ALU
+ * roofline of the FP64 paths. Synchronises. */
+gs_status gs_measure_fp64_peak(double* tflops, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GS_B300_H */

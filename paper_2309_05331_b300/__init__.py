@@ -1,0 +1,282 @@
+"""Python binding of libgs_b300 (C ABI in include/gs.h).
+
+Argument marshalling only: every computation runs in the library's CUDA
+kernels.  Device arrays are PyTorch CUDA tensors (contiguous, 16-byte
+aligned); streams default to PyTorch's current stream.  There is no CPU
+fallback: if the shared library is missing or no CUDA device is present the
+calls raise.
+
+The functions keep the C names (gs_create, gs_step, gs_integrate_adaptive,
+ode_axpy_stage, ...); ``GrayScott`` is a small owner of one gs_ctx.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgs_b300.so")
+
+GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_NOMEM = 0, 1, 2, 3
+GS_ERR_STEP_UNDERFLOW, GS_ERR_MAX_STEPS, GS_ERR_NONFINITE = 4, 5, 6
+GS_FP64, GS_FP32 = 0, 1
+GS_RK4, GS_DOPRI5, GS_AB4, GS_EULER = 0, 1, 2, 3
+ODE_EXP_DECAY, ODE_LOGISTIC = 0, 1
+
+STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID", 2: "GS_ERR_CUDA", 3: "GS_ERR_NOMEM",
+                4: "GS_ERR_STEP_UNDERFLOW", 5: "GS_ERR_MAX_STEPS", 6: "GS_ERR_NONFINITE"}
+
+
+class GSError(RuntimeError):
+    def __init__(self, status, msg=""):
+        self.status = status
+        super().__init__(f"{STATUS_NAMES.get(status, status)} {msg}".strip())
+
+
+class gs_params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("Lx", C.c_double), ("Ly", C.c_double), ("Lz", C.c_double),
+                ("Du", C.c_double), ("Dv", C.c_double), ("F", C.c_double), ("k", C.c_double),
+                ("prec", C.c_int)]
+
+
+_lib = None
+_vp, _dp, _lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)
+
+_SIGNATURES = {
+    "gs_create": ([C.POINTER(gs_params), _vp, C.POINTER(_vp)], C.c_int),
+    "gs_destroy": ([_vp], C.c_int),
+    "gs_bind_state": ([_vp, _vp, _vp], C.c_int),
+    "gs_upload_state": ([_vp, _vp, _vp], C.c_int),
+    "gs_download_state": ([_vp, _vp, _vp], C.c_int),
+    "gs_rhs": ([_vp, C.c_double, _vp, _vp, _vp, _vp], C.c_int),
+    "gs_step": ([_vp, C.c_int, _dp, C.c_double, C.c_long], C.c_int),
+    "gs_integrate_adaptive": ([_vp, C.c_double, C.c_double, _dp, C.c_double, _dp, C.c_long, _lp, _lp], C.c_int),
+    "gs_set_step_log": ([_vp, C.c_long], C.c_int),
+    "gs_get_step_log": ([_vp, _dp, C.c_long, _lp], C.c_int),
+    "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
+    "gs_last_error": ([_vp], C.c_char_p),
+    "gs_last_global_error": ([], C.c_char_p),
+    "ode_axpy_stage": ([C.c_long, C.c_int, C.c_int, _dp, C.POINTER(_vp), _vp, _vp], C.c_int),
+    "ode_workspace_size": ([C.c_long], C.c_size_t),
+    "ode_integrate_adaptive": ([C.c_int, C.c_long, _vp, _dp, C.c_double, _dp, C.c_double, C.c_double,
+                                C.c_long, _lp, _lp, _vp, C.c_size_t, _vp, C.c_long, _vp], C.c_int),
+    "ode_integrate_ab4": ([C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
+    "ode_integrate_const": ([C.c_int, C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
+    "gs_measure_fp64_peak": ([_dp, _vp], C.c_int),
+}
+
+
+def lib():
+    """Loads libgs_b300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2309_05331_b300.build`")
+    import torch  # noqa: F401  -- load PyTorch's CUDA runtime first so both share it
+    L = C.CDLL(LIB_PATH)
+    for name, (args, res) in _SIGNATURES.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_names():
+    """Names the binding expects the library to export."""
+    return list(_SIGNATURES)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+def _check(st, ctx=None):
+    if st != GS_OK:
+        L = lib()
+        msg = (L.gs_last_error(ctx) if ctx else L.gs_last_global_error()) or b""
+        raise GSError(st, msg.decode())
+
+
+# --------------------------------------------------------------------------
+# Same-named thin wrappers of the C ABI
+# --------------------------------------------------------------------------
+def gs_create(nx, ny, nz, L=2.5, Du=2e-5, Dv=1e-5, F=0.053, k=0.014, prec=GS_FP64, Ly=None, Lz=None,
+              stream=None):
+    p = gs_params(nx, ny, nz, L, L if Ly is None else Ly, L if Lz is None else Lz, Du, Dv, F, k, prec)
+    ctx = _vp()
+    _check(lib().gs_create(C.byref(p), _stream(stream), C.byref(ctx)))
+    return ctx
+
+
+def gs_destroy(ctx):
+    return lib().gs_destroy(ctx)
+
+
+def gs_bind_state(ctx, u, v):
+    _check(lib().gs_bind_state(ctx, _ptr(u), _ptr(v)), ctx)
+
+
+def gs_upload_state(ctx, u_host, v_host):
+    _check(lib().gs_upload_state(ctx, u_host.data_ptr(), v_host.data_ptr()), ctx)
+
+
+def gs_download_state(ctx, u_host, v_host):
+    _check(lib().gs_download_state(ctx, u_host.data_ptr(), v_host.data_ptr()), ctx)
+
+
+def gs_rhs(ctx, t, u, v, fu, fv):
+    _check(lib().gs_rhs(ctx, t, _ptr(u), _ptr(v), _ptr(fu), _ptr(fv)), ctx)
+
+
+def gs_step(ctx, method, t, dt, nsteps):
+    tt = C.c_double(t)
+    _check(lib().gs_step(ctx, method, C.byref(tt), dt, nsteps), ctx)
+    return tt.value
+
+
+def gs_integrate_adaptive(ctx, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
+    tt, dd = C.c_double(t), C.c_double(dt)
+    na, nr = C.c_long(0), C.c_long(0)
+    st = lib().gs_integrate_adaptive(ctx, atol, rtol, C.byref(tt), t_end, C.byref(dd), max_accepted,
+                                     C.byref(na), C.byref(nr))
+    if check:
+        _check(st, ctx)
+    return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}
+
+
+def gs_set_step_log(ctx, capacity):
+    _check(lib().gs_set_step_log(ctx, capacity), ctx)
+
+
+def gs_get_step_log(ctx, capacity):
+    import numpy as np
+    buf = np.zeros(max(capacity, 1))
+    cnt = C.c_long(0)
+    _check(lib().gs_get_step_log(ctx, buf.ctypes.data_as(_dp), capacity, C.byref(cnt)), ctx)
+    return buf[: min(cnt.value, capacity)].copy(), cnt.value
+
+
+def gs_set_tile(ctx, ty, zc):
+    _check(lib().gs_set_tile(ctx, ty, zc), ctx)
+
+
+def gs_get_tile(ctx):
+    a, b = C.c_int(0), C.c_int(0)
+    _check(lib().gs_get_tile(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def gs_autotune(ctx):
+    a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+    _check(lib().gs_autotune(ctx, C.byref(a), C.byref(b), C.byref(ms)), ctx)
+    return a.value, b.value, ms.value
+
+
+def ode_axpy_stage(coef, xs, y, stream=None):
+    """y = sum_j coef[j] * xs[j] on the GPU (1..15 operands, same dtype)."""
+    import torch
+    if y.dtype not in (torch.float32, torch.float64) or any(x.dtype != y.dtype for x in xs):
+        raise ValueError("operands must all be float32 or all float64")
+    if any(x.numel() != y.numel() for x in xs):
+        raise ValueError("operand sizes differ")
+    prec = GS_FP64 if y.dtype == torch.float64 else GS_FP32
+    c = (C.c_double * len(xs))(*[float(a) for a in coef])
+    ptrs = (_vp * len(xs))(*[_ptr(x) for x in xs])
+    _check(lib().ode_axpy_stage(y.numel(), prec, len(xs), c, ptrs, _ptr(y), _stream(stream)))
+
+
+def ode_workspace_size(n):
+    return lib().ode_workspace_size(n)
+
+
+def ode_integrate_adaptive(kind, x, t, t_end, dt, atol, rtol, max_steps=-1, workspace=None, dt_log=None,
+                           stream=None, check=True):
+    import torch
+    n = x.numel()
+    if workspace is None:
+        workspace = torch.empty(ode_workspace_size(n), dtype=torch.uint8, device=x.device)
+    tt, dd = C.c_double(t), C.c_double(dt)
+    na, nr = C.c_long(0), C.c_long(0)
+    st = lib().ode_integrate_adaptive(kind, n, _ptr(x), C.byref(tt), t_end, C.byref(dd), atol, rtol, max_steps,
+                                      C.byref(na), C.byref(nr), _ptr(workspace), workspace.numel(),
+                                      _ptr(dt_log), 0 if dt_log is None else dt_log.numel(), _stream(stream))
+    if check:
+        _check(st)
+    return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}
+
+
+def ode_integrate_ab4(kind, x, t0, dt, nsteps, stream=None):
+    _check(lib().ode_integrate_ab4(kind, x.numel(), _ptr(x), t0, dt, nsteps, _stream(stream)))
+
+
+def ode_integrate_const(kind, method, x, t0, dt, nsteps, stream=None):
+    _check(lib().ode_integrate_const(kind, method, x.numel(), _ptr(x), t0, dt, nsteps, _stream(stream)))
+
+
+def gs_measure_fp64_peak(stream=None):
+    v = C.c_double(0)
+    _check(lib().gs_measure_fp64_peak(C.byref(v), _stream(stream)))
+    return v.value
+
+
+# --------------------------------------------------------------------------
+# Owner of one Gray-Scott context and its state tensors
+# --------------------------------------------------------------------------
+class GrayScott:
+    """One periodic Gray-Scott problem (Eq. 2) with state tensors u, v on the GPU.
+
+    u, v: torch tensors shaped (nz, ny, nx), float64 or float32 (prec)."""
+
+    def __init__(self, nx, ny, nz, L=2.5, Du=2e-5, Dv=1e-5, F=0.053, k=0.014, prec=GS_FP64, u=None, v=None,
+                 Ly=None, Lz=None, stream=None, device="cuda"):
+        import torch
+        self.shape = (nz, ny, nx)
+        self.prec = prec
+        self.dtype = torch.float64 if prec == GS_FP64 else torch.float32
+        self.ctx = gs_create(nx, ny, nz, L, Du, Dv, F, k, prec, Ly, Lz, stream)
+        self.u = torch.empty(self.shape, dtype=self.dtype, device=device) if u is None else u
+        self.v = torch.empty(self.shape, dtype=self.dtype, device=device) if v is None else v
+        gs_bind_state(self.ctx, self.u, self.v)
+
+    def set_state(self, u, v):
+        self.u.copy_(u.to(self.u.device, self.dtype).reshape(self.shape))
+        self.v.copy_(v.to(self.v.device, self.dtype).reshape(self.shape))
+
+    def rhs(self, t=0.0):
+        import torch
+        fu, fv = torch.empty_like(self.u), torch.empty_like(self.v)
+        gs_rhs(self.ctx, t, self.u, self.v, fu, fv)
+        return fu, fv
+
+    def step(self, method, t, dt, nsteps):
+        return gs_step(self.ctx, method, t, dt, nsteps)
+
+    def integrate_adaptive(self, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
+        return gs_integrate_adaptive(self.ctx, atol, rtol, t, t_end, dt, max_accepted, check)
+
+    def close(self):
+        if self.ctx:
+            gs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

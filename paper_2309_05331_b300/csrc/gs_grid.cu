@@ -1,0 +1,716 @@
+// gs_grid.cu -- single-grid Gray-Scott integrators behind the C ABI of gs.h.
+//
+// Every integrator is one CUDA graph: a conditional WHILE node whose body is
+// the stage kernels of one step (RK4: 4, Dopri5: 6 after the first-same-as-
+// last k1, Euler / Adams-Bashforth: 1).  The last kernel of the body advances
+// the on-device control block (fixed-step counter, or the adaptive
+// controller) and sets the loop condition, so the host enqueues one graph per
+// call and reads the control block back once.
+//
+// Buffers: the caller's state (u, v) is state buffer 0; the context owns
+// state buffer 1 and seven stage fields.  Which state buffer is current
+// (and which k1 buffer, for Dopri5's first-same-as-last reuse) is a parity
+// bit in the control block; if a run ends on buffer 1 a final kernel copies
+// it back into the caller's arrays.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "gs_tile.cuh"
+#include "host_util.h"
+
+using namespace gsk;
+
+namespace {
+
+enum GraphId { G_RK4 = 0, G_DOPRI5_FIXED, G_EULER, G_DOPRI5_ADAPT, G_AB4_START, G_AB4_MAIN, G_COUNT };
+
+constexpr int kFields = 8;  // 0: second state buffer; 1..7: stage fields
+
+}  // namespace
+
+struct gs_ctx {
+    gs_params p;
+    long long N = 0;
+    size_t esz = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap = nullptr;
+    int dev = 0, nsm = 0;
+    void* state[2] = {nullptr, nullptr};
+    unsigned char* scratch = nullptr;
+    void* field[kFields][2] = {};
+    DevCtrl* dctrl = nullptr;
+    DevCtrl* hctrl = nullptr;     // pinned staging of the whole control block
+    long long* hpatch = nullptr;  // pinned staging of single-field patches
+    double* dlog = nullptr;
+    long log_cap = 0;
+    int ty = 6, zc = 32;
+    cudaGraph_t graph[G_COUNT] = {};
+    cudaGraphExec_t exec[G_COUNT] = {};
+    char err[512] = {0};
+};
+
+static void set_err(gs_ctx* c, cudaError_t e, const char* where) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        if (e_ != cudaSuccess) {                   \
+            set_err(ctx, e_, #call);               \
+            return GS_ERR_CUDA;                    \
+        }                                          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// kernel launch helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+static Geom<T> make_geom(const gs_params& p) {
+    Geom<T> g;
+    g.nx = p.nx;
+    g.ny = p.ny;
+    g.nz = p.nz;
+    const double hx = p.Lx / p.nx, hy = p.Ly / p.ny, hz = p.Lz / p.nz;
+    g.cx = (T)(1.0 / (hx * hx));
+    g.cy = (T)(1.0 / (hy * hy));
+    g.cz = (T)(1.0 / (hz * hz));
+    g.Du = (T)p.Du;
+    g.Dv = (T)p.Dv;
+    g.F = (T)p.F;
+    g.k = (T)p.k;
+    return g;
+}
+
+template <typename T, int NK, int MODE>
+static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
+    const Geom<T> g = make_geom<T>(ctx->p);
+    const size_t smem = stage_smem_bytes<T>(A.ty);
+    auto kern = gs_stage_kernel<T, NK, MODE>;
+    int occ = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const long long ntiles = (long long)A.ntx * A.nty * A.ntz;
+    const int grid = (int)std::min<long long>(ntiles, (long long)ctx->nsm * occ);
+    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A);
+    return cudaGetLastError();
+}
+
+template <int NK, int MODE>
+static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A) {
+    if (ctx->p.prec == GS_FP64) return launch_stage_t<double, NK, MODE>(ctx, s, A);
+    return launch_stage_t<float, NK, MODE>(ctx, s, A);
+}
+
+static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A) {
+#define GS_DISPATCH_MODE(NKV)                                                       \
+    case NKV:                                                                       \
+        if (mode == MODE_STAGE) return launch_stage_nk<NKV, MODE_STAGE>(ctx, s, A); \
+        if (mode == MODE_FINAL) return launch_stage_nk<NKV, MODE_FINAL>(ctx, s, A); \
+        return launch_stage_nk<NKV, MODE_DOPRI_FINAL>(ctx, s, A);
+    switch (nk) {
+        GS_DISPATCH_MODE(0)
+        GS_DISPATCH_MODE(1)
+        GS_DISPATCH_MODE(2)
+        GS_DISPATCH_MODE(3)
+        GS_DISPATCH_MODE(4)
+        GS_DISPATCH_MODE(5)
+        default: return cudaErrorInvalidValue;
+    }
+#undef GS_DISPATCH_MODE
+}
+
+static StageArgs base_args(gs_ctx* ctx) {
+    StageArgs A;
+    memset(&A, 0, sizeof(A));
+    A.ty = ctx->ty;
+    A.zc = ctx->zc;
+    A.ntx = (ctx->p.nx + kTileX - 1) / kTileX;
+    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
+    A.ntz = (ctx->p.nz + A.zc - 1) / A.zc;
+    A.ctrl = ctx->dctrl;
+    return A;
+}
+
+// slot helpers over the context buffers
+static Slot fld(gs_ctx* c, int f) { return slot_fixed(c->field[f][0], c->field[f][1]); }
+static Slot state_sel(gs_ctx* c, int sel) {
+    Slot s{};
+    s.p[0][0] = c->state[0];
+    s.p[0][1] = c->state[1];
+    s.p[1][0] = c->field[0][0];
+    s.p[1][1] = c->field[0][1];
+    s.sel = sel;
+    return s;
+}
+static Slot pair_sel(gs_ctx* c, int fa, int fb, int sel) {
+    Slot s{};
+    s.p[0][0] = c->field[fa][0];
+    s.p[0][1] = c->field[fa][1];
+    s.p[1][0] = c->field[fb][0];
+    s.p[1][1] = c->field[fb][1];
+    s.sel = sel;
+    return s;
+}
+// Adams-Bashforth history ring over fields 1..4: f_m lives in field 1 + (m & 3)
+static Slot ring(gs_ctx* c, int off) {
+    Slot s{};
+    for (int i = 0; i < 4; ++i) {
+        s.p[i][0] = c->field[1 + i][0];
+        s.p[i][1] = c->field[1 + i][1];
+    }
+    s.sel = SEL_RING;
+    s.off = off;
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// Step bodies (enqueued on stream s; final kernel sets conditional h)
+// ---------------------------------------------------------------------------
+// RK4 with k-storage: k1 = F(u); k2 = F(u + dt/2 k1); k3 = F(u + dt/2 k2);
+// u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) with k4 = F(u + dt k3).
+// k1 goes to field 1 (or to the history ring when starting Adams-Bashforth).
+static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond,
+                            bool k1_in_ring) {
+    const Slot k1 = k1_in_ring ? ring(ctx, 0) : fld(ctx, 1);
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.out0 = k1;
+    cudaError_t e = launch_stage(ctx, s, 0, MODE_STAGE, A);
+    if (e != cudaSuccess) return e;
+    A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.kin[0] = k1;
+    A.a[0] = 0.5;
+    A.out0 = fld(ctx, 5);
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A)) != cudaSuccess) return e;
+    A.kin[0] = fld(ctx, 5);
+    A.out0 = fld(ctx, 6);
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A)) != cudaSuccess) return e;
+    A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.kin[0] = fld(ctx, 6);
+    A.a[0] = 1.0;
+    A.bk[0] = 1.0 / 3.0;
+    A.ex[0] = k1;
+    A.ex[1] = fld(ctx, 5);
+    A.be[0] = 1.0 / 6.0;
+    A.be[1] = 1.0 / 3.0;
+    A.n_ex = 2;
+    A.bf = 1.0 / 6.0;
+    A.out0 = state_sel(ctx, SEL_NEXT);
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_stage(ctx, s, 1, MODE_FINAL, A);
+}
+
+static cudaError_t body_euler(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.bf = 1.0;
+    A.out0 = state_sel(ctx, SEL_NEXT);
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_stage(ctx, s, 0, MODE_FINAL, A);
+}
+
+// Adams-Bashforth 4 step m >= 3: f_m = F(u_m) into the ring,
+// u_{m+1} = u_m + dt (55 f_m - 59 f_{m-1} + 37 f_{m-2} - 9 f_{m-3}) / 24.
+static cudaError_t body_ab4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.bf = 55.0 / 24.0;
+    A.ex[0] = ring(ctx, -1);
+    A.ex[1] = ring(ctx, -2);
+    A.ex[2] = ring(ctx, -3);
+    A.be[0] = -59.0 / 24.0;
+    A.be[1] = 37.0 / 24.0;
+    A.be[2] = -9.0 / 24.0;
+    A.n_ex = 3;
+    A.out0 = state_sel(ctx, SEL_NEXT);
+    A.out1 = ring(ctx, 0);
+    A.has_out1 = 1;
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_stage(ctx, s, 0, MODE_FINAL, A);
+}
+
+// Dormand-Prince stages 2..7 with k1 in the parity pair (fields 1, 2) and
+// k2..k6 in fields 3..7; stage 7 writes y5 and k7 to the other buffers of
+// their pairs and reduces the error norm.
+static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+    const Slot k1 = pair_sel(ctx, 1, 2, SEL_CUR);
+    const Slot k[7] = {k1, k1, fld(ctx, 3), fld(ctx, 4), fld(ctx, 5), fld(ctx, 6), fld(ctx, 7)};
+    // k[i] = k_i for i = 1..6
+    const double A2[1] = {dp5::A21};
+    const double A3[2] = {dp5::A31, dp5::A32};
+    const double A4[3] = {dp5::A41, dp5::A42, dp5::A43};
+    const double A5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
+    const double A6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
+    const double* rows[5] = {A2, A3, A4, A5, A6};
+    cudaError_t e;
+    for (int st = 2; st <= 6; ++st) {
+        StageArgs A = base_args(ctx);
+        A.u = state_sel(ctx, SEL_CUR);
+        const int nk = st - 1;
+        for (int j = 0; j < nk; ++j) {
+            A.kin[j] = k[j + 1];
+            A.a[j] = rows[st - 2][j];
+        }
+        A.out0 = k[st];
+        if ((e = launch_stage(ctx, s, nk, MODE_STAGE, A)) != cudaSuccess) return e;
+    }
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.kin[0] = k[1];
+    A.kin[1] = k[3];
+    A.kin[2] = k[4];
+    A.kin[3] = k[5];
+    A.kin[4] = k[6];
+    A.a[0] = dp5::B1;
+    A.a[1] = dp5::B3;
+    A.a[2] = dp5::B4;
+    A.a[3] = dp5::B5;
+    A.a[4] = dp5::B6;
+    A.out0 = state_sel(ctx, SEL_NEXT);
+    A.out1 = pair_sel(ctx, 1, 2, SEL_NEXT);
+    A.has_out1 = 1;
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A);
+}
+
+// k1 = F(u) into the current k1 buffer (start of a Dormand-Prince run)
+static cudaError_t launch_dopri5_k1(gs_ctx* ctx, cudaStream_t s) {
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.out0 = pair_sel(ctx, 1, 2, SEL_CUR);
+    return launch_stage(ctx, s, 0, MODE_STAGE, A);
+}
+
+static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned long long h, int use_cond) {
+    switch (gid) {
+        case G_RK4: return body_rk4(ctx, s, h, use_cond, false);
+        case G_AB4_START: return body_rk4(ctx, s, h, use_cond, true);
+        case G_EULER: return body_euler(ctx, s, h, use_cond);
+        case G_AB4_MAIN: return body_ab4(ctx, s, h, use_cond);
+        case G_DOPRI5_FIXED:
+        case G_DOPRI5_ADAPT: return body_dopri5(ctx, s, h, use_cond);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static void drop_graphs(gs_ctx* ctx) {
+    for (int i = 0; i < G_COUNT; ++i) {
+        if (ctx->exec[i]) cudaGraphExecDestroy(ctx->exec[i]);
+        if (ctx->graph[i]) cudaGraphDestroy(ctx->graph[i]);
+        ctx->exec[i] = nullptr;
+        ctx->graph[i] = nullptr;
+    }
+}
+
+// WHILE(cond) { body } as an executable graph, cached per id.
+static gs_status get_loop_graph(gs_ctx* ctx, int gid, cudaGraphExec_t* out) {
+    if (ctx->exec[gid]) {
+        *out = ctx->exec[gid];
+        return GS_OK;
+    }
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaError_t e = make_while_graph(&g, &h, &body);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        set_err(ctx, e, "make_while_graph");
+        return GS_ERR_CUDA;
+    }
+    e = cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t eb = build_body(ctx, gid, ctx->cap, (unsigned long long)h, 1);
+        cudaGraph_t tmp = body;
+        e = cudaStreamEndCapture(ctx->cap, &tmp);
+        if (eb != cudaSuccess) e = eb;
+    }
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        set_err(ctx, e, "capture of the step body");
+        return GS_ERR_CUDA;
+    }
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        set_err(ctx, e, "cudaGraphInstantiate");
+        return GS_ERR_CUDA;
+    }
+    ctx->graph[gid] = g;
+    ctx->exec[gid] = ex;
+    *out = ex;
+    return GS_OK;
+}
+
+// copy state buffer 1 back into the caller's arrays if the run ended there
+template <typename T>
+__global__ void copy_back_kernel(const DevCtrl* c, const T* __restrict__ a0, const T* __restrict__ a1,
+                                 T* __restrict__ b0, T* __restrict__ b1, long long n) {
+    if (c->parity == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        b0[i] = a0[i];
+        b1[i] = a1[i];
+    }
+}
+
+static cudaError_t launch_copy_back(gs_ctx* ctx) {
+    const int grid = ctx->nsm * 8;
+    if (ctx->p.prec == GS_FP64)
+        copy_back_kernel<double><<<grid, 256, 0, ctx->stream>>>(
+            ctx->dctrl, (const double*)ctx->field[0][0], (const double*)ctx->field[0][1],
+            (double*)ctx->state[0], (double*)ctx->state[1], ctx->N);
+    else
+        copy_back_kernel<float><<<grid, 256, 0, ctx->stream>>>(
+            ctx->dctrl, (const float*)ctx->field[0][0], (const float*)ctx->field[0][1],
+            (float*)ctx->state[0], (float*)ctx->state[1], ctx->N);
+    return cudaGetLastError();
+}
+
+static gs_status upload_ctrl(gs_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->dctrl, ctx->hctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, ctx->stream));
+    return GS_OK;
+}
+
+static gs_status download_ctrl_sync(gs_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->hctrl, ctx->dctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+static void init_fixed_ctrl(gs_ctx* ctx, double t0, double dt, long long limit) {
+    DevCtrl* h = ctx->hctrl;
+    memset(h, 0, sizeof(DevCtrl));
+    h->mode = CTRL_FIXED;
+    h->t = t0;
+    h->t0 = t0;
+    h->dt = dt;
+    h->dt_try = dt;
+    h->step_limit = limit;
+    h->max_acc = -1;
+    h->max_att = kMaxAttempts;
+    h->t_end = INFINITY;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out) {
+    if (!p || !out) return GS_ERR_INVALID;
+    *out = nullptr;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || p->nx > 65535 || p->ny > 65535 || p->nz > 65535)
+        return GS_ERR_INVALID;
+    if (!(p->Lx > 0) || !(p->Ly > 0) || !(p->Lz > 0)) return GS_ERR_INVALID;
+    if (p->prec != GS_FP64 && p->prec != GS_FP32) return GS_ERR_INVALID;
+    gs_ctx* ctx = new (std::nothrow) gs_ctx();
+    if (!ctx) return GS_ERR_NOMEM;
+    ctx->p = *p;
+    ctx->N = (long long)p->nx * p->ny * p->nz;
+    ctx->esz = p->prec == GS_FP64 ? 8 : 4;
+    ctx->stream = (cudaStream_t)stream;
+    gs_status st = GS_OK;
+    cudaError_t e;
+    do {
+        if ((e = cudaGetDevice(&ctx->dev)) != cudaSuccess) break;
+        if ((e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->dev)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
+        // one allocation: fields padded to 256 bytes
+        const size_t fbytes = ((size_t)ctx->N * ctx->esz + 255) / 256 * 256;
+        const size_t total = fbytes * 2 * kFields;
+        if ((e = cudaMalloc(&ctx->scratch, total)) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
+        for (int f = 0; f < kFields; ++f)
+            for (int c = 0; c < 2; ++c) ctx->field[f][c] = ctx->scratch + fbytes * (2 * f + c);
+        if ((e = cudaMalloc(&ctx->dctrl, sizeof(DevCtrl))) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
+        if ((e = cudaMemset(ctx->dctrl, 0, sizeof(DevCtrl))) != cudaSuccess) break;
+        if ((e = cudaMallocHost(&ctx->hctrl, sizeof(DevCtrl))) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
+        if ((e = cudaMallocHost(&ctx->hpatch, 4 * sizeof(long long))) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
+        memset(ctx->hctrl, 0, sizeof(DevCtrl));
+        ctx->ty = 6;
+        ctx->zc = 32;
+    } while (0);
+    if (e != cudaSuccess) {
+        if (st == GS_OK) st = GS_ERR_CUDA;
+        set_global_error(e, "gs_create");
+        gs_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+gs_status gs_destroy(gs_ctx* ctx) {
+    if (!ctx) return GS_OK;
+    drop_graphs(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->dctrl) cudaFree(ctx->dctrl);
+    if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
+    if (ctx->hpatch) cudaFreeHost(ctx->hpatch);
+    if (ctx->dlog) cudaFree(ctx->dlog);
+    delete ctx;
+    return GS_OK;
+}
+
+gs_status gs_bind_state(gs_ctx* ctx, void* u, void* v) {
+    if (!ctx || !u || !v) return GS_ERR_INVALID;
+    if (((uintptr_t)u & 15) || ((uintptr_t)v & 15)) return GS_ERR_INVALID;
+    if (ctx->state[0] != u || ctx->state[1] != v) drop_graphs(ctx);
+    ctx->state[0] = u;
+    ctx->state[1] = v;
+    return GS_OK;
+}
+
+gs_status gs_upload_state(gs_ctx* ctx, const void* uh, const void* vh) {
+    if (!ctx || !uh || !vh || !ctx->state[0]) return GS_ERR_INVALID;
+    const size_t bytes = (size_t)ctx->N * ctx->esz;
+    CK(cudaMemcpyAsync(ctx->state[0], uh, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->state[1], vh, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    return GS_OK;
+}
+
+gs_status gs_download_state(gs_ctx* ctx, void* uh, void* vh) {
+    if (!ctx || !uh || !vh || !ctx->state[0]) return GS_ERR_INVALID;
+    const size_t bytes = (size_t)ctx->N * ctx->esz;
+    CK(cudaMemcpyAsync(uh, ctx->state[0], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(vh, ctx->state[1], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, void* fv) {
+    (void)t;  // the Gray-Scott system is autonomous
+    if (!ctx || !u || !v || !fu || !fv) return GS_ERR_INVALID;
+    StageArgs A = base_args(ctx);
+    A.ctrl = nullptr;
+    A.u = slot_fixed(const_cast<void*>(u), const_cast<void*>(v));
+    A.out0 = slot_fixed(fu, fv);
+    CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A));
+    return GS_OK;
+}
+
+gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps) {
+    if (!ctx || !t || !ctx->state[0] || nsteps < 0 || !std::isfinite(dt)) return GS_ERR_INVALID;
+    if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER)
+        return GS_ERR_INVALID;
+    if (nsteps == 0) return GS_OK;
+    const double t0 = *t;
+    gs_status st;
+    cudaGraphExec_t ex;
+    if (method == GS_AB4) {
+        const long long nstart = std::min<long long>(3, nsteps);
+        init_fixed_ctrl(ctx, t0, dt, nstart);
+        if ((st = upload_ctrl(ctx)) != GS_OK) return st;
+        if ((st = get_loop_graph(ctx, G_AB4_START, &ex)) != GS_OK) return st;
+        CK(cudaGraphLaunch(ex, ctx->stream));
+        if (nsteps > 3) {
+            // raise the step limit and clear `done` (own pinned staging: the
+            // whole-block upload above may still be reading hctrl)
+            ctx->hpatch[0] = nsteps;
+            ctx->hpatch[1] = 0;
+            CK(cudaMemcpyAsync(&ctx->dctrl->step_limit, &ctx->hpatch[0], sizeof(long long),
+                               cudaMemcpyHostToDevice, ctx->stream));
+            CK(cudaMemcpyAsync(&ctx->dctrl->done, &ctx->hpatch[1], sizeof(int), cudaMemcpyHostToDevice,
+                               ctx->stream));
+            if ((st = get_loop_graph(ctx, G_AB4_MAIN, &ex)) != GS_OK) return st;
+            CK(cudaGraphLaunch(ex, ctx->stream));
+        }
+    } else {
+        const int gid = method == GS_RK4 ? G_RK4 : method == GS_EULER ? G_EULER : G_DOPRI5_FIXED;
+        init_fixed_ctrl(ctx, t0, dt, nsteps);
+        if ((st = upload_ctrl(ctx)) != GS_OK) return st;
+        if (method == GS_DOPRI5) CK(launch_dopri5_k1(ctx, ctx->stream));
+        if ((st = get_loop_graph(ctx, gid, &ex)) != GS_OK) return st;
+        CK(cudaGraphLaunch(ex, ctx->stream));
+    }
+    CK(launch_copy_back(ctx));
+    if ((st = download_ctrl_sync(ctx)) != GS_OK) return st;
+    *t = t0 + (double)nsteps * dt;
+    return GS_OK;
+}
+
+gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t, double t_end,
+                                double* dt, long max_accepted, long* n_accepted, long* n_rejected) {
+    if (!ctx || !t || !dt || !ctx->state[0]) return GS_ERR_INVALID;
+    if (!(atol >= 0) || !(rtol >= 0) || !(atol > 0 || rtol > 0) || !(*dt > 0) || std::isnan(t_end))
+        return GS_ERR_INVALID;
+    if (n_accepted) *n_accepted = 0;
+    if (n_rejected) *n_rejected = 0;
+    if (!(*t < t_end) || max_accepted == 0) return GS_OK;
+    DevCtrl* h = ctx->hctrl;
+    memset(h, 0, sizeof(DevCtrl));
+    h->mode = CTRL_ADAPTIVE;
+    h->t = *t;
+    h->t0 = *t;
+    h->t_end = t_end;
+    h->dt = *dt;
+    h->atol = atol;
+    h->rtol = rtol;
+    h->max_acc = max_accepted < 0 ? -1 : max_accepted;
+    h->max_att = kMaxAttempts;
+    h->log_dt = ctx->dlog;
+    h->log_cap = ctx->log_cap;
+    double ht = *dt;
+    if (h->t + ht >= t_end) {
+        ht = t_end - h->t;
+        h->last = 1;
+    }
+    if (!(ht > 0.0) || h->t + ht == h->t) return GS_ERR_STEP_UNDERFLOW;
+    h->dt_try = ht;
+    gs_status st;
+    if ((st = upload_ctrl(ctx)) != GS_OK) return st;
+    CK(launch_dopri5_k1(ctx, ctx->stream));
+    cudaGraphExec_t ex;
+    if ((st = get_loop_graph(ctx, G_DOPRI5_ADAPT, &ex)) != GS_OK) return st;
+    CK(cudaGraphLaunch(ex, ctx->stream));
+    CK(launch_copy_back(ctx));
+    if ((st = download_ctrl_sync(ctx)) != GS_OK) return st;
+    *t = h->t;
+    *dt = h->dt;
+    if (n_accepted) *n_accepted = (long)h->n_acc;
+    if (n_rejected) *n_rejected = (long)h->n_rej;
+    return (gs_status)h->status;
+}
+
+gs_status gs_set_step_log(gs_ctx* ctx, long capacity) {
+    if (!ctx || capacity < 0) return GS_ERR_INVALID;
+    if (ctx->dlog) {
+        CK(cudaFree(ctx->dlog));
+        ctx->dlog = nullptr;
+    }
+    ctx->log_cap = 0;
+    if (capacity > 0) {
+        CK(cudaMalloc(&ctx->dlog, sizeof(double) * (size_t)capacity));
+        ctx->log_cap = capacity;
+    }
+    return GS_OK;
+}
+
+gs_status gs_get_step_log(gs_ctx* ctx, double* dts, long capacity, long* count) {
+    if (!ctx || capacity < 0 || (capacity > 0 && !dts)) return GS_ERR_INVALID;
+    const long n = (long)ctx->hctrl->n_acc;
+    if (count) *count = n;
+    const long m = std::min(std::min(n, capacity), ctx->log_cap);
+    if (m > 0) {
+        CK(cudaMemcpyAsync(dts, ctx->dlog, sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return GS_OK;
+}
+
+gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc) {
+    if (!ctx) return GS_ERR_INVALID;
+    if (!(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 1 || zc > 1024)
+        return GS_ERR_INVALID;
+    if (ctx->ty != ty || ctx->zc != zc) drop_graphs(ctx);
+    ctx->ty = ty;
+    ctx->zc = zc;
+    return GS_OK;
+}
+
+gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc) {
+    if (!ctx || !ty || !zc) return GS_ERR_INVALID;
+    *ty = ctx->ty;
+    *zc = ctx->zc;
+    return GS_OK;
+}
+
+gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
+    if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
+    static const int cand[][2] = {{4, 16}, {4, 32}, {6, 16}, {6, 32}, {6, 64}, {8, 32},
+                                  {8, 64}, {14, 32}, {14, 64}, {2, 64}};
+    const int old_ty = ctx->ty, old_zc = ctx->zc;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bty = old_ty, bzc = old_zc;
+    gs_status st = GS_OK;
+    for (const auto& c : cand) {
+        ctx->ty = c[0];
+        ctx->zc = c[1];
+        // fixed Dormand-Prince steps from the bound state: every output goes
+        // to the context's second buffers (parity is reset to 0 before each
+        // repetition), so the caller's arrays are only read
+        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+        if ((st = upload_ctrl(ctx)) != GS_OK) break;
+        cudaError_t ek = launch_dopri5_k1(ctx, ctx->stream);
+        if (ek != cudaSuccess) {
+            set_err(ctx, ek, "autotune k1");
+            st = GS_ERR_CUDA;
+            break;
+        }
+        float ms_sum = 0.f;
+        const int reps = 3;
+        for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
+            CK(cudaEventRecord(e0, ctx->stream));
+            cudaError_t e = body_dopri5(ctx, ctx->stream, 0, 0);
+            if (e != cudaSuccess) {
+                set_err(ctx, e, "autotune");
+                st = GS_ERR_CUDA;
+                break;
+            }
+            CK(cudaEventRecord(e1, ctx->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) ms_sum += ms;
+            ctx->hctrl->parity = 0;
+            ctx->hctrl->step = 0;
+            st = upload_ctrl(ctx);
+        }
+        if (st != GS_OK) break;
+        CK(cudaStreamSynchronize(ctx->stream));  // hctrl is rewritten for the next candidate
+        const float ms = ms_sum / reps;
+        if (ms < best) {
+            best = ms;
+            bty = c[0];
+            bzc = c[1];
+        }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->ty = old_ty;
+    ctx->zc = old_zc;
+    if (st != GS_OK) return st;
+    gs_set_tile(ctx, bty, bzc);
+    if (ty_out) *ty_out = bty;
+    if (zc_out) *zc_out = bzc;
+    if (best_ms) *best_ms = best;
+    return GS_OK;
+}
+
+const char* gs_last_error(const gs_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+}  // extern "C"

@@ -1,0 +1,279 @@
+"""GPU parity of the Gray-Scott path (Eq. 2 + Table 1 steppers) against the
+CPU FP64 oracle, element by element on the same seeded inputs.
+
+Tolerances (relative L2 over both components): FP64 path <= 1e-12, FP32 path
+<= 1e-5 (against the FP64 oracle started from the same FP32-rounded state).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+from tests._gpu_common import cuda_or_skip, periodic_box, to_np
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_TOL = 1e-5
+
+
+def _gs(torch, dims, prec, u0, v0, **phys):
+    import paper_2309_05331_b300 as gs
+    nx, ny, nz = dims
+    g = gs.GrayScott(nx, ny, nz, prec=prec, **phys)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    return g
+
+
+def _round32(a):
+    return a.astype(np.float32).astype(np.float64)
+
+
+DIMS = [(8, 8, 8), (9, 6, 5), (33, 17, 40), (64, 31, 30), (1, 1, 1), (2, 3, 1), (61, 14, 3), (32, 32, 32)]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_rhs_fp64(dims):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    u0, v0 = si.gs_initial_state(*dims, seed=11)
+    phys = dict(L=2.5, Ly=1.9, Lz=3.3, Du=2e-3, Dv=1e-3)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    fu, fv = g.rhs()
+    torch.cuda.synchronize()
+    eu, ev = oracle.gs_rhs(oracle.GSParams(*dims, **phys), u0, v0)
+    assert oracle.rel_l2([to_np(fu), to_np(fv)], [eu, ev]) < 1e-14
+    g.close()
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8), (33, 17, 40), (61, 14, 3)])
+def test_rhs_fp32(dims):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    u0, v0 = si.gs_initial_state(*dims, seed=12)
+    u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, dims, gs.GS_FP32, u0, v0)
+    fu, fv = g.rhs()
+    torch.cuda.synchronize()
+    eu, ev = oracle.gs_rhs(oracle.GSParams(*dims), u0, v0)
+    assert oracle.rel_l2([to_np(fu), to_np(fv)], [eu, ev]) < 1e-6
+    g.close()
+
+
+def test_rk4_32cubed_fp64_100_steps():
+    """Gray-Scott 32^3, dt = 0.1, 100 RK4 steps, FP64 (the small fixed-step workload)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 32
+    u0, v0 = si.gs_initial_state(n, n, n, seed=0)
+    g = _gs(torch, (n, n, n), gs.GS_FP64, u0, v0)
+    t = g.step(gs.GS_RK4, 0.0, 0.1, 100)
+    assert t == pytest.approx(10.0, abs=1e-12)
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(n, n, n), u0, v0, oracle.RK4, 0.1, 100)
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    g.close()
+
+
+def test_rk4_32cubed_fp32():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 32
+    u0, v0 = si.gs_initial_state(n, n, n, seed=0)
+    u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
+    g.step(gs.GS_RK4, 0.0, 0.1, 100)
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(n, n, n), u0, v0, oracle.RK4, 0.1, 100)
+    err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov])
+    assert err < FP32_TOL, err
+    g.close()
+
+
+@pytest.mark.parametrize("method", ["euler", "rk4", "dopri5", "ab4"])
+@pytest.mark.parametrize("nsteps", [1, 2, 3, 4, 7])
+def test_fixed_step_methods_fp64(method, nsteps):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (37, 10, 7)
+    phys = dict(Du=3e-3, Dv=1.5e-3)
+    u0, v0 = si.gs_initial_state(*dims, seed=21)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    dt = 0.2
+    m = {"euler": gs.GS_EULER, "rk4": gs.GS_RK4, "dopri5": gs.GS_DOPRI5, "ab4": gs.GS_AB4}[method]
+    g.step(m, 0.0, dt, nsteps)
+    p = oracle.GSParams(*dims, **phys)
+    if method == "ab4":
+        ou, ov = oracle.gs_integrate_ab4(p, u0, v0, dt, nsteps)
+    else:
+        om = {"euler": oracle.EULER, "rk4": oracle.RK4, "dopri5": oracle.DOPRI5}[method]
+        ou, ov = oracle.gs_integrate_const(p, u0, v0, om, dt, nsteps)
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    g.close()
+
+
+@pytest.mark.parametrize("tile", [(2, 1), (4, 3), (6, 32), (8, 5), (14, 64)])
+def test_tile_shape_does_not_change_results(tile):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (45, 29, 19)
+    u0, v0 = si.gs_initial_state(*dims, seed=31)
+    res = []
+    for ty, zc in [(6, 32), tile]:
+        g = _gs(torch, dims, gs.GS_FP64, u0, v0, Du=2e-3, Dv=1e-3)
+        gs.gs_set_tile(g.ctx, ty, zc)
+        g.step(gs.GS_DOPRI5, 0.0, 0.3, 3)
+        res.append((to_np(g.u), to_np(g.v)))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_adaptive_fp64_matches_oracle_run():
+    """Error-controlled Dopri5 on 16^3 FP64: same accepted/rejected counts and
+    step sizes as the oracle's own adaptive run, final state within 1e-12."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (16, 16, 16)
+    phys = dict(Du=2e-3, Dv=1e-3)
+    u0, v0 = si.gs_initial_state(*dims, seed=2)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    gs.gs_set_step_log(g.ctx, 10000)
+    r = g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 0.1)
+    dts, cnt = gs.gs_get_step_log(g.ctx, 10000)
+    ref = oracle.gs_integrate_adaptive(oracle.GSParams(*dims, **phys), u0, v0, 0.0, 20.0, 0.1, 1e-8, 1e-8,
+                                       log_cap=10000)
+    assert ref["status"] == 0 and r["status"] == 0
+    assert r["t"] == 20.0 and ref["t"] == 20.0
+    assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"])
+    assert np.allclose(dts, ref["dts"], rtol=1e-9, atol=0)
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]]) < FP64_TOL
+    g.close()
+
+
+def test_adaptive_fp32_against_fp64_oracle():
+    """FP32 stage arithmetic with FP64 control vs the FP64 oracle (32^3, tol 1e-6)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 32
+    u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+    u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
+    r = g.integrate_adaptive(1e-6, 1e-6, 0.0, 50.0, 0.1)
+    ref = oracle.gs_integrate_adaptive(oracle.GSParams(n, n, n), u0, v0, 0.0, 50.0, 0.1, 1e-6, 1e-6)
+    assert r["status"] == 0 and r["t"] == 50.0
+    assert abs(r["n_acc"] - ref["n_acc"]) <= max(1, 0.01 * ref["n_acc"])
+    err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]])
+    assert err < FP32_TOL, err
+    g.close()
+
+
+def test_adaptive_max_accepted_and_time_accounting():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (20, 12, 9)
+    u0, v0 = si.gs_initial_state(*dims, seed=4)
+    g = _gs(torch, dims, gs.GS_FP32, u0, v0)
+    gs.gs_set_step_log(g.ctx, 100)
+    r = g.integrate_adaptive(1e-6, 1e-6, 1.5, math.inf, 0.1, max_accepted=7)
+    dts, cnt = gs.gs_get_step_log(g.ctx, 100)
+    assert r["n_acc"] == 7 and cnt == 7
+    assert r["t"] == pytest.approx(1.5 + float(np.sum(dts)), rel=1e-15)
+    g.close()
+
+
+def test_nonfinite_state_is_reported():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (12, 12, 12)
+    u0, v0 = si.gs_initial_state(*dims, seed=5)
+    u0[3, 4, 5] = np.nan
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0)
+    r = g.integrate_adaptive(1e-6, 1e-6, 0.0, 1.0, 0.1, check=False)
+    assert r["status"] == gs.GS_ERR_NONFINITE
+    g.close()
+
+
+@pytest.mark.parametrize("prec,rtol", [(0, 1e-300), (1, 1e-30)])
+def test_unreachable_tolerance_underflows(prec, rtol):
+    """atol = 0 and a tolerance no step can meet: rejections shrink dt by 5x
+    each until t + dt == t at t = 1 (about 22 attempts), then STEP_UNDERFLOW."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (8, 8, 8)
+    u0, v0 = si.gs_initial_state(*dims, seed=6)
+    g = _gs(torch, dims, prec, u0, v0)
+    before = to_np(g.u)
+    r = g.integrate_adaptive(0.0, rtol, 1.0, 2.0, 0.1, check=False)
+    assert r["status"] == gs.GS_ERR_STEP_UNDERFLOW
+    assert r["n_acc"] == 0 and 15 < r["n_rej"] < 40
+    # rejected attempts leave the state untouched
+    assert np.array_equal(to_np(g.u), before)
+    g.close()
+
+
+def test_invalid_calls():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    g = _gs(torch, (8, 8, 8), gs.GS_FP64, *si.gs_initial_state(8, 8, 8))
+    with pytest.raises(gs.GSError):
+        g.step(17, 0.0, 0.1, 1)
+    with pytest.raises(gs.GSError):
+        g.step(gs.GS_RK4, 0.0, 0.1, -1)
+    with pytest.raises(gs.GSError):
+        gs.gs_set_tile(g.ctx, 5, 8)
+    assert g.step(gs.GS_RK4, 0.0, 0.1, 0) == 0.0
+    g.close()
+
+
+def _light_cone_check(state_after, u0, v0, dims, method, dt, nsteps, radius, centers, tol):
+    """Oracle values of sampled cells computed on periodic boxes around them
+    (the dependence cone of nsteps steps lies inside the box)."""
+    num, den = 0.0, 0.0
+    gu, gv = state_after
+    h = [2.5 / n for n in dims]
+    e = 2 * radius + 1
+    p = oracle.GSParams(e, e, e, L=e * h[0], Ly=e * h[1], Lz=e * h[2])
+    for c in centers:
+        bu, bv = periodic_box(u0, c, radius), periodic_box(v0, c, radius)
+        ou, ov = oracle.gs_integrate_const(p, bu, bv, method, dt, nsteps)
+        ref = np.array([ou[radius, radius, radius], ov[radius, radius, radius]])
+        got = np.array([gu[c], gv[c]])
+        num += float(np.sum((got - ref) ** 2))
+        den += float(np.sum(ref ** 2))
+    err = math.sqrt(num / den)
+    assert err < tol, err
+
+
+def test_full_size_256cubed_fp32_dopri5_sampled():
+    """256^3 FP32 (the large adaptive workload's grid and kernels, autotuned
+    tile): 3 fixed Dopri5 steps, 12 sampled cells against the oracle on their
+    dependence cones (radius 6 per step)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 256
+    u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+    u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
+    gs.gs_autotune(g.ctx)
+    g.step(gs.GS_DOPRI5, 0.0, 0.5, 3)
+    gu, gv = to_np(g.u), to_np(g.v)
+    rng = np.random.default_rng(0)
+    centers = [tuple(int(a) for a in rng.integers(0, n, 3)) for _ in range(8)]
+    centers += [(0, 0, 0), (255, 255, 255), (128, 100, 96), (96, 96, 159)]
+    _light_cone_check((gu, gv), u0, v0, (n, n, n), oracle.DOPRI5, 0.5, 3, 19, centers, FP32_TOL)
+    g.close()
+
+
+def test_full_size_256cubed_adaptive_properties():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 256
+    u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+    g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
+    gs.gs_set_step_log(g.ctx, 100)
+    r = g.integrate_adaptive(1e-6, 1e-6, 0.0, math.inf, 0.1, max_accepted=10)
+    dts, cnt = gs.gs_get_step_log(g.ctx, 100)
+    assert r["status"] == 0 and r["n_acc"] == 10 and cnt == 10
+    assert r["t"] == pytest.approx(float(np.sum(dts)), rel=1e-14)
+    assert bool(torch.isfinite(g.u).all()) and bool(torch.isfinite(g.v).all())
+    g.close()
