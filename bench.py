@@ -1,0 +1,398 @@
+"""Benchmark of the explicit time-stepping hot path on B300.
+
+Workload (one bench step): the 3D Gray-Scott system (Eq. 2) on a 256^3
+periodic grid, [0,2.5]^3, Du=2e-5, Dv=1e-5, F=0.053, k=0.014, centred-cube
+initial state with +-0.01 seeded noise, advanced by ERROR-CONTROLLED
+Dormand-Prince 5(4) (atol = rtol = 1e-6) for 10 accepted steps: FP32 stencil /
+stage arithmetic, FP64 error-norm reduction, controller and time.  Rejected
+attempts are cost, not steps.  Metric: cell-steps/s = cells x accepted steps /
+time.  The working set (u, v and 8 stage fields, 1.3 GB) is far larger than
+L2, so no flush is needed between timed steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun): every rank integrates its own independent 256^3 problem
+(replicas; no data-path collective), value = all ranks' cell-steps / max time.
+--impl reference times the CPU FP64 oracle on the same workload, a bounded
+sample per step (one accepted step of the same grid), on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gray-Scott cell-steps/s & HBM roofline %; surrogate speedup at matched L2 error"
+UNIT = "cell-steps/s"
+N = 256
+ACC_PER_STEP = 10
+TOL = 1e-6
+DT0 = 0.1
+WORKLOAD = ("gray-scott 256^3 periodic [0,2.5]^3, Du=2e-5 Dv=1e-5 F=0.053 k=0.014, cube+noise init (seed 2), "
+            "adaptive Dormand-Prince 5(4) atol=rtol=1e-6, FP32 stencil/stage, FP64 norm/control/time, "
+            "10 accepted steps per bench step")
+
+# Per-cell algorithmic bytes of each kernel of one Dormand-Prince attempt in
+# FP32 (2 components x 4 B per field pass): k1 kernel reads u, writes k1;
+# stage i (2..6) reads u, k1..k_{i-1} and writes k_i; stage 7 reads u, k1,
+# k3..k6 and writes y5, k7.
+STAGE_NAMES = ["k1", "stage2", "stage3", "stage4", "stage5", "stage6", "stage7"]
+STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
+BYTES_PER_FIELD_CELL = 8
+ATTEMPT_FIELDS = sum(STAGE_FIELDS[1:])  # 33 field passes per attempt (k1 is reused)
+
+# DRAM traffic of the dominant kernel from one ncu capture (profiles/
+# gs_stage7_fp32_256cubed.md); valid only while the kernel source is unchanged.
+NCU_TRAFFIC = {"kernel": None, "source_sha": None, "bytes_per_launch": None}
+
+
+def _kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("gs_tile.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2309_05331_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in out.splitlines():
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The oracle (CPU FP64, single-threaded) on the same workload: each step
+    is one accepted Dormand-Prince step of the full 256^3 grid."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    import synthetic_inputs as si
+    u0, v0 = si.gs_initial_state(N, N, N, seed=2)
+    u = u0.astype(np.float32).astype(np.float64)
+    v = v0.astype(np.float32).astype(np.float64)
+    p = oracle.GSParams(N, N, N)
+    t, dt = 0.0, DT0
+    times, acc = [], 0
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.gs_integrate_adaptive(p, u, v, t, math.inf, dt, TOL, TOL, max_acc=1)
+        el = time.perf_counter() - t0
+        u, v, t, dt = r["u"], r["v"], r["t"], r["dt"]
+        if i >= args.warmup:
+            times.append(el)
+            acc += r["n_acc"]
+    total = sum(times)
+    value = N ** 3 * acc / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.replace("10 accepted steps per bench step",
+                                                     "1 accepted step per bench step (bounded CPU sample)"),
+                       "grid": [N, N, N], "accepted_per_step": 1},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+                             "sample": f"one accepted Dormand-Prince step of the full {N}^3 grid per step, "
+                                       "FP64 oracle (plain C, single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline_sample():
+    """Oracle time for one accepted Dormand-Prince step of the 256^3 grid."""
+    import numpy as np
+
+    import oracle
+    import synthetic_inputs as si
+    u0, v0 = si.gs_initial_state(N, N, N, seed=2)
+    u = u0.astype(np.float32).astype(np.float64)
+    v = v0.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    r = oracle.gs_integrate_adaptive(oracle.GSParams(N, N, N), u, v, 0.0, math.inf, DT0, TOL, TOL, max_acc=1)
+    el = time.perf_counter() - t0
+    return {"value": N ** 3 * r["n_acc"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"one accepted Dormand-Prince step of the full {N}^3 grid ({el:.1f} s, "
+                      f"{r['n_acc'] + r['n_rej']} attempt(s)), FP64 oracle, plain C, single thread"}
+
+
+def extra_workloads(torch, gs, si):
+    """The other configurations, timed once each (context, not the headline)."""
+    out = {}
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    stream = torch.cuda.current_stream()
+    # Gray-Scott 32^3 FP64 RK4 dt=0.1 x 100 steps
+    n = 32
+    u0, v0 = si.gs_initial_state(n, n, n, seed=0)
+    g = gs.GrayScott(n, n, n, prec=gs.GS_FP64)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    g.step(gs.GS_RK4, 0.0, 0.1, 100)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    a, b = ev(), ev()
+    a.record(stream)
+    g.step(gs.GS_RK4, 0.0, 0.1, 100)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    out["gs_32cubed_fp64_rk4_dt0.1_x100"] = {"ms": ms, "cell_steps_per_s": n ** 3 * 100 / (ms * 1e-3)}
+    g.close()
+    # pointwise ODEs, 2^24 FP64
+    m = 1 << 24
+    x0 = torch.from_numpy(si.ode_initial_values(m, seed=1)).cuda()
+    ws = torch.empty(gs.ode_workspace_size(m), dtype=torch.uint8, device="cuda")
+    for kind, name in ((gs.ODE_EXP_DECAY, "exp_decay"), (gs.ODE_LOGISTIC, "logistic")):
+        x = x0.clone()
+        a, b = ev(), ev()
+        a.record(stream)
+        r = gs.ode_integrate_adaptive(kind, x, 0.0, 10.0, 1e-3, 1e-8, 1e-8, workspace=ws)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[f"ode_2^24_fp64_dopri5_{name}_tol1e-8_t10"] = {
+            "ms": ms, "accepted": r["n_acc"], "rejected": r["n_rej"],
+            "element_steps_per_s": m * r["n_acc"] / (ms * 1e-3)}
+        x = x0.clone()
+        a, b = ev(), ev()
+        a.record(stream)
+        gs.ode_integrate_ab4(kind, x, 0.0, 1e-3, 10000)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {"ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3)}
+    out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=256, help="grid edge (profiling of smaller cases)")
+    ap.add_argument("--tile", default=None, help="fixed tile 'ty,zc' instead of the autotuner")
+    args = ap.parse_args()
+    global N, WORKLOAD
+    if args.grid != N:
+        WORKLOAD = WORKLOAD.replace("256^3", f"{args.grid}^3")
+        N = args.grid
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2309_05331_b300 as gs
+    import synthetic_inputs as si
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    stream = torch.cuda.current_stream()
+    u0, v0 = si.gs_initial_state(N, N, N, seed=2 + rank)
+    g = gs.GrayScott(N, N, N, prec=gs.GS_FP32)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    if args.tile:
+        ty, zc = (int(a) for a in args.tile.split(","))
+        gs.gs_set_tile(g.ctx, ty, zc)
+        tile = (ty, zc, None)
+    else:
+        tile = gs.gs_autotune(g.ctx)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+
+    t, dt = 0.0, DT0
+    for _ in range(args.warmup):
+        r = g.integrate_adaptive(TOL, TOL, t, math.inf, dt, max_accepted=ACC_PER_STEP)
+        t, dt = r["t"], r["dt"]
+
+    sampler = ClockSampler(dev)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    acc = rej = 0
+    launches = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        r = g.integrate_adaptive(TOL, TOL, t, math.inf, dt, max_accepted=ACC_PER_STEP)
+        t, dt = r["t"], r["dt"]
+        acc += r["n_acc"]
+        rej += r["n_rej"]
+        launches += 2 + 6 * (r["n_acc"] + r["n_rej"])  # k1, copy-back, 6 stage kernels per attempt
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    acc_all = acc
+    if ws > 1:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(tt.item())
+        ta = torch.tensor([acc], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(ta)
+        acc_all = int(ta.item())
+    cells = N ** 3
+    value = cells * acc_all / (ms_max * 1e-3)
+
+    # end to end through the C ABI with host buffers: pinned host -> device,
+    # integrate, device -> host, every step
+    hu = torch.from_numpy(u0.astype(np.float32)).pin_memory()
+    hv = torch.from_numpy(v0.astype(np.float32)).pin_memory()
+    te, dte = 0.0, DT0
+    for _ in range(args.warmup):
+        gs.gs_upload_state(g.ctx, hu, hv)
+        r = g.integrate_adaptive(TOL, TOL, te, math.inf, dte, max_accepted=ACC_PER_STEP)
+        te, dte = r["t"], r["dt"]
+        gs.gs_download_state(g.ctx, hu, hv)
+    barrier()
+    torch.cuda.synchronize()
+    acc_e = 0
+    e0.record(stream)
+    for _ in range(args.steps):
+        gs.gs_upload_state(g.ctx, hu, hv)
+        r = g.integrate_adaptive(TOL, TOL, te, math.inf, dte, max_accepted=ACC_PER_STEP)
+        te, dte = r["t"], r["dt"]
+        acc_e += r["n_acc"]
+        gs.gs_download_state(g.ctx, hu, hv)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e = e0.elapsed_time(e1)
+    if ws > 1:
+        tt = torch.tensor([ms_e, acc_e], device="cuda", dtype=torch.float64)
+        tmax = tt.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(tt)
+        ms_e, acc_e = float(tmax[0].item()), int(tt[1].item())
+    e2e_value = cells * acc_e / (ms_e * 1e-3)
+
+    # roofline of the dominant kernel: each kernel of one attempt timed alone
+    # with CUDA events on the launching (context) stream
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    stage_ms = gs.gs_time_stages(g.ctx, reps=5)
+    peak, peak_kind = _peaks()
+    dom = max(range(1, 7), key=lambda i: stage_ms[i])
+    dom_bytes = STAGE_FIELDS[dom] * BYTES_PER_FIELD_CELL * cells
+    achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
+    attempt_ms = sum(stage_ms[1:])
+    attempt_gbs = ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]:
+        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
+                "measured" else "fallback 6.4 TB/s",
+                "kernel": f"gs_stage_kernel {STAGE_NAMES[dom]} (FP32)",
+                "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
+                "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
+                "attempt": {"algorithmic_bytes_per_cell": ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL,
+                            "ms": attempt_ms, "achieved_gbs": attempt_gbs, "frac": attempt_gbs / peak}}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "control_dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "grid": [N, N, N], "accepted_per_step": ACC_PER_STEP,
+                           "tolerance": TOL, "tile_ty_zc": [tile[0], tile[1]],
+                           "l2": "inputs larger than L2 (u, v + 8 stage fields = 1.3 GB per GPU); no flush",
+                           "parallelism": f"replicas x{ws} (independent problems, no collective)"},
+                "accepted_steps": acc_all, "rejected_attempts_rank0": rej,
+                "gpu_launches": launches,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * cells * 4,
+                        "d2h_bytes_per_step": 2 * cells * 4},
+                "roofline": roofline, "clocks": clocks}
+    g.close()
+    if rank == 0:
+        if ws == 1 and not args.no_extras:
+            line["workloads"] = extra_workloads(torch, gs, si)
+        if ws == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

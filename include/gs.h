@@ -149,6 +149,15 @@ gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
  * modified), selects the fastest, and returns it.  best_ms may be NULL. */
 gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
 
+/* Measurement aid: launches the kernels of one Dormand-Prince attempt of
+ * the bound state one at a time between CUDA events on the context stream
+ * and returns their average durations over `reps` repetitions (after one
+ * warm-up): ms[0] = the k1 = F(u) kernel, ms[1..6] = stages 2..7 (stage 7
+ * includes the error-norm reduction).  Outputs go to the context's scratch;
+ * the bound state is not modified.  ms: host array of 7 doubles.
+ * Synchronises. */
+gs_status gs_time_stages(gs_ctx* ctx, int reps, double* ms);
+
 /* Text of the last CUDA error seen by ctx ("" if none). */
 const char* gs_last_error(const gs_ctx* ctx);
 /* Text of the last CUDA error seen by a context-free entry point. */

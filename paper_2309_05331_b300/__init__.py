@@ -57,6 +57,7 @@ _SIGNATURES = {
     "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
+    "gs_time_stages": ([_vp, C.c_int, _dp], C.c_int),
     "gs_last_error": ([_vp], C.c_char_p),
     "gs_last_global_error": ([], C.c_char_p),
     "ode_axpy_stage": ([C.c_long, C.c_int, C.c_int, _dp, C.POINTER(_vp), _vp, _vp], C.c_int),
@@ -186,6 +187,13 @@ def gs_autotune(ctx):
     a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
     _check(lib().gs_autotune(ctx, C.byref(a), C.byref(b), C.byref(ms)), ctx)
     return a.value, b.value, ms.value
+
+
+def gs_time_stages(ctx, reps=5):
+    """Average durations (ms) of the k1 kernel and Dormand-Prince stages 2..7."""
+    ms = (C.c_double * 7)()
+    _check(lib().gs_time_stages(ctx, reps, ms), ctx)
+    return list(ms)
 
 
 def ode_axpy_stage(coef, xs, y, stream=None):

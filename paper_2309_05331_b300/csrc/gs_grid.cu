@@ -245,33 +245,31 @@ static cudaError_t body_ab4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     return launch_stage(ctx, s, 0, MODE_FINAL, A);
 }
 
-// Dormand-Prince stages 2..7 with k1 in the parity pair (fields 1, 2) and
-// k2..k6 in fields 3..7; stage 7 writes y5 and k7 to the other buffers of
-// their pairs and reduces the error norm.
-static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+// Dormand-Prince stage st (2..7) with k1 in the parity pair (fields 1, 2)
+// and k2..k6 in fields 3..7; stage 7 writes y5 and k7 to the other buffers
+// of their pairs and reduces the error norm.
+static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsigned long long h,
+                                       int use_cond) {
     const Slot k1 = pair_sel(ctx, 1, 2, SEL_CUR);
     const Slot k[7] = {k1, k1, fld(ctx, 3), fld(ctx, 4), fld(ctx, 5), fld(ctx, 6), fld(ctx, 7)};
     // k[i] = k_i for i = 1..6
-    const double A2[1] = {dp5::A21};
-    const double A3[2] = {dp5::A31, dp5::A32};
-    const double A4[3] = {dp5::A41, dp5::A42, dp5::A43};
-    const double A5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
-    const double A6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
-    const double* rows[5] = {A2, A3, A4, A5, A6};
-    cudaError_t e;
-    for (int st = 2; st <= 6; ++st) {
-        StageArgs A = base_args(ctx);
-        A.u = state_sel(ctx, SEL_CUR);
+    static const double A2[1] = {dp5::A21};
+    static const double A3[2] = {dp5::A31, dp5::A32};
+    static const double A4[3] = {dp5::A41, dp5::A42, dp5::A43};
+    static const double A5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
+    static const double A6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
+    static const double* rows[5] = {A2, A3, A4, A5, A6};
+    StageArgs A = base_args(ctx);
+    A.u = state_sel(ctx, SEL_CUR);
+    if (st < 7) {
         const int nk = st - 1;
         for (int j = 0; j < nk; ++j) {
             A.kin[j] = k[j + 1];
             A.a[j] = rows[st - 2][j];
         }
         A.out0 = k[st];
-        if ((e = launch_stage(ctx, s, nk, MODE_STAGE, A)) != cudaSuccess) return e;
+        return launch_stage(ctx, s, nk, MODE_STAGE, A);
     }
-    StageArgs A = base_args(ctx);
-    A.u = state_sel(ctx, SEL_CUR);
     A.kin[0] = k[1];
     A.kin[1] = k[3];
     A.kin[2] = k[4];
@@ -289,6 +287,14 @@ static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h
     A.cond = h;
     A.use_cond = use_cond;
     return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A);
+}
+
+static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+    for (int st = 2; st <= 7; ++st) {
+        cudaError_t e = launch_dopri5_stage(ctx, s, st, h, use_cond);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // k1 = F(u) into the current k1 buffer (start of a Dormand-Prince run)
@@ -708,6 +714,41 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (ty_out) *ty_out = bty;
     if (zc_out) *zc_out = bzc;
     if (best_ms) *best_ms = best;
+    return GS_OK;
+}
+
+gs_status gs_time_stages(gs_ctx* ctx, int reps, double* ms) {
+    if (!ctx || !ctx->state[0] || reps < 1 || !ms) return GS_ERR_INVALID;
+    cudaEvent_t ev[8];
+    for (int i = 0; i < 8; ++i) CK(cudaEventCreate(&ev[i]));
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    gs_status st = GS_OK;
+    for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
+        // fixed-step control block, parity 0: outputs go to the context's
+        // second buffers only; the bound state is read, never written
+        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+        if ((st = upload_ctrl(ctx)) != GS_OK) break;
+        cudaError_t e = cudaEventRecord(ev[0], ctx->stream);
+        if (e == cudaSuccess) e = launch_dopri5_k1(ctx, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], ctx->stream);
+        for (int k = 2; k <= 7 && e == cudaSuccess; ++k) {
+            e = launch_dopri5_stage(ctx, ctx->stream, k, 0, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[k], ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[7]);
+        for (int k = 0; k < 7 && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            if (r > 0) acc[k] += t;  // repetition 0 is a warm-up
+        }
+        if (e != cudaSuccess) {
+            set_err(ctx, e, "gs_time_stages");
+            st = GS_ERR_CUDA;
+        }
+    }
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+    if (st != GS_OK) return st;
+    for (int k = 0; k < 7; ++k) ms[k] = acc[k] / reps;
     return GS_OK;
 }
 

@@ -145,7 +145,8 @@ def test_adaptive_fp64_matches_oracle_run():
     assert ref["status"] == 0 and r["status"] == 0
     assert r["t"] == 20.0 and ref["t"] == 20.0
     assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"])
-    assert np.allclose(dts, ref["dts"], rtol=1e-9, atol=0)
+    # E is a cancelling sum: FMA vs non-FMA rounding moves it by ~1e-9 relative
+    assert np.allclose(dts, ref["dts"], rtol=1e-7, atol=0), np.max(np.abs(dts / ref["dts"] - 1))
     assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]]) < FP64_TOL
     g.close()
 
@@ -195,17 +196,20 @@ def test_nonfinite_state_is_reported():
 
 @pytest.mark.parametrize("prec,rtol", [(0, 1e-300), (1, 1e-30)])
 def test_unreachable_tolerance_underflows(prec, rtol):
-    """atol = 0 and a tolerance no step can meet: rejections shrink dt by 5x
-    each until t + dt == t at t = 1 (about 22 attempts), then STEP_UNDERFLOW."""
+    """atol = 0 and a tolerance no step can meet.  The problem is autonomous,
+    so it starts at t = 1e12, where t + dt == t once dt < 6e-5: rejections
+    shrink dt by 5x each (0.1, 0.02, ...) and STEP_UNDERFLOW follows after a
+    handful of attempts, while every attempted step still changes the state
+    (so the error estimate stays far above the tolerance)."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     dims = (8, 8, 8)
     u0, v0 = si.gs_initial_state(*dims, seed=6)
     g = _gs(torch, dims, prec, u0, v0)
     before = to_np(g.u)
-    r = g.integrate_adaptive(0.0, rtol, 1.0, 2.0, 0.1, check=False)
+    r = g.integrate_adaptive(0.0, rtol, 1e12, 2e12, 0.1, check=False)
     assert r["status"] == gs.GS_ERR_STEP_UNDERFLOW
-    assert r["n_acc"] == 0 and 15 < r["n_rej"] < 40
+    assert r["n_acc"] == 0 and 2 <= r["n_rej"] <= 10, r
     # rejected attempts leave the state untouched
     assert np.array_equal(to_np(g.u), before)
     g.close()

