@@ -231,7 +231,7 @@ def extra_workloads(torch, gs, si):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")
@@ -286,6 +286,7 @@ def main():
     barrier()
     torch.cuda.synchronize()
     sampler.start()
+    time.sleep(0.5)  # let nvidia-smi start sampling before the timed region
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     acc = rej = 0
     launches = 0
