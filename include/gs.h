@@ -202,6 +202,32 @@ gs_status ode_integrate_adaptive(ode_rhs rhs, long n, double* x_dev, double* t, 
                                  size_t workspace_bytes, double* dt_log, long log_cap,
                                  void* stream);
 
+/* Allocation-free form of ode_integrate_adaptive (the paper has no
+ * counterpart; it exists for callers that cannot allocate GPU memory when
+ * they integrate: a host application that owns every device allocation
+ * through its own pool, a real-time loop where cudaMalloc's implicit device
+ * synchronisation and latency are not allowed, or a plugin that may only use
+ * memory it was handed).  Same method, norm, controller, arguments and
+ * results as ode_integrate_adaptive, without the workspace and step log: its
+ * scratch (control block + one second state buffer) is a static device array
+ * of 256 B + 8 MiB compiled into the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - n must be <= 1048576 (2^20) elements, else GS_ERR_INVALID with the
+ *     reason in gs_last_global_error().
+ *   - Calls no cudaMalloc/cudaFree and allocates no host or device memory;
+ *     the attempts are driven by a host loop (one stream synchronisation per
+ *     16 attempts) instead of a graph.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call on a device shares the one array and rewrites its control
+ *     block at the start; calls that overlap on the GPU (other streams, other
+ *     host threads) race on it and must be serialised by the caller.
+ * Synchronises the stream. */
+gs_status ode_integrate_adaptive_noalloc(ode_rhs rhs, long n, double* x_dev, double* t,
+                                         double t_end, double* dt, double atol, double rtol,
+                                         long max_steps, long* n_acc, long* n_rej, void* stream);
+
 /* Adams-Bashforth 4 (Table 1) for nsteps steps of size dt from t0; the first
  * three steps by RK4.  All steps of an element run in registers in one
  * kernel (no global synchronisation is needed between fixed steps).

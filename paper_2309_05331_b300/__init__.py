@@ -64,6 +64,8 @@ _SIGNATURES = {
     "ode_workspace_size": ([C.c_long], C.c_size_t),
     "ode_integrate_adaptive": ([C.c_int, C.c_long, _vp, _dp, C.c_double, _dp, C.c_double, C.c_double,
                                 C.c_long, _lp, _lp, _vp, C.c_size_t, _vp, C.c_long, _vp], C.c_int),
+    "ode_integrate_adaptive_noalloc": ([C.c_int, C.c_long, _vp, _dp, C.c_double, _dp, C.c_double, C.c_double,
+                                        C.c_long, _lp, _lp, _vp], C.c_int),
     "ode_integrate_ab4": ([C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
     "ode_integrate_const": ([C.c_int, C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
     "gs_measure_fp64_peak": ([_dp, _vp], C.c_int),
@@ -224,6 +226,17 @@ def ode_integrate_adaptive(kind, x, t, t_end, dt, atol, rtol, max_steps=-1, work
     st = lib().ode_integrate_adaptive(kind, n, _ptr(x), C.byref(tt), t_end, C.byref(dd), atol, rtol, max_steps,
                                       C.byref(na), C.byref(nr), _ptr(workspace), workspace.numel(),
                                       _ptr(dt_log), 0 if dt_log is None else dt_log.numel(), _stream(stream))
+    if check:
+        _check(st)
+    return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}
+
+
+def ode_integrate_adaptive_noalloc(kind, x, t, t_end, dt, atol, rtol, max_steps=-1, stream=None, check=True):
+    """ode_integrate_adaptive without a workspace (static scratch, n <= 2^20)."""
+    tt, dd = C.c_double(t), C.c_double(dt)
+    na, nr = C.c_long(0), C.c_long(0)
+    st = lib().ode_integrate_adaptive_noalloc(kind, x.numel(), _ptr(x), C.byref(tt), t_end, C.byref(dd), atol,
+                                              rtol, max_steps, C.byref(na), C.byref(nr), _stream(stream))
     if check:
         _check(st)
     return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}

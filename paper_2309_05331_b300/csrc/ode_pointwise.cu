@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "host_util.h"
@@ -324,3 +325,122 @@ gs_status ode_integrate_const(ode_rhs kind, gs_method method, long n, double* x,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of ode_integrate_adaptive.
+//
+// Some callers cannot allocate GPU memory at the time they integrate: code
+// that runs under a host application which owns every device allocation
+// through its own pool, real-time loops where cudaMalloc's implicit device
+// synchronisation and unbounded latency are not allowed, or plugins that may
+// only touch memory they were handed.  For them the scratch of the adaptive
+// driver (control block + second state buffer) lives in this file-scope
+// device array instead of a caller workspace.  Every GPU that loads the
+// library holds the array until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr long kStaticMaxElements = 1L << 20;  // 8 MiB of FP64 state
+static __device__ __align__(256) unsigned char g_ode_static_scratch[kCtrlBytes + 8 * kStaticMaxElements];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of the static scratch for the current device (looked up
+// once per device; the host-side symbol is only a stand-in).
+cudaError_t static_scratch_address(void** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_ode_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_addr[dev] = p;
+    }
+    *out = g_static_addr[dev];
+    return cudaSuccess;
+}
+
+__global__ void ctrl_init_kernel(DevCtrl* c, DevCtrl v) { *c = v; }
+
+}  // namespace
+
+extern "C" gs_status ode_integrate_adaptive_noalloc(ode_rhs kind, long n, double* x, double* t, double t_end,
+                                                   double* dt, double atol, double rtol, long max_steps,
+                                                   long* n_acc, long* n_rej, void* stream) {
+    if ((kind != ODE_EXP_DECAY && kind != ODE_LOGISTIC) || n < 0 || !t || !dt) return GS_ERR_INVALID;
+    if (n > kStaticMaxElements) {
+        set_global_error(cudaErrorInvalidValue,
+                         "ode_integrate_adaptive_noalloc: n exceeds the static scratch capacity of 1048576 elements");
+        return GS_ERR_INVALID;
+    }
+    if (n > 0 && !x) return GS_ERR_INVALID;
+    if (!(atol >= 0) || !(rtol >= 0) || !(atol > 0 || rtol > 0) || !(*dt > 0) || std::isnan(t_end))
+        return GS_ERR_INVALID;
+    if (n_acc) *n_acc = 0;
+    if (n_rej) *n_rej = 0;
+    if (!(*t < t_end) || max_steps == 0 || n == 0) return GS_OK;
+
+    DevCtrl h;
+    memset(&h, 0, sizeof(h));
+    h.mode = CTRL_ADAPTIVE;
+    h.t = *t;
+    h.t0 = *t;
+    h.t_end = t_end;
+    h.dt = *dt;
+    h.atol = atol;
+    h.rtol = rtol;
+    h.max_acc = max_steps < 0 ? -1 : max_steps;
+    h.max_att = kMaxAttempts;
+    double ht = *dt;
+    if (h.t + ht >= t_end) {
+        ht = t_end - h.t;
+        h.last = 1;
+    }
+    if (!(ht > 0.0) || h.t + ht == h.t) return GS_ERR_STEP_UNDERFLOW;
+    h.dt_try = ht;
+
+    void* base = nullptr;
+    GCK(static_scratch_address(&base));
+    DevCtrl* dc = (DevCtrl*)base;
+    double* xb = (double*)((unsigned char*)base + kCtrlBytes);
+    cudaStream_t s = (cudaStream_t)stream;
+
+    // the array keeps the previous call's contents: the whole control block
+    // (counters, error accumulator, arrival counter, parity) is rewritten
+    ctrl_init_kernel<<<1, 1, 0, s>>>(dc, h);
+    GCK(cudaGetLastError());
+    int grid = 0;
+    if (kind == ODE_EXP_DECAY)
+        grid = persistent_grid(ode_dp5_attempt_kernel<ODE_EXP_DECAY>, 256, n);
+    else
+        grid = persistent_grid(ode_dp5_attempt_kernel<ODE_LOGISTIC>, 256, n);
+    // host-driven loop: batches of attempts, then one look at `done`; the
+    // attempt kernel does nothing once the run has ended
+    const int kBatch = 16;
+    int done = 0;
+    while (!done) {
+        for (int b = 0; b < kBatch; ++b) {
+            if (kind == ODE_EXP_DECAY)
+                ode_dp5_attempt_kernel<ODE_EXP_DECAY><<<grid, 256, 0, s>>>(n, x, xb, dc, 0ull, 0);
+            else
+                ode_dp5_attempt_kernel<ODE_LOGISTIC><<<grid, 256, 0, s>>>(n, x, xb, dc, 0ull, 0);
+        }
+        GCK(cudaGetLastError());
+        GCK(cudaMemcpyAsync(&done, &dc->done, sizeof(int), cudaMemcpyDeviceToHost, s));
+        GCK(cudaStreamSynchronize(s));
+    }
+    copy_if_odd_kernel<double><<<sm_count() * 8, 256, 0, s>>>(dc, xb, x, n);
+    GCK(cudaGetLastError());
+    GCK(cudaMemcpyAsync(&h, dc, sizeof(DevCtrl), cudaMemcpyDeviceToHost, s));
+    GCK(cudaStreamSynchronize(s));
+    *t = h.t;
+    *dt = h.dt;
+    if (n_acc) *n_acc = (long)h.n_acc;
+    if (n_rej) *n_rej = (long)h.n_rej;
+    return (gs_status)h.status;
+}
