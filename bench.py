@@ -50,9 +50,10 @@ STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
 BYTES_PER_FIELD_CELL = 8
 ATTEMPT_FIELDS = sum(STAGE_FIELDS[1:])  # 33 field passes per attempt (k1 is reused)
 
-# DRAM traffic of the dominant kernel from one ncu capture (profiles/
-# gs_stage7_fp32_256cubed.md); valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"kernel": None, "source_sha": None, "bytes_per_launch": None}
+# DRAM traffic of the dominant kernel from one ncu capture at 192^3
+# (profiles/gs_stage7_fp32_192cubed_full.md: 452.2 MB per launch), scaled by
+# cells to 256^3; valid only while the kernel source is unchanged.
+NCU_TRAFFIC = {"kernel": "stage7", "source_sha": "6b1468d0ccd07ee2", "bytes_per_launch": 452179456 * (256 / 192) ** 3}
 
 
 def _kernel_source_sha():
