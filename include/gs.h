@@ -99,8 +99,9 @@ gs_status gs_upload_state(gs_ctx* ctx, const void* u_host, const void* v_host);
 gs_status gs_download_state(gs_ctx* ctx, void* u_host, void* v_host);
 
 /* One evaluation of the System F(t, (u,v)) (Listing 2):
- * (fu, fv) = F(t, (u, v)).  All four are device arrays of nx*ny*nz elements;
- * outputs must not alias inputs.  Enqueued on the context stream. */
+ * (fu, fv) = F(t, (u, v)).  All four are device arrays of nx*ny*nz elements,
+ * 16-byte aligned (else INVALID); outputs must not alias inputs.  Enqueued
+ * on the context stream. */
 gs_status gs_rhs(gs_ctx* ctx, double t, const void* u_dev, const void* v_dev, void* fu_dev,
                  void* fv_dev);
 
@@ -143,6 +144,13 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* co
  * 1 <= zc <= 1024.  Takes effect at the next integrator call. */
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);
 gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
+
+/* Stencil kernel form: 0 = automatic (the vectorised kernel -- 16-byte
+ * accesses, 4 FP32 or 2 FP64 cells per thread, 128- or 64-cell rows per
+ * warp -- when nx is a multiple of 4 (FP32) or 2 (FP64) cells, else the
+ * generic one-cell-per-thread kernel), 1 = generic, 2 = vectorised (INVALID
+ * if nx is not such a multiple).  Both compute the same formulas. */
+gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant);
 
 /* Times each candidate tile shape on one Dormand-Prince step from the bound
  * state (outputs go to the context's scratch only; the bound state is not

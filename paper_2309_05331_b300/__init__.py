@@ -55,6 +55,7 @@ _SIGNATURES = {
     "gs_set_step_log": ([_vp, C.c_long], C.c_int),
     "gs_get_step_log": ([_vp, _dp, C.c_long, _lp], C.c_int),
     "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gs_set_kernel_variant": ([_vp, C.c_int], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gs_time_stages": ([_vp, C.c_int, _dp], C.c_int),
@@ -177,6 +178,10 @@ def gs_get_step_log(ctx, capacity):
 
 def gs_set_tile(ctx, ty, zc):
     _check(lib().gs_set_tile(ctx, ty, zc), ctx)
+
+
+def gs_set_kernel_variant(ctx, variant):
+    _check(lib().gs_set_kernel_variant(ctx, variant), ctx)
 
 
 def gs_get_tile(ctx):

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_wide.cuh"
 #include "host_util.h"
 
 using namespace gsk;
@@ -50,6 +51,7 @@ struct gs_ctx {
     double* dlog = nullptr;
     long log_cap = 0;
     int ty = 6, zc = 32;
+    int variant = 0;  // 0 automatic, 1 generic, 2 vectorised
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -88,13 +90,29 @@ static Geom<T> make_geom(const gs_params& p) {
     return g;
 }
 
+// vectorised kernel applicable: x-extent a multiple of the 16-byte vector width
+static bool wide_ok(const gs_ctx* ctx) {
+    const int vx = ctx->p.prec == GS_FP64 ? 2 : 4;
+    return ctx->p.nx % vx == 0;
+}
+static bool use_wide(const gs_ctx* ctx) {
+    return ctx->variant == 2 || (ctx->variant == 0 && wide_ok(ctx));
+}
+
 template <typename T, int NK, int MODE>
 static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     const Geom<T> g = make_geom<T>(ctx->p);
-    const size_t smem = stage_smem_bytes<T>(A.ty);
-    auto kern = gs_stage_kernel<T, NK, MODE>;
+    const bool wide = use_wide(ctx);
+    auto kern = wide ? gs_stage_wide_kernel<T, NK, MODE> : gs_stage_kernel<T, NK, MODE>;
+    const int txw = wide ? 32 * wide_vx<T>() : kTileX;
+    if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
+    A.ntx = (ctx->p.nx + txw - 1) / txw;
+    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
+    const size_t smem = wide ? wide_smem_bytes<T>(A.ty) : stage_smem_bytes<T>(A.ty);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int occ = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const long long ntiles = (long long)A.ntx * A.nty * A.ntz;
@@ -109,22 +127,28 @@ static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs&
     return launch_stage_t<float, NK, MODE>(ctx, s, A);
 }
 
+// Instantiated (NK, mode) pairs: stages with 0..5 inputs, final combinations
+// with 0 (Euler, Adams-Bashforth) or 1 (RK4) halo inputs, Dormand-Prince
+// stage 7 with 5.
 static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A) {
-#define GS_DISPATCH_MODE(NKV)                                                       \
-    case NKV:                                                                       \
-        if (mode == MODE_STAGE) return launch_stage_nk<NKV, MODE_STAGE>(ctx, s, A); \
-        if (mode == MODE_FINAL) return launch_stage_nk<NKV, MODE_FINAL>(ctx, s, A); \
-        return launch_stage_nk<NKV, MODE_DOPRI_FINAL>(ctx, s, A);
-    switch (nk) {
-        GS_DISPATCH_MODE(0)
-        GS_DISPATCH_MODE(1)
-        GS_DISPATCH_MODE(2)
-        GS_DISPATCH_MODE(3)
-        GS_DISPATCH_MODE(4)
-        GS_DISPATCH_MODE(5)
-        default: return cudaErrorInvalidValue;
+    if (mode == MODE_STAGE) {
+        switch (nk) {
+            case 0: return launch_stage_nk<0, MODE_STAGE>(ctx, s, A);
+            case 1: return launch_stage_nk<1, MODE_STAGE>(ctx, s, A);
+            case 2: return launch_stage_nk<2, MODE_STAGE>(ctx, s, A);
+            case 3: return launch_stage_nk<3, MODE_STAGE>(ctx, s, A);
+            case 4: return launch_stage_nk<4, MODE_STAGE>(ctx, s, A);
+            case 5: return launch_stage_nk<5, MODE_STAGE>(ctx, s, A);
+            default: return cudaErrorInvalidValue;
+        }
     }
-#undef GS_DISPATCH_MODE
+    if (mode == MODE_FINAL) {
+        if (nk == 0) return launch_stage_nk<0, MODE_FINAL>(ctx, s, A);
+        if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A);
+        return cudaErrorInvalidValue;
+    }
+    if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A);
+    return cudaErrorInvalidValue;
 }
 
 static StageArgs base_args(gs_ctx* ctx) {
@@ -517,6 +541,7 @@ gs_status gs_download_state(gs_ctx* ctx, void* uh, void* vh) {
 gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, void* fv) {
     (void)t;  // the Gray-Scott system is autonomous
     if (!ctx || !u || !v || !fu || !fv) return GS_ERR_INVALID;
+    if (((uintptr_t)u | (uintptr_t)v | (uintptr_t)fu | (uintptr_t)fv) & 15) return GS_ERR_INVALID;
     StageArgs A = base_args(ctx);
     A.ctrl = nullptr;
     A.u = slot_fixed(const_cast<void*>(u), const_cast<void*>(v));
@@ -648,6 +673,14 @@ gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc) {
     if (!ctx || !ty || !zc) return GS_ERR_INVALID;
     *ty = ctx->ty;
     *zc = ctx->zc;
+    return GS_OK;
+}
+
+gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant) {
+    if (!ctx || variant < 0 || variant > 2) return GS_ERR_INVALID;
+    if (variant == 2 && !wide_ok(ctx)) return GS_ERR_INVALID;
+    if (ctx->variant != variant) drop_graphs(ctx);
+    ctx->variant = variant;
     return GS_OK;
 }
 

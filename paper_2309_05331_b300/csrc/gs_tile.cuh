@@ -44,6 +44,7 @@ constexpr int kTileX = 30;      // interior columns per CTA (32 lanes incl. 2 ha
 constexpr int kMaxNK = 5;       // stage inputs combined into Y
 constexpr int kMaxNE = 3;       // pointwise inputs of a final combination
 constexpr int kMaxTY = 14;      // rows per tile (CTA = 32 x (ty+2) <= 512 threads)
+constexpr int kMaxTYFinal = 6;  // final kernels: CTA <= 256 threads (more registers per thread)
 
 struct StageArgs {
     Slot u;                 // state the stage starts from
@@ -81,7 +82,7 @@ __device__ __forceinline__ int wrap1(int a, int n) {
 }
 
 template <typename T, int NK, int MODE>
-__global__ void __launch_bounds__(512) gs_stage_kernel(const Geom<T> g, const StageArgs A) {
+__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_kernel(const Geom<T> g, const StageArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     __shared__ T red[32];

@@ -1,0 +1,385 @@
+// gs_wide.cuh -- vectorised form of the fused Gray-Scott stage kernel for
+// grids whose x-extent is a multiple of the 16-byte vector width (4 FP32 or
+// 2 FP64 cells).  Same arithmetic contract as gs_stage_kernel (gs_tile.cuh):
+//   Y = u + dt sum_j a_j k_j,  f = F(Y),  mode-specific epilogue.
+//
+// Mapping: a warp owns one row of 32*VX cells (VX cells per lane, one 16-byte
+// load per field and component), a CTA owns ty such rows plus one halo row
+// above and below (warps 0 and ty+1) and marches over zc planes.  The z
+// neighbours of a thread's cells stay in registers (planes z-1, z, z+1); only
+// the centre plane goes through shared memory (a 3-buffer ring, one barrier
+// per plane) for the y neighbours and the two x-halo columns, which the first
+// and last active lanes load.  x neighbours inside the row come from warp
+// shuffles.  The stage-7 error terms that do not depend on k7 are folded into
+// two numbers per cell when the plane is loaded, so the epilogue of the next
+// iteration carries 2 values per cell and component instead of 6.
+#pragma once
+
+#include "gs_tile.cuh"
+
+namespace gsk {
+
+template <typename T>
+struct VecT;
+template <>
+struct VecT<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct VecT<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+
+template <typename T>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T* out);
+template <>
+__device__ __forceinline__ void ldv<float>(const float* __restrict__ p, float* out) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = q.x;
+    out[1] = q.y;
+    out[2] = q.z;
+    out[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ldv<double>(const double* __restrict__ p, double* out) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    out[0] = q.x;
+    out[1] = q.y;
+}
+
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const T* v);
+template <>
+__device__ __forceinline__ void stv<float>(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <>
+__device__ __forceinline__ void stv<double>(double* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+}
+
+// 16-byte shared-memory accesses (addresses are 16-byte aligned by the pitch)
+template <typename T>
+__device__ __forceinline__ void sts_v(T* p, const T* v) {
+    stv<T>(p, v);
+}
+template <typename T>
+__device__ __forceinline__ void lds_v(const T* p, T* out) {
+    using VTy = typename VecT<T>::type;
+    const VTy q = *reinterpret_cast<const VTy*>(p);
+    const T* qs = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int v = 0; v < VecT<T>::n; ++v) out[v] = qs[v];
+}
+
+template <typename T>
+__device__ __forceinline__ T fast_ratio(T a, T b) {
+    return a / b;
+}
+template <>
+__device__ __forceinline__ float fast_ratio<float>(float a, float b) {
+    return __fdividef(a, b);  // error ratio: a few ulp are irrelevant to the controller
+}
+
+template <typename T>
+__host__ __device__ constexpr int wide_vx() {
+    return 16 / (int)sizeof(T);
+}
+template <typename T>
+__host__ __device__ constexpr int wide_pitch() {
+    return 32 * wide_vx<T>() + wide_vx<T>();  // row of cells + 2 halo columns, 16-byte aligned
+}
+template <typename T>
+__host__ __device__ inline size_t wide_smem_bytes(int ty) {
+    return sizeof(T) * 3 * (size_t)(ty + 2) * 2 * wide_pitch<T>();
+}
+
+// Per-cell values a final epilogue needs from the plane's inputs.
+template <typename T, int NK, int MODE, int VX>
+struct Carry {
+    // FINAL: u and the stage inputs; DOPRI_FINAL: error scale and folded error terms
+    T a[2][VX];
+    T b[MODE == MODE_FINAL ? (NK > 0 ? NK : 1) : 1][2][VX];
+};
+
+template <typename T, int NK, int MODE>
+__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_kernel(const Geom<T> g, const StageArgs A) {
+    constexpr int VX = wide_vx<T>();
+    constexpr int TXW = 32 * VX;
+    constexpr int PITCH = wide_pitch<T>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T red[32];
+    __shared__ int s_last;
+
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int TY = A.ty;
+    const int TYP = TY + 2;
+
+    int parity = 0;
+    long long step = 0;
+    double dtd = 0.0, atol = 0.0, rtol = 0.0;
+    int skip = 0;
+    if (A.ctrl) {
+        parity = A.ctrl->parity;
+        step = A.ctrl->step;
+        dtd = A.ctrl->dt_try;
+        atol = A.ctrl->atol;
+        rtol = A.ctrl->rtol;
+        skip = A.ctrl->done;
+    }
+    const T dt = (T)dtd;
+    const T ta = (T)atol, tr = (T)rtol;
+
+    const T* uin[2] = {resolve<T>(A.u, 0, parity, step), resolve<T>(A.u, 1, parity, step)};
+    const T* kin[NK > 0 ? NK : 1][2];
+    T aT[NK > 0 ? NK : 1];
+#pragma unroll
+    for (int j = 0; j < NK; ++j) {
+        kin[j][0] = resolve<T>(A.kin[j], 0, parity, step);
+        kin[j][1] = resolve<T>(A.kin[j], 1, parity, step);
+        aT[j] = (T)A.a[j];
+    }
+    T* o0[2] = {resolve<T>(A.out0, 0, parity, step), resolve<T>(A.out0, 1, parity, step)};
+    const T* exs[kMaxNE][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
+    if (MODE == MODE_FINAL) {
+        for (int j = 0; j < A.n_ex; ++j) {
+            exs[j][0] = resolve<T>(A.ex[j], 0, parity, step);
+            exs[j][1] = resolve<T>(A.ex[j], 1, parity, step);
+        }
+    }
+    T* o1[2] = {nullptr, nullptr};
+    if (MODE != MODE_STAGE && A.has_out1) {
+        o1[0] = resolve<T>(A.out1, 0, parity, step);
+        o1[1] = resolve<T>(A.out1, 1, parity, step);
+    }
+    // Dormand-Prince error weights of k3..k6 in T (kin = {k1, k3, k4, k5, k6})
+    const T ew[4] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5, (T)dp5::E6};
+    const T e7 = (T)dp5::E7;
+
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long plane = (long long)nx * ny;
+    T emax = T(0);
+
+    auto sidx = [&](int buf, int ww, int c, int col) -> int { return ((buf * TYP + ww) * 2 + c) * PITCH + col; };
+
+    // Y of VX cells at idx, and the epilogue's per-cell values
+    auto loadY = [&](long long idx, T (&Y)[2][VX], Carry<T, NK, MODE, VX>& cr) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            T uu[VX];
+            ldv<T>(uin[c] + idx, uu);
+            T s[VX], k1[VX], q[VX];
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                s[v] = T(0);
+                q[v] = T(0);
+                k1[v] = T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < NK; ++j) {
+                T kk[VX];
+                ldv<T>(kin[j][c] + idx, kk);
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                    s[v] = (j == 0) ? aT[0] * kk[v] : s[v] + aT[j] * kk[v];
+                    if (MODE == MODE_FINAL) cr.b[j][c][v] = kk[v];
+                    if (MODE == MODE_DOPRI_FINAL) {
+                        if (j == 0)
+                            k1[v] = kk[v];
+                        else
+                            q[v] += ew[j - 1] * (kk[v] - k1[v]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s[v];
+                if (MODE == MODE_FINAL) cr.a[c][v] = uu[v];
+                if (MODE == MODE_DOPRI_FINAL) {
+                    cr.a[c][v] = ta + tr * (fabs(uu[v]) + dt * fabs(k1[v]));  // error scale
+                    cr.b[0][c][v] = q[v] - e7 * k1[v];                       // folded error terms
+                }
+            }
+        }
+    };
+    // Y of one cell (x-halo column)
+    auto loadY1 = [&](long long idx, int c) -> T {
+        const T uu = __ldg(uin[c] + idx);
+        if (NK == 0) return uu;
+        T s = aT[0] * __ldg(kin[0][c] + idx);
+#pragma unroll
+        for (int j = 1; j < NK; ++j) s += aT[j] * __ldg(kin[j][c] + idx);
+        return uu + dt * s;
+    };
+
+    if (!skip) {
+        const int ntiles = A.ntx * A.nty * A.ntz;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int tx = tile % A.ntx;
+            const int rr = tile / A.ntx;
+            const int tyi = rr % A.nty;
+            const int tz = rr / A.nty;
+            const int x0 = tx * TXW, y0 = tyi * TY, z0 = tz * A.zc;
+            const int z1 = min(z0 + A.zc, nz);
+            const int aw = min(TXW, nx - x0);
+            const int nl = aw / VX;  // active lanes
+            const int ah = min(TY, ny - y0);
+            const bool irow = (w >= 1) && (w <= ah);
+            const bool act = (w <= ah + 1) && (lane < nl);
+            const bool inner = irow && (lane < nl);
+            const bool do_left = irow && (lane == 0);
+            const bool do_right = irow && (lane == nl - 1);
+            const int y = wrap1(y0 - 1 + w, ny);
+            const long long rowb = (long long)nx * y;
+            const long long cbase = rowb + x0 + VX * lane;
+            const long long lbase = rowb + wrap1(x0 - 1, nx);
+            const long long rbase = rowb + wrap1(x0 + aw, nx);
+
+            T ym[2][VX], yc[2][VX], yp[2][VX];
+            Carry<T, NK, MODE, VX> cur, nxt;
+            {
+                const int b0 = 0;  // plane z0 -> buffer 0, z0+1 -> 1, ...
+                if (inner) loadY(cbase + plane * wrap1(z0 - 1, nz), ym, nxt);
+                if (act) {
+                    loadY(cbase + plane * z0, yc, cur);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(b0, w, c, VX * lane), yc[c]);
+                }
+                if (do_left)
+                    for (int c = 0; c < 2; ++c) S[sidx(b0, w, c, TXW)] = loadY1(lbase + plane * z0, c);
+                if (do_right)
+                    for (int c = 0; c < 2; ++c) S[sidx(b0, w, c, TXW + 1)] = loadY1(rbase + plane * z0, c);
+            }
+            int bz = 0;  // buffer of plane z
+            for (int z = z0; z < z1; ++z) {
+                const int bn = (bz == 2) ? 0 : bz + 1;  // buffer of plane z+1
+                const long long zoff = plane * wrap1(z + 1, nz);
+                if (act) {
+                    loadY(cbase + zoff, yp, nxt);
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(bn, w, c, VX * lane), yp[c]);
+                }
+                if (do_left)
+                    for (int c = 0; c < 2; ++c) S[sidx(bn, w, c, TXW)] = loadY1(lbase + zoff, c);
+                if (do_right)
+                    for (int c = 0; c < 2; ++c) S[sidx(bn, w, c, TXW + 1)] = loadY1(rbase + zoff, c);
+                __syncthreads();
+                T xl[2], xr[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    xl[c] = __shfl_up_sync(0xffffffffu, yc[c][VX - 1], 1);
+                    xr[c] = __shfl_down_sync(0xffffffffu, yc[c][0], 1);
+                }
+                if (inner) {
+                    T lap[2][VX];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (lane == 0) xl[c] = S[sidx(bz, w, c, TXW)];
+                        if (lane == nl - 1) xr[c] = S[sidx(bz, w, c, TXW + 1)];
+                        T ys[VX], yn[VX];
+                        lds_v<T>(S + sidx(bz, w - 1, c, VX * lane), ys);
+                        lds_v<T>(S + sidx(bz, w + 1, c, VX * lane), yn);
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const T xm = (v == 0) ? xl[c] : yc[c][v - 1];
+                            const T xp = (v == VX - 1) ? xr[c] : yc[c][v + 1];
+                            const T yy = yc[c][v];
+                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
+                                        (ym[c][v] - T(2) * yy + yp[c][v]) * g.cz;
+                        }
+                    }
+                    T f[2][VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        const T uvv = yc[0][v] * yc[1][v] * yc[1][v];
+                        f[0][v] = g.Du * lap[0][v] - uvv + g.F * (T(1) - yc[0][v]);
+                        f[1][v] = g.Dv * lap[1][v] + uvv - (g.F + g.k) * yc[1][v];
+                    }
+                    const long long i = cbase + plane * z;
+                    if (MODE == MODE_STAGE) {
+                        stv<T>(o0[0] + i, f[0]);
+                        stv<T>(o0[1] + i, f[1]);
+                    } else if (MODE == MODE_FINAL) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            T s[VX];
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) {
+                                s[v] = (T)A.bf * f[c][v];
+#pragma unroll
+                                for (int j = 0; j < NK; ++j) s[v] += (T)A.bk[j] * cur.b[j][c][v];
+                            }
+#pragma unroll
+                            for (int j = 0; j < kMaxNE; ++j) {
+                                if (j < A.n_ex) {
+                                    T e[VX];
+                                    ldv<T>(exs[j][c] + i, e);
+#pragma unroll
+                                    for (int v = 0; v < VX; ++v) s[v] += (T)A.be[j] * e[v];
+                                }
+                            }
+                            T o[VX];
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) o[v] = cur.a[c][v] + dt * s[v];
+                            stv<T>(o0[c] + i, o);
+                            if (A.has_out1) stv<T>(o1[c] + i, f[c]);
+                        }
+                    } else {  // MODE_DOPRI_FINAL
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            stv<T>(o0[c] + i, yc[c]);
+                            stv<T>(o1[c] + i, f[c]);
+                            if (NK == 5) {
+#pragma unroll
+                                for (int v = 0; v < VX; ++v) {
+                                    const T err = dt * (cur.b[0][c][v] + e7 * f[c][v]);
+                                    emax = nanmax(emax, fast_ratio<T>(fabs(err), cur.a[c][v]));
+                                }
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        ym[c][v] = yc[c][v];
+                        yc[c][v] = yp[c][v];
+                    }
+                cur = nxt;
+                bz = bn;
+            }
+            __syncthreads();  // the smem ring is reused by the next tile
+        }
+    }
+
+    if (MODE != MODE_STAGE && A.run_ctrl && A.ctrl) {
+        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+        if (MODE == MODE_DOPRI_FINAL) {
+            const T bmax = block_nanmax(emax, red);
+            if (tid == 0) atomic_max_nonneg(&A.ctrl->err_bits, (double)bmax);
+        }
+        if (tid == 0) {
+            __threadfence();
+            const unsigned prev = atomicAdd(&A.ctrl->arrive, 1u);
+            s_last = (prev == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (s_last && tid == 0) {
+            __threadfence();
+            DevCtrl* c = A.ctrl;
+            const double E = __longlong_as_double((long long)atomicOr(&c->err_bits, 0ull));
+            c->err_bits = 0ull;
+            c->arrive = 0u;
+            int cont = 0;
+            if (!c->done) cont = controller_update(c, E);
+            if (A.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, cont ? 1u : 0u);
+        }
+    }
+}
+
+}  // namespace gsk

@@ -90,12 +90,12 @@ def test_rk4_32cubed_fp32():
     g.close()
 
 
+@pytest.mark.parametrize("dims", [(37, 10, 7), (36, 10, 7)])  # generic / vectorised kernel
 @pytest.mark.parametrize("method", ["euler", "rk4", "dopri5", "ab4"])
 @pytest.mark.parametrize("nsteps", [1, 2, 3, 4, 7])
-def test_fixed_step_methods_fp64(method, nsteps):
+def test_fixed_step_methods_fp64(dims, method, nsteps):
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
-    dims = (37, 10, 7)
     phys = dict(Du=3e-3, Dv=1.5e-3)
     u0, v0 = si.gs_initial_state(*dims, seed=21)
     g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
@@ -112,11 +112,11 @@ def test_fixed_step_methods_fp64(method, nsteps):
     g.close()
 
 
+@pytest.mark.parametrize("dims", [(45, 29, 19), (44, 29, 19), (264, 9, 5)])
 @pytest.mark.parametrize("tile", [(2, 1), (4, 3), (6, 32), (8, 5), (14, 64)])
-def test_tile_shape_does_not_change_results(tile):
+def test_tile_shape_does_not_change_results(dims, tile):
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
-    dims = (45, 29, 19)
     u0, v0 = si.gs_initial_state(*dims, seed=31)
     res = []
     for ty, zc in [(6, 32), tile]:
@@ -126,6 +126,40 @@ def test_tile_shape_does_not_change_results(tile):
         res.append((to_np(g.u), to_np(g.v)))
         g.close()
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2)])
+def test_kernel_variants_match_oracle(prec, dims):
+    """The generic (one cell per thread) and vectorised (16-byte rows) stencil
+    kernels on the same grid: both against the oracle, Dopri5 and RK4 steps."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    phys = dict(Du=3e-3, Dv=1.5e-3)
+    u0, v0 = si.gs_initial_state(*dims, seed=41)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    p = oracle.GSParams(*dims, **phys)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    for method, om in ((gs.GS_DOPRI5, oracle.DOPRI5), (gs.GS_RK4, oracle.RK4)):
+        ou, ov = oracle.gs_integrate_const(p, u0, v0, om, 0.25, 3)
+        for variant in (1, 2):
+            g = _gs(torch, dims, prec, u0, v0, **phys)
+            gs.gs_set_kernel_variant(g.ctx, variant)
+            g.step(method, 0.0, 0.25, 3)
+            err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov])
+            g.close()
+            assert err < tol, (variant, method, err)
+
+
+def test_vectorised_variant_rejects_unaligned_rows():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    g = _gs(torch, (10, 4, 4), gs.GS_FP32, *si.gs_initial_state(10, 4, 4))
+    with pytest.raises(gs.GSError):
+        gs.gs_set_kernel_variant(g.ctx, 2)
+    gs.gs_set_kernel_variant(g.ctx, 1)
+    g.close()
 
 
 def test_adaptive_fp64_matches_oracle_run():
