@@ -276,6 +276,7 @@ def main():
         tile = (ty, zc, None)
     else:
         tile = gs.gs_autotune(g.ctx)
+    variant = gs.gs_get_kernel_variant(g.ctx)
     g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
 
     t, dt = 0.0, DT0
@@ -363,7 +364,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
-                "kernel": f"gs_stage_kernel {STAGE_NAMES[dom]} (FP32)",
+                "kernel": f"{'gs_stage_wide_kernel' if variant == 2 else 'gs_stage_kernel'} {STAGE_NAMES[dom]} (FP32)",
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
                 "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
                 "attempt": {"algorithmic_bytes_per_cell": ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL,
@@ -377,6 +378,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "accepted_per_step": ACC_PER_STEP,
                            "tolerance": TOL, "tile_ty_zc": [tile[0], tile[1]],
+                           "stencil_kernel": "vectorised" if variant == 2 else "generic",
                            "l2": "inputs larger than L2 (u, v + 8 stage fields = 1.3 GB per GPU); no flush",
                            "parallelism": f"replicas x{ws} (independent problems, no collective)"},
                 "accepted_steps": acc_all, "rejected_attempts_rank0": rej,

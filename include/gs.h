@@ -139,9 +139,11 @@ gs_status gs_set_step_log(gs_ctx* ctx, long capacity);
  * the number recorded by the last call (may exceed capacity). Synchronises. */
 gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* count);
 
-/* Tile shape of the stencil kernels: ty rows of 30 interior cells per CTA
- * (CTA = 32 x (ty+2) threads), marching over zc planes.  ty in {2,4,6,8,14},
- * 1 <= zc <= 1024.  Takes effect at the next integrator call. */
+/* Tile shape of the stencil kernels: a CTA of 32 x (ty+2) threads works on
+ * columns of ty rows (30 cells wide in the generic kernel, 128 FP32 / 64 FP64
+ * cells in the vectorised one) and owns an equal share, of at least zc
+ * planes, of all columns' planes.  ty in {2,4,6,8,14} (final kernels use at
+ * most 6), 1 <= zc <= 1024.  Takes effect at the next integrator call. */
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);
 gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
 
@@ -151,10 +153,14 @@ gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
  * generic one-cell-per-thread kernel), 1 = generic, 2 = vectorised (INVALID
  * if nx is not such a multiple).  Both compute the same formulas. */
 gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant);
+/* The stencil kernel form the next call will use: 1 generic, 2 vectorised. */
+gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use);
 
-/* Times each candidate tile shape on one Dormand-Prince step from the bound
- * state (outputs go to the context's scratch only; the bound state is not
- * modified), selects the fastest, and returns it.  best_ms may be NULL. */
+/* Times each candidate tile shape -- and, when the kernel variant is
+ * automatic and both forms apply, each kernel form -- on one Dormand-Prince
+ * step from the bound state (outputs go to the context's scratch only; the
+ * bound state is not modified), selects the fastest, and returns its tile.
+ * best_ms may be NULL. */
 gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
 
 /* Measurement aid: launches the kernels of one Dormand-Prince attempt of

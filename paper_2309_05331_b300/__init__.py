@@ -56,6 +56,7 @@ _SIGNATURES = {
     "gs_get_step_log": ([_vp, _dp, C.c_long, _lp], C.c_int),
     "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gs_set_kernel_variant": ([_vp, C.c_int], C.c_int),
+    "gs_get_kernel_variant": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gs_time_stages": ([_vp, C.c_int, _dp], C.c_int),
@@ -182,6 +183,12 @@ def gs_set_tile(ctx, ty, zc):
 
 def gs_set_kernel_variant(ctx, variant):
     _check(lib().gs_set_kernel_variant(ctx, variant), ctx)
+
+
+def gs_get_kernel_variant(ctx):
+    v = C.c_int(0)
+    _check(lib().gs_get_kernel_variant(ctx, C.byref(v)), ctx)
+    return v.value
 
 
 def gs_get_tile(ctx):

@@ -51,7 +51,8 @@ struct gs_ctx {
     double* dlog = nullptr;
     long log_cap = 0;
     int ty = 6, zc = 32;
-    int variant = 0;  // 0 automatic, 1 generic, 2 vectorised
+    int variant = 0;       // requested: 0 automatic, 1 generic, 2 vectorised
+    bool auto_wide = true;  // automatic choice (set by the autotuner)
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -96,7 +97,7 @@ static bool wide_ok(const gs_ctx* ctx) {
     return ctx->p.nx % vx == 0;
 }
 static bool use_wide(const gs_ctx* ctx) {
-    return ctx->variant == 2 || (ctx->variant == 0 && wide_ok(ctx));
+    return ctx->variant == 2 || (ctx->variant == 0 && ctx->auto_wide && wide_ok(ctx));
 }
 
 template <typename T, int NK, int MODE>
@@ -115,8 +116,10 @@ static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    const long long ntiles = (long long)A.ntx * A.nty * A.ntz;
-    const int grid = (int)std::min<long long>(ntiles, (long long)ctx->nsm * occ);
+    // every CTA owns at least zc planes of the (column, z) space
+    const long long L = (long long)A.ntx * A.nty * ctx->p.nz;
+    const long long gmax = std::max<long long>(1, L / std::max(1, A.zc));
+    const int grid = (int)std::min<long long>(gmax, (long long)ctx->nsm * occ);
     kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A);
     return cudaGetLastError();
 }
@@ -684,10 +687,16 @@ gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant) {
     return GS_OK;
 }
 
+gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use) {
+    if (!ctx || !in_use) return GS_ERR_INVALID;
+    *in_use = use_wide(ctx) ? 2 : 1;
+    return GS_OK;
+}
+
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
-    static const int cand[][2] = {{4, 16}, {4, 32}, {6, 16}, {6, 32}, {6, 64}, {8, 32},
-                                  {8, 64}, {14, 32}, {14, 64}, {2, 64}};
+    static const int cand[][2] = {{2, 32}, {4, 8}, {4, 32}, {6, 8}, {6, 32}, {8, 8},
+                                  {8, 32}, {14, 8}, {14, 32}};
     const int old_ty = ctx->ty, old_zc = ctx->zc;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -695,48 +704,60 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     float best = 1e30f;
     int bty = old_ty, bzc = old_zc;
     gs_status st = GS_OK;
-    for (const auto& c : cand) {
-        ctx->ty = c[0];
-        ctx->zc = c[1];
-        // fixed Dormand-Prince steps from the bound state: every output goes
-        // to the context's second buffers (parity is reset to 0 before each
-        // repetition), so the caller's arrays are only read
-        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
-        if ((st = upload_ctrl(ctx)) != GS_OK) break;
-        cudaError_t ek = launch_dopri5_k1(ctx, ctx->stream);
-        if (ek != cudaSuccess) {
-            set_err(ctx, ek, "autotune k1");
-            st = GS_ERR_CUDA;
-            break;
+    const bool try_both = ctx->variant == 0 && wide_ok(ctx);
+    const bool old_auto = ctx->auto_wide;
+    bool bwide = old_auto;
+    for (int vi = 0; vi < (try_both ? 2 : 1) && st == GS_OK; ++vi) {
+        if (try_both) {
+            ctx->auto_wide = (vi == 1);
+            drop_graphs(ctx);
         }
-        float ms_sum = 0.f;
-        const int reps = 3;
-        for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
-            CK(cudaEventRecord(e0, ctx->stream));
-            cudaError_t e = body_dopri5(ctx, ctx->stream, 0, 0);
-            if (e != cudaSuccess) {
-                set_err(ctx, e, "autotune");
+        for (const auto& c : cand) {
+            ctx->ty = c[0];
+            ctx->zc = c[1];
+            // fixed Dormand-Prince steps from the bound state: every output
+            // goes to the context's second buffers (parity is reset to 0
+            // before each repetition), so the caller's arrays are only read
+            init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+            if ((st = upload_ctrl(ctx)) != GS_OK) break;
+            cudaError_t ek = launch_dopri5_k1(ctx, ctx->stream);
+            if (ek != cudaSuccess) {
+                set_err(ctx, ek, "autotune k1");
                 st = GS_ERR_CUDA;
                 break;
             }
-            CK(cudaEventRecord(e1, ctx->stream));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (r > 0) ms_sum += ms;
-            ctx->hctrl->parity = 0;
-            ctx->hctrl->step = 0;
-            st = upload_ctrl(ctx);
-        }
-        if (st != GS_OK) break;
-        CK(cudaStreamSynchronize(ctx->stream));  // hctrl is rewritten for the next candidate
-        const float ms = ms_sum / reps;
-        if (ms < best) {
-            best = ms;
-            bty = c[0];
-            bzc = c[1];
+            float ms_sum = 0.f;
+            const int reps = 3;
+            for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
+                CK(cudaEventRecord(e0, ctx->stream));
+                cudaError_t e = body_dopri5(ctx, ctx->stream, 0, 0);
+                if (e != cudaSuccess) {
+                    set_err(ctx, e, "autotune");
+                    st = GS_ERR_CUDA;
+                    break;
+                }
+                CK(cudaEventRecord(e1, ctx->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (r > 0) ms_sum += ms;
+                ctx->hctrl->parity = 0;
+                ctx->hctrl->step = 0;
+                st = upload_ctrl(ctx);
+            }
+            if (st != GS_OK) break;
+            CK(cudaStreamSynchronize(ctx->stream));  // hctrl is rewritten for the next candidate
+            const float ms = ms_sum / reps;
+            if (ms < best) {
+                best = ms;
+                bty = c[0];
+                bzc = c[1];
+                bwide = ctx->auto_wide;
+            }
         }
     }
+    ctx->auto_wide = try_both ? bwide : old_auto;
+    drop_graphs(ctx);
     cudaStreamSynchronize(ctx->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

@@ -13,8 +13,8 @@
 //     DOPRI_FINAL : write Y (= the 5th-order solution) and f (= k7, reused as
 //                   the next k1), and reduce the scaled error norm.
 //
-// Tiling: persistent CTAs walk a list of tiles of 30 (x) by ty (y) interior
-// cells and zc planes (z).  A CTA has 32 x (ty + 2) threads: lane L covers
+// Tiling: persistent CTAs own equal shares of the (column, z-plane) space;
+// a column is 30 (x) by ty (y) interior cells.  A CTA has 32 x (ty + 2) threads: lane L covers
 // column x0 - 1 + L and warp w covers row y0 - 1 + w, so lanes 0 and 31 and
 // warps 0 and ty+1 load the xy-halo while the interior threads compute.  Y of
 // the current plane and its two z-neighbours live in a 4-slot shared-memory
@@ -154,14 +154,19 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_kerne
     };
 
     if (!skip) {
-        const int ntiles = A.ntx * A.nty * A.ntz;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int tx = tile % A.ntx;
-            const int rr = tile / A.ntx;
-            const int tyi = rr % A.nty;
-            const int tz = rr / A.nty;
-            const int x0 = tx * kTileX, y0 = tyi * TY, z0 = tz * A.zc;
-            const int z1 = min(z0 + A.zc, nz);
+        // balanced schedule: CTA b owns planes [L b / G, L (b+1) / G) of the
+        // linearised (column, z) space, L = columns * nz, cut into segments
+        // at column ends
+        const long long L = (long long)A.ntx * A.nty * nz;
+        const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
+        for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
+            const int col = (int)(sg / nz);
+            const int z0 = (int)(sg - (long long)col * nz);
+            const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
+            sg += z1 - z0;
+            const int tx = col % A.ntx;
+            const int tyi = col / A.ntx;
+            const int x0 = tx * kTileX, y0 = tyi * TY;
             const int aw = min(kTileX, nx - x0);
             const int ah = min(TY, ny - y0);
             const bool act = (lane <= aw + 1) && (w <= ah + 1);

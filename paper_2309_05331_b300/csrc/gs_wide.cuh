@@ -8,8 +8,8 @@
 // above and below (warps 0 and ty+1) and marches over zc planes.  The z
 // neighbours of a thread's cells stay in registers (planes z-1, z, z+1); only
 // the centre plane goes through shared memory (a 3-buffer ring, one barrier
-// per plane) for the y neighbours and the two x-halo columns, which the first
-// and last active lanes load.  x neighbours inside the row come from warp
+// per plane) for the y neighbours and the two x-halo columns, which the lanes
+// of the two halo warps load.  x neighbours inside the row come from warp
 // shuffles.  The stage-7 error terms that do not depend on k7 are folded into
 // two numbers per cell when the plane is loaded, so the epilogue of the next
 // iteration carries 2 values per cell and component instead of 6.
@@ -217,27 +217,35 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
     };
 
     if (!skip) {
-        const int ntiles = A.ntx * A.nty * A.ntz;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int tx = tile % A.ntx;
-            const int rr = tile / A.ntx;
-            const int tyi = rr % A.nty;
-            const int tz = rr / A.nty;
-            const int x0 = tx * TXW, y0 = tyi * TY, z0 = tz * A.zc;
-            const int z1 = min(z0 + A.zc, nz);
+        // balanced schedule over the (column, z) space, as in gs_stage_kernel
+        const long long L = (long long)A.ntx * A.nty * nz;
+        const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
+        for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
+            const int col = (int)(sg / nz);
+            const int z0 = (int)(sg - (long long)col * nz);
+            const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
+            sg += z1 - z0;
+            const int tx = col % A.ntx;
+            const int tyi = col / A.ntx;
+            const int x0 = tx * TXW, y0 = tyi * TY;
             const int aw = min(TXW, nx - x0);
             const int nl = aw / VX;  // active lanes
             const int ah = min(TY, ny - y0);
             const bool irow = (w >= 1) && (w <= ah);
             const bool act = (w <= ah + 1) && (lane < nl);
             const bool inner = irow && (lane < nl);
-            const bool do_left = irow && (lane == 0);
-            const bool do_right = irow && (lane == nl - 1);
             const int y = wrap1(y0 - 1 + w, ny);
             const long long rowb = (long long)nx * y;
             const long long cbase = rowb + x0 + VX * lane;
-            const long long lbase = rowb + wrap1(x0 - 1, nx);
-            const long long rbase = rowb + wrap1(x0 + aw, nx);
+            // x-halo columns of the interior rows: lane r-1 of the top halo
+            // warp takes the left column of row r, of the bottom halo warp
+            // the right column
+            const bool hwarp = (w == 0) || (w == ah + 1);
+            const bool do_halo = hwarp && (lane < ah);
+            const int hrow = lane + 1;
+            const int hcol = (w == 0) ? TXW : TXW + 1;
+            const long long hbase =
+                (long long)nx * wrap1(y0 + lane, ny) + ((w == 0) ? wrap1(x0 - 1, nx) : wrap1(x0 + aw, nx));
 
             T ym[2][VX], yc[2][VX], yp[2][VX];
             Carry<T, NK, MODE, VX> cur, nxt;
@@ -249,10 +257,8 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
                     for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(b0, w, c, VX * lane), yc[c]);
                 }
-                if (do_left)
-                    for (int c = 0; c < 2; ++c) S[sidx(b0, w, c, TXW)] = loadY1(lbase + plane * z0, c);
-                if (do_right)
-                    for (int c = 0; c < 2; ++c) S[sidx(b0, w, c, TXW + 1)] = loadY1(rbase + plane * z0, c);
+                if (do_halo)
+                    for (int c = 0; c < 2; ++c) S[sidx(b0, hrow, c, hcol)] = loadY1(hbase + plane * z0, c);
             }
             int bz = 0;  // buffer of plane z
             for (int z = z0; z < z1; ++z) {
@@ -263,10 +269,8 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
                     for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(bn, w, c, VX * lane), yp[c]);
                 }
-                if (do_left)
-                    for (int c = 0; c < 2; ++c) S[sidx(bn, w, c, TXW)] = loadY1(lbase + zoff, c);
-                if (do_right)
-                    for (int c = 0; c < 2; ++c) S[sidx(bn, w, c, TXW + 1)] = loadY1(rbase + zoff, c);
+                if (do_halo)
+                    for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
                 __syncthreads();
                 T xl[2], xr[2];
 #pragma unroll
