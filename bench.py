@@ -352,6 +352,7 @@ def main():
     # with CUDA events on the launching (context) stream
     g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
     stage_ms = gs.gs_time_stages(g.ctx, reps=5)
+    stage_cfg = gs.gs_get_stage_configs(g.ctx)
     peak, peak_kind = _peaks()
     dom = max(range(1, 7), key=lambda i: stage_ms[i])
     dom_bytes = STAGE_FIELDS[dom] * BYTES_PER_FIELD_CELL * cells
@@ -364,7 +365,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
-                "kernel": f"{'gs_stage_wide_kernel' if variant == 2 else 'gs_stage_kernel'} {STAGE_NAMES[dom]} (FP32)",
+                "kernel": f"{STAGE_NAMES[dom]} kernel, {['', 'generic', 'vec16B', 'vec8B'][stage_cfg[dom][0]]} form (FP32)",
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
                 "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
                 "attempt": {"algorithmic_bytes_per_cell": ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL,
@@ -379,6 +380,9 @@ def main():
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "accepted_per_step": ACC_PER_STEP,
                            "tolerance": TOL, "tile_ty_zc": [tile[0], tile[1]],
                            "stencil_kernel": "vectorised" if variant == 2 else "generic",
+                           "dopri5_kernel_configs": {nm: {"form": ["", "generic", "vec16B", "vec8B"][f], "ty": t,
+                                                          "zc": z} for nm, (f, t, z) in
+                                                     zip(STAGE_NAMES, gs.gs_get_stage_configs(g.ctx))},
                            "l2": "inputs larger than L2 (u, v + 8 stage fields = 1.3 GB per GPU); no flush",
                            "parallelism": f"replicas x{ws} (independent problems, no collective)"},
                 "accepted_steps": acc_all, "rejected_attempts_rank0": rej,

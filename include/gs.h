@@ -147,21 +147,32 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* co
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);
 gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
 
-/* Stencil kernel form: 0 = automatic (the vectorised kernel -- 16-byte
- * accesses, 4 FP32 or 2 FP64 cells per thread, 128- or 64-cell rows per
- * warp -- when nx is a multiple of 4 (FP32) or 2 (FP64) cells, else the
- * generic one-cell-per-thread kernel), 1 = generic, 2 = vectorised (INVALID
- * if nx is not such a multiple).  Both compute the same formulas. */
+/* Stencil kernel form: 0 = automatic (a vectorised kernel when nx is a
+ * multiple of its vector width, else the generic one; the autotuner may pick
+ * per kernel), 1 = generic (one cell per thread, 30-cell rows), 2 =
+ * vectorised (16-byte accesses: 4 FP32 or 2 FP64 cells per thread, 128- or
+ * 64-cell rows per warp; the autotuner may still pick 8-byte rows), 3 =
+ * vectorised 8-byte (FP32 only: 2 cells per thread, 64-cell rows).  INVALID
+ * if the form does not apply (nx not a multiple of the vector width).  All
+ * forms compute the same formulas. */
 gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant);
 /* The stencil kernel form the next call will use: 1 generic, 2 vectorised. */
 gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use);
 
-/* Times each candidate tile shape -- and, when the kernel variant is
- * automatic and both forms apply, each kernel form -- on one Dormand-Prince
- * step from the bound state (outputs go to the context's scratch only; the
- * bound state is not modified), selects the fastest, and returns its tile.
- * best_ms may be NULL. */
+/* Project autotuner: for each kernel of a Dormand-Prince attempt (k1 and
+ * stages 2..7) times every candidate kernel form allowed by the variant
+ * setting and every candidate tile (ty, zc), each launched alone from the
+ * bound state (outputs go to the context's scratch; the bound state is not
+ * modified), and keeps the fastest per kernel.  RK4, Euler, Adams-Bashforth
+ * and gs_rhs then use stage 2's configuration.  *ty, *zc: that
+ * configuration's tile; *best_ms: the sum of the best kernel times.  ty, zc
+ * and best_ms may be NULL. */
 gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
+
+/* Configuration in use for each Dormand-Prince kernel (index 0: k1, 1..6:
+ * stages 2..7): form (1 generic, 2 vectorised 16-byte rows, 3 vectorised
+ * 8-byte rows), ty, zc.  Each argument: host array of 7 ints. */
+gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc);
 
 /* Measurement aid: launches the kernels of one Dormand-Prince attempt of
  * the bound state one at a time between CUDA events on the context stream

@@ -57,6 +57,7 @@ _SIGNATURES = {
     "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gs_set_kernel_variant": ([_vp, C.c_int], C.c_int),
     "gs_get_kernel_variant": ([_vp, C.POINTER(C.c_int)], C.c_int),
+    "gs_get_stage_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gs_time_stages": ([_vp, C.c_int, _dp], C.c_int),
@@ -189,6 +190,13 @@ def gs_get_kernel_variant(ctx):
     v = C.c_int(0)
     _check(lib().gs_get_kernel_variant(ctx, C.byref(v)), ctx)
     return v.value
+
+
+def gs_get_stage_configs(ctx):
+    """[(form, ty, zc)] of the Dormand-Prince kernels k1, stage 2..7."""
+    f, t, z = (C.c_int * 7)(), (C.c_int * 7)(), (C.c_int * 7)()
+    _check(lib().gs_get_stage_configs(ctx, f, t, z), ctx)
+    return [(f[i], t[i], z[i]) for i in range(7)]
 
 
 def gs_get_tile(ctx):

@@ -33,6 +33,15 @@ enum GraphId { G_RK4 = 0, G_DOPRI5_FIXED, G_EULER, G_DOPRI5_ADAPT, G_AB4_START, 
 
 constexpr int kFields = 8;  // 0: second state buffer; 1..7: stage fields
 
+// Launch configuration of one stencil kernel.  form: 0 automatic, 1 generic
+// (one cell per thread), 2 vectorised 16-byte rows (4 FP32 / 2 FP64 cells per
+// thread), 3 vectorised 8-byte rows (2 FP32 cells per thread).
+struct KCfg {
+    int form;
+    int ty;
+    int zc;
+};
+
 }  // namespace
 
 struct gs_ctx {
@@ -50,9 +59,10 @@ struct gs_ctx {
     long long* hpatch = nullptr;  // pinned staging of single-field patches
     double* dlog = nullptr;
     long log_cap = 0;
-    int ty = 6, zc = 32;
-    int variant = 0;       // requested: 0 automatic, 1 generic, 2 vectorised
-    bool auto_wide = true;  // automatic choice (set by the autotuner)
+    KCfg def{0, 6, 32};     // kernels of RK4 / Euler / AB4 / F (form 0: automatic)
+    KCfg dp[7];             // Dormand-Prince k1 and stages 2..7 once tuned
+    bool dp_tuned = false;
+    int variant = 0;        // requested: 0 automatic, 1 generic, 2 vectorised, 3 vectorised 8-byte
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -91,25 +101,32 @@ static Geom<T> make_geom(const gs_params& p) {
     return g;
 }
 
-// vectorised kernel applicable: x-extent a multiple of the 16-byte vector width
-static bool wide_ok(const gs_ctx* ctx) {
-    const int vx = ctx->p.prec == GS_FP64 ? 2 : 4;
-    return ctx->p.nx % vx == 0;
+// vectorised form applicable: x-extent a multiple of the vector width
+static bool form_ok(const gs_ctx* ctx, int form) {
+    if (form == 1) return true;
+    if (form == 2) return ctx->p.nx % (ctx->p.prec == GS_FP64 ? 2 : 4) == 0;
+    if (form == 3) return ctx->p.prec == GS_FP32 && ctx->p.nx % 2 == 0;
+    return false;
 }
-static bool use_wide(const gs_ctx* ctx) {
-    return ctx->variant == 2 || (ctx->variant == 0 && ctx->auto_wide && wide_ok(ctx));
+static bool wide_ok(const gs_ctx* ctx) { return form_ok(ctx, 2) || form_ok(ctx, 3); }
+// the form a launch with configured form `form` actually uses
+static int pick_form(const gs_ctx* ctx, int form) {
+    if (ctx->variant == 1) return 1;
+    if (ctx->variant == 3) return 3;
+    if (form == 0) form = form_ok(ctx, 2) ? 2 : (form_ok(ctx, 3) ? 3 : 1);
+    if (ctx->variant == 2 && form == 1) form = form_ok(ctx, 2) ? 2 : 3;
+    if (!form_ok(ctx, form)) form = 1;
+    return form;
 }
 
-template <typename T, int NK, int MODE>
-static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
+template <typename T, int NK, int MODE, int VX>
+static cudaError_t launch_wide(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     const Geom<T> g = make_geom<T>(ctx->p);
-    const bool wide = use_wide(ctx);
-    auto kern = wide ? gs_stage_wide_kernel<T, NK, MODE> : gs_stage_kernel<T, NK, MODE>;
-    const int txw = wide ? 32 * wide_vx<T>() : kTileX;
-    if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
+    auto kern = gs_stage_wide_kernel<T, NK, MODE, VX>;
+    const int txw = 32 * VX;
     A.ntx = (ctx->p.nx + txw - 1) / txw;
     A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
-    const size_t smem = wide ? wide_smem_bytes<T>(A.ty) : stage_smem_bytes<T>(A.ty);
+    const size_t smem = wide_smem_bytes<T, VX>(A.ty);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -124,47 +141,79 @@ static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     return cudaGetLastError();
 }
 
+template <typename T, int NK, int MODE>
+static cudaError_t launch_generic(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
+    const Geom<T> g = make_geom<T>(ctx->p);
+    auto kern = gs_stage_kernel<T, NK, MODE>;
+    A.ntx = (ctx->p.nx + kTileX - 1) / kTileX;
+    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
+    const size_t smem = stage_smem_bytes<T>(A.ty);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const long long L = (long long)A.ntx * A.nty * ctx->p.nz;
+    const long long gmax = std::max<long long>(1, L / std::max(1, A.zc));
+    const int grid = (int)std::min<long long>(gmax, (long long)ctx->nsm * occ);
+    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A);
+    return cudaGetLastError();
+}
+
+template <typename T, int NK, int MODE>
+static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A, int form) {
+    if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
+    form = pick_form(ctx, form);
+    if (form == 1) return launch_generic<T, NK, MODE>(ctx, s, A);
+    if constexpr (sizeof(T) == 4) {
+        if (form == 2) return launch_wide<T, NK, MODE, 4>(ctx, s, A);
+        return launch_wide<T, NK, MODE, 2>(ctx, s, A);
+    } else {
+        return launch_wide<T, NK, MODE, 2>(ctx, s, A);
+    }
+}
+
 template <int NK, int MODE>
-static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A) {
-    if (ctx->p.prec == GS_FP64) return launch_stage_t<double, NK, MODE>(ctx, s, A);
-    return launch_stage_t<float, NK, MODE>(ctx, s, A);
+static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A, int form) {
+    if (ctx->p.prec == GS_FP64) return launch_stage_t<double, NK, MODE>(ctx, s, A, form);
+    return launch_stage_t<float, NK, MODE>(ctx, s, A, form);
 }
 
 // Instantiated (NK, mode) pairs: stages with 0..5 inputs, final combinations
 // with 0 (Euler, Adams-Bashforth) or 1 (RK4) halo inputs, Dormand-Prince
 // stage 7 with 5.
-static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A) {
+static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, int form) {
     if (mode == MODE_STAGE) {
         switch (nk) {
-            case 0: return launch_stage_nk<0, MODE_STAGE>(ctx, s, A);
-            case 1: return launch_stage_nk<1, MODE_STAGE>(ctx, s, A);
-            case 2: return launch_stage_nk<2, MODE_STAGE>(ctx, s, A);
-            case 3: return launch_stage_nk<3, MODE_STAGE>(ctx, s, A);
-            case 4: return launch_stage_nk<4, MODE_STAGE>(ctx, s, A);
-            case 5: return launch_stage_nk<5, MODE_STAGE>(ctx, s, A);
+            case 0: return launch_stage_nk<0, MODE_STAGE>(ctx, s, A, form);
+            case 1: return launch_stage_nk<1, MODE_STAGE>(ctx, s, A, form);
+            case 2: return launch_stage_nk<2, MODE_STAGE>(ctx, s, A, form);
+            case 3: return launch_stage_nk<3, MODE_STAGE>(ctx, s, A, form);
+            case 4: return launch_stage_nk<4, MODE_STAGE>(ctx, s, A, form);
+            case 5: return launch_stage_nk<5, MODE_STAGE>(ctx, s, A, form);
             default: return cudaErrorInvalidValue;
         }
     }
     if (mode == MODE_FINAL) {
-        if (nk == 0) return launch_stage_nk<0, MODE_FINAL>(ctx, s, A);
-        if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A);
+        if (nk == 0) return launch_stage_nk<0, MODE_FINAL>(ctx, s, A, form);
+        if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A, form);
         return cudaErrorInvalidValue;
     }
-    if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A);
+    if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, form);
     return cudaErrorInvalidValue;
 }
 
-static StageArgs base_args(gs_ctx* ctx) {
+static StageArgs base_args(gs_ctx* ctx, const KCfg& cfg) {
     StageArgs A;
     memset(&A, 0, sizeof(A));
-    A.ty = ctx->ty;
-    A.zc = ctx->zc;
-    A.ntx = (ctx->p.nx + kTileX - 1) / kTileX;
-    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
-    A.ntz = (ctx->p.nz + A.zc - 1) / A.zc;
+    A.ty = cfg.ty;
+    A.zc = cfg.zc;
     A.ctrl = ctx->dctrl;
     return A;
 }
+// configuration of Dormand-Prince kernel k (0: k1, 1..6: stages 2..7)
+static const KCfg& dp_cfg(const gs_ctx* ctx, int k) { return ctx->dp_tuned ? ctx->dp[k] : ctx->def; }
 
 // slot helpers over the context buffers
 static Slot fld(gs_ctx* c, int f) { return slot_fixed(c->field[f][0], c->field[f][1]); }
@@ -207,21 +256,21 @@ static Slot ring(gs_ctx* c, int off) {
 static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond,
                             bool k1_in_ring) {
     const Slot k1 = k1_in_ring ? ring(ctx, 0) : fld(ctx, 1);
-    StageArgs A = base_args(ctx);
+    StageArgs A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.out0 = k1;
-    cudaError_t e = launch_stage(ctx, s, 0, MODE_STAGE, A);
+    cudaError_t e = launch_stage(ctx, s, 0, MODE_STAGE, A, ctx->def.form);
     if (e != cudaSuccess) return e;
-    A = base_args(ctx);
+    A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.kin[0] = k1;
     A.a[0] = 0.5;
     A.out0 = fld(ctx, 5);
-    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A)) != cudaSuccess) return e;
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def.form)) != cudaSuccess) return e;
     A.kin[0] = fld(ctx, 5);
     A.out0 = fld(ctx, 6);
-    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A)) != cudaSuccess) return e;
-    A = base_args(ctx);
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def.form)) != cudaSuccess) return e;
+    A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.kin[0] = fld(ctx, 6);
     A.a[0] = 1.0;
@@ -236,24 +285,24 @@ static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 1, MODE_FINAL, A);
+    return launch_stage(ctx, s, 1, MODE_FINAL, A, ctx->def.form);
 }
 
 static cudaError_t body_euler(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
-    StageArgs A = base_args(ctx);
+    StageArgs A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.bf = 1.0;
     A.out0 = state_sel(ctx, SEL_NEXT);
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 0, MODE_FINAL, A);
+    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def.form);
 }
 
 // Adams-Bashforth 4 step m >= 3: f_m = F(u_m) into the ring,
 // u_{m+1} = u_m + dt (55 f_m - 59 f_{m-1} + 37 f_{m-2} - 9 f_{m-3}) / 24.
 static cudaError_t body_ab4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
-    StageArgs A = base_args(ctx);
+    StageArgs A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.bf = 55.0 / 24.0;
     A.ex[0] = ring(ctx, -1);
@@ -269,7 +318,7 @@ static cudaError_t body_ab4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 0, MODE_FINAL, A);
+    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def.form);
 }
 
 // Dormand-Prince stage st (2..7) with k1 in the parity pair (fields 1, 2)
@@ -286,7 +335,8 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     static const double A5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
     static const double A6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
     static const double* rows[5] = {A2, A3, A4, A5, A6};
-    StageArgs A = base_args(ctx);
+    const KCfg& cfg = dp_cfg(ctx, st - 1);
+    StageArgs A = base_args(ctx, cfg);
     A.u = state_sel(ctx, SEL_CUR);
     if (st < 7) {
         const int nk = st - 1;
@@ -295,7 +345,7 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
             A.a[j] = rows[st - 2][j];
         }
         A.out0 = k[st];
-        return launch_stage(ctx, s, nk, MODE_STAGE, A);
+        return launch_stage(ctx, s, nk, MODE_STAGE, A, cfg.form);
     }
     A.kin[0] = k[1];
     A.kin[1] = k[3];
@@ -313,7 +363,7 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A);
+    return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A, cfg.form);
 }
 
 static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -326,10 +376,11 @@ static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h
 
 // k1 = F(u) into the current k1 buffer (start of a Dormand-Prince run)
 static cudaError_t launch_dopri5_k1(gs_ctx* ctx, cudaStream_t s) {
-    StageArgs A = base_args(ctx);
+    const KCfg& cfg = dp_cfg(ctx, 0);
+    StageArgs A = base_args(ctx, cfg);
     A.u = state_sel(ctx, SEL_CUR);
     A.out0 = pair_sel(ctx, 1, 2, SEL_CUR);
-    return launch_stage(ctx, s, 0, MODE_STAGE, A);
+    return launch_stage(ctx, s, 0, MODE_STAGE, A, cfg.form);
 }
 
 static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -489,8 +540,7 @@ gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out) {
             break;
         }
         memset(ctx->hctrl, 0, sizeof(DevCtrl));
-        ctx->ty = 6;
-        ctx->zc = 32;
+        ctx->def = KCfg{0, 6, 32};
     } while (0);
     if (e != cudaSuccess) {
         if (st == GS_OK) st = GS_ERR_CUDA;
@@ -545,11 +595,11 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, 
     (void)t;  // the Gray-Scott system is autonomous
     if (!ctx || !u || !v || !fu || !fv) return GS_ERR_INVALID;
     if (((uintptr_t)u | (uintptr_t)v | (uintptr_t)fu | (uintptr_t)fv) & 15) return GS_ERR_INVALID;
-    StageArgs A = base_args(ctx);
+    StageArgs A = base_args(ctx, ctx->def);
     A.ctrl = nullptr;
     A.u = slot_fixed(const_cast<void*>(u), const_cast<void*>(v));
     A.out0 = slot_fixed(fu, fv);
-    CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A));
+    CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A, ctx->def.form));
     return GS_OK;
 }
 
@@ -666,108 +716,130 @@ gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc) {
     if (!ctx) return GS_ERR_INVALID;
     if (!(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 1 || zc > 1024)
         return GS_ERR_INVALID;
-    if (ctx->ty != ty || ctx->zc != zc) drop_graphs(ctx);
-    ctx->ty = ty;
-    ctx->zc = zc;
+    drop_graphs(ctx);
+    ctx->def.ty = ty;
+    ctx->def.zc = zc;
+    ctx->dp_tuned = false;  // an explicit tile applies to every kernel
     return GS_OK;
 }
 
 gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc) {
     if (!ctx || !ty || !zc) return GS_ERR_INVALID;
-    *ty = ctx->ty;
-    *zc = ctx->zc;
+    *ty = ctx->def.ty;
+    *zc = ctx->def.zc;
     return GS_OK;
 }
 
 gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant) {
-    if (!ctx || variant < 0 || variant > 2) return GS_ERR_INVALID;
+    if (!ctx || variant < 0 || variant > 3) return GS_ERR_INVALID;
     if (variant == 2 && !wide_ok(ctx)) return GS_ERR_INVALID;
-    if (ctx->variant != variant) drop_graphs(ctx);
+    if (variant == 3 && !form_ok(ctx, 3)) return GS_ERR_INVALID;
+    drop_graphs(ctx);
     ctx->variant = variant;
     return GS_OK;
 }
 
 gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use) {
     if (!ctx || !in_use) return GS_ERR_INVALID;
-    *in_use = use_wide(ctx) ? 2 : 1;
+    *in_use = pick_form(ctx, ctx->def.form) == 1 ? 1 : 2;
+    return GS_OK;
+}
+
+gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc) {
+    if (!ctx || !form || !ty || !zc) return GS_ERR_INVALID;
+    for (int k = 0; k < 7; ++k) {
+        const KCfg& c = dp_cfg(ctx, k);
+        form[k] = pick_form(ctx, c.form);
+        ty[k] = (k == 6 && c.ty > kMaxTYFinal) ? kMaxTYFinal : c.ty;
+        zc[k] = c.zc;
+    }
+    return GS_OK;
+}
+
+// time one Dormand-Prince kernel k (0: k1, 1..6: stages 2..7) with the
+// configuration currently in ctx->dp[k], from a fixed control block (parity 0)
+static gs_status time_dp_kernel(gs_ctx* ctx, int k, int reps, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+    float acc = 0.f;
+    for (int r = 0; r < reps + 1; ++r) {
+        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+        gs_status st = upload_ctrl(ctx);
+        if (st != GS_OK) return st;
+        CK(cudaEventRecord(e0, ctx->stream));
+        cudaError_t e = (k == 0) ? launch_dopri5_k1(ctx, ctx->stream)
+                                 : launch_dopri5_stage(ctx, ctx->stream, k + 1, 0, 0);
+        if (e != cudaSuccess) {
+            set_err(ctx, e, "autotune launch");
+            return GS_ERR_CUDA;
+        }
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) acc += ms;  // the first launch is a warm-up
+    }
+    *ms_out = acc / reps;
     return GS_OK;
 }
 
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
-    static const int cand[][2] = {{2, 32}, {4, 8}, {4, 32}, {6, 8}, {6, 32}, {8, 8},
-                                  {8, 32}, {14, 8}, {14, 32}};
-    const int old_ty = ctx->ty, old_zc = ctx->zc;
+    static const int cand[][2] = {{2, 32}, {4, 8}, {4, 32}, {6, 8}, {6, 32}, {8, 8}, {8, 32}, {14, 8}, {14, 32}};
+    int forms[3], nf = 0;
+    for (int f = 1; f <= 3; ++f) {
+        if (!form_ok(ctx, f)) continue;
+        if (ctx->variant == 1 && f != 1) continue;
+        if (ctx->variant == 2 && f == 1) continue;
+        if (ctx->variant == 3 && f != 3) continue;
+        forms[nf++] = f;
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bty = old_ty, bzc = old_zc;
-    gs_status st = GS_OK;
-    const bool try_both = ctx->variant == 0 && wide_ok(ctx);
-    const bool old_auto = ctx->auto_wide;
-    bool bwide = old_auto;
-    for (int vi = 0; vi < (try_both ? 2 : 1) && st == GS_OK; ++vi) {
-        if (try_both) {
-            ctx->auto_wide = (vi == 1);
-            drop_graphs(ctx);
-        }
-        for (const auto& c : cand) {
-            ctx->ty = c[0];
-            ctx->zc = c[1];
-            // fixed Dormand-Prince steps from the bound state: every output
-            // goes to the context's second buffers (parity is reset to 0
-            // before each repetition), so the caller's arrays are only read
-            init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
-            if ((st = upload_ctrl(ctx)) != GS_OK) break;
-            cudaError_t ek = launch_dopri5_k1(ctx, ctx->stream);
-            if (ek != cudaSuccess) {
-                set_err(ctx, ek, "autotune k1");
-                st = GS_ERR_CUDA;
-                break;
-            }
-            float ms_sum = 0.f;
-            const int reps = 3;
-            for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
-                CK(cudaEventRecord(e0, ctx->stream));
-                cudaError_t e = body_dopri5(ctx, ctx->stream, 0, 0);
-                if (e != cudaSuccess) {
-                    set_err(ctx, e, "autotune");
-                    st = GS_ERR_CUDA;
-                    break;
-                }
-                CK(cudaEventRecord(e1, ctx->stream));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (r > 0) ms_sum += ms;
-                ctx->hctrl->parity = 0;
-                ctx->hctrl->step = 0;
-                st = upload_ctrl(ctx);
-            }
-            if (st != GS_OK) break;
-            CK(cudaStreamSynchronize(ctx->stream));  // hctrl is rewritten for the next candidate
-            const float ms = ms_sum / reps;
-            if (ms < best) {
-                best = ms;
-                bty = c[0];
-                bzc = c[1];
-                bwide = ctx->auto_wide;
-            }
-        }
-    }
-    ctx->auto_wide = try_both ? bwide : old_auto;
     drop_graphs(ctx);
+    // realistic stage inputs: one full attempt with the current configuration
+    gs_status st = GS_OK;
+    for (int k = 0; k < 7 && st == GS_OK; ++k) {
+        float ms;
+        st = time_dp_kernel(ctx, k, 1, e0, e1, &ms);
+    }
+    KCfg best_cfg[7];
+    float total = 0.f;
+    for (int k = 0; k < 7 && st == GS_OK; ++k) {
+        float best = 1e30f;
+        best_cfg[k] = dp_cfg(ctx, k);
+        const KCfg saved = ctx->dp[k];
+        const bool saved_tuned = ctx->dp_tuned;
+        for (int i = 0; i < 7; ++i)
+            if (!ctx->dp_tuned) ctx->dp[i] = ctx->def;
+        ctx->dp_tuned = true;
+        for (int fi = 0; fi < nf && st == GS_OK; ++fi) {
+            for (const auto& c : cand) {
+                if (k == 6 && c[0] > kMaxTYFinal) continue;
+                ctx->dp[k] = KCfg{forms[fi], c[0], c[1]};
+                float ms = 0.f;
+                if ((st = time_dp_kernel(ctx, k, 3, e0, e1, &ms)) != GS_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    best_cfg[k] = ctx->dp[k];
+                }
+            }
+        }
+        ctx->dp[k] = saved;
+        ctx->dp_tuned = saved_tuned;
+        total += best;
+    }
     cudaStreamSynchronize(ctx->stream);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->ty = old_ty;
-    ctx->zc = old_zc;
     if (st != GS_OK) return st;
-    gs_set_tile(ctx, bty, bzc);
-    if (ty_out) *ty_out = bty;
-    if (zc_out) *zc_out = bzc;
-    if (best_ms) *best_ms = best;
+    for (int k = 0; k < 7; ++k) ctx->dp[k] = best_cfg[k];
+    ctx->dp_tuned = true;
+    // the other integrators use the configuration of the one-input stage
+    ctx->def = best_cfg[1];
+    drop_graphs(ctx);
+    if (ty_out) *ty_out = ctx->def.ty;
+    if (zc_out) *zc_out = ctx->def.zc;
+    if (best_ms) *best_ms = total;  // sum of the best kernel times (k1 included)
     return GS_OK;
 }
 

@@ -1,9 +1,9 @@
 // gs_wide.cuh -- vectorised form of the fused Gray-Scott stage kernel for
-// grids whose x-extent is a multiple of the 16-byte vector width (4 FP32 or
-// 2 FP64 cells).  Same arithmetic contract as gs_stage_kernel (gs_tile.cuh):
+// grids whose x-extent is a multiple of the vector width VX (FP32: 4 cells =
+// 16 bytes or 2 cells = 8 bytes; FP64: 2 cells = 16 bytes).  Same arithmetic contract as gs_stage_kernel (gs_tile.cuh):
 //   Y = u + dt sum_j a_j k_j,  f = F(Y),  mode-specific epilogue.
 //
-// Mapping: a warp owns one row of 32*VX cells (VX cells per lane, one 16-byte
+// Mapping: a warp owns one row of 32*VX cells (VX cells per lane, one vector
 // load per field and component), a CTA owns ty such rows plus one halo row
 // above and below (warps 0 and ty+1) and marches over zc planes.  The z
 // neighbours of a thread's cells stay in registers (planes z-1, z, z+1); only
@@ -19,59 +19,49 @@
 
 namespace gsk {
 
-template <typename T>
+// Vector of VX elements of T moved as one access (8 or 16 bytes).
+template <typename T, int VX>
 struct VecT;
 template <>
-struct VecT<float> {
+struct VecT<float, 4> {
     using type = float4;
-    static constexpr int n = 4;
 };
 template <>
-struct VecT<double> {
+struct VecT<float, 2> {
+    using type = float2;
+};
+template <>
+struct VecT<double, 2> {
     using type = double2;
-    static constexpr int n = 2;
 };
 
-template <typename T>
-__device__ __forceinline__ void ldv(const T* __restrict__ p, T* out);
-template <>
-__device__ __forceinline__ void ldv<float>(const float* __restrict__ p, float* out) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
-    out[0] = q.x;
-    out[1] = q.y;
-    out[2] = q.z;
-    out[3] = q.w;
-}
-template <>
-__device__ __forceinline__ void ldv<double>(const double* __restrict__ p, double* out) {
-    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
-    out[0] = q.x;
-    out[1] = q.y;
+template <typename T, int VX>
+__device__ __forceinline__ void ldv(const T* __restrict__ p, T* out) {
+    using VTy = typename VecT<T, VX>::type;
+    const VTy q = __ldg(reinterpret_cast<const VTy*>(p));
+    const T* qs = reinterpret_cast<const T*>(&q);
+#pragma unroll
+    for (int v = 0; v < VX; ++v) out[v] = qs[v];
 }
 
-template <typename T>
-__device__ __forceinline__ void stv(T* p, const T* v);
-template <>
-__device__ __forceinline__ void stv<float>(float* p, const float* v) {
-    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-template <>
-__device__ __forceinline__ void stv<double>(double* p, const double* v) {
-    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+template <typename T, int VX>
+__device__ __forceinline__ void stv(T* p, const T* v) {
+    using VTy = typename VecT<T, VX>::type;
+    VTy q;
+    T* qs = reinterpret_cast<T*>(&q);
+#pragma unroll
+    for (int i = 0; i < VX; ++i) qs[i] = v[i];
+    *reinterpret_cast<VTy*>(p) = q;
 }
 
-// 16-byte shared-memory accesses (addresses are 16-byte aligned by the pitch)
-template <typename T>
-__device__ __forceinline__ void sts_v(T* p, const T* v) {
-    stv<T>(p, v);
-}
-template <typename T>
+// vector shared-memory load (addresses are aligned to the vector by the pitch)
+template <typename T, int VX>
 __device__ __forceinline__ void lds_v(const T* p, T* out) {
-    using VTy = typename VecT<T>::type;
+    using VTy = typename VecT<T, VX>::type;
     const VTy q = *reinterpret_cast<const VTy*>(p);
     const T* qs = reinterpret_cast<const T*>(&q);
 #pragma unroll
-    for (int v = 0; v < VecT<T>::n; ++v) out[v] = qs[v];
+    for (int v = 0; v < VX; ++v) out[v] = qs[v];
 }
 
 template <typename T>
@@ -83,17 +73,14 @@ __device__ __forceinline__ float fast_ratio<float>(float a, float b) {
     return __fdividef(a, b);  // error ratio: a few ulp are irrelevant to the controller
 }
 
-template <typename T>
-__host__ __device__ constexpr int wide_vx() {
-    return 16 / (int)sizeof(T);
-}
-template <typename T>
+// row of 32*VX cells + 2 halo columns, padded to a whole vector
+template <int VX>
 __host__ __device__ constexpr int wide_pitch() {
-    return 32 * wide_vx<T>() + wide_vx<T>();  // row of cells + 2 halo columns, 16-byte aligned
+    return 32 * VX + VX;
 }
-template <typename T>
+template <typename T, int VX>
 __host__ __device__ inline size_t wide_smem_bytes(int ty) {
-    return sizeof(T) * 3 * (size_t)(ty + 2) * 2 * wide_pitch<T>();
+    return sizeof(T) * 3 * (size_t)(ty + 2) * 2 * wide_pitch<VX>();
 }
 
 // Per-cell values a final epilogue needs from the plane's inputs.
@@ -104,11 +91,10 @@ struct Carry {
     T b[MODE == MODE_FINAL ? (NK > 0 ? NK : 1) : 1][2][VX];
 };
 
-template <typename T, int NK, int MODE>
+template <typename T, int NK, int MODE, int VX>
 __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_kernel(const Geom<T> g, const StageArgs A) {
-    constexpr int VX = wide_vx<T>();
     constexpr int TXW = 32 * VX;
-    constexpr int PITCH = wide_pitch<T>();
+    constexpr int PITCH = wide_pitch<VX>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
     __shared__ T red[32];
@@ -171,7 +157,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             T uu[VX];
-            ldv<T>(uin[c] + idx, uu);
+            ldv<T, VX>(uin[c] + idx, uu);
             T s[VX], k1[VX], q[VX];
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
@@ -182,7 +168,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
                 T kk[VX];
-                ldv<T>(kin[j][c] + idx, kk);
+                ldv<T, VX>(kin[j][c] + idx, kk);
 #pragma unroll
                 for (int v = 0; v < VX; ++v) {
                     s[v] = (j == 0) ? aT[0] * kk[v] : s[v] + aT[j] * kk[v];
@@ -255,7 +241,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                 if (act) {
                     loadY(cbase + plane * z0, yc, cur);
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(b0, w, c, VX * lane), yc[c]);
+                    for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(b0, w, c, VX * lane), yc[c]);
                 }
                 if (do_halo)
                     for (int c = 0; c < 2; ++c) S[sidx(b0, hrow, c, hcol)] = loadY1(hbase + plane * z0, c);
@@ -267,7 +253,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                 if (act) {
                     loadY(cbase + zoff, yp, nxt);
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) sts_v<T>(S + sidx(bn, w, c, VX * lane), yp[c]);
+                    for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
                 }
                 if (do_halo)
                     for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
@@ -285,8 +271,8 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                         if (lane == 0) xl[c] = S[sidx(bz, w, c, TXW)];
                         if (lane == nl - 1) xr[c] = S[sidx(bz, w, c, TXW + 1)];
                         T ys[VX], yn[VX];
-                        lds_v<T>(S + sidx(bz, w - 1, c, VX * lane), ys);
-                        lds_v<T>(S + sidx(bz, w + 1, c, VX * lane), yn);
+                        lds_v<T, VX>(S + sidx(bz, w - 1, c, VX * lane), ys);
+                        lds_v<T, VX>(S + sidx(bz, w + 1, c, VX * lane), yn);
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
                             const T xm = (v == 0) ? xl[c] : yc[c][v - 1];
@@ -305,8 +291,8 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                     }
                     const long long i = cbase + plane * z;
                     if (MODE == MODE_STAGE) {
-                        stv<T>(o0[0] + i, f[0]);
-                        stv<T>(o0[1] + i, f[1]);
+                        stv<T, VX>(o0[0] + i, f[0]);
+                        stv<T, VX>(o0[1] + i, f[1]);
                     } else if (MODE == MODE_FINAL) {
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
@@ -321,7 +307,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                             for (int j = 0; j < kMaxNE; ++j) {
                                 if (j < A.n_ex) {
                                     T e[VX];
-                                    ldv<T>(exs[j][c] + i, e);
+                                    ldv<T, VX>(exs[j][c] + i, e);
 #pragma unroll
                                     for (int v = 0; v < VX; ++v) s[v] += (T)A.be[j] * e[v];
                                 }
@@ -329,14 +315,14 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                             T o[VX];
 #pragma unroll
                             for (int v = 0; v < VX; ++v) o[v] = cur.a[c][v] + dt * s[v];
-                            stv<T>(o0[c] + i, o);
-                            if (A.has_out1) stv<T>(o1[c] + i, f[c]);
+                            stv<T, VX>(o0[c] + i, o);
+                            if (A.has_out1) stv<T, VX>(o1[c] + i, f[c]);
                         }
                     } else {  // MODE_DOPRI_FINAL
 #pragma unroll
                         for (int c = 0; c < 2; ++c) {
-                            stv<T>(o0[c] + i, yc[c]);
-                            stv<T>(o1[c] + i, f[c]);
+                            stv<T, VX>(o0[c] + i, yc[c]);
+                            stv<T, VX>(o1[c] + i, f[c]);
                             if (NK == 5) {
 #pragma unroll
                                 for (int v = 0; v < VX; ++v) {

@@ -131,10 +131,11 @@ def test_tile_shape_does_not_change_results(dims, L, tile):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2)])
+@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (70, 5, 6)])
 def test_kernel_variants_match_oracle(prec, dims):
-    """The generic (one cell per thread) and vectorised (16-byte rows) stencil
-    kernels on the same grid: both against the oracle, Dopri5 and RK4 steps."""
+    """The generic (one cell per thread) and vectorised (16-byte rows; FP32
+    also 8-byte rows) stencil kernels on the same grid, each against the
+    oracle, Dopri5 and RK4 steps."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     # x spacing at least 2.5/45 keeps dt * lambda_max well inside the
@@ -147,7 +148,10 @@ def test_kernel_variants_match_oracle(prec, dims):
     tol = FP64_TOL if prec == 0 else FP32_TOL
     for method, om in ((gs.GS_DOPRI5, oracle.DOPRI5), (gs.GS_RK4, oracle.RK4)):
         ou, ov = oracle.gs_integrate_const(p, u0, v0, om, 0.25, 3)
-        for variant in (1, 2):
+        for variant in ((1, 2) if prec == 0 else (1, 2, 3)):
+            vx = {1: 1, 2: 2 if prec == 0 else 4, 3: 2}[variant]
+            if dims[0] % vx:
+                continue
             g = _gs(torch, dims, prec, u0, v0, **phys)
             gs.gs_set_kernel_variant(g.ctx, variant)
             g.step(method, 0.0, 0.25, 3)
@@ -159,10 +163,21 @@ def test_kernel_variants_match_oracle(prec, dims):
 def test_vectorised_variant_rejects_unaligned_rows():
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
+    # nx = 10 (FP32): 10 = 5 x 2 cells, so the 8-byte rows apply and variant 2
+    # falls back to them; nx = 9 admits no vectorised form
     g = _gs(torch, (10, 4, 4), gs.GS_FP32, *si.gs_initial_state(10, 4, 4))
-    with pytest.raises(gs.GSError):
-        gs.gs_set_kernel_variant(g.ctx, 2)
+    gs.gs_set_kernel_variant(g.ctx, 2)
+    gs.gs_set_kernel_variant(g.ctx, 3)
     gs.gs_set_kernel_variant(g.ctx, 1)
+    g.close()
+    g = _gs(torch, (9, 4, 4), gs.GS_FP32, *si.gs_initial_state(9, 4, 4))
+    for variant in (2, 3):
+        with pytest.raises(gs.GSError):
+            gs.gs_set_kernel_variant(g.ctx, variant)
+    g.close()
+    g = _gs(torch, (10, 4, 4), gs.GS_FP64, *si.gs_initial_state(10, 4, 4))
+    with pytest.raises(gs.GSError):
+        gs.gs_set_kernel_variant(g.ctx, 3)  # 8-byte rows exist for FP32 only
     g.close()
 
 
