@@ -189,6 +189,61 @@ const char* gs_last_error(const gs_ctx* ctx);
 const char* gs_last_global_error(void);
 
 /* ------------------------------------------------------------------------ */
+/* Batched ensembles: many independent Gray-Scott problems of uneven sizes    */
+/* and parameters, each with its own adaptive step (the error-controlled    */
+/* integrate_adaptive of section "Architecture and nomenclature of Boost    */
+/* Odeint", applied per instance)                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nx, ny, nz; /* grid of this instance, each 1..65535 */
+    double F, k;    /* feed and kill rates of this instance */
+} gsb_instance;
+
+typedef struct gsb_ctx gsb_ctx; /* opaque; owns the stage scratch of all instances */
+
+/* Creates an ensemble of `count` (1..65536) instances, each on the periodic
+ * box [0,L)^3 with spacing L/n_d per axis, shared diffusivities Du, Dv and
+ * precision prec.  The instances' states are concatenated in two arrays
+ * (u, v) at the element offsets reported by gsb_layout (each 16-byte
+ * aligned, cell (x,y,z) of instance i at offset_i + x + nx_i (y + ny_i z)).
+ * Errors: INVALID, NOMEM, CUDA. */
+gs_status gsb_create(int count, const gsb_instance* inst, double L, double Du, double Dv, int prec,
+                     void* stream, gsb_ctx** out);
+gs_status gsb_destroy(gsb_ctx* ctx);
+
+/* offsets[i] = element offset of instance i, offsets[count] = total length
+ * of each state array.  offsets: host array of count + 1. */
+gs_status gsb_layout(const gsb_ctx* ctx, long long* offsets);
+
+/* Binds the caller-owned concatenated state arrays (total length each, of
+ * the ensemble precision, 16-byte aligned); updated in place. */
+gs_status gsb_bind_state(gsb_ctx* ctx, void* u_dev, void* v_dev);
+
+/* Error-controlled Dormand-Prince 5(4) for every instance from t[i] towards
+ * t_end with its own step size: same norm, controller and clipping as
+ * gs_integrate_adaptive, decided per instance.  Each Dormand-Prince stage of
+ * all instances is one persistent kernel launch (CTAs take segments of any
+ * running instance from an atomic counter); the stage loop is one CUDA graph
+ * (WHILE any instance is running).  t, dt: host arrays of count, in/out.
+ * n_acc, n_rej, status: optional host arrays of count.  Returns GS_OK if
+ * every instance ended OK, else the first failing instance's status (the
+ * others are integrated regardless).  Synchronises the stream. */
+gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double* t, double t_end,
+                                 double* dt, long max_accepted, long* n_acc, long* n_rej,
+                                 int* status);
+
+/* Segment shape: ty rows (2,4,6,8,14; stage 7 uses at most 6) of 32 cells,
+ * zc planes (1..1024). */
+gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc);
+
+/* Project autotuner for the batched kernels: times one Dormand-Prince attempt
+ * of the bound ensemble for each candidate segment shape and keeps the
+ * fastest (the bound state is not modified). */
+gs_status gsb_autotune(gsb_ctx* ctx, int* ty, int* zc, double* best_ms);
+
+const char* gsb_last_error(const gsb_ctx* ctx);
+
+/* ------------------------------------------------------------------------ */
 /* Stage algebra (section "The distributed OpenFPM state type and algebra":  */
 /* for_each operations over up to 15 states)                                 */
 /* ------------------------------------------------------------------------ */

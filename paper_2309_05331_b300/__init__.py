@@ -40,6 +40,10 @@ class gs_params(C.Structure):
                 ("prec", C.c_int)]
 
 
+class gsb_instance(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("F", C.c_double), ("k", C.c_double)]
+
+
 _lib = None
 _vp, _dp, _lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)
 
@@ -72,6 +76,16 @@ _SIGNATURES = {
     "ode_integrate_ab4": ([C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
     "ode_integrate_const": ([C.c_int, C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
     "gs_measure_fp64_peak": ([_dp, _vp], C.c_int),
+    "gsb_create": ([C.c_int, C.POINTER(gsb_instance), C.c_double, C.c_double, C.c_double, C.c_int, _vp,
+                    C.POINTER(_vp)], C.c_int),
+    "gsb_destroy": ([_vp], C.c_int),
+    "gsb_layout": ([_vp, C.POINTER(C.c_longlong)], C.c_int),
+    "gsb_bind_state": ([_vp, _vp, _vp], C.c_int),
+    "gsb_integrate_adaptive": ([_vp, C.c_double, C.c_double, _dp, C.c_double, _dp, C.c_long, _lp, _lp,
+                                C.POINTER(C.c_int)], C.c_int),
+    "gsb_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
+    "gsb_last_error": ([_vp], C.c_char_p),
 }
 
 
@@ -314,6 +328,83 @@ class GrayScott:
     def close(self):
         if self.ctx:
             gs_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# Batched ensembles of uneven Gray-Scott problems
+# --------------------------------------------------------------------------
+def _bcheck(st, ctx):
+    if st != GS_OK:
+        msg = lib().gsb_last_error(ctx) or b""
+        raise GSError(st, msg.decode())
+
+
+class GrayScottBatch:
+    """Ensemble of independent Gray-Scott problems (gsb_* C ABI).
+
+    instances: list of dicts {nx, ny, nz, F, k}.  u, v: concatenated state
+    tensors of the ensemble precision; ``view(i)`` gives instance i's
+    (nz, ny, nx) views."""
+
+    def __init__(self, instances, L=2.5, Du=2e-5, Dv=1e-5, prec=GS_FP32, stream=None, device="cuda"):
+        import torch
+        n = len(instances)
+        arr = (gsb_instance * n)(*[gsb_instance(d["nx"], d["ny"], d["nz"], d["F"], d["k"]) for d in instances])
+        self.ctx = _vp()
+        _check(lib().gsb_create(n, arr, L, Du, Dv, prec, _stream(stream), C.byref(self.ctx)))
+        self.instances = [dict(d) for d in instances]
+        offs = (C.c_longlong * (n + 1))()
+        _bcheck(lib().gsb_layout(self.ctx, offs), self.ctx)
+        self.offsets = [int(o) for o in offs]
+        self.dtype = torch.float64 if prec == GS_FP64 else torch.float32
+        self.u = torch.zeros(self.offsets[-1], dtype=self.dtype, device=device)
+        self.v = torch.zeros(self.offsets[-1], dtype=self.dtype, device=device)
+        _bcheck(lib().gsb_bind_state(self.ctx, _ptr(self.u), _ptr(self.v)), self.ctx)
+
+    def view(self, i):
+        d = self.instances[i]
+        o, n = self.offsets[i], d["nx"] * d["ny"] * d["nz"]
+        shape = (d["nz"], d["ny"], d["nx"])
+        return self.u[o:o + n].view(shape), self.v[o:o + n].view(shape)
+
+    def set_instance(self, i, u, v):
+        uu, vv = self.view(i)
+        uu.copy_(u.to(uu.device, self.dtype).reshape(uu.shape))
+        vv.copy_(v.to(vv.device, self.dtype).reshape(vv.shape))
+
+    def integrate_adaptive(self, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
+        import numpy as np
+        n = len(self.instances)
+        tt = np.ascontiguousarray(np.broadcast_to(np.asarray(t, dtype=np.float64), (n,)).copy())
+        dd = np.ascontiguousarray(np.broadcast_to(np.asarray(dt, dtype=np.float64), (n,)).copy())
+        na = np.zeros(n, dtype=np.int64)
+        nr = np.zeros(n, dtype=np.int64)
+        stv = np.zeros(n, dtype=np.int32)
+        st = lib().gsb_integrate_adaptive(self.ctx, atol, rtol, tt.ctypes.data_as(_dp), t_end, dd.ctypes.data_as(_dp),
+                                          max_accepted, na.ctypes.data_as(_lp), nr.ctypes.data_as(_lp),
+                                          stv.ctypes.data_as(C.POINTER(C.c_int)))
+        if check:
+            _bcheck(st, self.ctx)
+        return {"status": st, "t": tt, "dt": dd, "n_acc": na, "n_rej": nr, "statuses": stv}
+
+    def set_tile(self, ty, zc):
+        _bcheck(lib().gsb_set_tile(self.ctx, ty, zc), self.ctx)
+
+    def autotune(self):
+        a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        _bcheck(lib().gsb_autotune(self.ctx, C.byref(a), C.byref(b), C.byref(ms)), self.ctx)
+        return a.value, b.value, ms.value
+
+    def close(self):
+        if self.ctx:
+            lib().gsb_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

@@ -1,0 +1,572 @@
+// gs_batch.cu -- error-controlled Dormand-Prince 5(4) for ensembles of
+// independent Gray-Scott problems of uneven grid sizes and parameters.
+//
+// All instances live in one set of concatenated fields (instance i at element
+// offset off_i).  Every instance has its own control block: time, step size,
+// accept/reject, parity of its buffers, status.  Each Dormand-Prince stage is
+// ONE persistent launch over all instances: CTAs take segments (instance,
+// column of ty rows x 32 cells, run of zc planes) from an atomic counter, skip
+// instances that have finished, and run the same segment code as the
+// single-grid vectorised kernel (one cell per lane, so any nx works).  Stage 7
+// folds each segment's error maximum into its instance's accumulator; a
+// controller kernel (one thread per instance) then accepts or rejects every
+// instance, picks its next step and sets the loop condition of the CUDA graph
+// (WHILE any instance is still running).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "common.cuh"
+#include "gs_tile.cuh"
+#include "gs_wide.cuh"
+#include "host_util.h"
+
+using namespace gsk;
+
+namespace {
+
+struct BInst {
+    int nx, ny, nz;
+    int pad;
+    long long off;  // element offset in the concatenated fields
+    double cx, cy, cz, Du, Dv, F, k;
+};
+
+struct BSeg {
+    int inst, col, z0, z1;
+};
+
+constexpr int kBFields = 8;   // 0: second state buffer; 1..7: stage fields
+constexpr int kCounters = 8;  // segment counters: k1, stages 2..7
+
+template <typename T, int NK, int MODE>
+__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
+    gsb_stage_kernel(const BInst* __restrict__ insts, DevCtrl* ctrls, const BSeg* __restrict__ segs, int nseg,
+                     unsigned int* counter, const StageArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T red[32];
+    __shared__ int s_seg;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    for (;;) {
+        if (tid == 0) s_seg = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int sgi = s_seg;
+        __syncthreads();  // every thread has read s_seg before it is replaced
+        if (sgi >= nseg) break;
+        const BSeg sg = segs[sgi];
+        const DevCtrl* c = ctrls + sg.inst;
+        if (c->done) continue;  // block-uniform: control blocks are read-only here
+        const BInst in = insts[sg.inst];
+        Geom<T> g;
+        g.nx = in.nx;
+        g.ny = in.ny;
+        g.nz = in.nz;
+        g.cx = (T)in.cx;
+        g.cy = (T)in.cy;
+        g.cz = (T)in.cz;
+        g.Du = (T)in.Du;
+        g.Dv = (T)in.Dv;
+        g.F = (T)in.F;
+        g.k = (T)in.k;
+        const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, c->parity, 0, in.off);
+        const StageCoef<T, NK> C = stage_coef<T, NK>(A, c->dt_try, c->atol, c->rtol);
+        const int ntx = (in.nx + 31) / 32;
+        T emax = T(0);
+        wide_segment<T, NK, MODE, 1>(g, P, C, S, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1, emax);
+        if (MODE == MODE_DOPRI_FINAL) {
+            const T bmax = block_nanmax(emax, red);
+            if (tid == 0) atomic_max_nonneg(&ctrls[sg.inst].err_bits, (double)bmax);
+        }
+    }
+}
+
+// One thread per instance: accept / reject, next step, stop.  Resets the
+// stage segment counters for the next attempt and sets the loop condition.
+__global__ void __launch_bounds__(1024) gsb_controller_kernel(DevCtrl* ctrls, int n, unsigned int* counters,
+                                                              unsigned long long cond, int use_cond) {
+    int active = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        DevCtrl* c = ctrls + i;
+        if (!c->done) {
+            const double E = __longlong_as_double((long long)c->err_bits);
+            c->err_bits = 0ull;
+            controller_update(c, E);
+        }
+        active |= c->done ? 0 : 1;
+    }
+    active = __syncthreads_or(active);
+    if (threadIdx.x >= 1 && threadIdx.x < kCounters) counters[threadIdx.x] = 0u;
+    if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, active ? 1u : 0u);
+}
+
+template <typename T>
+__global__ void gsb_copy_back_kernel(const BInst* __restrict__ insts, const DevCtrl* ctrls, int n,
+                                     const T* __restrict__ a0, const T* __restrict__ a1, T* __restrict__ b0,
+                                     T* __restrict__ b1) {
+    for (int i = blockIdx.x; i < n; i += gridDim.x) {
+        if (ctrls[i].parity == 0) continue;
+        const BInst in = insts[i];
+        const long long N = (long long)in.nx * in.ny * in.nz;
+        for (long long e = threadIdx.x; e < N; e += blockDim.x) {
+            b0[in.off + e] = a0[in.off + e];
+            b1[in.off + e] = a1[in.off + e];
+        }
+    }
+}
+
+}  // namespace
+
+struct gsb_ctx {
+    int count = 0;
+    int prec = GS_FP32;
+    size_t esz = 4;
+    long long total = 0;
+    std::vector<BInst> hinst;
+    cudaStream_t stream = nullptr, cap = nullptr;
+    int dev = 0, nsm = 0;
+    void* state[2] = {nullptr, nullptr};
+    unsigned char* scratch = nullptr;
+    void* field[kBFields][2] = {};
+    BInst* dinst = nullptr;
+    DevCtrl* dctrl = nullptr;
+    DevCtrl* hctrl = nullptr;  // pinned, count entries
+    unsigned int* counters = nullptr;
+    BSeg* dseg[2] = {nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles
+    int nseg[2] = {0, 0};
+    int ty = 6, zc = 16;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    char err[512] = {0};
+};
+
+static void bset_err(gsb_ctx* c, cudaError_t e, const char* where) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define BCK(call)                     \
+    do {                              \
+        cudaError_t e_ = (call);      \
+        if (e_ != cudaSuccess) {      \
+            bset_err(ctx, e_, #call); \
+            return GS_ERR_CUDA;       \
+        }                             \
+    } while (0)
+
+static void bdrop_graph(gsb_ctx* ctx) {
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->exec = nullptr;
+    ctx->graph = nullptr;
+}
+
+// segment lists for rows-per-CTA ty (stages) and min(ty, 6) (stage 7)
+static gs_status build_segments(gsb_ctx* ctx) {
+    for (int li = 0; li < 2; ++li) {
+        const int ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
+        std::vector<BSeg> v;
+        for (int i = 0; i < ctx->count; ++i) {
+            const BInst& in = ctx->hinst[i];
+            const int ncol = ((in.nx + 31) / 32) * ((in.ny + ty - 1) / ty);
+            for (int col = 0; col < ncol; ++col)
+                for (int z0 = 0; z0 < in.nz; z0 += ctx->zc) v.push_back(BSeg{i, col, z0, std::min(in.nz, z0 + ctx->zc)});
+        }
+        if (ctx->dseg[li]) cudaFree(ctx->dseg[li]);
+        ctx->dseg[li] = nullptr;
+        BCK(cudaMalloc(&ctx->dseg[li], sizeof(BSeg) * v.size()));
+        BCK(cudaMemcpy(ctx->dseg[li], v.data(), sizeof(BSeg) * v.size(), cudaMemcpyHostToDevice));
+        ctx->nseg[li] = (int)v.size();
+    }
+    return GS_OK;
+}
+
+template <typename T, int NK, int MODE>
+static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int slot) {
+    const int li = MODE == MODE_STAGE ? 0 : 1;
+    A.ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
+    auto kern = gsb_stage_kernel<T, NK, MODE>;
+    const size_t smem = wide_smem_bytes<T, 1>(A.ty);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int grid = std::max(1, std::min(ctx->nseg[li], ctx->nsm * occ));
+    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[li], ctx->nseg[li],
+                                                ctx->counters + slot, A);
+    return cudaGetLastError();
+}
+
+template <int NK, int MODE>
+static cudaError_t blaunch_nk(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int slot) {
+    if (ctx->prec == GS_FP64) return blaunch_t<double, NK, MODE>(ctx, s, A, slot);
+    return blaunch_t<float, NK, MODE>(ctx, s, A, slot);
+}
+
+static cudaError_t blaunch(gsb_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, int slot) {
+    if (mode == MODE_STAGE) {
+        switch (nk) {
+            case 0: return blaunch_nk<0, MODE_STAGE>(ctx, s, A, slot);
+            case 1: return blaunch_nk<1, MODE_STAGE>(ctx, s, A, slot);
+            case 2: return blaunch_nk<2, MODE_STAGE>(ctx, s, A, slot);
+            case 3: return blaunch_nk<3, MODE_STAGE>(ctx, s, A, slot);
+            case 4: return blaunch_nk<4, MODE_STAGE>(ctx, s, A, slot);
+            case 5: return blaunch_nk<5, MODE_STAGE>(ctx, s, A, slot);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (mode == MODE_DOPRI_FINAL && nk == 5) return blaunch_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, slot);
+    return cudaErrorInvalidValue;
+}
+
+static Slot bfld(gsb_ctx* c, int f) { return slot_fixed(c->field[f][0], c->field[f][1]); }
+static Slot bstate(gsb_ctx* c, int sel) {
+    Slot s{};
+    s.p[0][0] = c->state[0];
+    s.p[0][1] = c->state[1];
+    s.p[1][0] = c->field[0][0];
+    s.p[1][1] = c->field[0][1];
+    s.sel = sel;
+    return s;
+}
+static Slot bpair(gsb_ctx* c, int fa, int fb, int sel) {
+    Slot s{};
+    s.p[0][0] = c->field[fa][0];
+    s.p[0][1] = c->field[fa][1];
+    s.p[1][0] = c->field[fb][0];
+    s.p[1][1] = c->field[fb][1];
+    s.sel = sel;
+    return s;
+}
+
+// stage st (1 = k1, 2..7): same buffers and coefficients as the single grid
+static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st) {
+    const Slot k1 = bpair(ctx, 1, 2, SEL_CUR);
+    const Slot k[7] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4), bfld(ctx, 5), bfld(ctx, 6), bfld(ctx, 7)};
+    static const double A2[1] = {dp5::A21};
+    static const double A3[2] = {dp5::A31, dp5::A32};
+    static const double A4[3] = {dp5::A41, dp5::A42, dp5::A43};
+    static const double A5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
+    static const double A6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
+    static const double* rows[5] = {A2, A3, A4, A5, A6};
+    StageArgs A;
+    memset(&A, 0, sizeof(A));
+    A.u = bstate(ctx, SEL_CUR);
+    if (st == 1) {
+        A.out0 = k1;
+        return blaunch(ctx, s, 0, MODE_STAGE, A, 0);
+    }
+    if (st < 7) {
+        const int nk = st - 1;
+        for (int j = 0; j < nk; ++j) {
+            A.kin[j] = k[j + 1];
+            A.a[j] = rows[st - 2][j];
+        }
+        A.out0 = k[st];
+        return blaunch(ctx, s, nk, MODE_STAGE, A, st - 1);
+    }
+    A.kin[0] = k[1];
+    A.kin[1] = k[3];
+    A.kin[2] = k[4];
+    A.kin[3] = k[5];
+    A.kin[4] = k[6];
+    A.a[0] = dp5::B1;
+    A.a[1] = dp5::B3;
+    A.a[2] = dp5::B4;
+    A.a[3] = dp5::B5;
+    A.a[4] = dp5::B6;
+    A.out0 = bstate(ctx, SEL_NEXT);
+    A.out1 = bpair(ctx, 1, 2, SEL_NEXT);
+    A.has_out1 = 1;
+    return blaunch(ctx, s, 5, MODE_DOPRI_FINAL, A, 6);
+}
+
+static cudaError_t bbody(gsb_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond, bool with_ctrl) {
+    for (int st = 2; st <= 7; ++st) {
+        cudaError_t e = blaunch_dopri5_stage(ctx, s, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!with_ctrl) return cudaSuccess;
+    const int threads = std::min(1024, std::max(32, (ctx->count + 31) / 32 * 32));
+    gsb_controller_kernel<<<1, threads, 0, s>>>(ctx->dctrl, ctx->count, ctx->counters, h, use_cond);
+    return cudaGetLastError();
+}
+
+static gs_status bget_graph(gsb_ctx* ctx, cudaGraphExec_t* out) {
+    if (ctx->exec) {
+        *out = ctx->exec;
+        return GS_OK;
+    }
+    cudaGraph_t g = nullptr, body = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaError_t e = make_while_graph(&g, &h, &body);
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(ctx->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t eb = bbody(ctx, ctx->cap, (unsigned long long)h, 1, true);
+        cudaGraph_t tmp = body;
+        e = cudaStreamEndCapture(ctx->cap, &tmp);
+        if (eb != cudaSuccess) e = eb;
+    }
+    cudaGraphExec_t ex = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        bset_err(ctx, e, "batched step graph");
+        return GS_ERR_CUDA;
+    }
+    ctx->graph = g;
+    ctx->exec = ex;
+    *out = ex;
+    return GS_OK;
+}
+
+extern "C" {
+
+gs_status gsb_create(int count, const gsb_instance* inst, double L, double Du, double Dv, int prec, void* stream,
+                     gsb_ctx** out) {
+    if (!out) return GS_ERR_INVALID;
+    *out = nullptr;
+    if (count < 1 || count > 65536 || !inst || !(L > 0) || (prec != GS_FP32 && prec != GS_FP64))
+        return GS_ERR_INVALID;
+    for (int i = 0; i < count; ++i)
+        if (inst[i].nx < 1 || inst[i].ny < 1 || inst[i].nz < 1 || inst[i].nx > 65535 || inst[i].ny > 65535 ||
+            inst[i].nz > 65535)
+            return GS_ERR_INVALID;
+    gsb_ctx* ctx = new (std::nothrow) gsb_ctx();
+    if (!ctx) return GS_ERR_NOMEM;
+    ctx->count = count;
+    ctx->prec = prec;
+    ctx->esz = prec == GS_FP64 ? 8 : 4;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->hinst.resize(count);
+    long long off = 0;
+    for (int i = 0; i < count; ++i) {
+        BInst& b = ctx->hinst[i];
+        b.nx = inst[i].nx;
+        b.ny = inst[i].ny;
+        b.nz = inst[i].nz;
+        b.pad = 0;
+        b.off = off;
+        const double hx = L / b.nx, hy = L / b.ny, hz = L / b.nz;
+        b.cx = 1.0 / (hx * hx);
+        b.cy = 1.0 / (hy * hy);
+        b.cz = 1.0 / (hz * hz);
+        b.Du = Du;
+        b.Dv = Dv;
+        b.F = inst[i].F;
+        b.k = inst[i].k;
+        off += ((long long)b.nx * b.ny * b.nz + 3) / 4 * 4;  // instances start 16-byte aligned
+    }
+    ctx->total = off;
+    gs_status st = GS_OK;
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaGetDevice(&ctx->dev)) != cudaSuccess) break;
+        if ((e = cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, ctx->dev)) != cudaSuccess) break;
+        if ((e = cudaStreamCreateWithFlags(&ctx->cap, cudaStreamNonBlocking)) != cudaSuccess) break;
+        const size_t fbytes = ((size_t)ctx->total * ctx->esz + 255) / 256 * 256;
+        if ((e = cudaMalloc(&ctx->scratch, fbytes * 2 * kBFields)) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
+        for (int f = 0; f < kBFields; ++f)
+            for (int c = 0; c < 2; ++c) ctx->field[f][c] = ctx->scratch + fbytes * (2 * f + c);
+        if ((e = cudaMalloc(&ctx->dinst, sizeof(BInst) * count)) != cudaSuccess) break;
+        if ((e = cudaMemcpy(ctx->dinst, ctx->hinst.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            break;
+        if ((e = cudaMalloc(&ctx->dctrl, sizeof(DevCtrl) * count)) != cudaSuccess) break;
+        if ((e = cudaMemset(ctx->dctrl, 0, sizeof(DevCtrl) * count)) != cudaSuccess) break;
+        if ((e = cudaMallocHost(&ctx->hctrl, sizeof(DevCtrl) * count)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->counters, sizeof(unsigned int) * kCounters)) != cudaSuccess) break;
+    } while (0);
+    if (e == cudaSuccess && st == GS_OK) st = build_segments(ctx);
+    if (e != cudaSuccess || st != GS_OK) {
+        if (st == GS_OK) st = (e == cudaErrorMemoryAllocation) ? GS_ERR_NOMEM : GS_ERR_CUDA;
+        if (e != cudaSuccess) set_global_error(e, "gsb_create");
+        gsb_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+gs_status gsb_destroy(gsb_ctx* ctx) {
+    if (!ctx) return GS_OK;
+    bdrop_graph(ctx);
+    if (ctx->cap) cudaStreamDestroy(ctx->cap);
+    if (ctx->scratch) cudaFree(ctx->scratch);
+    if (ctx->dinst) cudaFree(ctx->dinst);
+    if (ctx->dctrl) cudaFree(ctx->dctrl);
+    if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
+    if (ctx->counters) cudaFree(ctx->counters);
+    for (int i = 0; i < 2; ++i)
+        if (ctx->dseg[i]) cudaFree(ctx->dseg[i]);
+    delete ctx;
+    return GS_OK;
+}
+
+gs_status gsb_layout(const gsb_ctx* ctx, long long* offsets) {
+    if (!ctx || !offsets) return GS_ERR_INVALID;
+    for (int i = 0; i < ctx->count; ++i) offsets[i] = ctx->hinst[i].off;
+    offsets[ctx->count] = ctx->total;
+    return GS_OK;
+}
+
+gs_status gsb_bind_state(gsb_ctx* ctx, void* u, void* v) {
+    if (!ctx || !u || !v || (((uintptr_t)u | (uintptr_t)v) & 15)) return GS_ERR_INVALID;
+    if (ctx->state[0] != u || ctx->state[1] != v) bdrop_graph(ctx);
+    ctx->state[0] = u;
+    ctx->state[1] = v;
+    return GS_OK;
+}
+
+gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc) {
+    if (!ctx || !(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 1 || zc > 1024)
+        return GS_ERR_INVALID;
+    if (ty == ctx->ty && zc == ctx->zc) return GS_OK;
+    bdrop_graph(ctx);
+    ctx->ty = ty;
+    ctx->zc = zc;
+    return build_segments(ctx);
+}
+
+gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double* t, double t_end, double* dt,
+                                 long max_accepted, long* n_acc, long* n_rej, int* status) {
+    if (!ctx || !t || !dt || !ctx->state[0]) return GS_ERR_INVALID;
+    if (!(atol >= 0) || !(rtol >= 0) || !(atol > 0 || rtol > 0) || std::isnan(t_end)) return GS_ERR_INVALID;
+    for (int i = 0; i < ctx->count; ++i)
+        if (!(dt[i] > 0)) return GS_ERR_INVALID;
+    int active = 0;
+    for (int i = 0; i < ctx->count; ++i) {
+        DevCtrl* h = ctx->hctrl + i;
+        memset(h, 0, sizeof(DevCtrl));
+        h->mode = CTRL_ADAPTIVE;
+        h->t = t[i];
+        h->t0 = t[i];
+        h->t_end = t_end;
+        h->dt = dt[i];
+        h->atol = atol;
+        h->rtol = rtol;
+        h->max_acc = max_accepted < 0 ? -1 : max_accepted;
+        h->max_att = kMaxAttempts;
+        if (!(h->t < t_end) || max_accepted == 0) {
+            h->done = 1;
+            continue;
+        }
+        double ht = dt[i];
+        if (h->t + ht >= t_end) {
+            ht = t_end - h->t;
+            h->last = 1;
+        }
+        if (!(ht > 0.0) || h->t + ht == h->t) {
+            h->status = GS_ERR_STEP_UNDERFLOW;
+            h->done = 1;
+            continue;
+        }
+        h->dt_try = ht;
+        ++active;
+    }
+    BCK(cudaMemcpyAsync(ctx->dctrl, ctx->hctrl, sizeof(DevCtrl) * ctx->count, cudaMemcpyHostToDevice, ctx->stream));
+    if (active > 0) {
+        BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * kCounters, ctx->stream));
+        BCK(blaunch_dopri5_stage(ctx, ctx->stream, 1));
+        cudaGraphExec_t ex;
+        gs_status st = bget_graph(ctx, &ex);
+        if (st != GS_OK) return st;
+        BCK(cudaGraphLaunch(ex, ctx->stream));
+        if (ctx->prec == GS_FP64)
+            gsb_copy_back_kernel<double><<<std::min(ctx->count, ctx->nsm * 4), 256, 0, ctx->stream>>>(
+                ctx->dinst, ctx->dctrl, ctx->count, (const double*)ctx->field[0][0], (const double*)ctx->field[0][1],
+                (double*)ctx->state[0], (double*)ctx->state[1]);
+        else
+            gsb_copy_back_kernel<float><<<std::min(ctx->count, ctx->nsm * 4), 256, 0, ctx->stream>>>(
+                ctx->dinst, ctx->dctrl, ctx->count, (const float*)ctx->field[0][0], (const float*)ctx->field[0][1],
+                (float*)ctx->state[0], (float*)ctx->state[1]);
+        BCK(cudaGetLastError());
+    }
+    BCK(cudaMemcpyAsync(ctx->hctrl, ctx->dctrl, sizeof(DevCtrl) * ctx->count, cudaMemcpyDeviceToHost, ctx->stream));
+    BCK(cudaStreamSynchronize(ctx->stream));
+    gs_status first = GS_OK;
+    for (int i = 0; i < ctx->count; ++i) {
+        const DevCtrl* h = ctx->hctrl + i;
+        t[i] = h->t;
+        dt[i] = h->dt;
+        if (n_acc) n_acc[i] = (long)h->n_acc;
+        if (n_rej) n_rej[i] = (long)h->n_rej;
+        if (status) status[i] = h->status;
+        if (first == GS_OK && h->status != GS_OK) first = (gs_status)h->status;
+    }
+    return first;
+}
+
+gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
+    if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
+    static const int cand[][2] = {{4, 8}, {4, 16}, {6, 8}, {6, 16}, {6, 32}, {8, 8}, {8, 16}, {14, 8}, {14, 16}};
+    // control blocks for timing: every instance running, parity 0, dt 1e-3
+    for (int i = 0; i < ctx->count; ++i) {
+        DevCtrl* h = ctx->hctrl + i;
+        memset(h, 0, sizeof(DevCtrl));
+        h->mode = CTRL_ADAPTIVE;
+        h->dt = h->dt_try = 1e-3;
+        h->atol = h->rtol = 1e-6;
+        h->t_end = INFINITY;
+        h->max_acc = -1;
+        h->max_att = kMaxAttempts;
+    }
+    BCK(cudaMemcpyAsync(ctx->dctrl, ctx->hctrl, sizeof(DevCtrl) * ctx->count, cudaMemcpyHostToDevice, ctx->stream));
+    cudaEvent_t e0, e1;
+    BCK(cudaEventCreate(&e0));
+    BCK(cudaEventCreate(&e1));
+    const int old_ty = ctx->ty, old_zc = ctx->zc;
+    float best = 1e30f;
+    int bty = old_ty, bzc = old_zc;
+    gs_status st = GS_OK;
+    for (const auto& c : cand) {
+        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK) break;
+        float acc = 0.f;
+        for (int r = 0; r < 3 && st == GS_OK; ++r) {
+            BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * kCounters, ctx->stream));
+            BCK(cudaEventRecord(e0, ctx->stream));
+            cudaError_t e = blaunch_dopri5_stage(ctx, ctx->stream, 1);
+            if (e == cudaSuccess) e = bbody(ctx, ctx->stream, 0, 0, false);
+            if (e != cudaSuccess) {
+                bset_err(ctx, e, "gsb_autotune");
+                st = GS_ERR_CUDA;
+                break;
+            }
+            BCK(cudaEventRecord(e1, ctx->stream));
+            BCK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            BCK(cudaEventElapsedTime(&ms, e0, e1));
+            if (r > 0) acc += ms;  // repetition 0 warms up
+        }
+        if (st != GS_OK) break;
+        if (acc / 2 < best) {
+            best = acc / 2;
+            bty = c[0];
+            bzc = c[1];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != GS_OK) return st;
+    (void)old_ty;
+    (void)old_zc;
+    if ((st = gsb_set_tile(ctx, bty, bzc)) != GS_OK) return st;
+    if (ty_out) *ty_out = bty;
+    if (zc_out) *zc_out = bzc;
+    if (best_ms) *best_ms = best;
+    return GS_OK;
+}
+
+const char* gsb_last_error(const gsb_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+}  // extern "C"

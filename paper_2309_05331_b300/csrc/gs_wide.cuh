@@ -23,6 +23,14 @@ namespace gsk {
 template <typename T, int VX>
 struct VecT;
 template <>
+struct VecT<float, 1> {
+    using type = float;
+};
+template <>
+struct VecT<double, 1> {
+    using type = double;
+};
+template <>
 struct VecT<float, 4> {
     using type = float4;
 };
@@ -76,7 +84,7 @@ __device__ __forceinline__ float fast_ratio<float>(float a, float b) {
 // row of 32*VX cells + 2 halo columns, padded to a whole vector
 template <int VX>
 __host__ __device__ constexpr int wide_pitch() {
-    return 32 * VX + VX;
+    return 32 * VX + (VX >= 2 ? VX : 2);
 }
 template <typename T, int VX>
 __host__ __device__ inline size_t wide_smem_bytes(int ty) {
@@ -91,64 +99,81 @@ struct Carry {
     T b[MODE == MODE_FINAL ? (NK > 0 ? NK : 1) : 1][2][VX];
 };
 
-template <typename T, int NK, int MODE, int VX>
-__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_kernel(const Geom<T> g, const StageArgs A) {
-    constexpr int TXW = 32 * VX;
-    constexpr int PITCH = wide_pitch<VX>();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* S = reinterpret_cast<T*>(smem_raw);
-    __shared__ T red[32];
-    __shared__ int s_last;
+// Resolved buffers of one stage launch (one grid, or one batched instance).
+template <typename T, int NK>
+struct StagePtrs {
+    const T* u[2];
+    const T* k[NK > 0 ? NK : 1][2];
+    T* o0[2];
+    T* o1[2];
+    const T* ex[kMaxNE][2];
+};
 
-    const int lane = threadIdx.x;
-    const int w = threadIdx.y;
-    const int TY = A.ty;
-    const int TYP = TY + 2;
-
-    int parity = 0;
-    long long step = 0;
-    double dtd = 0.0, atol = 0.0, rtol = 0.0;
-    int skip = 0;
-    if (A.ctrl) {
-        parity = A.ctrl->parity;
-        step = A.ctrl->step;
-        dtd = A.ctrl->dt_try;
-        atol = A.ctrl->atol;
-        rtol = A.ctrl->rtol;
-        skip = A.ctrl->done;
+template <typename T, int NK, int MODE>
+__device__ __forceinline__ StagePtrs<T, NK> resolve_stage(const StageArgs& A, int parity, long long step,
+                                                          long long off) {
+    StagePtrs<T, NK> P;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        P.u[c] = resolve<T>(A.u, c, parity, step) + off;
+#pragma unroll
+        for (int j = 0; j < NK; ++j) P.k[j][c] = resolve<T>(A.kin[j], c, parity, step) + off;
+        P.o0[c] = resolve<T>(A.out0, c, parity, step) + off;
+        P.o1[c] = (MODE != MODE_STAGE && A.has_out1) ? resolve<T>(A.out1, c, parity, step) + off : nullptr;
+#pragma unroll
+        for (int j = 0; j < kMaxNE; ++j)
+            P.ex[j][c] = (MODE == MODE_FINAL && j < A.n_ex) ? resolve<T>(A.ex[j], c, parity, step) + off : nullptr;
     }
-    const T dt = (T)dtd;
-    const T ta = (T)atol, tr = (T)rtol;
+    return P;
+}
 
-    const T* uin[2] = {resolve<T>(A.u, 0, parity, step), resolve<T>(A.u, 1, parity, step)};
-    const T* kin[NK > 0 ? NK : 1][2];
-    T aT[NK > 0 ? NK : 1];
+// Scalars of one stage launch: stage coefficients in T, dt and tolerances.
+template <typename T, int NK>
+struct StageCoef {
+    T a[NK > 0 ? NK : 1];
+    T bk[NK > 0 ? NK : 1];
+    T be[kMaxNE];
+    T bf;
+    T dt, ta, tr;
+    int n_ex, has_out1;
+};
+
+template <typename T, int NK>
+__device__ __forceinline__ StageCoef<T, NK> stage_coef(const StageArgs& A, double dt, double atol, double rtol) {
+    StageCoef<T, NK> C;
 #pragma unroll
     for (int j = 0; j < NK; ++j) {
-        kin[j][0] = resolve<T>(A.kin[j], 0, parity, step);
-        kin[j][1] = resolve<T>(A.kin[j], 1, parity, step);
-        aT[j] = (T)A.a[j];
+        C.a[j] = (T)A.a[j];
+        C.bk[j] = (T)A.bk[j];
     }
-    T* o0[2] = {resolve<T>(A.out0, 0, parity, step), resolve<T>(A.out0, 1, parity, step)};
-    const T* exs[kMaxNE][2] = {{nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}};
-    if (MODE == MODE_FINAL) {
-        for (int j = 0; j < A.n_ex; ++j) {
-            exs[j][0] = resolve<T>(A.ex[j], 0, parity, step);
-            exs[j][1] = resolve<T>(A.ex[j], 1, parity, step);
-        }
-    }
-    T* o1[2] = {nullptr, nullptr};
-    if (MODE != MODE_STAGE && A.has_out1) {
-        o1[0] = resolve<T>(A.out1, 0, parity, step);
-        o1[1] = resolve<T>(A.out1, 1, parity, step);
-    }
-    // Dormand-Prince error weights of k3..k6 in T (kin = {k1, k3, k4, k5, k6})
-    const T ew[4] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5, (T)dp5::E6};
-    const T e7 = (T)dp5::E7;
+#pragma unroll
+    for (int j = 0; j < kMaxNE; ++j) C.be[j] = (T)A.be[j];
+    C.bf = (T)A.bf;
+    C.dt = (T)dt;
+    C.ta = (T)atol;
+    C.tr = (T)rtol;
+    C.n_ex = A.n_ex;
+    C.has_out1 = A.has_out1;
+    return C;
+}
 
+// One segment: column (tx, tyi) of ty rows x 32*VX cells, planes [z0, z1).
+// Called by every thread of the CTA (it contains barriers).  Updates emax
+// (DOPRI_FINAL) with the scaled errors of this thread's cells.
+template <typename T, int NK, int MODE, int VX>
+__device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const StageCoef<T, NK>& C,
+                                             T* S, int TY, int tx, int tyi, int z0, int z1, T& emax) {
+    constexpr int TXW = 32 * VX;
+    constexpr int PITCH = wide_pitch<VX>();
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int TYP = TY + 2;
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const long long plane = (long long)nx * ny;
-    T emax = T(0);
+    const T dt = C.dt;
+    // Dormand-Prince error weights of k3..k6 (kin = {k1, k3, k4, k5, k6})
+    const T ew[4] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5, (T)dp5::E6};
+    const T e7 = (T)dp5::E7;
 
     auto sidx = [&](int buf, int ww, int c, int col) -> int { return ((buf * TYP + ww) * 2 + c) * PITCH + col; };
 
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             T uu[VX];
-            ldv<T, VX>(uin[c] + idx, uu);
+            ldv<T, VX>(P.u[c] + idx, uu);
             T s[VX], k1[VX], q[VX];
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
@@ -168,10 +193,10 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
                 T kk[VX];
-                ldv<T, VX>(kin[j][c] + idx, kk);
+                ldv<T, VX>(P.k[j][c] + idx, kk);
 #pragma unroll
                 for (int v = 0; v < VX; ++v) {
-                    s[v] = (j == 0) ? aT[0] * kk[v] : s[v] + aT[j] * kk[v];
+                    s[v] = (j == 0) ? C.a[0] * kk[v] : s[v] + C.a[j] * kk[v];
                     if (MODE == MODE_FINAL) cr.b[j][c][v] = kk[v];
                     if (MODE == MODE_DOPRI_FINAL) {
                         if (j == 0)
@@ -186,24 +211,204 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s[v];
                 if (MODE == MODE_FINAL) cr.a[c][v] = uu[v];
                 if (MODE == MODE_DOPRI_FINAL) {
-                    cr.a[c][v] = ta + tr * (fabs(uu[v]) + dt * fabs(k1[v]));  // error scale
-                    cr.b[0][c][v] = q[v] - e7 * k1[v];                       // folded error terms
+                    cr.a[c][v] = C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v]));  // error scale
+                    cr.b[0][c][v] = q[v] - e7 * k1[v];                            // folded error terms
                 }
             }
         }
     };
     // Y of one cell (x-halo column)
     auto loadY1 = [&](long long idx, int c) -> T {
-        const T uu = __ldg(uin[c] + idx);
+        const T uu = __ldg(P.u[c] + idx);
         if (NK == 0) return uu;
-        T s = aT[0] * __ldg(kin[0][c] + idx);
+        T s = C.a[0] * __ldg(P.k[0][c] + idx);
 #pragma unroll
-        for (int j = 1; j < NK; ++j) s += aT[j] * __ldg(kin[j][c] + idx);
+        for (int j = 1; j < NK; ++j) s += C.a[j] * __ldg(P.k[j][c] + idx);
         return uu + dt * s;
     };
 
+    const int x0 = tx * TXW, y0 = tyi * TY;
+    const int aw = min(TXW, nx - x0);
+    const int nl = (aw + VX - 1) / VX;  // active lanes (aw is a multiple of VX)
+    const int ah = min(TY, ny - y0);
+    const bool irow = (w >= 1) && (w <= ah);
+    const bool act = (w <= ah + 1) && (lane < nl);
+    const bool inner = irow && (lane < nl);
+    const int y = wrap1(y0 - 1 + w, ny);
+    const long long rowb = (long long)nx * y;
+    const long long cbase = rowb + x0 + VX * lane;
+    // x-halo columns of the interior rows: lane r-1 of the top halo warp
+    // takes the left column of row r, of the bottom halo warp the right one
+    const bool hwarp = (w == 0) || (w == ah + 1);
+    const bool do_halo = hwarp && (lane < ah);
+    const int hrow = lane + 1;
+    const int hcol = (w == 0) ? TXW : TXW + 1;
+    const long long hbase =
+        (long long)nx * wrap1(y0 + lane, ny) + ((w == 0) ? wrap1(x0 - 1, nx) : wrap1(x0 + aw, nx));
+
+    T ym[2][VX], yc[2][VX], yp[2][VX];
+    Carry<T, NK, MODE, VX> cur, nxt;
+    if (inner) loadY(cbase + plane * wrap1(z0 - 1, nz), ym, nxt);
+    if (act) {
+        loadY(cbase + plane * z0, yc, cur);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(0, w, c, VX * lane), yc[c]);
+    }
+    if (do_halo)
+        for (int c = 0; c < 2; ++c) S[sidx(0, hrow, c, hcol)] = loadY1(hbase + plane * z0, c);
+    int bz = 0;  // ring buffer of plane z
+    for (int z = z0; z < z1; ++z) {
+        const int bn = (bz == 2) ? 0 : bz + 1;  // ring buffer of plane z+1
+        const long long zoff = plane * wrap1(z + 1, nz);
+        if (act) {
+            loadY(cbase + zoff, yp, nxt);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
+        }
+        if (do_halo)
+            for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
+        __syncthreads();
+        T xl[2], xr[2];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            xl[c] = __shfl_up_sync(0xffffffffu, yc[c][VX - 1], 1);
+            xr[c] = __shfl_down_sync(0xffffffffu, yc[c][0], 1);
+        }
+        if (inner) {
+            T lap[2][VX];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                if (lane == 0) xl[c] = S[sidx(bz, w, c, TXW)];
+                if (lane == nl - 1) xr[c] = S[sidx(bz, w, c, TXW + 1)];
+                T ys[VX], yn[VX];
+                lds_v<T, VX>(S + sidx(bz, w - 1, c, VX * lane), ys);
+                lds_v<T, VX>(S + sidx(bz, w + 1, c, VX * lane), yn);
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                    const T xm = (v == 0) ? xl[c] : yc[c][v - 1];
+                    const T xp = (v == VX - 1) ? xr[c] : yc[c][v + 1];
+                    const T yy = yc[c][v];
+                    lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
+                                (ym[c][v] - T(2) * yy + yp[c][v]) * g.cz;
+                }
+            }
+            T f[2][VX];
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                const T uvv = yc[0][v] * yc[1][v] * yc[1][v];
+                f[0][v] = g.Du * lap[0][v] - uvv + g.F * (T(1) - yc[0][v]);
+                f[1][v] = g.Dv * lap[1][v] + uvv - (g.F + g.k) * yc[1][v];
+            }
+            const long long i = cbase + plane * z;
+            if (MODE == MODE_STAGE) {
+                stv<T, VX>(P.o0[0] + i, f[0]);
+                stv<T, VX>(P.o0[1] + i, f[1]);
+            } else if (MODE == MODE_FINAL) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    T s[VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        s[v] = C.bf * f[c][v];
+#pragma unroll
+                        for (int j = 0; j < NK; ++j) s[v] += C.bk[j] * cur.b[j][c][v];
+                    }
+#pragma unroll
+                    for (int j = 0; j < kMaxNE; ++j) {
+                        if (j < C.n_ex) {
+                            T e[VX];
+                            ldv<T, VX>(P.ex[j][c] + i, e);
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) s[v] += C.be[j] * e[v];
+                        }
+                    }
+                    T o[VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) o[v] = cur.a[c][v] + dt * s[v];
+                    stv<T, VX>(P.o0[c] + i, o);
+                    if (C.has_out1) stv<T, VX>(P.o1[c] + i, f[c]);
+                }
+            } else {  // MODE_DOPRI_FINAL
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    stv<T, VX>(P.o0[c] + i, yc[c]);
+                    stv<T, VX>(P.o1[c] + i, f[c]);
+                    if (NK == 5) {
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const T err = dt * (cur.b[0][c][v] + e7 * f[c][v]);
+                            emax = nanmax(emax, fast_ratio<T>(fabs(err), cur.a[c][v]));
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                ym[c][v] = yc[c][v];
+                yc[c][v] = yp[c][v];
+            }
+        cur = nxt;
+        bz = bn;
+    }
+    __syncthreads();  // the smem ring is reused by the next segment
+}
+
+// Last CTA of a final kernel: fold the error maximum into the control
+// block, run the controller and set the loop condition.
+template <typename T, int MODE>
+__device__ __forceinline__ void final_kernel_epilogue(const StageArgs& A, T emax, T* red, int* s_last) {
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    if (MODE == MODE_DOPRI_FINAL) {
+        const T bmax = block_nanmax(emax, red);
+        if (tid == 0) atomic_max_nonneg(&A.ctrl->err_bits, (double)bmax);
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&A.ctrl->arrive, 1u);
+        *s_last = (prev == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*s_last && tid == 0) {
+        __threadfence();
+        DevCtrl* c = A.ctrl;
+        const double E = __longlong_as_double((long long)atomicOr(&c->err_bits, 0ull));
+        c->err_bits = 0ull;
+        c->arrive = 0u;
+        int cont = 0;
+        if (!c->done) cont = controller_update(c, E);
+        if (A.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, cont ? 1u : 0u);
+    }
+}
+
+template <typename T, int NK, int MODE, int VX>
+__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_kernel(const Geom<T> g, const StageArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* S = reinterpret_cast<T*>(smem_raw);
+    __shared__ T red[32];
+    __shared__ int s_last;
+
+    int parity = 0;
+    long long step = 0;
+    double dtd = 0.0, atol = 0.0, rtol = 0.0;
+    int skip = 0;
+    if (A.ctrl) {
+        parity = A.ctrl->parity;
+        step = A.ctrl->step;
+        dtd = A.ctrl->dt_try;
+        atol = A.ctrl->atol;
+        rtol = A.ctrl->rtol;
+        skip = A.ctrl->done;
+    }
+    const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, parity, step, 0);
+    const StageCoef<T, NK> C = stage_coef<T, NK>(A, dtd, atol, rtol);
+    T emax = T(0);
     if (!skip) {
-        // balanced schedule over the (column, z) space, as in gs_stage_kernel
+        // balanced schedule over the (column, z) space: CTA b owns planes
+        // [L b / G, L (b+1) / G), L = columns * nz, cut at column ends
+        const int nz = g.nz;
         const long long L = (long long)A.ntx * A.nty * nz;
         const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
         for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
@@ -211,165 +416,10 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
             const int z0 = (int)(sg - (long long)col * nz);
             const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
             sg += z1 - z0;
-            const int tx = col % A.ntx;
-            const int tyi = col / A.ntx;
-            const int x0 = tx * TXW, y0 = tyi * TY;
-            const int aw = min(TXW, nx - x0);
-            const int nl = aw / VX;  // active lanes
-            const int ah = min(TY, ny - y0);
-            const bool irow = (w >= 1) && (w <= ah);
-            const bool act = (w <= ah + 1) && (lane < nl);
-            const bool inner = irow && (lane < nl);
-            const int y = wrap1(y0 - 1 + w, ny);
-            const long long rowb = (long long)nx * y;
-            const long long cbase = rowb + x0 + VX * lane;
-            // x-halo columns of the interior rows: lane r-1 of the top halo
-            // warp takes the left column of row r, of the bottom halo warp
-            // the right column
-            const bool hwarp = (w == 0) || (w == ah + 1);
-            const bool do_halo = hwarp && (lane < ah);
-            const int hrow = lane + 1;
-            const int hcol = (w == 0) ? TXW : TXW + 1;
-            const long long hbase =
-                (long long)nx * wrap1(y0 + lane, ny) + ((w == 0) ? wrap1(x0 - 1, nx) : wrap1(x0 + aw, nx));
-
-            T ym[2][VX], yc[2][VX], yp[2][VX];
-            Carry<T, NK, MODE, VX> cur, nxt;
-            {
-                const int b0 = 0;  // plane z0 -> buffer 0, z0+1 -> 1, ...
-                if (inner) loadY(cbase + plane * wrap1(z0 - 1, nz), ym, nxt);
-                if (act) {
-                    loadY(cbase + plane * z0, yc, cur);
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(b0, w, c, VX * lane), yc[c]);
-                }
-                if (do_halo)
-                    for (int c = 0; c < 2; ++c) S[sidx(b0, hrow, c, hcol)] = loadY1(hbase + plane * z0, c);
-            }
-            int bz = 0;  // buffer of plane z
-            for (int z = z0; z < z1; ++z) {
-                const int bn = (bz == 2) ? 0 : bz + 1;  // buffer of plane z+1
-                const long long zoff = plane * wrap1(z + 1, nz);
-                if (act) {
-                    loadY(cbase + zoff, yp, nxt);
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
-                }
-                if (do_halo)
-                    for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
-                __syncthreads();
-                T xl[2], xr[2];
-#pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    xl[c] = __shfl_up_sync(0xffffffffu, yc[c][VX - 1], 1);
-                    xr[c] = __shfl_down_sync(0xffffffffu, yc[c][0], 1);
-                }
-                if (inner) {
-                    T lap[2][VX];
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (lane == 0) xl[c] = S[sidx(bz, w, c, TXW)];
-                        if (lane == nl - 1) xr[c] = S[sidx(bz, w, c, TXW + 1)];
-                        T ys[VX], yn[VX];
-                        lds_v<T, VX>(S + sidx(bz, w - 1, c, VX * lane), ys);
-                        lds_v<T, VX>(S + sidx(bz, w + 1, c, VX * lane), yn);
-#pragma unroll
-                        for (int v = 0; v < VX; ++v) {
-                            const T xm = (v == 0) ? xl[c] : yc[c][v - 1];
-                            const T xp = (v == VX - 1) ? xr[c] : yc[c][v + 1];
-                            const T yy = yc[c][v];
-                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
-                                        (ym[c][v] - T(2) * yy + yp[c][v]) * g.cz;
-                        }
-                    }
-                    T f[2][VX];
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) {
-                        const T uvv = yc[0][v] * yc[1][v] * yc[1][v];
-                        f[0][v] = g.Du * lap[0][v] - uvv + g.F * (T(1) - yc[0][v]);
-                        f[1][v] = g.Dv * lap[1][v] + uvv - (g.F + g.k) * yc[1][v];
-                    }
-                    const long long i = cbase + plane * z;
-                    if (MODE == MODE_STAGE) {
-                        stv<T, VX>(o0[0] + i, f[0]);
-                        stv<T, VX>(o0[1] + i, f[1]);
-                    } else if (MODE == MODE_FINAL) {
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            T s[VX];
-#pragma unroll
-                            for (int v = 0; v < VX; ++v) {
-                                s[v] = (T)A.bf * f[c][v];
-#pragma unroll
-                                for (int j = 0; j < NK; ++j) s[v] += (T)A.bk[j] * cur.b[j][c][v];
-                            }
-#pragma unroll
-                            for (int j = 0; j < kMaxNE; ++j) {
-                                if (j < A.n_ex) {
-                                    T e[VX];
-                                    ldv<T, VX>(exs[j][c] + i, e);
-#pragma unroll
-                                    for (int v = 0; v < VX; ++v) s[v] += (T)A.be[j] * e[v];
-                                }
-                            }
-                            T o[VX];
-#pragma unroll
-                            for (int v = 0; v < VX; ++v) o[v] = cur.a[c][v] + dt * s[v];
-                            stv<T, VX>(o0[c] + i, o);
-                            if (A.has_out1) stv<T, VX>(o1[c] + i, f[c]);
-                        }
-                    } else {  // MODE_DOPRI_FINAL
-#pragma unroll
-                        for (int c = 0; c < 2; ++c) {
-                            stv<T, VX>(o0[c] + i, yc[c]);
-                            stv<T, VX>(o1[c] + i, f[c]);
-                            if (NK == 5) {
-#pragma unroll
-                                for (int v = 0; v < VX; ++v) {
-                                    const T err = dt * (cur.b[0][c][v] + e7 * f[c][v]);
-                                    emax = nanmax(emax, fast_ratio<T>(fabs(err), cur.a[c][v]));
-                                }
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int c = 0; c < 2; ++c)
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) {
-                        ym[c][v] = yc[c][v];
-                        yc[c][v] = yp[c][v];
-                    }
-                cur = nxt;
-                bz = bn;
-            }
-            __syncthreads();  // the smem ring is reused by the next tile
+            wide_segment<T, NK, MODE, VX>(g, P, C, S, A.ty, col % A.ntx, col / A.ntx, z0, z1, emax);
         }
     }
-
-    if (MODE != MODE_STAGE && A.run_ctrl && A.ctrl) {
-        const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-        if (MODE == MODE_DOPRI_FINAL) {
-            const T bmax = block_nanmax(emax, red);
-            if (tid == 0) atomic_max_nonneg(&A.ctrl->err_bits, (double)bmax);
-        }
-        if (tid == 0) {
-            __threadfence();
-            const unsigned prev = atomicAdd(&A.ctrl->arrive, 1u);
-            s_last = (prev == gridDim.x - 1) ? 1 : 0;
-        }
-        __syncthreads();
-        if (s_last && tid == 0) {
-            __threadfence();
-            DevCtrl* c = A.ctrl;
-            const double E = __longlong_as_double((long long)atomicOr(&c->err_bits, 0ull));
-            c->err_bits = 0ull;
-            c->arrive = 0u;
-            int cont = 0;
-            if (!c->done) cont = controller_update(c, E);
-            if (A.use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)A.cond, cont ? 1u : 0u);
-        }
-    }
+    if (MODE != MODE_STAGE && A.run_ctrl && A.ctrl) final_kernel_epilogue<T, MODE>(A, emax, red, &s_last);
 }
 
 }  // namespace gsk

@@ -1,0 +1,158 @@
+"""GPU parity of the batched ensemble (uneven grids, per-instance F, k and
+per-instance adaptive Dormand-Prince) against the oracle run instance by
+instance, against single-grid runs, and at the full 512-instance size."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+from tests._gpu_common import cuda_or_skip, to_np
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [dict(nx=12, ny=9, nz=7, F=0.03, k=0.05), dict(nx=5, ny=16, nz=3, F=0.045, k=0.061),
+         dict(nx=33, ny=4, nz=10, F=0.053, k=0.014), dict(nx=1, ny=1, nz=1, F=0.04, k=0.06),
+         dict(nx=8, ny=8, nz=8, F=0.025, k=0.055), dict(nx=17, ny=23, nz=5, F=0.058, k=0.065),
+         dict(nx=40, ny=2, nz=1, F=0.035, k=0.045)]
+PHYS = dict(Du=2e-3, Dv=1e-3)
+
+
+def _inits(insts, seed0=100, round32=False):
+    out = []
+    for i, d in enumerate(insts):
+        u, v = si.gs_initial_state(d["nx"], d["ny"], d["nz"], seed=seed0 + i)
+        if round32:
+            u, v = u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
+        out.append((u, v))
+    return out
+
+
+def _batch(torch, insts, inits, prec):
+    import paper_2309_05331_b300 as gs
+    b = gs.GrayScottBatch(insts, L=2.5, prec=prec, **PHYS)
+    for i, (u, v) in enumerate(inits):
+        b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
+    return b
+
+
+def _oracle_adaptive(d, u, v, t_end, tol, max_acc=-1):
+    p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], **PHYS)
+    return oracle.gs_integrate_adaptive(p, u, v, 0.0, t_end, 0.1, tol, tol, max_acc=max_acc)
+
+
+def test_batched_fp64_matches_oracle_per_instance():
+    torch = cuda_or_skip()
+    inits = _inits(SMALL)
+    b = _batch(torch, SMALL, inits, 0)
+    r = b.integrate_adaptive(1e-8, 1e-8, 0.0, 5.0, 0.1)
+    for i, d in enumerate(SMALL):
+        ref = _oracle_adaptive(d, *inits[i], 5.0, 1e-8)
+        assert r["t"][i] == 5.0 and ref["t"] == 5.0
+        assert (r["n_acc"][i], r["n_rej"][i]) == (ref["n_acc"], ref["n_rej"]), i
+        gu, gv = b.view(i)
+        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-12, i
+    b.close()
+
+
+def test_batched_fp32_against_fp64_oracle():
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, round32=True)
+    b = _batch(torch, SMALL, inits, 1)
+    r = b.integrate_adaptive(1e-6, 1e-6, 0.0, 8.0, 0.1)
+    for i, d in enumerate(SMALL):
+        ref = _oracle_adaptive(d, *inits[i], 8.0, 1e-6)
+        assert abs(int(r["n_acc"][i]) - ref["n_acc"]) <= 1
+        gu, gv = b.view(i)
+        err = oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]])
+        assert err < 1e-5, (i, err)
+    b.close()
+
+
+def test_failure_of_one_instance_is_isolated():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    inits = _inits(SMALL)
+    inits[2][0][1, 2, 3] = np.nan
+    b = _batch(torch, SMALL, inits, 0)
+    r = b.integrate_adaptive(1e-8, 1e-8, 0.0, 2.0, 0.1, check=False)
+    assert r["status"] == gs.GS_ERR_NONFINITE
+    assert r["statuses"][2] == gs.GS_ERR_NONFINITE
+    for i, d in enumerate(SMALL):
+        if i == 2:
+            continue
+        assert r["statuses"][i] == gs.GS_OK and r["t"][i] == 2.0
+        ref = _oracle_adaptive(d, *inits[i], 2.0, 1e-8)
+        gu, gv = b.view(i)
+        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-12, i
+    b.close()
+
+
+def test_batched_equals_single_grid_runs():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    insts = SMALL[:3] + SMALL[4:]
+    inits = _inits(insts, seed0=7)
+    b = _batch(torch, insts, inits, 0)
+    r = b.integrate_adaptive(1e-8, 1e-8, 0.0, 3.0, 0.1)
+    for i, d in enumerate(insts):
+        g = gs.GrayScott(d["nx"], d["ny"], d["nz"], L=2.5, F=d["F"], k=d["k"], prec=gs.GS_FP64, **PHYS)
+        g.set_state(torch.from_numpy(inits[i][0]), torch.from_numpy(inits[i][1]))
+        rs = g.integrate_adaptive(1e-8, 1e-8, 0.0, 3.0, 0.1)
+        assert (rs["n_acc"], rs["n_rej"]) == (r["n_acc"][i], r["n_rej"][i])
+        gu, gv = b.view(i)
+        assert oracle.rel_l2([to_np(gu), to_np(gv)], [to_np(g.u), to_np(g.v)]) < 1e-13
+        g.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tile", [(2, 1), (4, 5), (14, 64)])
+def test_batched_segment_shape_does_not_change_results(tile):
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=11)
+    res = []
+    for ty, zc in [(6, 16), tile]:
+        b = _batch(torch, SMALL, inits, 0)
+        b.set_tile(ty, zc)
+        b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
+        res.append([to_np(x) for i in range(len(SMALL)) for x in b.view(i)])
+        b.close()
+    for a, c in zip(*res):
+        assert np.array_equal(a, c)
+
+
+def test_batched_max_accepted_and_per_instance_times():
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=3)
+    b = _batch(torch, SMALL, inits, 1)
+    t0 = np.linspace(0.0, 3.0, len(SMALL))
+    r = b.integrate_adaptive(1e-6, 1e-6, t0, np.inf, 0.1, max_accepted=4)
+    assert np.all(r["n_acc"] == 4) and np.all(r["t"] > t0)
+    b.close()
+
+
+def test_full_size_512_instance_ensemble():
+    """512 instances, per-axis edges U{16..96}, F in [0.02,0.06], k in
+    [0.04,0.07], FP32 state / FP64 control, 3 accepted steps each; the three
+    smallest instances against the FP64 oracle."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    insts = si.batch_instances(512, seed=3)
+    b = gs.GrayScottBatch(insts, L=2.5, Du=2e-5, Dv=1e-5, prec=gs.GS_FP32)
+    inits = []
+    for i, d in enumerate(insts):
+        u, v = si.gs_initial_state(d["nx"], d["ny"], d["nz"], seed=1000 + i)
+        b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
+        inits.append((u, v))
+    b.autotune()
+    r = b.integrate_adaptive(1e-6, 1e-6, 0.0, np.inf, 0.1, max_accepted=3)
+    assert np.all(r["statuses"] == 0) and np.all(r["n_acc"] == 3)
+    sizes = [d["nx"] * d["ny"] * d["nz"] for d in insts]
+    for i in np.argsort(sizes)[:3]:
+        d = insts[i]
+        u, v = (a.astype(np.float32).astype(np.float64) for a in inits[i])
+        p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], Du=2e-5, Dv=1e-5)
+        ref = oracle.gs_integrate_adaptive(p, u, v, 0.0, np.inf, 0.1, 1e-6, 1e-6, max_acc=3)
+        gu, gv = b.view(int(i))
+        assert abs(ref["t"] - r["t"][i]) < 1e-6 * max(1.0, ref["t"])
+        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-5
+    b.close()
