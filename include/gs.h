@@ -143,7 +143,9 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* co
  * columns of ty rows (30 cells wide in the generic kernel, 128 FP32 / 64 FP64
  * cells in the vectorised one) and owns an equal share, of at least zc
  * planes, of all columns' planes.  ty in {2,4,6,8,14} (final kernels use at
- * most 6), 1 <= zc <= 1024.  Takes effect at the next integrator call. */
+ * most 6), 0 <= zc <= 1024; zc = 0 (the default) lets every resident CTA
+ * take a share (at least one plane).  Takes effect at the next integrator
+ * call. */
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);
 gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
 

@@ -173,8 +173,10 @@ static gs_status build_segments(gsb_ctx* ctx) {
         for (int i = 0; i < ctx->count; ++i) {
             const BInst& in = ctx->hinst[i];
             const int ncol = ((in.nx + 31) / 32) * ((in.ny + ty - 1) / ty);
-            for (int col = 0; col < ncol; ++col)
-                for (int z0 = 0; z0 < in.nz; z0 += ctx->zc) v.push_back(BSeg{i, col, z0, std::min(in.nz, z0 + ctx->zc)});
+            // z-chunk major: segments taken one after another cover the same
+            // planes of neighbouring columns, so their halos meet in L2
+            for (int z0 = 0; z0 < in.nz; z0 += ctx->zc)
+                for (int col = 0; col < ncol; ++col) v.push_back(BSeg{i, col, z0, std::min(in.nz, z0 + ctx->zc)});
         }
         if (ctx->dseg[li]) cudaFree(ctx->dseg[li]);
         ctx->dseg[li] = nullptr;

@@ -59,7 +59,7 @@ struct gs_ctx {
     long long* hpatch = nullptr;  // pinned staging of single-field patches
     double* dlog = nullptr;
     long log_cap = 0;
-    KCfg def{0, 6, 32};     // kernels of RK4 / Euler / AB4 / F (form 0: automatic)
+    KCfg def{0, 6, 0};      // kernels of RK4 / Euler / AB4 / F (form 0, zc 0: automatic)
     KCfg dp[7];             // Dormand-Prince k1 and stages 2..7 once tuned
     bool dp_tuned = false;
     int variant = 0;        // requested: 0 automatic, 1 generic, 2 vectorised, 3 vectorised 8-byte
@@ -119,6 +119,26 @@ static int pick_form(const gs_ctx* ctx, int form) {
     return form;
 }
 
+// Grid and schedule of a stencil launch.  zc == 0 (automatic): if the
+// columns fit in the resident CTAs, give each column k = min(nz, resident /
+// columns) CTAs with one z-band each (column-split: all columns sweep the
+// same planes together, no partial last wave); otherwise balanced linear
+// shares over all resident CTAs.  zc > 0: balanced linear shares of at
+// least zc planes.
+static int plan_schedule(const gs_ctx* ctx, StageArgs& A, int occ) {
+    const long long ncols = (long long)A.ntx * A.nty;
+    const long long gmax_res = (long long)ctx->nsm * occ;
+    const long long L = ncols * ctx->p.nz;
+    A.kper = 0;
+    if (A.zc == 0 && ncols <= gmax_res) {
+        const long long k = std::min<long long>(ctx->p.nz, gmax_res / ncols);
+        A.kper = (int)k;
+        return (int)(k * ncols);
+    }
+    const long long g = std::max<long long>(1, A.zc > 0 ? L / A.zc : L);
+    return (int)std::min<long long>(g, gmax_res);
+}
+
 template <typename T, int NK, int MODE, int VX>
 static cudaError_t launch_wide(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     const Geom<T> g = make_geom<T>(ctx->p);
@@ -134,9 +154,7 @@ static cudaError_t launch_wide(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     // every CTA owns at least zc planes of the (column, z) space
-    const long long L = (long long)A.ntx * A.nty * ctx->p.nz;
-    const long long gmax = std::max<long long>(1, L / std::max(1, A.zc));
-    const int grid = (int)std::min<long long>(gmax, (long long)ctx->nsm * occ);
+    const int grid = plan_schedule(ctx, A, occ);
     kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A);
     return cudaGetLastError();
 }
@@ -154,9 +172,7 @@ static cudaError_t launch_generic(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    const long long L = (long long)A.ntx * A.nty * ctx->p.nz;
-    const long long gmax = std::max<long long>(1, L / std::max(1, A.zc));
-    const int grid = (int)std::min<long long>(gmax, (long long)ctx->nsm * occ);
+    const int grid = plan_schedule(ctx, A, occ);
     kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A);
     return cudaGetLastError();
 }
@@ -540,7 +556,7 @@ gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out) {
             break;
         }
         memset(ctx->hctrl, 0, sizeof(DevCtrl));
-        ctx->def = KCfg{0, 6, 32};
+        ctx->def = KCfg{0, 6, 0};
     } while (0);
     if (e != cudaSuccess) {
         if (st == GS_OK) st = GS_ERR_CUDA;
@@ -714,7 +730,7 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts, long capacity, long* count) 
 
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc) {
     if (!ctx) return GS_ERR_INVALID;
-    if (!(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 1 || zc > 1024)
+    if (!(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 0 || zc > 1024)
         return GS_ERR_INVALID;
     drop_graphs(ctx);
     ctx->def.ty = ty;
@@ -783,7 +799,7 @@ static gs_status time_dp_kernel(gs_ctx* ctx, int k, int reps, cudaEvent_t e0, cu
 
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
-    static const int cand[][2] = {{2, 32}, {4, 8}, {4, 32}, {6, 8}, {6, 32}, {8, 8}, {8, 32}, {14, 8}, {14, 32}};
+    static const int cand[][2] = {{2, 0}, {4, 0}, {6, 0}, {8, 0}, {14, 0}, {4, 4}, {6, 4}, {8, 4}, {6, 16}, {8, 16}};
     int forms[3], nf = 0;
     for (int f = 1; f <= 3; ++f) {
         if (!form_ok(ctx, f)) continue;

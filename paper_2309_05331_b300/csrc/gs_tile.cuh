@@ -59,6 +59,7 @@ struct StageArgs {
     int has_out1;
     int ty, zc;             // tile shape
     int ntx, nty, ntz;      // tile counts
+    int kper;               // > 0: column-split schedule with kper z-bands per column
     DevCtrl* ctrl;          // may be null: plain F evaluation with dt = 0
     int run_ctrl;           // final kernels: run the controller in the last CTA
     unsigned long long cond;  // cudaGraphConditionalHandle (valid if use_cond)
@@ -154,16 +155,29 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_kerne
     };
 
     if (!skip) {
-        // balanced schedule: CTA b owns planes [L b / G, L (b+1) / G) of the
-        // linearised (column, z) space, L = columns * nz, cut into segments
-        // at column ends
-        const long long L = (long long)A.ntx * A.nty * nz;
-        const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
-        for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
-            const int col = (int)(sg / nz);
-            const int z0 = (int)(sg - (long long)col * nz);
-            const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
-            sg += z1 - z0;
+        // schedule (host-chosen): kper > 0 -- column-split: column b % ncols,
+        // z-band b / ncols of kper equal bands, so every column advances
+        // through the same planes in step and halos are shared through L2;
+        // kper == 0 -- CTA b owns planes [L b / G, L (b+1) / G) of the
+        // linearised (column, z) space, L = columns * nz, cut at column ends
+        const int ncols = A.ntx * A.nty;
+        const long long L = A.kper > 0 ? (long long)ncols * A.kper : (long long)ncols * nz;
+        const long long s_end = A.kper > 0 ? blockIdx.x + 1 : L * (blockIdx.x + 1) / gridDim.x;
+        for (long long sg = A.kper > 0 ? blockIdx.x : L * blockIdx.x / gridDim.x; sg < s_end;) {
+            int col, z0, z1;
+            if (A.kper > 0) {
+                col = (int)(sg % ncols);
+                const int band = (int)(sg / ncols);
+                z0 = (int)((long long)band * nz / A.kper);
+                z1 = (int)((long long)(band + 1) * nz / A.kper);
+                sg += 1;
+                if (band >= A.kper || z0 >= z1) continue;
+            } else {
+                col = (int)(sg / nz);
+                z0 = (int)(sg - (long long)col * nz);
+                z1 = (int)min((long long)nz, z0 + (s_end - sg));
+                sg += z1 - z0;
+            }
             const int tx = col % A.ntx;
             const int tyi = col / A.ntx;
             const int x0 = tx * kTileX, y0 = tyi * TY;

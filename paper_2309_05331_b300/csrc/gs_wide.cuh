@@ -406,16 +406,27 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
     const StageCoef<T, NK> C = stage_coef<T, NK>(A, dtd, atol, rtol);
     T emax = T(0);
     if (!skip) {
-        // balanced schedule over the (column, z) space: CTA b owns planes
-        // [L b / G, L (b+1) / G), L = columns * nz, cut at column ends
+        // schedule: see gs_stage_kernel (column-split when kper > 0, else
+        // balanced linear (column, z) shares)
         const int nz = g.nz;
-        const long long L = (long long)A.ntx * A.nty * nz;
-        const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
-        for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
-            const int col = (int)(sg / nz);
-            const int z0 = (int)(sg - (long long)col * nz);
-            const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
-            sg += z1 - z0;
+        const int ncols = A.ntx * A.nty;
+        const long long L = A.kper > 0 ? (long long)ncols * A.kper : (long long)ncols * nz;
+        const long long s_end = A.kper > 0 ? blockIdx.x + 1 : L * (blockIdx.x + 1) / gridDim.x;
+        for (long long sg = A.kper > 0 ? blockIdx.x : L * blockIdx.x / gridDim.x; sg < s_end;) {
+            int col, z0, z1;
+            if (A.kper > 0) {
+                col = (int)(sg % ncols);
+                const int band = (int)(sg / ncols);
+                z0 = (int)((long long)band * nz / A.kper);
+                z1 = (int)((long long)(band + 1) * nz / A.kper);
+                sg += 1;
+                if (band >= A.kper || z0 >= z1) continue;
+            } else {
+                col = (int)(sg / nz);
+                z0 = (int)(sg - (long long)col * nz);
+                z1 = (int)min((long long)nz, z0 + (s_end - sg));
+                sg += z1 - z0;
+            }
             wide_segment<T, NK, MODE, VX>(g, P, C, S, A.ty, col % A.ntx, col / A.ntx, z0, z1, emax);
         }
     }
