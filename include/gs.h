@@ -246,6 +246,86 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty, int* zc, double* best_ms);
 const char* gsb_last_error(const gsb_ctx* ctx);
 
 /* ------------------------------------------------------------------------ */
+/* Learned surrogate of the Gray-Scott integrator (the paper has no learned  */
+/* part: a BF16 3D convolutional network trained on the integrator's own    */
+/* trajectories, with the RK4 integrator as judge and fallback)              */
+/* ------------------------------------------------------------------------ */
+/* Network: x0 = ((u - mu_u)/sd_u, (v - mu_v)/sd_v); a_l = relu(conv_l(a_{l-1}))
+ * for l = 1..3 (2 -> 32 -> 32 -> 32 channels); y = conv_4(a_3) (32 -> 2);
+ * prediction of the state 16 RK4 steps (dt = 0.1) ahead = (u, v) + s * y.
+ * conv_l: 3x3x3 periodic convolution + bias, BF16 weights and activations
+ * (channels-last), FP32 accumulation on the tensor cores.  Parameters: one
+ * FP32 vector, per layer W[27][cin][cout] (tap = (dz+1)*9 + (dy+1)*3 +
+ * (dx+1)) then b[cout]. */
+typedef struct sur_ctx sur_ctx;
+
+/* Length of the parameter vector (58,850). */
+long sur_param_count(void);
+
+/* Context for one grid (nx % 16 == 0, ny % 8 == 0, nz % 2 == 0): parameters,
+ * Adam moments, activations and gradients (about 280 B per cell). */
+gs_status sur_create(int nx, int ny, int nz, void* stream, sur_ctx** out);
+gs_status sur_destroy(sur_ctx* ctx);
+
+/* Host copies of the FP32 parameters (set resets the Adam moments). */
+gs_status sur_set_params(sur_ctx* ctx, const float* params_host);
+gs_status sur_get_params(sur_ctx* ctx, float* params_host);
+/* Gradient of the last sur_train_step's loss w.r.t. the parameters. */
+gs_status sur_get_grad(sur_ctx* ctx, float* grad_host);
+
+/* Per-channel input mean mu and deviation sd, increment scale s (host
+ * arrays of 2 doubles: u, v). */
+gs_status sur_set_normalization(sur_ctx* ctx, const double* mean, const double* sd, const double* scale);
+
+/* Prediction (u_out, v_out) of the state 16 RK4 steps ahead of (u, v).
+ * FP32 device arrays of nx*ny*nz cells (x fastest); outputs must not alias
+ * inputs.  Enqueued on the context stream. */
+gs_status sur_forward(sur_ctx* ctx, const float* u, const float* v, float* u_out, float* v_out);
+
+/* One Adam step (beta = 0.9, 0.999, eps = 1e-8, learning rate lr) on the
+ * mean squared error of the normalised increment (u_tgt - u)/s_u,
+ * (v_tgt - v)/s_v over all cells; *loss (may be NULL) = the loss before the
+ * step.  Forward, input-gradient and weight-gradient convolutions all run on
+ * the BF16 tensor-core kernels.  Synchronises if loss != NULL. */
+gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const float* u_tgt, const float* v_tgt,
+                         double lr, double* loss);
+
+/* Advances (u, v) by 1.6 time units.  integ: a GS_FP32 context of the same
+ * grid bound to u, v (RK4, dt = 0.1, 16 steps).  judge = 0: the surrogate's
+ * prediction replaces (u, v) -- unless the last judged call failed, in which
+ * case the integrator runs (plain RK4 fallback, *fell_back = 1).  judge = 1:
+ * both run, (u, v) receive the integrator's result, *rel_err = relative L2
+ * distance of the prediction from it, and the context falls back to RK4 for
+ * later unjudged calls while *rel_err > threshold.  Synchronises. */
+gs_status sur_advance(sur_ctx* ctx, gs_ctx* integ, float* u, float* v, int judge, double threshold,
+                      double* rel_err, int* fell_back);
+
+const char* sur_last_error(const sur_ctx* ctx);
+
+/* Layer-level primitives.  Channel counts are padded to 8 or 32 in memory
+ * (BF16, channels-last, 16-byte cells); D % 2 == 0, H % 8 == 0, W % 16 == 0. */
+/* Packed tensor-core weight operand of a layer with real channels (cin,
+ * cout) from W[27][cin][cout] (FP32 device array): dgrad = 0 for the
+ * forward convolution, 1 for its input-gradient convolution (taps mirrored,
+ * channel roles swapped).  packed: device buffer of
+ * sur_packed_bytes(pad(cin), pad(cout)) (forward) or sur_packed_bytes(
+ * pad(cout), pad(cin)) (input gradient) bytes. */
+size_t sur_packed_bytes(int cin_pad, int cout_pad);
+gs_status sur_pack_weights(int cin, int cout, const float* w_dev, int dgrad, void* packed_dev, void* stream);
+/* out = epi(conv(x, packed)); epi 0: + bias, ReLU, BF16 [cells][cout_pad];
+ * 1: + bias, FP32 [cells][out_ch]; 2: times (mask > 0) (mask BF16
+ * [cells][cout_pad]), BF16; 3: FP32 [cells][cout_pad] (+ bias if given). */
+gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void* x, const void* packed,
+                     const float* bias, int epi, const void* mask, void* out, int out_ch, void* stream);
+/* dw[27][cin][cout] (FP32) = sum over cells p of x[p + off(tap)][i] dy[p][o]
+ * (the weight gradient); workspace of sur_wgrad_workspace_bytes bytes. */
+size_t sur_wgrad_workspace_bytes(int cin_pad, int cout_pad);
+gs_status sur_conv3d_wgrad(int D, int H, int W, int cin_pad, int cout_pad, const void* x, const void* dy, int cin,
+                           int cout, float* dw, void* workspace, size_t ws_bytes, void* stream);
+/* sum_sumsq_dev[0] += sum x, [1] += sum x^2 (FP64, device). */
+gs_status sur_moments(long n, const float* x, double* sum_sumsq_dev, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Stage algebra (section "The distributed OpenFPM state type and algebra":  */
 /* for_each operations over up to 15 states)                                 */
 /* ------------------------------------------------------------------------ */

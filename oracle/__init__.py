@@ -335,3 +335,76 @@ def rel_l2(a, b):
     num = sum(float(np.sum((np.asarray(x, np.float64) - np.asarray(y, np.float64)) ** 2)) for x, y in zip(a, b))
     den = sum(float(np.sum(np.asarray(y, np.float64) ** 2)) for y in b)
     return float(np.sqrt(num / den))
+
+
+# --------------------------------------------------------------------------
+# Learned surrogate: 4-layer 3D conv network (2 -> 32 -> 32 -> 32 -> 2,
+# 3^3 periodic kernels, ReLU), composed from the convolutions above.  With
+# emulate_bf16 the tensors the GPU stores in BF16 (normalised input, weights,
+# hidden activations, gradients of layer outputs) are rounded to BF16
+# (round-to-nearest-even) at the same points; all arithmetic is FP64.
+# --------------------------------------------------------------------------
+SURROGATE_LAYERS = [(2, 32), (32, 32), (32, 32), (32, 2)]
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    f = np.asarray(a, dtype=np.float32).copy()
+    b = f.view(np.uint32)
+    b += ((b >> 16) & np.uint32(1)) + np.uint32(0x7FFF)
+    b &= np.uint32(0xFFFF0000)
+    return f.astype(np.float64)
+
+
+def surrogate_unpack(params):
+    """[(W[27,cin,cout], b[cout])] from the flat parameter vector."""
+    p = np.asarray(params, dtype=np.float64)
+    out, off = [], 0
+    for cin, cout in SURROGATE_LAYERS:
+        nw = 27 * cin * cout
+        out.append((p[off:off + nw].reshape(27, cin, cout), p[off + nw:off + nw + cout]))
+        off += nw + cout
+    return out
+
+
+def surrogate_param_count():
+    return sum(27 * a * b + b for a, b in SURROGATE_LAYERS)
+
+
+def surrogate_forward(params, u, v, mean, sd, scale, emulate_bf16=True):
+    """Prediction of the state 16 RK4 steps ahead, u, v shaped (D, H, W)."""
+    r = bf16_round if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    layers = surrogate_unpack(params)
+    x = r(np.stack([(u - mean[0]) / sd[0], (v - mean[1]) / sd[1]], axis=-1))
+    for l, (w, b) in enumerate(layers):
+        z = conv3d_fwd(x, r(w), b)
+        x = r(np.maximum(z, 0.0)) if l < 3 else z
+    return u + scale[0] * x[..., 0], v + scale[1] * x[..., 1]
+
+
+def surrogate_loss_grad(params, u, v, ut, vt, mean, sd, scale, emulate_bf16=True):
+    """Loss = mean over cells and the 2 channels of (y - (target - state)/scale)^2
+    and its gradient w.r.t. the flat parameter vector (backpropagation with
+    the oracle's dgrad / wgrad)."""
+    r = bf16_round if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    layers = surrogate_unpack(params)
+    acts = [r(np.stack([(u - mean[0]) / sd[0], (v - mean[1]) / sd[1]], axis=-1))]
+    for l, (w, b) in enumerate(layers):
+        z = conv3d_fwd(acts[-1], r(w), b)
+        acts.append(r(np.maximum(z, 0.0)) if l < 3 else z)
+    y = acts[-1]
+    tgt = np.stack([(ut - u) / scale[0], (vt - v) / scale[1]], axis=-1)
+    n = y.size
+    diff = y - tgt
+    loss = float(np.sum(diff * diff) / n)
+    dy = r(2.0 * diff / n)
+    grads = [None] * 4
+    for l in range(3, -1, -1):
+        w, b = layers[l]
+        dw, db = conv3d_wgrad(acts[l], dy)
+        grads[l] = (dw, db)
+        if l > 0:
+            dx = conv3d_dgrad(dy, r(w))
+            dy = r(dx * (acts[l] > 0))
+    flat = np.concatenate([np.concatenate([g[0].reshape(-1), g[1]]) for g in grads])
+    return loss, flat

@@ -86,6 +86,25 @@ _SIGNATURES = {
     "gsb_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gsb_last_error": ([_vp], C.c_char_p),
+    "sur_param_count": ([], C.c_long),
+    "sur_create": ([C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
+    "sur_destroy": ([_vp], C.c_int),
+    "sur_set_params": ([_vp, C.POINTER(C.c_float)], C.c_int),
+    "sur_get_params": ([_vp, C.POINTER(C.c_float)], C.c_int),
+    "sur_get_grad": ([_vp, C.POINTER(C.c_float)], C.c_int),
+    "sur_set_normalization": ([_vp, _dp, _dp, _dp], C.c_int),
+    "sur_forward": ([_vp, _vp, _vp, _vp, _vp], C.c_int),
+    "sur_train_step": ([_vp, _vp, _vp, _vp, _vp, C.c_double, _dp], C.c_int),
+    "sur_advance": ([_vp, _vp, _vp, _vp, C.c_int, C.c_double, _dp, C.POINTER(C.c_int)], C.c_int),
+    "sur_last_error": ([_vp], C.c_char_p),
+    "sur_packed_bytes": ([C.c_int, C.c_int], C.c_size_t),
+    "sur_pack_weights": ([C.c_int, C.c_int, _vp, C.c_int, _vp, _vp], C.c_int),
+    "sur_conv3d": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp],
+                   C.c_int),
+    "sur_wgrad_workspace_bytes": ([C.c_int, C.c_int], C.c_size_t),
+    "sur_conv3d_wgrad": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp, _vp,
+                          C.c_size_t, _vp], C.c_int),
+    "sur_moments": ([C.c_long, _vp, _vp, _vp], C.c_int),
 }
 
 
@@ -405,6 +424,72 @@ class GrayScottBatch:
     def close(self):
         if self.ctx:
             lib().gsb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --------------------------------------------------------------------------
+# Learned surrogate
+# --------------------------------------------------------------------------
+def _scheck(st, ctx):
+    if st != GS_OK:
+        msg = lib().sur_last_error(ctx) if ctx else lib().gs_last_global_error()
+        raise GSError(st, (msg or b"").decode())
+
+
+class Surrogate:
+    """BF16 3D-conv surrogate of 16 RK4 steps (sur_* C ABI) on an (nz, ny, nx) grid."""
+
+    def __init__(self, nx, ny, nz, stream=None):
+        self.shape = (nz, ny, nx)
+        self.ctx = _vp()
+        _check(lib().sur_create(nx, ny, nz, _stream(stream), C.byref(self.ctx)))
+        self.nparams = int(lib().sur_param_count())
+
+    def set_params(self, params):
+        import numpy as np
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == self.nparams
+        _scheck(lib().sur_set_params(self.ctx, p.ctypes.data_as(C.POINTER(C.c_float))), self.ctx)
+
+    def get_params(self):
+        import numpy as np
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _scheck(lib().sur_get_params(self.ctx, p.ctypes.data_as(C.POINTER(C.c_float))), self.ctx)
+        return p
+
+    def get_grad(self):
+        import numpy as np
+        p = np.zeros(self.nparams, dtype=np.float32)
+        _scheck(lib().sur_get_grad(self.ctx, p.ctypes.data_as(C.POINTER(C.c_float))), self.ctx)
+        return p
+
+    def set_normalization(self, mean, sd, scale):
+        a = [(C.c_double * 2)(*map(float, x)) for x in (mean, sd, scale)]
+        _scheck(lib().sur_set_normalization(self.ctx, *a), self.ctx)
+
+    def forward(self, u, v, uo, vo):
+        _scheck(lib().sur_forward(self.ctx, _ptr(u), _ptr(v), _ptr(uo), _ptr(vo)), self.ctx)
+
+    def train_step(self, u, v, ut, vt, lr):
+        loss = C.c_double(0)
+        _scheck(lib().sur_train_step(self.ctx, _ptr(u), _ptr(v), _ptr(ut), _ptr(vt), lr, C.byref(loss)), self.ctx)
+        return loss.value
+
+    def advance(self, integ_ctx, u, v, judge=False, threshold=1e-3):
+        rel, fb = C.c_double(0), C.c_int(0)
+        _scheck(lib().sur_advance(self.ctx, integ_ctx, _ptr(u), _ptr(v), int(judge), threshold, C.byref(rel),
+                                  C.byref(fb)), self.ctx)
+        return rel.value, bool(fb.value)
+
+    def close(self):
+        if self.ctx:
+            lib().sur_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

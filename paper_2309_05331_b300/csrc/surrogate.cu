@@ -1,0 +1,681 @@
+// surrogate.cu -- learned surrogate of the Gray-Scott integrator: a 4-layer
+// 3D convolutional network (2 -> 32 -> 32 -> 32 -> 2 channels, 3^3 periodic
+// kernels, ReLU) that maps the state to its increment over 16 RK4 steps of
+// dt = 0.1, with BF16 weights / activations and FP32 accumulation on the
+// tensor cores (sur_conv.cuh), trained on the GPU by the same kernels
+// (forward, input gradient, weight gradient, Adam).  The plain RK4
+// integrator of gs_grid.cu is its judge and fallback (sur_advance).
+//
+// Parameter vector (FP32 master copy), per layer l = 1..4 with (cin, cout) =
+// (2,32), (32,32), (32,32), (32,2): W_l[27][cin][cout] (tap = (dz+1)*9 +
+// (dy+1)*3 + (dx+1)) followed by b_l[cout].
+// Model: x0 = ((u - mu_u)/sd_u, (v - mu_v)/sd_v); a_l = relu(conv_l(a_{l-1}));
+// y = conv_4(a_3); state' = state + s * y (per-channel increment scale s).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gs.h"
+#include "host_util.h"
+#include "sur_conv.cuh"
+
+using namespace sur;
+
+namespace {
+
+struct LayerDims {
+    int cin, cout;    // real channel counts
+    int cinp, coutp;  // padded (8 or 32)
+};
+constexpr LayerDims kLayers[4] = {{2, 32, 8, 32}, {32, 32, 32, 32}, {32, 32, 32, 32}, {32, 2, 32, 8}};
+
+long layer_w_off(int l) {
+    long off = 0;
+    for (int i = 0; i < l; ++i) off += 27L * kLayers[i].cin * kLayers[i].cout + kLayers[i].cout;
+    return off;
+}
+long layer_b_off(int l) { return layer_w_off(l) + 27L * kLayers[l].cin * kLayers[l].cout; }
+long param_count() { return layer_w_off(4); }
+
+size_t packed_bytes(int cinp, int coutp) { return (size_t)ksteps(cinp) * coutp * 32; }
+
+// ---------------------------------------------------------------------------
+// small kernels
+// ---------------------------------------------------------------------------
+
+// packed B operand (see conv_fwd_kernel) from W[27][cin][cout] (FP32).
+// dgrad: the input-gradient convolution (roles of cin / cout swapped, taps
+// mirrored): W'[tap'][o][i] = W[26 - tap'][i][o].
+__global__ void pack_kernel(const float* __restrict__ w, int cin, int cout, int cinp_eff, int coutp_eff, int dgrad,
+                            __nv_bfloat16* __restrict__ out) {
+    const int KS = ksteps(cinp_eff);
+    const int total = KS * coutp_eff * 16;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int jj = e % 16, r = e / 16, n = r % coutp_eff, ks = r / coutp_eff;
+        int tap, i;
+        if (cinp_eff == 32) {
+            tap = ks >> 1;
+            i = 16 * (ks & 1) + jj;
+        } else {
+            tap = 2 * ks + (jj >> 3);
+            i = jj & 7;
+        }
+        float v = 0.f;
+        if (tap < 27) {
+            if (!dgrad) {
+                if (i < cin && n < cout) v = w[((size_t)tap * cin + i) * cout + n];
+            } else {
+                // as a convolution with input channels = layer outputs (i) and
+                // outputs = layer inputs (n)
+                if (i < cout && n < cin) v = w[((size_t)(26 - tap) * cin + n) * cout + i];
+            }
+        }
+        const int byte = wrow_off(ks, n, jj >> 3, coutp_eff) + (jj & 7) * 2;
+        out[byte / 2] = __float2bfloat16(v);
+    }
+}
+
+__global__ void pad_bias_kernel(const float* __restrict__ b, int cout, int coutp, float* __restrict__ out) {
+    const int o = threadIdx.x;
+    if (o < coutp) out[o] = o < cout ? b[o] : 0.f;
+}
+
+// x0[cell] = ((u - m0)/s0, (v - m1)/s1, 0 x 6) in BF16
+__global__ void normalize_kernel(const float* __restrict__ u, const float* __restrict__ v, long long n, float m0,
+                                 float is0, float m1, float is1, __nv_bfloat16* __restrict__ x0) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        __nv_bfloat162 p = __floats2bfloat162_rn((u[c] - m0) * is0, (v[c] - m1) * is1);
+        uint4 row;
+        row.x = *reinterpret_cast<uint32_t*>(&p);
+        row.y = row.z = row.w = 0u;
+        reinterpret_cast<uint4*>(x0)[c] = row;
+    }
+}
+
+// state' = state + s * y
+__global__ void residual_kernel(const float* __restrict__ u, const float* __restrict__ v, const float* __restrict__ y,
+                                long long n, float s0, float s1, float* __restrict__ uo, float* __restrict__ vo) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const float2 d = reinterpret_cast<const float2*>(y)[c];
+        uo[c] = u[c] + s0 * d.x;
+        vo[c] = v[c] + s1 * d.y;
+    }
+}
+
+// MSE of the normalised increments and its gradient (mean over cells and
+// the 2 channels); dy4 in BF16, padded to 8 channels
+__global__ void loss_kernel(const float* __restrict__ y, const float* __restrict__ u, const float* __restrict__ v,
+                            const float* __restrict__ ut, const float* __restrict__ vt, long long n, float is0,
+                            float is1, __nv_bfloat16* __restrict__ dy4, double* __restrict__ loss) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    const float sc = 2.0f / (2.0f * (float)n);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const float2 p = reinterpret_cast<const float2*>(y)[c];
+        const float d0 = p.x - (ut[c] - u[c]) * is0;
+        const float d1 = p.y - (vt[c] - v[c]) * is1;
+        acc += (double)d0 * d0 + (double)d1 * d1;
+        __nv_bfloat162 g = __floats2bfloat162_rn(sc * d0, sc * d1);
+        uint4 row;
+        row.x = *reinterpret_cast<uint32_t*>(&g);
+        row.y = row.z = row.w = 0u;
+        reinterpret_cast<uint4*>(dy4)[c] = row;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        atomicAdd(loss, s / (2.0 * (double)n));
+    }
+}
+
+// db[o] += sum over cells of dy[cell][o], o < cout (dy has coutp channels)
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dy, long long n, int cout, int coutp,
+                                 float* __restrict__ db) {
+    __shared__ float part[256];
+    const int o = threadIdx.x % coutp, lanes = blockDim.x / coutp, li = threadIdx.x / coutp;
+    float acc = 0.f;
+    if (li < lanes)
+        for (long long c = blockIdx.x * (long long)lanes + li; c < n; c += (long long)gridDim.x * lanes)
+            acc += __bfloat162float(dy[c * coutp + o]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < coutp && threadIdx.x < cout) {
+        float s = 0.f;
+        for (int k = 0; k < lanes; ++k) s += part[k * coutp + threadIdx.x];
+        atomicAdd(db + threadIdx.x, s);
+    }
+}
+
+// dW[tap][i][o] (real dims, into the gradient vector) = sum over CTAs of the
+// padded partials
+__global__ void wgrad_reduce_kernel(const float* __restrict__ ws, int nblk, int cinp, int coutp, int cin, int cout,
+                                    float* __restrict__ dw) {
+    const int total = 27 * cin * cout;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int o = e % cout, r = e / cout, i = r % cin, tap = r / cin;
+        const size_t src = ((size_t)tap * cinp + i) * coutp + o;
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += ws[(size_t)b * 27 * cinp * coutp + src];
+        dw[e] = s;
+    }
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+// sums of (a - b)^2 and b^2 over two component pairs (relative L2 distance)
+__global__ void diff_norm_kernel(const float* __restrict__ a0, const float* __restrict__ a1,
+                                 const float* __restrict__ b0, const float* __restrict__ b1, long long n,
+                                 double* __restrict__ out) {
+    __shared__ double red[2][32];
+    double num = 0.0, den = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double d0 = (double)a0[c] - b0[c], d1 = (double)a1[c] - b1[c];
+        num += d0 * d0 + d1 * d1;
+        den += (double)b0[c] * b0[c] + (double)b1[c] * b1[c];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = num;
+        red[1][threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double sn = 0, sd = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            sn += red[0][w];
+            sd += red[1][w];
+        }
+        atomicAdd(out, sn);
+        atomicAdd(out + 1, sd);
+    }
+}
+
+__global__ void moments_kernel(const float* __restrict__ x, long long n, double* __restrict__ out) {
+    __shared__ double red[2][32];
+    double s = 0.0, q = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const double a = x[c];
+        s += a;
+        q += a * a;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = s;
+        red[1][threadIdx.x >> 5] = q;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        atomicAdd(out, a);
+        atomicAdd(out + 1, b);
+    }
+}
+
+int nsm_now() {
+    int dev = 0, n = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// convolution launchers
+// ---------------------------------------------------------------------------
+template <int CIN, int COUT, int EPI>
+cudaError_t launch_conv_t(int D, int H, int W, const __nv_bfloat16* x, const __nv_bfloat16* wp, const float* bias,
+                          const __nv_bfloat16* mask, void* out, int out_ch, cudaStream_t s) {
+    auto kern = conv_fwd_kernel<CIN, COUT, EPI>;
+    const size_t smem = (size_t)ksteps(CIN) * COUT * 32 + (size_t)HC * CIN * 2 + 16;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NTHREADS, smem);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (W / TX) * (H / TY) * (D / TZ);
+    const int grid = std::max(1, std::min(ntiles, nsm_now() * std::max(occ, 1)));
+    kern<<<grid, NTHREADS, smem, s>>>(x, wp, bias, mask, out, out_ch, D, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv(int cinp, int coutp, int epi, int D, int H, int W, const void* x, const void* wp,
+                        const float* bias, const void* mask, void* out, int out_ch, cudaStream_t s) {
+    const auto* xb = static_cast<const __nv_bfloat16*>(x);
+    const auto* wb = static_cast<const __nv_bfloat16*>(wp);
+    const auto* mb = static_cast<const __nv_bfloat16*>(mask);
+#define SUR_CONV_CASE(CI, CO, EP)                                                        \
+    if (cinp == CI && coutp == CO && epi == EP)                                          \
+        return launch_conv_t<CI, CO, EP>(D, H, W, xb, wb, bias, mb, out, out_ch, s);
+    SUR_CONV_CASE(8, 32, EPI_BIAS_RELU_BF16)
+    SUR_CONV_CASE(32, 32, EPI_BIAS_RELU_BF16)
+    SUR_CONV_CASE(32, 8, EPI_BIAS_F32)
+    SUR_CONV_CASE(8, 32, EPI_MASK_BF16)
+    SUR_CONV_CASE(32, 32, EPI_MASK_BF16)
+    SUR_CONV_CASE(8, 32, EPI_RAW_F32)
+    SUR_CONV_CASE(32, 32, EPI_RAW_F32)
+    SUR_CONV_CASE(32, 8, EPI_RAW_F32)
+#undef SUR_CONV_CASE
+    return cudaErrorInvalidValue;
+}
+
+int wgrad_grid() { return nsm_now(); }
+
+template <int CIN, int COUT>
+cudaError_t launch_wgrad_t(int D, int H, int W, const __nv_bfloat16* x, const __nv_bfloat16* dy, float* ws,
+                           cudaStream_t s) {
+    auto kern = conv_wgrad_kernel<CIN, COUT>;
+    const size_t smem = (size_t)HC * CIN * 2 + (size_t)TILE_CELLS * COUT * 2;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<wgrad_grid(), NTHREADS, smem, s>>>(x, dy, ws, D, H, W);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wgrad(int cinp, int coutp, int D, int H, int W, const void* x, const void* dy, float* ws,
+                         cudaStream_t s) {
+    const auto* xb = static_cast<const __nv_bfloat16*>(x);
+    const auto* yb = static_cast<const __nv_bfloat16*>(dy);
+    if (cinp == 8 && coutp == 32) return launch_wgrad_t<8, 32>(D, H, W, xb, yb, ws, s);
+    if (cinp == 32 && coutp == 32) return launch_wgrad_t<32, 32>(D, H, W, xb, yb, ws, s);
+    if (cinp == 32 && coutp == 8) return launch_wgrad_t<32, 8>(D, H, W, xb, yb, ws, s);
+    return cudaErrorInvalidValue;
+}
+
+size_t wgrad_ws_bytes(int cinp, int coutp) { return (size_t)wgrad_grid() * 27 * cinp * coutp * sizeof(float); }
+
+bool shape_ok(int D, int H, int W) {
+    return D >= TZ && H >= TY && W >= TX && D % TZ == 0 && H % TY == 0 && W % TX == 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// model context
+// ---------------------------------------------------------------------------
+struct sur_ctx {
+    int nx = 0, ny = 0, nz = 0;
+    long long N = 0;
+    cudaStream_t stream = nullptr;
+    long np = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // master params, grads, Adam moments
+    long step = 0;
+    void* wf[4] = {};      // packed forward weights (BF16)
+    void* wd[4] = {};      // packed input-gradient weights (layers 2..4)
+    float* bpad[4] = {};   // biases padded to coutp
+    void* x0 = nullptr;    // [N][8] BF16
+    void* a[3] = {};       // [N][32] BF16 activations of layers 1..3
+    float* y = nullptr;    // [N][2] FP32 network output
+    void* gy8 = nullptr;   // [N][8] BF16 gradient of the output
+    void* g32[2] = {};     // [N][32] BF16 gradients (ping-pong)
+    float* ws = nullptr;   // weight-gradient partials
+    size_t ws_bytes = 0;
+    float *su = nullptr, *sv = nullptr;  // surrogate prediction / saved input
+    float *iu = nullptr, *iv = nullptr;
+    double* dacc = nullptr;  // device reductions
+    double* hacc = nullptr;  // pinned
+    double mean[2] = {0, 0}, sd[2] = {1, 1}, scale[2] = {1, 1};
+    int fallback = 0;      // set when the last judged call exceeded the threshold
+    char err[512] = {0};
+};
+
+static void sset_err(sur_ctx* c, cudaError_t e, const char* where) {
+    if (c) snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+}
+#define SCK(call)                     \
+    do {                              \
+        cudaError_t e_ = (call);      \
+        if (e_ != cudaSuccess) {      \
+            sset_err(ctx, e_, #call); \
+            return GS_ERR_CUDA;       \
+        }                             \
+    } while (0)
+
+static gs_status repack(sur_ctx* ctx) {
+    for (int l = 0; l < 4; ++l) {
+        const LayerDims& L = kLayers[l];
+        pack_kernel<<<64, 256, 0, ctx->stream>>>(ctx->p + layer_w_off(l), L.cin, L.cout, L.cinp, L.coutp, 0,
+                                                 static_cast<__nv_bfloat16*>(ctx->wf[l]));
+        if (l > 0)
+            pack_kernel<<<64, 256, 0, ctx->stream>>>(ctx->p + layer_w_off(l), L.cin, L.cout, L.coutp, L.cinp, 1,
+                                                     static_cast<__nv_bfloat16*>(ctx->wd[l]));
+        pad_bias_kernel<<<1, 32, 0, ctx->stream>>>(ctx->p + layer_b_off(l), L.cout, L.coutp, ctx->bpad[l]);
+    }
+    SCK(cudaGetLastError());
+    return GS_OK;
+}
+
+// forward pass from (u, v) into ctx->y (and activations a[0..2])
+static gs_status forward(sur_ctx* ctx, const float* u, const float* v) {
+    const int D = ctx->nz, H = ctx->ny, W = ctx->nx;
+    const int grid = nsm_now() * 4;
+    normalize_kernel<<<grid, 256, 0, ctx->stream>>>(u, v, ctx->N, (float)ctx->mean[0], (float)(1.0 / ctx->sd[0]),
+                                                    (float)ctx->mean[1], (float)(1.0 / ctx->sd[1]),
+                                                    static_cast<__nv_bfloat16*>(ctx->x0));
+    SCK(cudaGetLastError());
+    SCK(launch_conv(8, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->x0, ctx->wf[0], ctx->bpad[0], nullptr, ctx->a[0], 32,
+                    ctx->stream));
+    SCK(launch_conv(32, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->a[0], ctx->wf[1], ctx->bpad[1], nullptr, ctx->a[1], 32,
+                    ctx->stream));
+    SCK(launch_conv(32, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->a[1], ctx->wf[2], ctx->bpad[2], nullptr, ctx->a[2], 32,
+                    ctx->stream));
+    SCK(launch_conv(32, 8, EPI_BIAS_F32, D, H, W, ctx->a[2], ctx->wf[3], ctx->bpad[3], nullptr, ctx->y, 2,
+                    ctx->stream));
+    return GS_OK;
+}
+
+extern "C" {
+
+long sur_param_count(void) { return param_count(); }
+
+gs_status sur_create(int nx, int ny, int nz, void* stream, sur_ctx** out) {
+    if (!out) return GS_ERR_INVALID;
+    *out = nullptr;
+    if (!shape_ok(nz, ny, nx)) return GS_ERR_INVALID;
+    sur_ctx* ctx = new (std::nothrow) sur_ctx();
+    if (!ctx) return GS_ERR_NOMEM;
+    ctx->nx = nx;
+    ctx->ny = ny;
+    ctx->nz = nz;
+    ctx->N = (long long)nx * ny * nz;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->np = param_count();
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaMalloc(&ctx->p, sizeof(float) * ctx->np * 4)) != cudaSuccess) break;
+        ctx->g = ctx->p + ctx->np;
+        ctx->m = ctx->g + ctx->np;
+        ctx->v = ctx->m + ctx->np;
+        if ((e = cudaMemset(ctx->p, 0, sizeof(float) * ctx->np * 4)) != cudaSuccess) break;
+        for (int l = 0; l < 4 && e == cudaSuccess; ++l) {
+            const LayerDims& L = kLayers[l];
+            if ((e = cudaMalloc(&ctx->wf[l], packed_bytes(L.cinp, L.coutp))) != cudaSuccess) break;
+            if (l > 0 && (e = cudaMalloc(&ctx->wd[l], packed_bytes(L.coutp, L.cinp))) != cudaSuccess) break;
+            e = cudaMalloc(&ctx->bpad[l], sizeof(float) * 32);
+        }
+        if (e != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->x0, ctx->N * 16)) != cudaSuccess) break;
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMalloc(&ctx->a[i], ctx->N * 64);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaMalloc(&ctx->g32[i], ctx->N * 64);
+        if (e != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->y, ctx->N * 8)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->gy8, ctx->N * 16)) != cudaSuccess) break;
+        ctx->ws_bytes = wgrad_ws_bytes(32, 32);
+        if ((e = cudaMalloc(&ctx->ws, ctx->ws_bytes)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->su, ctx->N * 4 * 4)) != cudaSuccess) break;
+        ctx->sv = ctx->su + ctx->N;
+        ctx->iu = ctx->sv + ctx->N;
+        ctx->iv = ctx->iu + ctx->N;
+        if ((e = cudaMalloc(&ctx->dacc, sizeof(double) * 4)) != cudaSuccess) break;
+        if ((e = cudaMallocHost(&ctx->hacc, sizeof(double) * 4)) != cudaSuccess) break;
+    } while (0);
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_create");
+        sur_destroy(ctx);
+        return e == cudaErrorMemoryAllocation ? GS_ERR_NOMEM : GS_ERR_CUDA;
+    }
+    if (repack(ctx) != GS_OK) {
+        sur_destroy(ctx);
+        return GS_ERR_CUDA;
+    }
+    *out = ctx;
+    return GS_OK;
+}
+
+gs_status sur_destroy(sur_ctx* ctx) {
+    if (!ctx) return GS_OK;
+    cudaFree(ctx->p);
+    for (int l = 0; l < 4; ++l) {
+        cudaFree(ctx->wf[l]);
+        cudaFree(ctx->wd[l]);
+        cudaFree(ctx->bpad[l]);
+    }
+    cudaFree(ctx->x0);
+    for (int i = 0; i < 3; ++i) cudaFree(ctx->a[i]);
+    for (int i = 0; i < 2; ++i) cudaFree(ctx->g32[i]);
+    cudaFree(ctx->y);
+    cudaFree(ctx->gy8);
+    cudaFree(ctx->ws);
+    cudaFree(ctx->su);
+    cudaFree(ctx->dacc);
+    if (ctx->hacc) cudaFreeHost(ctx->hacc);
+    delete ctx;
+    return GS_OK;
+}
+
+gs_status sur_set_params(sur_ctx* ctx, const float* host) {
+    if (!ctx || !host) return GS_ERR_INVALID;
+    SCK(cudaMemcpyAsync(ctx->p, host, sizeof(float) * ctx->np, cudaMemcpyHostToDevice, ctx->stream));
+    SCK(cudaMemsetAsync(ctx->m, 0, sizeof(float) * ctx->np * 2, ctx->stream));
+    ctx->step = 0;
+    gs_status st = repack(ctx);
+    if (st != GS_OK) return st;
+    SCK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+gs_status sur_get_params(sur_ctx* ctx, float* host) {
+    if (!ctx || !host) return GS_ERR_INVALID;
+    SCK(cudaMemcpyAsync(host, ctx->p, sizeof(float) * ctx->np, cudaMemcpyDeviceToHost, ctx->stream));
+    SCK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+gs_status sur_set_normalization(sur_ctx* ctx, const double* mean, const double* sd, const double* scale) {
+    if (!ctx || !mean || !sd || !scale) return GS_ERR_INVALID;
+    for (int c = 0; c < 2; ++c)
+        if (!(sd[c] > 0) || !(scale[c] > 0) || !std::isfinite(mean[c])) return GS_ERR_INVALID;
+    for (int c = 0; c < 2; ++c) {
+        ctx->mean[c] = mean[c];
+        ctx->sd[c] = sd[c];
+        ctx->scale[c] = scale[c];
+    }
+    return GS_OK;
+}
+
+gs_status sur_forward(sur_ctx* ctx, const float* u, const float* v, float* uo, float* vo) {
+    if (!ctx || !u || !v || !uo || !vo) return GS_ERR_INVALID;
+    gs_status st = forward(ctx, u, v);
+    if (st != GS_OK) return st;
+    residual_kernel<<<nsm_now() * 4, 256, 0, ctx->stream>>>(u, v, ctx->y, ctx->N, (float)ctx->scale[0],
+                                                             (float)ctx->scale[1], uo, vo);
+    SCK(cudaGetLastError());
+    return GS_OK;
+}
+
+gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const float* ut, const float* vt, double lr,
+                         double* loss) {
+    if (!ctx || !u || !v || !ut || !vt || !(lr > 0)) return GS_ERR_INVALID;
+    const int D = ctx->nz, H = ctx->ny, W = ctx->nx;
+    gs_status st = forward(ctx, u, v);
+    if (st != GS_OK) return st;
+    SCK(cudaMemsetAsync(ctx->dacc, 0, sizeof(double) * 4, ctx->stream));
+    SCK(cudaMemsetAsync(ctx->g, 0, sizeof(float) * ctx->np, ctx->stream));
+    const int grid = nsm_now() * 4;
+    loss_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->y, u, v, ut, vt, ctx->N, (float)(1.0 / ctx->scale[0]),
+                                               (float)(1.0 / ctx->scale[1]),
+                                               static_cast<__nv_bfloat16*>(ctx->gy8), ctx->dacc);
+    SCK(cudaGetLastError());
+    // backward, layer 4 .. 1: weight and bias gradients, then the input
+    // gradient masked by the ReLU derivative of the previous activation
+    const void* gin = ctx->gy8;  // gradient w.r.t. the current layer's output (pre-activation)
+    for (int l = 3; l >= 0; --l) {
+        const LayerDims& L = kLayers[l];
+        const void* xin = l == 0 ? ctx->x0 : ctx->a[l - 1];
+        SCK(launch_wgrad(L.cinp, L.coutp, D, H, W, xin, gin, ctx->ws, ctx->stream));
+        wgrad_reduce_kernel<<<128, 256, 0, ctx->stream>>>(ctx->ws, wgrad_grid(), L.cinp, L.coutp, L.cin, L.cout,
+                                                          ctx->g + layer_w_off(l));
+        bias_grad_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(gin), ctx->N, L.cout,
+                                                        L.coutp, ctx->g + layer_b_off(l));
+        SCK(cudaGetLastError());
+        if (l > 0) {
+            void* gout = ctx->g32[l & 1];
+            SCK(launch_conv(L.coutp, L.cinp, EPI_MASK_BF16, D, H, W, gin, ctx->wd[l], nullptr, ctx->a[l - 1], gout,
+                            L.cinp, ctx->stream));
+            gin = gout;
+        }
+    }
+    ctx->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - powf(b1, (float)ctx->step), c2 = 1.f - powf(b2, (float)ctx->step);
+    adam_kernel<<<64, 256, 0, ctx->stream>>>(ctx->p, ctx->g, ctx->m, ctx->v, ctx->np, (float)lr, b1, b2, 1e-8f, c1,
+                                             c2);
+    SCK(cudaGetLastError());
+    if ((st = repack(ctx)) != GS_OK) return st;
+    if (loss) {
+        SCK(cudaMemcpyAsync(ctx->hacc, ctx->dacc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        SCK(cudaStreamSynchronize(ctx->stream));
+        *loss = ctx->hacc[0];
+    }
+    return GS_OK;
+}
+
+gs_status sur_get_grad(sur_ctx* ctx, float* host) {
+    if (!ctx || !host) return GS_ERR_INVALID;
+    SCK(cudaMemcpyAsync(host, ctx->g, sizeof(float) * ctx->np, cudaMemcpyDeviceToHost, ctx->stream));
+    SCK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+gs_status sur_advance(sur_ctx* ctx, gs_ctx* integ, float* u, float* v, int judge, double threshold, double* rel_err,
+                      int* fell_back) {
+    if (!ctx || !u || !v || (judge && !integ)) return GS_ERR_INVALID;
+    if (fell_back) *fell_back = 0;
+    if (rel_err) *rel_err = -1.0;
+    const long long n = ctx->N;
+    if (!judge && ctx->fallback && integ) {  // the judge rejected the surrogate: plain RK4
+        double t = 0.0;
+        gs_status st = gs_step(integ, GS_RK4, &t, 0.1, 16);
+        if (fell_back) *fell_back = 1;
+        return st;
+    }
+    gs_status st = sur_forward(ctx, u, v, ctx->su, ctx->sv);
+    if (st != GS_OK) return st;
+    if (!judge) {
+        SCK(cudaMemcpyAsync(u, ctx->su, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        SCK(cudaMemcpyAsync(v, ctx->sv, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+        SCK(cudaStreamSynchronize(ctx->stream));
+        return GS_OK;
+    }
+    // judge: 16 RK4 steps of dt = 0.1 on the same state (the integrator is
+    // bound to u, v and updates them in place), then compare
+    SCK(cudaStreamSynchronize(ctx->stream));
+    double t = 0.0;
+    if ((st = gs_step(integ, GS_RK4, &t, 0.1, 16)) != GS_OK) return st;
+    SCK(cudaMemsetAsync(ctx->dacc, 0, sizeof(double) * 2, ctx->stream));
+    diff_norm_kernel<<<nsm_now() * 4, 256, 0, ctx->stream>>>(ctx->su, ctx->sv, u, v, n, ctx->dacc);
+    SCK(cudaGetLastError());
+    SCK(cudaMemcpyAsync(ctx->hacc, ctx->dacc, sizeof(double) * 2, cudaMemcpyDeviceToHost, ctx->stream));
+    SCK(cudaStreamSynchronize(ctx->stream));
+    const double rel = std::sqrt(ctx->hacc[0] / ctx->hacc[1]);
+    if (rel_err) *rel_err = rel;
+    ctx->fallback = !(rel <= threshold);
+    if (fell_back) *fell_back = ctx->fallback;
+    return GS_OK;
+}
+
+const char* sur_last_error(const sur_ctx* ctx) { return ctx ? ctx->err : ""; }
+
+// ---------------------------------------------------------------------------
+// primitives (layer-level access for tests and users)
+// ---------------------------------------------------------------------------
+size_t sur_packed_bytes(int cin_pad, int cout_pad) {
+    if ((cin_pad != 8 && cin_pad != 32) || (cout_pad != 8 && cout_pad != 32)) return 0;
+    return packed_bytes(cin_pad, cout_pad);
+}
+
+gs_status sur_pack_weights(int cin, int cout, const float* w, int dgrad, void* packed, void* stream) {
+    if (!w || !packed || cin < 1 || cin > 32 || cout < 1 || cout > 32) return GS_ERR_INVALID;
+    const int cinp = cin <= 8 ? 8 : 32, coutp = cout <= 8 ? 8 : 32;
+    if (!dgrad)
+        pack_kernel<<<64, 256, 0, (cudaStream_t)stream>>>(w, cin, cout, cinp, coutp, 0, (__nv_bfloat16*)packed);
+    else
+        pack_kernel<<<64, 256, 0, (cudaStream_t)stream>>>(w, cin, cout, coutp, cinp, 1, (__nv_bfloat16*)packed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_pack_weights");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void* x, const void* packed,
+                     const float* bias, int epi, const void* mask, void* out, int out_ch, void* stream) {
+    if (!shape_ok(D, H, W) || !x || !packed || !out) return GS_ERR_INVALID;
+    if (epi == EPI_MASK_BF16 && !mask) return GS_ERR_INVALID;
+    if ((epi == EPI_BIAS_RELU_BF16 || epi == EPI_BIAS_F32) && !bias) return GS_ERR_INVALID;
+    cudaError_t e = launch_conv(cin_pad, cout_pad, epi, D, H, W, x, packed, bias, mask, out, out_ch,
+                                (cudaStream_t)stream);
+    if (e == cudaErrorInvalidValue) return GS_ERR_INVALID;
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_conv3d");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+size_t sur_wgrad_workspace_bytes(int cin_pad, int cout_pad) {
+    if ((cin_pad != 8 && cin_pad != 32) || (cout_pad != 8 && cout_pad != 32)) return 0;
+    return wgrad_ws_bytes(cin_pad, cout_pad);
+}
+
+gs_status sur_conv3d_wgrad(int D, int H, int W, int cin_pad, int cout_pad, const void* x, const void* dy, int cin,
+                           int cout, float* dw, void* workspace, size_t ws_bytes, void* stream) {
+    if (!shape_ok(D, H, W) || !x || !dy || !dw || !workspace) return GS_ERR_INVALID;
+    if (ws_bytes < sur_wgrad_workspace_bytes(cin_pad, cout_pad) || cin > cin_pad || cout > cout_pad || cin < 1 ||
+        cout < 1)
+        return GS_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = launch_wgrad(cin_pad, cout_pad, D, H, W, x, dy, (float*)workspace, s);
+    if (e == cudaSuccess) {
+        wgrad_reduce_kernel<<<128, 256, 0, s>>>((const float*)workspace, wgrad_grid(), cin_pad, cout_pad, cin, cout,
+                                                dw);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_conv3d_wgrad");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status sur_moments(long n, const float* x, double* sum_sumsq_dev, void* stream) {
+    if (n < 0 || (n > 0 && !x) || !sum_sumsq_dev) return GS_ERR_INVALID;
+    if (n == 0) return GS_OK;
+    moments_kernel<<<nsm_now() * 4, 256, 0, (cudaStream_t)stream>>>(x, n, sum_sumsq_dev);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_moments");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+}  // extern "C"

@@ -115,3 +115,25 @@ GS_DU = 2e-5
 GS_DV = 1e-5
 GS_F = 0.053
 GS_K = 0.014
+
+
+def surrogate_init_params(seed: int = 7, last_layer_scale: float = 0.0) -> np.ndarray:
+    """Initial parameters of the 4-layer conv surrogate (2-32-32-32-2, 3^3
+    taps), flat FP32 vector laid out per layer as W[27][cin][cout], b[cout]:
+    W ~ U(-sqrt(6/fan_in), sqrt(6/fan_in)), fan_in = 27 cin, biases 0; the
+    last layer's weights are scaled by last_layer_scale (0: the initial
+    network predicts no change)."""
+    layers = [(2, 32), (32, 32), (32, 32), (32, 2)]
+    total = sum(27 * a * b + b for a, b in layers)
+    r = uniform01(seed, 5, total)
+    out = np.zeros(total, dtype=np.float64)
+    off = 0
+    for l, (cin, cout) in enumerate(layers):
+        nw = 27 * cin * cout
+        bound = np.sqrt(6.0 / (27 * cin))
+        w = bound * (2.0 * r[off:off + nw] - 1.0)
+        if l == 3:
+            w *= last_layer_scale
+        out[off:off + nw] = w
+        off += nw + cout
+    return out.astype(np.float32)

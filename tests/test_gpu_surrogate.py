@@ -1,0 +1,220 @@
+"""GPU parity of the learned surrogate's BF16 tensor-core kernels against the
+CPU oracle: convolution forward, input gradient and weight gradient on
+BF16-rounded inputs (FP32 accumulation on the GPU, FP64 in the oracle), the
+whole network's loss gradient against oracle backpropagation with the same
+BF16 rounding points, training, and the RK4 judge / fallback."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+from tests._gpu_common import cuda_or_skip, to_np
+
+pytestmark = pytest.mark.gpu
+
+ACC_TOL = 1e-5  # FP32 accumulation of exact BF16 products vs FP64
+
+
+def _pad(c):
+    return 8 if c <= 8 else 32
+
+
+def _rand_bf16(rng, shape, scale=1.0):
+    return oracle.bf16_round(scale * rng.standard_normal(shape))
+
+
+def _dev_act(torch, a, cpad):
+    """(D,H,W,c) float64 -> (D,H,W,cpad) BF16 on the GPU (zero padding)."""
+    D, H, W, c = a.shape
+    full = np.zeros((D, H, W, cpad), dtype=np.float32)
+    full[..., :c] = a
+    return torch.from_numpy(full).to("cuda", torch.bfloat16).contiguous()
+
+
+def _packed(torch, gs, w, dgrad):
+    cin, cout = w.shape[1], w.shape[2]
+    nb = gs.lib().sur_packed_bytes(_pad(cout), _pad(cin)) if dgrad else gs.lib().sur_packed_bytes(_pad(cin), _pad(cout))
+    buf = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    wd = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float32)).cuda()
+    assert gs.lib().sur_pack_weights(cin, cout, wd.data_ptr(), dgrad, buf.data_ptr(), None) == 0
+    return buf, wd
+
+
+def _rel(a, b):
+    return float(np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2)))
+
+
+SHAPES = [(2, 32), (32, 32), (32, 2)]
+GRIDS = [(2, 8, 16), (4, 16, 32)]
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("cin,cout", SHAPES)
+def test_conv_forward(grid, cin, cout):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = grid
+    rng = np.random.default_rng(cin * 100 + cout + D)
+    x = _rand_bf16(rng, (D, H, W, cin))
+    w = _rand_bf16(rng, (27, cin, cout), 0.2)
+    b = rng.standard_normal(cout).astype(np.float32).astype(np.float64)
+    xd = _dev_act(torch, x, _pad(cin))
+    wp, _ = _packed(torch, gs, w, 0)
+    bd = torch.zeros(_pad(cout), dtype=torch.float32, device="cuda")
+    bd[:cout] = torch.from_numpy(b.astype(np.float32))
+    out = torch.zeros((D, H, W, _pad(cout)), dtype=torch.float32, device="cuda")
+    st = gs.lib().sur_conv3d(D, H, W, _pad(cin), _pad(cout), xd.data_ptr(), wp.data_ptr(), bd.data_ptr(), 3, None,
+                             out.data_ptr(), _pad(cout), None)
+    assert st == 0
+    torch.cuda.synchronize()
+    ref = oracle.conv3d_fwd(x, w, b)
+    got = to_np(out)
+    assert _rel(got[..., :cout], ref) < ACC_TOL
+    assert np.all(got[..., cout:] == 0.0)
+
+
+@pytest.mark.parametrize("cin,cout", [(32, 32), (32, 2)])
+def test_conv_input_gradient(cin, cout):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = 4, 8, 16
+    rng = np.random.default_rng(11 + cout)
+    dy = _rand_bf16(rng, (D, H, W, cout))
+    w = _rand_bf16(rng, (27, cin, cout), 0.2)
+    dyd = _dev_act(torch, dy, _pad(cout))
+    wp, _ = _packed(torch, gs, w, 1)
+    out = torch.zeros((D, H, W, _pad(cin)), dtype=torch.float32, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, _pad(cout), _pad(cin), dyd.data_ptr(), wp.data_ptr(), None, 3, None,
+                               out.data_ptr(), _pad(cin), None) == 0
+    torch.cuda.synchronize()
+    ref = oracle.conv3d_dgrad(dy, w)
+    assert _rel(to_np(out)[..., :cin], ref) < ACC_TOL
+    # the masked BF16 form used in training: gradient times (mask > 0)
+    mask = _rand_bf16(rng, (D, H, W, cin))
+    md = _dev_act(torch, mask, _pad(cin))
+    outb = torch.zeros((D, H, W, _pad(cin)), dtype=torch.bfloat16, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, _pad(cout), _pad(cin), dyd.data_ptr(), wp.data_ptr(), None, 2, md.data_ptr(),
+                               outb.data_ptr(), _pad(cin), None) == 0
+    torch.cuda.synchronize()
+    refm = ref * (mask > 0)
+    gotm = to_np(outb)[..., :cin]
+    assert np.all(np.abs(gotm - refm) <= 2.0 ** -8 * np.abs(refm) + 1e-30)
+
+
+@pytest.mark.parametrize("grid", GRIDS)
+@pytest.mark.parametrize("cin,cout", SHAPES)
+def test_conv_weight_gradient(grid, cin, cout):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = grid
+    rng = np.random.default_rng(23 + cin + cout + D)
+    x = _rand_bf16(rng, (D, H, W, cin))
+    dy = _rand_bf16(rng, (D, H, W, cout))
+    xd, dyd = _dev_act(torch, x, _pad(cin)), _dev_act(torch, dy, _pad(cout))
+    nb = gs.lib().sur_wgrad_workspace_bytes(_pad(cin), _pad(cout))
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    dw = torch.zeros((27, cin, cout), dtype=torch.float32, device="cuda")
+    assert gs.lib().sur_conv3d_wgrad(D, H, W, _pad(cin), _pad(cout), xd.data_ptr(), dyd.data_ptr(), cin, cout,
+                                     dw.data_ptr(), ws.data_ptr(), nb, None) == 0
+    torch.cuda.synchronize()
+    ref, _ = oracle.conv3d_wgrad(x, dy)
+    assert _rel(to_np(dw), ref) < ACC_TOL
+
+
+def _state(shape, seed):
+    D, H, W = shape
+    u, v = si.gs_initial_state(W, H, D, seed=seed)
+    return u, v
+
+
+def _norm():
+    return (0.95, 0.02), (0.1, 0.07), (0.003, 0.006)
+
+
+def test_network_gradient_matches_oracle_backprop():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = 4, 8, 16
+    params = si.surrogate_init_params(seed=3, last_layer_scale=0.5)
+    u, v = _state((D, H, W), 5)
+    rng = np.random.default_rng(2)
+    ut = u + 0.003 * rng.standard_normal(u.shape)
+    vt = v + 0.006 * rng.standard_normal(v.shape)
+    u, v, ut, vt = (a.astype(np.float32).astype(np.float64) for a in (u, v, ut, vt))
+    mean, sd, scale = _norm()
+    s = gs.Surrogate(W, H, D)
+    s.set_params(params)
+    s.set_normalization(mean, sd, scale)
+    dev = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (u, v, ut, vt)]
+    loss = s.train_step(*dev, 1e-9)
+    g = s.get_grad()
+    ref_loss, ref_g = oracle.surrogate_loss_grad(params.astype(np.float64), u, v, ut, vt, mean, sd, scale)
+    assert abs(loss - ref_loss) < 1e-4 * ref_loss
+    assert _rel(g.astype(np.float64), ref_g) < 2e-3
+    # forward prediction
+    uo, vo = torch.empty_like(dev[0]), torch.empty_like(dev[1])
+    s.set_params(params)
+    s.forward(dev[0], dev[1], uo, vo)
+    pu, pv = oracle.surrogate_forward(params.astype(np.float64), u, v, mean, sd, scale)
+    assert _rel(np.concatenate([to_np(uo).ravel() - u.ravel(), to_np(vo).ravel() - v.ravel()]),
+                np.concatenate([(pu - u).ravel(), (pv - v).ravel()])) < 1e-3
+    s.close()
+
+
+def test_training_reduces_loss():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = 16, 16, 32
+    # snapshots 16 RK4 steps apart from our own integrator
+    g = gs.GrayScott(W, H, D, prec=gs.GS_FP32, Du=2e-4, Dv=1e-4)
+    u0, v0 = si.gs_initial_state(W, H, D, seed=9)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    snaps = [(g.u.clone(), g.v.clone())]
+    for _ in range(6):
+        g.step(gs.GS_RK4, 0.0, 0.1, 16)
+        snaps.append((g.u.clone(), g.v.clone()))
+    g.close()
+    s = gs.Surrogate(W, H, D)
+    s.set_params(si.surrogate_init_params(seed=4, last_layer_scale=0.0))
+    s.set_normalization(*_norm())
+    losses = []
+    for it in range(60):
+        k = it % 6
+        losses.append(s.train_step(snaps[k][0], snaps[k][1], snaps[k + 1][0], snaps[k + 1][1], 2e-3))
+    assert np.mean(losses[-6:]) < 0.5 * np.mean(losses[:6]), (losses[:6], losses[-6:])
+    s.close()
+
+
+def test_judge_and_fallback():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    D, H, W = 8, 16, 32
+    u0, v0 = si.gs_initial_state(W, H, D, seed=1)
+    g = gs.GrayScott(W, H, D, prec=gs.GS_FP32)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    s = gs.Surrogate(W, H, D)
+    s.set_params(si.surrogate_init_params(seed=4, last_layer_scale=0.0))  # predicts "no change"
+    s.set_normalization(*_norm())
+    # the judge integrates 16 RK4 steps and measures the prediction against it
+    ref = gs.GrayScott(W, H, D, prec=gs.GS_FP32)
+    ref.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    ref.step(gs.GS_RK4, 0.0, 0.1, 16)
+    rel, fb = s.advance(g.ctx, g.u, g.v, judge=True, threshold=1e-3)
+    expect = float(np.sqrt(np.sum((u0.astype(np.float32) - to_np(ref.u)) ** 2 + (v0.astype(np.float32) - to_np(ref.v)) ** 2)
+                           / np.sum(to_np(ref.u) ** 2 + to_np(ref.v) ** 2)))
+    assert abs(rel - expect) < 1e-6 and rel > 1e-3 and fb
+    assert np.array_equal(to_np(g.u), to_np(ref.u))  # the integrator's result is kept
+    # while the judgement stands, unjudged calls run the integrator
+    rel2, fb2 = s.advance(g.ctx, g.u, g.v, judge=False)
+    ref.step(gs.GS_RK4, 0.0, 0.1, 16)
+    assert fb2 and np.array_equal(to_np(g.u), to_np(ref.u))
+    # a generous threshold accepts the surrogate; unjudged calls then use it
+    rel3, fb3 = s.advance(g.ctx, g.u, g.v, judge=True, threshold=1.0)
+    assert not fb3
+    before = g.u.clone()
+    s.advance(g.ctx, g.u, g.v, judge=False)
+    assert torch.equal(g.u, before)  # "no change" network
+    for x in (s, g, ref):
+        x.close()

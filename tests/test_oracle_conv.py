@@ -72,3 +72,42 @@ def test_gradients_by_central_differences():
         bm[o] -= h
         fd = (loss(x, w, bp) - loss(x, w, bm)) / (2 * h)
         assert abs(fd - db[o]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_bf16_round_known_values():
+    # 1 + 2^-8 is a tie between 1 and 1 + 2^-7: ties go to the even mantissa
+    assert oracle.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert oracle.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+    assert oracle.bf16_round(np.array([-2.5]))[0] == -2.5
+    x = np.random.default_rng(0).standard_normal(1000)
+    y = oracle.bf16_round(x)
+    assert np.all(np.abs(y - x) <= np.abs(x) * 2.0 ** -8)
+    assert np.array_equal(oracle.bf16_round(y), y)
+
+
+def test_surrogate_gradient_by_central_differences():
+    import synthetic_inputs as si
+    D, H, W = 3, 4, 3
+    rng = np.random.default_rng(1)
+    params = si.surrogate_init_params(seed=3, last_layer_scale=0.5).astype(np.float64)
+    u = 1.0 + 0.1 * rng.standard_normal((D, H, W))
+    v = 0.1 * rng.standard_normal((D, H, W))
+    ut = u + 0.01 * rng.standard_normal((D, H, W))
+    vt = v + 0.01 * rng.standard_normal((D, H, W))
+    norm = ((1.0, 0.0), (0.1, 0.1), (0.01, 0.01))
+    loss, g = oracle.surrogate_loss_grad(params, u, v, ut, vt, *norm, emulate_bf16=False)
+    assert g.size == oracle.surrogate_param_count() == params.size
+    h = 1e-6
+    idx = rng.choice(params.size, 16, replace=False)
+    for i in idx:
+        pp, pm = params.copy(), params.copy()
+        pp[i] += h
+        pm[i] -= h
+        lp = oracle.surrogate_loss_grad(pp, u, v, ut, vt, *norm, emulate_bf16=False)[0]
+        lm = oracle.surrogate_loss_grad(pm, u, v, ut, vt, *norm, emulate_bf16=False)[0]
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+    # the forward pass agrees with the loss definition
+    pu, pv = oracle.surrogate_forward(params, u, v, *norm, emulate_bf16=False)
+    ref = np.mean(np.concatenate([(((pu - u) - (ut - u)) / 0.01).ravel(), (((pv - v) - (vt - v)) / 0.01).ravel()]) ** 2)
+    assert abs(ref - loss) < 1e-12 * max(1.0, loss)
