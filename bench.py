@@ -227,6 +227,8 @@ def extra_workloads(torch, gs, si):
         out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {"ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3)}
     out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
     out.update(batched_workload(torch, gs, si))
+    from paper_2309_05331_b300 import surrogate_workload
+    out["surrogate_128cubed"] = surrogate_workload.run(torch, n=128, trajectories=8, per_traj=250, iters=3000)
     return out
 
 
@@ -450,6 +452,9 @@ def main():
     if rank == 0:
         if ws == 1 and not args.no_extras:
             line["workloads"] = extra_workloads(torch, gs, si)
+            sw = line["workloads"]["surrogate_128cubed"]
+            line["surrogate_speedup_at_matched_l2"] = sw.get("surrogate_speedup_at_matched_error")
+            line["surrogate_heldout_rel_l2"] = sw["heldout_rel_l2_mean"]
         if ws == 1 and not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline_sample()
         print(json.dumps(line))
