@@ -118,6 +118,20 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max_sum(time_ms, work, device="cpu"):
+    """(max over ranks of time_ms, sum over ranks of work); identity when no
+    process group of more than one rank is initialised."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(time_ms), float(work)
+    t = torch.tensor([float(time_ms)], dtype=torch.float64, device=device)
+    w = torch.tensor([float(work)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w)
+    return float(t.item()), float(w.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -362,15 +376,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    acc_all = acc
-    if ws > 1:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(tt.item())
-        ta = torch.tensor([acc], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(ta)
-        acc_all = int(ta.item())
+    ms_max, acc_all = reduce_max_sum(ms, acc, "cuda")
+    acc_all = int(acc_all)
     cells = N ** 3
     value = cells * acc_all / (ms_max * 1e-3)
 
@@ -397,13 +404,7 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e = e0.elapsed_time(e1)
-    if ws > 1:
-        tt = torch.tensor([ms_e, acc_e], device="cuda", dtype=torch.float64)
-        tmax = tt.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(tt)
-        ms_e, acc_e = float(tmax[0].item()), int(tt[1].item())
+    ms_e, acc_e = reduce_max_sum(e0.elapsed_time(e1), acc_e, "cuda")
     e2e_value = cells * acc_e / (ms_e * 1e-3)
 
     # roofline of the dominant kernel: each kernel of one attempt timed alone

@@ -200,3 +200,19 @@ def run(torch, n=128, trajectories=8, per_traj=250, iters=2000, threshold=1e-3, 
     del data
     torch.cuda.empty_cache()
     return res
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+
+    import torch
+
+    ap = argparse.ArgumentParser(description="surrogate workload (data, training, evaluation, timing)")
+    ap.add_argument("--grid", type=int, default=128)
+    ap.add_argument("--trajectories", type=int, default=8)
+    ap.add_argument("--per-traj", type=int, default=250)
+    ap.add_argument("--iters", type=int, default=3000)
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    print(json.dumps(run(torch, a.grid, a.trajectories, a.per_traj, a.iters), indent=1))
