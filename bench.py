@@ -50,15 +50,18 @@ STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
 BYTES_PER_FIELD_CELL = 8
 ATTEMPT_FIELDS = sum(STAGE_FIELDS[1:])  # 33 field passes per attempt (k1 is reused)
 
-# DRAM traffic of the dominant kernel from one ncu capture at 192^3
-# (profiles/gs_stage7_fp32_192cubed_full.md: 452.2 MB per launch), scaled by
-# cells to 256^3; valid only while the kernel source is unchanged.
-NCU_TRAFFIC = {"kernel": "stage7", "source_sha": "6b1468d0ccd07ee2", "bytes_per_launch": 452179456 * (256 / 192) ** 3}
+# DRAM traffic of the dominant kernel from one ncu capture of the standalone
+# stage-7 launch at 256^3 (profiles/gs_stage7_wide_fp32_256cubed_full.md:
+# 824.2 MB read + 247.9 MB written), per cell so that other grids scale by
+# cells; valid only for that kernel form while the stage-kernel sources are
+# unchanged.
+NCU_TRAFFIC = {"kernel": "stage7", "form": 2, "source_sha": "8d78d3f185837cc6", "bytes_per_cell": (824249856 + 247850496) / 256 ** 3}
+KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_grid.cu")
 
 
 def _kernel_source_sha():
     h = hashlib.sha256()
-    for f in ("gs_tile.cuh", "common.cuh"):
+    for f in KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2309_05331_b300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -421,8 +424,9 @@ def main():
     attempt_ms = sum(stage_ms[1:])
     attempt_gbs = ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
     traffic = None
-    if NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]:
-        traffic = NCU_TRAFFIC["bytes_per_launch"]
+    if (NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]
+            and NCU_TRAFFIC["form"] == stage_cfg[dom][0]):
+        traffic = NCU_TRAFFIC["bytes_per_cell"] * cells
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
