@@ -56,7 +56,8 @@ ATTEMPT_FIELDS = sum(STAGE_FIELDS[1:])  # 33 field passes per attempt (k1 is reu
 # cells; valid only for that kernel form while the stage-kernel sources are
 # unchanged.
 NCU_TRAFFIC = {"kernel": "stage7", "form": 2, "source_sha": "8d78d3f185837cc6", "bytes_per_cell": (824249856 + 247850496) / 256 ** 3}
-KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_grid.cu")
+KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_grid.cu")
+FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
 
 def _kernel_source_sha():
@@ -430,7 +431,7 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
-                "kernel": f"{STAGE_NAMES[dom]} kernel, {['', 'generic', 'vec16B', 'vec8B'][stage_cfg[dom][0]]} form (FP32)",
+                "kernel": f"{STAGE_NAMES[dom]} kernel, {FORM_NAMES[stage_cfg[dom][0]]} form (FP32)",
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
                 "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
                 "attempt": {"algorithmic_bytes_per_cell": ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL,
@@ -444,10 +445,12 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "accepted_per_step": ACC_PER_STEP,
                            "tolerance": TOL, "tile_ty_zc": [tile[0], tile[1]],
-                           "stencil_kernel": "vectorised" if variant == 2 else "generic",
-                           "dopri5_kernel_configs": {nm: {"form": ["", "generic", "vec16B", "vec8B"][f], "ty": t,
-                                                          "zc": z} for nm, (f, t, z) in
-                                                     zip(STAGE_NAMES, gs.gs_get_stage_configs(g.ctx))},
+                           "stencil_kernel": {1: "generic", 2: "vectorised", 4: "staged"}.get(variant, str(variant)),
+                           "dopri5_kernel_configs": {nm: {"form": FORM_NAMES[f], "ty": t, "zc": z,
+                                                          **({"depth": d} if f == 4 else {})}
+                                                     for nm, (f, t, z), d in
+                                                     zip(STAGE_NAMES, gs.gs_get_stage_configs(g.ctx),
+                                                         gs.gs_get_stage_depths(g.ctx))},
                            "l2": "inputs larger than L2 (u, v + 8 stage fields = 1.3 GB per GPU); no flush",
                            "parallelism": f"replicas x{ws} (independent problems, no collective)"},
                 "accepted_steps": acc_all, "rejected_attempts_rank0": rej,

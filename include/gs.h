@@ -154,11 +154,14 @@ gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc);
  * per kernel), 1 = generic (one cell per thread, 30-cell rows), 2 =
  * vectorised (16-byte accesses: 4 FP32 or 2 FP64 cells per thread, 128- or
  * 64-cell rows per warp; the autotuner may still pick 8-byte rows), 3 =
- * vectorised 8-byte (FP32 only: 2 cells per thread, 64-cell rows).  INVALID
- * if the form does not apply (nx not a multiple of the vector width).  All
+ * vectorised 8-byte (FP32 only: 2 cells per thread, 64-cell rows), 4 =
+ * staged (the 16-byte rows of form 2, with every thread copying its inputs
+ * into a shared-memory ring 1 to 3 planes ahead with cp.async).  INVALID if
+ * the form does not apply (nx not a multiple of the vector width).  All
  * forms compute the same formulas. */
 gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant);
-/* The stencil kernel form the next call will use: 1 generic, 2 vectorised. */
+/* The stencil kernel form the next call will use: 1 generic, 2 vectorised,
+ * 4 staged. */
 gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use);
 
 /* Project autotuner: for each kernel of a Dormand-Prince attempt (k1 and
@@ -173,8 +176,16 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
 
 /* Configuration in use for each Dormand-Prince kernel (index 0: k1, 1..6:
  * stages 2..7): form (1 generic, 2 vectorised 16-byte rows, 3 vectorised
- * 8-byte rows), ty, zc.  Each argument: host array of 7 ints. */
+ * 8-byte rows, 4 staged 16-byte rows), ty, zc.  Each argument: host array of 7 ints. */
 gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc);
+
+/* Ring depth of the staged form (form 4): how many planes ahead each thread
+ * copies its inputs, 1..3.  Sets the depth of every kernel (the autotuner
+ * picks its own per kernel); a depth whose ring does not fit in shared
+ * memory is reduced at launch.  gs_get_stage_depths: the depth each
+ * Dormand-Prince kernel uses when it runs in form 4 (host array of 7 ints). */
+gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);
+gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);
 
 /* Measurement aid: launches the kernels of one Dormand-Prince attempt of
  * the bound state one at a time between CUDA events on the context stream

@@ -62,6 +62,8 @@ _SIGNATURES = {
     "gs_set_kernel_variant": ([_vp, C.c_int], C.c_int),
     "gs_get_kernel_variant": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "gs_set_stage_depth": ([_vp, C.c_int], C.c_int),
+    "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gs_time_stages": ([_vp, C.c_int, _dp], C.c_int),
@@ -230,6 +232,17 @@ def gs_get_stage_configs(ctx):
     f, t, z = (C.c_int * 7)(), (C.c_int * 7)(), (C.c_int * 7)()
     _check(lib().gs_get_stage_configs(ctx, f, t, z), ctx)
     return [(f[i], t[i], z[i]) for i in range(7)]
+
+
+def gs_set_stage_depth(ctx, depth):
+    _check(lib().gs_set_stage_depth(ctx, depth), ctx)
+
+
+def gs_get_stage_depths(ctx):
+    """Ring depth of the staged form for k1 and stages 2..7."""
+    d = (C.c_int * 7)()
+    _check(lib().gs_get_stage_depths(ctx, d), ctx)
+    return list(d)
 
 
 def gs_get_tile(ctx):

@@ -77,8 +77,9 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
         const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, c->parity, 0, in.off);
         const StageCoef<T, NK> C = stage_coef<T, NK>(A, c->dt_try, c->atol, c->rtol);
         const int ntx = (in.nx + 31) / 32;
-        T emax = T(0);
-        wide_segment<T, NK, MODE, 1>(g, P, C, S, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1, emax);
+        typename ErrBits<T>::U ebits = 0;
+        wide_segment<T, NK, MODE, 1>(g, P, C, S, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1, ebits);
+        const T emax = ErrBits<T>::value(ebits);
         if (MODE == MODE_DOPRI_FINAL) {
             const T bmax = block_nanmax(emax, red);
             if (tid == 0) atomic_max_nonneg(&ctrls[sg.inst].err_bits, (double)bmax);

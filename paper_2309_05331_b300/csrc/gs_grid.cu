@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_staged.cuh"
 #include "gs_wide.cuh"
 #include "host_util.h"
 
@@ -35,11 +36,14 @@ constexpr int kFields = 8;  // 0: second state buffer; 1..7: stage fields
 
 // Launch configuration of one stencil kernel.  form: 0 automatic, 1 generic
 // (one cell per thread), 2 vectorised 16-byte rows (4 FP32 / 2 FP64 cells per
-// thread), 3 vectorised 8-byte rows (2 FP32 cells per thread).
+// thread), 3 vectorised 8-byte rows (2 FP32 cells per thread), 4 staged
+// 16-byte rows (form 2 with the inputs copied into shared memory `depth`
+// planes ahead).
 struct KCfg {
     int form;
     int ty;
     int zc;
+    int depth = 2;  // form 4 only: 1..kMaxDepth
 };
 
 }  // namespace
@@ -106,6 +110,7 @@ static bool form_ok(const gs_ctx* ctx, int form) {
     if (form == 1) return true;
     if (form == 2) return ctx->p.nx % (ctx->p.prec == GS_FP64 ? 2 : 4) == 0;
     if (form == 3) return ctx->p.prec == GS_FP32 && ctx->p.nx % 2 == 0;
+    if (form == 4) return ctx->p.nx % (ctx->p.prec == GS_FP64 ? 2 : 4) == 0;
     return false;
 }
 static bool wide_ok(const gs_ctx* ctx) { return form_ok(ctx, 2) || form_ok(ctx, 3); }
@@ -113,6 +118,7 @@ static bool wide_ok(const gs_ctx* ctx) { return form_ok(ctx, 2) || form_ok(ctx, 
 static int pick_form(const gs_ctx* ctx, int form) {
     if (ctx->variant == 1) return 1;
     if (ctx->variant == 3) return 3;
+    if (ctx->variant == 4) return form_ok(ctx, 4) ? 4 : 1;
     if (form == 0) form = form_ok(ctx, 2) ? 2 : (form_ok(ctx, 3) ? 3 : 1);
     if (ctx->variant == 2 && form == 1) form = form_ok(ctx, 2) ? 2 : 3;
     if (!form_ok(ctx, form)) form = 1;
@@ -159,6 +165,29 @@ static cudaError_t launch_wide(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     return cudaGetLastError();
 }
 
+template <typename T, int NK, int MODE, int VX>
+static cudaError_t launch_staged(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
+    const Geom<T> g = make_geom<T>(ctx->p);
+    auto kern = gs_stage_staged_kernel<T, NK, MODE, VX>;
+    const int txw = 32 * VX;
+    A.ntx = (ctx->p.nx + txw - 1) / txw;
+    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
+    depth = std::max(1, std::min(depth, kMaxDepth));
+    size_t smem = staged_smem_bytes<T, NK, VX>(A.ty, depth);
+    // a deeper ring than shared memory holds is cut back
+    while (depth > 1 && smem > kMaxSmemPerCta) smem = staged_smem_bytes<T, NK, VX>(A.ty, --depth);
+    if (smem > kMaxSmemPerCta) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int grid = plan_schedule(ctx, A, occ);
+    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A, depth);
+    return cudaGetLastError();
+}
+
 template <typename T, int NK, int MODE>
 static cudaError_t launch_generic(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
     const Geom<T> g = make_geom<T>(ctx->p);
@@ -178,9 +207,10 @@ static cudaError_t launch_generic(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
 }
 
 template <typename T, int NK, int MODE>
-static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A, int form) {
-    if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
+static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A, int form, int depth) {
     form = pick_form(ctx, form);
+    if (form == 4) return launch_staged<T, NK, MODE, 16 / sizeof(T)>(ctx, s, A, depth);
+    if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
     if (form == 1) return launch_generic<T, NK, MODE>(ctx, s, A);
     if constexpr (sizeof(T) == 4) {
         if (form == 2) return launch_wide<T, NK, MODE, 4>(ctx, s, A);
@@ -191,32 +221,32 @@ static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A, int 
 }
 
 template <int NK, int MODE>
-static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A, int form) {
-    if (ctx->p.prec == GS_FP64) return launch_stage_t<double, NK, MODE>(ctx, s, A, form);
-    return launch_stage_t<float, NK, MODE>(ctx, s, A, form);
+static cudaError_t launch_stage_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A, const KCfg& cfg) {
+    if (ctx->p.prec == GS_FP64) return launch_stage_t<double, NK, MODE>(ctx, s, A, cfg.form, cfg.depth);
+    return launch_stage_t<float, NK, MODE>(ctx, s, A, cfg.form, cfg.depth);
 }
 
 // Instantiated (NK, mode) pairs: stages with 0..5 inputs, final combinations
 // with 0 (Euler, Adams-Bashforth) or 1 (RK4) halo inputs, Dormand-Prince
 // stage 7 with 5.
-static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, int form) {
+static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, const KCfg& cfg) {
     if (mode == MODE_STAGE) {
         switch (nk) {
-            case 0: return launch_stage_nk<0, MODE_STAGE>(ctx, s, A, form);
-            case 1: return launch_stage_nk<1, MODE_STAGE>(ctx, s, A, form);
-            case 2: return launch_stage_nk<2, MODE_STAGE>(ctx, s, A, form);
-            case 3: return launch_stage_nk<3, MODE_STAGE>(ctx, s, A, form);
-            case 4: return launch_stage_nk<4, MODE_STAGE>(ctx, s, A, form);
-            case 5: return launch_stage_nk<5, MODE_STAGE>(ctx, s, A, form);
+            case 0: return launch_stage_nk<0, MODE_STAGE>(ctx, s, A, cfg);
+            case 1: return launch_stage_nk<1, MODE_STAGE>(ctx, s, A, cfg);
+            case 2: return launch_stage_nk<2, MODE_STAGE>(ctx, s, A, cfg);
+            case 3: return launch_stage_nk<3, MODE_STAGE>(ctx, s, A, cfg);
+            case 4: return launch_stage_nk<4, MODE_STAGE>(ctx, s, A, cfg);
+            case 5: return launch_stage_nk<5, MODE_STAGE>(ctx, s, A, cfg);
             default: return cudaErrorInvalidValue;
         }
     }
     if (mode == MODE_FINAL) {
-        if (nk == 0) return launch_stage_nk<0, MODE_FINAL>(ctx, s, A, form);
-        if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A, form);
+        if (nk == 0) return launch_stage_nk<0, MODE_FINAL>(ctx, s, A, cfg);
+        if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A, cfg);
         return cudaErrorInvalidValue;
     }
-    if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, form);
+    if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, cfg);
     return cudaErrorInvalidValue;
 }
 
@@ -275,17 +305,17 @@ static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     StageArgs A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.out0 = k1;
-    cudaError_t e = launch_stage(ctx, s, 0, MODE_STAGE, A, ctx->def.form);
+    cudaError_t e = launch_stage(ctx, s, 0, MODE_STAGE, A, ctx->def);
     if (e != cudaSuccess) return e;
     A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.kin[0] = k1;
     A.a[0] = 0.5;
     A.out0 = fld(ctx, 5);
-    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def.form)) != cudaSuccess) return e;
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def)) != cudaSuccess) return e;
     A.kin[0] = fld(ctx, 5);
     A.out0 = fld(ctx, 6);
-    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def.form)) != cudaSuccess) return e;
+    if ((e = launch_stage(ctx, s, 1, MODE_STAGE, A, ctx->def)) != cudaSuccess) return e;
     A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
     A.kin[0] = fld(ctx, 6);
@@ -301,7 +331,7 @@ static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 1, MODE_FINAL, A, ctx->def.form);
+    return launch_stage(ctx, s, 1, MODE_FINAL, A, ctx->def);
 }
 
 static cudaError_t body_euler(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -312,7 +342,7 @@ static cudaError_t body_euler(gs_ctx* ctx, cudaStream_t s, unsigned long long h,
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def.form);
+    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def);
 }
 
 // Adams-Bashforth 4 step m >= 3: f_m = F(u_m) into the ring,
@@ -334,7 +364,7 @@ static cudaError_t body_ab4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, i
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def.form);
+    return launch_stage(ctx, s, 0, MODE_FINAL, A, ctx->def);
 }
 
 // Dormand-Prince stage st (2..7) with k1 in the parity pair (fields 1, 2)
@@ -361,7 +391,7 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
             A.a[j] = rows[st - 2][j];
         }
         A.out0 = k[st];
-        return launch_stage(ctx, s, nk, MODE_STAGE, A, cfg.form);
+        return launch_stage(ctx, s, nk, MODE_STAGE, A, cfg);
     }
     A.kin[0] = k[1];
     A.kin[1] = k[3];
@@ -379,7 +409,7 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A, cfg.form);
+    return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A, cfg);
 }
 
 static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -396,7 +426,7 @@ static cudaError_t launch_dopri5_k1(gs_ctx* ctx, cudaStream_t s) {
     StageArgs A = base_args(ctx, cfg);
     A.u = state_sel(ctx, SEL_CUR);
     A.out0 = pair_sel(ctx, 1, 2, SEL_CUR);
-    return launch_stage(ctx, s, 0, MODE_STAGE, A, cfg.form);
+    return launch_stage(ctx, s, 0, MODE_STAGE, A, cfg);
 }
 
 static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -615,7 +645,7 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, 
     A.ctrl = nullptr;
     A.u = slot_fixed(const_cast<void*>(u), const_cast<void*>(v));
     A.out0 = slot_fixed(fu, fv);
-    CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A, ctx->def.form));
+    CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A, ctx->def));
     return GS_OK;
 }
 
@@ -747,9 +777,10 @@ gs_status gs_get_tile(const gs_ctx* ctx, int* ty, int* zc) {
 }
 
 gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant) {
-    if (!ctx || variant < 0 || variant > 3) return GS_ERR_INVALID;
+    if (!ctx || variant < 0 || variant > 4) return GS_ERR_INVALID;
     if (variant == 2 && !wide_ok(ctx)) return GS_ERR_INVALID;
     if (variant == 3 && !form_ok(ctx, 3)) return GS_ERR_INVALID;
+    if (variant == 4 && !form_ok(ctx, 4)) return GS_ERR_INVALID;
     drop_graphs(ctx);
     ctx->variant = variant;
     return GS_OK;
@@ -757,7 +788,22 @@ gs_status gs_set_kernel_variant(gs_ctx* ctx, int variant) {
 
 gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use) {
     if (!ctx || !in_use) return GS_ERR_INVALID;
-    *in_use = pick_form(ctx, ctx->def.form) == 1 ? 1 : 2;
+    const int f = pick_form(ctx, ctx->def.form);
+    *in_use = f == 1 ? 1 : (f == 4 ? 4 : 2);
+    return GS_OK;
+}
+
+gs_status gs_set_stage_depth(gs_ctx* ctx, int depth) {
+    if (!ctx || depth < 1 || depth > kMaxDepth) return GS_ERR_INVALID;
+    drop_graphs(ctx);
+    ctx->def.depth = depth;
+    for (int k = 0; k < 7; ++k) ctx->dp[k].depth = depth;
+    return GS_OK;
+}
+
+gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth) {
+    if (!ctx || !depth) return GS_ERR_INVALID;
+    for (int k = 0; k < 7; ++k) depth[k] = dp_cfg(ctx, k).depth;
     return GS_OK;
 }
 
@@ -766,7 +812,7 @@ gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc) {
     for (int k = 0; k < 7; ++k) {
         const KCfg& c = dp_cfg(ctx, k);
         form[k] = pick_form(ctx, c.form);
-        ty[k] = (k == 6 && c.ty > kMaxTYFinal) ? kMaxTYFinal : c.ty;
+        ty[k] = (k == 6 && form[k] != 4 && c.ty > kMaxTYFinal) ? kMaxTYFinal : c.ty;
         zc[k] = c.zc;
     }
     return GS_OK;
@@ -800,12 +846,16 @@ static gs_status time_dp_kernel(gs_ctx* ctx, int k, int reps, cudaEvent_t e0, cu
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
     static const int cand[][2] = {{2, 0}, {4, 0}, {6, 0}, {8, 0}, {14, 0}, {4, 4}, {6, 4}, {8, 4}, {6, 16}, {8, 16}};
-    int forms[3], nf = 0;
-    for (int f = 1; f <= 3; ++f) {
+    // the staged form: tile height x ring depth, column-split schedule
+    static const int cand_staged[][2] = {{2, 1}, {2, 2}, {2, 3}, {4, 1}, {4, 2}, {4, 3}, {6, 1}, {6, 2},
+                                         {8, 1}, {8, 2}, {12, 1}, {12, 2}, {14, 1}, {14, 2}};
+    int forms[4], nf = 0;
+    for (int f = 1; f <= 4; ++f) {
         if (!form_ok(ctx, f)) continue;
         if (ctx->variant == 1 && f != 1) continue;
         if (ctx->variant == 2 && f == 1) continue;
         if (ctx->variant == 3 && f != 3) continue;
+        if (ctx->variant == 4 && f != 4) continue;
         forms[nf++] = f;
     }
     cudaEvent_t e0, e1;
@@ -828,16 +878,27 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         for (int i = 0; i < 7; ++i)
             if (!ctx->dp_tuned) ctx->dp[i] = ctx->def;
         ctx->dp_tuned = true;
+        auto try_cfg = [&](const KCfg& c) {
+            ctx->dp[k] = c;
+            float ms = 0.f;
+            if ((st = time_dp_kernel(ctx, k, 3, e0, e1, &ms)) != GS_OK) return;
+            if (ms < best) {
+                best = ms;
+                best_cfg[k] = c;
+            }
+        };
         for (int fi = 0; fi < nf && st == GS_OK; ++fi) {
-            for (const auto& c : cand) {
-                if (k == 6 && c[0] > kMaxTYFinal) continue;
-                ctx->dp[k] = KCfg{forms[fi], c[0], c[1]};
-                float ms = 0.f;
-                if ((st = time_dp_kernel(ctx, k, 3, e0, e1, &ms)) != GS_OK) break;
-                if (ms < best) {
-                    best = ms;
-                    best_cfg[k] = ctx->dp[k];
+            if (forms[fi] == 4) {
+                for (const auto& c : cand_staged) {
+                    if (st != GS_OK) break;
+                    try_cfg(KCfg{4, c[0], 0, c[1]});
                 }
+                continue;
+            }
+            for (const auto& c : cand) {
+                if (st != GS_OK) break;
+                if (k == 6 && c[0] > kMaxTYFinal) continue;
+                try_cfg(KCfg{forms[fi], c[0], c[1]});
             }
         }
         ctx->dp[k] = saved;

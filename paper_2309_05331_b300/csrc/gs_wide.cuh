@@ -72,14 +72,30 @@ __device__ __forceinline__ void lds_v(const T* p, T* out) {
     for (int v = 0; v < VX; ++v) out[v] = qs[v];
 }
 
+// Running maximum of the scaled errors as the integer maximum of their bit
+// patterns (one instruction per cell).  The ratios are products of two
+// non-negative numbers, so they are +0, positive or NaN; for IEEE values
+// >= +0 the bit order is the value order, and every NaN pattern (exponent all
+// ones, non-zero mantissa, either sign) sorts above +inf, so one NaN ratio
+// makes the maximum NaN, as the controller requires.
 template <typename T>
-__device__ __forceinline__ T fast_ratio(T a, T b) {
-    return a / b;
-}
+struct ErrBits;
 template <>
-__device__ __forceinline__ float fast_ratio<float>(float a, float b) {
-    return __fdividef(a, b);  // error ratio: a few ulp are irrelevant to the controller
-}
+struct ErrBits<float> {
+    using U = unsigned;
+    static __device__ __forceinline__ U bits(float x) { return __float_as_uint(x); }
+    static __device__ __forceinline__ float value(U b) { return __uint_as_float(b); }
+    // error scale: a few ulp are irrelevant to the controller
+    static __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+};
+template <>
+struct ErrBits<double> {
+    using U = unsigned long long;
+    static __device__ __forceinline__ U bits(double x) { return (U)__double_as_longlong(x); }
+    static __device__ __forceinline__ double value(U b) { return __longlong_as_double((long long)b); }
+    static __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+};
+
 
 // row of 32*VX cells + 2 halo columns, padded to a whole vector
 template <int VX>
@@ -162,7 +178,8 @@ __device__ __forceinline__ StageCoef<T, NK> stage_coef(const StageArgs& A, doubl
 // (DOPRI_FINAL) with the scaled errors of this thread's cells.
 template <typename T, int NK, int MODE, int VX>
 __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const StageCoef<T, NK>& C,
-                                             T* S, int TY, int tx, int tyi, int z0, int z1, T& emax) {
+                                             T* S, int TY, int tx, int tyi, int z0, int z1,
+                                             typename ErrBits<T>::U& ebits) {
     constexpr int TXW = 32 * VX;
     constexpr int PITCH = wide_pitch<VX>();
     const int lane = threadIdx.x;
@@ -174,6 +191,7 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
     // Dormand-Prince error weights of k3..k6 (kin = {k1, k3, k4, k5, k6})
     const T ew[4] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5, (T)dp5::E6};
     const T e7 = (T)dp5::E7;
+    const T dte7 = dt * e7;
 
     auto sidx = [&](int buf, int ww, int c, int col) -> int { return ((buf * TYP + ww) * 2 + c) * PITCH + col; };
 
@@ -211,8 +229,9 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s[v];
                 if (MODE == MODE_FINAL) cr.a[c][v] = uu[v];
                 if (MODE == MODE_DOPRI_FINAL) {
-                    cr.a[c][v] = C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v]));  // error scale
-                    cr.b[0][c][v] = q[v] - e7 * k1[v];                            // folded error terms
+                    // 1 / (atol + rtol (|u| + dt |k1|)) and dt (sum_{j<7} e_j (k_j - k1) - e7 k1)
+                    cr.a[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v])));
+                    cr.b[0][c][v] = dt * (q[v] - e7 * k1[v]);
                 }
             }
         }
@@ -336,8 +355,8 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
                     if (NK == 5) {
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            const T err = dt * (cur.b[0][c][v] + e7 * f[c][v]);
-                            emax = nanmax(emax, fast_ratio<T>(fabs(err), cur.a[c][v]));
+                            const T err = cur.b[0][c][v] + dte7 * f[c][v];  // + dt e7 k7
+                            ebits = max(ebits, ErrBits<T>::bits(fabs(err) * cur.a[c][v]));
                         }
                     }
                 }
@@ -383,6 +402,32 @@ __device__ __forceinline__ void final_kernel_epilogue(const StageArgs& A, T emax
     }
 }
 
+// The segments (column, planes [z0, z1)) of this CTA.  Column-split schedule
+// when A.kper > 0: CTA b owns z-band b / ncols of column b % ncols, so all
+// columns sweep the same planes in step; otherwise a balanced linear share of
+// the (column, z) space, cut into per-column runs.
+template <typename F>
+__device__ __forceinline__ void for_each_segment(const StageArgs& A, int nz, F&& body) {
+    const int ncols = A.ntx * A.nty;
+    if (A.kper > 0) {
+        const int col = (int)(blockIdx.x % ncols);
+        const int band = (int)(blockIdx.x / ncols);
+        const int z0 = (int)((long long)band * nz / A.kper);
+        const int z1 = (int)((long long)(band + 1) * nz / A.kper);
+        if (band < A.kper && z0 < z1) body(col, z0, z1);
+        return;
+    }
+    const long long L = (long long)ncols * nz;
+    const long long s_end = L * (blockIdx.x + 1) / gridDim.x;
+    for (long long sg = L * blockIdx.x / gridDim.x; sg < s_end;) {
+        const int col = (int)(sg / nz);
+        const int z0 = (int)(sg - (long long)col * nz);
+        const int z1 = (int)min((long long)nz, z0 + (s_end - sg));
+        sg += z1 - z0;
+        body(col, z0, z1);
+    }
+}
+
 template <typename T, int NK, int MODE, int VX>
 __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_kernel(const Geom<T> g, const StageArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -404,32 +449,13 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256) gs_stage_wide_
     }
     const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, parity, step, 0);
     const StageCoef<T, NK> C = stage_coef<T, NK>(A, dtd, atol, rtol);
-    T emax = T(0);
+    typename ErrBits<T>::U ebits = 0;
     if (!skip) {
-        // schedule: see gs_stage_kernel (column-split when kper > 0, else
-        // balanced linear (column, z) shares)
-        const int nz = g.nz;
-        const int ncols = A.ntx * A.nty;
-        const long long L = A.kper > 0 ? (long long)ncols * A.kper : (long long)ncols * nz;
-        const long long s_end = A.kper > 0 ? blockIdx.x + 1 : L * (blockIdx.x + 1) / gridDim.x;
-        for (long long sg = A.kper > 0 ? blockIdx.x : L * blockIdx.x / gridDim.x; sg < s_end;) {
-            int col, z0, z1;
-            if (A.kper > 0) {
-                col = (int)(sg % ncols);
-                const int band = (int)(sg / ncols);
-                z0 = (int)((long long)band * nz / A.kper);
-                z1 = (int)((long long)(band + 1) * nz / A.kper);
-                sg += 1;
-                if (band >= A.kper || z0 >= z1) continue;
-            } else {
-                col = (int)(sg / nz);
-                z0 = (int)(sg - (long long)col * nz);
-                z1 = (int)min((long long)nz, z0 + (s_end - sg));
-                sg += z1 - z0;
-            }
-            wide_segment<T, NK, MODE, VX>(g, P, C, S, A.ty, col % A.ntx, col / A.ntx, z0, z1, emax);
-        }
+        for_each_segment(A, g.nz, [&](int col, int z0, int z1) {
+            wide_segment<T, NK, MODE, VX>(g, P, C, S, A.ty, col % A.ntx, col / A.ntx, z0, z1, ebits);
+        });
     }
+    const T emax = ErrBits<T>::value(ebits);
     if (MODE != MODE_STAGE && A.run_ctrl && A.ctrl) final_kernel_epilogue<T, MODE>(A, emax, red, &s_last);
 }
 

@@ -115,13 +115,19 @@ def test_fixed_step_methods_fp64(dims, method, nsteps):
 # (dims, L): the domain grows with the grid so the explicit step stays stable
 @pytest.mark.parametrize("dims,L", [((45, 29, 19), 2.5), ((44, 29, 19), 2.5), ((264, 9, 5), 2.5 * 264 / 45)])
 @pytest.mark.parametrize("tile", [(2, 1), (4, 3), (6, 32), (8, 5), (14, 64)])
-def test_tile_shape_does_not_change_results(dims, L, tile):
+@pytest.mark.parametrize("variant", [0, 4])
+def test_tile_shape_does_not_change_results(dims, L, tile, variant):
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     u0, v0 = si.gs_initial_state(*dims, seed=31)
     res = []
-    for ty, zc in [(6, 32), tile]:
+    if variant == 4 and dims[0] % 2:
+        pytest.skip("the staged form needs whole 16-byte rows")
+    for i, (ty, zc) in enumerate([(6, 32), tile]):
         g = _gs(torch, dims, gs.GS_FP64, u0, v0, L=L, Du=2e-3, Dv=1e-3)
+        if variant:
+            gs.gs_set_kernel_variant(g.ctx, variant)
+            gs.gs_set_stage_depth(g.ctx, 1 + (ty + zc + i) % 3)
         gs.gs_set_tile(g.ctx, ty, zc)
         g.step(gs.GS_DOPRI5, 0.0, 0.3, 3)
         res.append((to_np(g.u), to_np(g.v)))
@@ -133,9 +139,10 @@ def test_tile_shape_does_not_change_results(dims, L, tile):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (70, 5, 6)])
 def test_kernel_variants_match_oracle(prec, dims):
-    """The generic (one cell per thread) and vectorised (16-byte rows; FP32
-    also 8-byte rows) stencil kernels on the same grid, each against the
-    oracle, Dopri5 and RK4 steps."""
+    """The generic (one cell per thread), vectorised (16-byte rows; FP32 also
+    8-byte rows) and staged (16-byte rows, inputs copied 1..3 planes ahead)
+    stencil kernels on the same grid, each against the oracle, Dopri5 and RK4
+    steps."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     # x spacing at least 2.5/45 keeps dt * lambda_max well inside the
@@ -148,16 +155,21 @@ def test_kernel_variants_match_oracle(prec, dims):
     tol = FP64_TOL if prec == 0 else FP32_TOL
     for method, om in ((gs.GS_DOPRI5, oracle.DOPRI5), (gs.GS_RK4, oracle.RK4)):
         ou, ov = oracle.gs_integrate_const(p, u0, v0, om, 0.25, 3)
-        for variant in ((1, 2) if prec == 0 else (1, 2, 3)):
-            vx = {1: 1, 2: 2 if prec == 0 else 4, 3: 2}[variant]
+        runs = [(1, 0), (2, 0)] + ([(3, 0)] if prec == 1 else []) + [(4, d) for d in (1, 2, 3)]
+        for variant, depth in runs:
+            vx = {1: 1, 2: 2 if prec == 0 else 4, 3: 2, 4: 2 if prec == 0 else 4}[variant]
             if dims[0] % vx:
                 continue
             g = _gs(torch, dims, prec, u0, v0, **phys)
             gs.gs_set_kernel_variant(g.ctx, variant)
+            if depth:
+                gs.gs_set_stage_depth(g.ctx, depth)
+                assert gs.gs_get_kernel_variant(g.ctx) == 4
+                assert gs.gs_get_stage_depths(g.ctx) == [depth] * 7
             g.step(method, 0.0, 0.25, 3)
             err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov])
             g.close()
-            assert err < tol, (variant, method, err)
+            assert err < tol, (variant, depth, method, err)
 
 
 def test_vectorised_variant_rejects_unaligned_rows():
@@ -171,13 +183,18 @@ def test_vectorised_variant_rejects_unaligned_rows():
     gs.gs_set_kernel_variant(g.ctx, 1)
     g.close()
     g = _gs(torch, (9, 4, 4), gs.GS_FP32, *si.gs_initial_state(9, 4, 4))
-    for variant in (2, 3):
+    for variant in (2, 3, 4):
         with pytest.raises(gs.GSError):
             gs.gs_set_kernel_variant(g.ctx, variant)
     g.close()
     g = _gs(torch, (10, 4, 4), gs.GS_FP64, *si.gs_initial_state(10, 4, 4))
     with pytest.raises(gs.GSError):
         gs.gs_set_kernel_variant(g.ctx, 3)  # 8-byte rows exist for FP32 only
+    for depth in (0, 4):  # the staged ring holds 1..3 planes
+        with pytest.raises(gs.GSError):
+            gs.gs_set_stage_depth(g.ctx, depth)
+    with pytest.raises(gs.GSError):
+        gs.gs_set_kernel_variant(g.ctx, 5)
     g.close()
 
 
