@@ -142,8 +142,8 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts_host, long capacity, long* co
 /* Tile shape of the stencil kernels: a CTA of 32 x (ty+2) threads works on
  * columns of ty rows (30 cells wide in the generic kernel, 128 FP32 / 64 FP64
  * cells in the vectorised one) and owns an equal share, of at least zc
- * planes, of all columns' planes.  ty in {2,4,6,8,14} (final kernels use at
- * most 6), 0 <= zc <= 1024; zc = 0 (the default) lets every resident CTA
+ * planes, of all columns' planes.  2 <= ty <= 14 (final kernels of the
+ * generic and vectorised forms use at most 6), 0 <= zc <= 1024; zc = 0 (the default) lets every resident CTA
  * take a share (at least one plane).  Takes effect at the next integrator
  * call. */
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc);

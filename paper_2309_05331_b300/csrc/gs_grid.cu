@@ -760,7 +760,7 @@ gs_status gs_get_step_log(gs_ctx* ctx, double* dts, long capacity, long* count) 
 
 gs_status gs_set_tile(gs_ctx* ctx, int ty, int zc) {
     if (!ctx) return GS_ERR_INVALID;
-    if (!(ty == 2 || ty == 4 || ty == 6 || ty == 8 || ty == 14) || zc < 0 || zc > 1024)
+    if (ty < 2 || ty > kMaxTY || zc < 0 || zc > 1024)
         return GS_ERR_INVALID;
     drop_graphs(ctx);
     ctx->def.ty = ty;
@@ -846,9 +846,9 @@ static gs_status time_dp_kernel(gs_ctx* ctx, int k, int reps, cudaEvent_t e0, cu
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
     static const int cand[][2] = {{2, 0}, {4, 0}, {6, 0}, {8, 0}, {14, 0}, {4, 4}, {6, 4}, {8, 4}, {6, 16}, {8, 16}};
-    // the staged form: tile height x ring depth, column-split schedule
-    static const int cand_staged[][2] = {{2, 1}, {2, 2}, {2, 3}, {4, 1}, {4, 2}, {4, 3}, {6, 1}, {6, 2},
-                                         {8, 1}, {8, 2}, {12, 1}, {12, 2}, {14, 1}, {14, 2}};
+    // the staged form: every tile height (the column-split schedule fills
+    // the resident CTAs best at a height that depends on the grid) x ring
+    // depth 1 or 2 (a third plane in flight never paid for its shared memory)
     int forms[4], nf = 0;
     for (int f = 1; f <= 4; ++f) {
         if (!form_ok(ctx, f)) continue;
@@ -889,10 +889,8 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         };
         for (int fi = 0; fi < nf && st == GS_OK; ++fi) {
             if (forms[fi] == 4) {
-                for (const auto& c : cand_staged) {
-                    if (st != GS_OK) break;
-                    try_cfg(KCfg{4, c[0], 0, c[1]});
-                }
+                for (int ty = 2; ty <= kMaxTY && st == GS_OK; ++ty)
+                    for (int depth = 1; depth <= 2 && st == GS_OK; ++depth) try_cfg(KCfg{4, ty, 0, depth});
                 continue;
             }
             for (const auto& c : cand) {

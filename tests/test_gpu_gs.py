@@ -114,7 +114,7 @@ def test_fixed_step_methods_fp64(dims, method, nsteps):
 
 # (dims, L): the domain grows with the grid so the explicit step stays stable
 @pytest.mark.parametrize("dims,L", [((45, 29, 19), 2.5), ((44, 29, 19), 2.5), ((264, 9, 5), 2.5 * 264 / 45)])
-@pytest.mark.parametrize("tile", [(2, 1), (4, 3), (6, 32), (8, 5), (14, 64)])
+@pytest.mark.parametrize("tile", [(2, 1), (4, 3), (6, 32), (8, 5), (14, 64), (7, 0), (11, 0)])
 @pytest.mark.parametrize("variant", [0, 4])
 def test_tile_shape_does_not_change_results(dims, L, tile, variant):
     torch = cuda_or_skip()
@@ -293,8 +293,9 @@ def test_invalid_calls():
         g.step(17, 0.0, 0.1, 1)
     with pytest.raises(gs.GSError):
         g.step(gs.GS_RK4, 0.0, 0.1, -1)
-    with pytest.raises(gs.GSError):
-        gs.gs_set_tile(g.ctx, 5, 8)
+    for ty, zc in ((1, 0), (15, 0), (6, -1), (6, 1025)):
+        with pytest.raises(gs.GSError):
+            gs.gs_set_tile(g.ctx, ty, zc)
     assert g.step(gs.GS_RK4, 0.0, 0.1, 0) == 0.0
     g.close()
 
