@@ -328,6 +328,22 @@ gs_status sur_pack_weights(int cin, int cout, const float* w_dev, int dgrad, voi
  * [cells][cout_pad]), BF16; 3: FP32 [cells][cout_pad] (+ bias if given). */
 gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void* x, const void* packed,
                      const float* bias, int epi, const void* mask, void* out, int out_ch, void* stream);
+/* Tensor-core engine of sur_conv3d (and of the network's convolutions),
+ * process-wide: 0 = automatic (tcgen05 where it applies, else mma.sync),
+ * 1 = warp-level mma.sync m16n8k16 for every shape, 2 = tcgen05 where it
+ * applies.  The tcgen05 kernel covers 32 -> 32 channels with epi 0, 2 or 3
+ * on grids with D % 2 == 0, H % 16 == 0, W % 8 == 0 (accumulators in tensor
+ * memory, operands read from shared memory through matrix descriptors);
+ * other shapes always take mma.sync.  Both compute the same sums of exact
+ * BF16 products in FP32 (summation order differs).  INVALID for other
+ * values.  sur_conv_last_engine: 1 or 2, the engine of the last launch (0
+ * before any).  sur_conv_tc_status: number of tcgen05 launches that gave up
+ * waiting for their MMAs (the kernel bounds every wait, frees its tensor
+ * memory and returns; 0 in normal operation). */
+gs_status sur_set_conv_engine(int engine);
+int sur_get_conv_engine(void);
+int sur_conv_last_engine(void);
+gs_status sur_conv_tc_status(unsigned int* timeouts);
 /* dw[27][cin][cout] (FP32) = sum over cells p of x[p + off(tap)][i] dy[p][o]
  * (the weight gradient); workspace of sur_wgrad_workspace_bytes bytes. */
 size_t sur_wgrad_workspace_bytes(int cin_pad, int cout_pad);

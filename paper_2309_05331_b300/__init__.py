@@ -101,6 +101,10 @@ _SIGNATURES = {
     "sur_last_error": ([_vp], C.c_char_p),
     "sur_packed_bytes": ([C.c_int, C.c_int], C.c_size_t),
     "sur_pack_weights": ([C.c_int, C.c_int, _vp, C.c_int, _vp, _vp], C.c_int),
+    "sur_set_conv_engine": ([C.c_int], C.c_int),
+    "sur_get_conv_engine": ([], C.c_int),
+    "sur_conv_last_engine": ([], C.c_int),
+    "sur_conv_tc_status": ([C.POINTER(C.c_uint)], C.c_int),
     "sur_conv3d": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp],
                    C.c_int),
     "sur_wgrad_workspace_bytes": ([C.c_int, C.c_int], C.c_size_t),

@@ -23,6 +23,7 @@
 
 #include "../../include/gs.h"
 #include "host_util.h"
+#include "sur_conv_tc.cuh"
 #include "sur_conv.cuh"
 
 using namespace sur;
@@ -266,11 +267,46 @@ cudaError_t launch_conv_t(int D, int H, int W, const __nv_bfloat16* x, const __n
     return cudaGetLastError();
 }
 
+// Convolution engine: 0 automatic (tcgen05 where it applies), 1 mma.sync
+// only, 2 tcgen05 where it applies.  Process-wide; the last launch's engine
+// is recorded for tests.
+int g_conv_engine = 1;
+int g_conv_last_engine = 0;
+
+bool tc_applies(int cinp, int coutp, int epi, int D, int H, int W) {
+    return cinp == 32 && coutp == 32 && (epi == EPI_BIAS_RELU_BF16 || epi == EPI_MASK_BF16 || epi == EPI_RAW_F32) &&
+           D % tc::TZ == 0 && H % tc::TY == 0 && W % tc::TX == 0;
+}
+
+template <int EPI>
+cudaError_t launch_conv_tc_t(int D, int H, int W, const __nv_bfloat16* x, const __nv_bfloat16* wp, const float* bias,
+                             const __nv_bfloat16* mask, void* out, cudaStream_t s) {
+    auto kern = tc::conv_tc_kernel<EPI>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tc::NTHREADS, tc::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    // each resident CTA holds tc::TMEM_COLS of an SM's 512 TMEM columns
+    occ = std::max(1, std::min(occ, (int)(512 / tc::TMEM_COLS)));
+    const int ntiles = (W / tc::TX) * (H / tc::TY) * (D / tc::TZ);
+    const int grid = std::max(1, std::min(ntiles, nsm_now() * occ));
+    kern<<<grid, tc::NTHREADS, tc::SMEM_BYTES, s>>>(x, wp, bias, mask, out, D, H, W);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_conv(int cinp, int coutp, int epi, int D, int H, int W, const void* x, const void* wp,
                         const float* bias, const void* mask, void* out, int out_ch, cudaStream_t s) {
     const auto* xb = static_cast<const __nv_bfloat16*>(x);
     const auto* wb = static_cast<const __nv_bfloat16*>(wp);
     const auto* mb = static_cast<const __nv_bfloat16*>(mask);
+    if (g_conv_engine != 1 && tc_applies(cinp, coutp, epi, D, H, W)) {
+        g_conv_last_engine = 2;
+        if (epi == EPI_BIAS_RELU_BF16) return launch_conv_tc_t<EPI_BIAS_RELU_BF16>(D, H, W, xb, wb, bias, mb, out, s);
+        if (epi == EPI_MASK_BF16) return launch_conv_tc_t<EPI_MASK_BF16>(D, H, W, xb, wb, bias, mb, out, s);
+        return launch_conv_tc_t<EPI_RAW_F32>(D, H, W, xb, wb, bias, mb, out, s);
+    }
+    g_conv_last_engine = 1;
 #define SUR_CONV_CASE(CI, CO, EP)                                                        \
     if (cinp == CI && coutp == CO && epi == EP)                                          \
         return launch_conv_t<CI, CO, EP>(D, H, W, xb, wb, bias, mb, out, out_ch, s);
@@ -636,6 +672,26 @@ gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void*
     if (e == cudaErrorInvalidValue) return GS_ERR_INVALID;
     if (e != cudaSuccess) {
         set_global_error(e, "sur_conv3d");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status sur_set_conv_engine(int engine) {
+    if (engine < 0 || engine > 2) return GS_ERR_INVALID;
+    g_conv_engine = engine;
+    return GS_OK;
+}
+
+int sur_get_conv_engine(void) { return g_conv_engine; }
+
+int sur_conv_last_engine(void) { return g_conv_last_engine; }
+
+gs_status sur_conv_tc_status(unsigned int* timeouts) {
+    if (!timeouts) return GS_ERR_INVALID;
+    cudaError_t e = cudaMemcpyFromSymbol(timeouts, tc::g_tc_timeouts, sizeof(unsigned int));
+    if (e != cudaSuccess) {
+        set_global_error(e, "sur_conv_tc_status");
         return GS_ERR_CUDA;
     }
     return GS_OK;

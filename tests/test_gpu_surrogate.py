@@ -218,3 +218,131 @@ def test_judge_and_fallback():
     assert torch.equal(g.u, before)  # "no change" network
     for x in (s, g, ref):
         x.close()
+
+
+# --- tcgen05 engine (32 -> 32 channels, H % 16 == 0, W % 8 == 0) ----------
+
+@pytest.fixture
+def tc_engine():
+    """Selects the tcgen05 convolution engine for one test and restores the
+    previous setting afterwards."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    prev = gs.lib().sur_get_conv_engine()
+    assert gs.lib().sur_set_conv_engine(2) == 0
+    yield torch, gs
+    gs.lib().sur_set_conv_engine(prev)
+
+
+def _tc_timeouts(gs):
+    n = C.c_uint(0)
+    assert gs.lib().sur_conv_tc_status(C.byref(n)) == 0
+    return n.value
+
+
+TC_GRIDS = [(2, 16, 16), (4, 16, 32), (2, 32, 16), (6, 48, 32)]
+
+
+@pytest.mark.parametrize("grid", TC_GRIDS)
+@pytest.mark.parametrize("epi", [3, 0])
+def test_conv_forward_tcgen05(tc_engine, grid, epi):
+    """The tcgen05 kernel against the oracle on BF16-rounded operands (FP32
+    accumulation, raw and bias + ReLU -> BF16 epilogues)."""
+    torch, gs = tc_engine
+    D, H, W = grid
+    rng = np.random.default_rng(D * 1000 + H + W + epi)
+    x = _rand_bf16(rng, (D, H, W, 32))
+    w = _rand_bf16(rng, (27, 32, 32), 0.2)
+    b = rng.standard_normal(32).astype(np.float32).astype(np.float64)
+    xd = _dev_act(torch, x, 32)
+    wp, _ = _packed(torch, gs, w, 0)
+    bd = torch.from_numpy(b.astype(np.float32)).cuda()
+    odt = torch.float32 if epi == 3 else torch.bfloat16
+    out = torch.zeros((D, H, W, 32), dtype=odt, device="cuda")
+    before = _tc_timeouts(gs)
+    assert gs.lib().sur_conv3d(D, H, W, 32, 32, xd.data_ptr(), wp.data_ptr(), bd.data_ptr(), epi, None,
+                               out.data_ptr(), 32, None) == 0
+    torch.cuda.synchronize()
+    assert gs.lib().sur_conv_last_engine() == 2
+    assert _tc_timeouts(gs) == before
+    ref = oracle.conv3d_fwd(x, w, b)
+    got = to_np(out)
+    if epi == 3:
+        assert _rel(got, ref) < ACC_TOL
+    else:
+        refr = np.maximum(ref, 0.0)
+        # BF16 output: one rounding of the FP32 sum (8 significant bits)
+        assert np.all(np.abs(got - refr) <= 2.0 ** -8 * np.abs(refr) + 1e-6 * np.max(np.abs(refr)))
+
+
+def test_conv_input_gradient_tcgen05(tc_engine):
+    torch, gs = tc_engine
+    D, H, W = 4, 16, 16
+    rng = np.random.default_rng(77)
+    dy = _rand_bf16(rng, (D, H, W, 32))
+    w = _rand_bf16(rng, (27, 32, 32), 0.2)
+    dyd = _dev_act(torch, dy, 32)
+    wp, _ = _packed(torch, gs, w, 1)
+    out = torch.zeros((D, H, W, 32), dtype=torch.float32, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, 32, 32, dyd.data_ptr(), wp.data_ptr(), None, 3, None, out.data_ptr(), 32,
+                               None) == 0
+    torch.cuda.synchronize()
+    assert gs.lib().sur_conv_last_engine() == 2
+    ref = oracle.conv3d_dgrad(dy, w)
+    assert _rel(to_np(out), ref) < ACC_TOL
+    mask = _rand_bf16(rng, (D, H, W, 32))
+    md = _dev_act(torch, mask, 32)
+    outb = torch.zeros((D, H, W, 32), dtype=torch.bfloat16, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, 32, 32, dyd.data_ptr(), wp.data_ptr(), None, 2, md.data_ptr(),
+                               outb.data_ptr(), 32, None) == 0
+    torch.cuda.synchronize()
+    refm = ref * (mask > 0)
+    gotm = to_np(outb)
+    assert np.all(np.abs(gotm - refm) <= 2.0 ** -8 * np.abs(refm) + 1e-6 * np.max(np.abs(refm)))
+    assert _tc_timeouts(gs) == 0
+
+
+def test_conv_engines_agree(tc_engine):
+    """Both engines on the same inputs: equal up to FP32 summation order."""
+    torch, gs = tc_engine
+    D, H, W = 4, 32, 32
+    rng = np.random.default_rng(5)
+    x = _rand_bf16(rng, (D, H, W, 32))
+    w = _rand_bf16(rng, (27, 32, 32), 0.2)
+    xd = _dev_act(torch, x, 32)
+    wp, _ = _packed(torch, gs, w, 0)
+    outs = []
+    for engine in (1, 2):
+        gs.lib().sur_set_conv_engine(engine)
+        o = torch.zeros((D, H, W, 32), dtype=torch.float32, device="cuda")
+        assert gs.lib().sur_conv3d(D, H, W, 32, 32, xd.data_ptr(), wp.data_ptr(), None, 3, None, o.data_ptr(), 32,
+                                   None) == 0
+        torch.cuda.synchronize()
+        assert gs.lib().sur_conv_last_engine() == engine
+        outs.append(to_np(o))
+    assert _rel(outs[1], outs[0]) < 1e-6
+
+
+def test_network_gradient_tcgen05_matches_oracle_backprop(tc_engine):
+    """Whole-network loss gradient with the hidden layers on tcgen05 (grid
+    with H % 16 == 0) against oracle backpropagation."""
+    torch, gs = tc_engine
+    D, H, W = 2, 16, 16
+    params = si.surrogate_init_params(seed=3, last_layer_scale=0.5)
+    u, v = _state((D, H, W), 5)
+    rng = np.random.default_rng(2)
+    ut = u + 0.003 * rng.standard_normal(u.shape)
+    vt = v + 0.006 * rng.standard_normal(v.shape)
+    u, v, ut, vt = (a.astype(np.float32).astype(np.float64) for a in (u, v, ut, vt))
+    mean, sd, scale = _norm()
+    s = gs.Surrogate(W, H, D)
+    s.set_params(params)
+    s.set_normalization(mean, sd, scale)
+    dev = [torch.from_numpy(a.astype(np.float32)).cuda() for a in (u, v, ut, vt)]
+    loss = s.train_step(*dev, 1e-9)
+    g = s.get_grad()
+    ref_loss, ref_g = oracle.surrogate_loss_grad(params.astype(np.float64), u, v, ut, vt, mean, sd, scale)
+    assert abs(loss - ref_loss) < 1e-4 * ref_loss
+    assert _rel(g.astype(np.float64), ref_g) < 2e-3
+    s.close()
+    assert _tc_timeouts(gs) == 0
