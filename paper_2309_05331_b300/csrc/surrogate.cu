@@ -270,7 +270,7 @@ cudaError_t launch_conv_t(int D, int H, int W, const __nv_bfloat16* x, const __n
 // Convolution engine: 0 automatic (tcgen05 where it applies), 1 mma.sync
 // only, 2 tcgen05 where it applies.  Process-wide; the last launch's engine
 // is recorded for tests.
-int g_conv_engine = 1;
+int g_conv_engine = 0;
 int g_conv_last_engine = 0;
 
 bool tc_applies(int cinp, int coutp, int epi, int D, int H, int W) {
@@ -284,13 +284,9 @@ cudaError_t launch_conv_tc_t(int D, int H, int W, const __nv_bfloat16* x, const 
     auto kern = tc::conv_tc_kernel<EPI>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, tc::NTHREADS, tc::SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    // each resident CTA holds tc::TMEM_COLS of an SM's 512 TMEM columns
-    occ = std::max(1, std::min(occ, (int)(512 / tc::TMEM_COLS)));
+    // one CTA per SM: it holds all 512 TMEM columns (and most of the shared memory)
     const int ntiles = (W / tc::TX) * (H / tc::TY) * (D / tc::TZ);
-    const int grid = std::max(1, std::min(ntiles, nsm_now() * occ));
+    const int grid = std::max(1, std::min(ntiles, nsm_now()));
     kern<<<grid, tc::NTHREADS, tc::SMEM_BYTES, s>>>(x, wp, bias, mask, out, D, H, W);
     return cudaGetLastError();
 }

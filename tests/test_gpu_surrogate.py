@@ -220,7 +220,7 @@ def test_judge_and_fallback():
         x.close()
 
 
-# --- tcgen05 engine (32 -> 32 channels, H % 16 == 0, W % 8 == 0) ----------
+# --- tcgen05 engine (32 -> 32 channels, D % 4 == 0, H % 16 == 0) ----------
 
 @pytest.fixture
 def tc_engine():
@@ -240,7 +240,7 @@ def _tc_timeouts(gs):
     return n.value
 
 
-TC_GRIDS = [(2, 16, 16), (4, 16, 32), (2, 32, 16), (6, 48, 32)]
+TC_GRIDS = [(4, 16, 16), (4, 16, 32), (8, 32, 16), (12, 48, 32)]
 
 
 @pytest.mark.parametrize("grid", TC_GRIDS)
@@ -327,7 +327,7 @@ def test_network_gradient_tcgen05_matches_oracle_backprop(tc_engine):
     """Whole-network loss gradient with the hidden layers on tcgen05 (grid
     with H % 16 == 0) against oracle backpropagation."""
     torch, gs = tc_engine
-    D, H, W = 2, 16, 16
+    D, H, W = 4, 16, 16
     params = si.surrogate_init_params(seed=3, last_layer_scale=0.5)
     u, v = _state((D, H, W), 5)
     rng = np.random.default_rng(2)
