@@ -213,6 +213,8 @@ if __name__ == "__main__":
     ap.add_argument("--trajectories", type=int, default=8)
     ap.add_argument("--per-traj", type=int, default=250)
     ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--conv-engine", type=int, default=0, help="0 automatic, 1 mma.sync, 2 tcgen05 where it applies")
     a = ap.parse_args()
     torch.cuda.set_device(0)
+    assert lib().sur_set_conv_engine(a.conv_engine) == 0
     print(json.dumps(run(torch, a.grid, a.trajectories, a.per_traj, a.iters), indent=1))
