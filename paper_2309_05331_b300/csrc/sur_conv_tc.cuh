@@ -33,6 +33,13 @@
 //   B: the packed weights re-laid once per CTA as [dy, dx][K half][chunk]
 //      [96 stacked output rows] x 16 bytes (SBO 128, LBO 1536 bytes).
 //
+// The 8-channel layers use the same kernel.  CIN = 8: a tap carries one
+// 16-byte chunk, so an MMA (K = 16) pairs two (dy, dx) taps of the same input
+// plane, the second core matrix LBO bytes after the first (the two taps'
+// cell distance); 5 pairs cover the 9 taps (the tenth weight block is zero).
+// COUT = 8: a plane's accumulator is 16 columns wide (8 zero weight rows),
+// so the stacked MMA has N = 48 and the first-touch split N = 32 + 16.
+//
 // Warp-specialised persistent pipeline (9 warps): warp 8 allocates TMEM and
 // issues each tile's MMAs from one thread; warps 0-7 copy halos (cp.async)
 // and run the fused epilogue (warp w reads TMEM lanes 32 (w mod 4) .. of
@@ -55,18 +62,24 @@ namespace tc {
 constexpr int TX = 8, TY = 16, TZ = 4;  // output tile; M = TX * TY = 128 per z-plane
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
 constexpr int HC = HX * HY * HZ;  // 1080 halo cells
-constexpr int CH = 32;            // channels in and out
-constexpr int NCHUNK = CH / 8;    // 16-byte chunks per cell
-constexpr int NSTK = 3 * CH;      // stacked B rows: W(dz=+1), W(0), W(-1)
 constexpr int NTHREADS = 288;     // 8 loader / epilogue warps + 1 MMA warp
 constexpr int NLOAD = 256;        // loader / epilogue threads
-constexpr int SET_COLS = (TZ + 4) * CH;             // planes -2 .. TZ+1: 256 columns
-constexpr uint32_t TMEM_COLS = 2 * SET_COLS;        // two accumulator sets: all 512
-constexpr int NBUF = 2;                             // halo buffers
-constexpr size_t W_BYTES = (size_t)9 * 2 * 2 * NSTK * 16;   // 55,296
-constexpr size_t X_BYTES = (size_t)NCHUNK * HC * 16;        // 69,120 per halo buffer
-constexpr size_t SMEM_BYTES = W_BYTES + NBUF * X_BYTES + 128;  // + mbarriers, TMEM address, abort flag
-constexpr long kMaxPolls = 1L << 22;                        // mbarrier wait limit (try_wait calls)
+constexpr int NBUF = 2;           // halo buffers
+constexpr long kMaxPolls = 1L << 22;  // mbarrier wait limit (try_wait calls)
+
+// Shapes of one (CIN, COUT) instance; CIN, COUT in {8, 32} (padded counts).
+template <int CIN, int COUT>
+struct Cfg {
+    static constexpr int NCI = CIN / 8;                   // 16-byte chunks per input cell
+    static constexpr int CW = COUT == 32 ? 32 : 16;       // accumulator columns per plane
+    static constexpr int NSTK = 3 * CW;                   // stacked B rows: W(dz=+1), W(0), W(-1)
+    static constexpr int KG = CIN == 32 ? 18 : 5;         // K groups (MMAs) per input plane
+    static constexpr int SET_COLS = (TZ + 4) * CW;        // planes -2 .. TZ+1
+    static constexpr uint32_t TMEM_COLS = 2 * SET_COLS;   // two accumulator sets (512 or 256)
+    static constexpr size_t W_BYTES = (size_t)KG * 2 * NSTK * 16;
+    static constexpr size_t X_BYTES = (size_t)NCI * HC * 16;
+    static constexpr size_t SMEM_BYTES = W_BYTES + NBUF * X_BYTES + 128;  // + mbarriers, TMEM address, abort flag
+};
 
 // kind::f16 instruction descriptor: D FP32 (bits 4-5 = 1), A and B BF16
 // (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bit
@@ -137,8 +150,20 @@ __device__ __forceinline__ void tmem_alloc(uint32_t slot_saddr, uint32_t ncols) 
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 // 32 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     uint32_t r[32];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
@@ -155,10 +180,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 // Periodic halo of the tile at (x0, y0, z0), chunk-major: chunk q of halo
 // cell c at byte (q * HC + c) * 16; copied with cp.async (this thread's
-// copies only).
+// copies only).  NCI chunks (CIN = 8 NCI channels) per cell.
+template <int NCI>
 __device__ __forceinline__ void halo_async(unsigned char* Xs, const __nv_bfloat16* __restrict__ x, int x0, int y0,
                                            int z0, int D, int H, int W) {
-    for (int idx = threadIdx.x; idx < HC * NCHUNK; idx += NLOAD) {
+    for (int idx = threadIdx.x; idx < HC * NCI; idx += NLOAD) {
         const int q = idx / HC, c = idx - q * HC;
         const int hx = c % HX, rr = c / HX, hy = rr % HY, hz = rr / HY;
         // periodic wrap of a coordinate in [-1, n]
@@ -166,7 +192,7 @@ __device__ __forceinline__ void halo_async(unsigned char* Xs, const __nv_bfloat1
         gx += gx < 0 ? W : (gx >= W ? -W : 0);
         gy += gy < 0 ? H : (gy >= H ? -H : 0);
         gz += gz < 0 ? D : (gz >= D ? -D : 0);
-        const size_t g = ((size_t)gx + (size_t)W * ((size_t)gy + (size_t)H * gz)) * CH + 8 * q;
+        const size_t g = ((size_t)gx + (size_t)W * ((size_t)gy + (size_t)H * gz)) * (8 * NCI) + 8 * q;
         const uint32_t dst = smem_u32(Xs + (size_t)idx * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(x + g) : "memory");
     }
@@ -176,41 +202,53 @@ __device__ __forceinline__ void halo_async(unsigned char* Xs, const __nv_bfloat1
 // weights at ws_addr, accumulator set at d_tmem.  Descriptor start addresses
 // advance by adding 16-byte units to the low field: the sum stays inside
 // shared memory (< 2^18 bytes), so it never carries out of the 14-bit field.
+// K group g of an input plane: CIN = 32: tap pair r = g / 2, channel half
+// h = g % 2 (second core matrix one chunk plane further); CIN = 8: taps 2g
+// and 2g+1 (second core matrix at the second tap's cell, or the first one
+// again with zero weights for g = 4).
+template <int CIN, int COUT>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t xs_addr, uint32_t ws_addr, uint32_t d_tmem) {
-    const uint64_t a_base = sdesc(xs_addr, HC * 16, HX * 16);
+    using C = Cfg<CIN, COUT>;
+    constexpr int CW = C::CW, NSTK = C::NSTK;
     const uint64_t b_base = sdesc(ws_addr, NSTK * 16, 8 * 16);
-    constexpr uint32_t ID96 = idesc_m128(NSTK), ID64 = idesc_m128(2 * CH), ID32 = idesc_m128(CH);
+    constexpr uint32_t IDS = idesc_m128(NSTK), ID2 = idesc_m128(2 * CW), ID1 = idesc_m128(CW);
+    auto cell0 = [](int r) { return (r % 3) + HX * (r / 3); };  // (dx+1) + HX (dy+1)
 #pragma unroll 1
     for (int q = 0; q < HZ; ++q) {
-        const uint32_t d = d_tmem + (uint32_t)(q * CH);  // planes q-2, q-1, q
+        const uint32_t d = d_tmem + (uint32_t)(q * CW);  // planes q-2, q-1, q
 #pragma unroll
-        for (int r = 0; r < 9; ++r) {
-            const int dy = r / 3 - 1, dx = r % 3 - 1;
-            const int c0 = (dx + 1) + HX * ((dy + 1) + HY * q);  // halo cell of output row 0 for this tap pair
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const uint64_t ad = a_base + (uint64_t)(c0 + 2 * h * HC);
-                const uint64_t bd = b_base + (uint64_t)((r * 2 + h) * 2 * NSTK);
-                if (r == 0 && h == 0) {
-                    // first contribution to plane q: accumulate into q-2, q-1, overwrite q
-                    mma_bf16_tmem(d, ad, bd, ID64, 1u);
-                    mma_bf16_tmem(d + 2 * CH, ad, bd + (uint64_t)(2 * CH), ID32, 0u);
-                } else {
-                    mma_bf16_tmem(d, ad, bd, ID96, 1u);
-                }
+        for (int g = 0; g < C::KG; ++g) {
+            uint64_t ad;
+            if (CIN == 32) {
+                const int r = g >> 1, h = g & 1;
+                ad = sdesc(xs_addr, HC * 16, HX * 16) + (uint64_t)(cell0(r) + HX * HY * q + 2 * h * HC);
+            } else {
+                const int ra = 2 * g, rb = 2 * g + 1;
+                const uint32_t lbo = rb < 9 ? (uint32_t)((cell0(rb) - cell0(ra)) * 16) : 0u;
+                ad = sdesc(xs_addr, lbo, HX * 16) + (uint64_t)(cell0(ra) + HX * HY * q);
+            }
+            const uint64_t bd = b_base + (uint64_t)(g * 2 * NSTK);
+            if (g == 0) {
+                // first contribution to plane q: accumulate into q-2, q-1, overwrite q
+                mma_bf16_tmem(d, ad, bd, ID2, 1u);
+                mma_bf16_tmem(d + 2 * CW, ad, bd + (uint64_t)(2 * CW), ID1, 0u);
+            } else {
+                mma_bf16_tmem(d, ad, bd, IDS, 1u);
             }
         }
     }
 }
 
-// Same contract as conv_fwd_kernel<32, 32, EPI> (sur_conv.cuh) for
-// EPI in {BIAS_RELU_BF16, MASK_BF16, RAW_F32}; D % 4 == 0, H % 16 == 0,
-// W % 8 == 0.  wp: the packed weights of sur_pack_weights.
-template <int EPI>
+// Same contract as conv_fwd_kernel<CIN, COUT, EPI> (sur_conv.cuh); D % 4 == 0,
+// H % 16 == 0, W % 8 == 0.  wp: the packed weights of sur_pack_weights.
+template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
     conv_tc_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ wp,
-                   const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* out, int D, int H,
-                   int W) {
+                   const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* out, int out_ch,
+                   int D, int H, int W) {
+    using C = Cfg<CIN, COUT>;
+    constexpr int CW = C::CW, NSTK = C::NSTK, SET_COLS = C::SET_COLS;
+    constexpr size_t W_BYTES = C::W_BYTES, X_BYTES = C::X_BYTES;
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* Ws = smem;
     unsigned char* Xs[NBUF];
@@ -224,18 +262,32 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     const uint32_t ws_addr = smem_u32(Ws);
     auto bar = [&](int k) -> uint32_t { return smem_u32(mb + k); };
 
-    // stacked weights: B row n' = 32 j + o of tap pair r = 3 (dy+1) + (dx+1)
-    // holds W(dz = 1 - j, dy, dx)[., o]; packed row (ks = 2 tap + h, o) holds
-    // chunks q = 0, 1 (swizzled by o) of input channels 16 h + 8 q ..
-    for (int i = tid; i < 9 * 2 * 2 * NSTK; i += NTHREADS) {
-        const int n = i % NSTK, rq = i / NSTK, q = rq & 1, rh = rq >> 1, h = rh & 1, r = rh >> 1;
-        const int j = n / CH, o = n - j * CH, dz = 1 - j;
-        const int tap = (dz + 1) * 9 + r, ks = 2 * tap + h;
-        const uint4 v = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(wp) +
-                                                             wrow_off(ks, o, q, CH)));
+    // stacked weights: B row n' = CW j + o of K group g, core-matrix column k
+    // holds W(dz = 1 - j, tap of (g, k))[input chunk of (g, k)][o] (zero for
+    // o >= COUT or a missing tap).  Packed rows: CIN = 32, row (ks = 2 tap +
+    // h, o) holds chunks q = 0, 1 of channels 16 h + 8 q ..; CIN = 8, row (ks,
+    // o) holds chunk q = tap of taps 2 ks, 2 ks + 1.  Chunks are swizzled by o.
+    for (int i = tid; i < C::KG * 2 * NSTK; i += NTHREADS) {
+        const int n = i % NSTK, gk = i / NSTK, k = gk & 1, g = gk >> 1;
+        const int j = n / CW, o = n - j * CW, dz = 1 - j;
+        int r, ks, q;
+        if (CIN == 32) {
+            r = g >> 1;
+            ks = 2 * ((dz + 1) * 9 + r) + (g & 1);
+            q = k;
+        } else {
+            r = 2 * g + k;
+            const int tap = (dz + 1) * 9 + r;
+            ks = tap >> 1;
+            q = tap & 1;
+        }
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (o < COUT && r < 9)
+            v = __ldg(reinterpret_cast<const uint4*>(reinterpret_cast<const unsigned char*>(wp) +
+                                                     wrow_off(ks, o, q, COUT)));
         *reinterpret_cast<uint4*>(Ws + (size_t)i * 16) = v;
     }
-    if (warp == 8) tmem_alloc(smem_u32(tslot), TMEM_COLS);
+    if (warp == 8) tmem_alloc(smem_u32(tslot), C::TMEM_COLS);
     if (tid == 0) {
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(bar(HF + b), NLOAD);  // halo full: every loader thread
@@ -274,7 +326,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 if (!mbar_wait_bounded(bar(HF + b), (uint32_t)((i >> 1) & 1), abort)) break;
                 if (i >= 2 && !mbar_wait_bounded(bar(AE + b), (uint32_t)(((i >> 1) - 1) & 1), abort)) break;
                 fence_after_sync();
-                issue_tile_mmas(smem_u32(Xs[b]), ws_addr, tbase + (uint32_t)(b * SET_COLS));
+                issue_tile_mmas<CIN, COUT>(smem_u32(Xs[b]), ws_addr, tbase + (uint32_t)(b * SET_COLS));
                 mma_commit(bar(AF + b));  // accumulators full
                 mma_commit(bar(HE + b));  // halo buffer free
             }
@@ -285,7 +337,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         auto load = [&](int i) {
             int a, b, c;
             tile_origin(i, a, b, c);
-            halo_async(Xs[i & 1], x, a, b, c, D, H, W);
+            halo_async<C::NCI>(Xs[i & 1], x, a, b, c, D, H, W);
         };
         auto publish = [&](int i) {  // this thread's copies of tile i are in shared memory
             asm volatile("cp.async.wait_all;\n" ::: "memory");
@@ -316,26 +368,31 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll 1
             for (int pp = 0; pp < 2; ++pp) {
                 const int p = 2 * (warp >> 2) + pp;  // output plane of the tile
-                float v[32];
-                tmem_ld32(tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(s * SET_COLS + (p + 2) * CH), v);
+                float v[CW];
+                const uint32_t ta =
+                    tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(s * SET_COLS + (p + 2) * CW);
+                if (CW == 32)
+                    tmem_ld32(ta, v);
+                else
+                    tmem_ld16(ta, v);
                 if (pp == 1) {
                     fence_before_sync();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar(AE + s));  // this warp's accumulator rows are read
                 }
                 const size_t cell = (size_t)(x0 + mx) + (size_t)W * ((size_t)(y0 + my) + (size_t)H * (z0 + p));
-                if (EPI == EPI_BIAS_RELU_BF16 || (EPI == EPI_RAW_F32 && bias)) {
+                if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32 || (EPI == EPI_RAW_F32 && bias)) {
 #pragma unroll
-                    for (int o = 0; o < 32; ++o) v[o] += __ldg(bias + o);
+                    for (int o = 0; o < COUT; ++o) v[o] += __ldg(bias + o);
                 }
                 if (EPI == EPI_BIAS_RELU_BF16) {
 #pragma unroll
-                    for (int o = 0; o < 32; ++o) v[o] = fmaxf(v[o], 0.f);
+                    for (int o = 0; o < COUT; ++o) v[o] = fmaxf(v[o], 0.f);
                 }
                 if (EPI == EPI_MASK_BF16) {
-                    const uint4* mp = reinterpret_cast<const uint4*>(mask + cell * CH);
+                    const uint4* mp = reinterpret_cast<const uint4*>(mask + cell * COUT);
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
+                    for (int qq = 0; qq < COUT / 8; ++qq) {
                         const uint4 mv = __ldg(mp + qq);
                         const __nv_bfloat16* mbf = reinterpret_cast<const __nv_bfloat16*>(&mv);
 #pragma unroll
@@ -344,9 +401,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     }
                 }
                 if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_MASK_BF16) {
-                    uint4* po = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + cell * CH);
+                    uint4* po = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(out) + cell * COUT);
 #pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
+                    for (int qq = 0; qq < COUT / 8; ++qq) {
                         uint4 w4;
                         __nv_bfloat162* wb = reinterpret_cast<__nv_bfloat162*>(&w4);
 #pragma unroll
@@ -354,10 +411,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                             wb[e] = __floats2bfloat162_rn(v[8 * qq + 2 * e], v[8 * qq + 2 * e + 1]);
                         po[qq] = w4;
                     }
-                } else {
-                    float4* po = reinterpret_cast<float4*>(static_cast<float*>(out) + cell * CH);
+                } else if (EPI == EPI_BIAS_F32) {
+                    float* po = static_cast<float*>(out) + cell * out_ch;
 #pragma unroll
-                    for (int qq = 0; qq < 8; ++qq)
+                    for (int o = 0; o < COUT; ++o)
+                        if (o < out_ch) po[o] = v[o];
+                } else {
+                    float4* po = reinterpret_cast<float4*>(static_cast<float*>(out) + cell * COUT);
+#pragma unroll
+                    for (int qq = 0; qq < COUT / 4; ++qq)
                         po[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
                 }
             }
@@ -367,7 +429,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == 8) tmem_dealloc(tbase, TMEM_COLS);
+    if (warp == 8) tmem_dealloc(tbase, C::TMEM_COLS);
 }
 
 }  // namespace tc

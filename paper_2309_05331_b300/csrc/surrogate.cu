@@ -274,20 +274,26 @@ int g_conv_engine = 0;
 int g_conv_last_engine = 0;
 
 bool tc_applies(int cinp, int coutp, int epi, int D, int H, int W) {
-    return cinp == 32 && coutp == 32 && (epi == EPI_BIAS_RELU_BF16 || epi == EPI_MASK_BF16 || epi == EPI_RAW_F32) &&
-           D % tc::TZ == 0 && H % tc::TY == 0 && W % tc::TX == 0;
+    const bool shape = D % tc::TZ == 0 && H % tc::TY == 0 && W % tc::TX == 0;
+    if (cinp == 32 && coutp == 32) return shape && (epi == EPI_BIAS_RELU_BF16 || epi == EPI_MASK_BF16 || epi == EPI_RAW_F32);
+    if (cinp == 8 && coutp == 32) return shape && (epi == EPI_BIAS_RELU_BF16 || epi == EPI_MASK_BF16 || epi == EPI_RAW_F32);
+    if (cinp == 32 && coutp == 8) return shape && (epi == EPI_BIAS_F32 || epi == EPI_RAW_F32);
+    return false;
 }
 
-template <int EPI>
+template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv_tc_t(int D, int H, int W, const __nv_bfloat16* x, const __nv_bfloat16* wp, const float* bias,
-                             const __nv_bfloat16* mask, void* out, cudaStream_t s) {
-    auto kern = tc::conv_tc_kernel<EPI>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc::SMEM_BYTES);
+                             const __nv_bfloat16* mask, void* out, int out_ch, cudaStream_t s) {
+    auto kern = tc::conv_tc_kernel<CIN, COUT, EPI>;
+    // one CTA per SM: a CTA allocates up to all 512 TMEM columns, and a second
+    // one on the same SM would wait in tcgen05.alloc; asking for more shared
+    // memory than half an SM holds keeps the scheduler from co-locating them
+    const size_t smem = std::max(tc::Cfg<CIN, COUT>::SMEM_BYTES, (size_t)120 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // one CTA per SM: it holds all 512 TMEM columns (and most of the shared memory)
     const int ntiles = (W / tc::TX) * (H / tc::TY) * (D / tc::TZ);
     const int grid = std::max(1, std::min(ntiles, nsm_now()));
-    kern<<<grid, tc::NTHREADS, tc::SMEM_BYTES, s>>>(x, wp, bias, mask, out, D, H, W);
+    kern<<<grid, tc::NTHREADS, smem, s>>>(x, wp, bias, mask, out, out_ch, D, H, W);
     return cudaGetLastError();
 }
 
@@ -298,9 +304,19 @@ cudaError_t launch_conv(int cinp, int coutp, int epi, int D, int H, int W, const
     const auto* mb = static_cast<const __nv_bfloat16*>(mask);
     if (g_conv_engine != 1 && tc_applies(cinp, coutp, epi, D, H, W)) {
         g_conv_last_engine = 2;
-        if (epi == EPI_BIAS_RELU_BF16) return launch_conv_tc_t<EPI_BIAS_RELU_BF16>(D, H, W, xb, wb, bias, mb, out, s);
-        if (epi == EPI_MASK_BF16) return launch_conv_tc_t<EPI_MASK_BF16>(D, H, W, xb, wb, bias, mb, out, s);
-        return launch_conv_tc_t<EPI_RAW_F32>(D, H, W, xb, wb, bias, mb, out, s);
+#define SUR_TC_CASE(CI, CO, EP)                   \
+    if (cinp == CI && coutp == CO && epi == EP) \
+        return launch_conv_tc_t<CI, CO, EP>(D, H, W, xb, wb, bias, mb, out, out_ch, s);
+        SUR_TC_CASE(32, 32, EPI_BIAS_RELU_BF16)
+        SUR_TC_CASE(32, 32, EPI_MASK_BF16)
+        SUR_TC_CASE(32, 32, EPI_RAW_F32)
+        SUR_TC_CASE(8, 32, EPI_BIAS_RELU_BF16)
+        SUR_TC_CASE(8, 32, EPI_MASK_BF16)
+        SUR_TC_CASE(8, 32, EPI_RAW_F32)
+        SUR_TC_CASE(32, 8, EPI_BIAS_F32)
+        SUR_TC_CASE(32, 8, EPI_RAW_F32)
+#undef SUR_TC_CASE
+        return cudaErrorInvalidValue;
     }
     g_conv_last_engine = 1;
 #define SUR_CONV_CASE(CI, CO, EP)                                                        \

@@ -243,61 +243,77 @@ def _tc_timeouts(gs):
 TC_GRIDS = [(4, 16, 16), (4, 16, 32), (8, 32, 16), (12, 48, 32)]
 
 
+TC_CASES = [(32, 32, 3), (32, 32, 0), (2, 32, 3), (2, 32, 0), (32, 2, 3), (32, 2, 1)]
+
+
 @pytest.mark.parametrize("grid", TC_GRIDS)
-@pytest.mark.parametrize("epi", [3, 0])
-def test_conv_forward_tcgen05(tc_engine, grid, epi):
+@pytest.mark.parametrize("cin,cout,epi", TC_CASES)
+def test_conv_forward_tcgen05(tc_engine, grid, cin, cout, epi):
     """The tcgen05 kernel against the oracle on BF16-rounded operands (FP32
-    accumulation, raw and bias + ReLU -> BF16 epilogues)."""
+    accumulation; raw, bias + ReLU -> BF16 and bias -> FP32 epilogues) for the
+    network's three layer shapes (2 -> 32, 32 -> 32, 32 -> 2 channels)."""
     torch, gs = tc_engine
     D, H, W = grid
-    rng = np.random.default_rng(D * 1000 + H + W + epi)
-    x = _rand_bf16(rng, (D, H, W, 32))
-    w = _rand_bf16(rng, (27, 32, 32), 0.2)
-    b = rng.standard_normal(32).astype(np.float32).astype(np.float64)
-    xd = _dev_act(torch, x, 32)
+    rng = np.random.default_rng(D * 1000 + H + W + epi + 7 * cin + cout)
+    x = _rand_bf16(rng, (D, H, W, cin))
+    w = _rand_bf16(rng, (27, cin, cout), 0.2)
+    b = rng.standard_normal(cout).astype(np.float32).astype(np.float64)
+    cip, cop = _pad(cin), _pad(cout)
+    xd = _dev_act(torch, x, cip)
     wp, _ = _packed(torch, gs, w, 0)
-    bd = torch.from_numpy(b.astype(np.float32)).cuda()
-    odt = torch.float32 if epi == 3 else torch.bfloat16
-    out = torch.zeros((D, H, W, 32), dtype=odt, device="cuda")
+    bd = torch.zeros(cop, dtype=torch.float32, device="cuda")
+    bd[:cout] = torch.from_numpy(b.astype(np.float32))
+    if epi == 0:
+        out = torch.zeros((D, H, W, cop), dtype=torch.bfloat16, device="cuda")
+    elif epi == 1:
+        out = torch.zeros((D, H, W, cout), dtype=torch.float32, device="cuda")
+    else:
+        out = torch.zeros((D, H, W, cop), dtype=torch.float32, device="cuda")
     before = _tc_timeouts(gs)
-    assert gs.lib().sur_conv3d(D, H, W, 32, 32, xd.data_ptr(), wp.data_ptr(), bd.data_ptr(), epi, None,
-                               out.data_ptr(), 32, None) == 0
+    assert gs.lib().sur_conv3d(D, H, W, cip, cop, xd.data_ptr(), wp.data_ptr(), bd.data_ptr(), epi, None,
+                               out.data_ptr(), cout if epi == 1 else cop, None) == 0
     torch.cuda.synchronize()
     assert gs.lib().sur_conv_last_engine() == 2
     assert _tc_timeouts(gs) == before
     ref = oracle.conv3d_fwd(x, w, b)
     got = to_np(out)
-    if epi == 3:
-        assert _rel(got, ref) < ACC_TOL
+    if epi in (1, 3):
+        assert _rel(got[..., :cout], ref) < ACC_TOL
+        if epi == 3:
+            assert np.all(got[..., cout:] == 0.0)  # padded output channels
     else:
         refr = np.maximum(ref, 0.0)
         # BF16 output: one rounding of the FP32 sum (8 significant bits)
-        assert np.all(np.abs(got - refr) <= 2.0 ** -8 * np.abs(refr) + 1e-6 * np.max(np.abs(refr)))
+        assert np.all(np.abs(got[..., :cout] - refr) <= 2.0 ** -8 * np.abs(refr) + 1e-6 * np.max(np.abs(refr)))
 
 
-def test_conv_input_gradient_tcgen05(tc_engine):
+@pytest.mark.parametrize("cin,cout", [(32, 32), (32, 2)])
+def test_conv_input_gradient_tcgen05(tc_engine, cin, cout):
+    """Input gradient (mirrored taps, transposed weights) of a cin -> cout
+    layer on tcgen05: a cout -> cin convolution, raw and ReLU-masked."""
     torch, gs = tc_engine
     D, H, W = 4, 16, 16
-    rng = np.random.default_rng(77)
-    dy = _rand_bf16(rng, (D, H, W, 32))
-    w = _rand_bf16(rng, (27, 32, 32), 0.2)
-    dyd = _dev_act(torch, dy, 32)
+    rng = np.random.default_rng(77 + cout)
+    dy = _rand_bf16(rng, (D, H, W, cout))
+    w = _rand_bf16(rng, (27, cin, cout), 0.2)
+    cip, cop = _pad(cin), _pad(cout)
+    dyd = _dev_act(torch, dy, cop)
     wp, _ = _packed(torch, gs, w, 1)
-    out = torch.zeros((D, H, W, 32), dtype=torch.float32, device="cuda")
-    assert gs.lib().sur_conv3d(D, H, W, 32, 32, dyd.data_ptr(), wp.data_ptr(), None, 3, None, out.data_ptr(), 32,
+    out = torch.zeros((D, H, W, cip), dtype=torch.float32, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, cop, cip, dyd.data_ptr(), wp.data_ptr(), None, 3, None, out.data_ptr(), cip,
                                None) == 0
     torch.cuda.synchronize()
     assert gs.lib().sur_conv_last_engine() == 2
     ref = oracle.conv3d_dgrad(dy, w)
-    assert _rel(to_np(out), ref) < ACC_TOL
-    mask = _rand_bf16(rng, (D, H, W, 32))
-    md = _dev_act(torch, mask, 32)
-    outb = torch.zeros((D, H, W, 32), dtype=torch.bfloat16, device="cuda")
-    assert gs.lib().sur_conv3d(D, H, W, 32, 32, dyd.data_ptr(), wp.data_ptr(), None, 2, md.data_ptr(),
-                               outb.data_ptr(), 32, None) == 0
+    assert _rel(to_np(out)[..., :cin], ref) < ACC_TOL
+    mask = _rand_bf16(rng, (D, H, W, cin))
+    md = _dev_act(torch, mask, cip)
+    outb = torch.zeros((D, H, W, cip), dtype=torch.bfloat16, device="cuda")
+    assert gs.lib().sur_conv3d(D, H, W, cop, cip, dyd.data_ptr(), wp.data_ptr(), None, 2, md.data_ptr(),
+                               outb.data_ptr(), cip, None) == 0
     torch.cuda.synchronize()
     refm = ref * (mask > 0)
-    gotm = to_np(outb)
+    gotm = to_np(outb)[..., :cin]
     assert np.all(np.abs(gotm - refm) <= 2.0 ** -8 * np.abs(refm) + 1e-6 * np.max(np.abs(refm)))
     assert _tc_timeouts(gs) == 0
 
