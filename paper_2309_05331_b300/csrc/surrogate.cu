@@ -24,6 +24,7 @@
 #include "../../include/gs.h"
 #include "host_util.h"
 #include "sur_conv_tc.cuh"
+#include "sur_wgrad_tc.cuh"
 #include "sur_conv.cuh"
 
 using namespace sur;
@@ -352,7 +353,20 @@ cudaError_t launch_wgrad(int cinp, int coutp, int D, int H, int W, const void* x
     const auto* xb = static_cast<const __nv_bfloat16*>(x);
     const auto* yb = static_cast<const __nv_bfloat16*>(dy);
     if (cinp == 8 && coutp == 32) return launch_wgrad_t<8, 32>(D, H, W, xb, yb, ws, s);
-    if (cinp == 32 && coutp == 32) return launch_wgrad_t<32, 32>(D, H, W, xb, yb, ws, s);
+    if (cinp == 32 && coutp == 32) {
+        if (g_conv_engine != 1 && H % wtc::TY == 0 && W % wtc::TX == 0) {
+            g_conv_last_engine = 2;
+            // one CTA per SM (all 512 TMEM columns; see launch_conv_tc_t)
+            const size_t smem = std::max(wtc::SMEM_BYTES, (size_t)120 * 1024);
+            cudaError_t e = cudaFuncSetAttribute(wtc::conv_wgrad_tc_kernel,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            wtc::conv_wgrad_tc_kernel<<<wgrad_grid(), wtc::NTHREADS, smem, s>>>(xb, yb, ws, D, H, W);
+            return cudaGetLastError();
+        }
+        g_conv_last_engine = 1;
+        return launch_wgrad_t<32, 32>(D, H, W, xb, yb, ws, s);
+    }
     if (cinp == 32 && coutp == 8) return launch_wgrad_t<32, 8>(D, H, W, xb, yb, ws, s);
     return cudaErrorInvalidValue;
 }

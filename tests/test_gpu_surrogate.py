@@ -318,6 +318,30 @@ def test_conv_input_gradient_tcgen05(tc_engine, cin, cout):
     assert _tc_timeouts(gs) == 0
 
 
+@pytest.mark.parametrize("grid", TC_GRIDS + [(2, 16, 16), (2, 32, 32), (6, 16, 48)])
+def test_conv_weight_gradient_tcgen05(tc_engine, grid):
+    """32 x 32 weight gradient on tcgen05 (one MMA spans four z-shifts)
+    against the oracle, including depth 2, where the tile's z-halo wraps onto
+    its own plane."""
+    torch, gs = tc_engine
+    D, H, W = grid
+    rng = np.random.default_rng(101 + D * 7 + H + W)
+    x = _rand_bf16(rng, (D, H, W, 32))
+    dy = _rand_bf16(rng, (D, H, W, 32))
+    xd, dyd = _dev_act(torch, x, 32), _dev_act(torch, dy, 32)
+    nb = gs.lib().sur_wgrad_workspace_bytes(32, 32)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    dw = torch.zeros((27, 32, 32), dtype=torch.float32, device="cuda")
+    before = _tc_timeouts(gs)
+    assert gs.lib().sur_conv3d_wgrad(D, H, W, 32, 32, xd.data_ptr(), dyd.data_ptr(), 32, 32, dw.data_ptr(),
+                                     ws.data_ptr(), nb, None) == 0
+    torch.cuda.synchronize()
+    assert gs.lib().sur_conv_last_engine() == 2
+    assert _tc_timeouts(gs) == before
+    ref, _ = oracle.conv3d_wgrad(x, dy)
+    assert _rel(to_np(dw), ref) < ACC_TOL
+
+
 def test_conv_engines_agree(tc_engine):
     """Both engines on the same inputs: equal up to FP32 summation order."""
     torch, gs = tc_engine
