@@ -253,8 +253,8 @@ def extra_workloads(torch, gs, si):
 def batched_workload(torch, gs, si, count=512, t_end=20.0):
     """512 uneven Gray-Scott instances (edges U{16..96} per axis, F in
     [0.02,0.06], k in [0.04,0.07]), adaptive Dopri5 atol=rtol=1e-6 to t=20,
-    FP32 state / FP64 control: the batched ensemble (one persistent launch per
-    stage) against the plain per-instance loop of the single-grid integrator
+    FP32 state / FP64 control: the batched ensemble (persistent launches per
+    stage and instance group) against the plain per-instance loop of the single-grid integrator
     (one gs_integrate_adaptive call per instance), same tolerance."""
     import numpy as np
     insts = si.batch_instances(count, seed=3)
@@ -264,6 +264,7 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
     for i, (u, v) in enumerate(inits):
         b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
     tile = b.autotune()
+    groups = b.grouping()
     stream = torch.cuda.current_stream()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -298,7 +299,8 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
     b.close()
     return {"gs_batched_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_b, "cell_steps_per_s": work_b / (ms_b * 1e-3), "accepted_total": int(rb["n_acc"].sum()),
-        "rejected_total": int(rb["n_rej"].sum()), "cells_total": int(cells.sum()), "tile_ty_zc": [tile[0], tile[1]]},
+        "rejected_total": int(rb["n_rej"].sum()), "cells_total": int(cells.sum()), "tile_ty_zc": [tile[0], tile[1]],
+        "instance_groups": groups[1], "group_budget_cells": groups[0]},
         "gs_per_instance_loop_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_s, "cell_steps_per_s": work_s / (ms_s * 1e-3), "accepted_total": int(acc_s.sum())},
         "batched_speedup_vs_per_instance_loop": (work_b / ms_b) / (work_s / ms_s),

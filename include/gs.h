@@ -248,6 +248,15 @@ gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double*
 /* Segment shape: ty rows (2,4,6,8,14; stage 7 uses at most 6) of 32 cells,
  * zc planes (1..1024). */
 gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc);
+/* Cache blocking by instance group: each attempt runs stages 2..7 over one
+ * group of consecutive instances at a time, so a group's stage fields are
+ * re-read from L2 instead of HBM.  cells_per_group: the group budget (a
+ * group holds at least one instance); -1 = half the L2 over the working set
+ * of a cell (state and stage fields, 18 values); 0 (the default) = one group
+ * (every stage over all instances).  gsb_get_grouping: the budget in
+ * use and the number of groups.  gsb_autotune also chooses the grouping. */
+gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group);
+gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* ngroups);
 
 /* Project autotuner for the batched kernels: times one Dormand-Prince attempt
  * of the bound ensemble for each candidate segment shape and keeps the

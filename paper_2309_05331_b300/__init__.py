@@ -86,6 +86,8 @@ _SIGNATURES = {
     "gsb_integrate_adaptive": ([_vp, C.c_double, C.c_double, _dp, C.c_double, _dp, C.c_long, _lp, _lp,
                                 C.POINTER(C.c_int)], C.c_int),
     "gsb_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gsb_set_grouping": ([_vp, C.c_longlong], C.c_int),
+    "gsb_get_grouping": ([_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gsb_last_error": ([_vp], C.c_char_p),
     "sur_param_count": ([], C.c_long),
@@ -437,6 +439,16 @@ class GrayScottBatch:
         a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
         _bcheck(lib().gsb_autotune(self.ctx, C.byref(a), C.byref(b), C.byref(ms)), self.ctx)
         return a.value, b.value, ms.value
+
+    def set_grouping(self, cells_per_group):
+        """Instance-group budget in cells (-1 automatic, 0 one group)."""
+        _bcheck(lib().gsb_set_grouping(self.ctx, cells_per_group), self.ctx)
+
+    def grouping(self):
+        """(budget in cells, number of groups) in use."""
+        c, n = C.c_longlong(0), C.c_int(0)
+        _bcheck(lib().gsb_get_grouping(self.ctx, C.byref(c), C.byref(n)), self.ctx)
+        return c.value, n.value
 
     def close(self):
         if self.ctx:

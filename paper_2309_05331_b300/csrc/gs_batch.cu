@@ -12,6 +12,13 @@
 // controller kernel (one thread per instance) then accepts or rejects every
 // instance, picks its next step and sets the loop condition of the CUDA graph
 // (WHILE any instance is still running).
+//
+// Cache blocking by instance group: a whole batch's stage fields are many
+// times the L2, but one instance's are small.  The instances are split into
+// consecutive groups whose working set (state, stage fields) fits a budget
+// of L2, and each attempt runs stages 2..7 group by group: a group's k2..k6
+// are written and read again while they are still in L2, so HBM sees little
+// more than each group's state, k1 and results.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -41,8 +48,11 @@ struct BSeg {
     int inst, col, z0, z1;
 };
 
-constexpr int kBFields = 8;   // 0: second state buffer; 1..7: stage fields
-constexpr int kCounters = 8;  // segment counters: k1, stages 2..7
+constexpr int kBFields = 8;    // 0: second state buffer; 1..7: stage fields
+constexpr int kStageCtrs = 6;  // segment counters per group: stages 2..7 (counter 0: the k1 stage)
+// working set of a cell in units of the element size: state and second
+// buffer, k1..k7, two components each
+constexpr int kCellFields = 2 * 9;
 
 template <typename T, int NK, int MODE>
 __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
@@ -88,8 +98,9 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
 }
 
 // One thread per instance: accept / reject, next step, stop.  Resets the
-// stage segment counters for the next attempt and sets the loop condition.
-__global__ void __launch_bounds__(1024) gsb_controller_kernel(DevCtrl* ctrls, int n, unsigned int* counters,
+// stage segment counters (1 .. nctr-1) for the next attempt and sets the
+// loop condition.
+__global__ void __launch_bounds__(1024) gsb_controller_kernel(DevCtrl* ctrls, int n, unsigned int* counters, int nctr,
                                                               unsigned long long cond, int use_cond) {
     int active = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -102,7 +113,7 @@ __global__ void __launch_bounds__(1024) gsb_controller_kernel(DevCtrl* ctrls, in
         active |= c->done ? 0 : 1;
     }
     active = __syncthreads_or(active);
-    if (threadIdx.x >= 1 && threadIdx.x < kCounters) counters[threadIdx.x] = 0u;
+    for (int i = 1 + threadIdx.x; i < nctr; i += blockDim.x) counters[i] = 0u;
     if (threadIdx.x == 0 && use_cond) cudaGraphSetConditional((cudaGraphConditionalHandle)cond, active ? 1u : 0u);
 }
 
@@ -141,6 +152,9 @@ struct gsb_ctx {
     BSeg* dseg[2] = {nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles
     int nseg[2] = {0, 0};
     int ty = 6, zc = 16;
+    long long group_cells = 0;            // cells per group: -1 automatic (half the L2), 0 one group
+    std::vector<int> gseg0[2], gsegn[2];  // per group: first segment and count in each list
+    int ngroups = 1, nctr = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     char err[512] = {0};
@@ -166,18 +180,48 @@ static void bdrop_graph(gsb_ctx* ctx) {
     ctx->graph = nullptr;
 }
 
-// segment lists for rows-per-CTA ty (stages) and min(ty, 6) (stage 7)
+static long long budget_cells(const gsb_ctx* ctx) {
+    if (ctx->group_cells >= 0) return ctx->group_cells;
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, ctx->dev);
+    return std::max<long long>(1, (long long)l2 / 2 / ((long long)kCellFields * (long long)ctx->esz));
+}
+
+// segment lists for rows-per-CTA ty (stages) and min(ty, 6) (stage 7), and
+// the instance groups (consecutive instances, at most budget_cells cells,
+// at least one instance each)
 static gs_status build_segments(gsb_ctx* ctx) {
+    std::vector<int> first_inst;  // first instance of each group
+    {
+        const long long budget = budget_cells(ctx);
+        long long acc = 0;
+        for (int i = 0; i < ctx->count; ++i) {
+            const BInst& in = ctx->hinst[i];
+            const long long n = (long long)in.nx * in.ny * in.nz;
+            if (i == 0 || (budget > 0 && acc + n > budget && acc > 0)) {
+                first_inst.push_back(i);
+                acc = 0;
+            }
+            acc += n;
+        }
+    }
+    ctx->ngroups = (int)first_inst.size();
     for (int li = 0; li < 2; ++li) {
         const int ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
         std::vector<BSeg> v;
+        ctx->gseg0[li].assign(ctx->ngroups, 0);
+        ctx->gsegn[li].assign(ctx->ngroups, 0);
+        int g = 0;
         for (int i = 0; i < ctx->count; ++i) {
+            if (g + 1 < ctx->ngroups && i == first_inst[g + 1]) ++g;
+            if (i == first_inst[g]) ctx->gseg0[li][g] = (int)v.size();
             const BInst& in = ctx->hinst[i];
             const int ncol = ((in.nx + 31) / 32) * ((in.ny + ty - 1) / ty);
             // z-chunk major: segments taken one after another cover the same
             // planes of neighbouring columns, so their halos meet in L2
             for (int z0 = 0; z0 < in.nz; z0 += ctx->zc)
                 for (int col = 0; col < ncol; ++col) v.push_back(BSeg{i, col, z0, std::min(in.nz, z0 + ctx->zc)});
+            ctx->gsegn[li][g] = (int)v.size() - ctx->gseg0[li][g];
         }
         if (ctx->dseg[li]) cudaFree(ctx->dseg[li]);
         ctx->dseg[li] = nullptr;
@@ -185,12 +229,25 @@ static gs_status build_segments(gsb_ctx* ctx) {
         BCK(cudaMemcpy(ctx->dseg[li], v.data(), sizeof(BSeg) * v.size(), cudaMemcpyHostToDevice));
         ctx->nseg[li] = (int)v.size();
     }
+    const int nctr = 1 + kStageCtrs * ctx->ngroups;
+    if (nctr != ctx->nctr) {
+        if (ctx->counters) cudaFree(ctx->counters);
+        ctx->counters = nullptr;
+        ctx->nctr = 0;
+        BCK(cudaMalloc(&ctx->counters, sizeof(unsigned int) * nctr));
+        ctx->nctr = nctr;
+    }
+    BCK(cudaMemset(ctx->counters, 0, sizeof(unsigned int) * nctr));
     return GS_OK;
 }
 
+// launch over segments [seg0, seg0 + nseg) of the tile list of this mode,
+// taken from the segment counter `counter`
 template <typename T, int NK, int MODE>
-static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int slot) {
+static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int group, int counter) {
     const int li = MODE == MODE_STAGE ? 0 : 1;
+    const int seg0 = group < 0 ? 0 : ctx->gseg0[li][group];
+    const int nseg = group < 0 ? ctx->nseg[li] : ctx->gsegn[li][group];
     A.ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
     auto kern = gsb_stage_kernel<T, NK, MODE>;
     const size_t smem = wide_smem_bytes<T, 1>(A.ty);
@@ -200,31 +257,31 @@ static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int slot
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 2), smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
-    const int grid = std::max(1, std::min(ctx->nseg[li], ctx->nsm * occ));
-    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[li], ctx->nseg[li],
-                                                ctx->counters + slot, A);
+    const int grid = std::max(1, std::min(nseg, ctx->nsm * occ));
+    kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[li] + seg0, nseg,
+                                                ctx->counters + counter, A);
     return cudaGetLastError();
 }
 
 template <int NK, int MODE>
-static cudaError_t blaunch_nk(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int slot) {
-    if (ctx->prec == GS_FP64) return blaunch_t<double, NK, MODE>(ctx, s, A, slot);
-    return blaunch_t<float, NK, MODE>(ctx, s, A, slot);
+static cudaError_t blaunch_nk(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int g, int slot) {
+    if (ctx->prec == GS_FP64) return blaunch_t<double, NK, MODE>(ctx, s, A, g, slot);
+    return blaunch_t<float, NK, MODE>(ctx, s, A, g, slot);
 }
 
-static cudaError_t blaunch(gsb_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, int slot) {
+static cudaError_t blaunch(gsb_ctx* ctx, cudaStream_t s, int nk, int mode, const StageArgs& A, int g, int slot) {
     if (mode == MODE_STAGE) {
         switch (nk) {
-            case 0: return blaunch_nk<0, MODE_STAGE>(ctx, s, A, slot);
-            case 1: return blaunch_nk<1, MODE_STAGE>(ctx, s, A, slot);
-            case 2: return blaunch_nk<2, MODE_STAGE>(ctx, s, A, slot);
-            case 3: return blaunch_nk<3, MODE_STAGE>(ctx, s, A, slot);
-            case 4: return blaunch_nk<4, MODE_STAGE>(ctx, s, A, slot);
-            case 5: return blaunch_nk<5, MODE_STAGE>(ctx, s, A, slot);
+            case 0: return blaunch_nk<0, MODE_STAGE>(ctx, s, A, g, slot);
+            case 1: return blaunch_nk<1, MODE_STAGE>(ctx, s, A, g, slot);
+            case 2: return blaunch_nk<2, MODE_STAGE>(ctx, s, A, g, slot);
+            case 3: return blaunch_nk<3, MODE_STAGE>(ctx, s, A, g, slot);
+            case 4: return blaunch_nk<4, MODE_STAGE>(ctx, s, A, g, slot);
+            case 5: return blaunch_nk<5, MODE_STAGE>(ctx, s, A, g, slot);
             default: return cudaErrorInvalidValue;
         }
     }
-    if (mode == MODE_DOPRI_FINAL && nk == 5) return blaunch_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, slot);
+    if (mode == MODE_DOPRI_FINAL && nk == 5) return blaunch_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, g, slot);
     return cudaErrorInvalidValue;
 }
 
@@ -248,8 +305,10 @@ static Slot bpair(gsb_ctx* c, int fa, int fb, int sel) {
     return s;
 }
 
-// stage st (1 = k1, 2..7): same buffers and coefficients as the single grid
-static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st) {
+// stage st (1 = k1, 2..7) of instance group g (k1: every instance, g < 0):
+// same buffers and coefficients as the single grid
+static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st, int g) {
+    const int ctr = st == 1 ? 0 : 1 + kStageCtrs * g + (st - 2);
     const Slot k1 = bpair(ctx, 1, 2, SEL_CUR);
     const Slot k[7] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4), bfld(ctx, 5), bfld(ctx, 6), bfld(ctx, 7)};
     static const double A2[1] = {dp5::A21};
@@ -263,7 +322,7 @@ static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st) {
     A.u = bstate(ctx, SEL_CUR);
     if (st == 1) {
         A.out0 = k1;
-        return blaunch(ctx, s, 0, MODE_STAGE, A, 0);
+        return blaunch(ctx, s, 0, MODE_STAGE, A, -1, 0);
     }
     if (st < 7) {
         const int nk = st - 1;
@@ -272,7 +331,7 @@ static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st) {
             A.a[j] = rows[st - 2][j];
         }
         A.out0 = k[st];
-        return blaunch(ctx, s, nk, MODE_STAGE, A, st - 1);
+        return blaunch(ctx, s, nk, MODE_STAGE, A, g, ctr);
     }
     A.kin[0] = k[1];
     A.kin[1] = k[3];
@@ -287,17 +346,19 @@ static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st) {
     A.out0 = bstate(ctx, SEL_NEXT);
     A.out1 = bpair(ctx, 1, 2, SEL_NEXT);
     A.has_out1 = 1;
-    return blaunch(ctx, s, 5, MODE_DOPRI_FINAL, A, 6);
+    return blaunch(ctx, s, 5, MODE_DOPRI_FINAL, A, g, ctr);
 }
 
 static cudaError_t bbody(gsb_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond, bool with_ctrl) {
-    for (int st = 2; st <= 7; ++st) {
-        cudaError_t e = blaunch_dopri5_stage(ctx, s, st);
-        if (e != cudaSuccess) return e;
+    for (int g = 0; g < ctx->ngroups; ++g) {
+        for (int st = 2; st <= 7; ++st) {
+            cudaError_t e = blaunch_dopri5_stage(ctx, s, st, g);
+            if (e != cudaSuccess) return e;
+        }
     }
     if (!with_ctrl) return cudaSuccess;
     const int threads = std::min(1024, std::max(32, (ctx->count + 31) / 32 * 32));
-    gsb_controller_kernel<<<1, threads, 0, s>>>(ctx->dctrl, ctx->count, ctx->counters, h, use_cond);
+    gsb_controller_kernel<<<1, threads, 0, s>>>(ctx->dctrl, ctx->count, ctx->counters, ctx->nctr, h, use_cond);
     return cudaGetLastError();
 }
 
@@ -388,7 +449,6 @@ gs_status gsb_create(int count, const gsb_instance* inst, double L, double Du, d
         if ((e = cudaMalloc(&ctx->dctrl, sizeof(DevCtrl) * count)) != cudaSuccess) break;
         if ((e = cudaMemset(ctx->dctrl, 0, sizeof(DevCtrl) * count)) != cudaSuccess) break;
         if ((e = cudaMallocHost(&ctx->hctrl, sizeof(DevCtrl) * count)) != cudaSuccess) break;
-        if ((e = cudaMalloc(&ctx->counters, sizeof(unsigned int) * kCounters)) != cudaSuccess) break;
     } while (0);
     if (e == cudaSuccess && st == GS_OK) st = build_segments(ctx);
     if (e != cudaSuccess || st != GS_OK) {
@@ -441,6 +501,21 @@ gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc) {
     return build_segments(ctx);
 }
 
+gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group) {
+    if (!ctx || cells_per_group < -1) return GS_ERR_INVALID;
+    if (cells_per_group == ctx->group_cells) return GS_OK;
+    bdrop_graph(ctx);
+    ctx->group_cells = cells_per_group;
+    return build_segments(ctx);
+}
+
+gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* ngroups) {
+    if (!ctx) return GS_ERR_INVALID;
+    if (cells_per_group) *cells_per_group = budget_cells(ctx);
+    if (ngroups) *ngroups = ctx->ngroups;
+    return GS_OK;
+}
+
 gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double* t, double t_end, double* dt,
                                  long max_accepted, long* n_acc, long* n_rej, int* status) {
     if (!ctx || !t || !dt || !ctx->state[0]) return GS_ERR_INVALID;
@@ -479,8 +554,8 @@ gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double*
     }
     BCK(cudaMemcpyAsync(ctx->dctrl, ctx->hctrl, sizeof(DevCtrl) * ctx->count, cudaMemcpyHostToDevice, ctx->stream));
     if (active > 0) {
-        BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * kCounters, ctx->stream));
-        BCK(blaunch_dopri5_stage(ctx, ctx->stream, 1));
+        BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * ctx->nctr, ctx->stream));
+        BCK(blaunch_dopri5_stage(ctx, ctx->stream, 1, -1));
         cudaGraphExec_t ex;
         gs_status st = bget_graph(ctx, &ex);
         if (st != GS_OK) return st;
@@ -510,9 +585,36 @@ gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double*
     return first;
 }
 
+// device time of one attempt round (k1 stage + stages 2..7 of every group)
+// with the current tile and grouping, averaged over 2 runs after a warm-up
+static gs_status time_round(gsb_ctx* ctx, cudaEvent_t e0, cudaEvent_t e1, float* out) {
+    float acc = 0.f;
+    for (int r = 0; r < 3; ++r) {
+        BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * ctx->nctr, ctx->stream));
+        BCK(cudaEventRecord(e0, ctx->stream));
+        cudaError_t e = blaunch_dopri5_stage(ctx, ctx->stream, 1, -1);
+        if (e == cudaSuccess) e = bbody(ctx, ctx->stream, 0, 0, false);
+        if (e != cudaSuccess) {
+            bset_err(ctx, e, "gsb_autotune");
+            return GS_ERR_CUDA;
+        }
+        BCK(cudaEventRecord(e1, ctx->stream));
+        BCK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BCK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) acc += ms;  // repetition 0 warms up
+    }
+    *out = acc / 2;
+    return GS_OK;
+}
+
 gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
-    static const int cand[][2] = {{4, 8}, {4, 16}, {6, 8}, {6, 16}, {6, 32}, {8, 8}, {8, 16}, {14, 8}, {14, 16}};
+    // the timing round has every instance running; a real integration also
+    // has sparse rounds (finished instances' segments are still walked), so
+    // only z-chunks of 16 planes or more are candidates (measured on 512
+    // uneven instances to t = 20: zc = 8 took 119 ms, zc = 32 101 ms)
+    static const int cand[][2] = {{4, 16}, {6, 16}, {6, 32}, {6, 64}, {8, 32}, {14, 16}, {14, 32}};
     // control blocks for timing: every instance running, parity 0, dt 1e-3
     for (int i = 0; i < ctx->count; ++i) {
         DevCtrl* h = ctx->hctrl + i;
@@ -528,42 +630,44 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) 
     cudaEvent_t e0, e1;
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
-    const int old_ty = ctx->ty, old_zc = ctx->zc;
     float best = 1e30f;
-    int bty = old_ty, bzc = old_zc;
+    int bty = ctx->ty, bzc = ctx->zc;
     gs_status st = GS_OK;
     for (const auto& c : cand) {
-        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK) break;
-        float acc = 0.f;
-        for (int r = 0; r < 3 && st == GS_OK; ++r) {
-            BCK(cudaMemsetAsync(ctx->counters, 0, sizeof(unsigned int) * kCounters, ctx->stream));
-            BCK(cudaEventRecord(e0, ctx->stream));
-            cudaError_t e = blaunch_dopri5_stage(ctx, ctx->stream, 1);
-            if (e == cudaSuccess) e = bbody(ctx, ctx->stream, 0, 0, false);
-            if (e != cudaSuccess) {
-                bset_err(ctx, e, "gsb_autotune");
-                st = GS_ERR_CUDA;
-                break;
-            }
-            BCK(cudaEventRecord(e1, ctx->stream));
-            BCK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            BCK(cudaEventElapsedTime(&ms, e0, e1));
-            if (r > 0) acc += ms;  // repetition 0 warms up
-        }
-        if (st != GS_OK) break;
-        if (acc / 2 < best) {
-            best = acc / 2;
+        float ms = 0.f;
+        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK) break;
+        if (ms < best) {
+            best = ms;
             bty = c[0];
             bzc = c[1];
+        }
+    }
+    // instance grouping for the chosen tile: one group, or groups of a
+    // quarter, half, one or two times the automatic (half-L2) budget (on the
+    // 512-instance ensemble one group wins: 101 ms against 172-450 ms, the
+    // per-group launches being too small to fill the GPU)
+    long long bgroup = ctx->group_cells;
+    if (st == GS_OK && (st = gsb_set_tile(ctx, bty, bzc)) == GS_OK) {
+        const long long saved = ctx->group_cells;
+        ctx->group_cells = -1;
+        const long long autob = budget_cells(ctx);
+        ctx->group_cells = saved;
+        const long long gcand[5] = {0, autob / 4, autob / 2, autob, 2 * autob};
+        best = 1e30f;
+        for (long long gc : gcand) {
+            float ms = 0.f;
+            if ((st = gsb_set_grouping(ctx, gc)) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK) break;
+            if (ms < best) {
+                best = ms;
+                bgroup = gc;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != GS_OK) return st;
-    (void)old_ty;
-    (void)old_zc;
     if ((st = gsb_set_tile(ctx, bty, bzc)) != GS_OK) return st;
+    if ((st = gsb_set_grouping(ctx, bgroup)) != GS_OK) return st;
     if (ty_out) *ty_out = bty;
     if (zc_out) *zc_out = bzc;
     if (best_ms) *best_ms = best;

@@ -120,6 +120,44 @@ def test_batched_segment_shape_does_not_change_results(tile):
         assert np.array_equal(a, c)
 
 
+@pytest.mark.parametrize("group_cells", [1, 2000, 30000, 0])
+def test_instance_grouping_does_not_change_results(group_cells):
+    """Stages run group by group (cache blocking): every grouping, from one
+    instance per group to a single group, gives bit-identical results (each
+    instance's arithmetic and max-norm are independent of the order)."""
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=17)
+    res = []
+    for gc in (0, group_cells):
+        b = _batch(torch, SMALL, inits, 0)
+        b.set_grouping(gc)
+        budget, ngroups = b.grouping()
+        if gc == 1:
+            assert ngroups == len(SMALL)  # at least one instance per group
+        if gc == 0:
+            assert ngroups == 1
+        r = b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
+        res.append(([to_np(x) for i in range(len(SMALL)) for x in b.view(i)], r["n_acc"].copy(), r["n_rej"].copy()))
+        b.close()
+    (a0, acc0, rej0), (a1, acc1, rej1) = res
+    assert np.array_equal(acc0, acc1) and np.array_equal(rej0, rej1)
+    for a, c in zip(a0, a1):
+        assert np.array_equal(a, c)
+
+
+def test_grouping_rejects_invalid_budget():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    inits = _inits(SMALL, seed0=1)
+    b = _batch(torch, SMALL, inits, 0)
+    with pytest.raises(gs.GSError):
+        b.set_grouping(-2)
+    b.set_grouping(-1)
+    budget, ngroups = b.grouping()
+    assert budget > 0 and ngroups >= 1
+    b.close()
+
+
 def test_batched_max_accepted_and_per_instance_times():
     torch = cuda_or_skip()
     inits = _inits(SMALL, seed0=3)
