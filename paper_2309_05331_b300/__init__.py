@@ -87,6 +87,7 @@ _SIGNATURES = {
                                 C.POINTER(C.c_int)], C.c_int),
     "gsb_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gsb_set_grouping": ([_vp, C.c_longlong], C.c_int),
+    "gsb_set_stage_depth": ([_vp, C.c_int], C.c_int),
     "gsb_get_grouping": ([_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
     "gsb_last_error": ([_vp], C.c_char_p),
@@ -439,6 +440,10 @@ class GrayScottBatch:
         a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
         _bcheck(lib().gsb_autotune(self.ctx, C.byref(a), C.byref(b), C.byref(ms)), self.ctx)
         return a.value, b.value, ms.value
+
+    def set_stage_depth(self, depth):
+        """Staged-form ring depth of the stage kernels (0: vectorised form)."""
+        _bcheck(lib().gsb_set_stage_depth(self.ctx, depth), self.ctx)
 
     def set_grouping(self, cells_per_group):
         """Instance-group budget in cells (-1 automatic, 0 one group)."""

@@ -11,7 +11,9 @@
 // folds each segment's error maximum into its instance's accumulator; a
 // controller kernel (one thread per instance) then accepts or rejects every
 // instance, picks its next step and sets the loop condition of the CUDA graph
-// (WHILE any instance is still running).
+// (WHILE any instance is still running).  With a ring depth d > 0 the
+// segment code is the staged form (each thread copies its inputs d planes
+// ahead into shared memory with cp.async), else the vectorised form.
 //
 // Cache blocking by instance group: a whole batch's stage fields are many
 // times the L2, but one instance's are small.  The instances are split into
@@ -30,6 +32,7 @@
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_staged.cuh"
 #include "gs_wide.cuh"
 #include "host_util.h"
 
@@ -57,9 +60,10 @@ constexpr int kCellFields = 2 * 9;
 template <typename T, int NK, int MODE>
 __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
     gsb_stage_kernel(const BInst* __restrict__ insts, DevCtrl* ctrls, const BSeg* __restrict__ segs, int nseg,
-                     unsigned int* counter, const StageArgs A) {
+                     unsigned int* counter, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* S = reinterpret_cast<T*>(smem_raw);
+    unsigned char* R = smem_raw + (wide_smem_bytes<T, 1>(A.ty) + 15) / 16 * 16;  // staged form's ring
     __shared__ T red[32];
     __shared__ int s_seg;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
@@ -88,7 +92,11 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
         const StageCoef<T, NK> C = stage_coef<T, NK>(A, c->dt_try, c->atol, c->rtol);
         const int ntx = (in.nx + 31) / 32;
         typename ErrBits<T>::U ebits = 0;
-        wide_segment<T, NK, MODE, 1>(g, P, C, S, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1, ebits);
+        if (depth > 0)
+            staged_segment<T, NK, MODE, 1>(g, P, C, S, R, depth, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1,
+                                           ebits);
+        else
+            wide_segment<T, NK, MODE, 1>(g, P, C, S, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1, ebits);
         const T emax = ErrBits<T>::value(ebits);
         if (MODE == MODE_DOPRI_FINAL) {
             const T bmax = block_nanmax(emax, red);
@@ -152,6 +160,7 @@ struct gsb_ctx {
     BSeg* dseg[2] = {nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles
     int nseg[2] = {0, 0};
     int ty = 6, zc = 16;
+    int depth = 0;                        // staged-form ring depth (0: vectorised form)
     long long group_cells = 0;            // cells per group: -1 automatic (half the L2), 0 one group
     std::vector<int> gseg0[2], gsegn[2];  // per group: first segment and count in each list
     int ngroups = 1, nctr = 0;
@@ -250,7 +259,7 @@ static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int grou
     const int nseg = group < 0 ? ctx->nseg[li] : ctx->gsegn[li][group];
     A.ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
     auto kern = gsb_stage_kernel<T, NK, MODE>;
-    const size_t smem = wide_smem_bytes<T, 1>(A.ty);
+    const size_t smem = ctx->depth > 0 ? staged_smem_bytes<T, NK, 1>(A.ty, ctx->depth) : wide_smem_bytes<T, 1>(A.ty);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -259,7 +268,7 @@ static cudaError_t blaunch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int grou
     if (occ < 1) occ = 1;
     const int grid = std::max(1, std::min(nseg, ctx->nsm * occ));
     kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[li] + seg0, nseg,
-                                                ctx->counters + counter, A);
+                                                ctx->counters + counter, A, ctx->depth);
     return cudaGetLastError();
 }
 
@@ -501,6 +510,14 @@ gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc) {
     return build_segments(ctx);
 }
 
+gs_status gsb_set_stage_depth(gsb_ctx* ctx, int depth) {
+    if (!ctx || depth < 0 || depth > kMaxDepth) return GS_ERR_INVALID;
+    if (depth == ctx->depth) return GS_OK;
+    bdrop_graph(ctx);
+    ctx->depth = depth;
+    return GS_OK;
+}
+
 gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group) {
     if (!ctx || cells_per_group < -1) return GS_ERR_INVALID;
     if (cells_per_group == ctx->group_cells) return GS_OK;
@@ -631,17 +648,25 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) 
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bty = ctx->ty, bzc = ctx->zc;
+    int bty = ctx->ty, bzc = ctx->zc, bdepth = ctx->depth;
     gs_status st = GS_OK;
-    for (const auto& c : cand) {
-        float ms = 0.f;
-        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK) break;
-        if (ms < best) {
-            best = ms;
-            bty = c[0];
-            bzc = c[1];
+    // the staged form copies one cell per lane (4- or 8-byte cp.async): on 512
+    // uneven instances it took 129 ms against 101 ms for the vectorised form
+    for (int depth = 0; depth <= 1 && st == GS_OK; ++depth) {
+        if ((st = gsb_set_stage_depth(ctx, depth)) != GS_OK) break;
+        for (const auto& c : cand) {
+            float ms = 0.f;
+            if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK)
+                break;
+            if (ms < best) {
+                best = ms;
+                bty = c[0];
+                bzc = c[1];
+                bdepth = depth;
+            }
         }
     }
+    if (st == GS_OK) st = gsb_set_stage_depth(ctx, bdepth);
     // instance grouping for the chosen tile: one group, or groups of a
     // quarter, half, one or two times the automatic (half-L2) budget (on the
     // 512-instance ensemble one group wins: 101 ms against 172-450 ms, the

@@ -39,6 +39,14 @@ __device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
 }
+// one vector of BYTES (4, 8: through L1; 16: L2 only)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_vec(void* smem, const void* gmem) {
+    if constexpr (BYTES == 16)
+        cp_async16(smem, gmem);
+    else
+        cp_async_small<BYTES>(smem, gmem);
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // wait until at most n of this thread's committed groups are pending (n < kMaxDepth)
 __device__ __forceinline__ void cp_async_wait_pending(int n) {
@@ -72,7 +80,7 @@ template <typename T, int NK, int MODE, int VX>
 __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const StageCoef<T, NK>& C,
                                                T* S, unsigned char* R, int depth, int TY, int tx, int tyi, int z0,
                                                int z1, typename ErrBits<T>::U& ebits) {
-    static_assert(sizeof(T) * VX == 16, "the staged form moves 16-byte vectors");
+    static_assert(sizeof(T) * VX == 4 || sizeof(T) * VX == 8 || sizeof(T) * VX == 16, "4-, 8- or 16-byte vectors");
     constexpr int TXW = 32 * VX;
     constexpr int PITCH = wide_pitch<VX>();
     constexpr int NA = staged_arrays<T, NK, VX>();
@@ -123,9 +131,10 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
             if (act) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    cp_async16(rvec(s, c * (1 + NK)), P.u[c] + cbase + zo);
+                    cp_async_vec<sizeof(VTy)>(rvec(s, c * (1 + NK)), P.u[c] + cbase + zo);
 #pragma unroll
-                    for (int j = 0; j < NK; ++j) cp_async16(rvec(s, c * (1 + NK) + 1 + j), P.k[j][c] + cbase + zo);
+                    for (int j = 0; j < NK; ++j)
+                        cp_async_vec<sizeof(VTy)>(rvec(s, c * (1 + NK) + 1 + j), P.k[j][c] + cbase + zo);
                 }
             }
             if (do_halo) {
