@@ -47,8 +47,11 @@ WORKLOAD = ("gray-scott 256^3 periodic [0,2.5]^3, Du=2e-5 Dv=1e-5 F=0.053 k=0.01
 # k3..k6 and writes y5, k7.
 STAGE_NAMES = ["k1", "stage2", "stage3", "stage4", "stage5", "stage6", "stage7"]
 STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
+# with stages 6/7 split: stage 6 reads u, k1..k5 and writes y5, the error
+# terms and the inverse error scale; stage 7 reads y5, the error terms and
+# the scale and writes k7
+STAGE_FIELDS_SPLIT = [2, 3, 4, 5, 6, 9, 4]
 BYTES_PER_FIELD_CELL = 8
-ATTEMPT_FIELDS = sum(STAGE_FIELDS[1:])  # 33 field passes per attempt (k1 is reused)
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stage-7 launch at 256^3 (profiles/gs_stage7_wide_fp32_256cubed_full.md:
@@ -422,10 +425,12 @@ def main():
     stage_cfg = gs.gs_get_stage_configs(g.ctx)
     peak, peak_kind = _peaks()
     dom = max(range(1, 7), key=lambda i: stage_ms[i])
-    dom_bytes = STAGE_FIELDS[dom] * BYTES_PER_FIELD_CELL * cells
+    fields = STAGE_FIELDS_SPLIT if gs.gs_get_dopri5_split(g.ctx) else STAGE_FIELDS
+    attempt_fields = sum(fields[1:])  # field passes per attempt (k1 is reused): 31 split, 33 unsplit
+    dom_bytes = fields[dom] * BYTES_PER_FIELD_CELL * cells
     achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
     attempt_ms = sum(stage_ms[1:])
-    attempt_gbs = ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
+    attempt_gbs = attempt_fields * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
     traffic = None
     if (NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]
             and NCU_TRAFFIC["form"] == stage_cfg[dom][0]):
@@ -433,10 +438,11 @@ def main():
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
-                "kernel": f"{STAGE_NAMES[dom]} kernel, {FORM_NAMES[stage_cfg[dom][0]]} form (FP32)",
+                "kernel": f"{STAGE_NAMES[dom]} kernel, {FORM_NAMES[stage_cfg[dom][0]]} form (FP32)"
+                          + (", stages 6/7 split" if fields is STAGE_FIELDS_SPLIT else ""),
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
                 "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
-                "attempt": {"algorithmic_bytes_per_cell": ATTEMPT_FIELDS * BYTES_PER_FIELD_CELL,
+                "attempt": {"algorithmic_bytes_per_cell": attempt_fields * BYTES_PER_FIELD_CELL,
                             "ms": attempt_ms, "achieved_gbs": attempt_gbs, "frac": attempt_gbs / peak}}
 
     line = None

@@ -184,6 +184,17 @@ gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc);
  * picks its own per kernel); a depth whose ring does not fit in shared
  * memory is reduced at launch.  gs_get_stage_depths: the depth each
  * Dormand-Prince kernel uses when it runs in form 4 (host array of 7 ints). */
+/* Split of Dormand-Prince stages 6 and 7 (staged form): stage 6 also forms
+ * the 5th-order solution y5 (b7 = 0, so y5 needs k1..k6 only), the error
+ * terms of k1..k6 and the inverse error scale, and never stores k6; stage 7
+ * evaluates k7 = F(y5) and adds its error term.  Two fewer field passes per
+ * attempt (31 instead of 33).  mode: -1 automatic (on when the staged form
+ * applies and no other kernel form is forced; the default), 0 off, 1 on
+ * (INVALID if the staged form does not apply).  Same formulas, summed in
+ * another order (y5 as (u + dt sum_{j<6} b_j k_j) + dt b6 k6).
+ * gs_get_dopri5_split: 1 if the split is in use. */
+gs_status gs_set_dopri5_split(gs_ctx* ctx, int mode);
+int gs_get_dopri5_split(const gs_ctx* ctx);
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);
 gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);
 

@@ -63,6 +63,8 @@ _SIGNATURES = {
     "gs_get_kernel_variant": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_set_stage_depth": ([_vp, C.c_int], C.c_int),
+    "gs_set_dopri5_split": ([_vp, C.c_int], C.c_int),
+    "gs_get_dopri5_split": ([_vp], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
@@ -239,6 +241,14 @@ def gs_get_stage_configs(ctx):
     f, t, z = (C.c_int * 7)(), (C.c_int * 7)(), (C.c_int * 7)()
     _check(lib().gs_get_stage_configs(ctx, f, t, z), ctx)
     return [(f[i], t[i], z[i]) for i in range(7)]
+
+
+def gs_set_dopri5_split(ctx, mode):
+    _check(lib().gs_set_dopri5_split(ctx, mode), ctx)
+
+
+def gs_get_dopri5_split(ctx):
+    return lib().gs_get_dopri5_split(ctx)
 
 
 def gs_set_stage_depth(ctx, depth):

@@ -32,7 +32,7 @@ namespace {
 
 enum GraphId { G_RK4 = 0, G_DOPRI5_FIXED, G_EULER, G_DOPRI5_ADAPT, G_AB4_START, G_AB4_MAIN, G_COUNT };
 
-constexpr int kFields = 8;  // 0: second state buffer; 1..7: stage fields
+constexpr int kFields = 9;  // 0: second state buffer; 1..7: stage fields; 8: inverse error scale (split stages 6/7)
 
 // Launch configuration of one stencil kernel.  form: 0 automatic, 1 generic
 // (one cell per thread), 2 vectorised 16-byte rows (4 FP32 / 2 FP64 cells per
@@ -67,6 +67,7 @@ struct gs_ctx {
     KCfg dp[7];             // Dormand-Prince k1 and stages 2..7 once tuned
     bool dp_tuned = false;
     int variant = 0;        // requested: 0 automatic, 1 generic, 2 vectorised, 3 vectorised 8-byte
+    int split67 = -1;       // Dormand-Prince stages 6/7 split (MODE_DOPRI_S6/S7): -1 automatic, 0 off, 1 on
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -114,6 +115,13 @@ static bool form_ok(const gs_ctx* ctx, int form) {
     return false;
 }
 static bool wide_ok(const gs_ctx* ctx) { return form_ok(ctx, 2) || form_ok(ctx, 3); }
+// Dormand-Prince stages 6 and 7 split as MODE_DOPRI_S6 / S7 (staged form):
+// automatic when the staged form applies and no other form is forced
+static bool split67_on(const gs_ctx* ctx) {
+    if (!form_ok(ctx, 4)) return false;
+    if (ctx->split67 >= 0) return ctx->split67 == 1;
+    return ctx->variant == 0 || ctx->variant == 4;
+}
 // the form a launch with configured form `form` actually uses
 static int pick_form(const gs_ctx* ctx, int form) {
     if (ctx->variant == 1) return 1;
@@ -208,6 +216,11 @@ static cudaError_t launch_generic(gs_ctx* ctx, cudaStream_t s, StageArgs A) {
 
 template <typename T, int NK, int MODE>
 static cudaError_t launch_stage_t(gs_ctx* ctx, cudaStream_t s, StageArgs A, int form, int depth) {
+    if constexpr (MODE == MODE_DOPRI_S6 || MODE == MODE_DOPRI_S7) {
+        // the split stages exist in the staged form only
+        if (!form_ok(ctx, 4)) return cudaErrorInvalidConfiguration;
+        return launch_staged<T, NK, MODE, 16 / sizeof(T)>(ctx, s, A, depth);
+    }
     form = pick_form(ctx, form);
     if (form == 4) return launch_staged<T, NK, MODE, 16 / sizeof(T)>(ctx, s, A, depth);
     if (MODE != MODE_STAGE && A.ty > kMaxTYFinal) A.ty = kMaxTYFinal;
@@ -246,6 +259,8 @@ static cudaError_t launch_stage(gs_ctx* ctx, cudaStream_t s, int nk, int mode, c
         if (nk == 1) return launch_stage_nk<1, MODE_FINAL>(ctx, s, A, cfg);
         return cudaErrorInvalidValue;
     }
+    if (mode == MODE_DOPRI_S6) return nk == 5 ? launch_stage_nk<5, MODE_DOPRI_S6>(ctx, s, A, cfg) : cudaErrorInvalidValue;
+    if (mode == MODE_DOPRI_S7) return nk == 0 ? launch_stage_nk<0, MODE_DOPRI_S7>(ctx, s, A, cfg) : cudaErrorInvalidValue;
     if (nk == 5) return launch_stage_nk<5, MODE_DOPRI_FINAL>(ctx, s, A, cfg);
     return cudaErrorInvalidValue;
 }
@@ -384,6 +399,30 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     const KCfg& cfg = dp_cfg(ctx, st - 1);
     StageArgs A = base_args(ctx, cfg);
     A.u = state_sel(ctx, SEL_CUR);
+    if (split67_on(ctx) && st >= 6) {
+        if (st == 6) {
+            // k6 in registers only: y5 -> next state, error terms -> field 7,
+            // inverse error scale -> field 8
+            for (int j = 0; j < 5; ++j) {
+                A.kin[j] = k[j + 1];
+                A.a[j] = A6[j];
+            }
+            A.out0 = state_sel(ctx, SEL_NEXT);
+            A.out1 = fld(ctx, 7);
+            A.has_out1 = 1;
+            A.out2 = fld(ctx, 8);
+            return launch_stage(ctx, s, 5, MODE_DOPRI_S6, A, cfg);
+        }
+        A.u = state_sel(ctx, SEL_NEXT);  // y5
+        A.ex[0] = fld(ctx, 7);
+        A.ex[1] = fld(ctx, 8);
+        A.n_ex = 2;
+        A.out0 = pair_sel(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
+        A.run_ctrl = 1;
+        A.cond = h;
+        A.use_cond = use_cond;
+        return launch_stage(ctx, s, 0, MODE_DOPRI_S7, A, cfg);
+    }
     if (st < 7) {
         const int nk = st - 1;
         for (int j = 0; j < nk; ++j) {
@@ -793,6 +832,16 @@ gs_status gs_get_kernel_variant(const gs_ctx* ctx, int* in_use) {
     return GS_OK;
 }
 
+gs_status gs_set_dopri5_split(gs_ctx* ctx, int mode) {
+    if (!ctx || mode < -1 || mode > 1) return GS_ERR_INVALID;
+    if (mode == 1 && !form_ok(ctx, 4)) return GS_ERR_INVALID;
+    drop_graphs(ctx);
+    ctx->split67 = mode;
+    return GS_OK;
+}
+
+int gs_get_dopri5_split(const gs_ctx* ctx) { return ctx && split67_on(ctx) ? 1 : 0; }
+
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth) {
     if (!ctx || depth < 1 || depth > kMaxDepth) return GS_ERR_INVALID;
     drop_graphs(ctx);
@@ -811,7 +860,7 @@ gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc) {
     if (!ctx || !form || !ty || !zc) return GS_ERR_INVALID;
     for (int k = 0; k < 7; ++k) {
         const KCfg& c = dp_cfg(ctx, k);
-        form[k] = pick_form(ctx, c.form);
+        form[k] = (k >= 5 && split67_on(ctx)) ? 4 : pick_form(ctx, c.form);
         ty[k] = (k == 6 && form[k] != 4 && c.ty > kMaxTYFinal) ? kMaxTYFinal : c.ty;
         zc[k] = c.zc;
     }
@@ -887,7 +936,9 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
                 best_cfg[k] = c;
             }
         };
+        const bool staged_only = k >= 5 && split67_on(ctx);
         for (int fi = 0; fi < nf && st == GS_OK; ++fi) {
+            if (staged_only && forms[fi] != 4) continue;
             if (forms[fi] == 4) {
                 for (int ty = 2; ty <= kMaxTY && st == GS_OK; ++ty)
                     for (int depth = 1; depth <= 2 && st == GS_OK; ++depth) try_cfg(KCfg{4, ty, 0, depth});

@@ -94,6 +94,9 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
     const T ew[4] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5, (T)dp5::E6};
     const T e7 = (T)dp5::E7;
     const T dte7 = dt * e7;
+    // stage 6 of the split scheme: b of k1, k3, k4, k5; e3..e5 are ew[0..2]
+    const T bw[4] = {(T)dp5::B1, (T)dp5::B3, (T)dp5::B4, (T)dp5::B5};
+    const T e67 = (T)(dp5::E6 + dp5::E7), dtb6 = dt * (T)dp5::B6, dte6 = dt * (T)dp5::E6;
     const size_t slot_bytes = staged_slot_bytes<T, NK, VX>(TY);
     const size_t vec_bytes = (size_t)TYP * NA * 32 * sizeof(VTy);
 
@@ -156,12 +159,13 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
         for (int c = 0; c < 2; ++c) {
             T uu[VX];
             lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, c * (1 + NK))), uu);
-            T sacc[VX], k1[VX], q[VX];
+            T sacc[VX], k1[VX], q[VX], sb[VX];
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
                 sacc[v] = T(0);
                 q[v] = T(0);
                 k1[v] = T(0);
+                sb[v] = T(0);
             }
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
@@ -177,6 +181,16 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
                         else
                             q[v] += ew[j - 1] * (kk[v] - k1[v]);
                     }
+                    if (MODE == MODE_DOPRI_S6) {
+                        // inputs k1..k5; b2 = e2 = 0
+                        if (j == 0) {
+                            k1[v] = kk[v];
+                            sb[v] = bw[0] * kk[v];
+                        } else if (j >= 2) {
+                            sb[v] += bw[j - 1] * kk[v];
+                            q[v] += ew[j - 2] * (kk[v] - k1[v]);
+                        }
+                    }
                 }
             }
 #pragma unroll
@@ -187,6 +201,13 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
                     // 1 / (atol + rtol (|u| + dt |k1|)) and dt (sum_{j<7} e_j (k_j - k1) - e7 k1)
                     cr.a[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v])));
                     cr.b[0][c][v] = dt * (q[v] - e7 * k1[v]);
+                }
+                if (MODE == MODE_DOPRI_S6) {
+                    // u + dt sum_{j=1,3,4,5} b_j k_j, dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1),
+                    // 1 / (atol + rtol (|u| + dt |k1|))
+                    cr.a[c][v] = uu[v] + dt * sb[v];
+                    cr.b[0][c][v] = dt * (q[v] - e67 * k1[v]);
+                    cr.b[1][c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v])));
                 }
             }
         }
@@ -209,12 +230,22 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
     if (inner) formY(0, ym, nxt);
     fetch(z0 - 1 + depth);
     cp_async_wait_pending(depth - 1);  // plane z0
+    // split stage 6: the inverse error scale of a plane is written as soon as
+    // the plane is formed (its own rows only)
+    auto put_isc = [&](int zz, const Carry<T, NK, MODE, VX>& cr) {
+        if (MODE == MODE_DOPRI_S6 && inner) {
+            const long long i = cbase + plane * zz;
+#pragma unroll
+            for (int c = 0; c < 2; ++c) stv<T, VX>(P.o2[c] + i, cr.b[MODE == MODE_DOPRI_S6 ? 1 : 0][c]);
+        }
+    };
     {
         const int s = 1 % depth;
         if (act) {
             formY(s, yc, cur);
 #pragma unroll
             for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(0, w, c, VX * lane), yc[c]);
+            put_isc(z0, cur);
         }
         if (do_halo)
             for (int c = 0; c < 2; ++c) S[sidx(0, hrow, c, hcol)] = formY1(s, c);
@@ -229,6 +260,7 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
             formY(s, yp, nxt);
 #pragma unroll
             for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
+            if (z + 1 < z1) put_isc(z + 1, nxt);
         }
         if (do_halo)
             for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = formY1(s, c);
@@ -294,6 +326,33 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
                     for (int v = 0; v < VX; ++v) o[v] = cur.a[c][v] + dt * sacc[v];
                     stv<T, VX>(P.o0[c] + i, o);
                     if (C.has_out1) stv<T, VX>(P.o1[c] + i, f[c]);
+                }
+            } else if (MODE == MODE_DOPRI_S6) {
+                // k6 = f: y5 = (u + dt sum_{j<6} b_j k_j) + dt b6 k6, error terms up to k6
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    T y5[VX], ep[VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        y5[v] = cur.a[c][v] + dtb6 * f[c][v];
+                        ep[v] = cur.b[0][c][v] + dte6 * f[c][v];
+                    }
+                    stv<T, VX>(P.o0[c] + i, y5);
+                    stv<T, VX>(P.o1[c] + i, ep);
+                }
+            } else if (MODE == MODE_DOPRI_S7) {
+                // k7 = F(y5); error = stage-6 terms + dt e7 k7, scaled
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    stv<T, VX>(P.o0[c] + i, f[c]);
+                    T ep[VX], isc[VX];
+                    ldv<T, VX>(P.ex[0][c] + i, ep);
+                    ldv<T, VX>(P.ex[1][c] + i, isc);
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) {
+                        const T err = ep[v] + dte7 * f[c][v];
+                        ebits = max(ebits, ErrBits<T>::bits(fabs(err) * isc[v]));
+                    }
                 }
             } else {  // MODE_DOPRI_FINAL
 #pragma unroll

@@ -31,7 +31,11 @@
 
 namespace gsk {
 
-enum StageMode : int { MODE_STAGE = 0, MODE_FINAL = 1, MODE_DOPRI_FINAL = 2 };
+// MODE_DOPRI_S6 / S7: the Dormand-Prince stages 6 and 7 with the work split
+// differently (staged form only): stage 6 also forms y5 (b7 = 0, so y5 needs
+// k1..k6 only), the error terms of k1..k6 and the inverse error scale, and
+// never stores k6; stage 7 evaluates k7 = F(y5) and adds its error term.
+enum StageMode : int { MODE_STAGE = 0, MODE_FINAL = 1, MODE_DOPRI_FINAL = 2, MODE_DOPRI_S6 = 3, MODE_DOPRI_S7 = 4 };
 
 template <typename T>
 struct Geom {
@@ -55,6 +59,7 @@ struct StageArgs {
     double be[kMaxNE];
     double bf;
     Slot out0, out1;
+    Slot out2;              // MODE_DOPRI_S6: inverse error scale
     int n_ex;
     int has_out1;
     int ty, zc;             // tile shape

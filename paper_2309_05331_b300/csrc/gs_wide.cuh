@@ -112,7 +112,9 @@ template <typename T, int NK, int MODE, int VX>
 struct Carry {
     // FINAL: u and the stage inputs; DOPRI_FINAL: error scale and folded error terms
     T a[2][VX];
-    T b[MODE == MODE_FINAL ? (NK > 0 ? NK : 1) : 1][2][VX];
+    // DOPRI_S6: a = u + dt sum_{j=1,3,4,5} b_j k_j, b[0] = dt (folded error
+    // terms), b[1] = inverse error scale (written as soon as it is formed)
+    T b[MODE == MODE_FINAL ? (NK > 0 ? NK : 1) : (MODE == MODE_DOPRI_S6 ? 2 : 1)][2][VX];
 };
 
 // Resolved buffers of one stage launch (one grid, or one batched instance).
@@ -122,6 +124,7 @@ struct StagePtrs {
     const T* k[NK > 0 ? NK : 1][2];
     T* o0[2];
     T* o1[2];
+    T* o2[2];
     const T* ex[kMaxNE][2];
 };
 
@@ -136,9 +139,12 @@ __device__ __forceinline__ StagePtrs<T, NK> resolve_stage(const StageArgs& A, in
         for (int j = 0; j < NK; ++j) P.k[j][c] = resolve<T>(A.kin[j], c, parity, step) + off;
         P.o0[c] = resolve<T>(A.out0, c, parity, step) + off;
         P.o1[c] = (MODE != MODE_STAGE && A.has_out1) ? resolve<T>(A.out1, c, parity, step) + off : nullptr;
+        P.o2[c] = MODE == MODE_DOPRI_S6 ? resolve<T>(A.out2, c, parity, step) + off : nullptr;
 #pragma unroll
         for (int j = 0; j < kMaxNE; ++j)
-            P.ex[j][c] = (MODE == MODE_FINAL && j < A.n_ex) ? resolve<T>(A.ex[j], c, parity, step) + off : nullptr;
+            P.ex[j][c] = ((MODE == MODE_FINAL || MODE == MODE_DOPRI_S7) && j < A.n_ex)
+                             ? resolve<T>(A.ex[j], c, parity, step) + off
+                             : nullptr;
     }
     return P;
 }
@@ -380,7 +386,7 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
 template <typename T, int MODE>
 __device__ __forceinline__ void final_kernel_epilogue(const StageArgs& A, T emax, T* red, int* s_last) {
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    if (MODE == MODE_DOPRI_FINAL) {
+    if (MODE == MODE_DOPRI_FINAL || MODE == MODE_DOPRI_S7) {
         const T bmax = block_nanmax(emax, red);
         if (tid == 0) atomic_max_nonneg(&A.ctrl->err_bits, (double)bmax);
     }

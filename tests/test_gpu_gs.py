@@ -172,6 +172,48 @@ def test_kernel_variants_match_oracle(prec, dims):
             assert err < tol, (variant, depth, method, err)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2)])
+def test_split_stages_match_unsplit_and_oracle(prec, dims):
+    """Fixed Dopri5 steps with stages 6/7 split and unsplit: both against the
+    oracle, and against each other (FP64: 1e-13; the split sums y5 and the
+    error terms in another order)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    phys = dict(Du=3e-3, Dv=1.5e-3, L=max(2.5, dims[0] * 2.5 / 45))
+    u0, v0 = si.gs_initial_state(*dims, seed=43)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    if dims[0] % (2 if prec == 0 else 4):
+        pytest.skip("the split exists in the staged form only")
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(*dims, **phys), u0, v0, oracle.DOPRI5, 0.25, 3)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    res = []
+    for split in (1, 0):
+        g = _gs(torch, dims, prec, u0, v0, **phys)
+        gs.gs_set_dopri5_split(g.ctx, split)
+        g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
+        res.append((to_np(g.u), to_np(g.v)))
+        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, split
+        g.close()
+    if prec == 0:
+        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+
+
+def test_split_rejected_without_staged_form():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    g = _gs(torch, (9, 4, 4), gs.GS_FP32, *si.gs_initial_state(9, 4, 4))
+    assert gs.gs_get_dopri5_split(g.ctx) == 0
+    with pytest.raises(gs.GSError):
+        gs.gs_set_dopri5_split(g.ctx, 1)
+    gs.gs_set_dopri5_split(g.ctx, 0)
+    for bad in (-2, 2):
+        with pytest.raises(gs.GSError):
+            gs.gs_set_dopri5_split(g.ctx, bad)
+    g.close()
+
+
 def test_vectorised_variant_rejects_unaligned_rows():
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
@@ -198,15 +240,20 @@ def test_vectorised_variant_rejects_unaligned_rows():
     g.close()
 
 
-def test_adaptive_fp64_matches_oracle_run():
+@pytest.mark.parametrize("split", [1, 0])
+def test_adaptive_fp64_matches_oracle_run(split):
     """Error-controlled Dopri5 on 16^3 FP64: same accepted/rejected counts and
-    step sizes as the oracle's own adaptive run, final state within 1e-12."""
+    step sizes as the oracle's own adaptive run, final state within 1e-12;
+    with Dormand-Prince stages 6/7 split (stage 6 forms y5 and the error terms
+    of k1..k6) and unsplit."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     dims = (16, 16, 16)
     phys = dict(Du=2e-3, Dv=1e-3)
     u0, v0 = si.gs_initial_state(*dims, seed=2)
     g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    gs.gs_set_dopri5_split(g.ctx, split)
+    assert gs.gs_get_dopri5_split(g.ctx) == split
     gs.gs_set_step_log(g.ctx, 10000)
     r = g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 0.1)
     dts, cnt = gs.gs_get_step_log(g.ctx, 10000)
