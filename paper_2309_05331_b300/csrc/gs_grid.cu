@@ -181,9 +181,10 @@ static cudaError_t launch_staged(gs_ctx* ctx, cudaStream_t s, StageArgs A, int d
     A.ntx = (ctx->p.nx + txw - 1) / txw;
     A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
     depth = std::max(1, std::min(depth, kMaxDepth));
-    size_t smem = staged_smem_bytes<T, NK, VX>(A.ty, depth);
+    constexpr int NP = staged_pointwise<MODE>();
+    size_t smem = staged_smem_bytes<T, NK, VX, NP>(A.ty, depth);
     // a deeper ring than shared memory holds is cut back
-    while (depth > 1 && smem > kMaxSmemPerCta) smem = staged_smem_bytes<T, NK, VX>(A.ty, --depth);
+    while (depth > 1 && smem > kMaxSmemPerCta) smem = staged_smem_bytes<T, NK, VX, NP>(A.ty, --depth);
     if (smem > kMaxSmemPerCta) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -61,19 +61,26 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
 // Shared-memory layout of one launch: the Y ring of the wide form, then DEPTH
 // raw slots.  A slot holds (ty+2) rows x NA arrays x 32 lanes of 16-byte
 // vectors, then the x-halo columns: 2 sides x NA arrays x ty rows of T.
-template <typename T, int NK, int VX>
-__host__ __device__ constexpr int staged_arrays() {
-    return 2 * (1 + NK);  // u and k_1..k_NK, two components each
+// Arrays of a slot: u and k_1..k_NK (two components each), then NP
+// pointwise arrays (split stage 7: error terms and inverse scale, two
+// components each; copied for the tile's own rows only).
+template <int MODE>
+__host__ __device__ constexpr int staged_pointwise() {
+    return MODE == MODE_DOPRI_S7 ? 4 : 0;
 }
-template <typename T, int NK, int VX>
+template <typename T, int NK, int VX, int NP = 0>
+__host__ __device__ constexpr int staged_arrays() {
+    return 2 * (1 + NK) + NP;
+}
+template <typename T, int NK, int VX, int NP = 0>
 __host__ __device__ inline size_t staged_slot_bytes(int ty) {
-    const size_t vec = (size_t)(ty + 2) * staged_arrays<T, NK, VX>() * 32 * sizeof(T) * VX;
-    const size_t halo = (size_t)2 * staged_arrays<T, NK, VX>() * ty * sizeof(T);
+    const size_t vec = (size_t)(ty + 2) * staged_arrays<T, NK, VX, NP>() * 32 * sizeof(T) * VX;
+    const size_t halo = (size_t)2 * staged_arrays<T, NK, VX, NP>() * ty * sizeof(T);
     return (vec + halo + 15) / 16 * 16;
 }
-template <typename T, int NK, int VX>
+template <typename T, int NK, int VX, int NP = 0>
 __host__ __device__ inline size_t staged_smem_bytes(int ty, int depth) {
-    return (wide_smem_bytes<T, VX>(ty) + 15) / 16 * 16 + (size_t)depth * staged_slot_bytes<T, NK, VX>(ty);
+    return (wide_smem_bytes<T, VX>(ty) + 15) / 16 * 16 + (size_t)depth * staged_slot_bytes<T, NK, VX, NP>(ty);
 }
 
 template <typename T, int NK, int MODE, int VX>
@@ -83,7 +90,8 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
     static_assert(sizeof(T) * VX == 4 || sizeof(T) * VX == 8 || sizeof(T) * VX == 16, "4-, 8- or 16-byte vectors");
     constexpr int TXW = 32 * VX;
     constexpr int PITCH = wide_pitch<VX>();
-    constexpr int NA = staged_arrays<T, NK, VX>();
+    constexpr int NP = staged_pointwise<MODE>();
+    constexpr int NA = staged_arrays<T, NK, VX, NP>();
     using VTy = typename VecT<T, VX>::type;
     const int lane = threadIdx.x;
     const int w = threadIdx.y;
@@ -97,7 +105,7 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
     // stage 6 of the split scheme: b of k1, k3, k4, k5; e3..e5 are ew[0..2]
     const T bw[4] = {(T)dp5::B1, (T)dp5::B3, (T)dp5::B4, (T)dp5::B5};
     const T e67 = (T)(dp5::E6 + dp5::E7), dtb6 = dt * (T)dp5::B6, dte6 = dt * (T)dp5::E6;
-    const size_t slot_bytes = staged_slot_bytes<T, NK, VX>(TY);
+    const size_t slot_bytes = staged_slot_bytes<T, NK, VX, NP>(TY);
     const size_t vec_bytes = (size_t)TYP * NA * 32 * sizeof(VTy);
 
     auto sidx = [&](int buf, int ww, int c, int col) -> int { return ((buf * TYP + ww) * 2 + c) * PITCH + col; };
@@ -140,6 +148,13 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
                         cp_async_vec<sizeof(VTy)>(rvec(s, c * (1 + NK) + 1 + j), P.k[j][c] + cbase + zo);
                 }
             }
+            if (NP > 0 && inner) {
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    cp_async_vec<sizeof(VTy)>(rvec(s, 2 * (1 + NK) + c), P.ex[0][c] + cbase + zo);
+                    cp_async_vec<sizeof(VTy)>(rvec(s, 2 * (1 + NK) + 2 + c), P.ex[1][c] + cbase + zo);
+                }
+            }
             if (do_halo) {
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
@@ -159,7 +174,11 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
         for (int c = 0; c < 2; ++c) {
             T uu[VX];
             lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, c * (1 + NK))), uu);
-            T sacc[VX], k1[VX], q[VX], sb[VX];
+            T sacc[VX], k1[VX], q[VX], sb[VX], pe[VX], pi[VX];
+            if (NP > 0) {
+                lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, 2 * (1 + NK) + c)), pe);
+                lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, 2 * (1 + NK) + 2 + c)), pi);
+            }
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
                 sacc[v] = T(0);
@@ -201,6 +220,10 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
                     // 1 / (atol + rtol (|u| + dt |k1|)) and dt (sum_{j<7} e_j (k_j - k1) - e7 k1)
                     cr.a[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1[v])));
                     cr.b[0][c][v] = dt * (q[v] - e7 * k1[v]);
+                }
+                if (MODE == MODE_DOPRI_S7) {  // error terms and inverse scale of stage 6
+                    cr.b[0][c][v] = pe[v];
+                    cr.a[c][v] = pi[v];
                 }
                 if (MODE == MODE_DOPRI_S6) {
                     // u + dt sum_{j=1,3,4,5} b_j k_j, dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1),
@@ -345,13 +368,10 @@ __device__ __forceinline__ void staged_segment(const Geom<T>& g, const StagePtrs
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     stv<T, VX>(P.o0[c] + i, f[c]);
-                    T ep[VX], isc[VX];
-                    ldv<T, VX>(P.ex[0][c] + i, ep);
-                    ldv<T, VX>(P.ex[1][c] + i, isc);
 #pragma unroll
                     for (int v = 0; v < VX; ++v) {
-                        const T err = ep[v] + dte7 * f[c][v];
-                        ebits = max(ebits, ErrBits<T>::bits(fabs(err) * isc[v]));
+                        const T err = cur.b[0][c][v] + dte7 * f[c][v];
+                        ebits = max(ebits, ErrBits<T>::bits(fabs(err) * cur.a[c][v]));
                     }
                 }
             } else {  // MODE_DOPRI_FINAL
