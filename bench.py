@@ -247,9 +247,42 @@ def extra_workloads(torch, gs, si):
         ms = a.elapsed_time(b)
         out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {"ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3)}
     out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
+    out.update(precision_workload(torch, gs, si))
     out.update(batched_workload(torch, gs, si))
     from paper_2309_05331_b300 import surrogate_workload
     out["surrogate_128cubed"] = surrogate_workload.run(torch, n=128, trajectories=8, per_traj=250, iters=3000)
+    return out
+
+
+def precision_workload(torch, gs, si, n=N, accepted=1000):
+    """Precision form of the headline workload: the FP32-stage / FP64-control
+    run takes 1000 accepted Dormand-Prince steps from the initial state; the
+    all-FP64 run (the path that is pinned to the FP64 oracle) integrates the
+    same initial state to the same time with the same tolerance; relative L2
+    of the two states over the full grid and over the 64^3 downsample (every
+    4th point per axis)."""
+    u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+    out = {}
+    g32 = gs.GrayScott(n, n, n, prec=gs.GS_FP32)
+    g32.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    r32 = g32.integrate_adaptive(TOL, TOL, 0.0, math.inf, DT0, max_accepted=accepted)
+    u32, v32 = g32.u.double(), g32.v.double()
+    g32.close()
+    g64 = gs.GrayScott(n, n, n, prec=gs.GS_FP64)
+    g64.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    r64 = g64.integrate_adaptive(TOL, TOL, 0.0, r32["t"], DT0)
+    u64, v64 = g64.u, g64.v
+
+    def rel(a, b, c, d):
+        return float(torch.sqrt(((a - c) ** 2).sum() + ((b - d) ** 2).sum()) / torch.sqrt((c ** 2).sum() + (d ** 2).sum()))
+
+    s = (slice(None, None, 4),) * 3
+    out["gs_256cubed_fp32_vs_fp64_1000_accepted"] = {
+        "t": r32["t"], "fp32_accepted": r32["n_acc"], "fp32_rejected": r32["n_rej"],
+        "fp64_accepted": r64["n_acc"], "fp64_rejected": r64["n_rej"], "tolerance": TOL,
+        "rel_l2_full": rel(u32, v32, u64, v64),
+        "rel_l2_64cubed_downsample": rel(u32[s], v32[s], u64[s], v64[s])}
+    g64.close()
     return out
 
 
@@ -313,7 +346,7 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=100)  # 1000 accepted steps
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true")

@@ -270,7 +270,7 @@ gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group);
 /* Segment code of the batched stage kernels: depth 1..3 = staged form (each
  * thread copies its inputs that many planes ahead into shared memory with
  * cp.async), 0 = vectorised form (direct loads; the default).  Same results.
- * gsb_autotune also chooses between depth 0 and 1. */
+ * gsb_autotune tunes the tile of the depth in use. */
 gs_status gsb_set_stage_depth(gsb_ctx* ctx, int depth);
 gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* ngroups);
 

@@ -648,25 +648,21 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) 
     BCK(cudaEventCreate(&e0));
     BCK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bty = ctx->ty, bzc = ctx->zc, bdepth = ctx->depth;
+    int bty = ctx->ty, bzc = ctx->zc;
     gs_status st = GS_OK;
-    // the staged form copies one cell per lane (4- or 8-byte cp.async): on 512
-    // uneven instances it took 129 ms against 101 ms for the vectorised form
-    for (int depth = 0; depth <= 1 && st == GS_OK; ++depth) {
-        if ((st = gsb_set_stage_depth(ctx, depth)) != GS_OK) break;
-        for (const auto& c : cand) {
-            float ms = 0.f;
-            if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK)
-                break;
-            if (ms < best) {
-                best = ms;
-                bty = c[0];
-                bzc = c[1];
-                bdepth = depth;
-            }
+    // tiles of the segment code in use (the staged form copies one cell per
+    // lane with 4- or 8-byte cp.async: on 512 uneven instances it took 129 ms
+    // against 101 ms for the vectorised form, and a dense timing round does
+    // not show it, so the depth is left to gsb_set_stage_depth)
+    for (const auto& c : cand) {
+        float ms = 0.f;
+        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK || (st = time_round(ctx, e0, e1, &ms)) != GS_OK) break;
+        if (ms < best) {
+            best = ms;
+            bty = c[0];
+            bzc = c[1];
         }
     }
-    if (st == GS_OK) st = gsb_set_stage_depth(ctx, bdepth);
     // instance grouping for the chosen tile: one group, or groups of a
     // quarter, half, one or two times the automatic (half-L2) budget (on the
     // 512-instance ensemble one group wins: 101 ms against 172-450 ms, the
