@@ -193,6 +193,16 @@ gs_status gs_get_stage_configs(const gs_ctx* ctx, int* form, int* ty, int* zc);
  * (INVALID if the staged form does not apply).  Same formulas, summed in
  * another order (y5 as (u + dt sum_{j<6} b_j k_j) + dt b6 k6).
  * gs_get_dopri5_split: 1 if the split is in use. */
+/* Fixed-step RK4 (gs_step) on small grids in ONE cooperative launch: every
+ * step's four stages run in a persistent kernel, separated by a grid
+ * barrier, instead of four launches per step.  mode: -1 automatic (grids of
+ * at most 2^18 cells; the default), 0 off, 1 on; ctas: the launch's CTA count
+ * (0: automatic, at most what the GPU holds resident).  Same formulas and
+ * summation order as the stage kernels.  A barrier wait that passes its
+ * iteration limit makes gs_step return GS_ERR_CUDA.  gs_get_small_grid_path:
+ * 1 if gs_step(GS_RK4) takes this path. */
+gs_status gs_set_small_grid_path(gs_ctx* ctx, int mode, int ctas);
+int gs_get_small_grid_path(const gs_ctx* ctx);
 gs_status gs_set_dopri5_split(gs_ctx* ctx, int mode);
 int gs_get_dopri5_split(const gs_ctx* ctx);
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);

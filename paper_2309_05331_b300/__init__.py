@@ -64,6 +64,8 @@ _SIGNATURES = {
     "gs_get_stage_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_set_stage_depth": ([_vp, C.c_int], C.c_int),
     "gs_set_dopri5_split": ([_vp, C.c_int], C.c_int),
+    "gs_set_small_grid_path": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gs_get_small_grid_path": ([_vp], C.c_int),
     "gs_get_dopri5_split": ([_vp], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
@@ -241,6 +243,14 @@ def gs_get_stage_configs(ctx):
     f, t, z = (C.c_int * 7)(), (C.c_int * 7)(), (C.c_int * 7)()
     _check(lib().gs_get_stage_configs(ctx, f, t, z), ctx)
     return [(f[i], t[i], z[i]) for i in range(7)]
+
+
+def gs_set_small_grid_path(ctx, mode, ctas=0):
+    _check(lib().gs_set_small_grid_path(ctx, mode, ctas), ctx)
+
+
+def gs_get_small_grid_path(ctx):
+    return lib().gs_get_small_grid_path(ctx)
 
 
 def gs_set_dopri5_split(ctx, mode):

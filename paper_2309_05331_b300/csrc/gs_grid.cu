@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_persist.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
 #include "host_util.h"
@@ -68,6 +69,9 @@ struct gs_ctx {
     bool dp_tuned = false;
     int variant = 0;        // requested: 0 automatic, 1 generic, 2 vectorised, 3 vectorised 8-byte
     int split67 = -1;       // Dormand-Prince stages 6/7 split (MODE_DOPRI_S6/S7): -1 automatic, 0 off, 1 on
+    int small_mode = -1;    // fixed-step RK4 in one cooperative launch: -1 automatic (small grids), 0 off, 1 on
+    int small_ctas = 0;     // its CTA count (0: automatic)
+    unsigned* pbar = nullptr;  // its grid barrier: count, generation, error
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -582,6 +586,45 @@ static void init_fixed_ctrl(gs_ctx* ctx, double t0, double dt, long long limit) 
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+// Grids up to this many cells keep their fields in L2: fixed-step RK4 then
+// runs in one cooperative launch (gs_persist.cuh) by default.
+constexpr long long kSmallGridCells = 1LL << 18;
+
+template <typename T>
+static gs_status rk4_persistent(gs_ctx* ctx, double dt, long nsteps) {
+    auto kern = rk4_persistent_kernel<T>;
+    const Geom<T> g = make_geom<T>(ctx->p);
+    RK4Bufs<T> B;
+    for (int c = 0; c < 2; ++c) {
+        B.s[0][c] = static_cast<T*>(ctx->state[c]);
+        B.s[1][c] = static_cast<T*>(ctx->field[0][c]);
+        for (int j = 0; j < 3; ++j) B.k[j][c] = static_cast<T*>(ctx->field[1 + j][c]);
+    }
+    int occ = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0));
+    const long long want = ctx->small_ctas > 0 ? ctx->small_ctas : std::min<long long>(ctx->nsm, (ctx->N + 255) / 256);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(want, (long long)ctx->nsm * std::max(occ, 1)));
+    CK(cudaMemsetAsync(ctx->pbar, 0, 4 * sizeof(unsigned), ctx->stream));
+    double dtv = dt;
+    long long nst = nsteps;
+    unsigned* bar = ctx->pbar;
+    void* args[] = {(void*)&g, (void*)&B, (void*)&dtv, (void*)&nst, (void*)&bar};
+    CK(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, 0, ctx->stream));
+    unsigned err = 0;
+    CK(cudaMemcpyAsync(&err, ctx->pbar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (err) {
+        snprintf(ctx->err, sizeof(ctx->err), "rk4 persistent kernel: grid barrier wait expired");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+static bool small_path(const gs_ctx* ctx) {
+    if (ctx->small_mode >= 0) return ctx->small_mode == 1;
+    return ctx->N <= kSmallGridCells;
+}
+
 extern "C" {
 
 gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out) {
@@ -617,6 +660,10 @@ gs_status gs_create(const gs_params* p, void* stream, gs_ctx** out) {
             break;
         }
         if ((e = cudaMemset(ctx->dctrl, 0, sizeof(DevCtrl))) != cudaSuccess) break;
+        if ((e = cudaMalloc(&ctx->pbar, 4 * sizeof(unsigned))) != cudaSuccess) {
+            st = GS_ERR_NOMEM;
+            break;
+        }
         if ((e = cudaMallocHost(&ctx->hctrl, sizeof(DevCtrl))) != cudaSuccess) {
             st = GS_ERR_NOMEM;
             break;
@@ -644,6 +691,7 @@ gs_status gs_destroy(gs_ctx* ctx) {
     if (ctx->cap) cudaStreamDestroy(ctx->cap);
     if (ctx->scratch) cudaFree(ctx->scratch);
     if (ctx->dctrl) cudaFree(ctx->dctrl);
+    if (ctx->pbar) cudaFree(ctx->pbar);
     if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
     if (ctx->hpatch) cudaFreeHost(ctx->hpatch);
     if (ctx->dlog) cudaFree(ctx->dlog);
@@ -689,6 +737,15 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, 
     return GS_OK;
 }
 
+gs_status gs_set_small_grid_path(gs_ctx* ctx, int mode, int ctas) {
+    if (!ctx || mode < -1 || mode > 1 || ctas < 0 || ctas > 65535) return GS_ERR_INVALID;
+    ctx->small_mode = mode;
+    ctx->small_ctas = ctas;
+    return GS_OK;
+}
+
+int gs_get_small_grid_path(const gs_ctx* ctx) { return ctx && small_path(ctx) ? 1 : 0; }
+
 gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps) {
     if (!ctx || !t || !ctx->state[0] || nsteps < 0 || !std::isfinite(dt)) return GS_ERR_INVALID;
     if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER)
@@ -697,6 +754,12 @@ gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nste
     const double t0 = *t;
     gs_status st;
     cudaGraphExec_t ex;
+    if (method == GS_RK4 && small_path(ctx)) {
+        st = ctx->p.prec == GS_FP64 ? rk4_persistent<double>(ctx, dt, nsteps) : rk4_persistent<float>(ctx, dt, nsteps);
+        if (st != GS_OK) return st;
+        *t = t0 + (double)nsteps * dt;
+        return GS_OK;
+    }
     if (method == GS_AB4) {
         const long long nstart = std::min<long long>(3, nsteps);
         init_fixed_ctrl(ctx, t0, dt, nstart);

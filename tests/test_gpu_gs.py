@@ -200,6 +200,36 @@ def test_split_stages_match_unsplit_and_oracle(prec, dims):
         assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("nsteps,ctas", [(7, 0), (8, 1), (5, 3), (20, 37)])
+def test_rk4_small_grid_path_matches_graph_path(prec, nsteps, ctas):
+    """Fixed-step RK4 in one cooperative launch (grid barrier between stages)
+    against the four-kernel graph path and the oracle; odd and even step
+    counts (copy-back), CTA counts that do and do not divide the cells."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (20, 12, 9)
+    phys = dict(Du=2e-3, Dv=1e-3)
+    u0, v0 = si.gs_initial_state(*dims, seed=51)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    res = []
+    for mode in (1, 0):
+        g = _gs(torch, dims, prec, u0, v0, **phys)
+        gs.gs_set_small_grid_path(g.ctx, mode, ctas)
+        assert gs.gs_get_small_grid_path(g.ctx) == mode
+        t = g.step(gs.GS_RK4, 0.0, 0.2, nsteps)
+        assert abs(t - 0.2 * nsteps) < 1e-12
+        res.append((to_np(g.u), to_np(g.v)))
+        g.close()
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(*dims, **phys), u0, v0, oracle.RK4, 0.2, nsteps)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    for r in res:
+        assert oracle.rel_l2(list(r), [ou, ov]) < tol
+    if prec == 0:
+        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-14
+
+
 def test_split_rejected_without_staged_form():
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
