@@ -71,7 +71,7 @@ struct gs_ctx {
     int split67 = -1;       // Dormand-Prince stages 6/7 split (MODE_DOPRI_S6/S7): -1 automatic, 0 off, 1 on
     int small_mode = -1;    // fixed-step RK4 in one cooperative launch: -1 automatic (small grids), 0 off, 1 on
     int small_ctas = 0;     // its CTA count (0: automatic)
-    unsigned* pbar = nullptr;  // its grid barrier: count, generation, error
+    unsigned* pbar = nullptr;  // its grid barrier: u64 count, generation, error
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -611,7 +611,7 @@ static gs_status rk4_persistent(gs_ctx* ctx, double dt, long nsteps) {
     void* args[] = {(void*)&g, (void*)&B, (void*)&dtv, (void*)&nst, (void*)&bar};
     CK(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, 0, ctx->stream));
     unsigned err = 0;
-    CK(cudaMemcpyAsync(&err, ctx->pbar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&err, ctx->pbar + 3, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (err) {
         snprintf(ctx->err, sizeof(ctx->err), "rk4 persistent kernel: grid barrier wait expired");
@@ -621,6 +621,7 @@ static gs_status rk4_persistent(gs_ctx* ctx, double dt, long nsteps) {
 }
 
 static bool small_path(const gs_ctx* ctx) {
+    if (ctx->N >= (1LL << 31)) return false;  // 32-bit cell indices
     if (ctx->small_mode >= 0) return ctx->small_mode == 1;
     return ctx->N <= kSmallGridCells;
 }
