@@ -54,11 +54,11 @@ STAGE_FIELDS_SPLIT = [2, 3, 4, 5, 6, 9, 4]
 BYTES_PER_FIELD_CELL = 8
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
-# stage-7 launch at 256^3 (profiles/gs_stage7_wide_fp32_256cubed_full.md:
-# 824.2 MB read + 247.9 MB written), per cell so that other grids scale by
+# split stage-6 launch at 256^3 (profiles/gs_stage6_split_fp32_256cubed_full.md:
+# 827.2 MB read + 371.8 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel form while the stage-kernel sources are
 # unchanged.
-NCU_TRAFFIC = {"kernel": "stage7", "form": 2, "source_sha": "8d78d3f185837cc6", "bytes_per_cell": (824249856 + 247850496) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stage6", "form": 4, "split": True, "source_sha": "c1d3aaddb0749d51", "bytes_per_cell": (827151104 + 371779072) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
@@ -466,7 +466,7 @@ def main():
     attempt_gbs = attempt_fields * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
     traffic = None
     if (NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]
-            and NCU_TRAFFIC["form"] == stage_cfg[dom][0]):
+            and NCU_TRAFFIC["form"] == stage_cfg[dom][0] and NCU_TRAFFIC["split"] == (fields is STAGE_FIELDS_SPLIT)):
         traffic = NCU_TRAFFIC["bytes_per_cell"] * cells
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
