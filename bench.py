@@ -51,6 +51,11 @@ STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
 # terms and the inverse error scale; stage 7 reads y5, the error terms and
 # the scale and writes k7
 STAGE_FIELDS_SPLIT = [2, 3, 4, 5, 6, 9, 4]
+# with the stages in pairs (one launch each): stages 2+3 read u, k1 and write
+# k2, k3; stages 4+5 read u, k1..k3 and write k4, k5; stages 6+7 read u,
+# k1..k5 and write y5 and k7 (the error norm is reduced, not stored)
+PAIR_NAMES = ["k1", "stages2+3", "stages4+5", "stages6+7"]
+PAIR_FIELDS = [2, 4, 6, 8]
 BYTES_PER_FIELD_CELL = 8
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
@@ -58,8 +63,8 @@ BYTES_PER_FIELD_CELL = 8
 # 827.2 MB read + 371.8 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel form while the stage-kernel sources are
 # unchanged.
-NCU_TRAFFIC = {"kernel": "stage6", "form": 4, "split": True, "source_sha": "c1d3aaddb0749d51", "bytes_per_cell": (827151104 + 371779072) / 256 ** 3}
-KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_grid.cu")
+NCU_TRAFFIC = {"kernel": "stage6", "path": "split", "source_sha": "c1d3aaddb0749d51", "bytes_per_cell": (827151104 + 371779072) / 256 ** 3}
+KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
 
@@ -391,6 +396,8 @@ def main():
     else:
         tile = gs.gs_autotune(g.ctx)
     variant = gs.gs_get_kernel_variant(g.ctx)
+    fused = gs.gs_get_dopri5_fusion(g.ctx) == 1
+    per_attempt = 3 if fused else 6  # stage kernels per Dormand-Prince attempt
     g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
 
     t, dt = 0.0, DT0
@@ -412,7 +419,7 @@ def main():
         t, dt = r["t"], r["dt"]
         acc += r["n_acc"]
         rej += r["n_rej"]
-        launches += 2 + 6 * (r["n_acc"] + r["n_rej"])  # k1, copy-back, 6 stage kernels per attempt
+        launches += 2 + per_attempt * (r["n_acc"] + r["n_rej"])  # k1, copy-back, stage kernels per attempt
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -453,28 +460,43 @@ def main():
     # with CUDA events on the launching (context) stream
     g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
     torch.cuda.nvtx.range_push("time_stages")  # profilers select these launches
-    stage_ms = gs.gs_time_stages(g.ctx, reps=5)
+    if fused:
+        stage_ms = gs.gs_time_pairs(g.ctx, reps=5)
+        names, fields, path = PAIR_NAMES, PAIR_FIELDS, "pairs"
+    else:
+        stage_ms = gs.gs_time_stages(g.ctx, reps=5)
+        split = gs.gs_get_dopri5_split(g.ctx) == 1
+        names, fields, path = STAGE_NAMES, (STAGE_FIELDS_SPLIT if split else STAGE_FIELDS), (
+            "split" if split else "single")
     torch.cuda.nvtx.range_pop()
     stage_cfg = gs.gs_get_stage_configs(g.ctx)
+    pair_cfg = gs.gs_get_pair_configs(g.ctx)
     peak, peak_kind = _peaks()
-    dom = max(range(1, 7), key=lambda i: stage_ms[i])
-    fields = STAGE_FIELDS_SPLIT if gs.gs_get_dopri5_split(g.ctx) else STAGE_FIELDS
-    attempt_fields = sum(fields[1:])  # field passes per attempt (k1 is reused): 31 split, 33 unsplit
+    dom = max(range(1, len(stage_ms)), key=lambda i: stage_ms[i])
+    attempt_fields = sum(fields[1:])  # field passes per attempt (k1 is reused): 18 pairs, 31 split, 33 single
     dom_bytes = fields[dom] * BYTES_PER_FIELD_CELL * cells
     achieved = dom_bytes / (stage_ms[dom] * 1e-3) / 1e9
     attempt_ms = sum(stage_ms[1:])
     attempt_gbs = attempt_fields * BYTES_PER_FIELD_CELL * cells / (attempt_ms * 1e-3) / 1e9
     traffic = None
-    if (NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == STAGE_NAMES[dom]
-            and NCU_TRAFFIC["form"] == stage_cfg[dom][0] and NCU_TRAFFIC["split"] == (fields is STAGE_FIELDS_SPLIT)):
+    if (NCU_TRAFFIC["source_sha"] == _kernel_source_sha() and NCU_TRAFFIC["kernel"] == names[dom]
+            and NCU_TRAFFIC["path"] == path):
         traffic = NCU_TRAFFIC["bytes_per_cell"] * cells
+    if fused:
+        kdesc = f"{names[dom]} pair kernel (FP32), tile height {pair_cfg[dom - 1][0]}, ring depth {pair_cfg[dom - 1][1]}"
+        kcfg = {"k1": {"form": FORM_NAMES[stage_cfg[0][0]], "ty": stage_cfg[0][1]},
+                **{nm: {"form": "pair", "ty": t, "depth": d} for nm, (t, d) in zip(PAIR_NAMES[1:], pair_cfg)}}
+    else:
+        kdesc = (f"{names[dom]} kernel, {FORM_NAMES[stage_cfg[dom][0]]} form (FP32)"
+                 + (", stages 6/7 split" if path == "split" else ""))
+        kcfg = {nm: {"form": FORM_NAMES[f], "ty": t, "zc": z, **({"depth": d} if f == 4 else {})}
+                for nm, (f, t, z), d in zip(STAGE_NAMES, stage_cfg, gs.gs_get_stage_depths(g.ctx))}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind ==
                 "measured" else "fallback 6.4 TB/s",
-                "kernel": f"{STAGE_NAMES[dom]} kernel, {FORM_NAMES[stage_cfg[dom][0]]} form (FP32)"
-                          + (", stages 6/7 split" if fields is STAGE_FIELDS_SPLIT else ""),
+                "kernel": kdesc,
                 "algorithmic_bytes_per_launch": dom_bytes, "launch_ms": stage_ms[dom],
-                "per_kernel_ms": dict(zip(STAGE_NAMES, stage_ms)),
+                "per_kernel_ms": dict(zip(names, stage_ms)),
                 "attempt": {"algorithmic_bytes_per_cell": attempt_fields * BYTES_PER_FIELD_CELL,
                             "ms": attempt_ms, "achieved_gbs": attempt_gbs, "frac": attempt_gbs / peak}}
 
@@ -487,11 +509,8 @@ def main():
                 "config": {"workload": WORKLOAD, "grid": [N, N, N], "accepted_per_step": ACC_PER_STEP,
                            "tolerance": TOL, "tile_ty_zc": [tile[0], tile[1]],
                            "stencil_kernel": {1: "generic", 2: "vectorised", 4: "staged"}.get(variant, str(variant)),
-                           "dopri5_kernel_configs": {nm: {"form": FORM_NAMES[f], "ty": t, "zc": z,
-                                                          **({"depth": d} if f == 4 else {})}
-                                                     for nm, (f, t, z), d in
-                                                     zip(STAGE_NAMES, gs.gs_get_stage_configs(g.ctx),
-                                                         gs.gs_get_stage_depths(g.ctx))},
+                           "dopri5_path": path,
+                           "dopri5_kernel_configs": kcfg,
                            "l2": "inputs larger than L2 (u, v + 8 stage fields = 1.3 GB per GPU); no flush",
                            "parallelism": f"replicas x{ws} (independent problems, no collective)"},
                 "accepted_steps": acc_all, "rejected_attempts_rank0": rej,

@@ -205,6 +205,29 @@ gs_status gs_set_small_grid_path(gs_ctx* ctx, int mode, int ctas);
 int gs_get_small_grid_path(const gs_ctx* ctx);
 gs_status gs_set_dopri5_split(gs_ctx* ctx, int mode);
 int gs_get_dopri5_split(const gs_ctx* ctx);
+
+/* Dormand-Prince stages in pairs (Table 1 tableau; Eq. 2 right-hand side):
+ * stages 2+3, 4+5 and 6+7 each run as ONE launch that computes the first
+ * stage's k on the tile plus a one-cell ring (recomputed by neighbouring
+ * tiles) and the second stage from it, so k2, k4 and k6 are never read back
+ * and k6 is never stored: an attempt moves 18 field passes instead of 31.
+ * Stages 6+7 write y5 (the next state) and k7 (the next k1), reduce the
+ * scaled error norm and run the controller.  Requires the staged form (x
+ * extent a multiple of the vector width); any ny, nz.  mode: -1 automatic
+ * (on when the staged form applies and no other kernel form is forced;
+ * gs_autotune keeps it on only if the pairs' summed kernel time beats the
+ * single stages'), 0 off, 1 on (INVALID if the staged form does not apply).
+ * The stage formulas are those of the single stages; Y_{i+1} is summed as
+ * (u + dt sum_{j<i} a_{i+1,j} k_j) + dt a_{i+1,i} k_i.
+ * gs_get_dopri5_fusion: 1 if the pairs are in use. */
+gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode);
+int gs_get_dopri5_fusion(const gs_ctx* ctx);
+/* Launch shape of pair kernel `pair` (0: stages 2+3, 1: 4+5, 2: 6+7; -1: all
+ * three): tile height ty (1..7 rows; the CTA has ty + 5 warps) and input
+ * ring depth (1..3 planes; cut back at launch to what shared memory holds).
+ * gs_autotune overwrites it.  gs_get_pair_configs: host arrays of 3 ints. */
+gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth);
+gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth);
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);
 gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);
 
@@ -216,6 +239,10 @@ gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);
  * the bound state is not modified.  ms: host array of 7 doubles.
  * Synchronises. */
 gs_status gs_time_stages(gs_ctx* ctx, int reps, double* ms);
+/* Same for the pair kernels: ms[0] = k1, ms[1..3] = stages 2+3, 4+5, 6+7
+ * (the last includes the error-norm reduction).  ms: host array of 4
+ * doubles.  INVALID if the pair kernels do not apply.  Synchronises. */
+gs_status gs_time_pairs(gs_ctx* ctx, int reps, double* ms);
 
 /* Text of the last CUDA error seen by ctx ("" if none). */
 const char* gs_last_error(const gs_ctx* ctx);

@@ -67,6 +67,11 @@ _SIGNATURES = {
     "gs_set_small_grid_path": ([_vp, C.c_int, C.c_int], C.c_int),
     "gs_get_small_grid_path": ([_vp], C.c_int),
     "gs_get_dopri5_split": ([_vp], C.c_int),
+    "gs_set_dopri5_fusion": ([_vp, C.c_int], C.c_int),
+    "gs_get_dopri5_fusion": ([_vp], C.c_int),
+    "gs_set_pair_config": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
+    "gs_get_pair_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
@@ -259,6 +264,33 @@ def gs_set_dopri5_split(ctx, mode):
 
 def gs_get_dopri5_split(ctx):
     return lib().gs_get_dopri5_split(ctx)
+
+
+def gs_set_dopri5_fusion(ctx, mode):
+    _check(lib().gs_set_dopri5_fusion(ctx, mode), ctx)
+
+
+def gs_get_dopri5_fusion(ctx):
+    return lib().gs_get_dopri5_fusion(ctx)
+
+
+def gs_set_pair_config(ctx, pair, ty, depth):
+    _check(lib().gs_set_pair_config(ctx, pair, ty, depth), ctx)
+
+
+def gs_get_pair_configs(ctx):
+    """(tile height, ring depth) of the pair kernels (stages 2+3, 4+5, 6+7)."""
+    t = (C.c_int * 3)()
+    d = (C.c_int * 3)()
+    _check(lib().gs_get_pair_configs(ctx, t, d), ctx)
+    return [(t[i], d[i]) for i in range(3)]
+
+
+def gs_time_pairs(ctx, reps=5):
+    """Average durations (ms) of the k1 kernel and the three Dormand-Prince pair kernels."""
+    ms = (C.c_double * 4)()
+    _check(lib().gs_time_pairs(ctx, reps, ms), ctx)
+    return list(ms)
 
 
 def gs_set_stage_depth(ctx, depth):

@@ -22,6 +22,7 @@
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_pair.cuh"
 #include "gs_persist.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
@@ -69,6 +70,9 @@ struct gs_ctx {
     bool dp_tuned = false;
     int variant = 0;        // requested: 0 automatic, 1 generic, 2 vectorised, 3 vectorised 8-byte
     int split67 = -1;       // Dormand-Prince stages 6/7 split (MODE_DOPRI_S6/S7): -1 automatic, 0 off, 1 on
+    int fuse = -1;          // Dormand-Prince stage pairs (2,3) (4,5) (6,7) in one launch each: -1 automatic, 0 off, 1 on
+    bool fuse_auto = true;  // the automatic choice (the autotuner's verdict once tuned)
+    KCfg pc[3] = {{5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}};  // pair kernels: tile height, ring depth
     int small_mode = -1;    // fixed-step RK4 in one cooperative launch: -1 automatic (small grids), 0 off, 1 on
     int small_ctas = 0;     // its CTA count (0: automatic)
     unsigned* pbar = nullptr;  // its grid barrier: u64 count, generation, error
@@ -125,6 +129,14 @@ static bool split67_on(const gs_ctx* ctx) {
     if (!form_ok(ctx, 4)) return false;
     if (ctx->split67 >= 0) return ctx->split67 == 1;
     return ctx->variant == 0 || ctx->variant == 4;
+}
+// Dormand-Prince stages as three pair launches (gs_pair.cuh): automatic when
+// the staged form applies and no other form is forced (then the autotuner's
+// verdict)
+static bool pairs_on(const gs_ctx* ctx) {
+    if (!form_ok(ctx, 4)) return false;
+    if (ctx->fuse >= 0) return ctx->fuse == 1;
+    return (ctx->variant == 0 || ctx->variant == 4) && ctx->fuse_auto;
 }
 // the form a launch with configured form `form` actually uses
 static int pick_form(const gs_ctx* ctx, int form) {
@@ -199,6 +211,37 @@ static cudaError_t launch_staged(gs_ctx* ctx, cudaStream_t s, StageArgs A, int d
     const int grid = plan_schedule(ctx, A, occ);
     kern<<<grid, dim3(32, A.ty + 2), smem, s>>>(g, A, depth);
     return cudaGetLastError();
+}
+
+template <typename T, int NK, int MODE>
+static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
+    const Geom<T> g = make_geom<T>(ctx->p);
+    auto kern = gs_pair_kernel<T, NK, MODE>;
+    if (A.ty < 1 || A.ty > kPairMaxTY) return cudaErrorInvalidConfiguration;
+    const int txw = 32 * pair_vx<T>();
+    A.ntx = (ctx->p.nx + txw - 1) / txw;
+    A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
+    depth = std::max(1, std::min(depth, kMaxDepth));
+    // dynamic shared memory, leaving room for the kernel's static arrays
+    const size_t cap = kMaxSmemPerCta - 1024;
+    size_t smem = pair_smem_bytes<T, NK, MODE>(A.ty, depth);
+    while (depth > 1 && smem > cap) smem = pair_smem_bytes<T, NK, MODE>(A.ty, --depth);
+    if (smem > cap) return cudaErrorInvalidConfiguration;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 5), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int grid = plan_schedule(ctx, A, occ);
+    kern<<<grid, dim3(32, A.ty + 5), smem, s>>>(g, A, depth);
+    return cudaGetLastError();
+}
+
+template <int NK, int MODE>
+static cudaError_t launch_pair_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A, const KCfg& cfg) {
+    if (ctx->p.prec == GS_FP64) return launch_pair<double, NK, MODE>(ctx, s, A, cfg.depth);
+    return launch_pair<float, NK, MODE>(ctx, s, A, cfg.depth);
 }
 
 template <typename T, int NK, int MODE>
@@ -456,7 +499,57 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A, cfg);
 }
 
+// Dormand-Prince stage pair pi (0: stages 2, 3; 1: stages 4, 5; 2: stages 6,
+// 7 with y5 -> next state, k7 -> next k1, the error norm and the controller)
+static cudaError_t launch_dopri5_pair(gs_ctx* ctx, cudaStream_t s, int pi, unsigned long long h, int use_cond) {
+    const Slot k1 = pair_sel(ctx, 1, 2, SEL_CUR);
+    const Slot k[6] = {k1, k1, fld(ctx, 3), fld(ctx, 4), fld(ctx, 5), fld(ctx, 6)};  // k[i] = k_i
+    const KCfg& cfg = ctx->pc[pi];
+    StageArgs A = base_args(ctx, cfg);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.has_out1 = 1;
+    if (pi == 0) {
+        A.kin[0] = k[1];
+        A.a[0] = dp5::A21;
+        A.bk[0] = dp5::A31;
+        A.bk[1] = dp5::A32;
+        A.out0 = k[2];
+        A.out1 = k[3];
+        return launch_pair_nk<1, MODE_PAIR_STAGE>(ctx, s, A, cfg);
+    }
+    if (pi == 1) {
+        static const double a4[3] = {dp5::A41, dp5::A42, dp5::A43};
+        static const double a5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
+        for (int j = 0; j < 3; ++j) {
+            A.kin[j] = k[j + 1];
+            A.a[j] = a4[j];
+        }
+        for (int j = 0; j < 4; ++j) A.bk[j] = a5[j];
+        A.out0 = k[4];
+        A.out1 = k[5];
+        return launch_pair_nk<3, MODE_PAIR_STAGE>(ctx, s, A, cfg);
+    }
+    static const double a6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
+    for (int j = 0; j < 5; ++j) {
+        A.kin[j] = k[j + 1];
+        A.a[j] = a6[j];
+    }
+    A.out0 = state_sel(ctx, SEL_NEXT);       // y5
+    A.out1 = pair_sel(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_pair_nk<5, MODE_PAIR_DOPRI67>(ctx, s, A, cfg);
+}
+
 static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
+    if (pairs_on(ctx)) {
+        for (int pi = 0; pi < 3; ++pi) {
+            cudaError_t e = launch_dopri5_pair(ctx, s, pi, h, use_cond);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     for (int st = 2; st <= 7; ++st) {
         cudaError_t e = launch_dopri5_stage(ctx, s, st, h, use_cond);
         if (e != cudaSuccess) return e;
@@ -907,6 +1000,34 @@ gs_status gs_set_dopri5_split(gs_ctx* ctx, int mode) {
 
 int gs_get_dopri5_split(const gs_ctx* ctx) { return ctx && split67_on(ctx) ? 1 : 0; }
 
+gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode) {
+    if (!ctx || mode < -1 || mode > 1) return GS_ERR_INVALID;
+    if (mode == 1 && !form_ok(ctx, 4)) return GS_ERR_INVALID;
+    drop_graphs(ctx);
+    ctx->fuse = mode;
+    return GS_OK;
+}
+
+int gs_get_dopri5_fusion(const gs_ctx* ctx) { return ctx && pairs_on(ctx) ? 1 : 0; }
+
+gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth) {
+    if (!ctx || pair < -1 || pair > 2 || ty < 1 || ty > kPairMaxTY || depth < 1 || depth > kMaxDepth)
+        return GS_ERR_INVALID;
+    drop_graphs(ctx);
+    for (int pi = 0; pi < 3; ++pi)
+        if (pair < 0 || pair == pi) ctx->pc[pi] = KCfg{5, ty, 0, depth};
+    return GS_OK;
+}
+
+gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth) {
+    if (!ctx || !ty || !depth) return GS_ERR_INVALID;
+    for (int pi = 0; pi < 3; ++pi) {
+        ty[pi] = ctx->pc[pi].ty;
+        depth[pi] = ctx->pc[pi].depth;
+    }
+    return GS_OK;
+}
+
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth) {
     if (!ctx || depth < 1 || depth > kMaxDepth) return GS_ERR_INVALID;
     drop_graphs(ctx);
@@ -957,6 +1078,29 @@ static gs_status time_dp_kernel(gs_ctx* ctx, int k, int reps, cudaEvent_t e0, cu
     return GS_OK;
 }
 
+// time Dormand-Prince pair kernel pi with the configuration in ctx->pc[pi]
+static gs_status time_pair_kernel(gs_ctx* ctx, int pi, int reps, cudaEvent_t e0, cudaEvent_t e1, float* ms_out) {
+    float acc = 0.f;
+    for (int r = 0; r < reps + 1; ++r) {
+        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+        gs_status st = upload_ctrl(ctx);
+        if (st != GS_OK) return st;
+        CK(cudaEventRecord(e0, ctx->stream));
+        cudaError_t e = launch_dopri5_pair(ctx, ctx->stream, pi, 0, 0);
+        if (e != cudaSuccess) {
+            set_err(ctx, e, "autotune launch");
+            return GS_ERR_CUDA;
+        }
+        CK(cudaEventRecord(e1, ctx->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (r > 0) acc += ms;
+    }
+    *ms_out = acc / reps;
+    return GS_OK;
+}
+
 gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0]) return GS_ERR_INVALID;
     static const int cand[][2] = {{2, 0}, {4, 0}, {6, 0}, {8, 0}, {14, 0}, {4, 4}, {6, 4}, {8, 4}, {6, 16}, {8, 16}};
@@ -983,7 +1127,7 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         st = time_dp_kernel(ctx, k, 1, e0, e1, &ms);
     }
     KCfg best_cfg[7];
-    float total = 0.f;
+    float total = 0.f, stage_best[7] = {0, 0, 0, 0, 0, 0, 0};
     for (int k = 0; k < 7 && st == GS_OK; ++k) {
         float best = 1e30f;
         best_cfg[k] = dp_cfg(ctx, k);
@@ -1017,7 +1161,30 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         }
         ctx->dp[k] = saved;
         ctx->dp_tuned = saved_tuned;
+        stage_best[k] = best;
         total += best;
+    }
+    // stage pairs: every tile height x ring depth 1..3, then the automatic
+    // choice between pairs and single stages by the summed kernel times of an
+    // attempt
+    KCfg best_pc[3] = {ctx->pc[0], ctx->pc[1], ctx->pc[2]};
+    float pair_total = 0.f;
+    const bool tune_pairs = form_ok(ctx, 4) && (ctx->variant == 0 || ctx->variant == 4) && ctx->fuse != 0;
+    for (int pi = 0; pi < 3 && tune_pairs && st == GS_OK; ++pi) {
+        float best = 1e30f;
+        const KCfg saved = ctx->pc[pi];
+        for (int ty = 2; ty <= kPairMaxTY && st == GS_OK; ++ty)
+            for (int depth = 1; depth <= kMaxDepth && st == GS_OK; ++depth) {
+                ctx->pc[pi] = KCfg{5, ty, 0, depth};
+                float ms = 0.f;
+                if ((st = time_pair_kernel(ctx, pi, 3, e0, e1, &ms)) != GS_OK) break;
+                if (ms < best) {
+                    best = ms;
+                    best_pc[pi] = ctx->pc[pi];
+                }
+            }
+        ctx->pc[pi] = saved;
+        pair_total += best;
     }
     cudaStreamSynchronize(ctx->stream);
     cudaEventDestroy(e0);
@@ -1025,6 +1192,10 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     if (st != GS_OK) return st;
     for (int k = 0; k < 7; ++k) ctx->dp[k] = best_cfg[k];
     ctx->dp_tuned = true;
+    if (tune_pairs) {
+        for (int pi = 0; pi < 3; ++pi) ctx->pc[pi] = best_pc[pi];
+        ctx->fuse_auto = pair_total < total - stage_best[0];
+    }
     // the other integrators use the configuration of the one-input stage
     ctx->def = best_cfg[1];
     drop_graphs(ctx);
@@ -1066,6 +1237,40 @@ gs_status gs_time_stages(gs_ctx* ctx, int reps, double* ms) {
     for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
     if (st != GS_OK) return st;
     for (int k = 0; k < 7; ++k) ms[k] = acc[k] / reps;
+    return GS_OK;
+}
+
+gs_status gs_time_pairs(gs_ctx* ctx, int reps, double* ms) {
+    if (!ctx || !ctx->state[0] || reps < 1 || !ms) return GS_ERR_INVALID;
+    if (!form_ok(ctx, 4)) return GS_ERR_INVALID;
+    cudaEvent_t ev[5];
+    for (int i = 0; i < 5; ++i) CK(cudaEventCreate(&ev[i]));
+    double acc[4] = {0, 0, 0, 0};
+    gs_status st = GS_OK;
+    for (int r = 0; r < reps + 1 && st == GS_OK; ++r) {
+        init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+        if ((st = upload_ctrl(ctx)) != GS_OK) break;
+        cudaError_t e = cudaEventRecord(ev[0], ctx->stream);
+        if (e == cudaSuccess) e = launch_dopri5_k1(ctx, ctx->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[1], ctx->stream);
+        for (int pi = 0; pi < 3 && e == cudaSuccess; ++pi) {
+            e = launch_dopri5_pair(ctx, ctx->stream, pi, 0, 0);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[pi + 2], ctx->stream);
+        }
+        if (e == cudaSuccess) e = cudaEventSynchronize(ev[4]);
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+            if (r > 0) acc[k] += t;
+        }
+        if (e != cudaSuccess) {
+            set_err(ctx, e, "gs_time_pairs");
+            st = GS_ERR_CUDA;
+        }
+    }
+    for (int i = 0; i < 5; ++i) cudaEventDestroy(ev[i]);
+    if (st != GS_OK) return st;
+    for (int k = 0; k < 4; ++k) ms[k] = acc[k] / reps;
     return GS_OK;
 }
 

@@ -1,0 +1,476 @@
+// gs_pair.cuh -- two consecutive Runge-Kutta stages of the Gray-Scott system
+// in one pass over HBM.
+//
+// Stage i forms Y_i = u + dt sum_{j<i} a_ij k_j and k_i = F(Y_i) (Eq. 2: the
+// 7-point periodic Laplacian plus the u v^2 reaction).  Stage i+1 needs
+// Y_{i+1} = u + dt sum_{j<=i} a_{i+1,j} k_j at the six neighbours of every
+// cell, so k_i is needed on the tile plus a one-cell ring and Y_i on the tile
+// plus a two-cell ring.  This kernel computes k_i on that ring (the ring
+// cells are also computed by the neighbouring tiles) instead of storing k_i
+// and reading it back with a halo in a second launch: the pair reads u and
+// k_1..k_{i-1} once and writes k_i and k_{i+1}, i + 3 field passes instead
+// of 2i + 3.  Dormand-Prince stages 6 and 7 fuse the same way: stage 7's
+// input is y5 = u + dt sum_j b_j k_j (b7 = 0), so that pair reads u, k1..k5,
+// writes y5 and k7 (the next k1) and reduces the scaled error norm, with
+// the arithmetic of the split stages 6/7 (gs_staged.cuh): 8 field passes
+// instead of 13.
+//
+// Mapping (the staged form's, widened): a warp owns a row of 32*VX cells
+// (one 16-byte vector per lane).  The CTA has ty + 4 row warps for rows
+// y0-2 .. y0+ty+1 and one halo warp whose lane 2(r+2)+s owns the two x-halo
+// columns of row y0+r on side s (s = 0: x0-2, x0-1; s = 1: x0+aw,
+// x0+aw+1).  Planes advance in z with three phases per iteration:
+//   A(z+2): Y_i of plane z+2 on every row and halo column, from the inputs;
+//           stored in the Y_i plane buffer;
+//   B(z+1): k_i of plane z+1 on rows -1..ty and the two inner halo columns
+//           (centre plane from shared memory, z neighbours in registers),
+//           stored for the tile rows; Y_{i+1} of plane z+1 formed and stored
+//           in the Y_{i+1} plane buffer;
+//   C(z):   k_{i+1} of plane z on the tile rows, stored.
+// B reads the Y_i plane that A wrote one iteration earlier and C the Y_{i+1}
+// plane that B wrote one iteration earlier, so two buffers of each and one
+// barrier per iteration order every shared-memory access.  The inputs
+// arrive through the staged form's per-thread cp.async ring, DEPTH planes
+// ahead (a slot is written and read only by the thread that copies it).
+#pragma once
+
+#include "gs_staged.cuh"
+
+namespace gsk {
+
+constexpr int kPairMaxTY = 7;                        // rows per tile: ty + 5 warps (3 per SM sub-partition)
+constexpr int kPairThreads = 32 * (kPairMaxTY + 5);  // launch bound: 168 registers per thread
+
+template <typename T>
+__host__ __device__ constexpr int pair_vx() {
+    return 16 / (int)sizeof(T);
+}
+// a plane row: 2 halo cells on each side of the 32*VX main cells, the main
+// cells starting at a whole vector (column c at OFF + c, OFF = VX)
+template <int VX>
+__host__ __device__ constexpr int pair_pitch() {
+    return 32 * VX + 2 * VX;
+}
+// Y_i: 2 buffers x (ty + 4) rows; Y_{i+1}: 2 buffers x (ty + 2) rows; 2 components
+template <typename T>
+__host__ __device__ inline size_t pair_plane_bytes(int ty) {
+    return sizeof(T) * 2 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<pair_vx<T>()>();
+}
+// one ring slot: (ty + 4) rows x NA arrays x 32 lanes of 16-byte vectors,
+// then the halo lanes' pairs: NA arrays x 32 lanes x 2 cells
+template <typename T, int NK>
+__host__ __device__ inline size_t pair_slot_bytes(int ty) {
+    constexpr int NA = 2 * (1 + NK);
+    const size_t vec = (size_t)(ty + 4) * NA * 32 * 16;
+    const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
+    return (vec + halo + 15) / 16 * 16;
+}
+// Dormand-Prince pair: the inverse error scale of each thread's cells for
+// the three planes between A and C (thread-private, 3 x 2 components)
+template <int MODE>
+__host__ __device__ inline size_t pair_isc_bytes(int ty) {
+    return MODE == MODE_PAIR_DOPRI67 ? (size_t)3 * 2 * (ty + 4) * 32 * 16 : 0;
+}
+template <typename T, int NK, int MODE>
+__host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
+    return (pair_plane_bytes<T>(ty) + 15) / 16 * 16 + pair_isc_bytes<MODE>(ty) +
+           (size_t)depth * pair_slot_bytes<T, NK>(ty);
+}
+
+// Coefficients of one pair launch in T.
+template <typename T, int NK>
+struct PairCoef {
+    T a1[NK > 0 ? NK : 1];  // stage i: Y_i = u + dt sum_j a1_j k_j
+    T a2[NK + 1];           // stage i+1: Y_{i+1} = u + dt sum_j a2_j k_j (j <= i)
+    T dt, ta, tr;
+};
+
+template <typename T, int NK>
+__device__ __forceinline__ PairCoef<T, NK> pair_coef(const StageArgs& A, double dt, double atol, double rtol) {
+    PairCoef<T, NK> C;
+#pragma unroll
+    for (int j = 0; j < NK; ++j) C.a1[j] = (T)A.a[j];
+#pragma unroll
+    for (int j = 0; j <= NK; ++j) C.a2[j] = (T)A.bk[j];
+    C.dt = (T)dt;
+    C.ta = (T)atol;
+    C.tr = (T)rtol;
+    return C;
+}
+
+__device__ __forceinline__ int wrapm(int a, int n) {
+    const int m = a % n;
+    return m < 0 ? m + n : m;
+}
+
+// One segment: column (tx, tyi), output planes [z0, z1).  Called by every
+// thread of the CTA (it contains barriers: (z1 - z0) + 4 per segment, the
+// same count in the row warps and in the halo warp).
+template <typename T, int NK, int MODE>
+__device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const PairCoef<T, NK>& C,
+                                             T* SA, T* SB, unsigned char* SI, unsigned char* R, int depth, int TY,
+                                             int tx, int tyi, int z0, int z1, typename ErrBits<T>::U& ebits) {
+    constexpr int VX = pair_vx<T>();
+    constexpr int TXW = 32 * VX;
+    constexpr int PITCH = pair_pitch<VX>();
+    constexpr int OFF = VX;
+    constexpr int NA = 2 * (1 + NK);
+    constexpr bool DP = MODE == MODE_PAIR_DOPRI67;
+    static_assert(!DP || NK == 5, "Dormand-Prince stages 6/7 take k1..k5");
+    using VTy = typename VecT<T, VX>::type;
+    using V2 = typename VecT<T, 2>::type;
+    const int lane = threadIdx.x;
+    const int w = threadIdx.y;
+    const int RA = TY + 4, RB = TY + 2;
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const long long plane = (long long)nx * ny;
+    const T dt = C.dt;
+    // weight of k_i in Y_{i+1} (Dormand-Prince: y5 = ... + dt b6 k6) and the
+    // split stage-6/7 error constants
+    const T dta2 = DP ? dt * (T)dp5::B6 : dt * C.a2[NK];
+    const T dte6 = dt * (T)dp5::E6, dte7 = dt * (T)dp5::E7;
+    const T e67 = (T)(dp5::E6 + dp5::E7);
+    const T bw[4] = {(T)dp5::B1, (T)dp5::B3, (T)dp5::B4, (T)dp5::B5};
+    const T ew[3] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5};
+
+    const int x0 = tx * TXW, y0 = tyi * TY;
+    const int aw = min(TXW, nx - x0);
+    const int ah = min(TY, ny - y0);
+    const int nl = aw / VX;
+    const bool hw = (w == TY + 4);                  // the halo warp
+    const int r = hw ? (lane >> 1) - 2 : w - 2;     // this thread's row, relative to y0
+    const int side = lane & 1;                      // halo warp: 0 left, 1 right
+    const bool inA = hw ? (lane < 2 * (ah + 4)) : (r < ah + 2 && lane < nl);
+    const bool inB = inA && r >= -1 && r < ah + 1;
+    const bool inC = !hw && inA && r >= 0 && r < ah;
+    const long long rowbase = (long long)nx * wrapm(y0 + r, ny);
+    const long long cbase = rowbase + (hw ? (side == 0 ? wrapm(x0 - 2, nx) : wrapm(x0 + aw, nx)) : x0 + VX * lane);
+    const int col = hw ? (side == 0 ? -2 : aw) : VX * lane;  // shared-memory column of the first cell
+    const int hin = side == 0 ? -1 : aw;                      // halo warp: its inner column
+    const int hsel = side == 0 ? 1 : 0;                       // ... and its index in the pair
+
+    auto ia = [&](int b, int row, int c, int cx) -> int { return ((b * RA + row + 2) * 2 + c) * PITCH + OFF + cx; };
+    auto ib = [&](int b, int row, int c, int cx) -> int { return ((b * RB + row + 1) * 2 + c) * PITCH + OFF + cx; };
+    const size_t slot_bytes = pair_slot_bytes<T, NK>(TY);
+    const size_t vec_bytes = (size_t)RA * NA * 32 * 16;
+    auto rvec = [&](int s, int a) -> VTy* {
+        return reinterpret_cast<VTy*>(R + (size_t)s * slot_bytes) + ((size_t)w * NA + a) * 32 + lane;
+    };
+    // this thread's inverse-scale vector of component c in plane slot k (0..2)
+    auto siv = [&](int k, int c) -> VTy* {
+        return reinterpret_cast<VTy*>(SI) + ((size_t)(k * 2 + c) * RA + w) * 32 + lane;
+    };
+    auto rhal = [&](int s, int a) -> V2* {
+        return reinterpret_cast<V2*>(R + (size_t)s * slot_bytes + vec_bytes) + (size_t)a * 32 + lane;
+    };
+
+    // input plane q (z0 - 2 .. z1 + 1) into slot (q - z0 + 2) % depth
+    auto fetch = [&](int q) {
+        if (q <= z1 + 1 && inA) {
+            const int s = (q - z0 + 2) % depth;
+            const long long zo = plane * wrapm(q, nz);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+#pragma unroll
+                for (int f = 0; f <= NK; ++f) {
+                    const T* src = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]) + cbase + zo;
+                    if (hw)
+                        cp_async_vec<2 * sizeof(T)>(rhal(s, c * (1 + NK) + f), src);
+                    else
+                        cp_async_vec<sizeof(VTy)>(rvec(s, c * (1 + NK) + f), src);
+                }
+            }
+        }
+        cp_async_commit();  // one group per plane and thread, empty or not
+    };
+
+    // Y_i of NV consecutive cells from the slot (ld(a, v) loads array a), the
+    // second-stage partial P2 = u + dt sum_{j<i} a2_j k_j (Dormand-Prince:
+    // u + dt sum_{j=1,3,4,5} b_j k_j) and, for Dormand-Prince, the error terms
+    // Q = dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1) and the inverse
+    // error scale I = 1 / (atol + rtol (|u| + dt |k1|)).
+    auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I) {
+        constexpr int NV = sizeof(Y[0]) / sizeof(T);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            T uu[NV], s1[NV], s2[NV], k1v[NV], q[NV];
+            ld(c * (1 + NK), uu);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                s1[v] = T(0);
+                s2[v] = T(0);
+                k1v[v] = T(0);
+                q[v] = T(0);
+            }
+#pragma unroll
+            for (int j = 0; j < NK; ++j) {
+                T kk[NV];
+                ld(c * (1 + NK) + 1 + j, kk);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    s1[v] = (j == 0) ? C.a1[0] * kk[v] : s1[v] + C.a1[j] * kk[v];
+                    if (!DP) {
+                        s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
+                    } else if (j == 0) {
+                        k1v[v] = kk[v];
+                        s2[v] = bw[0] * kk[v];
+                    } else if (j >= 2) {
+                        s2[v] += bw[j - 1] * kk[v];
+                        q[v] += ew[j - 2] * (kk[v] - k1v[v]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s1[v];
+                P2[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s2[v];
+                if (DP) {
+                    Q[c][v] = dt * (q[v] - e67 * k1v[v]);
+                    I[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
+                }
+            }
+        }
+    };
+    auto react = [&](T yu, T yv, T lu, T lv, T& fu, T& fv) {
+        const T uvv = yu * yv * yv;
+        fu = g.Du * lu - uvv + g.F * (T(1) - yu);
+        fv = g.Dv * lv + uvv - (g.F + g.k) * yv;
+    };
+
+    for (int i = 0; i < depth; ++i) fetch(z0 - 2 + i);
+    const int nit = (z1 - z0) + 4;
+
+    if (!hw) {
+        // ---------------- row warps ----------------
+        T ya0[2][VX], ya1[2][VX], ya2[2][VX];  // Y_i at planes p-1, p, p+1 of phase B
+        T yb0[2][VX], yb1[2][VX], yb2[2][VX];  // Y_{i+1} at planes o-1, o, o+1 of phase C
+        T p2a[2][VX], p2b[2][VX];              // P2 formed in A / used in B
+        T qa[2][VX], qb[2][VX];                // Dormand-Prince: Q formed in A / used in B
+        T isc[2][VX];                          // ... inverse scale of plane q (kept in SI until C)
+        T epb[2][VX], epc[2][VX];              // ... error through k6: B -> C
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                ya0[c][v] = ya1[c][v] = ya2[c][v] = T(0);
+                yb0[c][v] = yb1[c][v] = yb2[c][v] = T(0);
+                p2a[c][v] = p2b[c][v] = qa[c][v] = qb[c][v] = T(0);
+                isc[c][v] = epb[c][v] = epc[c][v] = T(0);
+            }
+        for (int it = 0; it < nit; ++it) {
+            const int q = z0 - 2 + it;  // plane of A; B works on q - 1, C on q - 2
+            const int ba = it & 1, bp = ba ^ 1;
+            // ---- A(q)
+            cp_async_wait_pending(depth - 1);
+            if (inA) {
+                const int s = it % depth;
+                formA([&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, a)), out); }, ya2, p2a,
+                      qa, isc);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    stv<T, VX>(SA + ia(ba, r, c, col), ya2[c]);
+                    if (DP) stv<T, VX>(reinterpret_cast<T*>(siv(it % 3, c)), isc[c]);
+                }
+            }
+            fetch(q + depth);  // the slot's values are in registers: reuse it
+            // ---- B(q - 1)
+            if (it >= 2) {
+                const int p = q - 1;
+                T xl[2], xr[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    xl[c] = __shfl_up_sync(0xffffffffu, ya1[c][VX - 1], 1);
+                    xr[c] = __shfl_down_sync(0xffffffffu, ya1[c][0], 1);
+                }
+                if (inB) {
+                    T lap[2][VX];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (lane == 0) xl[c] = SA[ia(bp, r, c, -1)];
+                        if (lane == nl - 1) xr[c] = SA[ia(bp, r, c, aw)];
+                        T ys[VX], yn[VX];
+                        lds_v<T, VX>(SA + ia(bp, r - 1, c, col), ys);
+                        lds_v<T, VX>(SA + ia(bp, r + 1, c, col), yn);
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const T xm = (v == 0) ? xl[c] : ya1[c][v - 1];
+                            const T xp = (v == VX - 1) ? xr[c] : ya1[c][v + 1];
+                            const T yy = ya1[c][v];
+                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
+                                        (ya0[c][v] - T(2) * yy + ya2[c][v]) * g.cz;
+                        }
+                    }
+                    T f[2][VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) react(ya1[0][v], ya1[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    const bool own = r >= 0 && r < ah && p >= z0 && p < z1;
+                    const long long gi = cbase + plane * p;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c)
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            yb2[c][v] = p2b[c][v] + dta2 * f[c][v];
+                            if (DP) epb[c][v] = qb[c][v] + dte6 * f[c][v];
+                        }
+                    if (own) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) stv<T, VX>(P.o0[c] + gi, DP ? yb2[c] : f[c]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) stv<T, VX>(SB + ib(ba, r, c, col), yb2[c]);
+                }
+            }
+            // ---- C(q - 2)
+            if (it >= 4) {
+                const int o = q - 2;
+                T xl[2], xr[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    xl[c] = __shfl_up_sync(0xffffffffu, yb1[c][VX - 1], 1);
+                    xr[c] = __shfl_down_sync(0xffffffffu, yb1[c][0], 1);
+                }
+                if (inC) {
+                    T lap[2][VX];
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        if (lane == 0) xl[c] = SB[ib(bp, r, c, -1)];
+                        if (lane == nl - 1) xr[c] = SB[ib(bp, r, c, aw)];
+                        T ys[VX], yn[VX];
+                        lds_v<T, VX>(SB + ib(bp, r - 1, c, col), ys);
+                        lds_v<T, VX>(SB + ib(bp, r + 1, c, col), yn);
+#pragma unroll
+                        for (int v = 0; v < VX; ++v) {
+                            const T xm = (v == 0) ? xl[c] : yb1[c][v - 1];
+                            const T xp = (v == VX - 1) ? xr[c] : yb1[c][v + 1];
+                            const T yy = yb1[c][v];
+                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
+                                        (yb0[c][v] - T(2) * yy + yb2[c][v]) * g.cz;
+                        }
+                    }
+                    T f[2][VX];
+#pragma unroll
+                    for (int v = 0; v < VX; ++v) react(yb1[0][v], yb1[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    const long long gi = cbase + plane * o;
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        stv<T, VX>(P.o1[c] + gi, f[c]);
+                        if (DP) {
+                            T sc[VX];
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv((it + 1) % 3, c)), sc);  // plane q - 2
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) {
+                                const T err = epc[c][v] + dte7 * f[c][v];
+                                ebits = max(ebits, ErrBits<T>::bits(fabs(err) * sc[v]));
+                            }
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+                for (int v = 0; v < VX; ++v) {
+                    ya0[c][v] = ya1[c][v];
+                    ya1[c][v] = ya2[c][v];
+                    yb0[c][v] = yb1[c][v];
+                    yb1[c][v] = yb2[c][v];
+                    p2b[c][v] = p2a[c][v];
+                    if (DP) {
+                        qb[c][v] = qa[c][v];
+                        epc[c][v] = epb[c][v];
+                    }
+                }
+            __syncthreads();
+        }
+    } else {
+        // ---------------- halo warp: the inner halo column of its row and side ----------------
+        T h0[2] = {T(0), T(0)}, h1[2] = {T(0), T(0)}, h2[2] = {T(0), T(0)};  // Y_i, planes p-1, p, p+1
+        T hp2a[2] = {T(0), T(0)}, hp2b[2] = {T(0), T(0)};
+        for (int it = 0; it < nit; ++it) {
+            const int ba = it & 1, bp = ba ^ 1;
+            cp_async_wait_pending(depth - 1);
+            if (inA) {
+                const int s = it % depth;
+                T Y[2][2], P2[2][2], Qd[2][2], Id[2][2];
+                formA(
+                    [&](int a, T* out) {
+                        const V2 q2 = *rhal(s, a);
+                        out[0] = reinterpret_cast<const T*>(&q2)[0];
+                        out[1] = reinterpret_cast<const T*>(&q2)[1];
+                    },
+                    Y, P2, Qd, Id);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    V2 st;
+                    reinterpret_cast<T*>(&st)[0] = Y[c][0];
+                    reinterpret_cast<T*>(&st)[1] = Y[c][1];
+                    *reinterpret_cast<V2*>(SA + ia(ba, r, c, col)) = st;
+                    h2[c] = Y[c][hsel];
+                    hp2a[c] = P2[c][hsel];
+                }
+            }
+            fetch(z0 - 2 + it + depth);
+            if (it >= 2 && inB) {
+                T lap[2];
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const T xm = SA[ia(bp, r, c, hin - 1)];
+                    const T xp = SA[ia(bp, r, c, hin + 1)];
+                    const T ys = SA[ia(bp, r - 1, c, hin)];
+                    const T yn = SA[ia(bp, r + 1, c, hin)];
+                    const T yy = h1[c];
+                    lap[c] = (xm - T(2) * yy + xp) * g.cx + (ys - T(2) * yy + yn) * g.cy + (h0[c] - T(2) * yy + h2[c]) * g.cz;
+                }
+                T f[2];
+                react(h1[0], h1[1], lap[0], lap[1], f[0], f[1]);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) SB[ib(ba, r, c, hin)] = hp2b[c] + dta2 * f[c];
+            }
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                h0[c] = h1[c];
+                h1[c] = h2[c];
+                hp2b[c] = hp2a[c];
+            }
+            __syncthreads();
+        }
+    }
+    cp_async_wait_pending(0);  // no copy may land in the ring after this segment
+    __syncthreads();           // the plane buffers are reused by the next segment
+}
+
+template <typename T, int NK, int MODE>
+__global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* SA = reinterpret_cast<T*>(smem_raw);
+    T* SB = SA + 2 * (size_t)(A.ty + 4) * 2 * pair_pitch<pair_vx<T>()>();
+    unsigned char* SI = smem_raw + (pair_plane_bytes<T>(A.ty) + 15) / 16 * 16;
+    unsigned char* R = SI + pair_isc_bytes<MODE>(A.ty);
+    __shared__ T red[32];
+    __shared__ int s_last;
+
+    int parity = 0;
+    long long step = 0;
+    double dtd = 0.0, atol = 0.0, rtol = 0.0;
+    int skip = 0;
+    if (A.ctrl) {
+        parity = A.ctrl->parity;
+        step = A.ctrl->step;
+        dtd = A.ctrl->dt_try;
+        atol = A.ctrl->atol;
+        rtol = A.ctrl->rtol;
+        skip = A.ctrl->done;
+    }
+    const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, parity, step, 0);
+    const PairCoef<T, NK> C = pair_coef<T, NK>(A, dtd, atol, rtol);
+    typename ErrBits<T>::U ebits = 0;
+    if (!skip) {
+        for_each_segment(A, g.nz, [&](int col, int z0, int z1) {
+            pair_segment<T, NK, MODE>(g, P, C, SA, SB, SI, R, depth, A.ty, col % A.ntx, col / A.ntx, z0, z1, ebits);
+        });
+    }
+    const T emax = ErrBits<T>::value(ebits);
+    if (MODE == MODE_PAIR_DOPRI67 && A.run_ctrl && A.ctrl) final_kernel_epilogue<T, MODE>(A, emax, red, &s_last);
+}
+
+}  // namespace gsk

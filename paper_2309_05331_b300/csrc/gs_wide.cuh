@@ -386,7 +386,7 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
 template <typename T, int MODE>
 __device__ __forceinline__ void final_kernel_epilogue(const StageArgs& A, T emax, T* red, int* s_last) {
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
-    if (MODE == MODE_DOPRI_FINAL || MODE == MODE_DOPRI_S7) {
+    if (MODE == MODE_DOPRI_FINAL || MODE == MODE_DOPRI_S7 || MODE == MODE_PAIR_DOPRI67) {
         const T bmax = block_nanmax(emax, red);
         if (tid == 0) atomic_max_nonneg(&A.ctrl->err_bits, (double)bmax);
     }

@@ -191,6 +191,7 @@ def test_split_stages_match_unsplit_and_oracle(prec, dims):
     res = []
     for split in (1, 0):
         g = _gs(torch, dims, prec, u0, v0, **phys)
+        gs.gs_set_dopri5_fusion(g.ctx, 0)
         gs.gs_set_dopri5_split(g.ctx, split)
         g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
         res.append((to_np(g.u), to_np(g.v)))
@@ -228,6 +229,82 @@ def test_rk4_small_grid_path_matches_graph_path(prec, nsteps, ctas):
         assert oracle.rel_l2(list(r), [ou, ov]) < tol
     if prec == 0:
         assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-14
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (8, 1, 1), (136, 13, 5)])
+@pytest.mark.parametrize("ty,depth", [(7, 2), (1, 1), (3, 3), (5, 1)])
+def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth):
+    """Fixed Dopri5 steps with the stages in pairs (2+3, 4+5, 6+7 in one
+    launch each, the first stage recomputed on a one-cell ring) against the
+    oracle and against the single-stage kernels; ragged x tiles (132, 136,
+    260), tile heights that do and do not divide ny, single-plane z, every
+    ring depth.  FP64: pairs and single stages agree to 1e-13 (Y_{i+1} is
+    summed in another order)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    phys = dict(Du=3e-3, Dv=1.5e-3, L=max(2.5, dims[0] * 2.5 / 45))
+    u0, v0 = si.gs_initial_state(*dims, seed=47)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(*dims, **phys), u0, v0, oracle.DOPRI5, 0.25, 3)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    res = []
+    for fusion in (1, 0):
+        g = _gs(torch, dims, prec, u0, v0, **phys)
+        gs.gs_set_dopri5_fusion(g.ctx, fusion)
+        gs.gs_set_pair_config(g.ctx, -1, ty, depth)
+        assert gs.gs_get_dopri5_fusion(g.ctx) == fusion
+        assert gs.gs_get_pair_configs(g.ctx) == [(ty, depth)] * 3
+        t = g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
+        assert abs(t - 0.75) < 1e-15
+        res.append((to_np(g.u), to_np(g.v)))
+        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, fusion
+        g.close()
+    if prec == 0:
+        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+
+
+def test_pairs_per_pair_configs_and_timing():
+    """Different launch shapes per pair give the same result; gs_time_pairs
+    times k1 and the three pair kernels without touching the state."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (68, 23, 11)
+    u0, v0 = si.gs_initial_state(*dims, seed=5)
+    res = []
+    for cfgs in ([(7, 1), (2, 3), (4, 2)], [(3, 2), (6, 1), (1, 3)]):
+        g = _gs(torch, dims, gs.GS_FP64, u0, v0, Du=2e-3, Dv=1e-3)
+        gs.gs_set_dopri5_fusion(g.ctx, 1)
+        for pi, (ty, d) in enumerate(cfgs):
+            gs.gs_set_pair_config(g.ctx, pi, ty, d)
+        assert gs.gs_get_pair_configs(g.ctx) == cfgs
+        ms = gs.gs_time_pairs(g.ctx, reps=2)
+        assert len(ms) == 4 and all(m > 0 for m in ms)
+        assert np.array_equal(to_np(g.u), u0) and np.array_equal(to_np(g.v), v0)
+        g.step(gs.GS_DOPRI5, 0.0, 0.2, 2)
+        res.append((to_np(g.u), to_np(g.v)))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
+def test_pairs_rejected_without_staged_form():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    g = _gs(torch, (9, 4, 4), gs.GS_FP32, *si.gs_initial_state(9, 4, 4))
+    assert gs.gs_get_dopri5_fusion(g.ctx) == 0
+    with pytest.raises(RuntimeError):
+        gs.gs_set_dopri5_fusion(g.ctx, 1)
+    with pytest.raises(RuntimeError):
+        gs.gs_time_pairs(g.ctx)
+    g.close()
+    g = _gs(torch, (8, 4, 4), gs.GS_FP32, *si.gs_initial_state(8, 4, 4))
+    for bad in [(0, 0, 1), (0, 8, 1), (0, 3, 0), (0, 3, 4), (3, 3, 1), (-2, 3, 1)]:
+        with pytest.raises(RuntimeError):
+            gs.gs_set_pair_config(g.ctx, *bad)
+    with pytest.raises(RuntimeError):
+        gs.gs_set_dopri5_fusion(g.ctx, 2)
+    g.close()
 
 
 def test_split_rejected_without_staged_form():
@@ -270,19 +347,22 @@ def test_vectorised_variant_rejects_unaligned_rows():
     g.close()
 
 
-@pytest.mark.parametrize("split", [1, 0])
-def test_adaptive_fp64_matches_oracle_run(split):
+@pytest.mark.parametrize("fusion,split", [(1, 1), (0, 1), (0, 0)])
+def test_adaptive_fp64_matches_oracle_run(fusion, split):
     """Error-controlled Dopri5 on 16^3 FP64: same accepted/rejected counts and
     step sizes as the oracle's own adaptive run, final state within 1e-12;
-    with Dormand-Prince stages 6/7 split (stage 6 forms y5 and the error terms
-    of k1..k6) and unsplit."""
+    with the stages in pairs (stages 6+7 reduce the error norm in one
+    launch), and single stages with stages 6/7 split (stage 6 forms y5 and
+    the error terms of k1..k6) and unsplit."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     dims = (16, 16, 16)
     phys = dict(Du=2e-3, Dv=1e-3)
     u0, v0 = si.gs_initial_state(*dims, seed=2)
     g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    gs.gs_set_dopri5_fusion(g.ctx, fusion)
     gs.gs_set_dopri5_split(g.ctx, split)
+    assert gs.gs_get_dopri5_fusion(g.ctx) == fusion
     assert gs.gs_get_dopri5_split(g.ctx) == split
     gs.gs_set_step_log(g.ctx, 10000)
     r = g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 0.1)
@@ -396,10 +476,12 @@ def _light_cone_check(state_after, u0, v0, dims, method, dt, nsteps, radius, cen
     assert err < tol, err
 
 
-def test_full_size_256cubed_fp32_dopri5_sampled():
+@pytest.mark.parametrize("fusion", [1, 0])
+def test_full_size_256cubed_fp32_dopri5_sampled(fusion):
     """256^3 FP32 (the large adaptive workload's grid and kernels, autotuned
-    tile): 3 fixed Dopri5 steps, 12 sampled cells against the oracle on their
-    dependence cones (radius 6 per step)."""
+    launch shapes; stage pairs and single stages): 3 fixed Dopri5 steps, 12
+    sampled cells against the oracle on their dependence cones (radius 6 per
+    step)."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     n = 256
@@ -407,6 +489,7 @@ def test_full_size_256cubed_fp32_dopri5_sampled():
     u0, v0 = _round32(u0), _round32(v0)
     g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
     gs.gs_autotune(g.ctx)
+    gs.gs_set_dopri5_fusion(g.ctx, fusion)  # the tuned launch shapes of either path
     g.step(gs.GS_DOPRI5, 0.0, 0.5, 3)
     gu, gv = to_np(g.u), to_np(g.v)
     rng = np.random.default_rng(0)
