@@ -23,16 +23,22 @@
 //   A(z+2): Y_i of plane z+2 on every row and halo column, from the inputs;
 //           stored in the Y_i plane buffer;
 //   B(z+1): k_i of plane z+1 on rows -1..ty and the two inner halo columns
-//           (centre plane from shared memory, z neighbours in registers),
-//           stored for the tile rows; Y_{i+1} of plane z+1 formed and stored
-//           in the Y_{i+1} plane buffer;
+//           (7-point stencil on the Y_i planes z, z+1, z+2), stored for the
+//           tile rows; Y_{i+1} of plane z+1 formed and stored in the Y_{i+1}
+//           plane buffer;
 //   C(z):   k_{i+1} of plane z on the tile rows, stored.
-// B reads the Y_i plane that A wrote one iteration earlier and C the Y_{i+1}
-// plane that B wrote one iteration earlier, so two buffers of each and one
-// barrier per iteration order every shared-memory access.  The inputs
-// arrive through the staged form's per-thread cp.async ring, DEPTH planes
-// ahead (a slot is written and read only by the thread that copies it).
+// B reads the Y_i plane that A wrote one iteration earlier (neighbours) and
+// its own cells of the plane before (lower z neighbour); C likewise on the
+// Y_{i+1} planes.  Three buffers of each and one barrier per iteration order
+// every shared-memory access: a buffer is rewritten three iterations after
+// it was filled, after the last iteration that reads another thread's cells
+// from it.  The upper z neighbour and the centre stay in registers.  The
+// inputs arrive through the staged form's per-thread cp.async ring, DEPTH
+// planes ahead (a slot is written and read only by the thread that copies
+// it).
 #pragma once
+
+#include <type_traits>
 
 #include "gs_staged.cuh"
 
@@ -51,10 +57,10 @@ template <int VX>
 __host__ __device__ constexpr int pair_pitch() {
     return 32 * VX + 2 * VX;
 }
-// Y_i: 2 buffers x (ty + 4) rows; Y_{i+1}: 2 buffers x (ty + 2) rows; 2 components
+// Y_i: 3 buffers x (ty + 4) rows; Y_{i+1}: 3 buffers x (ty + 2) rows; 2 components
 template <typename T>
 __host__ __device__ inline size_t pair_plane_bytes(int ty) {
-    return sizeof(T) * 2 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<pair_vx<T>()>();
+    return sizeof(T) * 3 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<pair_vx<T>()>();
 }
 // one ring slot: (ty + 4) rows x NA arrays x 32 lanes of 16-byte vectors,
 // then the halo lanes' pairs: NA arrays x 32 lanes x 2 cells
@@ -156,7 +162,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     auto rvec = [&](int s, int a) -> VTy* {
         return reinterpret_cast<VTy*>(R + (size_t)s * slot_bytes) + ((size_t)w * NA + a) * 32 + lane;
     };
-    // this thread's inverse-scale vector of component c in plane slot k (0..2)
+    // this thread's inverse-scale vector of component c in plane buffer k (0..2)
     auto siv = [&](int k, int c) -> VTy* {
         return reinterpret_cast<VTy*>(SI) + ((size_t)(k * 2 + c) * RA + w) * 32 + lane;
     };
@@ -164,10 +170,9 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
         return reinterpret_cast<V2*>(R + (size_t)s * slot_bytes + vec_bytes) + (size_t)a * 32 + lane;
     };
 
-    // input plane q (z0 - 2 .. z1 + 1) into slot (q - z0 + 2) % depth
-    auto fetch = [&](int q) {
+    // input plane q (z0 - 2 .. z1 + 1) into ring slot s
+    auto fetch = [&](int q, int s) {
         if (q <= z1 + 1 && inA) {
-            const int s = (q - z0 + 2) % depth;
             const long long zo = plane * wrapm(q, nz);
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -184,13 +189,14 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
         cp_async_commit();  // one group per plane and thread, empty or not
     };
 
-    // Y_i of NV consecutive cells from the slot (ld(a, v) loads array a), the
-    // second-stage partial P2 = u + dt sum_{j<i} a2_j k_j (Dormand-Prince:
-    // u + dt sum_{j=1,3,4,5} b_j k_j) and, for Dormand-Prince, the error terms
-    // Q = dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1) and the inverse
-    // error scale I = 1 / (atol + rtol (|u| + dt |k1|)).
-    auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I) {
+    // Y_i of NV consecutive cells from the slot (ld(a, v) loads array a) and
+    // the second-stage partial P2 = u + dt sum_{j<i} a2_j k_j (Dormand-Prince:
+    // u + dt sum_{j=1,3,4,5} b_j k_j); with E (Dormand-Prince tile rows) also
+    // the error terms Q = dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1) and
+    // the inverse error scale I = 1 / (atol + rtol (|u| + dt |k1|)).
+    auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I, auto E) {
         constexpr int NV = sizeof(Y[0]) / sizeof(T);
+        constexpr bool WE = DP && decltype(E)::value;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             T uu[NV], s1[NV], s2[NV], k1v[NV], q[NV];
@@ -216,7 +222,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         s2[v] = bw[0] * kk[v];
                     } else if (j >= 2) {
                         s2[v] += bw[j - 1] * kk[v];
-                        q[v] += ew[j - 2] * (kk[v] - k1v[v]);
+                        if (WE) q[v] += ew[j - 2] * (kk[v] - k1v[v]);
                     }
                 }
             }
@@ -224,7 +230,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             for (int v = 0; v < NV; ++v) {
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s1[v];
                 P2[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s2[v];
-                if (DP) {
+                if (WE) {
                     Q[c][v] = dt * (q[v] - e67 * k1v[v]);
                     I[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
                 }
@@ -237,194 +243,203 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
         fv = g.Dv * lv + uvv - (g.F + g.k) * yv;
     };
 
-    for (int i = 0; i < depth; ++i) fetch(z0 - 2 + i);
+    for (int i = 0; i < depth; ++i) fetch(z0 - 2 + i, i);
     const int nit = (z1 - z0) + 4;
 
+    // Plane buffers cycle through 3: Y_i of plane q in buffer b = it mod 3,
+    // Y_{i+1} of plane q - 1 in buffer b too; so the centre planes of B and C
+    // are in buffer b - 1 and their lower z neighbours (own cells) in b - 2.
     if (!hw) {
         // ---------------- row warps ----------------
-        T ya0[2][VX], ya1[2][VX], ya2[2][VX];  // Y_i at planes p-1, p, p+1 of phase B
-        T yb0[2][VX], yb1[2][VX], yb2[2][VX];  // Y_{i+1} at planes o-1, o, o+1 of phase C
-        T p2a[2][VX], p2b[2][VX];              // P2 formed in A / used in B
-        T qa[2][VX], qb[2][VX];                // Dormand-Prince: Q formed in A / used in B
-        T isc[2][VX];                          // ... inverse scale of plane q (kept in SI until C)
-        T epb[2][VX], epc[2][VX];              // ... error through k6: B -> C
+        // Values carried from one iteration to the next alternate between the
+        // X and Y sets (the loop is unrolled twice), so nothing is copied.
+        T yaX[2][VX], yaY[2][VX];  // Y_i of plane q (A's output; B's centre one iteration later)
+        T ybX[2][VX], ybY[2][VX];  // Y_{i+1} of plane q - 1 (B's output; C's centre one iteration later)
+        T p2X[2][VX], p2Y[2][VX];  // P2 (A -> B)
+        T qX[2][VX], qY[2][VX];    // Dormand-Prince: Q (A -> B)
+        T epX[2][VX], epY[2][VX];  // Dormand-Prince: error through k6 (B -> C)
+        T isc[2][VX];              // Dormand-Prince: inverse scale (A -> SI -> C)
 #pragma unroll
         for (int c = 0; c < 2; ++c)
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
-                ya0[c][v] = ya1[c][v] = ya2[c][v] = T(0);
-                yb0[c][v] = yb1[c][v] = yb2[c][v] = T(0);
-                p2a[c][v] = p2b[c][v] = qa[c][v] = qb[c][v] = T(0);
-                isc[c][v] = epb[c][v] = epc[c][v] = T(0);
+                yaX[c][v] = yaY[c][v] = ybX[c][v] = ybY[c][v] = T(0);
+                p2X[c][v] = p2Y[c][v] = qX[c][v] = qY[c][v] = epX[c][v] = epY[c][v] = isc[c][v] = T(0);
             }
-        for (int it = 0; it < nit; ++it) {
-            const int q = z0 - 2 + it;  // plane of A; B works on q - 1, C on q - 2
-            const int ba = it & 1, bp = ba ^ 1;
+        const bool wide = DP && inC;  // rows whose error terms are needed
+        auto body = [&](int it, int b, int sA, T(&yaN)[2][VX], const T(&yaC)[2][VX], T(&ybN)[2][VX],
+                        const T(&ybC)[2][VX], T(&p2N)[2][VX], const T(&p2C)[2][VX], T(&qN)[2][VX],
+                        const T(&qC)[2][VX], T(&epN)[2][VX], const T(&epC)[2][VX]) {
+            const int q = z0 - 2 + it;
+            const int b1 = b == 0 ? 2 : b - 1, b2 = b == 2 ? 0 : b + 1;  // planes q - 1 and q - 2
             // ---- A(q)
             cp_async_wait_pending(depth - 1);
             if (inA) {
-                const int s = it % depth;
-                formA([&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(s, a)), out); }, ya2, p2a,
-                      qa, isc);
+                auto ld = [&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(sA, a)), out); };
+                if (wide)
+                    formA(ld, yaN, p2N, qN, isc, std::true_type{});
+                else
+                    formA(ld, yaN, p2N, qN, isc, std::false_type{});
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    stv<T, VX>(SA + ia(ba, r, c, col), ya2[c]);
-                    if (DP) stv<T, VX>(reinterpret_cast<T*>(siv(it % 3, c)), isc[c]);
+                    stv<T, VX>(SA + ia(b, r, c, col), yaN[c]);
+                    if (wide) stv<T, VX>(reinterpret_cast<T*>(siv(b, c)), isc[c]);
                 }
             }
-            fetch(q + depth);  // the slot's values are in registers: reuse it
-            // ---- B(q - 1)
+            fetch(q + depth, sA);  // the slot's values are in registers: reuse it
+            // ---- B(p), p = q - 1: centre yaC, upper z neighbour yaN
             if (it >= 2) {
                 const int p = q - 1;
                 T xl[2], xr[2];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    xl[c] = __shfl_up_sync(0xffffffffu, ya1[c][VX - 1], 1);
-                    xr[c] = __shfl_down_sync(0xffffffffu, ya1[c][0], 1);
+                    xl[c] = __shfl_up_sync(0xffffffffu, yaC[c][VX - 1], 1);
+                    xr[c] = __shfl_down_sync(0xffffffffu, yaC[c][0], 1);
                 }
                 if (inB) {
                     T lap[2][VX];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        if (lane == 0) xl[c] = SA[ia(bp, r, c, -1)];
-                        if (lane == nl - 1) xr[c] = SA[ia(bp, r, c, aw)];
-                        T ys[VX], yn[VX];
-                        lds_v<T, VX>(SA + ia(bp, r - 1, c, col), ys);
-                        lds_v<T, VX>(SA + ia(bp, r + 1, c, col), yn);
+                        if (lane == 0) xl[c] = SA[ia(b1, r, c, -1)];
+                        if (lane == nl - 1) xr[c] = SA[ia(b1, r, c, aw)];
+                        T ys[VX], yn[VX], zm[VX];
+                        lds_v<T, VX>(SA + ia(b1, r - 1, c, col), ys);
+                        lds_v<T, VX>(SA + ia(b1, r + 1, c, col), yn);
+                        lds_v<T, VX>(SA + ia(b2, r, c, col), zm);
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            const T xm = (v == 0) ? xl[c] : ya1[c][v - 1];
-                            const T xp = (v == VX - 1) ? xr[c] : ya1[c][v + 1];
-                            const T yy = ya1[c][v];
+                            const T xm = (v == 0) ? xl[c] : yaC[c][v - 1];
+                            const T xp = (v == VX - 1) ? xr[c] : yaC[c][v + 1];
+                            const T yy = yaC[c][v];
                             lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
-                                        (ya0[c][v] - T(2) * yy + ya2[c][v]) * g.cz;
+                                        (zm[v] - T(2) * yy + yaN[c][v]) * g.cz;
                         }
                     }
                     T f[2][VX];
 #pragma unroll
-                    for (int v = 0; v < VX; ++v) react(ya1[0][v], ya1[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    for (int v = 0; v < VX; ++v) react(yaC[0][v], yaC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
                     const bool own = r >= 0 && r < ah && p >= z0 && p < z1;
                     const long long gi = cbase + plane * p;
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            yb2[c][v] = p2b[c][v] + dta2 * f[c][v];
-                            if (DP) epb[c][v] = qb[c][v] + dte6 * f[c][v];
+                            ybN[c][v] = p2C[c][v] + dta2 * f[c][v];
+                            if (DP) epN[c][v] = qC[c][v] + dte6 * f[c][v];
                         }
                     if (own) {
 #pragma unroll
-                        for (int c = 0; c < 2; ++c) stv<T, VX>(P.o0[c] + gi, DP ? yb2[c] : f[c]);
+                        for (int c = 0; c < 2; ++c) stv<T, VX>(P.o0[c] + gi, DP ? ybN[c] : f[c]);
                     }
 #pragma unroll
-                    for (int c = 0; c < 2; ++c) stv<T, VX>(SB + ib(ba, r, c, col), yb2[c]);
+                    for (int c = 0; c < 2; ++c) stv<T, VX>(SB + ib(b, r, c, col), ybN[c]);
                 }
             }
-            // ---- C(q - 2)
+            // ---- C(o), o = q - 2: centre ybC, upper z neighbour ybN
             if (it >= 4) {
                 const int o = q - 2;
                 T xl[2], xr[2];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    xl[c] = __shfl_up_sync(0xffffffffu, yb1[c][VX - 1], 1);
-                    xr[c] = __shfl_down_sync(0xffffffffu, yb1[c][0], 1);
+                    xl[c] = __shfl_up_sync(0xffffffffu, ybC[c][VX - 1], 1);
+                    xr[c] = __shfl_down_sync(0xffffffffu, ybC[c][0], 1);
                 }
                 if (inC) {
                     T lap[2][VX];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        if (lane == 0) xl[c] = SB[ib(bp, r, c, -1)];
-                        if (lane == nl - 1) xr[c] = SB[ib(bp, r, c, aw)];
-                        T ys[VX], yn[VX];
-                        lds_v<T, VX>(SB + ib(bp, r - 1, c, col), ys);
-                        lds_v<T, VX>(SB + ib(bp, r + 1, c, col), yn);
+                        if (lane == 0) xl[c] = SB[ib(b1, r, c, -1)];
+                        if (lane == nl - 1) xr[c] = SB[ib(b1, r, c, aw)];
+                        T ys[VX], yn[VX], zm[VX];
+                        lds_v<T, VX>(SB + ib(b1, r - 1, c, col), ys);
+                        lds_v<T, VX>(SB + ib(b1, r + 1, c, col), yn);
+                        lds_v<T, VX>(SB + ib(b2, r, c, col), zm);
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
-                            const T xm = (v == 0) ? xl[c] : yb1[c][v - 1];
-                            const T xp = (v == VX - 1) ? xr[c] : yb1[c][v + 1];
-                            const T yy = yb1[c][v];
+                            const T xm = (v == 0) ? xl[c] : ybC[c][v - 1];
+                            const T xp = (v == VX - 1) ? xr[c] : ybC[c][v + 1];
+                            const T yy = ybC[c][v];
                             lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
-                                        (yb0[c][v] - T(2) * yy + yb2[c][v]) * g.cz;
+                                        (zm[v] - T(2) * yy + ybN[c][v]) * g.cz;
                         }
                     }
                     T f[2][VX];
 #pragma unroll
-                    for (int v = 0; v < VX; ++v) react(yb1[0][v], yb1[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    for (int v = 0; v < VX; ++v) react(ybC[0][v], ybC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
                     const long long gi = cbase + plane * o;
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         stv<T, VX>(P.o1[c] + gi, f[c]);
                         if (DP) {
                             T sc[VX];
-                            lds_v<T, VX>(reinterpret_cast<const T*>(siv((it + 1) % 3, c)), sc);  // plane q - 2
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, c)), sc);  // plane q - 2
 #pragma unroll
                             for (int v = 0; v < VX; ++v) {
-                                const T err = epc[c][v] + dte7 * f[c][v];
+                                const T err = epC[c][v] + dte7 * f[c][v];
                                 ebits = max(ebits, ErrBits<T>::bits(fabs(err) * sc[v]));
                             }
                         }
                     }
                 }
             }
-#pragma unroll
-            for (int c = 0; c < 2; ++c)
-#pragma unroll
-                for (int v = 0; v < VX; ++v) {
-                    ya0[c][v] = ya1[c][v];
-                    ya1[c][v] = ya2[c][v];
-                    yb0[c][v] = yb1[c][v];
-                    yb1[c][v] = yb2[c][v];
-                    p2b[c][v] = p2a[c][v];
-                    if (DP) {
-                        qb[c][v] = qa[c][v];
-                        epc[c][v] = epb[c][v];
-                    }
-                }
             __syncthreads();
+        };
+        int b = 0, sA = 0;
+        auto advance = [&]() {
+            b = b == 2 ? 0 : b + 1;
+            sA = sA + 1 == depth ? 0 : sA + 1;
+        };
+        for (int it = 0; it < nit; it += 2) {
+            body(it, b, sA, yaX, yaY, ybX, ybY, p2X, p2Y, qX, qY, epX, epY);
+            advance();
+            if (it + 1 < nit) {
+                body(it + 1, b, sA, yaY, yaX, ybY, ybX, p2Y, p2X, qY, qX, epY, epX);
+                advance();
+            }
         }
     } else {
         // ---------------- halo warp: the inner halo column of its row and side ----------------
         T h0[2] = {T(0), T(0)}, h1[2] = {T(0), T(0)}, h2[2] = {T(0), T(0)};  // Y_i, planes p-1, p, p+1
         T hp2a[2] = {T(0), T(0)}, hp2b[2] = {T(0), T(0)};
+        int b = 0, sA = 0;
         for (int it = 0; it < nit; ++it) {
-            const int ba = it & 1, bp = ba ^ 1;
+            const int b1 = b == 0 ? 2 : b - 1;
             cp_async_wait_pending(depth - 1);
             if (inA) {
-                const int s = it % depth;
                 T Y[2][2], P2[2][2], Qd[2][2], Id[2][2];
                 formA(
                     [&](int a, T* out) {
-                        const V2 q2 = *rhal(s, a);
+                        const V2 q2 = *rhal(sA, a);
                         out[0] = reinterpret_cast<const T*>(&q2)[0];
                         out[1] = reinterpret_cast<const T*>(&q2)[1];
                     },
-                    Y, P2, Qd, Id);
+                    Y, P2, Qd, Id, std::false_type{});
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     V2 st;
                     reinterpret_cast<T*>(&st)[0] = Y[c][0];
                     reinterpret_cast<T*>(&st)[1] = Y[c][1];
-                    *reinterpret_cast<V2*>(SA + ia(ba, r, c, col)) = st;
+                    *reinterpret_cast<V2*>(SA + ia(b, r, c, col)) = st;
                     h2[c] = Y[c][hsel];
                     hp2a[c] = P2[c][hsel];
                 }
             }
-            fetch(z0 - 2 + it + depth);
+            fetch(z0 - 2 + it + depth, sA);
             if (it >= 2 && inB) {
                 T lap[2];
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    const T xm = SA[ia(bp, r, c, hin - 1)];
-                    const T xp = SA[ia(bp, r, c, hin + 1)];
-                    const T ys = SA[ia(bp, r - 1, c, hin)];
-                    const T yn = SA[ia(bp, r + 1, c, hin)];
+                    const T xm = SA[ia(b1, r, c, hin - 1)];
+                    const T xp = SA[ia(b1, r, c, hin + 1)];
+                    const T ys = SA[ia(b1, r - 1, c, hin)];
+                    const T yn = SA[ia(b1, r + 1, c, hin)];
                     const T yy = h1[c];
                     lap[c] = (xm - T(2) * yy + xp) * g.cx + (ys - T(2) * yy + yn) * g.cy + (h0[c] - T(2) * yy + h2[c]) * g.cz;
                 }
                 T f[2];
                 react(h1[0], h1[1], lap[0], lap[1], f[0], f[1]);
 #pragma unroll
-                for (int c = 0; c < 2; ++c) SB[ib(ba, r, c, hin)] = hp2b[c] + dta2 * f[c];
+                for (int c = 0; c < 2; ++c) SB[ib(b, r, c, hin)] = hp2b[c] + dta2 * f[c];
             }
 #pragma unroll
             for (int c = 0; c < 2; ++c) {
@@ -433,6 +448,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                 hp2b[c] = hp2a[c];
             }
             __syncthreads();
+            b = b == 2 ? 0 : b + 1;
+            sA = sA + 1 == depth ? 0 : sA + 1;
         }
     }
     cp_async_wait_pending(0);  // no copy may land in the ring after this segment
@@ -443,7 +460,7 @@ template <typename T, int NK, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
-    T* SB = SA + 2 * (size_t)(A.ty + 4) * 2 * pair_pitch<pair_vx<T>()>();
+    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<pair_vx<T>()>();
     unsigned char* SI = smem_raw + (pair_plane_bytes<T>(A.ty) + 15) / 16 * 16;
     unsigned char* R = SI + pair_isc_bytes<MODE>(A.ty);
     __shared__ T red[32];
