@@ -470,7 +470,7 @@ def main():
             "split" if split else "single")
     torch.cuda.nvtx.range_pop()
     stage_cfg = gs.gs_get_stage_configs(g.ctx)
-    pair_cfg = gs.gs_get_pair_configs(g.ctx)
+    pair_cfg = [(t, d) for (t, _), d in zip(gs.gs_get_pair_configs(g.ctx), gs.gs_get_pair_depths_in_use(g.ctx))]
     peak, peak_kind = _peaks()
     dom = max(range(1, len(stage_ms)), key=lambda i: stage_ms[i])
     attempt_fields = sum(fields[1:])  # field passes per attempt (k1 is reused): 18 pairs, 31 split, 33 single

@@ -228,6 +228,9 @@ int gs_get_dopri5_fusion(const gs_ctx* ctx);
  * gs_autotune overwrites it.  gs_get_pair_configs: host arrays of 3 ints. */
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth);
 gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth);
+/* The ring depth each pair kernel launches with: its configured depth cut
+ * back to what shared memory holds at its tile height (host array of 3). */
+gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth);
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);
 gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);
 

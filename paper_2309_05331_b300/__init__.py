@@ -72,6 +72,7 @@ _SIGNATURES = {
     "gs_set_pair_config": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
     "gs_get_pair_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
+    "gs_get_pair_depths_in_use": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
@@ -284,6 +285,13 @@ def gs_get_pair_configs(ctx):
     d = (C.c_int * 3)()
     _check(lib().gs_get_pair_configs(ctx, t, d), ctx)
     return [(t[i], d[i]) for i in range(3)]
+
+
+def gs_get_pair_depths_in_use(ctx):
+    """Ring depth each pair kernel launches with (configured depth cut to what shared memory holds)."""
+    d = (C.c_int * 3)()
+    _check(lib().gs_get_pair_depths_in_use(ctx, d), ctx)
+    return list(d)
 
 
 def gs_time_pairs(ctx, reps=5):

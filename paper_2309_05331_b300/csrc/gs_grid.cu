@@ -213,6 +213,16 @@ static cudaError_t launch_staged(gs_ctx* ctx, cudaStream_t s, StageArgs A, int d
     return cudaGetLastError();
 }
 
+// the ring depth a pair launch uses: the requested one, cut back to what
+// shared memory holds (leaving room for the kernel's static arrays)
+constexpr size_t kPairSmemCap = kMaxSmemPerCta - 1024;
+template <typename T, int NK, int MODE>
+static int pair_depth_fit(int ty, int depth) {
+    depth = std::max(1, std::min(depth, kMaxDepth));
+    while (depth > 1 && pair_smem_bytes<T, NK, MODE>(ty, depth) > kPairSmemCap) --depth;
+    return depth;
+}
+
 template <typename T, int NK, int MODE>
 static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
     const Geom<T> g = make_geom<T>(ctx->p);
@@ -221,12 +231,9 @@ static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int dep
     const int txw = 32 * pair_vx<T>();
     A.ntx = (ctx->p.nx + txw - 1) / txw;
     A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
-    depth = std::max(1, std::min(depth, kMaxDepth));
-    // dynamic shared memory, leaving room for the kernel's static arrays
-    const size_t cap = kMaxSmemPerCta - 1024;
-    size_t smem = pair_smem_bytes<T, NK, MODE>(A.ty, depth);
-    while (depth > 1 && smem > cap) smem = pair_smem_bytes<T, NK, MODE>(A.ty, --depth);
-    if (smem > cap) return cudaErrorInvalidConfiguration;
+    depth = pair_depth_fit<T, NK, MODE>(A.ty, depth);
+    const size_t smem = pair_smem_bytes<T, NK, MODE>(A.ty, depth);
+    if (smem > kPairSmemCap) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -1028,6 +1035,22 @@ gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth) {
     return GS_OK;
 }
 
+gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth) {
+    if (!ctx || !depth) return GS_ERR_INVALID;
+    const bool f64 = ctx->p.prec == GS_FP64;
+    for (int pi = 0; pi < 3; ++pi) {
+        const int ty = ctx->pc[pi].ty, d = ctx->pc[pi].depth;
+        if (pi == 0)
+            depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 1, MODE_PAIR_STAGE>(ty, d);
+        else if (pi == 1)
+            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 3, MODE_PAIR_STAGE>(ty, d);
+        else
+            depth[pi] = f64 ? pair_depth_fit<double, 5, MODE_PAIR_DOPRI67>(ty, d)
+                            : pair_depth_fit<float, 5, MODE_PAIR_DOPRI67>(ty, d);
+    }
+    return GS_OK;
+}
+
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth) {
     if (!ctx || depth < 1 || depth > kMaxDepth) return GS_ERR_INVALID;
     drop_graphs(ctx);
@@ -1176,6 +1199,9 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         for (int ty = 2; ty <= kPairMaxTY && st == GS_OK; ++ty)
             for (int depth = 1; depth <= kMaxDepth && st == GS_OK; ++depth) {
                 ctx->pc[pi] = KCfg{5, ty, 0, depth};
+                int used[3];
+                gs_get_pair_depths_in_use(ctx, used);
+                if (used[pi] < depth) break;  // shared memory holds no deeper ring
                 float ms = 0.f;
                 if ((st = time_pair_kernel(ctx, pi, 3, e0, e1, &ms)) != GS_OK) break;
                 if (ms < best) {

@@ -71,11 +71,11 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
     const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
     return (vec + halo + 15) / 16 * 16;
 }
-// Dormand-Prince pair: the inverse error scale of each thread's cells for
+// Dormand-Prince pair: the inverse error scale of the tile rows' cells for
 // the three planes between A and C (thread-private, 3 x 2 components)
 template <int MODE>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
-    return MODE == MODE_PAIR_DOPRI67 ? (size_t)3 * 2 * (ty + 4) * 32 * 16 : 0;
+    return MODE == MODE_PAIR_DOPRI67 ? (size_t)3 * 2 * ty * 32 * 16 : 0;
 }
 template <typename T, int NK, int MODE>
 __host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
@@ -162,9 +162,10 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     auto rvec = [&](int s, int a) -> VTy* {
         return reinterpret_cast<VTy*>(R + (size_t)s * slot_bytes) + ((size_t)w * NA + a) * 32 + lane;
     };
-    // this thread's inverse-scale vector of component c in plane buffer k (0..2)
+    // this thread's inverse-scale vector of component c in plane buffer k
+    // (0..2); tile rows only
     auto siv = [&](int k, int c) -> VTy* {
-        return reinterpret_cast<VTy*>(SI) + ((size_t)(k * 2 + c) * RA + w) * 32 + lane;
+        return reinterpret_cast<VTy*>(SI) + ((size_t)(k * 2 + c) * TY + r) * 32 + lane;
     };
     auto rhal = [&](int s, int a) -> V2* {
         return reinterpret_cast<V2*>(R + (size_t)s * slot_bytes + vec_bytes) + (size_t)a * 32 + lane;
@@ -266,29 +267,40 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                 yaX[c][v] = yaY[c][v] = ybX[c][v] = ybY[c][v] = T(0);
                 p2X[c][v] = p2Y[c][v] = qX[c][v] = qY[c][v] = epX[c][v] = epY[c][v] = isc[c][v] = T(0);
             }
-        const bool wide = DP && inC;  // rows whose error terms are needed
-        auto body = [&](int it, int b, int sA, T(&yaN)[2][VX], const T(&yaC)[2][VX], T(&ybN)[2][VX],
+        // tile-row warps (the longest path: A, B and C every iteration) run
+        // the steady state through a copy of the body without run-time phase
+        // tests (TILE), so each iteration is one block the compiler can
+        // schedule across phases; lanes past the row's end only skip memory
+        // accesses there
+        const bool act = lane < nl;
+        auto body = [&](const bool TILE, int it, int b, int sA, T(&yaN)[2][VX], const T(&yaC)[2][VX], T(&ybN)[2][VX],
                         const T(&ybC)[2][VX], T(&p2N)[2][VX], const T(&p2C)[2][VX], T(&qN)[2][VX],
                         const T(&qC)[2][VX], T(&epN)[2][VX], const T(&epC)[2][VX]) {
+            const bool doA = TILE || inA, doB = TILE ? act : (it >= 2 && inB), doC = TILE ? act : (it >= 4 && inC);
+            const bool wide = DP && (TILE || inC);  // rows whose error terms are needed
             const int q = z0 - 2 + it;
             const int b1 = b == 0 ? 2 : b - 1, b2 = b == 2 ? 0 : b + 1;  // planes q - 1 and q - 2
             // ---- A(q)
             cp_async_wait_pending(depth - 1);
-            if (inA) {
+            if (doA) {
                 auto ld = [&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(sA, a)), out); };
-                if (wide)
+                if (TILE)
+                    formA(ld, yaN, p2N, qN, isc, std::true_type{});
+                else if (wide)
                     formA(ld, yaN, p2N, qN, isc, std::true_type{});
                 else
                     formA(ld, yaN, p2N, qN, isc, std::false_type{});
+                if (TILE ? act : true) {
 #pragma unroll
-                for (int c = 0; c < 2; ++c) {
-                    stv<T, VX>(SA + ia(b, r, c, col), yaN[c]);
-                    if (wide) stv<T, VX>(reinterpret_cast<T*>(siv(b, c)), isc[c]);
+                    for (int c = 0; c < 2; ++c) {
+                        stv<T, VX>(SA + ia(b, r, c, col), yaN[c]);
+                        if (wide) stv<T, VX>(reinterpret_cast<T*>(siv(b, c)), isc[c]);
+                    }
                 }
             }
             fetch(q + depth, sA);  // the slot's values are in registers: reuse it
             // ---- B(p), p = q - 1: centre yaC, upper z neighbour yaN
-            if (it >= 2) {
+            if (TILE || it >= 2) {
                 const int p = q - 1;
                 T xl[2], xr[2];
 #pragma unroll
@@ -296,7 +308,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     xl[c] = __shfl_up_sync(0xffffffffu, yaC[c][VX - 1], 1);
                     xr[c] = __shfl_down_sync(0xffffffffu, yaC[c][0], 1);
                 }
-                if (inB) {
+                if (doB) {
                     T lap[2][VX];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
@@ -318,7 +330,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     T f[2][VX];
 #pragma unroll
                     for (int v = 0; v < VX; ++v) react(yaC[0][v], yaC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
-                    const bool own = r >= 0 && r < ah && p >= z0 && p < z1;
+                    const bool own = TILE ? p < z1 : (r >= 0 && r < ah && p >= z0 && p < z1);
                     const long long gi = cbase + plane * p;
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
@@ -336,7 +348,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                 }
             }
             // ---- C(o), o = q - 2: centre ybC, upper z neighbour ybN
-            if (it >= 4) {
+            if (TILE || it >= 4) {
                 const int o = q - 2;
                 T xl[2], xr[2];
 #pragma unroll
@@ -344,7 +356,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     xl[c] = __shfl_up_sync(0xffffffffu, ybC[c][VX - 1], 1);
                     xr[c] = __shfl_down_sync(0xffffffffu, ybC[c][0], 1);
                 }
-                if (inC) {
+                if (doC) {
                     T lap[2][VX];
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
@@ -389,13 +401,27 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             b = b == 2 ? 0 : b + 1;
             sA = sA + 1 == depth ? 0 : sA + 1;
         };
-        for (int it = 0; it < nit; it += 2) {
-            body(it, b, sA, yaX, yaY, ybX, ybY, p2X, p2Y, qX, qY, epX, epY);
+        // tile rows: the general body for the first four iterations (phases
+        // B and C start at iterations 2 and 4), then the tile body
+        const bool tilew = r >= 0 && r < ah;
+        const int nit0 = tilew ? 4 : nit;
+        int it = 0;
+        for (; it < nit0; it += 2) {
+            body(false, it, b, sA, yaX, yaY, ybX, ybY, p2X, p2Y, qX, qY, epX, epY);
             advance();
-            if (it + 1 < nit) {
-                body(it + 1, b, sA, yaY, yaX, ybY, ybX, p2Y, p2X, qY, qX, epY, epX);
+            if (it + 1 < nit0) {
+                body(false, it + 1, b, sA, yaY, yaX, ybY, ybX, p2Y, p2X, qY, qX, epY, epX);
                 advance();
             }
+        }
+        if (tilew) {
+            for (; it + 1 < nit; it += 2) {
+                body(true, it, b, sA, yaX, yaY, ybX, ybY, p2X, p2Y, qX, qY, epX, epY);
+                advance();
+                body(true, it + 1, b, sA, yaY, yaX, ybY, ybX, p2Y, p2X, qY, qX, epY, epX);
+                advance();
+            }
+            if (it < nit) body(true, it, b, sA, yaX, yaY, ybX, ybY, p2X, p2Y, qX, qY, epX, epY);
         }
     } else {
         // ---------------- halo warp: the inner halo column of its row and side ----------------

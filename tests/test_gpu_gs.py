@@ -279,6 +279,8 @@ def test_pairs_per_pair_configs_and_timing():
         for pi, (ty, d) in enumerate(cfgs):
             gs.gs_set_pair_config(g.ctx, pi, ty, d)
         assert gs.gs_get_pair_configs(g.ctx) == cfgs
+        used = gs.gs_get_pair_depths_in_use(g.ctx)
+        assert all(1 <= u <= d for u, (_, d) in zip(used, cfgs))
         ms = gs.gs_time_pairs(g.ctx, reps=2)
         assert len(ms) == 4 and all(m > 0 for m in ms)
         assert np.array_equal(to_np(g.u), u0) and np.array_equal(to_np(g.v), v0)
