@@ -59,11 +59,12 @@ PAIR_FIELDS = [2, 4, 6, 8]
 BYTES_PER_FIELD_CELL = 8
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
-# split stage-6 launch at 256^3 (profiles/gs_stage6_split_fp32_256cubed_full.md:
-# 827.2 MB read + 371.8 MB written), per cell so that other grids scale by
-# cells; valid only for that kernel form while the stage-kernel sources are
-# unchanged.
-NCU_TRAFFIC = {"kernel": "stage6", "path": "split", "source_sha": "c1d3aaddb0749d51", "bytes_per_cell": (827151104 + 371779072) / 256 ** 3}
+# stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
+# 842.0 MB read + 247.8 MB written), per cell so that other grids scale by
+# cells; valid only for that kernel on that path while the stage-kernel
+# sources are unchanged.
+NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "2fad902d24afa6d2",
+               "bytes_per_cell": (841986304 + 247811328) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
