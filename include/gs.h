@@ -222,14 +222,23 @@ int gs_get_dopri5_split(const gs_ctx* ctx);
  * gs_get_dopri5_fusion: 1 if the pairs are in use. */
 gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode);
 int gs_get_dopri5_fusion(const gs_ctx* ctx);
-/* Launch shape of pair kernel `pair` (0: stages 2+3, 1: 4+5, 2: 6+7; -1: all
- * three): tile height ty (1..7 rows; the CTA has ty + 5 warps) and input
- * ring depth (1..3 planes; cut back at launch to what shared memory holds).
- * gs_autotune overwrites it.  gs_get_pair_configs: host arrays of 3 ints. */
+/* The same switch runs fixed-step RK4 (gs_step, GS_RK4, on grids that do
+ * not take the small-grid path) as two pair launches: k1 = F(u) and k2 =
+ * F(u + dt/2 k1); then k3, k4 and the update u' = u + dt (k1/6 + k2/3 + k3/3
+ * + k4/6) without storing k3 or k4: 7 field passes per step instead of 13.
+ * Its automatic verdict is separate (gs_autotune times one RK4 step both
+ * ways).  The update is summed as ((u + dt (k1/6 + k2/3)) + dt k3/3) + dt
+ * k4/6.  gs_get_rk4_fusion: 1 if RK4 steps use the pairs. */
+int gs_get_rk4_fusion(const gs_ctx* ctx);
+/* Launch shape of pair kernel `pair` (0: Dormand-Prince stages 2+3, 1: 4+5,
+ * 2: 6+7; 3: RK4 stages 1+2, 4: RK4 stages 3+4 with the update; -1: all
+ * five): tile height ty (1..7 rows; the CTA has ty + 5 warps) and input ring
+ * depth (1..3 planes; cut back at launch to what shared memory holds).
+ * gs_autotune overwrites it.  gs_get_pair_configs: host arrays of 5 ints. */
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth);
 gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth);
 /* The ring depth each pair kernel launches with: its configured depth cut
- * back to what shared memory holds at its tile height (host array of 3). */
+ * back to what shared memory holds at its tile height (host array of 5). */
 gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth);
 gs_status gs_set_stage_depth(gs_ctx* ctx, int depth);
 gs_status gs_get_stage_depths(const gs_ctx* ctx, int* depth);

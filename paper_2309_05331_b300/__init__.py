@@ -69,6 +69,7 @@ _SIGNATURES = {
     "gs_get_dopri5_split": ([_vp], C.c_int),
     "gs_set_dopri5_fusion": ([_vp, C.c_int], C.c_int),
     "gs_get_dopri5_fusion": ([_vp], C.c_int),
+    "gs_get_rk4_fusion": ([_vp], C.c_int),
     "gs_set_pair_config": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
     "gs_get_pair_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
@@ -279,17 +280,22 @@ def gs_set_pair_config(ctx, pair, ty, depth):
     _check(lib().gs_set_pair_config(ctx, pair, ty, depth), ctx)
 
 
+def gs_get_rk4_fusion(ctx):
+    return lib().gs_get_rk4_fusion(ctx)
+
+
 def gs_get_pair_configs(ctx):
-    """(tile height, ring depth) of the pair kernels (stages 2+3, 4+5, 6+7)."""
-    t = (C.c_int * 3)()
-    d = (C.c_int * 3)()
+    """(tile height, ring depth) of the pair kernels: Dormand-Prince stages
+    2+3, 4+5, 6+7, RK4 stages 1+2, 3+4."""
+    t = (C.c_int * 5)()
+    d = (C.c_int * 5)()
     _check(lib().gs_get_pair_configs(ctx, t, d), ctx)
-    return [(t[i], d[i]) for i in range(3)]
+    return [(t[i], d[i]) for i in range(5)]
 
 
 def gs_get_pair_depths_in_use(ctx):
     """Ring depth each pair kernel launches with (configured depth cut to what shared memory holds)."""
-    d = (C.c_int * 3)()
+    d = (C.c_int * 5)()
     _check(lib().gs_get_pair_depths_in_use(ctx, d), ctx)
     return list(d)
 

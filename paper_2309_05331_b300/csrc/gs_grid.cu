@@ -72,7 +72,10 @@ struct gs_ctx {
     int split67 = -1;       // Dormand-Prince stages 6/7 split (MODE_DOPRI_S6/S7): -1 automatic, 0 off, 1 on
     int fuse = -1;          // Dormand-Prince stage pairs (2,3) (4,5) (6,7) in one launch each: -1 automatic, 0 off, 1 on
     bool fuse_auto = true;  // the automatic choice (the autotuner's verdict once tuned)
-    KCfg pc[3] = {{5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}};  // pair kernels: tile height, ring depth
+    bool rk4_fuse_auto = true;  // the automatic choice for RK4 (the autotuner's verdict once tuned)
+    // pair kernels (tile height, ring depth): Dormand-Prince stages 2+3, 4+5,
+    // 6+7; RK4 stages 1+2, 3+4
+    KCfg pc[5] = {{5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}};
     int small_mode = -1;    // fixed-step RK4 in one cooperative launch: -1 automatic (small grids), 0 off, 1 on
     int small_ctas = 0;     // its CTA count (0: automatic)
     unsigned* pbar = nullptr;  // its grid barrier: u64 count, generation, error
@@ -137,6 +140,12 @@ static bool pairs_on(const gs_ctx* ctx) {
     if (!form_ok(ctx, 4)) return false;
     if (ctx->fuse >= 0) return ctx->fuse == 1;
     return (ctx->variant == 0 || ctx->variant == 4) && ctx->fuse_auto;
+}
+// RK4 steps as two pair launches (same switch, its own automatic verdict)
+static bool rk4_pairs_on(const gs_ctx* ctx) {
+    if (!form_ok(ctx, 4)) return false;
+    if (ctx->fuse >= 0) return ctx->fuse == 1;
+    return (ctx->variant == 0 || ctx->variant == 4) && ctx->rk4_fuse_auto;
 }
 // the form a launch with configured form `form` actually uses
 static int pick_form(const gs_ctx* ctx, int form) {
@@ -369,8 +378,44 @@ static Slot ring(gs_ctx* c, int off) {
 // RK4 with k-storage: k1 = F(u); k2 = F(u + dt/2 k1); k3 = F(u + dt/2 k2);
 // u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) with k4 = F(u + dt k3).
 // k1 goes to field 1 (or to the history ring when starting Adams-Bashforth).
+// RK4 stage pair pi (3: k1 = F(u), k2 = F(u + dt/2 k1); 4: k3, k4 and the
+// update u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) -> next state, controller)
+static cudaError_t launch_rk4_pair(gs_ctx* ctx, cudaStream_t s, int pi, unsigned long long h, int use_cond) {
+    const KCfg& cfg = ctx->pc[pi];
+    StageArgs A = base_args(ctx, cfg);
+    A.u = state_sel(ctx, SEL_CUR);
+    A.has_out1 = 1;
+    if (pi == 3) {
+        A.bk[0] = 0.5;
+        A.out0 = fld(ctx, 1);
+        A.out1 = fld(ctx, 5);
+        return launch_pair_nk<0, MODE_PAIR_STAGE>(ctx, s, A, cfg);
+    }
+    A.kin[0] = fld(ctx, 1);
+    A.kin[1] = fld(ctx, 5);
+    A.a[0] = 0.0;
+    A.a[1] = 0.5;  // Y3 = u + dt/2 k2
+    A.bk[0] = 0.0;
+    A.bk[1] = 0.0;
+    A.bk[2] = 1.0;  // Y4 = u + dt k3
+    A.be[0] = 1.0 / 6.0;
+    A.be[1] = 1.0 / 3.0;
+    A.be[2] = 1.0 / 3.0;
+    A.bf = 1.0 / 6.0;
+    A.out0 = state_sel(ctx, SEL_NEXT);
+    A.run_ctrl = 1;
+    A.cond = h;
+    A.use_cond = use_cond;
+    return launch_pair_nk<2, MODE_PAIR_RK4>(ctx, s, A, cfg);
+}
+
 static cudaError_t body_rk4(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond,
                             bool k1_in_ring) {
+    if (!k1_in_ring && rk4_pairs_on(ctx)) {
+        cudaError_t e = launch_rk4_pair(ctx, s, 3, h, use_cond);
+        if (e != cudaSuccess) return e;
+        return launch_rk4_pair(ctx, s, 4, h, use_cond);
+    }
     const Slot k1 = k1_in_ring ? ring(ctx, 0) : fld(ctx, 1);
     StageArgs A = base_args(ctx, ctx->def);
     A.u = state_sel(ctx, SEL_CUR);
@@ -1018,17 +1063,19 @@ gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode) {
 int gs_get_dopri5_fusion(const gs_ctx* ctx) { return ctx && pairs_on(ctx) ? 1 : 0; }
 
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth) {
-    if (!ctx || pair < -1 || pair > 2 || ty < 1 || ty > kPairMaxTY || depth < 1 || depth > kMaxDepth)
+    if (!ctx || pair < -1 || pair > 4 || ty < 1 || ty > kPairMaxTY || depth < 1 || depth > kMaxDepth)
         return GS_ERR_INVALID;
     drop_graphs(ctx);
-    for (int pi = 0; pi < 3; ++pi)
+    for (int pi = 0; pi < 5; ++pi)
         if (pair < 0 || pair == pi) ctx->pc[pi] = KCfg{5, ty, 0, depth};
     return GS_OK;
 }
 
+int gs_get_rk4_fusion(const gs_ctx* ctx) { return ctx && rk4_pairs_on(ctx) ? 1 : 0; }
+
 gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth) {
     if (!ctx || !ty || !depth) return GS_ERR_INVALID;
-    for (int pi = 0; pi < 3; ++pi) {
+    for (int pi = 0; pi < 5; ++pi) {
         ty[pi] = ctx->pc[pi].ty;
         depth[pi] = ctx->pc[pi].depth;
     }
@@ -1038,9 +1085,13 @@ gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth) {
 gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth) {
     if (!ctx || !depth) return GS_ERR_INVALID;
     const bool f64 = ctx->p.prec == GS_FP64;
-    for (int pi = 0; pi < 3; ++pi) {
+    for (int pi = 0; pi < 5; ++pi) {
         const int ty = ctx->pc[pi].ty, d = ctx->pc[pi].depth;
-        if (pi == 0)
+        if (pi == 3)
+            depth[pi] = f64 ? pair_depth_fit<double, 0, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 0, MODE_PAIR_STAGE>(ty, d);
+        else if (pi == 4)
+            depth[pi] = f64 ? pair_depth_fit<double, 2, MODE_PAIR_RK4>(ty, d) : pair_depth_fit<float, 2, MODE_PAIR_RK4>(ty, d);
+        else if (pi == 0)
             depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 1, MODE_PAIR_STAGE>(ty, d);
         else if (pi == 1)
             depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 3, MODE_PAIR_STAGE>(ty, d);
@@ -1109,7 +1160,7 @@ static gs_status time_pair_kernel(gs_ctx* ctx, int pi, int reps, cudaEvent_t e0,
         gs_status st = upload_ctrl(ctx);
         if (st != GS_OK) return st;
         CK(cudaEventRecord(e0, ctx->stream));
-        cudaError_t e = launch_dopri5_pair(ctx, ctx->stream, pi, 0, 0);
+        cudaError_t e = pi < 3 ? launch_dopri5_pair(ctx, ctx->stream, pi, 0, 0) : launch_rk4_pair(ctx, ctx->stream, pi, 0, 0);
         if (e != cudaSuccess) {
             set_err(ctx, e, "autotune launch");
             return GS_ERR_CUDA;
@@ -1190,10 +1241,10 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     // stage pairs: every tile height x ring depth 1..3, then the automatic
     // choice between pairs and single stages by the summed kernel times of an
     // attempt
-    KCfg best_pc[3] = {ctx->pc[0], ctx->pc[1], ctx->pc[2]};
-    float pair_total = 0.f;
+    KCfg best_pc[5] = {ctx->pc[0], ctx->pc[1], ctx->pc[2], ctx->pc[3], ctx->pc[4]};
+    float pair_total = 0.f, rk4_pair_total = 0.f, rk4_single = 0.f;
     const bool tune_pairs = form_ok(ctx, 4) && (ctx->variant == 0 || ctx->variant == 4) && ctx->fuse != 0;
-    for (int pi = 0; pi < 3 && tune_pairs && st == GS_OK; ++pi) {
+    for (int pi = 0; pi < 5 && tune_pairs && st == GS_OK; ++pi) {
         float best = 1e30f;
         const KCfg saved = ctx->pc[pi];
         for (int ty = 2; ty <= kPairMaxTY && st == GS_OK; ++ty)
@@ -1210,7 +1261,33 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
                 }
             }
         ctx->pc[pi] = saved;
-        pair_total += best;
+        (pi < 3 ? pair_total : rk4_pair_total) += best;
+    }
+    // the single-stage RK4 step with the configuration the other integrators use
+    if (tune_pairs && st == GS_OK) {
+        const KCfg saved_def = ctx->def;
+        ctx->def = best_cfg[1];
+        const int saved_fuse = ctx->fuse;
+        ctx->fuse = 0;
+        float acc = 0.f;
+        for (int r = 0; r < 4 && st == GS_OK; ++r) {
+            init_fixed_ctrl(ctx, 0.0, 1e-3, 1 << 30);
+            if ((st = upload_ctrl(ctx)) != GS_OK) break;
+            cudaError_t e = cudaEventRecord(e0, ctx->stream);
+            if (e == cudaSuccess) e = body_rk4(ctx, ctx->stream, 0, 0, false);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ctx->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                set_err(ctx, e, "autotune RK4 step");
+                st = GS_ERR_CUDA;
+            }
+            if (r > 0) acc += ms;
+        }
+        rk4_single = acc / 3;
+        ctx->fuse = saved_fuse;
+        ctx->def = saved_def;
     }
     cudaStreamSynchronize(ctx->stream);
     cudaEventDestroy(e0);
@@ -1219,8 +1296,9 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     for (int k = 0; k < 7; ++k) ctx->dp[k] = best_cfg[k];
     ctx->dp_tuned = true;
     if (tune_pairs) {
-        for (int pi = 0; pi < 3; ++pi) ctx->pc[pi] = best_pc[pi];
+        for (int pi = 0; pi < 5; ++pi) ctx->pc[pi] = best_pc[pi];
         ctx->fuse_auto = pair_total < total - stage_best[0];
+        ctx->rk4_fuse_auto = rk4_pair_total < rk4_single;
     }
     // the other integrators use the configuration of the one-input stage
     ctx->def = best_cfg[1];

@@ -13,7 +13,9 @@
 // input is y5 = u + dt sum_j b_j k_j (b7 = 0), so that pair reads u, k1..k5,
 // writes y5 and k7 (the next k1) and reduces the scaled error norm, with
 // the arithmetic of the split stages 6/7 (gs_staged.cuh): 8 field passes
-// instead of 13.
+// instead of 13.  RK4 runs as two pairs: k1, k2 from u (stage 1 is F(u)),
+// then k3, k4 and the update u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) from u,
+// k1, k2 without storing k3 or k4: 7 field passes per step instead of 13.
 //
 // Mapping (the staged form's, widened): a warp owns a row of 32*VX cells
 // (one 16-byte vector per lane).  The CTA has ty + 4 row warps for rows
@@ -73,9 +75,10 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
 }
 // Dormand-Prince pair: the inverse error scale of the tile rows' cells for
 // the three planes between A and C (thread-private, 3 x 2 components)
+// (RK4 stages 3+4: the partial update u + dt (k1/6 + k2/3) between A and B)
 template <int MODE>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
-    return MODE == MODE_PAIR_DOPRI67 ? (size_t)3 * 2 * ty * 32 * 16 : 0;
+    return (MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? (size_t)3 * 2 * ty * 32 * 16 : 0;
 }
 template <typename T, int NK, int MODE>
 __host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
@@ -88,6 +91,7 @@ template <typename T, int NK>
 struct PairCoef {
     T a1[NK > 0 ? NK : 1];  // stage i: Y_i = u + dt sum_j a1_j k_j
     T a2[NK + 1];           // stage i+1: Y_{i+1} = u + dt sum_j a2_j k_j (j <= i)
+    T rb[4];                // RK4 update weights of k1..k4
     T dt, ta, tr;
 };
 
@@ -98,6 +102,10 @@ __device__ __forceinline__ PairCoef<T, NK> pair_coef(const StageArgs& A, double 
     for (int j = 0; j < NK; ++j) C.a1[j] = (T)A.a[j];
 #pragma unroll
     for (int j = 0; j <= NK; ++j) C.a2[j] = (T)A.bk[j];
+    C.rb[0] = (T)A.be[0];
+    C.rb[1] = (T)A.be[1];
+    C.rb[2] = (T)A.be[2];
+    C.rb[3] = (T)A.bf;
     C.dt = (T)dt;
     C.ta = (T)atol;
     C.tr = (T)rtol;
@@ -122,7 +130,9 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     constexpr int OFF = VX;
     constexpr int NA = 2 * (1 + NK);
     constexpr bool DP = MODE == MODE_PAIR_DOPRI67;
+    constexpr bool RK = MODE == MODE_PAIR_RK4;
     static_assert(!DP || NK == 5, "Dormand-Prince stages 6/7 take k1..k5");
+    static_assert(!RK || NK == 2, "RK4 stages 3/4 take k1, k2");
     using VTy = typename VecT<T, VX>::type;
     using V2 = typename VecT<T, 2>::type;
     const int lane = threadIdx.x;
@@ -194,10 +204,12 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     // the second-stage partial P2 = u + dt sum_{j<i} a2_j k_j (Dormand-Prince:
     // u + dt sum_{j=1,3,4,5} b_j k_j); with E (Dormand-Prince tile rows) also
     // the error terms Q = dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1) and
-    // the inverse error scale I = 1 / (atol + rtol (|u| + dt |k1|)).
+    // the inverse error scale I = 1 / (atol + rtol (|u| + dt |k1|)).  RK4
+    // stages 3+4 with E: I = u + dt (k1/6 + k2/3), the update so far.
     auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I, auto E) {
         constexpr int NV = sizeof(Y[0]) / sizeof(T);
         constexpr bool WE = DP && decltype(E)::value;
+        constexpr bool WR = RK && decltype(E)::value;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
             T uu[NV], s1[NV], s2[NV], k1v[NV], q[NV];
@@ -216,6 +228,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     s1[v] = (j == 0) ? C.a1[0] * kk[v] : s1[v] + C.a1[j] * kk[v];
+                    if (WR) q[v] = (j == 0) ? C.rb[0] * kk[v] : q[v] + C.rb[j] * kk[v];
                     if (!DP) {
                         s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
                     } else if (j == 0) {
@@ -235,6 +248,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     Q[c][v] = dt * (q[v] - e67 * k1v[v]);
                     I[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
                 }
+                if (WR) I[c][v] = uu[v] + dt * q[v];
             }
         }
     };
@@ -277,7 +291,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         const T(&ybC)[2][VX], T(&p2N)[2][VX], const T(&p2C)[2][VX], T(&qN)[2][VX],
                         const T(&qC)[2][VX], T(&epN)[2][VX], const T(&epC)[2][VX]) {
             const bool doA = TILE || inA, doB = TILE ? act : (it >= 2 && inB), doC = TILE ? act : (it >= 4 && inC);
-            const bool wide = DP && (TILE || inC);  // rows whose error terms are needed
+            // rows whose error terms (RK4: partial update) are needed
+            const bool wide = (DP || RK) && (TILE || inC);
             const int q = z0 - 2 + it;
             const int b1 = b == 0 ? 2 : b - 1, b2 = b == 2 ? 0 : b + 1;  // planes q - 1 and q - 2
             // ---- A(q)
@@ -332,14 +347,20 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     for (int v = 0; v < VX; ++v) react(yaC[0][v], yaC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
                     const bool own = TILE ? p < z1 : (r >= 0 && r < ah && p >= z0 && p < z1);
                     const long long gi = cbase + plane * p;
+                    T tu[2][VX] = {};  // RK4: the partial update of plane p (tile rows)
+                    if (RK && (TILE || (r >= 0 && r < ah))) {
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) lds_v<T, VX>(reinterpret_cast<const T*>(siv(b1, c)), tu[c]);
+                    }
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
 #pragma unroll
                         for (int v = 0; v < VX; ++v) {
                             ybN[c][v] = p2C[c][v] + dta2 * f[c][v];
                             if (DP) epN[c][v] = qC[c][v] + dte6 * f[c][v];
+                            if (RK) epN[c][v] = tu[c][v] + dt * C.rb[2] * f[c][v];
                         }
-                    if (own) {
+                    if (own && !RK) {
 #pragma unroll
                         for (int c = 0; c < 2; ++c) stv<T, VX>(P.o0[c] + gi, DP ? ybN[c] : f[c]);
                     }
@@ -381,7 +402,14 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     const long long gi = cbase + plane * o;
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
-                        stv<T, VX>(P.o1[c] + gi, f[c]);
+                        if (RK) {
+                            T un[VX];
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) un[v] = epC[c][v] + dt * C.rb[3] * f[c][v];
+                            stv<T, VX>(P.o0[c] + gi, un);
+                        } else {
+                            stv<T, VX>(P.o1[c] + gi, f[c]);
+                        }
                         if (DP) {
                             T sc[VX];
                             lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, c)), sc);  // plane q - 2
@@ -513,7 +541,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> 
         });
     }
     const T emax = ErrBits<T>::value(ebits);
-    if (MODE == MODE_PAIR_DOPRI67 && A.run_ctrl && A.ctrl) final_kernel_epilogue<T, MODE>(A, emax, red, &s_last);
+    if ((MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) && A.run_ctrl && A.ctrl)
+        final_kernel_epilogue<T, MODE>(A, emax, red, &s_last);
 }
 
 }  // namespace gsk

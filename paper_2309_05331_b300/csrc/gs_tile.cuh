@@ -35,9 +35,9 @@ namespace gsk {
 // differently (staged form only): stage 6 also forms y5 (b7 = 0, so y5 needs
 // k1..k6 only), the error terms of k1..k6 and the inverse error scale, and
 // never stores k6; stage 7 evaluates k7 = F(y5) and adds its error term.
-// MODE_PAIR_STAGE / MODE_PAIR_DOPRI67: two consecutive stages in one launch
-// (gs_pair.cuh): stages i and i+1, or Dormand-Prince stages 6 and 7 with y5,
-// k7 and the error norm.
+// MODE_PAIR_STAGE / MODE_PAIR_DOPRI67 / MODE_PAIR_RK4: two consecutive
+// stages in one launch (gs_pair.cuh): stages i and i+1; Dormand-Prince stages
+// 6 and 7 with y5, k7 and the error norm; RK4 stages 3 and 4 with the update.
 enum StageMode : int {
     MODE_STAGE = 0,
     MODE_FINAL = 1,
@@ -45,7 +45,8 @@ enum StageMode : int {
     MODE_DOPRI_S6 = 3,
     MODE_DOPRI_S7 = 4,
     MODE_PAIR_STAGE = 5,
-    MODE_PAIR_DOPRI67 = 6
+    MODE_PAIR_DOPRI67 = 6,
+    MODE_PAIR_RK4 = 7
 };
 
 template <typename T>

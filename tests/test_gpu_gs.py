@@ -255,9 +255,42 @@ def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth):
         gs.gs_set_dopri5_fusion(g.ctx, fusion)
         gs.gs_set_pair_config(g.ctx, -1, ty, depth)
         assert gs.gs_get_dopri5_fusion(g.ctx) == fusion
-        assert gs.gs_get_pair_configs(g.ctx) == [(ty, depth)] * 3
+        assert gs.gs_get_pair_configs(g.ctx) == [(ty, depth)] * 5
         t = g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
         assert abs(t - 0.75) < 1e-15
+        res.append((to_np(g.u), to_np(g.v)))
+        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, fusion
+        g.close()
+    if prec == 0:
+        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (8, 1, 1), (136, 13, 5)])
+@pytest.mark.parametrize("ty,depth,nsteps", [(7, 2, 3), (1, 1, 2), (3, 3, 5)])
+def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps):
+    """Fixed-step RK4 as two pair launches (k1 and k2 from u; k3, k4 and the
+    update without storing k3, k4) against the oracle and the four
+    single-stage kernels; odd and even step counts (the state ends in either
+    buffer), ragged tiles, single-plane z, every ring depth.  FP64: pairs and
+    single stages agree to 1e-13 (the update is summed in another order)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    phys = dict(Du=3e-3, Dv=1.5e-3, L=max(2.5, dims[0] * 2.5 / 45))
+    u0, v0 = si.gs_initial_state(*dims, seed=53)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    ou, ov = oracle.gs_integrate_const(oracle.GSParams(*dims, **phys), u0, v0, oracle.RK4, 0.2, nsteps)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    res = []
+    for fusion in (1, 0):
+        g = _gs(torch, dims, prec, u0, v0, **phys)
+        gs.gs_set_small_grid_path(g.ctx, 0)
+        gs.gs_set_dopri5_fusion(g.ctx, fusion)
+        gs.gs_set_pair_config(g.ctx, -1, ty, depth)
+        assert gs.gs_get_rk4_fusion(g.ctx) == fusion
+        t = g.step(gs.GS_RK4, 0.0, 0.2, nsteps)
+        assert abs(t - 0.2 * nsteps) < 1e-12
         res.append((to_np(g.u), to_np(g.v)))
         assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, fusion
         g.close()
@@ -273,7 +306,7 @@ def test_pairs_per_pair_configs_and_timing():
     dims = (68, 23, 11)
     u0, v0 = si.gs_initial_state(*dims, seed=5)
     res = []
-    for cfgs in ([(7, 1), (2, 3), (4, 2)], [(3, 2), (6, 1), (1, 3)]):
+    for cfgs in ([(7, 1), (2, 3), (4, 2), (5, 1), (2, 2)], [(3, 2), (6, 1), (1, 3), (7, 3), (4, 1)]):
         g = _gs(torch, dims, gs.GS_FP64, u0, v0, Du=2e-3, Dv=1e-3)
         gs.gs_set_dopri5_fusion(g.ctx, 1)
         for pi, (ty, d) in enumerate(cfgs):
@@ -301,7 +334,7 @@ def test_pairs_rejected_without_staged_form():
         gs.gs_time_pairs(g.ctx)
     g.close()
     g = _gs(torch, (8, 4, 4), gs.GS_FP32, *si.gs_initial_state(8, 4, 4))
-    for bad in [(0, 0, 1), (0, 8, 1), (0, 3, 0), (0, 3, 4), (3, 3, 1), (-2, 3, 1)]:
+    for bad in [(0, 0, 1), (0, 8, 1), (0, 3, 0), (0, 3, 4), (5, 3, 1), (-2, 3, 1)]:
         with pytest.raises(RuntimeError):
             gs.gs_set_pair_config(g.ctx, *bad)
     with pytest.raises(RuntimeError):
