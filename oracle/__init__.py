@@ -21,6 +21,14 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
                                scaling.  The controller formula itself is this
                                build's reading (paper silent)
   integrate_ab4                pinned: cubic exactness, observed order 4
+  CK54 / RKF78 tableaux        pinned: Butcher order conditions (orders 5/4,
+                               8/7) and observed orders
+  integrate_adaptive (any      pinned: closed-form error within C*tol per
+  pair), per element           element; elements with different dynamics take
+                               different step counts
+  ab_coefficients / AB 1..8    pinned: exactness on polynomials of degree
+                               s - 1, the AB2/AB4 coefficients, observed
+                               orders 1..8
   axpy                         pinned: exact small-integer sums
   conv3d fwd/dgrad/wgrad       pinned: FP64 central differences of a scalar
                                loss, 1x1x1-equivalent reduction to a matmul
@@ -34,7 +42,7 @@ import numpy as np
 
 from . import build as _build
 
-EULER, RK4, DOPRI5 = 0, 1, 2
+EULER, RK4, DOPRI5, CK54, RKF78 = 0, 1, 2, 3, 4
 PW_EXP_DECAY, PW_LOGISTIC, PW_PAPER_EXP, PW_PAPER_SIGMOID = 0, 1, 2, 3
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_STEP_UNDERFLOW, ERR_MAX_STEPS, ERR_NONFINITE = 0, 1, 3, 4, 5, 6
@@ -81,6 +89,17 @@ def lib():
         L.orc_pw_dopri5_attempt.argtypes = [C.c_int, _dp, C.c_long, C.c_double, C.c_double, _dp, _dp, _dp,
                                             C.c_double, C.c_double]
         L.orc_pw_dopri5_attempt.restype = C.c_double
+        L.orc_pw_integrate_ab.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, C.c_double, C.c_double,
+                                          C.c_long]
+        L.orc_pw_integrate_adaptive_m.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, _dp, C.c_double, _dp,
+                                                  C.c_double, C.c_double, C.c_long, C.c_long,
+                                                  C.POINTER(C.c_long), C.POINTER(C.c_long), _dp, C.c_long]
+        _lp = C.POINTER(C.c_long)
+        L.orc_pw_integrate_adaptive_each.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, C.c_double,
+                                                     C.c_double, C.c_double, C.c_double, C.c_double, C.c_long,
+                                                     C.c_long, _dp, _dp, _lp, _lp, C.POINTER(C.c_int)]
+        L.orc_ab_coefficients.argtypes = [C.c_int, _dp]
+        L.orc_pair_orders.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_axpy.argtypes = [C.c_long, C.c_int, _dp, C.POINTER(_dp), _dp]
         L.orc_conv3d_fwd.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp, _dp]
         L.orc_conv3d_dgrad.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp]
@@ -238,16 +257,17 @@ def pw_integrate_replay(kind, x, method, dts, t0=0.0, coef=None):
 
 
 def pw_integrate_adaptive(kind, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500, coef=None,
-                          log_cap=0):
+                          log_cap=0, method=DOPRI5):
+    """One state vector, one step size (global L-infinity norm)."""
     x = _f64(x).copy()
     c = _f64(coef) if coef is not None else None
     t = C.c_double(t0)
     dt = C.c_double(dt0)
     na, nr = C.c_long(0), C.c_long(0)
     log = np.zeros(max(log_cap, 1))
-    st = lib().orc_pw_integrate_adaptive(kind, _p(c), x.size, _p(x), C.byref(t), t_end, C.byref(dt), atol,
-                                         rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
-                                         _p(log) if log_cap else None, log_cap)
+    st = lib().orc_pw_integrate_adaptive_m(method, kind, _p(c), x.size, _p(x), C.byref(t), t_end, C.byref(dt),
+                                           atol, rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
+                                           _p(log) if log_cap else None, log_cap)
     return {"x": x, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
             "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
 
@@ -257,6 +277,48 @@ def pw_integrate_ab4(kind, x, dt, nsteps, t0=0.0, coef=None):
     c = _f64(coef) if coef is not None else None
     lib().orc_pw_integrate_ab4(kind, _p(c), x.size, _p(x), t0, dt, nsteps)
     return x
+
+
+def pw_integrate_adaptive_each(kind, x, t0, t_end, dt0, atol, rtol, method=DOPRI5, max_acc=-1, max_rej=500,
+                               coef=None):
+    """Every element its own step size and controller."""
+    x = _f64(x).copy()
+    n = x.size
+    c = _f64(coef) if coef is not None else None
+    t = np.zeros(n)
+    dt = np.zeros(n)
+    na = np.zeros(n, dtype=np.int64)
+    nr = np.zeros(n, dtype=np.int64)
+    stv = np.zeros(n, dtype=np.int32)
+    _lp = C.POINTER(C.c_long)
+    st = lib().orc_pw_integrate_adaptive_each(method, kind, _p(c), n, _p(x), t0, t_end, dt0, atol, rtol, max_acc,
+                                              max_rej, _p(t), _p(dt), na.ctypes.data_as(_lp),
+                                              nr.ctypes.data_as(_lp), stv.ctypes.data_as(C.POINTER(C.c_int)))
+    if st != OK:
+        raise ValueError(st)
+    return {"x": x, "t": t, "dt": dt, "n_acc": na, "n_rej": nr, "status": stv}
+
+
+def ab_coefficients(steps):
+    beta = np.zeros(steps)
+    if lib().orc_ab_coefficients(steps, _p(beta)) != OK:
+        raise ValueError(steps)
+    return beta
+
+
+def pw_integrate_ab(steps, kind, x, dt, nsteps, t0=0.0, coef=None):
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    if lib().orc_pw_integrate_ab(steps, kind, _p(c), x.size, _p(x), t0, dt, nsteps) != OK:
+        raise ValueError(steps)
+    return x
+
+
+def pair_orders(method):
+    p, q = C.c_int(0), C.c_int(0)
+    if lib().orc_pair_orders(method, C.byref(p), C.byref(q)) != 0:
+        raise ValueError(method)
+    return p.value, q.value
 
 
 def pw_dopri5_attempt(kind, x, dt, atol, rtol, t=0.0, coef=None):

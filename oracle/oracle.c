@@ -23,7 +23,12 @@
  *     nomenclature of Boost Odeint": error stepper + L-infinity norm + step
  *     size controller).  The paper gives no controller formula; the reading
  *     used here is stated at orc_integrate_adaptive.
- *   - the Adams-Bashforth 4 multistep method (Table 1) started by RK4.
+ *   - the Adams-Bashforth 4 multistep method (Table 1) started by RK4, and
+ *     Adams-Bashforth with 1..8 steps (Table 1, Fig. 2c,d) with coefficients
+ *     integrated from their definition.
+ *   - the further tableaux of Table 1: Cash-Karp 5(4) and Fehlberg 7(8), and
+ *     the adaptive driver for any embedded pair; per-element adaptive
+ *     integration of independent scalar ODEs (each its own step size).
  *   - the n-ary stage algebra y = sum_j a_j x_j (section "The distributed
  *     OpenFPM state type and algebra", for_each operations, up to 15 terms).
  *   - 3D periodic convolution forward / input-gradient / weight-gradient for
@@ -46,7 +51,7 @@ typedef struct {
     int has_bhat;
 } orc_tableau;
 
-enum { ORC_EULER = 0, ORC_RK4 = 1, ORC_DOPRI5 = 2 };
+enum { ORC_EULER = 0, ORC_RK4 = 1, ORC_DOPRI5 = 2, ORC_CK54 = 3, ORC_RKF78 = 4 };
 
 /* Fills tableau T for method id; returns 0 on success. */
 int orc_get_tableau(int id, orc_tableau* T) {
@@ -93,7 +98,82 @@ int orc_get_tableau(int id, orc_tableau* T) {
         T->has_bhat = 1;
         return 0;
     }
+    if (id == ORC_CK54) {
+        /* Cash & Karp (1990) embedded 5(4): the order-5 solution b is
+         * propagated, bhat is the order-4 one. */
+        const int s = 6;
+        double* a = T->a;
+        T->s = s;
+        T->c[0] = 0.0; T->c[1] = 1.0 / 5.0; T->c[2] = 3.0 / 10.0; T->c[3] = 3.0 / 5.0;
+        T->c[4] = 1.0; T->c[5] = 7.0 / 8.0;
+        a[1 * s + 0] = 1.0 / 5.0;
+        a[2 * s + 0] = 3.0 / 40.0;         a[2 * s + 1] = 9.0 / 40.0;
+        a[3 * s + 0] = 3.0 / 10.0;         a[3 * s + 1] = -9.0 / 10.0;     a[3 * s + 2] = 6.0 / 5.0;
+        a[4 * s + 0] = -11.0 / 54.0;       a[4 * s + 1] = 5.0 / 2.0;       a[4 * s + 2] = -70.0 / 27.0;
+        a[4 * s + 3] = 35.0 / 27.0;
+        a[5 * s + 0] = 1631.0 / 55296.0;   a[5 * s + 1] = 175.0 / 512.0;   a[5 * s + 2] = 575.0 / 13824.0;
+        a[5 * s + 3] = 44275.0 / 110592.0; a[5 * s + 4] = 253.0 / 4096.0;
+        T->b[0] = 37.0 / 378.0; T->b[2] = 250.0 / 621.0; T->b[3] = 125.0 / 594.0; T->b[5] = 512.0 / 1771.0;
+        T->bhat[0] = 2825.0 / 27648.0; T->bhat[2] = 18575.0 / 48384.0; T->bhat[3] = 13525.0 / 55296.0;
+        T->bhat[4] = 277.0 / 14336.0;  T->bhat[5] = 1.0 / 4.0;
+        T->has_bhat = 1;
+        return 0;
+    }
+    if (id == ORC_RKF78) {
+        /* Fehlberg (1968) embedded 7(8), 13 stages.  Table 1 lists the method
+         * as order 8: the order-8 solution b is propagated, bhat is the order-7
+         * one (they differ only in k1, k11, k12, k13). */
+        const int s = 13;
+        double* a = T->a;
+        T->s = s;
+        const double c[13] = {0.0, 2.0 / 27.0, 1.0 / 9.0, 1.0 / 6.0, 5.0 / 12.0, 1.0 / 2.0, 5.0 / 6.0,
+                              1.0 / 6.0, 2.0 / 3.0, 1.0 / 3.0, 1.0, 0.0, 1.0};
+        for (int i = 0; i < s; ++i) T->c[i] = c[i];
+        a[1 * s + 0] = 2.0 / 27.0;
+        a[2 * s + 0] = 1.0 / 36.0;      a[2 * s + 1] = 1.0 / 12.0;
+        a[3 * s + 0] = 1.0 / 24.0;      a[3 * s + 2] = 1.0 / 8.0;
+        a[4 * s + 0] = 5.0 / 12.0;      a[4 * s + 2] = -25.0 / 16.0;    a[4 * s + 3] = 25.0 / 16.0;
+        a[5 * s + 0] = 1.0 / 20.0;      a[5 * s + 3] = 1.0 / 4.0;       a[5 * s + 4] = 1.0 / 5.0;
+        a[6 * s + 0] = -25.0 / 108.0;   a[6 * s + 3] = 125.0 / 108.0;   a[6 * s + 4] = -65.0 / 27.0;
+        a[6 * s + 5] = 125.0 / 54.0;
+        a[7 * s + 0] = 31.0 / 300.0;    a[7 * s + 4] = 61.0 / 225.0;    a[7 * s + 5] = -2.0 / 9.0;
+        a[7 * s + 6] = 13.0 / 900.0;
+        a[8 * s + 0] = 2.0;             a[8 * s + 3] = -53.0 / 6.0;     a[8 * s + 4] = 704.0 / 45.0;
+        a[8 * s + 5] = -107.0 / 9.0;    a[8 * s + 6] = 67.0 / 90.0;     a[8 * s + 7] = 3.0;
+        a[9 * s + 0] = -91.0 / 108.0;   a[9 * s + 3] = 23.0 / 108.0;    a[9 * s + 4] = -976.0 / 135.0;
+        a[9 * s + 5] = 311.0 / 54.0;    a[9 * s + 6] = -19.0 / 60.0;    a[9 * s + 7] = 17.0 / 6.0;
+        a[9 * s + 8] = -1.0 / 12.0;
+        a[10 * s + 0] = 2383.0 / 4100.0; a[10 * s + 3] = -341.0 / 164.0; a[10 * s + 4] = 4496.0 / 1025.0;
+        a[10 * s + 5] = -301.0 / 82.0;   a[10 * s + 6] = 2133.0 / 4100.0; a[10 * s + 7] = 45.0 / 82.0;
+        a[10 * s + 8] = 45.0 / 164.0;    a[10 * s + 9] = 18.0 / 41.0;
+        a[11 * s + 0] = 3.0 / 205.0;     a[11 * s + 5] = -6.0 / 41.0;    a[11 * s + 6] = -3.0 / 205.0;
+        a[11 * s + 7] = -3.0 / 41.0;     a[11 * s + 8] = 3.0 / 41.0;     a[11 * s + 9] = 6.0 / 41.0;
+        a[12 * s + 0] = -1777.0 / 4100.0; a[12 * s + 3] = -341.0 / 164.0; a[12 * s + 4] = 4496.0 / 1025.0;
+        a[12 * s + 5] = -289.0 / 82.0;   a[12 * s + 6] = 2193.0 / 4100.0; a[12 * s + 7] = 51.0 / 82.0;
+        a[12 * s + 8] = 33.0 / 164.0;    a[12 * s + 9] = 12.0 / 41.0;    a[12 * s + 11] = 1.0;
+        const double w7[13] = {41.0 / 840.0, 0, 0, 0, 0, 34.0 / 105.0, 9.0 / 35.0, 9.0 / 35.0, 9.0 / 280.0,
+                               9.0 / 280.0, 41.0 / 840.0, 0, 0};
+        const double w8[13] = {0, 0, 0, 0, 0, 34.0 / 105.0, 9.0 / 35.0, 9.0 / 35.0, 9.0 / 280.0,
+                               9.0 / 280.0, 0, 41.0 / 840.0, 41.0 / 840.0};
+        for (int i = 0; i < s; ++i) {
+            T->b[i] = w8[i];
+            T->bhat[i] = w7[i];
+        }
+        T->has_bhat = 1;
+        return 0;
+    }
     return 1;
+}
+
+/* Orders of an embedded pair for the step-size controller: p of the
+ * propagated solution, q of the embedded one (0 if the method has none). */
+int orc_pair_orders(int id, int* p, int* q) {
+    switch (id) {
+        case ORC_DOPRI5: *p = 5; *q = 4; return 0;
+        case ORC_CK54: *p = 5; *q = 4; return 0;
+        case ORC_RKF78: *p = 8; *q = 7; return 0;
+        default: *p = 0; *q = 0; return 1;
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -281,11 +361,13 @@ double orc_error_attempt(const orc_tableau* T, orc_rhs_fn F, const void* sys, lo
 enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 3, ORC_ERR_STEP_UNDERFLOW = 4,
        ORC_ERR_MAX_STEPS = 5, ORC_ERR_NONFINITE = 6 };
 
-/* integrate_adaptive with Dormand-Prince 5(4).
+/* integrate_adaptive with an embedded pair (Dormand-Prince 5(4) by default;
+ * Cash-Karp 5(4), Fehlberg 7(8)).
  *
  * The paper states only that adaptive steppers size each step from an error
  * estimate and a tolerance, with an L-infinity norm.  The controller read
- * here (error order q = 4, stepper order p = 5):
+ * here (propagated order p, embedded order q: Dormand-Prince and Cash-Karp
+ * p = 5, q = 4; Fehlberg p = 8, q = 7):
  *   attempt size h = dt, clipped to t_end - t if t + dt >= t_end;
  *   E > 1            : reject; dt = h * max(0.9 E^(-1/(q-1)), 0.2)
  *   E < 0.5          : accept; dt = h * 0.9 * max(E, 5^-p)^(-1/p)
@@ -296,12 +378,13 @@ enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 3, ORC_ERR_STEP_UNDERFLO
  * t reaches t_end or after max_acc accepted steps (max_acc < 0: no limit).
  * If log_dt != NULL the accepted step sizes are written there (up to log_cap).
  */
-int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
-                           double t_end, double* dt_io, double atol, double rtol, long max_acc,
-                           long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
-                           long log_cap) {
+int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
+                             double t_end, double* dt_io, double atol, double rtol, long max_acc,
+                             long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
+                             long log_cap) {
     orc_tableau T;
-    orc_get_tableau(ORC_DOPRI5, &T);
+    int po = 0, qo = 0;
+    if (orc_get_tableau(method, &T) || orc_pair_orders(method, &po, &qo)) return ORC_ERR_INVALID;
     const int s = T.s;
     double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)s);
     double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
@@ -320,7 +403,7 @@ int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, dou
         if (!isfinite(E)) { status = ORC_ERR_NONFINITE; break; }
         if (E > 1.0) {
             ++n_rej; ++consec;
-            double fac = 0.9 * pow(E, -1.0 / 3.0);
+            double fac = 0.9 * pow(E, -1.0 / (double)(qo - 1));
             if (fac < 0.2) fac = 0.2;
             dt = h * fac;
             if (consec >= max_rej) { status = ORC_ERR_STEP_UNDERFLOW; break; }
@@ -333,9 +416,9 @@ int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, dou
         t = last ? t_end : t + h;
         if (E < 0.5) {
             double Em = E;
-            const double floor5 = pow(5.0, -5.0);
+            const double floor5 = pow(5.0, -(double)po);
             if (Em < floor5) Em = floor5;
-            dt = h * 0.9 * pow(Em, -1.0 / 5.0);
+            dt = h * 0.9 * pow(Em, -1.0 / (double)po);
         } else {
             dt = h;
         }
@@ -346,6 +429,79 @@ int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, dou
     if (n_rej_out) *n_rej_out = n_rej;
     free(k); free(ytmp); free(ynew); free(err);
     return status;
+}
+
+int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
+                           double t_end, double* dt_io, double atol, double rtol, long max_acc,
+                           long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
+                           long log_cap) {
+    return orc_integrate_adaptive_m(ORC_DOPRI5, F, sys, n, y, t_io, t_end, dt_io, atol, rtol, max_acc,
+                                    max_rej, n_acc_out, n_rej_out, log_dt, log_cap);
+}
+
+/* Adams-Bashforth with s steps (Table 1: 1..8; Fig. 2c,d):
+ *   u_{m+1} = u_m + dt sum_{j<s} beta_j f_{m-j},
+ * beta_j = the integral over [t_m, t_m + dt] of the Lagrange basis polynomial
+ * of node t_{m-j} among the nodes t_m, ..., t_{m-s+1}, divided by dt.  In
+ * the unit variable tau (node m-j at tau = -j):
+ *   beta_j = int_0^1 prod_{i != j} (tau + i) / (i - j) dtau.
+ * The polynomial is expanded in powers of tau and integrated term by term. */
+int orc_ab_coefficients(int s, double* beta) {
+    if (s < 1 || s > 8) return ORC_ERR_INVALID;
+    for (int j = 0; j < s; ++j) {
+        double poly[9] = {1.0, 0, 0, 0, 0, 0, 0, 0, 0}; /* coefficients of tau^0..tau^8 */
+        int deg = 0;
+        double denom = 1.0;
+        for (int i = 0; i < s; ++i) {
+            if (i == j) continue;
+            /* multiply by (tau + i) */
+            for (int d = deg + 1; d >= 1; --d) poly[d] = poly[d - 1] + (double)i * poly[d];
+            poly[0] = (double)i * poly[0];
+            ++deg;
+            denom *= (double)(i - j);
+        }
+        double integral = 0.0;
+        for (int d = 0; d <= deg; ++d) integral += poly[d] / (double)(d + 1);
+        beta[j] = integral / denom;
+    }
+    return ORC_OK;
+}
+
+/* Adams-Bashforth with s steps, t_m = t0 + m dt.  The first s - 1 steps of
+ * a call are one-step steps of order >= s (this build's reading: the paper
+ * does not say how the history is started): RK4 for s <= 4, the order-8
+ * Fehlberg solution for s >= 5, so the start-up does not limit the observed
+ * order.  s = 1 is explicit Euler. */
+int orc_integrate_ab(int s, orc_rhs_fn F, const void* sys, long n, double* y, double t0, double dt,
+                     long nsteps) {
+    double beta[8];
+    if (orc_ab_coefficients(s, beta)) return ORC_ERR_INVALID;
+    orc_tableau T;
+    orc_get_tableau(s <= 4 ? ORC_RK4 : ORC_RKF78, &T);
+    double* f = (double*)malloc(sizeof(double) * (size_t)n * (size_t)s);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!f || !k || !ytmp) { free(f); free(k); free(ytmp); return ORC_ERR_NOMEM; }
+    double* fm[8];
+    for (int j = 0; j < s; ++j) fm[j] = f + (long)j * n; /* fm[j] = f_{m-j} */
+    for (long m = 0; m < nsteps; ++m) {
+        const double t = t0 + (double)m * dt;
+        double* oldest = fm[s - 1];
+        for (int j = s - 1; j >= 1; --j) fm[j] = fm[j - 1];
+        fm[0] = oldest;
+        F(sys, t, n, y, fm[0]);
+        if (m < s - 1) {
+            orc_rk_step(&T, F, sys, n, t, dt, y, y, NULL, k, ytmp);
+        } else {
+            for (long e = 0; e < n; ++e) {
+                double acc = 0.0;
+                for (int j = 0; j < s; ++j) acc += beta[j] * fm[j][e];
+                y[e] = y[e] + dt * acc;
+            }
+        }
+    }
+    free(f); free(k); free(ytmp);
+    return ORC_OK;
 }
 
 /* Adams-Bashforth 4 (Table 1, multi-step), started with three RK4 steps:
@@ -440,6 +596,41 @@ int orc_pw_integrate_ab4(int kind, const double* coef, long n, double* y, double
                          long nsteps) {
     orc_pointwise p = {kind, coef};
     return orc_integrate_ab4(orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
+}
+int orc_pw_integrate_ab(int steps, int kind, const double* coef, long n, double* y, double t0, double dt,
+                        long nsteps) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_ab(steps, orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
+}
+int orc_pw_integrate_adaptive_m(int method, int kind, const double* coef, long n, double* y, double* t,
+                                double t_end, double* dt, double atol, double rtol, long max_acc,
+                                long max_rej, long* n_acc, long* n_rej, double* log_dt, long log_cap) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_adaptive_m(method, orc_pointwise_rhs, &p, n, y, t, t_end, dt, atol, rtol, max_acc,
+                                    max_rej, n_acc, n_rej, log_dt, log_cap);
+}
+/* Independent scalar ODEs, each with its own step size and controller: the
+ * adaptive driver applied to each element alone (element e: a one-element
+ * system; its coefficient coef[e] for the Eq. 1a family).  Per-element
+ * results: final t, next dt, accepted and rejected counts, status. */
+int orc_pw_integrate_adaptive_each(int method, int kind, const double* coef, long n, double* y, double t0,
+                                   double t_end, double dt0, double atol, double rtol, long max_acc,
+                                   long max_rej, double* t_out, double* dt_out, long* n_acc, long* n_rej,
+                                   int* status) {
+    for (long e = 0; e < n; ++e) {
+        orc_pointwise p = {kind, coef ? coef + e : NULL};
+        double t = t0, dt = dt0;
+        long na = 0, nr = 0;
+        const int st = orc_integrate_adaptive_m(method, orc_pointwise_rhs, &p, 1, y + e, &t, t_end, &dt, atol,
+                                                rtol, max_acc, max_rej, &na, &nr, NULL, 0);
+        if (st == ORC_ERR_INVALID || st == ORC_ERR_NOMEM) return st;
+        t_out[e] = t;
+        dt_out[e] = dt;
+        n_acc[e] = na;
+        n_rej[e] = nr;
+        status[e] = st;
+    }
+    return ORC_OK;
 }
 /* One Dopri5 attempt on a pointwise system: yout, err, returns the norm. */
 double orc_pw_dopri5_attempt(int kind, const double* coef, long n, double t, double dt,

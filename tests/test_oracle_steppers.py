@@ -211,3 +211,141 @@ def test_axpy_exact_and_limits():
     assert np.array_equal(y, expect)
     with pytest.raises(ValueError):
         oracle.axpy(np.ones(16), [np.ones(3)] * 16)
+
+
+# ------------------------------------------- Table 1: Cash-Karp 5(4), Fehlberg 7(8)
+@pytest.mark.parametrize("method,weights,order", [
+    (oracle.CK54, "b", 5),
+    (oracle.CK54, "bhat", 4),
+    (oracle.RKF78, "b", 8),
+    (oracle.RKF78, "bhat", 7),
+])
+def test_order_conditions_ck54_rkf78(method, weights, order):
+    # same conditions; the tolerance scales with the coefficient magnitudes
+    # (Fehlberg's rows hold entries up to 15.6, summed over 13 stages)
+    T = oracle.tableau(method)
+    A, b = T["A"], T[weights]
+    scale = 1.0 + float(np.abs(A).sum())
+    assert np.allclose(A.sum(axis=1), T["c"], atol=1e-16 * scale, rtol=0)
+    for p in range(1, order + 1):
+        for t in _trees(p):
+            assert abs(b @ _phi(t, A) - 1.0 / _gamma(t)) < 1e-15 * scale, (p, t)
+    worst = max(abs(b @ _phi(t, A) - 1.0 / _gamma(t)) for t in _trees(order + 1))
+    assert worst > 1e-9
+
+
+def test_rkf78_error_estimate_vanishes_for_time_only_rhs():
+    # b - bhat = 41/840 (-1, 0..0, -1, +1, +1) on stages 1, 11, 12, 13 with
+    # c = 0, 1, 0, 1: for f = f(t) the four stages pair up and the estimate is 0
+    T = oracle.tableau(oracle.RKF78)
+    d = T["b"] - T["bhat"]
+    assert np.allclose(d[[0, 10, 11, 12]], np.array([-1, -1, 1, 1]) * 41 / 840, rtol=1e-15, atol=0)
+    assert np.all(d[1:10] == 0)
+    assert (T["c"][0], T["c"][10], T["c"][11], T["c"][12]) == (0.0, 1.0, 0.0, 1.0)
+    assert oracle.pair_orders(oracle.RKF78) == (8, 7)
+    assert oracle.pair_orders(oracle.CK54) == (5, 4) == oracle.pair_orders(oracle.DOPRI5)
+
+
+@pytest.mark.parametrize("kind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP,
+                                  oracle.PW_PAPER_SIGMOID])
+@pytest.mark.parametrize("method,order,nbase", [(oracle.CK54, 5, 40), (oracle.RKF78, 8, 12)])
+def test_observed_order_ck54_rkf78(kind, method, order, nbase):
+    x0, t0, t1, coef = _family(kind)
+    exact = _closed_form(kind, x0, t0, t1, coef)
+    errs = []
+    for m in (nbase, 2 * nbase):
+        x = oracle.pw_integrate_const(kind, x0, method, (t1 - t0) / m, m, t0=t0, coef=coef)
+        errs.append(oracle.linf(x - exact))
+    if errs[1] < 1e-13:
+        # Eq. 1b: the order-8 rule is at round-off already; check accuracy only
+        assert kind == oracle.PW_PAPER_SIGMOID and errs[0] < 1e-9, errs
+        return
+    ratio = errs[0] / errs[1]
+    if kind == oracle.PW_PAPER_SIGMOID and order % 2 == 1:
+        order += 1  # even integrand on a symmetric interval (see test_observed_order)
+    assert abs(math.log2(ratio) - order) < 0.7, (errs, ratio)
+
+
+# ------------------------------------------------ Adams-Bashforth 1..8 (Fig. 2c,d)
+@pytest.mark.parametrize("steps", range(1, 9))
+def test_ab_coefficients_exact_on_polynomials(steps):
+    # an s-step Adams-Bashforth rule integrates polynomials of degree < s
+    # exactly: sum_j beta_j (-j)^k = 1 / (k + 1) for k = 0 .. s-1
+    beta = oracle.ab_coefficients(steps)
+    j = np.arange(steps)
+    for k in range(steps):
+        lhs = float(np.sum(beta * (-j) ** k)) if k else float(np.sum(beta))
+        assert abs(lhs - 1.0 / (k + 1)) < 1e-12 * max(1.0, float(np.sum(np.abs(beta * j ** k)))), (k, lhs)
+    # and not of degree s (the next moment fails)
+    assert abs(float(np.sum(beta * (-j) ** steps)) - 1.0 / (steps + 1)) > 1e-6
+
+
+def test_ab_coefficients_known_rules():
+    assert np.allclose(oracle.ab_coefficients(1), [1.0], rtol=0, atol=0)
+    assert np.allclose(oracle.ab_coefficients(2), [1.5, -0.5], rtol=1e-15, atol=0)
+    assert np.allclose(oracle.ab_coefficients(4), np.array([55, -59, 37, -9]) / 24, rtol=1e-14, atol=0)
+
+
+def test_ab4_generic_matches_ab4():
+    x0, t0, t1, coef = _family(oracle.PW_PAPER_EXP)
+    a = oracle.pw_integrate_ab(4, oracle.PW_PAPER_EXP, x0, 0.05, 200, t0=t0, coef=coef)
+    b = oracle.pw_integrate_ab4(oracle.PW_PAPER_EXP, x0, 0.05, 200, t0=t0, coef=coef)
+    assert np.allclose(a, b, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("steps", range(1, 9))
+def test_ab_observed_order_exponential_family(steps):
+    # Fig. 2c: the exponential family (Eq. 1a) with 1..8 steps shows order s
+    x0, t0, t1, coef = _family(oracle.PW_PAPER_EXP)
+    exact = _closed_form(oracle.PW_PAPER_EXP, x0, t0, t1, coef)
+    errs = []
+    for m in (200, 400):
+        x = oracle.pw_integrate_ab(steps, oracle.PW_PAPER_EXP, x0, (t1 - t0) / m, m, t0=t0, coef=coef)
+        errs.append(oracle.linf(x - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - steps) < 0.4, errs
+
+
+@pytest.mark.parametrize("steps", range(1, 6))
+def test_ab_observed_order_decay(steps):
+    x0, t0, t1, coef = _family(oracle.PW_EXP_DECAY)
+    exact = _closed_form(oracle.PW_EXP_DECAY, x0, t0, t1, coef)
+    errs = []
+    for m in (100, 200):
+        x = oracle.pw_integrate_ab(steps, oracle.PW_EXP_DECAY, x0, (t1 - t0) / m, m, t0=t0)
+        errs.append(oracle.linf(x - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - steps) < 0.45, errs
+
+
+# -------------------------------- adaptive: any embedded pair; per-element steps
+@pytest.mark.parametrize("method", [oracle.DOPRI5, oracle.CK54, oracle.RKF78])
+@pytest.mark.parametrize("tol", [1e-6, 1e-10])
+def test_adaptive_each_closed_form_and_independent_steps(method, tol):
+    # every element of dx/dt = -x integrated with its own step size: the
+    # closed form within C * tol, and elements of different size take
+    # different numbers of steps (x0 = 0 stays 0 and takes the fewest)
+    x0 = np.linspace(0.0, 1.0, 11)
+    r = oracle.pw_integrate_adaptive_each(oracle.PW_EXP_DECAY, x0, 0.0, 10.0, 0.1, tol, tol, method=method)
+    exact = x0 * np.exp(-10.0)
+    assert np.all(r["status"] == oracle.OK) and np.all(r["t"] == 10.0)
+    assert np.max(np.abs(r["x"] - exact) / (1.0 + np.abs(exact))) < 5 * tol
+    assert r["x"][0] == 0.0
+    assert r["n_acc"][0] == r["n_acc"].min() and r["n_acc"][0] < r["n_acc"][-1]
+    assert len(set(r["n_acc"].tolist())) > 3
+
+
+def test_adaptive_each_higher_order_takes_fewer_steps():
+    x0 = np.linspace(0.1, 0.9, 5)  # (x = 1 is a fixed point of the logistic)
+    n = {}
+    for m in (oracle.DOPRI5, oracle.RKF78):
+        r = oracle.pw_integrate_adaptive_each(oracle.PW_LOGISTIC, x0, 0.0, 10.0, 0.1, 1e-10, 1e-10, method=m)
+        n[m] = r["n_acc"]
+    assert np.all(n[oracle.RKF78] * 2 < n[oracle.DOPRI5])
+
+
+@pytest.mark.parametrize("method", [oracle.DOPRI5, oracle.CK54])
+def test_adaptive_global_norm_any_pair_closed_form(method):
+    x0, t0, t1, coef = _family(oracle.PW_PAPER_EXP)
+    exact = _closed_form(oracle.PW_PAPER_EXP, x0, t0, t1, coef)
+    r = oracle.pw_integrate_adaptive(oracle.PW_PAPER_EXP, x0, t0, t1, 0.1, 1e-9, 1e-9, coef=coef, method=method)
+    assert r["status"] == oracle.OK and r["t"] == t1
+    assert np.max(np.abs(r["x"] - exact) / (1.0 + np.abs(exact))) < 5e-9
