@@ -445,9 +445,22 @@ gs_status ode_axpy_stage(long n, gs_precision prec, int nterms, const double* co
 /* (autonomous forms of the benchmark families of "Accuracy Benchmarks")    */
 /* ------------------------------------------------------------------------ */
 typedef enum {
-    ODE_EXP_DECAY = 0, /* f(x) = -x,        x(t) = x0 e^-t */
-    ODE_LOGISTIC = 1   /* f(x) = x (1 - x), x(t) = x0 / (x0 + (1 - x0) e^-t) */
+    ODE_EXP_DECAY = 0,    /* f(x) = -x,        x(t) = x0 e^-t */
+    ODE_LOGISTIC = 1,     /* f(x) = x (1 - x), x(t) = x0 / (x0 + (1 - x0) e^-t) */
+    ODE_PAPER_EXP = 2,    /* Eq. 1a: f(t) = c_i e^t (c_i = x y of element i), u = c_i e^t */
+    ODE_PAPER_SIGMOID = 3 /* Eq. 1b: f(t) = s (1 - s), s = 1 / (1 + e^-t), u = s(t) */
 } ode_rhs;
+/* (ODE_PAPER_EXP and ODE_PAPER_SIGMOID: ode_integrate_tableau,
+ * ode_integrate_ab_steps and ode_integrate_adaptive_each only.) */
+
+/* Explicit Runge-Kutta tableaux of Table 1 for the pointwise ensembles. */
+typedef enum {
+    ODE_TAB_EULER = 0,
+    ODE_TAB_RK4 = 1,
+    ODE_TAB_DOPRI5 = 2, /* Dormand-Prince 5(4), order 5 propagated */
+    ODE_TAB_CK54 = 3,   /* Cash-Karp 5(4), order 5 propagated */
+    ODE_TAB_RKF78 = 4   /* Fehlberg 7(8), 13 stages, order 8 propagated */
+} ode_tableau;
 
 /* Workspace bytes needed by ode_integrate_adaptive for n elements. */
 size_t ode_workspace_size(long n);
@@ -503,6 +516,48 @@ gs_status ode_integrate_ab4(ode_rhs rhs, long n, double* x_dev, double t0, doubl
  * registers, one kernel.  Enqueued on stream. */
 gs_status ode_integrate_const(ode_rhs rhs, gs_method method, long n, double* x_dev, double t0,
                               double dt, long nsteps, void* stream);
+
+/* Fixed-step explicit Runge-Kutta with tableau `method` (Table 1) on n
+ * independent FP64 elements x (device), t_m = t0 + m dt, nsteps steps; all
+ * stages and steps of an element in registers, one kernel.  coef: device
+ * array of n coefficients c_i, required for ODE_PAPER_EXP, else ignored
+ * (may be NULL).  INVALID: unknown kind or method, n < 0, nsteps < 0,
+ * non-finite t0 or dt, coef missing for ODE_PAPER_EXP.  Enqueued on stream. */
+gs_status ode_integrate_tableau(ode_rhs rhs, ode_tableau method, long n, double* x_dev,
+                                const double* coef_dev, double t0, double dt, long nsteps,
+                                void* stream);
+
+/* Adams-Bashforth with `steps` = 1..8 steps (Table 1; Fig. 2c,d):
+ * u_{m+1} = u_m + dt sum_{j<s} beta_j f(t_{m-j}, u_{m-j}) with the
+ * Adams-Bashforth weights, t_m = t0 + m dt.  The first steps - 1 steps of a
+ * call are one-step steps of order >= steps (RK4 for steps <= 4, the order-8
+ * Fehlberg solution for 5..8), so the start-up does not limit the order; the
+ * history lives in registers.  Same arguments and errors as
+ * ode_integrate_tableau.  Enqueued on stream. */
+gs_status ode_integrate_ab_steps(ode_rhs rhs, int steps, long n, double* x_dev, const double* coef_dev,
+                                 double t0, double dt, long nsteps, void* stream);
+
+/* Error-controlled integration of n INDEPENDENT scalar ODEs, each with its
+ * own step size and controller (no global norm), from t0 to t_end with the
+ * embedded pair `method` (ODE_TAB_DOPRI5, ODE_TAB_CK54, ODE_TAB_RKF78).
+ * Per element: E = |err| / (atol + rtol (|x| + h |k1|)); E > 1 rejects and
+ * shrinks dt = h max(0.9 E^(-1/(q-1)), 0.2); else accept, and if E < 0.5
+ * grow dt = 0.9 h max(E, 5^-p)^(-1/p) (p, q = propagated / embedded order:
+ * 5, 4 for Dormand-Prince and Cash-Karp, 8, 7 for Fehlberg); the last step
+ * is clipped to t_end.  An element stops at t_end, after max_acc accepted
+ * steps (< 0: no limit), after max_rej consecutive rejections or a step that
+ * no longer advances t (GS_ERR_STEP_UNDERFLOW), on a non-finite error
+ * (GS_ERR_NONFINITE) or after 2^22 attempts (GS_ERR_MAX_STEPS).  Optional
+ * device outputs (each may be NULL): final t, next dt, accepted and rejected
+ * counts, status per element.  INVALID: bad kind / method, n < 0,
+ * non-finite t0 / t_end, dt0 <= 0, negative tolerances or both zero,
+ * max_rej < 1.  Enqueued on stream.  (Fehlberg's embedded estimate is zero
+ * for f = f(t), as for Eq. 1a/1b: its step size then only grows.) */
+gs_status ode_integrate_adaptive_each(ode_rhs rhs, ode_tableau method, long n, double* x_dev,
+                                      const double* coef_dev, double t0, double t_end, double dt0,
+                                      double atol, double rtol, long max_acc, long max_rej,
+                                      double* t_out_dev, double* dt_out_dev, long* n_acc_dev,
+                                      long* n_rej_dev, int* status_dev, void* stream);
 
 /* Measures this device's FP64 fused-multiply-add throughput (TFLOP/s,
  * 2 flops per FMA) with independent dependent-chains; used as the ALU

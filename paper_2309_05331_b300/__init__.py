@@ -88,6 +88,13 @@ _SIGNATURES = {
                                         C.c_long, _lp, _lp, _vp], C.c_int),
     "ode_integrate_ab4": ([C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
     "ode_integrate_const": ([C.c_int, C.c_int, C.c_long, _vp, C.c_double, C.c_double, C.c_long, _vp], C.c_int),
+    "ode_integrate_tableau": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_long, _vp],
+                              C.c_int),
+    "ode_integrate_ab_steps": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_long, _vp],
+                               C.c_int),
+    "ode_integrate_adaptive_each": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_double, C.c_long, C.c_long, _vp, _vp, _vp, _vp, _vp, _vp],
+                                    C.c_int),
     "gs_measure_fp64_peak": ([_dp, _vp], C.c_int),
     "gsb_create": ([C.c_int, C.POINTER(gsb_instance), C.c_double, C.c_double, C.c_double, C.c_int, _vp,
                     C.POINTER(_vp)], C.c_int),
@@ -387,6 +394,41 @@ def ode_integrate_ab4(kind, x, t0, dt, nsteps, stream=None):
 
 def ode_integrate_const(kind, method, x, t0, dt, nsteps, stream=None):
     _check(lib().ode_integrate_const(kind, method, x.numel(), _ptr(x), t0, dt, nsteps, _stream(stream)))
+
+
+ODE_PAPER_EXP, ODE_PAPER_SIGMOID = 2, 3
+ODE_TAB_EULER, ODE_TAB_RK4, ODE_TAB_DOPRI5, ODE_TAB_CK54, ODE_TAB_RKF78 = 0, 1, 2, 3, 4
+
+
+def ode_integrate_tableau(kind, method, x, t0, dt, nsteps, coef=None, stream=None):
+    """Fixed steps of a Table 1 tableau on x (FP64 CUDA tensor), in place."""
+    _check(lib().ode_integrate_tableau(kind, method, x.numel(), _ptr(x), _ptr(coef), t0, dt, nsteps,
+                                       _stream(stream)))
+
+
+def ode_integrate_ab_steps(kind, steps, x, t0, dt, nsteps, coef=None, stream=None):
+    """Adams-Bashforth with `steps` (1..8) steps on x, in place."""
+    _check(lib().ode_integrate_ab_steps(kind, steps, x.numel(), _ptr(x), _ptr(coef), t0, dt, nsteps,
+                                        _stream(stream)))
+
+
+def ode_integrate_adaptive_each(kind, method, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500, coef=None,
+                                outputs=True, stream=None):
+    """Every element its own step size; returns per-element t, dt, counts, status (CUDA tensors)."""
+    import torch
+    n = x.numel()
+    out = {}
+    if outputs:
+        out = {"t": torch.empty(n, dtype=torch.float64, device=x.device),
+               "dt": torch.empty(n, dtype=torch.float64, device=x.device),
+               "n_acc": torch.empty(n, dtype=torch.int64, device=x.device),
+               "n_rej": torch.empty(n, dtype=torch.int64, device=x.device),
+               "status": torch.empty(n, dtype=torch.int32, device=x.device)}
+    _check(lib().ode_integrate_adaptive_each(kind, method, n, _ptr(x), _ptr(coef), t0, t_end, dt0, atol, rtol,
+                                             max_acc, max_rej, _ptr(out.get("t")), _ptr(out.get("dt")),
+                                             _ptr(out.get("n_acc")), _ptr(out.get("n_rej")),
+                                             _ptr(out.get("status")), _stream(stream)))
+    return out
 
 
 def gs_measure_fp64_peak(stream=None):

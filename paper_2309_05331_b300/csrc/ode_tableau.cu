@@ -1,0 +1,489 @@
+// ode_tableau.cu -- the further steppers of Table 1 on ensembles of
+// independent scalar ODEs (FP64), with the benchmark families of the
+// section "Accuracy Benchmarks": dx/dt = -x, x (1 - x), and the paper's
+// exponential family du/dt = c e^t (Eq. 1a, one coefficient c = x y per
+// element) and sigmoidal dynamics du/dt = s(t) (1 - s(t)), s = 1 / (1 +
+// e^-t) (Eq. 1b).
+//
+//   - fixed-step explicit Runge-Kutta with any tableau of Table 1 (Euler,
+//     RK4, Dormand-Prince 5, Cash-Karp 5(4), Fehlberg 7(8));
+//   - Adams-Bashforth with 1..8 steps (Table 1; Fig. 2c,d), the history in
+//     registers, started by a one-step method of order >= s (RK4 for s <= 4,
+//     the order-8 Fehlberg solution for s >= 5);
+//   - error-controlled integration where EVERY element has its own step size
+//     and controller (no global norm: the elements are independent), with
+//     any embedded pair (Dormand-Prince, Cash-Karp, Fehlberg).
+//
+// One thread owns one element for the whole call (grid-stride over
+// elements): the element is read once and written once, every stage and
+// step runs in registers.  The tableaux are compile-time constants, so each
+// stage is a chain of FMAs with immediate coefficients and zero entries
+// vanish.  Adaptive elements run their own accept/reject loops; a warp
+// finishes when its slowest element does.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "common.cuh"
+#include "host_util.h"
+
+using namespace gsk;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Tableaux (Table 1).  A strictly lower triangular, row i: stage i+1.
+// ---------------------------------------------------------------------------
+struct TabEuler {
+    static constexpr int S = 1, P = 1, Q = 0;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[1] = {0.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[1][1] = {{0.0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[1] = {1.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[1] = {0.0};
+        return v[i];
+    }
+};
+struct TabRK4 {
+    static constexpr int S = 4, P = 4, Q = 0;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[4] = {0.0, 0.5, 0.5, 1.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[4][4] = {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1.0, 0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[4] = {0, 0, 0, 0};
+        return v[i];
+    }
+};
+struct TabDP5 {
+    static constexpr int S = 7, P = 5, Q = 4;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[7][7] = {
+        {0, 0, 0, 0, 0, 0, 0},
+        {dp5::A21, 0, 0, 0, 0, 0, 0},
+        {dp5::A31, dp5::A32, 0, 0, 0, 0, 0},
+        {dp5::A41, dp5::A42, dp5::A43, 0, 0, 0, 0},
+        {dp5::A51, dp5::A52, dp5::A53, dp5::A54, 0, 0, 0},
+        {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65, 0, 0},
+        {dp5::B1, 0, dp5::B3, dp5::B4, dp5::B5, dp5::B6, 0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[7] = {dp5::B1, 0, dp5::B3, dp5::B4, dp5::B5, dp5::B6, 0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[7] = {dp5::H1, 0, dp5::H3, dp5::H4, dp5::H5, dp5::H6, dp5::H7};
+        return v[i];
+    }
+};
+// Cash & Karp (1990): order-5 solution propagated, order-4 embedded.
+struct TabCK54 {
+    static constexpr int S = 6, P = 5, Q = 4;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[6] = {0.0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1.0, 7.0 / 8};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[6][6] = {{0, 0, 0, 0, 0, 0},
+                                       {1.0 / 5, 0, 0, 0, 0, 0},
+                                       {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
+                                       {3.0 / 10, -9.0 / 10, 6.0 / 5, 0, 0, 0},
+                                       {-11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27, 0, 0},
+                                       {1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592,
+                                        253.0 / 4096, 0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[6] = {37.0 / 378, 0, 250.0 / 621, 125.0 / 594, 0, 512.0 / 1771};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[6] = {2825.0 / 27648, 0, 18575.0 / 48384, 13525.0 / 55296, 277.0 / 14336,
+                                     1.0 / 4};
+        return v[i];
+    }
+};
+// Fehlberg (1968) 7(8), 13 stages; Table 1 lists it as order 8: the order-8
+// weights are propagated, the order-7 ones embedded.
+struct TabRKF78 {
+    static constexpr int S = 13, P = 8, Q = 7;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[13] = {0.0,       2.0 / 27, 1.0 / 9, 1.0 / 6, 5.0 / 12, 1.0 / 2, 5.0 / 6,
+                                     1.0 / 6,   2.0 / 3,  1.0 / 3, 1.0,     0.0,      1.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[13][13] = {
+        {0},
+        {2.0 / 27},
+        {1.0 / 36, 1.0 / 12},
+        {1.0 / 24, 0, 1.0 / 8},
+        {5.0 / 12, 0, -25.0 / 16, 25.0 / 16},
+        {1.0 / 20, 0, 0, 1.0 / 4, 1.0 / 5},
+        {-25.0 / 108, 0, 0, 125.0 / 108, -65.0 / 27, 125.0 / 54},
+        {31.0 / 300, 0, 0, 0, 61.0 / 225, -2.0 / 9, 13.0 / 900},
+        {2.0, 0, 0, -53.0 / 6, 704.0 / 45, -107.0 / 9, 67.0 / 90, 3.0},
+        {-91.0 / 108, 0, 0, 23.0 / 108, -976.0 / 135, 311.0 / 54, -19.0 / 60, 17.0 / 6, -1.0 / 12},
+        {2383.0 / 4100, 0, 0, -341.0 / 164, 4496.0 / 1025, -301.0 / 82, 2133.0 / 4100, 45.0 / 82, 45.0 / 164,
+         18.0 / 41},
+        {3.0 / 205, 0, 0, 0, 0, -6.0 / 41, -3.0 / 205, -3.0 / 41, 3.0 / 41, 6.0 / 41},
+        {-1777.0 / 4100, 0, 0, -341.0 / 164, 4496.0 / 1025, -289.0 / 82, 2193.0 / 4100, 51.0 / 82, 33.0 / 164,
+         12.0 / 41, 0, 1.0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[13] = {0, 0, 0, 0, 0, 34.0 / 105, 9.0 / 35, 9.0 / 35, 9.0 / 280, 9.0 / 280, 0,
+                                     41.0 / 840, 41.0 / 840};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[13] = {41.0 / 840, 0, 0, 0, 0, 34.0 / 105, 9.0 / 35, 9.0 / 35, 9.0 / 280,
+                                      9.0 / 280, 41.0 / 840, 0, 0};
+        return v[i];
+    }
+};
+
+// Adams-Bashforth weights beta_j of f_{m-j} with s steps (published
+// rational values: numerators over a common denominator).
+__host__ __device__ constexpr double ab_weight(int s, int j) {
+    constexpr double n1[1] = {1};
+    constexpr double n2[2] = {3, -1};
+    constexpr double n3[3] = {23, -16, 5};
+    constexpr double n4[4] = {55, -59, 37, -9};
+    constexpr double n5[5] = {1901, -2774, 2616, -1274, 251};
+    constexpr double n6[6] = {4277, -7923, 9982, -7298, 2877, -475};
+    constexpr double n7[7] = {198721, -447288, 705549, -688256, 407139, -134472, 19087};
+    constexpr double n8[8] = {434241, -1152169, 2183877, -2664477, 2102243, -1041723, 295767, -36799};
+    return s == 1 ? n1[j] : s == 2 ? n2[j] / 2 : s == 3 ? n3[j] / 12 : s == 4 ? n4[j] / 24
+         : s == 5 ? n5[j] / 720 : s == 6 ? n6[j] / 1440 : s == 7 ? n7[j] / 60480 : n8[j] / 120960;
+}
+
+// f(t, x) of each family; cf: the element's coefficient (Eq. 1a)
+template <int KIND>
+__device__ __forceinline__ double frhs(double t, double x, double cf) {
+    if (KIND == ODE_EXP_DECAY) return -x;
+    if (KIND == ODE_LOGISTIC) return x * (1.0 - x);
+    if (KIND == ODE_PAPER_EXP) return cf * exp(t);
+    const double s = 1.0 / (1.0 + exp(-t));
+    return s * (1.0 - s);
+}
+
+// One step of tableau TB: returns the propagated solution; with ERR also
+// err = h sum_i (B_i - BH_i) k_i and k1 (for the error scale).
+template <int KIND, class TB, bool ERR>
+__device__ __forceinline__ double tab_step(double u, double t, double h, double cf, double& err, double& k1) {
+    double k[TB::S];
+#pragma unroll
+    for (int i = 0; i < TB::S; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int j = 0; j < i; ++j)
+            if (TB::a(i, j) != 0.0) acc += TB::a(i, j) * k[j];
+        k[i] = frhs<KIND>(t + TB::c(i) * h, i == 0 ? u : u + h * acc, cf);
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int i = 0; i < TB::S; ++i)
+        if (TB::b(i) != 0.0) acc += TB::b(i) * k[i];
+    if (ERR) {
+        double e = 0.0;
+#pragma unroll
+        for (int i = 0; i < TB::S; ++i)
+            if (TB::b(i) - TB::bh(i) != 0.0) e += (TB::b(i) - TB::bh(i)) * k[i];
+        err = h * e;
+        k1 = k[0];
+    }
+    return u + h * acc;
+}
+
+template <int KIND, class TB>
+__global__ void __launch_bounds__(256) ode_tab_kernel(long long n, double* __restrict__ x,
+                                                      const double* __restrict__ coef, double t0, double dt,
+                                                      long long nsteps) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double u = x[i];
+        const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
+        double e, k1;
+        for (long long m = 0; m < nsteps; ++m) u = tab_step<KIND, TB, false>(u, t0 + (double)m * dt, dt, cf, e, k1);
+        x[i] = u;
+    }
+}
+
+// Adams-Bashforth with S steps: f[j] = f_{m-j} in registers.
+template <int KIND, int S>
+__global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __restrict__ x,
+                                                     const double* __restrict__ coef, double t0, double dt,
+                                                     long long nsteps) {
+    using Start = typename std::conditional<(S <= 4), TabRK4, TabRKF78>::type;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double u = x[i];
+        const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
+        double f[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) f[j] = 0.0;
+        double e, k1;
+        for (long long m = 0; m < nsteps; ++m) {
+            const double t = t0 + (double)m * dt;
+#pragma unroll
+            for (int j = S - 1; j >= 1; --j) f[j] = f[j - 1];
+            f[0] = frhs<KIND>(t, u, cf);
+            if (m < S - 1) {
+                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1);
+            } else {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc += ab_weight(S, j) * f[j];
+                u = u + dt * acc;
+            }
+        }
+        x[i] = u;
+    }
+}
+
+// Per-element error control: the controller of the adaptive drivers (reject
+// E > 1: dt = h max(0.9 E^(-1/(Q-1)), 0.2); accept, and if E < 0.5 grow dt
+// = 0.9 h max(E, 5^-P)^(-1/P); clip the last step to t_end) run by each
+// element on its own t and dt.  An element stops at t_end, after max_acc
+// accepted steps (< 0: no limit), after max_rej consecutive rejections or a
+// step that no longer advances t (STEP_UNDERFLOW), on a non-finite error
+// (NONFINITE), or after kMaxElementAttempts attempts (MAX_STEPS), which
+// bounds the kernel's run time.
+constexpr long long kMaxElementAttempts = 1LL << 22;
+
+template <int KIND, class TB>
+__global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double* __restrict__ x,
+                                                             const double* __restrict__ coef, double t0,
+                                                             double t_end, double dt0, double atol, double rtol,
+                                                             long long max_acc, long long max_rej,
+                                                             double* t_out, double* dt_out, long* na_out,
+                                                             long* nr_out, int* st_out) {
+    const double grow_floor = pow(5.0, -(double)TB::P);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double u = x[i];
+        const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
+        double t = t0, dt = dt0;
+        long long na = 0, nr = 0, consec = 0, att = 0;
+        int st = GS_OK;
+        while (t < t_end && (max_acc < 0 || na < max_acc)) {
+            if (++att > kMaxElementAttempts) {
+                st = GS_ERR_MAX_STEPS;
+                break;
+            }
+            bool last = false;
+            double h = dt;
+            if (t + dt >= t_end) {
+                h = t_end - t;
+                last = true;
+            }
+            if (!(h > 0.0) || t + h == t) {
+                st = GS_ERR_STEP_UNDERFLOW;
+                break;
+            }
+            double err, k1;
+            const double y = tab_step<KIND, TB, true>(u, t, h, cf, err, k1);
+            const double E = fabs(err) / (atol + rtol * (fabs(u) + h * fabs(k1)));
+            if (!isfinite(E)) {
+                st = GS_ERR_NONFINITE;
+                break;
+            }
+            if (E > 1.0) {
+                ++nr;
+                ++consec;
+                dt = h * fmax(0.9 * pow(E, -1.0 / (double)(TB::Q - 1)), 0.2);
+                if (consec >= max_rej) {
+                    st = GS_ERR_STEP_UNDERFLOW;
+                    break;
+                }
+                continue;
+            }
+            consec = 0;
+            u = y;
+            ++na;
+            t = last ? t_end : t + h;
+            dt = E < 0.5 ? h * 0.9 * pow(fmax(E, grow_floor), -1.0 / (double)TB::P) : h;
+        }
+        x[i] = u;
+        if (t_out) t_out[i] = t;
+        if (dt_out) dt_out[i] = dt;
+        if (na_out) na_out[i] = (long)na;
+        if (nr_out) nr_out[i] = (long)nr;
+        if (st_out) st_out[i] = st;
+    }
+}
+
+int sm_count_t() {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return nsm;
+}
+
+template <typename K>
+int grid_for(K kern, long long n) {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 256, 0);
+    if (occ < 1) occ = 1;
+    const long long need = (n + 255) / 256;
+    return (int)std::max<long long>(1, std::min<long long>(need, (long long)sm_count_t() * occ));
+}
+
+bool kind_ok(int kind, const double* coef) {
+    if (kind == ODE_PAPER_EXP) return coef != nullptr;
+    return kind == ODE_EXP_DECAY || kind == ODE_LOGISTIC || kind == ODE_PAPER_SIGMOID;
+}
+
+// dispatch over the right-hand side, then the tableau
+template <template <int, class> class Launch, class TB, typename... Args>
+cudaError_t by_kind(int kind, Args... args) {
+    switch (kind) {
+        case ODE_EXP_DECAY: return Launch<ODE_EXP_DECAY, TB>::run(args...);
+        case ODE_LOGISTIC: return Launch<ODE_LOGISTIC, TB>::run(args...);
+        case ODE_PAPER_EXP: return Launch<ODE_PAPER_EXP, TB>::run(args...);
+        default: return Launch<ODE_PAPER_SIGMOID, TB>::run(args...);
+    }
+}
+template <template <int, class> class Launch, typename... Args>
+cudaError_t by_tab(int method, int kind, Args... args) {
+    switch (method) {
+        case ODE_TAB_EULER: return by_kind<Launch, TabEuler>(kind, args...);
+        case ODE_TAB_RK4: return by_kind<Launch, TabRK4>(kind, args...);
+        case ODE_TAB_DOPRI5: return by_kind<Launch, TabDP5>(kind, args...);
+        case ODE_TAB_CK54: return by_kind<Launch, TabCK54>(kind, args...);
+        default: return by_kind<Launch, TabRKF78>(kind, args...);
+    }
+}
+
+template <int KIND, class TB>
+struct LaunchTab {
+    static cudaError_t run(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
+                           long long nsteps) {
+        auto k = ode_tab_kernel<KIND, TB>;
+        k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps);
+        return cudaGetLastError();
+    }
+};
+template <int KIND, class TB>
+struct LaunchEach {
+    static cudaError_t run(cudaStream_t s, long long n, double* x, const double* coef, double t0, double t_end,
+                           double dt0, double atol, double rtol, long long max_acc, long long max_rej,
+                           double* t_out, double* dt_out, long* na, long* nr, int* st) {
+        auto k = ode_adapt_each_kernel<KIND, TB>;
+        k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, t_end, dt0, atol, rtol, max_acc, max_rej, t_out,
+                                           dt_out, na, nr, st);
+        return cudaGetLastError();
+    }
+};
+
+template <int KIND, int S>
+cudaError_t launch_ab(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
+                      long long nsteps) {
+    auto k = ode_ab_kernel<KIND, S>;
+    k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps);
+    return cudaGetLastError();
+}
+template <int KIND>
+cudaError_t launch_ab_k(int steps, cudaStream_t s, long long n, double* x, const double* coef, double t0,
+                        double dt, long long nsteps) {
+    switch (steps) {
+        case 1: return launch_ab<KIND, 1>(s, n, x, coef, t0, dt, nsteps);
+        case 2: return launch_ab<KIND, 2>(s, n, x, coef, t0, dt, nsteps);
+        case 3: return launch_ab<KIND, 3>(s, n, x, coef, t0, dt, nsteps);
+        case 4: return launch_ab<KIND, 4>(s, n, x, coef, t0, dt, nsteps);
+        case 5: return launch_ab<KIND, 5>(s, n, x, coef, t0, dt, nsteps);
+        case 6: return launch_ab<KIND, 6>(s, n, x, coef, t0, dt, nsteps);
+        case 7: return launch_ab<KIND, 7>(s, n, x, coef, t0, dt, nsteps);
+        default: return launch_ab<KIND, 8>(s, n, x, coef, t0, dt, nsteps);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+gs_status ode_integrate_tableau(ode_rhs kind, ode_tableau method, long n, double* x, const double* coef,
+                                double t0, double dt, long nsteps, void* stream) {
+    if (!kind_ok(kind, coef) || method < ODE_TAB_EULER || method > ODE_TAB_RKF78 || n < 0 || nsteps < 0 ||
+        !std::isfinite(dt) || !std::isfinite(t0))
+        return GS_ERR_INVALID;
+    if (n > 0 && !x) return GS_ERR_INVALID;
+    if (n == 0 || nsteps == 0) return GS_OK;
+    const cudaError_t e = by_tab<LaunchTab>(method, kind, (cudaStream_t)stream, (long long)n, x, coef, t0, dt,
+                                            (long long)nsteps);
+    if (e != cudaSuccess) {
+        set_global_error(e, "ode_integrate_tableau");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status ode_integrate_ab_steps(ode_rhs kind, int steps, long n, double* x, const double* coef, double t0,
+                                 double dt, long nsteps, void* stream) {
+    if (!kind_ok(kind, coef) || steps < 1 || steps > 8 || n < 0 || nsteps < 0 || !std::isfinite(dt) ||
+        !std::isfinite(t0))
+        return GS_ERR_INVALID;
+    if (n > 0 && !x) return GS_ERR_INVALID;
+    if (n == 0 || nsteps == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    switch (kind) {
+        case ODE_EXP_DECAY: e = launch_ab_k<ODE_EXP_DECAY>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        case ODE_LOGISTIC: e = launch_ab_k<ODE_LOGISTIC>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        case ODE_PAPER_EXP: e = launch_ab_k<ODE_PAPER_EXP>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        default: e = launch_ab_k<ODE_PAPER_SIGMOID>(steps, s, n, x, coef, t0, dt, nsteps);
+    }
+    if (e != cudaSuccess) {
+        set_global_error(e, "ode_integrate_ab_steps");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status ode_integrate_adaptive_each(ode_rhs kind, ode_tableau method, long n, double* x, const double* coef,
+                                      double t0, double t_end, double dt0, double atol, double rtol,
+                                      long max_acc, long max_rej, double* t_out, double* dt_out, long* n_acc,
+                                      long* n_rej, int* status, void* stream) {
+    if (!kind_ok(kind, coef) ||
+        (method != ODE_TAB_DOPRI5 && method != ODE_TAB_CK54 && method != ODE_TAB_RKF78) || n < 0 ||
+        !std::isfinite(t0) || !std::isfinite(t_end) || !(dt0 > 0.0) || !std::isfinite(dt0) || !(atol >= 0.0) ||
+        !(rtol >= 0.0) || !(atol + rtol > 0.0) || max_rej < 1)
+        return GS_ERR_INVALID;
+    if (n > 0 && !x) return GS_ERR_INVALID;
+    if (n == 0) return GS_OK;
+    const cudaError_t e = by_tab<LaunchEach>(method, kind, (cudaStream_t)stream, (long long)n, x, coef, t0, t_end,
+                                             dt0, atol, rtol, (long long)max_acc, (long long)max_rej, t_out, dt_out,
+                                             n_acc, n_rej, status);
+    if (e != cudaSuccess) {
+        set_global_error(e, "ode_integrate_adaptive_each");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+}  // extern "C"
