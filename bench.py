@@ -252,6 +252,43 @@ def extra_workloads(torch, gs, si):
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
         out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {"ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3)}
+    # the paper's accuracy families (Eq. 1a: c = x y on a 4096 x 4096 grid of
+    # (x, y) in [0,1]^2, from the closed form at t = -5 to t = 5), Table 1's
+    # Fehlberg 7(8) and Adams-Bashforth 8 with fixed steps
+    g1 = torch.linspace(0.0, 1.0, 4096, dtype=torch.float64, device="cuda")
+    coef = torch.outer(g1, g1).reshape(-1).contiguous()
+    xe0 = coef * math.exp(-5.0)
+    for label, run, steps in (
+            ("rkf78", lambda x: gs.ode_integrate_tableau(gs.ODE_PAPER_EXP, gs.ODE_TAB_RKF78, x, -5.0, 0.1, 100,
+                                                         coef=coef), 100),
+            ("ab8", lambda x: gs.ode_integrate_ab_steps(gs.ODE_PAPER_EXP, 8, x, -5.0, 0.01, 1000, coef=coef), 1000)):
+        x = xe0.clone()
+        run(x)  # warm-up
+        x = xe0.clone()
+        a, b = ev(), ev()
+        a.record(stream)
+        run(x)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        err = float((x - coef * math.exp(5.0)).abs().max())
+        out[f"ode_2^24_fp64_{label}_paper_eq1a_t-5to5_x{steps}"] = {
+            "ms": ms, "element_steps_per_s": m * steps / (ms * 1e-3), "max_abs_error_vs_closed_form": err}
+    # every element its own step size (Dormand-Prince per element, dx/dt = -x
+    # and the logistic from the ensemble's initial values)
+    for kind, name in ((gs.ODE_EXP_DECAY, "exp_decay"), (gs.ODE_LOGISTIC, "logistic")):
+        x = x0.clone()
+        a, b = ev(), ev()
+        a.record(stream)
+        r = gs.ode_integrate_adaptive_each(kind, gs.ODE_TAB_DOPRI5, x, 0.0, 10.0, 1e-3, 1e-8, 1e-8)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        acc = int(r["n_acc"].sum())
+        out[f"ode_2^24_fp64_dopri5_per_element_{name}_tol1e-8_t10"] = {
+            "ms": ms, "accepted_total": acc, "rejected_total": int(r["n_rej"].sum()),
+            "accepted_per_element_min_max": [int(r["n_acc"].min()), int(r["n_acc"].max())],
+            "element_steps_per_s": acc / (ms * 1e-3)}
     out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
     out.update(precision_workload(torch, gs, si))
     out.update(batched_workload(torch, gs, si))
