@@ -30,6 +30,11 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
                                s - 1, the AB2/AB4 coefficients, observed
                                orders 1..8
   axpy                         pinned: exact small-integer sums
+  dcpse_stencil / gs_dcpse_*   pinned: exact Laplacian of every polynomial of
+                               degree <= 3 (not 4), second-order convergence
+                               on periodic trigonometric fields, reflection
+                               symmetry; kernel parameters are this build's
+                               reading (paper cites the method only)
   conv3d fwd/dgrad/wgrad       pinned: FP64 central differences of a scalar
                                loss, 1x1x1-equivalent reduction to a matmul
 """
@@ -100,6 +105,11 @@ def lib():
                                                      C.c_long, _dp, _dp, _lp, _lp, C.POINTER(C.c_int)]
         L.orc_ab_coefficients.argtypes = [C.c_int, _dp]
         L.orc_pair_orders.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.orc_dcpse_stencil.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int), _dp,
+                                         C.c_int]
+        L.orc_gs_dcpse_rhs_full.argtypes = [C.POINTER(_GS), C.c_double, _dp, _dp]
+        L.orc_gs_dcpse_integrate_const.argtypes = [C.POINTER(_GS), C.c_double, C.c_int, _dp, C.c_double,
+                                                   C.c_double, C.c_long]
         L.orc_axpy.argtypes = [C.c_long, C.c_int, _dp, C.POINTER(_dp), _dp]
         L.orc_conv3d_fwd.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp, _dp]
         L.orc_conv3d_dgrad.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp]
@@ -233,6 +243,33 @@ def gs_dopri5_attempt(p: GSParams, u, v, dt, atol, rtol, t=0.0):
 # Pointwise ODE families (closed-form benchmarks, Eq. 1a / 1b, and the
 # decay / logistic ensembles)
 # --------------------------------------------------------------------------
+def dcpse_stencil(h=(1.0, 1.0, 1.0), rc_over_h=3.1):
+    """DC-PSE Laplacian stencil: (offsets [m, 3] in spacings, weights [m])."""
+    cap = 4096
+    off = (C.c_int * (3 * cap))()
+    w = np.zeros(cap)
+    m = lib().orc_dcpse_stencil(h[0], h[1], h[2], rc_over_h, off, _p(w), cap)
+    if m < 0:
+        raise ValueError("DC-PSE moment system failed")
+    return np.array(off[: 3 * m], dtype=np.int64).reshape(m, 3), w[:m].copy()
+
+
+def gs_dcpse_rhs(p: GSParams, u, v, rc_over_h=3.1):
+    y = _pack(p, u, v)
+    f = np.empty_like(y)
+    if lib().orc_gs_dcpse_rhs_full(C.byref(p._c()), rc_over_h, _p(y), _p(f)) != 0:
+        raise ValueError("DC-PSE moment system failed")
+    return _unpack(p, f)
+
+
+def gs_dcpse_integrate_const(p: GSParams, u, v, method: int, dt: float, nsteps: int, t0: float = 0.0,
+                             rc_over_h=3.1):
+    y = _pack(p, u, v)
+    if lib().orc_gs_dcpse_integrate_const(C.byref(p._c()), rc_over_h, method, _p(y), t0, dt, nsteps) != 0:
+        raise ValueError("DC-PSE integration failed")
+    return _unpack(p, y)
+
+
 def pw_rhs(kind, x, t=0.0, coef=None):
     x = _f64(x)
     f = np.empty_like(x)

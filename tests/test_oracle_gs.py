@@ -154,3 +154,72 @@ def test_gs_uniform_state_reduces_to_reaction_ode():
                                      oracle.RK4, 0.01, 500)
     assert abs(u[0, 0, 0] - ref[0]) < 1e-9 and abs(v[0, 0, 0] - ref[1]) < 1e-9
     assert np.ptp(u) == 0.0 and np.ptp(v) == 0.0
+
+
+# ------------------------------------------- DC-PSE Laplacian (the paper's operator)
+def _mono_lap_at_0(e):
+    """Laplacian at the origin of x^a y^b z^c."""
+    return 2.0 if (sum(e) == 2 and max(e) == 2) else 0.0
+
+
+@pytest.mark.parametrize("h", [(1.0, 1.0, 1.0), (0.1, 0.2, 0.3), (2.5 / 64, 2.5 / 64, 2.5 / 64)])
+def test_dcpse_exact_on_cubics_not_quartics(h):
+    # the moment conditions make the stencil reproduce the Laplacian of every
+    # polynomial of degree <= 3 (r = 2, |beta| = 2), and no more
+    off, w = oracle.dcpse_stencil(h, 3.1)
+    x = off * np.asarray(h)
+    assert len(w) == 122  # integer offsets with |o| <= 3.1, o != 0
+    import itertools
+    scale = 1.0 / min(h) ** 2
+    worst4 = 0.0
+    for deg in range(0, 5):
+        for e in itertools.product(range(deg + 1), repeat=3):
+            if sum(e) != deg:
+                continue
+            vals = np.prod(x ** np.array(e), axis=1)
+            lap = float(np.sum(w * (vals - (1.0 if deg == 0 else 0.0))))
+            if deg <= 3:
+                assert abs(lap - _mono_lap_at_0(e)) < 1e-12 * scale * max(1.0, float(np.abs(w * vals).sum())), (e, lap)
+            else:
+                worst4 = max(worst4, abs(lap - _mono_lap_at_0(e)) / max(h) ** 2)
+    assert worst4 > 1e-3
+
+
+def test_dcpse_weights_symmetric():
+    off, w = oracle.dcpse_stencil((1.0, 1.0, 1.0), 3.1)
+    table = {tuple(o): wi for o, wi in zip(off.tolist(), w)}
+    for o, wi in table.items():
+        assert abs(table[(-o[0], -o[1], -o[2])] - wi) < 1e-14 * abs(wi) + 1e-18
+        assert abs(table[(o[1], o[2], o[0])] - wi) < 1e-12 * abs(wi) + 1e-16
+
+
+def test_dcpse_second_order_convergence():
+    # Du = 1, v = 0, F = k = 0: the right-hand side is the Laplacian of u;
+    # u = sin(2 pi x / L) sin(4 pi y / L) cos(2 pi z / L) has Lap u = -(24 pi^2 / L^2) u
+    errs = []
+    L = 2.5
+    for n in (16, 32):
+        p = oracle.GSParams(n, n, n, L=L, Du=1.0, Dv=0.0, F=0.0, k=0.0)
+        c = (np.arange(n) + 0.0) * (L / n)
+        Z, Y, X = np.meshgrid(c, c, c, indexing="ij")
+        u = np.sin(2 * np.pi * X / L) * np.sin(4 * np.pi * Y / L) * np.cos(2 * np.pi * Z / L)
+        fu, _ = oracle.gs_dcpse_rhs(p, u.reshape(-1), np.zeros(n ** 3))
+        exact = -(24 * np.pi ** 2 / L ** 2) * u.reshape(-1)
+        errs.append(np.max(np.abs(np.asarray(fu).reshape(-1) - exact)))
+    assert abs(np.log2(errs[0] / errs[1]) - 2.0) < 0.25, errs
+
+
+def test_dcpse_gs_fixed_point_and_reaction():
+    # the uniform state u = 1, v = 0 is a fixed point; a uniform field sees
+    # the reaction terms only (the stencil annihilates constants)
+    n = 8
+    p = oracle.GSParams(n, n, n, L=2.5, Du=2e-4, Dv=1e-4, F=0.053, k=0.014)
+    u = np.ones(n ** 3)
+    v = np.zeros(n ** 3)
+    uo, vo = oracle.gs_dcpse_integrate_const(p, u, v, oracle.RK4, 1.0, 5)
+    assert np.array_equal(np.asarray(uo).reshape(-1), u) and np.array_equal(np.asarray(vo).reshape(-1), v)
+    u = np.full(n ** 3, 0.4)
+    v = np.full(n ** 3, 0.3)
+    fu, fv = oracle.gs_dcpse_rhs(p, u, v)
+    assert np.allclose(fu, -0.4 * 0.09 + 0.053 * 0.6, rtol=1e-14, atol=1e-17)
+    assert np.allclose(fv, 0.4 * 0.09 - 0.067 * 0.3, rtol=1e-14, atol=1e-17)
