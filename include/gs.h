@@ -256,6 +256,27 @@ gs_status gs_time_stages(gs_ctx* ctx, int reps, double* ms);
  * doubles.  INVALID if the pair kernels do not apply.  Synchronises. */
 gs_status gs_time_pairs(gs_ctx* ctx, int reps, double* ms);
 
+/* Laplacian of the Gray-Scott right-hand side.  GS_LAP_7POINT (default):
+ * the 7-point central stencil of the stage kernels.  GS_LAP_DCPSE: the
+ * DC-PSE operator the paper's Gray-Scott benchmark uses (discretization-
+ * corrected particle strength exchange, cited, not specified, by the paper).
+ * This library's reading: Gaussian kernel, eps = h_d per axis, convergence
+ * order 2 (moment conditions on every monomial of degree 1..3), support all
+ * grid points within rc_over_h spacings (3.1: 122 neighbours); on the
+ * regular grid the operator is one stencil L f_p = sum_q w_q (f_{p+o_q} -
+ * f_p), whose weights gs_set_laplacian computes once (Cholesky of the
+ * moment system).  With GS_LAP_DCPSE, gs_rhs, gs_step (GS_EULER, GS_RK4,
+ * GS_DOPRI5; GS_AB4 -> INVALID) and gs_integrate_adaptive run a separate
+ * path: one tiled stage kernel per stage (8^3 cells + a halo of 3 in
+ * shared memory) and one combine kernel per step, the adaptive controller
+ * on the host with the formulas and limits of the graph path; synchronous.
+ * INVALID: unknown kind, rc_over_h outside [2, 4), a singular moment
+ * system.  gs_get_dcpse_stencil: the offsets (3 ints each, in spacings)
+ * and weights in use; capacity = 0 returns the count only. */
+typedef enum { GS_LAP_7POINT = 0, GS_LAP_DCPSE = 1 } gs_laplacian;
+gs_status gs_set_laplacian(gs_ctx* ctx, gs_laplacian kind, double rc_over_h);
+gs_status gs_get_dcpse_stencil(const gs_ctx* ctx, int* count, int* offsets, double* weights, int capacity);
+
 /* Text of the last CUDA error seen by ctx ("" if none). */
 const char* gs_last_error(const gs_ctx* ctx);
 /* Text of the last CUDA error seen by a context-free entry point. */

@@ -110,6 +110,9 @@ def lib():
         L.orc_gs_dcpse_rhs_full.argtypes = [C.POINTER(_GS), C.c_double, _dp, _dp]
         L.orc_gs_dcpse_integrate_const.argtypes = [C.POINTER(_GS), C.c_double, C.c_int, _dp, C.c_double,
                                                    C.c_double, C.c_long]
+        L.orc_gs_dcpse_integrate_adaptive.argtypes = [C.POINTER(_GS), C.c_double, _dp, _dp, C.c_double, _dp,
+                                                      C.c_double, C.c_double, C.c_long, C.c_long,
+                                                      C.POINTER(C.c_long), C.POINTER(C.c_long), _dp, C.c_long]
         L.orc_axpy.argtypes = [C.c_long, C.c_int, _dp, C.POINTER(_dp), _dp]
         L.orc_conv3d_fwd.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp, _dp]
         L.orc_conv3d_dgrad.argtypes = [C.c_int] * 5 + [_dp, _dp, _dp]
@@ -268,6 +271,21 @@ def gs_dcpse_integrate_const(p: GSParams, u, v, method: int, dt: float, nsteps: 
     if lib().orc_gs_dcpse_integrate_const(C.byref(p._c()), rc_over_h, method, _p(y), t0, dt, nsteps) != 0:
         raise ValueError("DC-PSE integration failed")
     return _unpack(p, y)
+
+
+def gs_dcpse_integrate_adaptive(p: GSParams, u, v, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500,
+                                rc_over_h=3.1, log_cap=0):
+    y = _pack(p, u, v)
+    t = C.c_double(t0)
+    dt = C.c_double(dt0)
+    na, nr = C.c_long(0), C.c_long(0)
+    log = np.zeros(max(log_cap, 1))
+    st = lib().orc_gs_dcpse_integrate_adaptive(C.byref(p._c()), rc_over_h, _p(y), C.byref(t), t_end, C.byref(dt),
+                                               atol, rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
+                                               _p(log) if log_cap else None, log_cap)
+    u2, v2 = _unpack(p, y)
+    return {"u": u2, "v": v2, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
+            "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
 
 
 def pw_rhs(kind, x, t=0.0, coef=None):

@@ -73,6 +73,8 @@ _SIGNATURES = {
     "gs_set_pair_config": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
     "gs_get_pair_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
+    "gs_set_laplacian": ([_vp, C.c_int, C.c_double], C.c_int),
+    "gs_get_dcpse_stencil": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, C.c_int], C.c_int),
     "gs_get_pair_depths_in_use": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
@@ -305,6 +307,24 @@ def gs_get_pair_depths_in_use(ctx):
     d = (C.c_int * 5)()
     _check(lib().gs_get_pair_depths_in_use(ctx, d), ctx)
     return list(d)
+
+
+GS_LAP_7POINT, GS_LAP_DCPSE = 0, 1
+
+
+def gs_set_laplacian(ctx, kind, rc_over_h=3.1):
+    _check(lib().gs_set_laplacian(ctx, kind, rc_over_h), ctx)
+
+
+def gs_get_dcpse_stencil(ctx):
+    """(offsets [m, 3] in spacings, weights [m]) of the DC-PSE stencil in use."""
+    import numpy as np
+    m = C.c_int(0)
+    _check(lib().gs_get_dcpse_stencil(ctx, C.byref(m), None, None, 0), ctx)
+    off = (C.c_int * (3 * m.value))()
+    w = np.zeros(m.value)
+    _check(lib().gs_get_dcpse_stencil(ctx, C.byref(m), off, w.ctypes.data_as(_dp), m.value), ctx)
+    return np.array(off[:], dtype=np.int64).reshape(-1, 3), w
 
 
 def gs_time_pairs(ctx, reps=5):

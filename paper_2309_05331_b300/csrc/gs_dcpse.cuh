@@ -1,0 +1,130 @@
+// gs_dcpse.cuh -- Gray-Scott with the DC-PSE Laplacian (the operator of the
+// paper's Gray-Scott benchmark, which cites the discretization-corrected
+// particle strength exchange of Schrader et al.) on the regular grid.
+//
+// On a regular grid every cell has the same neighbourhood, so the DC-PSE
+// Laplacian is one stencil: L f_p = sum_q w_q (f_{p+o_q} - f_p) over the
+// integer offsets o_q with |o_q| <= r_c (122 of them at r_c = 3.1 spacings).
+// The host solves the moment system for the weights once per context
+// (gs_grid.cu); they travel as a kernel parameter (constant bank, broadcast
+// to every thread).
+//
+// dcpse_stage_kernel: one stage k = F(Y), Y = u + dt sum_j a_j k_j, on a
+// tile of 8 x 8 x 8 cells: the CTA forms Y on the tile plus a halo of R = 3
+// cells (14^3 values per component) in shared memory, then each thread sums
+// its cell's stencil from there.  dcpse_combine_kernel: u' = u + dt sum_j
+// b_j k_j and, for an error-controlled attempt, the maximum over cells of
+// |dt sum_j e_j k_j| / (atol + rtol (|u| + dt |k1|)).
+#pragma once
+
+#include "gs_tile.cuh"
+
+namespace gsk {
+
+constexpr int kDcpseMax = 256;  // stencil entries (r_c < 4 spacings)
+constexpr int kDcpseR = 3;      // halo of the tile (r_c < 4)
+constexpr int kDcpseT = 8;      // tile edge
+constexpr int kDcpseE = kDcpseT + 2 * kDcpseR;
+constexpr int kDcpseMaxNK = 6;  // stage inputs (Dormand-Prince stage 7 reads k1..k6)
+
+template <typename T>
+struct DcpseStencil {
+    int count;
+    signed char off[kDcpseMax][3];
+    T w[kDcpseMax];
+};
+
+template <typename T>
+struct DcpseStageArgs {
+    const T* u[2];
+    const T* k[kDcpseMaxNK][2];
+    double a[kDcpseMaxNK];
+    int nk;
+    double dt;
+    T* out[2];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(512) dcpse_stage_kernel(const Geom<T> g, const DcpseStencil<T> S,
+                                                          const DcpseStageArgs<T> A) {
+    __shared__ T Ys[2][kDcpseE][kDcpseE][kDcpseE];
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    const int tilesx = (nx + kDcpseT - 1) / kDcpseT, tilesy = (ny + kDcpseT - 1) / kDcpseT;
+    const int bx = blockIdx.x % tilesx, by = (blockIdx.x / tilesx) % tilesy, bz = blockIdx.x / (tilesx * tilesy);
+    const int x0 = bx * kDcpseT, y0 = by * kDcpseT, z0 = bz * kDcpseT;
+    const int tid = threadIdx.x;
+    const T dt = (T)A.dt;
+    // Y on the tile and its halo (periodic)
+    for (int e = tid; e < kDcpseE * kDcpseE * kDcpseE; e += blockDim.x) {
+        const int ex = e % kDcpseE, ey = (e / kDcpseE) % kDcpseE, ez = e / (kDcpseE * kDcpseE);
+        int x = x0 + ex - kDcpseR, y = y0 + ey - kDcpseR, z = z0 + ez - kDcpseR;
+        x = ((x % nx) + nx) % nx;
+        y = ((y % ny) + ny) % ny;
+        z = ((z % nz) + nz) % nz;
+        const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            T s = T(0);
+            for (int j = 0; j < A.nk; ++j) s = (j == 0) ? (T)A.a[0] * A.k[0][c][i] : s + (T)A.a[j] * A.k[j][c][i];
+            Ys[c][ez][ey][ex] = A.nk > 0 ? A.u[c][i] + dt * s : A.u[c][i];
+        }
+    }
+    __syncthreads();
+    const int lx = tid % kDcpseT, ly = (tid / kDcpseT) % kDcpseT, lz = tid / (kDcpseT * kDcpseT);
+    const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
+    if (x >= nx || y >= ny || z >= nz) return;
+    const int cx = lx + kDcpseR, cy = ly + kDcpseR, cz = lz + kDcpseR;
+    const T yu = Ys[0][cz][cy][cx], yv = Ys[1][cz][cy][cx];
+    T lu = T(0), lv = T(0);
+    for (int q = 0; q < S.count; ++q) {
+        const int ox = S.off[q][0], oy = S.off[q][1], oz = S.off[q][2];
+        lu += S.w[q] * (Ys[0][cz + oz][cy + oy][cx + ox] - yu);
+        lv += S.w[q] * (Ys[1][cz + oz][cy + oy][cx + ox] - yv);
+    }
+    const T uvv = yu * yv * yv;
+    const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+    A.out[0][i] = g.Du * lu - uvv + g.F * (T(1) - yu);
+    A.out[1][i] = g.Dv * lv + uvv - (g.F + g.k) * yv;
+}
+
+template <typename T>
+struct DcpseCombineArgs {
+    const T* u[2];
+    const T* k[7][2];
+    double b[7];
+    double e[7];  // error weights (if emax != nullptr)
+    int nk;
+    double dt, atol, rtol;
+    T* out[2];
+    unsigned long long* emax;  // bits of the maximum scaled error (NaN sorts high)
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) dcpse_combine_kernel(long long n, const DcpseCombineArgs<T> A) {
+    __shared__ double red[32];
+    double emax = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const double u = (double)A.u[c][i];
+            double s = 0.0, e = 0.0;
+            for (int j = 0; j < A.nk; ++j) {
+                const double kj = (double)A.k[j][c][i];
+                s += A.b[j] * kj;
+                e += A.e[j] * kj;
+            }
+            A.out[c][i] = (T)(u + A.dt * s);
+            if (A.emax) {
+                const double sc = A.atol + A.rtol * (fabs(u) + A.dt * fabs((double)A.k[0][c][i]));
+                emax = nanmax(emax, fabs(A.dt * e) / sc);
+            }
+        }
+    }
+    if (A.emax) {
+        const double bmax = block_nanmax(emax, red);
+        if (threadIdx.x == 0) atomic_max_nonneg(A.emax, bmax);
+    }
+}
+
+}  // namespace gsk

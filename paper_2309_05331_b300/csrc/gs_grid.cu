@@ -19,9 +19,11 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 #include "gs_tile.cuh"
+#include "gs_dcpse.cuh"
 #include "gs_pair.cuh"
 #include "gs_persist.cuh"
 #include "gs_staged.cuh"
@@ -79,6 +81,12 @@ struct gs_ctx {
     int small_mode = -1;    // fixed-step RK4 in one cooperative launch: -1 automatic (small grids), 0 off, 1 on
     int small_ctas = 0;     // its CTA count (0: automatic)
     unsigned* pbar = nullptr;  // its grid barrier: u64 count, generation, error
+    int lap = 0;               // Laplacian: 0 the 7-point stencil, 1 DC-PSE (gs_set_laplacian)
+    double dcpse_rc = 0.0;
+    int dcpse_count = 0;
+    int dcpse_off[kDcpseMax][3] = {};
+    double dcpse_w[kDcpseMax] = {};
+    unsigned long long* demax = nullptr;  // DC-PSE attempts: bits of the scaled error maximum
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -630,6 +638,299 @@ static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned lon
     }
 }
 
+// ---------------------------------------------------------------------------
+// DC-PSE Laplacian (gs_dcpse.cuh): stencil from the moment conditions, and a
+// host-driven stepping path (one stage kernel per stage, one combine kernel
+// per step or attempt).
+// ---------------------------------------------------------------------------
+// Weights of L f_p = sum_q w_q (f_{p+o_q} - f_p): for each axis d the kernel
+// eta_d(z) = sum_g a_g z^g exp(-|z|^2) (z = -o_q, eps = h_d) with moments
+// sum_q z_q^alpha eta_d(z_q) = 2 for alpha = 2 e_d and 0 for every other
+// monomial of degree 1..3; the Gram system G a = m is symmetric positive
+// definite and solved by Cholesky; w_q = sum_d eta_d(z_q) / h_d^2.
+static bool dcpse_build(const double h[3], double rc, int off[][3], double* w, int* count) {
+    int mono[19][3];
+    int nm = 0;
+    for (int deg = 1; deg <= 3; ++deg)
+        for (int i = 0; i <= deg; ++i)
+            for (int j = 0; i + j <= deg; ++j) {
+                mono[nm][0] = i;
+                mono[nm][1] = j;
+                mono[nm][2] = deg - i - j;
+                ++nm;
+            }
+    const int R = (int)std::floor(rc);
+    int m = 0;
+    for (int k = -R; k <= R; ++k)
+        for (int j = -R; j <= R; ++j)
+            for (int i = -R; i <= R; ++i) {
+                if ((i | j | k) == 0 || (double)(i * i + j * j + k * k) > rc * rc) continue;
+                if (m >= kDcpseMax) return false;
+                off[m][0] = i;
+                off[m][1] = j;
+                off[m][2] = k;
+                w[m] = 0.0;
+                ++m;
+            }
+    if (m < nm) return false;
+    auto monov = [&](const double z[3], int g) {
+        double r = 1.0;
+        for (int d = 0; d < 3; ++d)
+            for (int e = 0; e < mono[g][d]; ++e) r *= z[d];
+        return r;
+    };
+    for (int d = 0; d < 3; ++d) {
+        double G[19][19] = {}, rhs[19];
+        for (int g = 0; g < nm; ++g) rhs[g] = (mono[g][d] == 2 && mono[g][0] + mono[g][1] + mono[g][2] == 2) ? 2.0 : 0.0;
+        for (int q = 0; q < m; ++q) {
+            const double z[3] = {-(double)off[q][0], -(double)off[q][1], -(double)off[q][2]};
+            const double ex = std::exp(-(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]));
+            double ph[19];
+            for (int g = 0; g < nm; ++g) ph[g] = monov(z, g);
+            for (int a = 0; a < nm; ++a)
+                for (int b = 0; b <= a; ++b) G[a][b] += ex * ph[a] * ph[b];
+        }
+        // Cholesky G = L L^T (lower triangle in place), then L y = rhs, L^T x = y
+        for (int c = 0; c < nm; ++c) {
+            double dsum = G[c][c];
+            for (int k = 0; k < c; ++k) dsum -= G[c][k] * G[c][k];
+            if (!(dsum > 0.0)) return false;
+            G[c][c] = std::sqrt(dsum);
+            for (int r = c + 1; r < nm; ++r) {
+                double v = G[r][c];
+                for (int k = 0; k < c; ++k) v -= G[r][k] * G[c][k];
+                G[r][c] = v / G[c][c];
+            }
+        }
+        double yv[19], coef[19];
+        for (int r = 0; r < nm; ++r) {
+            double v = rhs[r];
+            for (int k = 0; k < r; ++k) v -= G[r][k] * yv[k];
+            yv[r] = v / G[r][r];
+        }
+        for (int r = nm - 1; r >= 0; --r) {
+            double v = yv[r];
+            for (int k = r + 1; k < nm; ++k) v -= G[k][r] * coef[k];
+            coef[r] = v / G[r][r];
+        }
+        for (int q = 0; q < m; ++q) {
+            const double z[3] = {-(double)off[q][0], -(double)off[q][1], -(double)off[q][2]};
+            const double ex = std::exp(-(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]));
+            double eta = 0.0;
+            for (int g = 0; g < nm; ++g) eta += coef[g] * monov(z, g);
+            w[q] += eta * ex / (h[d] * h[d]);
+        }
+    }
+    *count = m;
+    return true;
+}
+
+template <typename T>
+static DcpseStencil<T> dcpse_stencil(const gs_ctx* ctx) {
+    DcpseStencil<T> S;
+    memset(&S, 0, sizeof(S));
+    S.count = ctx->dcpse_count;
+    for (int q = 0; q < S.count; ++q) {
+        for (int d = 0; d < 3; ++d) S.off[q][d] = (signed char)ctx->dcpse_off[q][d];
+        S.w[q] = (T)ctx->dcpse_w[q];
+    }
+    return S;
+}
+
+// k_out = F(u + dt sum_j a_j k_j) with the DC-PSE Laplacian
+template <typename T>
+static cudaError_t dcpse_stage(gs_ctx* ctx, void* const u[2], void* const* const kin[2], const double* a, int nk,
+                               double dt, void* const out[2]) {
+    DcpseStageArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    for (int c = 0; c < 2; ++c) {
+        A.u[c] = (const T*)u[c];
+        A.out[c] = (T*)out[c];
+        for (int j = 0; j < nk; ++j) A.k[j][c] = (const T*)kin[c][j];
+    }
+    for (int j = 0; j < nk; ++j) A.a[j] = a[j];
+    A.nk = nk;
+    A.dt = dt;
+    const Geom<T> g = make_geom<T>(ctx->p);
+    const int tiles = ((ctx->p.nx + kDcpseT - 1) / kDcpseT) * ((ctx->p.ny + kDcpseT - 1) / kDcpseT) *
+                      ((ctx->p.nz + kDcpseT - 1) / kDcpseT);
+    dcpse_stage_kernel<T><<<tiles, kDcpseT * kDcpseT * kDcpseT, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
+    return cudaGetLastError();
+}
+
+// out = u + dt sum_j b_j k_j; with emax, the attempt's scaled error maximum
+template <typename T>
+static cudaError_t dcpse_combine(gs_ctx* ctx, void* const u[2], int nk, const double* b, const double* e, double dt,
+                                 double atol, double rtol, void* const out[2], bool err) {
+    DcpseCombineArgs<T> A;
+    memset(&A, 0, sizeof(A));
+    for (int c = 0; c < 2; ++c) {
+        A.u[c] = (const T*)u[c];
+        A.out[c] = (T*)out[c];
+        for (int j = 0; j < nk; ++j) A.k[j][c] = (const T*)ctx->field[1 + j][c];
+    }
+    for (int j = 0; j < nk; ++j) {
+        A.b[j] = b[j];
+        A.e[j] = e ? e[j] : 0.0;
+    }
+    A.nk = nk;
+    A.dt = dt;
+    A.atol = atol;
+    A.rtol = rtol;
+    A.emax = err ? ctx->demax : nullptr;
+    const int blocks = (int)std::min<long long>((ctx->N + 255) / 256, (long long)ctx->nsm * 8);
+    dcpse_combine_kernel<T><<<blocks, 256, 0, ctx->stream>>>(ctx->N, A);
+    return cudaGetLastError();
+}
+
+// Butcher rows of the DC-PSE path: Euler, RK4, Dormand-Prince (7 stages)
+struct HostTab {
+    int s;
+    double a[7][7];
+    double b[7];
+    double e[7];
+};
+static HostTab host_tab(gs_method m) {
+    HostTab T;
+    memset(&T, 0, sizeof(T));
+    if (m == GS_EULER) {
+        T.s = 1;
+        T.b[0] = 1.0;
+    } else if (m == GS_RK4) {
+        T.s = 4;
+        T.a[1][0] = 0.5;
+        T.a[2][1] = 0.5;
+        T.a[3][2] = 1.0;
+        T.b[0] = 1.0 / 6.0;
+        T.b[1] = 1.0 / 3.0;
+        T.b[2] = 1.0 / 3.0;
+        T.b[3] = 1.0 / 6.0;
+    } else {
+        using namespace dp5;
+        T.s = 7;
+        const double A[7][7] = {{0}, {A21}, {A31, A32}, {A41, A42, A43}, {A51, A52, A53, A54},
+                                {A61, A62, A63, A64, A65}, {B1, 0, B3, B4, B5, B6}};
+        memcpy(T.a, A, sizeof(A));
+        const double b[7] = {B1, 0, B3, B4, B5, B6, 0};
+        const double e[7] = {E1, 0, E3, E4, E5, E6, E7};
+        memcpy(T.b, b, sizeof(b));
+        memcpy(T.e, e, sizeof(e));
+    }
+    return T;
+}
+
+// the stages of one step / attempt from state u into fields 1..s
+template <typename T>
+static cudaError_t dcpse_stages(gs_ctx* ctx, const HostTab& tab, int s_used, void* const u[2], double dt) {
+    for (int i = 0; i < s_used; ++i) {
+        void* kin0[kDcpseMaxNK];
+        void* kin1[kDcpseMaxNK];
+        double a[kDcpseMaxNK];
+        int nk = 0;
+        for (int j = 0; j < i; ++j) {
+            kin0[nk] = ctx->field[1 + j][0];
+            kin1[nk] = ctx->field[1 + j][1];
+            a[nk] = tab.a[i][j];
+            ++nk;
+        }
+        void* const* const kin[2] = {kin0, kin1};
+        void* const out[2] = {ctx->field[1 + i][0], ctx->field[1 + i][1]};
+        const cudaError_t e = dcpse_stage<T>(ctx, u, kin, a, nk, dt, out);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+static gs_status dcpse_step(gs_ctx* ctx, gs_method method, double t0, double dt, long nsteps) {
+    const HostTab tab = host_tab(method);
+    // Dormand-Prince with fixed steps: stage 7 does not enter the solution
+    const int s_used = method == GS_DOPRI5 ? 6 : tab.s;
+    void* const u[2] = {ctx->state[0], ctx->state[1]};
+    (void)t0;  // autonomous right-hand side
+    for (long m = 0; m < nsteps; ++m) {
+        CK(dcpse_stages<T>(ctx, tab, s_used, u, dt));
+        CK(dcpse_combine<T>(ctx, u, s_used, tab.b, nullptr, dt, 0.0, 0.0, u, false));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
+// error-controlled Dormand-Prince on the DC-PSE path: the device computes the
+// attempt and its error maximum, the host runs the controller of the graph
+// path (same formulas and limits)
+template <typename T>
+static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t_io, double t_end, double* dt_io,
+                                long max_acc, long* n_acc_out, long* n_rej_out) {
+    const HostTab tab = host_tab(GS_DOPRI5);
+    void* const u[2] = {ctx->state[0], ctx->state[1]};
+    void* const ynew[2] = {ctx->field[0][0], ctx->field[0][1]};
+    const size_t bytes = ctx->esz * (size_t)ctx->N;
+    double t = *t_io, dt = *dt_io;
+    long long n_acc = 0, n_rej = 0, consec = 0, att = 0;
+    gs_status status = GS_OK;
+    std::vector<double> log;
+    while (t < t_end && (max_acc < 0 || n_acc < max_acc)) {
+        if (att >= kMaxAttempts) {
+            status = GS_ERR_MAX_STEPS;
+            break;
+        }
+        bool last = false;
+        double h = dt;
+        if (t + dt >= t_end) {
+            h = t_end - t;
+            last = true;
+        }
+        if (!(h > 0.0) || t + h == t) {
+            status = GS_ERR_STEP_UNDERFLOW;
+            break;
+        }
+        ++att;
+        CK(cudaMemsetAsync(ctx->demax, 0, sizeof(unsigned long long), ctx->stream));
+        CK(dcpse_stages<T>(ctx, tab, 7, u, h));
+        CK(dcpse_combine<T>(ctx, u, 7, tab.b, tab.e, h, atol, rtol, ynew, true));
+        unsigned long long bits = 0;
+        CK(cudaMemcpyAsync(&bits, ctx->demax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        double E;
+        memcpy(&E, &bits, sizeof(E));
+        if (!std::isfinite(E)) {
+            status = GS_ERR_NONFINITE;
+            break;
+        }
+        if (E > 1.0) {
+            ++n_rej;
+            ++consec;
+            dt = h * std::max(0.9 * std::pow(E, -1.0 / 3.0), 0.2);
+            if (consec >= kMaxConsecutiveRejects) {
+                status = GS_ERR_STEP_UNDERFLOW;
+                break;
+            }
+            continue;
+        }
+        consec = 0;
+        for (int c = 0; c < 2; ++c)
+            CK(cudaMemcpyAsync(u[c], ynew[c], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        log.push_back(h);
+        ++n_acc;
+        t = last ? t_end : t + h;
+        dt = E < 0.5 ? h * 0.9 * std::pow(std::max(E, 1.0 / 3125.0), -1.0 / 5.0) : h;
+    }
+    // step log and counters where gs_get_step_log finds them
+    const long nlog = (long)std::min<size_t>(log.size(), (size_t)ctx->log_cap);
+    if (nlog > 0)
+        CK(cudaMemcpyAsync(ctx->dlog, log.data(), sizeof(double) * (size_t)nlog, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    memset(ctx->hctrl, 0, sizeof(DevCtrl));
+    ctx->hctrl->n_acc = n_acc;
+    ctx->hctrl->n_rej = n_rej;
+    *t_io = t;
+    *dt_io = dt;
+    if (n_acc_out) *n_acc_out = (long)n_acc;
+    if (n_rej_out) *n_rej_out = (long)n_rej;
+    return status;
+}
+
 static void drop_graphs(gs_ctx* ctx) {
     for (int i = 0; i < G_COUNT; ++i) {
         if (ctx->exec[i]) cudaGraphExecDestroy(ctx->exec[i]);
@@ -841,6 +1142,7 @@ gs_status gs_destroy(gs_ctx* ctx) {
     if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
     if (ctx->hpatch) cudaFreeHost(ctx->hpatch);
     if (ctx->dlog) cudaFree(ctx->dlog);
+    if (ctx->demax) cudaFree(ctx->demax);
     delete ctx;
     return GS_OK;
 }
@@ -879,7 +1181,46 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, 
     A.ctrl = nullptr;
     A.u = slot_fixed(const_cast<void*>(u), const_cast<void*>(v));
     A.out0 = slot_fixed(fu, fv);
+    if (ctx->lap == 1) {
+        void* const uu[2] = {const_cast<void*>(u), const_cast<void*>(v)};
+        void* const out[2] = {fu, fv};
+        void* const* const kin[2] = {nullptr, nullptr};
+        CK(ctx->p.prec == GS_FP64 ? dcpse_stage<double>(ctx, uu, kin, nullptr, 0, 0.0, out)
+                                  : dcpse_stage<float>(ctx, uu, kin, nullptr, 0, 0.0, out));
+        return GS_OK;
+    }
     CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A, ctx->def));
+    return GS_OK;
+}
+
+gs_status gs_set_laplacian(gs_ctx* ctx, gs_laplacian kind, double rc_over_h) {
+    if (!ctx) return GS_ERR_INVALID;
+    if (kind == GS_LAP_7POINT) {
+        drop_graphs(ctx);
+        ctx->lap = 0;
+        return GS_OK;
+    }
+    if (kind != GS_LAP_DCPSE || !(rc_over_h >= 2.0) || !(rc_over_h < 4.0)) return GS_ERR_INVALID;
+    const double h[3] = {ctx->p.Lx / ctx->p.nx, ctx->p.Ly / ctx->p.ny, ctx->p.Lz / ctx->p.nz};
+    int count = 0;
+    if (!dcpse_build(h, rc_over_h, ctx->dcpse_off, ctx->dcpse_w, &count)) return GS_ERR_INVALID;
+    if (!ctx->demax) CK(cudaMalloc(&ctx->demax, sizeof(unsigned long long)));
+    drop_graphs(ctx);
+    ctx->dcpse_count = count;
+    ctx->dcpse_rc = rc_over_h;
+    ctx->lap = 1;
+    return GS_OK;
+}
+
+gs_status gs_get_dcpse_stencil(const gs_ctx* ctx, int* count, int* offsets, double* weights, int capacity) {
+    if (!ctx || !count || ctx->lap != 1) return GS_ERR_INVALID;
+    *count = ctx->dcpse_count;
+    if (capacity < ctx->dcpse_count) return capacity == 0 ? GS_OK : GS_ERR_INVALID;
+    if (!offsets || !weights) return GS_ERR_INVALID;
+    for (int q = 0; q < ctx->dcpse_count; ++q) {
+        for (int d = 0; d < 3; ++d) offsets[3 * q + d] = ctx->dcpse_off[q][d];
+        weights[q] = ctx->dcpse_w[q];
+    }
     return GS_OK;
 }
 
@@ -896,9 +1237,17 @@ gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nste
     if (!ctx || !t || !ctx->state[0] || nsteps < 0 || !std::isfinite(dt)) return GS_ERR_INVALID;
     if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER)
         return GS_ERR_INVALID;
+    if (ctx->lap == 1 && method == GS_AB4) return GS_ERR_INVALID;
     if (nsteps == 0) return GS_OK;
     const double t0 = *t;
     gs_status st;
+    if (ctx->lap == 1) {
+        st = ctx->p.prec == GS_FP64 ? dcpse_step<double>(ctx, method, t0, dt, nsteps)
+                                    : dcpse_step<float>(ctx, method, t0, dt, nsteps);
+        if (st != GS_OK) return st;
+        *t = t0 + (double)nsteps * dt;
+        return GS_OK;
+    }
     cudaGraphExec_t ex;
     if (method == GS_RK4 && small_path(ctx)) {
         st = ctx->p.prec == GS_FP64 ? rk4_persistent<double>(ctx, dt, nsteps) : rk4_persistent<float>(ctx, dt, nsteps);
@@ -946,6 +1295,10 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     if (n_accepted) *n_accepted = 0;
     if (n_rejected) *n_rejected = 0;
     if (!(*t < t_end) || max_accepted == 0) return GS_OK;
+    if (ctx->lap == 1)
+        return ctx->p.prec == GS_FP64
+                   ? dcpse_adaptive<double>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected)
+                   : dcpse_adaptive<float>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
     DevCtrl* h = ctx->hctrl;
     memset(h, 0, sizeof(DevCtrl));
     h->mode = CTRL_ADAPTIVE;

@@ -547,3 +547,102 @@ def test_full_size_256cubed_adaptive_properties():
     assert r["t"] == pytest.approx(float(np.sum(dts)), rel=1e-14)
     assert bool(torch.isfinite(g.u).all()) and bool(torch.isfinite(g.v).all())
     g.close()
+
+
+# ------------------------------------------------------------ DC-PSE Laplacian
+PAPER_GS = dict(Du=2e-4, Dv=1e-4, F=0.053, k=0.014)  # the paper's constants
+
+
+def test_dcpse_stencil_matches_oracle():
+    """The library's weights (Cholesky of the moment system) against the
+    oracle's (Gaussian elimination), isotropic and anisotropic grids."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    for dims, L in (((64, 64, 64), (2.5, 2.5, 2.5)), ((20, 12, 9), (2.5, 1.5, 3.0))):
+        g = gs.GrayScott(*dims, L=L[0], Ly=L[1], Lz=L[2], prec=gs.GS_FP64, **PAPER_GS)
+        gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+        off, w = gs.gs_get_dcpse_stencil(g.ctx)
+        h = (L[0] / dims[0], L[1] / dims[1], L[2] / dims[2])
+        ooff, ow = oracle.dcpse_stencil(h, 3.1)
+        mine = {tuple(o): x for o, x in zip(off.tolist(), w)}
+        ref = {tuple(o): x for o, x in zip(ooff.tolist(), ow)}
+        assert mine.keys() == ref.keys() and len(mine) == 122
+        scale = max(abs(x) for x in ref.values())
+        assert max(abs(mine[k] - ref[k]) for k in ref) < 1e-11 * scale
+        g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims", [(16, 12, 20), (9, 8, 7), (4, 4, 4), (64, 64, 64)])
+def test_dcpse_rhs_matches_oracle(prec, dims):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    u0, v0 = si.gs_initial_state(*dims, seed=61)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, dims, prec, u0, v0, **PAPER_GS)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    fu, fv = g.rhs()
+    ou, ov = oracle.gs_dcpse_rhs(oracle.GSParams(*dims, **PAPER_GS), u0, v0)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    assert oracle.rel_l2([to_np(fu), to_np(fv)], [ou, ov]) < tol
+    g.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("method,omethod", [("euler", oracle.EULER), ("rk4", oracle.RK4), ("dopri5", oracle.DOPRI5)])
+def test_dcpse_fixed_steps_match_oracle(prec, method, omethod):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (16, 12, 10)
+    u0, v0 = si.gs_initial_state(*dims, seed=62)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, dims, prec, u0, v0, **PAPER_GS)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    m = {"euler": gs.GS_EULER, "rk4": gs.GS_RK4, "dopri5": gs.GS_DOPRI5}[method]
+    t = g.step(m, 0.0, 1.0, 4)
+    assert t == 4.0
+    ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, omethod, 1.0, 4)
+    tol = FP64_TOL if prec == 0 else FP32_TOL
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < tol
+    with pytest.raises(RuntimeError):
+        g.step(gs.GS_AB4, 0.0, 1.0, 4)
+    g.close()
+
+
+def test_dcpse_adaptive_fp64_matches_oracle_run():
+    """Error-controlled Dopri5 with the DC-PSE Laplacian (host controller):
+    same accepted / rejected counts and step sizes as the oracle's run."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (16, 16, 16)
+    u0, v0 = si.gs_initial_state(*dims, seed=2)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **PAPER_GS)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    gs.gs_set_step_log(g.ctx, 1000)
+    r = g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 1.0)
+    dts, cnt = gs.gs_get_step_log(g.ctx, 1000)
+    ref = oracle.gs_dcpse_integrate_adaptive(oracle.GSParams(*dims, **PAPER_GS), u0, v0, 0.0, 20.0, 1.0, 1e-8, 1e-8,
+                                             log_cap=1000)
+    assert r["status"] == 0 and ref["status"] == 0 and r["t"] == 20.0
+    assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"]) and cnt == r["n_acc"]
+    assert np.allclose(dts, ref["dts"], rtol=1e-7, atol=0)
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]]) < FP64_TOL
+    g.close()
+
+
+def test_dcpse_paper_workload_64cubed_rk4():
+    """The paper's Gray-Scott run: 64^3 on [0,2.5]^3, d1 = 2e-4, d2 = 1e-4,
+    F = 0.053, K = 0.014, DC-PSE Laplacian, RK4 with dt = 1 to t_f = 20, FP64:
+    against the oracle, and the 7-point path differs (the operators differ)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (64, 64, 64)
+    u0, v0 = si.gs_initial_state(*dims, seed=2)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **PAPER_GS)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    g.step(gs.GS_RK4, 0.0, 1.0, 20)
+    ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, oracle.RK4, 1.0, 20)
+    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    g.close()
