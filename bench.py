@@ -289,6 +289,30 @@ def extra_workloads(torch, gs, si):
             "ms": ms, "accepted_total": acc, "rejected_total": int(r["n_rej"].sum()),
             "accepted_per_element_min_max": [int(r["n_acc"].min()), int(r["n_acc"].max())],
             "element_steps_per_s": acc / (ms * 1e-3)}
+    # the paper's own Gray-Scott run: 64^3 on [0,2.5]^3, d1 = 2e-4, d2 = 1e-4,
+    # F = 0.053, K = 0.014, DC-PSE Laplacian (122-point stencil), dt = 1 to
+    # t_f = 20, FP64: RK4 and Dormand-Prince with fixed steps, and adaptive
+    # Dormand-Prince (tolerance 1e-8)
+    n64 = 64
+    u64, v64 = si.gs_initial_state(n64, n64, n64, seed=2)
+    g = gs.GrayScott(n64, n64, n64, Du=2e-4, Dv=1e-4, F=0.053, k=0.014, prec=gs.GS_FP64)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    for label, run in (("rk4_dt1_t20", lambda: g.step(gs.GS_RK4, 0.0, 1.0, 20)),
+                       ("dopri5_dt1_t20", lambda: g.step(gs.GS_DOPRI5, 0.0, 1.0, 20)),
+                       ("dopri5_adaptive_tol1e-8_t20", lambda: g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 1.0))):
+        g.set_state(torch.from_numpy(u64), torch.from_numpy(v64))
+        run()  # warm-up
+        g.set_state(torch.from_numpy(u64), torch.from_numpy(v64))
+        torch.cuda.synchronize()
+        t_0 = time.perf_counter()
+        r = run()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t_0) * 1e3
+        steps = r["n_acc"] if isinstance(r, dict) else 20
+        out[f"gs_64cubed_fp64_dcpse_paper_{label}"] = {
+            "ms": ms, "accepted_steps": steps, "cell_steps_per_s": n64 ** 3 * steps / (ms * 1e-3),
+            **({"rejected": r["n_rej"]} if isinstance(r, dict) else {})}
+    g.close()
     out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
     out.update(precision_workload(torch, gs, si))
     out.update(batched_workload(torch, gs, si))
