@@ -230,6 +230,18 @@ int gs_get_dopri5_fusion(const gs_ctx* ctx);
  * ways).  The update is summed as ((u + dt (k1/6 + k2/3)) + dt k3/3) + dt
  * k4/6.  gs_get_rk4_fusion: 1 if RK4 steps use the pairs. */
 int gs_get_rk4_fusion(const gs_ctx* ctx);
+/* How the pair kernels' row warps fill their input ring: bulk = 0 (default)
+ * every thread copies its own 16-byte vectors with cp.async; bulk = 1 lane 0
+ * of each row warp issues one TMA bulk copy (cp.async.bulk) per input array
+ * and plane (the row's 32*VX contiguous cells), completion tracked by an
+ * mbarrier per ring slot (measured slower at 256^3 FP32: stages 6+7 362 us
+ * against 272 us).  Bit-identical results.
+ * gs_pair_timeouts: the number of mbarrier waits, over all pair launches of
+ * the process, that passed their iteration limit (a wait never blocks
+ * forever; a nonzero count means the results of that launch are invalid). */
+gs_status gs_set_pair_loader(gs_ctx* ctx, int bulk);
+int gs_get_pair_loader(const gs_ctx* ctx);
+gs_status gs_pair_timeouts(unsigned* count);
 /* Launch shape of pair kernel `pair` (0: Dormand-Prince stages 2+3, 1: 4+5,
  * 2: 6+7; 3: RK4 stages 1+2, 4: RK4 stages 3+4 with the update; -1: all
  * five): tile height ty (1..7 rows; the CTA has ty + 5 warps) and input ring
