@@ -360,6 +360,16 @@ gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* 
  * of the bound ensemble for each candidate segment shape and keeps the
  * fastest (the bound state is not modified). */
 gs_status gsb_autotune(gsb_ctx* ctx, int* ty, int* zc, double* best_ms);
+/* Tile choice by timing the caller's integration itself: each candidate tile
+ * runs gsb_integrate_adaptive(atol, rtol, t0 -> t_end, dt0 for every
+ * instance) twice (the first run builds its graph) from the bound state,
+ * which is saved (a temporary copy of the state, allocated and freed here)
+ * and restored after every run and at the end; the fastest second run
+ * wins.  Unlike gsb_autotune's dense timing round, a real run of an uneven
+ * ensemble has instances finishing at different times.  Grouping is left as
+ * set.  Synchronises; INVALID for t0 >= t_end, dt0 <= 0 or bad tolerances. */
+gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, double t_end, double dt0, int* ty_out,
+                           int* zc_out, double* best_ms);
 
 const char* gsb_last_error(const gsb_ctx* ctx);
 

@@ -113,6 +113,8 @@ _SIGNATURES = {
     "gsb_set_stage_depth": ([_vp, C.c_int], C.c_int),
     "gsb_get_grouping": ([_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
+    "gsb_autotune_run": ([_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
+                          C.POINTER(C.c_int), _dp], C.c_int),
     "gsb_last_error": ([_vp], C.c_char_p),
     "sur_param_count": ([], C.c_long),
     "sur_create": ([C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
@@ -584,6 +586,13 @@ class GrayScottBatch:
     def autotune(self):
         a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
         _bcheck(lib().gsb_autotune(self.ctx, C.byref(a), C.byref(b), C.byref(ms)), self.ctx)
+        return a.value, b.value, ms.value
+
+    def autotune_run(self, atol, rtol, t0, t_end, dt0):
+        """Tile choice by timing this integration itself (state restored)."""
+        a, b, ms = C.c_int(0), C.c_int(0), C.c_double(0)
+        _bcheck(lib().gsb_autotune_run(self.ctx, atol, rtol, t0, t_end, dt0, C.byref(a), C.byref(b), C.byref(ms)),
+                self.ctx)
         return a.value, b.value, ms.value
 
     def set_stage_depth(self, depth):

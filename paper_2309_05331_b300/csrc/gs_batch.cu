@@ -630,7 +630,8 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) 
     // the timing round has every instance running; a real integration also
     // has sparse rounds (finished instances' segments are still walked), so
     // only z-chunks of 16 planes or more are candidates (measured on 512
-    // uneven instances to t = 20: zc = 8 took 119 ms, zc = 32 101 ms)
+    // uneven instances to t = 20, an earlier build: zc = 8 took 119 ms, zc =
+    // 32 101 ms)
     static const int cand[][2] = {{4, 16}, {6, 16}, {6, 32}, {6, 64}, {8, 32}, {14, 16}, {14, 32}};
     // control blocks for timing: every instance running, parity 0, dt 1e-3
     for (int i = 0; i < ctx->count; ++i) {
@@ -689,6 +690,82 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) 
     if (st != GS_OK) return st;
     if ((st = gsb_set_tile(ctx, bty, bzc)) != GS_OK) return st;
     if ((st = gsb_set_grouping(ctx, bgroup)) != GS_OK) return st;
+    if (ty_out) *ty_out = bty;
+    if (zc_out) *zc_out = bzc;
+    if (best_ms) *best_ms = best;
+    return GS_OK;
+}
+
+// Tile choice by timing the integration itself: every candidate tile runs
+// the caller's integration (same tolerance, interval and initial step) from
+// the bound state, which is saved first and restored after each run and at
+// the end.  A dense timing round (gsb_autotune) has every instance running;
+// a real run of an uneven ensemble has instances finishing at different
+// times, and the two rank tiles differently.
+gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, double t_end, double dt0, int* ty_out,
+                           int* zc_out, double* best_ms) {
+    if (!ctx || !ctx->state[0] || !(t0 < t_end) || !(dt0 > 0) || !(atol >= 0) || !(rtol >= 0) || !(atol + rtol > 0))
+        return GS_ERR_INVALID;
+    static const int cand[][2] = {{4, 16}, {6, 16}, {6, 32}, {6, 64}, {8, 32}, {14, 16}, {14, 32}};
+    const size_t bytes = ctx->esz * (size_t)ctx->total;
+    void* save[2] = {nullptr, nullptr};
+    for (int c = 0; c < 2; ++c) {
+        if (cudaMalloc(&save[c], bytes) != cudaSuccess) {
+            if (save[0]) cudaFree(save[0]);
+            return GS_ERR_NOMEM;
+        }
+        if (cudaMemcpyAsync(save[c], ctx->state[c], bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            cudaFree(save[0]);
+            if (save[1]) cudaFree(save[1]);
+            return GS_ERR_CUDA;
+        }
+    }
+    std::vector<double> t(ctx->count), dt(ctx->count);
+    cudaEvent_t e0, e1;
+    gs_status st = GS_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = GS_ERR_CUDA;
+    float best = 1e30f;
+    int bty = ctx->ty, bzc = ctx->zc;
+    auto restore = [&]() -> gs_status {
+        for (int c = 0; c < 2; ++c)
+            if (cudaMemcpyAsync(ctx->state[c], save[c], bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+                return GS_ERR_CUDA;
+        return GS_OK;
+    };
+    for (const auto& c : cand) {
+        if (st != GS_OK) break;
+        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK) break;
+        for (int rep = 0; rep < 2 && st == GS_OK; ++rep) {  // the first run also builds the graph
+            if ((st = restore()) != GS_OK) break;
+            for (int i = 0; i < ctx->count; ++i) {
+                t[i] = t0;
+                dt[i] = dt0;
+            }
+            if (cudaEventRecord(e0, ctx->stream) != cudaSuccess) st = GS_ERR_CUDA;
+            const gs_status r = st == GS_OK ? gsb_integrate_adaptive(ctx, atol, rtol, t.data(), t_end, dt.data(), -1,
+                                                                    nullptr, nullptr, nullptr)
+                                            : st;
+            if (r == GS_ERR_CUDA || r == GS_ERR_INVALID || r == GS_ERR_NOMEM) st = r;
+            if (st == GS_OK && (cudaEventRecord(e1, ctx->stream) != cudaSuccess ||
+                                cudaEventSynchronize(e1) != cudaSuccess))
+                st = GS_ERR_CUDA;
+            float ms = 0.f;
+            if (st == GS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = GS_ERR_CUDA;
+            if (st == GS_OK && rep == 1 && ms < best) {
+                best = ms;
+                bty = c[0];
+                bzc = c[1];
+            }
+        }
+    }
+    if (st == GS_OK) st = restore();
+    if (st == GS_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = GS_ERR_CUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(save[0]);
+    cudaFree(save[1]);
+    if (st != GS_OK) return st;
+    if ((st = gsb_set_tile(ctx, bty, bzc)) != GS_OK) return st;
     if (ty_out) *ty_out = bty;
     if (zc_out) *zc_out = bzc;
     if (best_ms) *best_ms = best;

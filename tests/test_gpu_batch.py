@@ -199,3 +199,26 @@ def test_full_size_512_instance_ensemble():
         assert abs(ref["t"] - r["t"][i]) < 1e-6 * max(1.0, ref["t"])
         assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-5
     b.close()
+
+
+def test_autotune_run_restores_state_and_picks_a_candidate():
+    """The run-based tuner integrates the caller's run once per candidate tile
+    and restores the bound state: afterwards the state is bit-identical to
+    before, the chosen tile is a candidate, and the integration gives the
+    same result as on the default tile."""
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=23)
+    b = _batch(torch, SMALL, inits, 0)
+    before = [to_np(x).copy() for i in range(len(SMALL)) for x in b.view(i)]
+    ty, zc, ms = b.autotune_run(1e-7, 1e-7, 0.0, 1.0, 0.1)
+    assert (ty, zc) in {(4, 16), (6, 16), (6, 32), (6, 64), (8, 32), (14, 16), (14, 32)} and ms > 0
+    after = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
+    assert all(np.array_equal(p, q) for p, q in zip(before, after))
+    b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
+    tuned = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
+    b.close()
+    b = _batch(torch, SMALL, inits, 0)
+    b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
+    ref = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
+    b.close()
+    assert all(np.array_equal(p, q) for p, q in zip(tuned, ref))
