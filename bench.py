@@ -60,11 +60,11 @@ BYTES_PER_FIELD_CELL = 8
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 842.0 MB read + 247.8 MB written), per cell so that other grids scale by
+# 842.3 MB read + 248.4 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "2fad902d24afa6d2",
-               "bytes_per_cell": (841986304 + 247811328) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "ac040cd45648445d",
+               "bytes_per_cell": (842321152 + 248414464) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
