@@ -294,13 +294,21 @@ def extra_workloads(torch, gs, si):
     # F = 0.053, K = 0.014, DC-PSE Laplacian (122-point stencil), dt = 1 to
     # t_f = 20, FP64: RK4 and Dormand-Prince with fixed steps, and adaptive
     # Dormand-Prince (tolerance 1e-8)
+    # The stage kernels are bound by the FP64 pipe: the roofline counts FP64
+    # operations (one FMA, add or multiply per cell) against the measured FP64
+    # FMA instruction rate (half the measured FP64 FLOP/s).
+    fp64_peak_tflops = gs.gs_measure_fp64_peak()
+    out["fp64_fma_peak_tflops"] = fp64_peak_tflops
     n64 = 64
     u64, v64 = si.gs_initial_state(n64, n64, n64, seed=2)
     g = gs.GrayScott(n64, n64, n64, Du=2e-4, Dv=1e-4, F=0.053, k=0.014, prec=gs.GS_FP64)
     gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
-    for label, run in (("rk4_dt1_t20", lambda: g.step(gs.GS_RK4, 0.0, 1.0, 20)),
-                       ("dopri5_dt1_t20", lambda: g.step(gs.GS_DOPRI5, 0.0, 1.0, 20)),
-                       ("dopri5_adaptive_tol1e-8_t20", lambda: g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 1.0))):
+    npair = len(gs.gs_get_dcpse_stencil(g.ctx)[1]) // 2
+    for label, meth, run in (
+            ("rk4_dt1_t20", "rk4", lambda: g.step(gs.GS_RK4, 0.0, 1.0, 20)),
+            ("dopri5_dt1_t20", "dopri5_fixed", lambda: g.step(gs.GS_DOPRI5, 0.0, 1.0, 20)),
+            ("dopri5_adaptive_tol1e-8_t20", "dopri5_adaptive",
+             lambda: g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 1.0))):
         g.set_state(torch.from_numpy(u64), torch.from_numpy(v64))
         run()  # warm-up
         g.set_state(torch.from_numpy(u64), torch.from_numpy(v64))
@@ -310,16 +318,36 @@ def extra_workloads(torch, gs, si):
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t_0) * 1e3
         steps = r["n_acc"] if isinstance(r, dict) else 20
+        attempts = steps + (r["n_rej"] if isinstance(r, dict) else 0)
+        ops = n64 ** 3 * attempts * dcpse_fp64_ops_per_cell(meth, npair)
+        achieved = ops / (ms * 1e-3) / 1e12
         out[f"gs_64cubed_fp64_dcpse_paper_{label}"] = {
             "ms": ms, "accepted_steps": steps, "cell_steps_per_s": n64 ** 3 * steps / (ms * 1e-3),
-            **({"rejected": r["n_rej"]} if isinstance(r, dict) else {})}
+            **({"rejected": r["n_rej"]} if isinstance(r, dict) else {}),
+            "roofline": {"bound": "alu", "unit": "T FP64 ops/s", "achieved": achieved,
+                         "peak": fp64_peak_tflops / 2, "frac": achieved / (fp64_peak_tflops / 2),
+                         "peak_source": "measured FP64 FMA rate (this run)",
+                         "ops_per_cell_attempt": dcpse_fp64_ops_per_cell(meth, npair)}}
     g.close()
-    out["fp64_fma_peak_tflops"] = gs.gs_measure_fp64_peak()
     out.update(precision_workload(torch, gs, si))
     out.update(batched_workload(torch, gs, si))
     from paper_2309_05331_b300 import surrogate_workload
     out["surrogate_128cubed"] = surrogate_workload.run(torch, n=128, trajectories=8, per_traj=250, iters=3000)
     return out
+
+
+def dcpse_fp64_ops_per_cell(method, npair):
+    """Algorithmic FP64 operations per cell for one step (attempt) of the
+    DC-PSE Gray-Scott path, per component: the paired stencil (an add and an
+    FMA per pair, the centre term), the reaction (5), the stage input
+    u + dt sum_j a_j k_j (j + 1 for a stage with j inputs), and the final
+    combination (s + 1 for s stages; the adaptive attempt adds the error
+    terms and their scaling, s + 5)."""
+    stage = 2 * npair + 1 + 5
+    s = {"rk4": 4, "dopri5_fixed": 6, "dopri5_adaptive": 7}[method]  # fixed steps skip stage 7 (b7 = 0)
+    inputs = sum(i + 1 for i in range(1, s))  # stage i reads k_1..k_i
+    final = s + 1 + (s + 5 if method == "dopri5_adaptive" else 0)
+    return 2 * (s * stage + inputs + final)
 
 
 def precision_workload(torch, gs, si, n=N, accepted=1000):

@@ -27,11 +27,24 @@ constexpr int kDcpseT = 8;      // tile edge
 constexpr int kDcpseE = kDcpseT + 2 * kDcpseR;
 constexpr int kDcpseMaxNK = 6;  // stage inputs (Dormand-Prince stage 7 reads k1..k6)
 
+// The weights are even in the offset (w_{-o} = w_o: the moment system is
+// symmetric under o -> -o, and the host averages the two solved values), so
+// the FP64 kernel sums the stencil over the npair pairs {o, -o}:
+// L f_p = sum_k w_k (f_{p+o_k} + f_{p-o_k}) - wsum f_p, wsum = sum_q w_q:
+// one add and one FMA per pair instead of a subtract and an FMA per
+// neighbour, half the FP64 operations (the bound of the FP64 kernel).  The
+// rounding differs from the per-neighbour form by a few ulp of sum |w| |f|.
+// The FP32 kernel keeps the per-neighbour differences (FP32 arithmetic is
+// not its bound, and the differences keep its rounding small).
 template <typename T>
 struct DcpseStencil {
     int count;
     signed char off[kDcpseMax][3];
     T w[kDcpseMax];
+    int npair;
+    short pidx[kDcpseMax / 2];  // offset of pair k in the flattened Ys tile: (oz E + oy) E + ox
+    T pw[kDcpseMax / 2];
+    T wsum;
 };
 
 template <typename T>
@@ -76,10 +89,23 @@ __global__ void __launch_bounds__(512) dcpse_stage_kernel(const Geom<T> g, const
     const int cx = lx + kDcpseR, cy = ly + kDcpseR, cz = lz + kDcpseR;
     const T yu = Ys[0][cz][cy][cx], yv = Ys[1][cz][cy][cx];
     T lu = T(0), lv = T(0);
-    for (int q = 0; q < S.count; ++q) {
-        const int ox = S.off[q][0], oy = S.off[q][1], oz = S.off[q][2];
-        lu += S.w[q] * (Ys[0][cz + oz][cy + oy][cx + ox] - yu);
-        lv += S.w[q] * (Ys[1][cz + oz][cy + oy][cx + ox] - yv);
+    if constexpr (sizeof(T) == 8) {
+        const T* pu = &Ys[0][cz][cy][cx];
+        const T* pv = &Ys[1][cz][cy][cx];
+#pragma unroll 4
+        for (int k = 0; k < S.npair; ++k) {
+            const int o = S.pidx[k];
+            lu = fma(S.pw[k], pu[o] + pu[-o], lu);
+            lv = fma(S.pw[k], pv[o] + pv[-o], lv);
+        }
+        lu = fma(-S.wsum, yu, lu);
+        lv = fma(-S.wsum, yv, lv);
+    } else {
+        for (int q = 0; q < S.count; ++q) {
+            const int ox = S.off[q][0], oy = S.off[q][1], oz = S.off[q][2];
+            lu += S.w[q] * (Ys[0][cz + oz][cy + oy][cx + ox] - yu);
+            lv += S.w[q] * (Ys[1][cz + oz][cy + oy][cx + ox] - yv);
+        }
     }
     const T uvv = yu * yv * yv;
     const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);

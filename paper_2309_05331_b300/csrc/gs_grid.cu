@@ -722,6 +722,14 @@ static bool dcpse_build(const double h[3], double rc, int off[][3], double* w, i
             w[q] += eta * ex / (h[d] * h[d]);
         }
     }
+    // the solution is even in the offset; make it exactly so (each pair
+    // takes the mean of its two solved weights)
+    for (int q = 0; q < m; ++q)
+        for (int p = q + 1; p < m; ++p)
+            if (off[p][0] == -off[q][0] && off[p][1] == -off[q][1] && off[p][2] == -off[q][2]) {
+                const double wm = 0.5 * (w[q] + w[p]);
+                w[q] = w[p] = wm;
+            }
     *count = m;
     return true;
 }
@@ -731,10 +739,21 @@ static DcpseStencil<T> dcpse_stencil(const gs_ctx* ctx) {
     DcpseStencil<T> S;
     memset(&S, 0, sizeof(S));
     S.count = ctx->dcpse_count;
+    double wsum = 0.0;
     for (int q = 0; q < S.count; ++q) {
-        for (int d = 0; d < 3; ++d) S.off[q][d] = (signed char)ctx->dcpse_off[q][d];
+        const int* o = ctx->dcpse_off[q];
+        for (int d = 0; d < 3; ++d) S.off[q][d] = (signed char)o[d];
         S.w[q] = (T)ctx->dcpse_w[q];
+        wsum += ctx->dcpse_w[q];
+        // pairs {o, -o}: the representative has its last nonzero component positive
+        const int lead = o[2] != 0 ? o[2] : (o[1] != 0 ? o[1] : o[0]);
+        if (lead > 0) {
+            S.pidx[S.npair] = (short)((o[2] * kDcpseE + o[1]) * kDcpseE + o[0]);
+            S.pw[S.npair] = (T)ctx->dcpse_w[q];
+            ++S.npair;
+        }
     }
+    S.wsum = (T)wsum;
     return S;
 }
 
