@@ -277,17 +277,26 @@ gs_status gs_time_pairs(gs_ctx* ctx, int reps, double* ms);
  * grid points within rc_over_h spacings (3.1: 122 neighbours); on the
  * regular grid the operator is one stencil L f_p = sum_q w_q (f_{p+o_q} -
  * f_p), whose weights gs_set_laplacian computes once (Cholesky of the
- * moment system).  With GS_LAP_DCPSE, gs_rhs, gs_step (GS_EULER, GS_RK4,
- * GS_DOPRI5; GS_AB4 -> INVALID) and gs_integrate_adaptive run a separate
- * path: one tiled stage kernel per stage (8^3 cells + a halo of 3 in
- * shared memory) and one combine kernel per step, the adaptive controller
- * on the host with the formulas and limits of the graph path; synchronous.
+ * moment system; the solved weights are even in the offset and are stored
+ * exactly so, each pair {o, -o} taking the mean of its two values).  With
+ * GS_LAP_DCPSE, gs_rhs, gs_step (GS_EULER, GS_RK4, GS_DOPRI5; GS_AB4 ->
+ * INVALID) and gs_integrate_adaptive run a separate path: one tiled stage
+ * kernel per stage (8 x 8 x 8 or 8 x 8 x 4 cells + a halo of 3 in shared
+ * memory), each stage also forming the next stage's input at its own cells
+ * and the last one the new state (and the attempt's error maximum), the
+ * adaptive controller on the host with the formulas and limits of the
+ * graph path; synchronous.  The FP64 kernel sums the stencil over the
+ * offset pairs, sum_k w_k (f_{p+o_k} + f_{p-o_k}) - (sum_q w_q) f_p.
  * INVALID: unknown kind, rc_over_h outside [2, 4), a singular moment
  * system.  gs_get_dcpse_stencil: the offsets (3 ints each, in spacings)
- * and weights in use; capacity = 0 returns the count only. */
+ * and weights in use; capacity = 0 returns the count only.
+ * gs_set_dcpse_tile: tile depth of the stage kernel, 0 (default: 4 where
+ * the grid has fewer than 16 tiles of 8^3 per SM, else 8), 4 or 8; the
+ * results do not depend on it.  INVALID: any other value. */
 typedef enum { GS_LAP_7POINT = 0, GS_LAP_DCPSE = 1 } gs_laplacian;
 gs_status gs_set_laplacian(gs_ctx* ctx, gs_laplacian kind, double rc_over_h);
 gs_status gs_get_dcpse_stencil(const gs_ctx* ctx, int* count, int* offsets, double* weights, int capacity);
+gs_status gs_set_dcpse_tile(gs_ctx* ctx, int tz);
 
 /* Text of the last CUDA error seen by ctx ("" if none). */
 const char* gs_last_error(const gs_ctx* ctx);

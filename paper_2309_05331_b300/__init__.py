@@ -78,6 +78,7 @@ _SIGNATURES = {
     "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
     "gs_set_laplacian": ([_vp, C.c_int, C.c_double], C.c_int),
     "gs_get_dcpse_stencil": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, C.c_int], C.c_int),
+    "gs_set_dcpse_tile": ([_vp, C.c_int], C.c_int),
     "gs_get_pair_depths_in_use": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
@@ -333,6 +334,10 @@ GS_LAP_7POINT, GS_LAP_DCPSE = 0, 1
 
 def gs_set_laplacian(ctx, kind, rc_over_h=3.1):
     _check(lib().gs_set_laplacian(ctx, kind, rc_over_h), ctx)
+
+
+def gs_set_dcpse_tile(ctx, tz):
+    _check(lib().gs_set_dcpse_tile(ctx, tz), ctx)
 
 
 def gs_get_dcpse_stencil(ctx):

@@ -9,12 +9,16 @@
 // (gs_grid.cu); they travel as a kernel parameter (constant bank, broadcast
 // to every thread).
 //
-// dcpse_stage_kernel: one stage k = F(Y), Y = u + dt sum_j a_j k_j, on a
-// tile of 8 x 8 x 8 cells: the CTA forms Y on the tile plus a halo of R = 3
-// cells (14^3 values per component) in shared memory, then each thread sums
-// its cell's stencil from there.  dcpse_combine_kernel: u' = u + dt sum_j
-// b_j k_j and, for an error-controlled attempt, the maximum over cells of
-// |dt sum_j e_j k_j| / (atol + rtol (|u| + dt |k1|)).
+// dcpse_stage_kernel: one stage k_i = F(Y_i) on a tile of 8 x 8 x TZ
+// cells (TZ = 8 or 4): the CTA loads Y_i on the tile plus a halo of R = 3
+// cells ((TZ + 6) x 14 x 14 values per component) into shared memory, then
+// each thread sums its cell's stencil from there.  Y_i is formed once per
+// cell by the stage before (Y_1 = u): at its own cell a stage also forms the
+// next stage's input Y_{i+1} = u + dt sum_{j<=i} a_{i+1,j} k_j from u,
+// k_1..k_{i-1} and the k_i it has just computed, and the last stage forms
+// u' = u + dt sum_j b_j k_j and, for an error-controlled attempt, the
+// maximum over cells of |dt sum_j e_j k_j| / (atol + rtol (|u| + dt |k1|)).
+// So every field value is formed once, and a step is s launches.
 #pragma once
 
 #include "gs_tile.cuh"
@@ -49,70 +53,115 @@ struct DcpseStencil {
 
 template <typename T>
 struct DcpseStageArgs {
-    const T* u[2];
-    const T* k[kDcpseMaxNK][2];
-    double a[kDcpseMaxNK];
-    int nk;
+    const T* y[2];               // stage input Y_i (read with the halo)
+    const T* u[2];               // state (own cell: next input and final combination)
+    const T* k[kDcpseMaxNK][2];  // k_1..k_{i-1} (own cell)
+    int nk;                      // i - 1
     double dt;
-    T* out[2];
+    T* out[2];                   // k_i
+    // next stage input (yn[0] != nullptr): Y_{i+1} = u + dt sum_{j<=i} an_j k_j
+    double an[kDcpseMaxNK + 1];
+    T* yn[2];
+    // last stage (fin != nullptr): fin = u + dt sum_{j<=i} b_j k_j and, with
+    // emax, the scaled error maximum (bits of a non-negative double)
+    double b[kDcpseMaxNK + 1];
+    double e[kDcpseMaxNK + 1];
+    double atol, rtol;
+    T* fin[2];
+    unsigned long long* emax;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(512) dcpse_stage_kernel(const Geom<T> g, const DcpseStencil<T> S,
-                                                          const DcpseStageArgs<T> A) {
-    __shared__ T Ys[2][kDcpseE][kDcpseE][kDcpseE];
+template <typename T, int TZ>
+__global__ void __launch_bounds__(64 * TZ) dcpse_stage_kernel(const Geom<T> g, const DcpseStencil<T> S,
+                                                              const DcpseStageArgs<T> A) {
+    constexpr int EZ = TZ + 2 * kDcpseR;
+    __shared__ T Ys[2][EZ][kDcpseE][kDcpseE];
+    __shared__ double red[32];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const int tilesx = (nx + kDcpseT - 1) / kDcpseT, tilesy = (ny + kDcpseT - 1) / kDcpseT;
     const int bx = blockIdx.x % tilesx, by = (blockIdx.x / tilesx) % tilesy, bz = blockIdx.x / (tilesx * tilesy);
-    const int x0 = bx * kDcpseT, y0 = by * kDcpseT, z0 = bz * kDcpseT;
+    const int x0 = bx * kDcpseT, y0 = by * kDcpseT, z0 = bz * TZ;
     const int tid = threadIdx.x;
-    const T dt = (T)A.dt;
-    // Y on the tile and its halo (periodic)
-    for (int e = tid; e < kDcpseE * kDcpseE * kDcpseE; e += blockDim.x) {
+    // Y_i on the tile and its halo (periodic)
+    for (int e = tid; e < EZ * kDcpseE * kDcpseE; e += blockDim.x) {
         const int ex = e % kDcpseE, ey = (e / kDcpseE) % kDcpseE, ez = e / (kDcpseE * kDcpseE);
         int x = x0 + ex - kDcpseR, y = y0 + ey - kDcpseR, z = z0 + ez - kDcpseR;
         x = ((x % nx) + nx) % nx;
         y = ((y % ny) + ny) % ny;
         z = ((z % nz) + nz) % nz;
         const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            T s = T(0);
-            for (int j = 0; j < A.nk; ++j) s = (j == 0) ? (T)A.a[0] * A.k[0][c][i] : s + (T)A.a[j] * A.k[j][c][i];
-            Ys[c][ez][ey][ex] = A.nk > 0 ? A.u[c][i] + dt * s : A.u[c][i];
-        }
+        Ys[0][ez][ey][ex] = A.y[0][i];
+        Ys[1][ez][ey][ex] = A.y[1][i];
     }
     __syncthreads();
     const int lx = tid % kDcpseT, ly = (tid / kDcpseT) % kDcpseT, lz = tid / (kDcpseT * kDcpseT);
     const int x = x0 + lx, y = y0 + ly, z = z0 + lz;
-    if (x >= nx || y >= ny || z >= nz) return;
-    const int cx = lx + kDcpseR, cy = ly + kDcpseR, cz = lz + kDcpseR;
-    const T yu = Ys[0][cz][cy][cx], yv = Ys[1][cz][cy][cx];
-    T lu = T(0), lv = T(0);
-    if constexpr (sizeof(T) == 8) {
-        const T* pu = &Ys[0][cz][cy][cx];
-        const T* pv = &Ys[1][cz][cy][cx];
+    const bool valid = x < nx && y < ny && z < nz;
+    double emax = 0.0;
+    if (valid) {
+        const int cx = lx + kDcpseR, cy = ly + kDcpseR, cz = lz + kDcpseR;
+        const T yu = Ys[0][cz][cy][cx], yv = Ys[1][cz][cy][cx];
+        T lu = T(0), lv = T(0);
+        if constexpr (sizeof(T) == 8) {
+            const T* pu = &Ys[0][cz][cy][cx];
+            const T* pv = &Ys[1][cz][cy][cx];
 #pragma unroll 4
-        for (int k = 0; k < S.npair; ++k) {
-            const int o = S.pidx[k];
-            lu = fma(S.pw[k], pu[o] + pu[-o], lu);
-            lv = fma(S.pw[k], pv[o] + pv[-o], lv);
+            for (int k = 0; k < S.npair; ++k) {
+                const int o = S.pidx[k];
+                lu = fma(S.pw[k], pu[o] + pu[-o], lu);
+                lv = fma(S.pw[k], pv[o] + pv[-o], lv);
+            }
+            lu = fma(-S.wsum, yu, lu);
+            lv = fma(-S.wsum, yv, lv);
+        } else {
+            for (int q = 0; q < S.count; ++q) {
+                const int ox = S.off[q][0], oy = S.off[q][1], oz = S.off[q][2];
+                lu += S.w[q] * (Ys[0][cz + oz][cy + oy][cx + ox] - yu);
+                lv += S.w[q] * (Ys[1][cz + oz][cy + oy][cx + ox] - yv);
+            }
         }
-        lu = fma(-S.wsum, yu, lu);
-        lv = fma(-S.wsum, yv, lv);
-    } else {
-        for (int q = 0; q < S.count; ++q) {
-            const int ox = S.off[q][0], oy = S.off[q][1], oz = S.off[q][2];
-            lu += S.w[q] * (Ys[0][cz + oz][cy + oy][cx + ox] - yu);
-            lv += S.w[q] * (Ys[1][cz + oz][cy + oy][cx + ox] - yv);
+        const T uvv = yu * yv * yv;
+        T f[2];
+        f[0] = g.Du * lu - uvv + g.F * (T(1) - yu);
+        f[1] = g.Dv * lv + uvv - (g.F + g.k) * yv;
+        const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
+        const T dt = (T)A.dt;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            A.out[c][i] = f[c];
+            if (A.yn[0]) {
+                // Y_{i+1} = u + dt (sum_j an_j k_j), summed from k_1 up
+                T s = T(0);
+                for (int j = 0; j < A.nk; ++j) s = (j == 0) ? (T)A.an[0] * A.k[j][c][i] : s + (T)A.an[j] * A.k[j][c][i];
+                s = (A.nk == 0) ? (T)A.an[0] * f[c] : s + (T)A.an[A.nk] * f[c];
+                A.yn[c][i] = A.u[c][i] + dt * s;
+            }
+            if (A.fin[0]) {
+                // u' = u + dt sum_j b_j k_j and the error terms, in FP64
+                const double u = (double)A.u[c][i];
+                double sb = 0.0, se = 0.0, k1 = 0.0;
+                for (int j = 0; j <= A.nk; ++j) {
+                    const double kj = (j < A.nk) ? (double)A.k[j][c][i] : (double)f[c];
+                    if (j == 0) k1 = kj;
+                    sb += A.b[j] * kj;
+                    se += A.e[j] * kj;
+                }
+                A.fin[c][i] = (T)(u + A.dt * sb);
+                if (A.emax) {
+                    const double sc = A.atol + A.rtol * (fabs(u) + A.dt * fabs(k1));
+                    emax = nanmax(emax, fabs(A.dt * se) / sc);
+                }
+            }
         }
     }
-    const T uvv = yu * yv * yv;
-    const long long i = (long long)x + (long long)nx * ((long long)y + (long long)ny * z);
-    A.out[0][i] = g.Du * lu - uvv + g.F * (T(1) - yu);
-    A.out[1][i] = g.Dv * lv + uvv - (g.F + g.k) * yv;
+    if (A.emax) {  // uniform over the launch: every thread reaches the block reduction
+        const double bmax = block_nanmax(emax, red);
+        if (tid == 0) atomic_max_nonneg(A.emax, bmax);
+    }
 }
 
+// u' = u + dt sum_j b_j k_j as its own pass (Euler: its one stage reads u
+// with the halo, so the update cannot overwrite u inside that stage)
 template <typename T>
 struct DcpseCombineArgs {
     const T* u[2];

@@ -87,6 +87,7 @@ struct gs_ctx {
     int dcpse_count = 0;
     int dcpse_off[kDcpseMax][3] = {};
     double dcpse_w[kDcpseMax] = {};
+    int dcpse_tz = 0;  // DC-PSE tile depth: 0 automatic, 4 or 8
     unsigned long long* demax = nullptr;  // DC-PSE attempts: bits of the scaled error maximum
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
@@ -641,8 +642,8 @@ static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned lon
 
 // ---------------------------------------------------------------------------
 // DC-PSE Laplacian (gs_dcpse.cuh): stencil from the moment conditions, and a
-// host-driven stepping path (one stage kernel per stage, one combine kernel
-// per step or attempt).
+// host-driven stepping path (one stage kernel per stage; the last stage of a
+// step or attempt also forms the new state and the error maximum).
 // ---------------------------------------------------------------------------
 // Weights of L f_p = sum_q w_q (f_{p+o_q} - f_p): for each axis d the kernel
 // eta_d(z) = sum_g a_g z^g exp(-|z|^2) (z = -o_q, eps = h_d) with moments
@@ -757,25 +758,35 @@ static DcpseStencil<T> dcpse_stencil(const gs_ctx* ctx) {
     return S;
 }
 
-// k_out = F(u + dt sum_j a_j k_j) with the DC-PSE Laplacian
+// one DC-PSE stage launch: tiles of 8 x 8 x 8 cells, or 8 x 8 x 4 where the
+// grid has fewer than 16 deep tiles per SM (more, smaller CTAs even out the
+// last wave; the deeper tile re-reads less halo)
 template <typename T>
-static cudaError_t dcpse_stage(gs_ctx* ctx, void* const u[2], void* const* const kin[2], const double* a, int nk,
-                               double dt, void* const out[2]) {
+static cudaError_t dcpse_launch(gs_ctx* ctx, const DcpseStageArgs<T>& A) {
+    const Geom<T> g = make_geom<T>(ctx->p);
+    const long long tx = (ctx->p.nx + kDcpseT - 1) / kDcpseT, ty = (ctx->p.ny + kDcpseT - 1) / kDcpseT;
+    const long long t8 = tx * ty * ((ctx->p.nz + 7) / 8);
+    const int tz = ctx->dcpse_tz ? ctx->dcpse_tz : (t8 < 16LL * ctx->nsm ? 4 : 8);
+    if (tz == 4) {
+        const long long tiles = tx * ty * ((ctx->p.nz + 3) / 4);
+        dcpse_stage_kernel<T, 4><<<(unsigned)tiles, 64 * 4, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
+    } else {
+        dcpse_stage_kernel<T, 8><<<(unsigned)t8, 64 * 8, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
+    }
+    return cudaGetLastError();
+}
+
+// k = F(y) at every cell (the right-hand side, no further output)
+template <typename T>
+static cudaError_t dcpse_rhs(gs_ctx* ctx, void* const y[2], void* const out[2]) {
     DcpseStageArgs<T> A;
     memset(&A, 0, sizeof(A));
     for (int c = 0; c < 2; ++c) {
-        A.u[c] = (const T*)u[c];
+        A.y[c] = (const T*)y[c];
+        A.u[c] = (const T*)y[c];
         A.out[c] = (T*)out[c];
-        for (int j = 0; j < nk; ++j) A.k[j][c] = (const T*)kin[c][j];
     }
-    for (int j = 0; j < nk; ++j) A.a[j] = a[j];
-    A.nk = nk;
-    A.dt = dt;
-    const Geom<T> g = make_geom<T>(ctx->p);
-    const int tiles = ((ctx->p.nx + kDcpseT - 1) / kDcpseT) * ((ctx->p.ny + kDcpseT - 1) / kDcpseT) *
-                      ((ctx->p.nz + kDcpseT - 1) / kDcpseT);
-    dcpse_stage_kernel<T><<<tiles, kDcpseT * kDcpseT * kDcpseT, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
-    return cudaGetLastError();
+    return dcpse_launch<T>(ctx, A);
 }
 
 // out = u + dt sum_j b_j k_j; with emax, the attempt's scaled error maximum
@@ -839,23 +850,40 @@ static HostTab host_tab(gs_method m) {
     return T;
 }
 
-// the stages of one step / attempt from state u into fields 1..s
+// The stages of one step / attempt from state u: k_i into field i (1..s),
+// the stage inputs Y_2..Y_s alternating between fields 8 and 0 (Y_1 = u).
+// With fin, the last stage also writes u + dt sum_j b_j k_j there and, with
+// err, reduces the scaled error maximum into ctx->demax.  fin may be u
+// itself when s_used > 1 (the last stage reads u at its own cells only).
 template <typename T>
-static cudaError_t dcpse_stages(gs_ctx* ctx, const HostTab& tab, int s_used, void* const u[2], double dt) {
+static cudaError_t dcpse_stages(gs_ctx* ctx, const HostTab& tab, int s_used, void* const u[2], double dt,
+                                void* const* fin, bool err, double atol, double rtol) {
+    void* const ybuf[2][2] = {{ctx->field[8][0], ctx->field[8][1]}, {ctx->field[0][0], ctx->field[0][1]}};
     for (int i = 0; i < s_used; ++i) {
-        void* kin0[kDcpseMaxNK];
-        void* kin1[kDcpseMaxNK];
-        double a[kDcpseMaxNK];
-        int nk = 0;
-        for (int j = 0; j < i; ++j) {
-            kin0[nk] = ctx->field[1 + j][0];
-            kin1[nk] = ctx->field[1 + j][1];
-            a[nk] = tab.a[i][j];
-            ++nk;
+        DcpseStageArgs<T> A;
+        memset(&A, 0, sizeof(A));
+        for (int c = 0; c < 2; ++c) {
+            A.y[c] = (const T*)(i == 0 ? u[c] : ybuf[i % 2][c]);
+            A.u[c] = (const T*)u[c];
+            A.out[c] = (T*)ctx->field[1 + i][c];
+            for (int j = 0; j < i; ++j) A.k[j][c] = (const T*)ctx->field[1 + j][c];
         }
-        void* const* const kin[2] = {kin0, kin1};
-        void* const out[2] = {ctx->field[1 + i][0], ctx->field[1 + i][1]};
-        const cudaError_t e = dcpse_stage<T>(ctx, u, kin, a, nk, dt, out);
+        A.nk = i;
+        A.dt = dt;
+        if (i + 1 < s_used) {
+            for (int j = 0; j <= i; ++j) A.an[j] = tab.a[i + 1][j];
+            for (int c = 0; c < 2; ++c) A.yn[c] = (T*)ybuf[(i + 1) % 2][c];
+        } else if (fin) {
+            for (int j = 0; j <= i; ++j) {
+                A.b[j] = tab.b[j];
+                A.e[j] = tab.e[j];
+            }
+            for (int c = 0; c < 2; ++c) A.fin[c] = (T*)fin[c];
+            A.atol = atol;
+            A.rtol = rtol;
+            A.emax = err ? ctx->demax : nullptr;
+        }
+        const cudaError_t e = dcpse_launch<T>(ctx, A);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -869,8 +897,13 @@ static gs_status dcpse_step(gs_ctx* ctx, gs_method method, double t0, double dt,
     void* const u[2] = {ctx->state[0], ctx->state[1]};
     (void)t0;  // autonomous right-hand side
     for (long m = 0; m < nsteps; ++m) {
-        CK(dcpse_stages<T>(ctx, tab, s_used, u, dt));
-        CK(dcpse_combine<T>(ctx, u, s_used, tab.b, nullptr, dt, 0.0, 0.0, u, false));
+        if (s_used > 1) {
+            CK(dcpse_stages<T>(ctx, tab, s_used, u, dt, u, false, 0.0, 0.0));
+        } else {
+            // one stage reads u with its halo: the update goes through its own pass
+            CK(dcpse_stages<T>(ctx, tab, s_used, u, dt, nullptr, false, 0.0, 0.0));
+            CK(dcpse_combine<T>(ctx, u, s_used, tab.b, nullptr, dt, 0.0, 0.0, u, false));
+        }
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return GS_OK;
@@ -907,8 +940,7 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         }
         ++att;
         CK(cudaMemsetAsync(ctx->demax, 0, sizeof(unsigned long long), ctx->stream));
-        CK(dcpse_stages<T>(ctx, tab, 7, u, h));
-        CK(dcpse_combine<T>(ctx, u, 7, tab.b, tab.e, h, atol, rtol, ynew, true));
+        CK(dcpse_stages<T>(ctx, tab, 7, u, h, ynew, true, atol, rtol));
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, ctx->demax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -1204,9 +1236,7 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u, const void* v, void* fu, 
     if (ctx->lap == 1) {
         void* const uu[2] = {const_cast<void*>(u), const_cast<void*>(v)};
         void* const out[2] = {fu, fv};
-        void* const* const kin[2] = {nullptr, nullptr};
-        CK(ctx->p.prec == GS_FP64 ? dcpse_stage<double>(ctx, uu, kin, nullptr, 0, 0.0, out)
-                                  : dcpse_stage<float>(ctx, uu, kin, nullptr, 0, 0.0, out));
+        CK(ctx->p.prec == GS_FP64 ? dcpse_rhs<double>(ctx, uu, out) : dcpse_rhs<float>(ctx, uu, out));
         return GS_OK;
     }
     CK(launch_stage(ctx, ctx->stream, 0, MODE_STAGE, A, ctx->def));
@@ -1229,6 +1259,12 @@ gs_status gs_set_laplacian(gs_ctx* ctx, gs_laplacian kind, double rc_over_h) {
     ctx->dcpse_count = count;
     ctx->dcpse_rc = rc_over_h;
     ctx->lap = 1;
+    return GS_OK;
+}
+
+gs_status gs_set_dcpse_tile(gs_ctx* ctx, int tz) {
+    if (!ctx || (tz != 0 && tz != 4 && tz != 8)) return GS_ERR_INVALID;
+    ctx->dcpse_tz = tz;
     return GS_OK;
 }
 

@@ -635,6 +635,44 @@ def test_dcpse_fixed_steps_match_oracle(prec, method, omethod):
     g.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_dcpse_tile_depths_agree(prec):
+    """Tiles of 8 x 8 x 4 and 8 x 8 x 8 cells give bit-identical states (every
+    cell's sums run in the same order), on a ragged grid, for RK4 steps and
+    an adaptive Dormand-Prince run, and both match the oracle."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (20, 12, 9)
+    u0, v0 = si.gs_initial_state(*dims, seed=63)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    tol = 1e-8 if prec == 0 else 1e-5
+    runs = {}
+    for tz in (4, 8):
+        g = _gs(torch, dims, prec, u0, v0, **PAPER_GS)
+        gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+        gs.gs_set_dcpse_tile(g.ctx, tz)
+        g.step(gs.GS_RK4, 0.0, 1.0, 3)
+        mid = (to_np(g.u).copy(), to_np(g.v).copy())
+        r = g.integrate_adaptive(tol, tol, 3.0, 6.0, 1.0)
+        runs[tz] = (mid, to_np(g.u).copy(), to_np(g.v).copy(), r["n_acc"], r["n_rej"])
+        with pytest.raises(RuntimeError):
+            gs.gs_set_dcpse_tile(g.ctx, 6)
+        g.close()
+    assert runs[4][3:] == runs[8][3:]
+    for a, b in ((runs[4][0][0], runs[8][0][0]), (runs[4][0][1], runs[8][0][1]), (runs[4][1], runs[8][1]),
+                 (runs[4][2], runs[8][2])):
+        assert np.array_equal(a, b)
+    p = oracle.GSParams(*dims, **PAPER_GS)
+    ou, ov = oracle.gs_dcpse_integrate_const(p, u0, v0, oracle.RK4, 1.0, 3)
+    bar = FP64_TOL if prec == 0 else FP32_TOL
+    assert oracle.rel_l2(list(runs[4][0]), [ou, ov]) < bar
+    if prec == 0:  # the FP64 run takes the oracle's steps
+        ref = oracle.gs_dcpse_integrate_adaptive(p, ou, ov, 3.0, 6.0, 1.0, tol, tol)
+        assert (ref["n_acc"], ref["n_rej"]) == runs[4][3:]
+        assert oracle.rel_l2([runs[4][1], runs[4][2]], [ref["u"], ref["v"]]) < bar
+
+
 def test_dcpse_adaptive_fp64_matches_oracle_run():
     """Error-controlled Dopri5 with the DC-PSE Laplacian (host controller):
     same accepted / rejected counts and step sizes as the oracle's run."""
