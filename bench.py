@@ -215,6 +215,18 @@ def extra_workloads(torch, gs, si):
     out = {}
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     stream = torch.cuda.current_stream()
+    # The FP64 workloads are bound by the FP64 pipe: their rooflines count
+    # FP64 operations (one FMA, add, multiply or divide) against the measured
+    # FP64 FMA instruction rate (half the measured FP64 FLOP/s).
+    fp64_peak_tflops = gs.gs_measure_fp64_peak()
+    out["fp64_fma_peak_tflops"] = fp64_peak_tflops
+
+    def fp64_roofline(ops, ms, ops_unit):
+        achieved = ops / (ms * 1e-3) / 1e12
+        return {"bound": "alu", "unit": "T FP64 ops/s", "achieved": achieved, "peak": fp64_peak_tflops / 2,
+                "frac": achieved / (fp64_peak_tflops / 2), "peak_source": "measured FP64 FMA rate (this run)",
+                "ops_per_unit": ops_unit}
+
     # Gray-Scott 32^3 FP64 RK4 dt=0.1 x 100 steps
     n = 32
     u0, v0 = si.gs_initial_state(n, n, n, seed=0)
@@ -242,9 +254,11 @@ def extra_workloads(torch, gs, si):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
+        ops = ODE_DP5_OPS[name]
         out[f"ode_2^24_fp64_dopri5_{name}_tol1e-8_t10"] = {
             "ms": ms, "accepted": r["n_acc"], "rejected": r["n_rej"],
-            "element_steps_per_s": m * r["n_acc"] / (ms * 1e-3)}
+            "element_steps_per_s": m * r["n_acc"] / (ms * 1e-3),
+            "roofline": fp64_roofline(m * (r["n_acc"] + r["n_rej"]) * ops, ms, {"element-attempt": ops})}
         x = x0.clone()
         a, b = ev(), ev()
         a.record(stream)
@@ -252,7 +266,10 @@ def extra_workloads(torch, gs, si):
         b.record(stream)
         torch.cuda.synchronize()
         ms = a.elapsed_time(b)
-        out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {"ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3)}
+        ops = ODE_AB4_OPS[name]
+        out[f"ode_2^24_fp64_ab4_{name}_dt1e-3_x1e4"] = {
+            "ms": ms, "element_steps_per_s": m * 1e4 / (ms * 1e-3),
+            "roofline": fp64_roofline(m * 1e4 * ops, ms, {"element-step": ops})}
     # the paper's accuracy families (Eq. 1a: c = x y on a 4096 x 4096 grid of
     # (x, y) in [0,1]^2, from the closed form at t = -5 to t = 5), Table 1's
     # Fehlberg 7(8) and Adams-Bashforth 8 with fixed steps
@@ -294,11 +311,6 @@ def extra_workloads(torch, gs, si):
     # F = 0.053, K = 0.014, DC-PSE Laplacian (122-point stencil), dt = 1 to
     # t_f = 20, FP64: RK4 and Dormand-Prince with fixed steps, and adaptive
     # Dormand-Prince (tolerance 1e-8)
-    # The stage kernels are bound by the FP64 pipe: the roofline counts FP64
-    # operations (one FMA, add or multiply per cell) against the measured FP64
-    # FMA instruction rate (half the measured FP64 FLOP/s).
-    fp64_peak_tflops = gs.gs_measure_fp64_peak()
-    out["fp64_fma_peak_tflops"] = fp64_peak_tflops
     n64 = 64
     u64, v64 = si.gs_initial_state(n64, n64, n64, seed=2)
     g = gs.GrayScott(n64, n64, n64, Du=2e-4, Dv=1e-4, F=0.053, k=0.014, prec=gs.GS_FP64)
@@ -320,20 +332,26 @@ def extra_workloads(torch, gs, si):
         steps = r["n_acc"] if isinstance(r, dict) else 20
         attempts = steps + (r["n_rej"] if isinstance(r, dict) else 0)
         ops = n64 ** 3 * attempts * dcpse_fp64_ops_per_cell(meth, npair)
-        achieved = ops / (ms * 1e-3) / 1e12
         out[f"gs_64cubed_fp64_dcpse_paper_{label}"] = {
             "ms": ms, "accepted_steps": steps, "cell_steps_per_s": n64 ** 3 * steps / (ms * 1e-3),
             **({"rejected": r["n_rej"]} if isinstance(r, dict) else {}),
-            "roofline": {"bound": "alu", "unit": "T FP64 ops/s", "achieved": achieved,
-                         "peak": fp64_peak_tflops / 2, "frac": achieved / (fp64_peak_tflops / 2),
-                         "peak_source": "measured FP64 FMA rate (this run)",
-                         "ops_per_cell_attempt": dcpse_fp64_ops_per_cell(meth, npair)}}
+            "roofline": fp64_roofline(ops, ms, {"cell-attempt": dcpse_fp64_ops_per_cell(meth, npair)})}
     g.close()
     out.update(precision_workload(torch, gs, si))
     out.update(batched_workload(torch, gs, si))
     from paper_2309_05331_b300 import surrogate_workload
     out["surrogate_128cubed"] = surrogate_workload.run(torch, n=128, trajectories=8, per_traj=250, iters=3000)
     return out
+
+
+# Algorithmic FP64 operations of the pointwise steppers (one per FMA, add,
+# multiply or divide in the formulas; negation and |x| are free operand
+# modifiers): a Dormand-Prince attempt forms the inputs of k2..k6 (2 + 3 + 4 +
+# 5 + 6), y5 (6), the error (7), its scale (2) and the ratio (1) = 36 plus
+# seven right-hand sides (-x: 0; x (1 - x): 2 each); an Adams-Bashforth 4
+# step is the four-term sum and the update (5) plus one right-hand side.
+ODE_DP5_OPS = {"exp_decay": 36, "logistic": 36 + 7 * 2}
+ODE_AB4_OPS = {"exp_decay": 5, "logistic": 5 + 2}
 
 
 def dcpse_fp64_ops_per_cell(method, npair):
