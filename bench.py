@@ -61,11 +61,11 @@ NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside 
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 842.3 MB read + 248.4 MB written), per cell so that other grids scale by
+# 842.7 MB read + 245.3 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "ac040cd45648445d",
-               "bytes_per_cell": (842321152 + 248414464) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "0c73f867a8f69359",
+               "bytes_per_cell": (842731776 + 245303552) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
@@ -240,7 +240,25 @@ def extra_workloads(torch, gs, si):
     b.record(stream)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    out["gs_32cubed_fp64_rk4_dt0.1_x100"] = {"ms": ms, "cell_steps_per_s": n ** 3 * 100 / (ms * 1e-3)}
+    out["gs_32cubed_fp64_rk4_dt0.1_x100"] = {"ms": ms, "cell_steps_per_s": n ** 3 * 100 / (ms * 1e-3),
+                                              "path": "persistent" if gs.gs_get_small_grid_path(g.ctx) else "graph"}
+    # launch overhead: the same run as one cooperative launch (persistent
+    # kernel, grid barrier between stages) and as a CUDA graph of per-stage
+    # launches
+    paths = {}
+    for mode, key in ((1, "persistent_one_launch"), (0, "graph_of_stage_launches")):
+        gs.gs_set_small_grid_path(g.ctx, mode, 0)
+        g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+        g.step(gs.GS_RK4, 0.0, 0.1, 100)
+        g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+        a, b = ev(), ev()
+        a.record(stream)
+        g.step(gs.GS_RK4, 0.0, 0.1, 100)
+        b.record(stream)
+        torch.cuda.synchronize()
+        paths[key] = {"ms": a.elapsed_time(b), "us_per_step": a.elapsed_time(b) * 10.0}
+    gs.gs_set_small_grid_path(g.ctx, -1, 0)
+    out["gs_32cubed_fp64_rk4_dt0.1_x100"]["launch_paths"] = paths
     g.close()
     # pointwise ODEs, 2^24 FP64
     m = 1 << 24
