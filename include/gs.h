@@ -130,6 +130,24 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
                                 double* dt, long max_accepted, long* n_accepted,
                                 long* n_rejected);
 
+/* Observer (the functor Odeint calls before each time step, e.g. to write
+ * output; section "Architecture and nomenclature of Boost Odeint"):
+ * fn(t, u, v, user) runs on the calling host thread with u, v the device
+ * pointers of the state bound to ctx, after ctx's stream has drained; it
+ * may read them (on any stream) but must not write them.  With an observer
+ * set, gs_step calls it at t0, t0 + dt, ..., t0 + nsteps dt (before each
+ * step and once after the last), and gs_integrate_adaptive at the start
+ * time and after every accepted step.  A nonzero return stops the call
+ * before its next step: it returns GS_OK with *t (and *dt, *n_accepted,
+ * *n_rejected) describing the steps taken.  The observed run launches
+ * each step on its own and synchronises after it, with the device control
+ * block carried from step to step, so its steps, its states and its
+ * results are those of the same call without an observer.  fn = NULL
+ * removes the observer; the library never frees `user`.  The observer is
+ * not called by the batched integrator (gsb_*). */
+typedef int (*gs_observer)(double t, void* u, void* v, void* user);
+gs_status gs_set_observer(gs_ctx* ctx, gs_observer fn, void* user);
+
 /* Enables (capacity > 0) or disables (0) recording of the accepted step
  * sizes of later gs_integrate_adaptive calls into a device buffer of
  * `capacity` doubles. */

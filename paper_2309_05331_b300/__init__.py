@@ -46,6 +46,8 @@ class gsb_instance(C.Structure):
 
 _lib = None
 _vp, _dp, _lp = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_long)
+# int (*gs_observer)(double t, void* u, void* v, void* user)
+GS_OBSERVER = C.CFUNCTYPE(C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p)
 
 _SIGNATURES = {
     "gs_create": ([C.POINTER(gs_params), _vp, C.POINTER(_vp)], C.c_int),
@@ -79,6 +81,7 @@ _SIGNATURES = {
     "gs_set_laplacian": ([_vp, C.c_int, C.c_double], C.c_int),
     "gs_get_dcpse_stencil": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp, C.c_int], C.c_int),
     "gs_set_dcpse_tile": ([_vp, C.c_int], C.c_int),
+    "gs_set_observer": ([_vp, GS_OBSERVER, _vp], C.c_int),
     "gs_get_pair_depths_in_use": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_stage_depths": ([_vp, C.POINTER(C.c_int)], C.c_int),
     "gs_get_tile": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
@@ -336,6 +339,18 @@ def gs_set_laplacian(ctx, kind, rc_over_h=3.1):
     _check(lib().gs_set_laplacian(ctx, kind, rc_over_h), ctx)
 
 
+def gs_set_observer(ctx, fn):
+    """Installs fn(t, u_ptr, v_ptr) -> bool (True stops) as ctx's observer, or
+    removes it (fn None).  Returns the ctypes callback, which the caller must
+    keep alive while it is installed."""
+    if fn is None:
+        _check(lib().gs_set_observer(ctx, C.cast(None, GS_OBSERVER), None), ctx)
+        return None
+    cb = GS_OBSERVER(lambda t, u, v, user: 1 if fn(t, u, v) else 0)
+    _check(lib().gs_set_observer(ctx, cb, None), ctx)
+    return cb
+
+
 def gs_set_dcpse_tile(ctx, tz):
     _check(lib().gs_set_dcpse_tile(ctx, tz), ctx)
 
@@ -515,6 +530,12 @@ class GrayScott:
 
     def integrate_adaptive(self, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
         return gs_integrate_adaptive(self.ctx, atol, rtol, t, t_end, dt, max_accepted, check)
+
+    def set_observer(self, fn):
+        """fn(t, u, v) -> bool, called by step / integrate_adaptive before each
+        step and after the last (u, v: this problem's state tensors, read
+        only); True stops the integration.  None removes the observer."""
+        self._obs = gs_set_observer(self.ctx, None if fn is None else (lambda t, pu, pv: fn(t, self.u, self.v)))
 
     def close(self):
         if self.ctx:

@@ -67,6 +67,8 @@ struct gs_ctx {
     long long* hpatch = nullptr;  // pinned staging of single-field patches
     double* dlog = nullptr;
     long log_cap = 0;
+    gs_observer obs = nullptr;  // user observer (gs_set_observer)
+    void* obs_user = nullptr;
     KCfg def{0, 6, 0};      // kernels of RK4 / Euler / AB4 / F (form 0, zc 0: automatic)
     KCfg dp[7];             // Dormand-Prince k1 and stages 2..7 once tuned
     bool dp_tuned = false;
@@ -640,6 +642,18 @@ static cudaError_t build_body(gs_ctx* ctx, int gid, cudaStream_t s, unsigned lon
     }
 }
 
+// The observer sees the state in the caller's buffers after the stream has
+// drained; true: it asks to stop.
+static bool observe(gs_ctx* ctx, double t, gs_status* st) {
+    const cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        set_err(ctx, e, "observer: cudaStreamSynchronize");
+        *st = GS_ERR_CUDA;
+        return true;
+    }
+    return ctx->obs(t, ctx->state[0], ctx->state[1], ctx->obs_user) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // DC-PSE Laplacian (gs_dcpse.cuh): stencil from the moment conditions, and a
 // host-driven stepping path (one stage kernel per stage; the last stage of a
@@ -923,7 +937,8 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     long long n_acc = 0, n_rej = 0, consec = 0, att = 0;
     gs_status status = GS_OK;
     std::vector<double> log;
-    while (t < t_end && (max_acc < 0 || n_acc < max_acc)) {
+    bool stop = ctx->obs && observe(ctx, t, &status);
+    while (!stop && t < t_end && (max_acc < 0 || n_acc < max_acc)) {
         if (att >= kMaxAttempts) {
             status = GS_ERR_MAX_STEPS;
             break;
@@ -967,6 +982,7 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         ++n_acc;
         t = last ? t_end : t + h;
         dt = E < 0.5 ? h * 0.9 * std::pow(std::max(E, 1.0 / 3125.0), -1.0 / 5.0) : h;
+        if (ctx->obs) stop = observe(ctx, t, &status);
     }
     // step log and counters where gs_get_step_log finds them
     const long nlog = (long)std::min<size_t>(log.size(), (size_t)ctx->log_cap);
@@ -1262,6 +1278,13 @@ gs_status gs_set_laplacian(gs_ctx* ctx, gs_laplacian kind, double rc_over_h) {
     return GS_OK;
 }
 
+gs_status gs_set_observer(gs_ctx* ctx, gs_observer fn, void* user) {
+    if (!ctx) return GS_ERR_INVALID;
+    ctx->obs = fn;
+    ctx->obs_user = fn ? user : nullptr;
+    return GS_OK;
+}
+
 gs_status gs_set_dcpse_tile(gs_ctx* ctx, int tz) {
     if (!ctx || (tz != 0 && tz != 4 && tz != 8)) return GS_ERR_INVALID;
     ctx->dcpse_tz = tz;
@@ -1289,12 +1312,59 @@ gs_status gs_set_small_grid_path(gs_ctx* ctx, int mode, int ctas) {
 
 int gs_get_small_grid_path(const gs_ctx* ctx) { return ctx && small_path(ctx) ? 1 : 0; }
 
+// Fixed steps with an observer: the step's loop graph runs one step per
+// launch, the device control block carried from launch to launch (step
+// limit raised, `done` cleared), so the step sequence, Dormand-Prince's
+// first-same-as-last k1 and the Adams-Bashforth history are those of one
+// uninterrupted run; after each step the state is copied to the caller's
+// buffers and observed.
+static gs_status step_observed(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps) {
+    const double t0 = *t;
+    gs_status st = GS_OK;
+    if (observe(ctx, t0, &st)) return st;
+    if (ctx->lap == 1) {
+        for (long n = 0; n < nsteps; ++n) {
+            st = ctx->p.prec == GS_FP64 ? dcpse_step<double>(ctx, method, t0 + (double)n * dt, dt, 1)
+                                        : dcpse_step<float>(ctx, method, t0 + (double)n * dt, dt, 1);
+            if (st != GS_OK) return st;
+            *t = t0 + (double)(n + 1) * dt;
+            if (observe(ctx, *t, &st) && n + 1 < nsteps) return st;
+        }
+        return st;
+    }
+    const int gid = method == GS_RK4 ? G_RK4 : method == GS_EULER ? G_EULER : G_DOPRI5_FIXED;
+    init_fixed_ctrl(ctx, t0, dt, 1);
+    if ((st = upload_ctrl(ctx)) != GS_OK) return st;
+    if (method == GS_DOPRI5) CK(launch_dopri5_k1(ctx, ctx->stream));
+    for (long n = 0; n < nsteps; ++n) {
+        if (n > 0) {
+            ctx->hpatch[0] = n + 1;
+            ctx->hpatch[1] = 0;
+            CK(cudaMemcpyAsync(&ctx->dctrl->step_limit, &ctx->hpatch[0], sizeof(long long), cudaMemcpyHostToDevice,
+                               ctx->stream));
+            CK(cudaMemcpyAsync(&ctx->dctrl->done, &ctx->hpatch[1], sizeof(int), cudaMemcpyHostToDevice,
+                               ctx->stream));
+        }
+        const int g = method == GS_AB4 ? (n < 3 ? G_AB4_START : G_AB4_MAIN) : gid;
+        cudaGraphExec_t ex;
+        if ((st = get_loop_graph(ctx, g, &ex)) != GS_OK) return st;
+        CK(cudaGraphLaunch(ex, ctx->stream));
+        CK(launch_copy_back(ctx));
+        if ((st = download_ctrl_sync(ctx)) != GS_OK) return st;
+        if (ctx->hctrl->status != GS_OK) return (gs_status)ctx->hctrl->status;
+        *t = t0 + (double)(n + 1) * dt;
+        if (ctx->obs(*t, ctx->state[0], ctx->state[1], ctx->obs_user) != 0 && n + 1 < nsteps) return GS_OK;
+    }
+    return GS_OK;
+}
+
 gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps) {
     if (!ctx || !t || !ctx->state[0] || nsteps < 0 || !std::isfinite(dt)) return GS_ERR_INVALID;
     if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER)
         return GS_ERR_INVALID;
     if (ctx->lap == 1 && method == GS_AB4) return GS_ERR_INVALID;
     if (nsteps == 0) return GS_OK;
+    if (ctx->obs) return step_observed(ctx, method, t, dt, nsteps);
     const double t0 = *t;
     gs_status st;
     if (ctx->lap == 1) {
@@ -1355,6 +1425,9 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         return ctx->p.prec == GS_FP64
                    ? dcpse_adaptive<double>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected)
                    : dcpse_adaptive<float>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
+    const bool obs = ctx->obs != nullptr;
+    gs_status st = GS_OK;
+    if (obs && observe(ctx, *t, &st)) return st;
     DevCtrl* h = ctx->hctrl;
     memset(h, 0, sizeof(DevCtrl));
     h->mode = CTRL_ADAPTIVE;
@@ -1364,7 +1437,8 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     h->dt = *dt;
     h->atol = atol;
     h->rtol = rtol;
-    h->max_acc = max_accepted < 0 ? -1 : max_accepted;
+    // with an observer the loop graph stops after every accepted step
+    h->max_acc = obs ? 1 : (max_accepted < 0 ? -1 : max_accepted);
     h->max_att = kMaxAttempts;
     h->log_dt = ctx->dlog;
     h->log_cap = ctx->log_cap;
@@ -1375,14 +1449,38 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     }
     if (!(ht > 0.0) || h->t + ht == h->t) return GS_ERR_STEP_UNDERFLOW;
     h->dt_try = ht;
-    gs_status st;
     if ((st = upload_ctrl(ctx)) != GS_OK) return st;
     CK(launch_dopri5_k1(ctx, ctx->stream));
     cudaGraphExec_t ex;
     if ((st = get_loop_graph(ctx, G_DOPRI5_ADAPT, &ex)) != GS_OK) return st;
-    CK(cudaGraphLaunch(ex, ctx->stream));
-    CK(launch_copy_back(ctx));
-    if ((st = download_ctrl_sync(ctx)) != GS_OK) return st;
+    for (;;) {
+        CK(cudaGraphLaunch(ex, ctx->stream));
+        CK(launch_copy_back(ctx));
+        if ((st = download_ctrl_sync(ctx)) != GS_OK) return st;
+        if (!obs || h->status != GS_OK) break;
+        const bool stop = ctx->obs(h->t, ctx->state[0], ctx->state[1], ctx->obs_user) != 0;
+        if (stop || !(h->t < t_end) || (max_accepted >= 0 && h->n_acc >= max_accepted)) break;
+        // the next attempt, prepared as the device controller prepares it
+        // when it continues (the control block is the device's own copy)
+        if (h->n_att >= h->max_att) {
+            h->status = GS_ERR_MAX_STEPS;
+            break;
+        }
+        ht = h->dt;
+        h->last = 0;
+        if (h->t + ht >= t_end) {
+            ht = t_end - h->t;
+            h->last = 1;
+        }
+        if (!(ht > 0.0) || h->t + ht == h->t) {
+            h->status = GS_ERR_STEP_UNDERFLOW;
+            break;
+        }
+        h->dt_try = ht;
+        h->max_acc = h->n_acc + 1;
+        h->done = 0;
+        if ((st = upload_ctrl(ctx)) != GS_OK) return st;
+    }
     *t = h->t;
     *dt = h->dt;
     if (n_accepted) *n_accepted = (long)h->n_acc;
