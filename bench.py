@@ -57,15 +57,16 @@ STAGE_FIELDS_SPLIT = [2, 3, 4, 5, 6, 9, 4]
 PAIR_NAMES = ["k1", "stages2+3", "stages4+5", "stages6+7"]
 PAIR_FIELDS = [2, 4, 6, 8]
 BYTES_PER_FIELD_CELL = 8
+BATCH_BYTES_PER_CELL_ATTEMPT = 33 * BYTES_PER_FIELD_CELL  # batched path: single-stage schedule, FP32
 NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside the measured copy peak)
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 842.7 MB read + 245.3 MB written), per cell so that other grids scale by
+# 841.8 MB read + 245.2 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "0c73f867a8f69359",
-               "bytes_per_cell": (842731776 + 245303552) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "45ba1093e747dcd3",
+               "bytes_per_cell": (841838080 + 245218048) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
@@ -466,10 +467,19 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
         den += float((g.u.double() ** 2).sum() + (g.v.double() ** 2).sum())
         g.close()
     b.close()
+    # algorithmic bytes: every attempt of an instance moves its cells' 33
+    # field passes of the single-stage schedule (k1 reused)
+    attempts_cells = float(np.sum(cells * (rb["n_acc"] + rb["n_rej"])))
+    achieved = attempts_cells * BATCH_BYTES_PER_CELL_ATTEMPT / (ms_b * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
     return {"gs_batched_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_b, "cell_steps_per_s": work_b / (ms_b * 1e-3), "accepted_total": int(rb["n_acc"].sum()),
         "rejected_total": int(rb["n_rej"].sum()), "cells_total": int(cells.sum()), "tile_ty_zc": [tile[0], tile[1]],
-        "instance_groups": groups[1], "group_budget_cells": groups[0]},
+        "instance_groups": groups[1], "group_budget_cells": groups[0],
+        "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_cell_attempt": BATCH_BYTES_PER_CELL_ATTEMPT,
+                     "cell_attempts": attempts_cells}},
         "gs_per_instance_loop_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_s, "cell_steps_per_s": work_s / (ms_s * 1e-3), "accepted_total": int(acc_s.sum())},
         "batched_speedup_vs_per_instance_loop": (work_b / ms_b) / (work_s / ms_s),
