@@ -475,10 +475,11 @@ gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void*
 /* Tensor-core engine of sur_conv3d (and of the network's convolutions),
  * process-wide: 0 = automatic (tcgen05 where it applies, else mma.sync),
  * 1 = warp-level mma.sync m16n8k16 for every shape, 2 = tcgen05 where it
- * applies.  The tcgen05 kernel covers 32 -> 32 channels with epi 0, 2 or 3
- * on grids with D % 4 == 0, H % 16 == 0, W % 16 == 0 (accumulators in tensor
- * memory, operands read from shared memory through matrix descriptors),
- * and the 32 x 32 weight gradient (sur_conv3d_wgrad) on grids with
+ * applies.  The tcgen05 kernel covers 32 -> 32 and 8 -> 32 channels with
+ * epi 0, 2 or 3 and 32 -> 8 channels with epi 1 or 3, on grids with
+ * D % 4 == 0, H % 16 == 0, W % 8 == 0 (accumulators in tensor memory,
+ * operands read from shared memory through matrix descriptors), and the
+ * 32 x 32 weight gradient (sur_conv3d_wgrad) on grids with
  * H % 16 == 0, W % 8 == 0; other shapes always take mma.sync.  Both compute the same sums of exact
  * BF16 products in FP32 (summation order differs).  INVALID for other
  * values.  sur_conv_last_engine: 1 or 2, the engine of the last launch (0
