@@ -21,6 +21,7 @@ from . import GS_FP32, GS_RK4, GrayScott, Surrogate, lib
 
 DT = 0.1
 STEPS = 16  # steps per surrogate advance: 1.6 time units
+JUDGE_EVERY = 10  # advances per judged advance in the reported speed-up
 
 
 def generate_snapshots(torch, n=128, trajectories=8, per_traj=250, seed0=0, Du=2e-5, Dv=1e-5, F=0.053, k=0.014):
@@ -195,6 +196,27 @@ def run(torch, n=128, trajectories=8, per_traj=250, iters=2000, threshold=1e-3, 
     rel, fb = sur.advance(g.ctx, g.u, g.v, judge=True, threshold=threshold)
     res["judge_rel_l2"] = rel
     res["judge_fell_back"] = fb
+    # wall time of the public calls (each synchronises): an advance, plain
+    # and judged, and the 16 RK4 steps at dt = 0.1 it stands for; the
+    # speed-up with one judged advance in every JUDGE_EVERY
+    def call_ms(fn, reps):
+        ts = []
+        for _ in range(reps):
+            g.u.view(-1).copy_(a[0])
+            g.v.view(-1).copy_(a[1])
+            torch.cuda.synchronize()
+            t_0 = time.perf_counter()
+            fn()
+            ts.append((time.perf_counter() - t_0) * 1e3)
+        return float(np.median(ts))
+    plain_ms = call_ms(lambda: sur.advance(g.ctx, g.u, g.v, judge=False, threshold=threshold), 7)
+    judged_ms = call_ms(lambda: sur.advance(g.ctx, g.u, g.v, judge=True, threshold=threshold), 5)
+    rk4_ms = call_ms(lambda: g.step(GS_RK4, 0.0, 0.1, STEPS), 7)
+    per_call = ((JUDGE_EVERY - 1) * plain_ms + judged_ms) / JUDGE_EVERY
+    res["advance"] = {"plain_ms": plain_ms, "judged_ms": judged_ms, "judge_every": JUDGE_EVERY,
+                      "ms_per_call": per_call, "rk4_dt0.1_call_ms": rk4_ms,
+                      "speedup_vs_rk4_dt0.1_with_judging": rk4_ms / per_call,
+                      "speedup_vs_rk4_dt0.1_unjudged": rk4_ms / plain_ms}
     g.close()
     sur.close()
     del data
