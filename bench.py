@@ -261,8 +261,31 @@ def extra_workloads(torch, gs, si):
     gs.gs_set_small_grid_path(g.ctx, -1, 0)
     out["gs_32cubed_fp64_rk4_dt0.1_x100"]["launch_paths"] = paths
     g.close()
-    # pointwise ODEs, 2^24 FP64
+    # the Algebra's linear combination y = sum_j a_j x_j (ode_axpy_stage),
+    # 2^24 FP64 elements per operand (128 MB, so every call streams from
+    # HBM): nterms + 1 arrays moved per call
     m = 1 << 24
+    peak_hbm, peak_kind = _peaks()
+    xs = [torch.rand(m, dtype=torch.float64, device="cuda") for _ in range(15)]
+    yv = torch.empty(m, dtype=torch.float64, device="cuda")
+    for nt in (2, 7, 15):
+        coef = [1.0 / (j + 1) for j in range(nt)]
+        for _ in range(3):
+            gs.ode_axpy_stage(coef, xs[:nt], yv)
+        a, b = ev(), ev()
+        a.record(stream)
+        for _ in range(10):
+            gs.ode_axpy_stage(coef, xs[:nt], yv)
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        gbs = (nt + 1) * 8 * m / (ms * 1e-3) / 1e9
+        out[f"ode_axpy_stage_fp64_2^24_nterms{nt}"] = {
+            "ms": ms, "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peak_hbm,
+                                   "frac": gbs / peak_hbm, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                                   "algorithmic_bytes": (nt + 1) * 8 * m}}
+    del xs, yv
+    # pointwise ODEs, 2^24 FP64
     x0 = torch.from_numpy(si.ode_initial_values(m, seed=1)).cuda()
     ws = torch.empty(gs.ode_workspace_size(m), dtype=torch.uint8, device="cuda")
     for kind, name in ((gs.ODE_EXP_DECAY, "exp_decay"), (gs.ODE_LOGISTIC, "logistic")):

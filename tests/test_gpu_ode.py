@@ -98,7 +98,7 @@ def test_full_size_ab4_sampled(kind, okind):
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("nterms", [1, 2, 7, 15])
-@pytest.mark.parametrize("n", [1, 5, 4096, 10007])
+@pytest.mark.parametrize("n", [1, 5, 4096, 10007, 3000017])  # the last: several chunks per warp
 def test_axpy_stage(prec, nterms, n):
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
