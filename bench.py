@@ -262,29 +262,37 @@ def extra_workloads(torch, gs, si):
     out["gs_32cubed_fp64_rk4_dt0.1_x100"]["launch_paths"] = paths
     g.close()
     # the Algebra's linear combination y = sum_j a_j x_j (ode_axpy_stage),
-    # 2^24 FP64 elements per operand (128 MB, so every call streams from
-    # HBM): nterms + 1 arrays moved per call
-    m = 1 << 24
+    # 128 MB per operand (2^25 FP32 / 2^24 FP64 elements, so every call
+    # streams from HBM): nterms + 1 arrays moved per call.  In FP64 each
+    # operand element costs one FP64 FMA, which with many operands makes the
+    # FP64 pipe the bound: that fraction is reported beside the HBM one.
     peak_hbm, peak_kind = _peaks()
-    xs = [torch.rand(m, dtype=torch.float64, device="cuda") for _ in range(15)]
-    yv = torch.empty(m, dtype=torch.float64, device="cuda")
-    for nt in (2, 7, 15):
-        coef = [1.0 / (j + 1) for j in range(nt)]
-        for _ in range(3):
-            gs.ode_axpy_stage(coef, xs[:nt], yv)
-        a, b = ev(), ev()
-        a.record(stream)
-        for _ in range(10):
-            gs.ode_axpy_stage(coef, xs[:nt], yv)
-        b.record(stream)
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 10
-        gbs = (nt + 1) * 8 * m / (ms * 1e-3) / 1e9
-        out[f"ode_axpy_stage_fp64_2^24_nterms{nt}"] = {
-            "ms": ms, "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peak_hbm,
-                                   "frac": gbs / peak_hbm, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                                   "algorithmic_bytes": (nt + 1) * 8 * m}}
-    del xs, yv
+    for dt, m, tag in ((torch.float32, 1 << 25, "fp32_2^25"), (torch.float64, 1 << 24, "fp64_2^24")):
+        es = 4 if dt == torch.float32 else 8
+        xs = [torch.rand(m, dtype=dt, device="cuda") for _ in range(15)]
+        yv = torch.empty(m, dtype=dt, device="cuda")
+        for nt in (2, 7, 15):
+            coef = [1.0 / (j + 1) for j in range(nt)]
+            for _ in range(3):
+                gs.ode_axpy_stage(coef, xs[:nt], yv)
+            a, b = ev(), ev()
+            a.record(stream)
+            for _ in range(10):
+                gs.ode_axpy_stage(coef, xs[:nt], yv)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / 10
+            gbs = (nt + 1) * es * m / (ms * 1e-3) / 1e9
+            ent = {"ms": ms, "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peak_hbm,
+                                          "frac": gbs / peak_hbm,
+                                          "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                                          "algorithmic_bytes": (nt + 1) * es * m}}
+            if es == 8:
+                ent["fp64_roofline"] = fp64_roofline(nt * m, ms, {"element": nt})
+            out[f"ode_axpy_stage_{tag}_nterms{nt}"] = ent
+        del xs, yv
+        torch.cuda.empty_cache()
+    m = 1 << 24
     # pointwise ODEs, 2^24 FP64
     x0 = torch.from_numpy(si.ode_initial_values(m, seed=1)).cuda()
     ws = torch.empty(gs.ode_workspace_size(m), dtype=torch.uint8, device="cuda")
