@@ -202,11 +202,13 @@ def test_split_stages_match_unsplit_and_oracle(prec, dims):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("nsteps,ctas", [(7, 0), (8, 1), (5, 3), (20, 37)])
+@pytest.mark.parametrize("nsteps,ctas", [(7, 0), (8, 1), (5, 3), (20, 37), (6, 600), (4, 5000)])
 def test_rk4_small_grid_path_matches_graph_path(prec, nsteps, ctas):
     """Fixed-step RK4 in one cooperative launch (grid barrier between stages)
     against the four-kernel graph path and the oracle; odd and even step
-    counts (copy-back), CTA counts that do and do not divide the cells."""
+    counts (copy-back), CTA counts that do and do not divide the cells, and
+    CTA counts far above the cells' need, up to the resident limit the launch
+    caps 5000 to."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     dims = (20, 12, 9)
