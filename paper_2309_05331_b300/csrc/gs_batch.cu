@@ -57,8 +57,12 @@ constexpr int kStageCtrs = 6;  // segment counters per group: stages 2..7 (count
 // buffer, k1..k7, two components each
 constexpr int kCellFields = 2 * 9;
 
+// FP32: registers capped for 4 CTAs of 256 threads per SM (stage kernels,
+// 64) or 3 (the final kernel, 85): the segment code prefetches a plane of
+// raw inputs into registers and would otherwise halve its occupancy
 template <typename T, int NK, int MODE>
-__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256)
+__global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256,
+                                  sizeof(T) == 4 ? (MODE == MODE_STAGE ? 2 : 3) : 1)
     gsb_stage_kernel(const BInst* __restrict__ insts, DevCtrl* ctrls, const BSeg* __restrict__ segs, int nseg,
                      unsigned int* counter, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -201,12 +201,24 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
 
     auto sidx = [&](int buf, int ww, int c, int col) -> int { return ((buf * TYP + ww) * 2 + c) * PITCH + col; };
 
-    // Y of VX cells at idx, and the epilogue's per-cell values
-    auto loadY = [&](long long idx, T (&Y)[2][VX], Carry<T, NK, MODE, VX>& cr) {
+    // Y of VX cells at idx, and the epilogue's per-cell values: the raw
+    // inputs (fetch), then the arithmetic on them (form)
+    struct Raw {
+        T u[2][VX];
+        T k[NK > 0 ? NK : 1][2][VX];
+    };
+    auto fetchY = [&](long long idx, Raw& R) {
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            T uu[VX];
-            ldv<T, VX>(P.u[c] + idx, uu);
+            ldv<T, VX>(P.u[c] + idx, R.u[c]);
+#pragma unroll
+            for (int j = 0; j < NK; ++j) ldv<T, VX>(P.k[j][c] + idx, R.k[j][c]);
+        }
+    };
+    auto formY = [&](const Raw& R, T (&Y)[2][VX], Carry<T, NK, MODE, VX>& cr) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const T* uu = R.u[c];
             T s[VX], k1[VX], q[VX];
 #pragma unroll
             for (int v = 0; v < VX; ++v) {
@@ -216,8 +228,7 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
             }
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
-                T kk[VX];
-                ldv<T, VX>(P.k[j][c] + idx, kk);
+                const T* kk = R.k[j][c];
 #pragma unroll
                 for (int v = 0; v < VX; ++v) {
                     s[v] = (j == 0) ? C.a[0] * kk[v] : s[v] + C.a[j] * kk[v];
@@ -242,14 +253,35 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
             }
         }
     };
-    // Y of one cell (x-halo column)
-    auto loadY1 = [&](long long idx, int c) -> T {
-        const T uu = __ldg(P.u[c] + idx);
-        if (NK == 0) return uu;
-        T s = C.a[0] * __ldg(P.k[0][c] + idx);
+    auto loadY = [&](long long idx, T (&Y)[2][VX], Carry<T, NK, MODE, VX>& cr) {
+        Raw R;
+        fetchY(idx, R);
+        formY(R, Y, cr);
+    };
+    // Y of one cell (x-halo column), from its raw inputs
+    struct RawH {
+        T u[2];
+        T k[NK > 0 ? NK : 1][2];
+    };
+    auto fetchY1 = [&](long long idx, RawH& R) {
 #pragma unroll
-        for (int j = 1; j < NK; ++j) s += C.a[j] * __ldg(P.k[j][c] + idx);
-        return uu + dt * s;
+        for (int c = 0; c < 2; ++c) {
+            R.u[c] = __ldg(P.u[c] + idx);
+#pragma unroll
+            for (int j = 0; j < NK; ++j) R.k[j][c] = __ldg(P.k[j][c] + idx);
+        }
+    };
+    auto formY1 = [&](const RawH& R, int c) -> T {
+        if (NK == 0) return R.u[c];
+        T s = C.a[0] * R.k[0][c];
+#pragma unroll
+        for (int j = 1; j < NK; ++j) s += C.a[j] * R.k[j][c];
+        return R.u[c] + dt * s;
+    };
+    auto loadY1 = [&](long long idx, int c) -> T {
+        RawH R;
+        fetchY1(idx, R);
+        return formY1(R, c);
     };
 
     const int x0 = tx * TXW, y0 = tyi * TY;
@@ -281,17 +313,36 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
     }
     if (do_halo)
         for (int c = 0; c < 2; ++c) S[sidx(0, hrow, c, hcol)] = loadY1(hbase + plane * z0, c);
+    // One cell per lane (VX = 1) leaves few bytes in flight per thread, so
+    // the row cells' raw inputs of plane z+2 are fetched into registers
+    // while plane z is computed and formed one iteration later (PF); wider
+    // vectors load plane z+1 in the iteration that needs it.
+    constexpr bool PF = VX == 1;
+    Raw rn;
+    if (PF && act) fetchY(cbase + plane * wrap1(z0 + 1, nz), rn);
     int bz = 0;  // ring buffer of plane z
     for (int z = z0; z < z1; ++z) {
         const int bn = (bz == 2) ? 0 : bz + 1;  // ring buffer of plane z+1
-        const long long zoff = plane * wrap1(z + 1, nz);
-        if (act) {
-            loadY(cbase + zoff, yp, nxt);
+        if (PF) {
+            if (act) {
+                formY(rn, yp, nxt);
 #pragma unroll
-            for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
+                for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
+            }
+            if (do_halo)  // two lanes per row: loaded where they are needed
+                for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + plane * wrap1(z + 1, nz), c);
+            if (act && z + 1 < z1)  // plane z+2 is the upper neighbour of the next iteration
+                fetchY(cbase + plane * wrap1(z + 2, nz), rn);
+        } else {
+            const long long zoff = plane * wrap1(z + 1, nz);
+            if (act) {
+                loadY(cbase + zoff, yp, nxt);
+#pragma unroll
+                for (int c = 0; c < 2; ++c) stv<T, VX>(S + sidx(bn, w, c, VX * lane), yp[c]);
+            }
+            if (do_halo)
+                for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
         }
-        if (do_halo)
-            for (int c = 0; c < 2; ++c) S[sidx(bn, hrow, c, hcol)] = loadY1(hbase + zoff, c);
         __syncthreads();
         T xl[2], xr[2];
 #pragma unroll
