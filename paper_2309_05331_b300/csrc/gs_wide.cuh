@@ -258,30 +258,14 @@ __device__ __forceinline__ void wide_segment(const Geom<T>& g, const StagePtrs<T
         fetchY(idx, R);
         formY(R, Y, cr);
     };
-    // Y of one cell (x-halo column), from its raw inputs
-    struct RawH {
-        T u[2];
-        T k[NK > 0 ? NK : 1][2];
-    };
-    auto fetchY1 = [&](long long idx, RawH& R) {
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            R.u[c] = __ldg(P.u[c] + idx);
-#pragma unroll
-            for (int j = 0; j < NK; ++j) R.k[j][c] = __ldg(P.k[j][c] + idx);
-        }
-    };
-    auto formY1 = [&](const RawH& R, int c) -> T {
-        if (NK == 0) return R.u[c];
-        T s = C.a[0] * R.k[0][c];
-#pragma unroll
-        for (int j = 1; j < NK; ++j) s += C.a[j] * R.k[j][c];
-        return R.u[c] + dt * s;
-    };
+    // Y of one cell (x-halo column)
     auto loadY1 = [&](long long idx, int c) -> T {
-        RawH R;
-        fetchY1(idx, R);
-        return formY1(R, c);
+        const T uu = __ldg(P.u[c] + idx);
+        if (NK == 0) return uu;
+        T s = C.a[0] * __ldg(P.k[0][c] + idx);
+#pragma unroll
+        for (int j = 1; j < NK; ++j) s += C.a[j] * __ldg(P.k[j][c] + idx);
+        return uu + dt * s;
     };
 
     const int x0 = tx * TXW, y0 = tyi * TY;
