@@ -4,13 +4,17 @@ so that a profiler sees each launch.
     python -m paper_2309_05331_b300.kernel_timing dcpse --grid 64 --method rk4 --steps 20
     python -m paper_2309_05331_b300.kernel_timing dp5 --n 1048576 --rhs 0
     python -m paper_2309_05331_b300.kernel_timing ab4 --n 16777216 --rhs 1 --steps 1000
+    python -m paper_2309_05331_b300.kernel_timing batch --count 512
 
 dcpse: the Gray-Scott run with the DC-PSE Laplacian (Du = 2e-4, Dv = 1e-4,
 F = 0.053, k = 0.014, FP64, fixed steps of dt = 1).  dp5: error-controlled
 Dormand-Prince on n independent elements through the allocation-free entry
 point (whose attempts are launched one by one), atol = rtol = 1e-8, t: 0 -> 10.
-ab4: Adams-Bashforth 4, dt = 1e-3.  Seeded synthetic inputs; prints one JSON
-line with the wall time (after a warm-up run) of the call.
+ab4: Adams-Bashforth 4, dt = 1e-3.  batch: the ensemble of `count` uneven
+Gray-Scott instances (FP32) and the batched integrator's autotuner, whose
+timing rounds launch every Dormand-Prince stage of the whole batch directly.
+Seeded synthetic inputs; prints one JSON line with the wall time (after a
+warm-up run) of the call.
 """
 from __future__ import annotations
 
@@ -28,7 +32,8 @@ def main(argv=None):
     from . import GS_DOPRI5, GS_FP64, GS_LAP_DCPSE, GS_RK4, GrayScott, gs_set_laplacian, lib, ode_integrate_ab4
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("what", choices=["dcpse", "dp5", "ab4"])
+    ap.add_argument("what", choices=["dcpse", "dp5", "ab4", "batch"])
+    ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--method", choices=["rk4", "dopri5"], default="rk4")
     ap.add_argument("--steps", type=int, default=20)
@@ -69,6 +74,18 @@ def main(argv=None):
         run()
         ms, na, nr = run()
         res.update(n=a.n, rhs=a.rhs, ms=ms, accepted=na, rejected=nr)
+    elif a.what == "batch":
+        from . import GS_FP32, GrayScottBatch
+        insts = si.batch_instances(a.count, seed=3)
+        b = GrayScottBatch(insts, L=2.5, Du=2e-5, Dv=1e-5, prec=GS_FP32)
+        for i, d in enumerate(insts):
+            u, v = si.gs_initial_state(d["nx"], d["ny"], d["nz"], seed=1000 + i)
+            b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
+        t0 = time.perf_counter()
+        ty, zc, ms = b.autotune()
+        res.update(count=a.count, cells=int(sum(d["nx"] * d["ny"] * d["nz"] for d in insts)), tile=[ty, zc],
+                   round_ms=ms, ms=(time.perf_counter() - t0) * 1e3)
+        b.close()
     else:
         x0 = torch.from_numpy(si.ode_initial_values(a.n, seed=1)).cuda()
 
