@@ -274,6 +274,14 @@ __global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __rest
 // step that no longer advances t (STEP_UNDERFLOW), on a non-finite error
 // (NONFINITE), or after kMaxElementAttempts attempts (MAX_STEPS), which
 // bounds the kernel's run time.
+//
+// Elements need from a few to hundreds of attempts, so a lane that kept one
+// element until the slowest lane of its warp finished would idle.  Each warp
+// owns a contiguous chunk of the elements instead, and a lane whose element
+// has stopped takes the chunk's next one (a ballot; the chunk cursor is the
+// same register value in every lane): every loop iteration is one attempt
+// of whichever element each lane holds.  An element's arithmetic is the same
+// in either order.
 constexpr long long kMaxElementAttempts = 1LL << 22;
 
 template <int KIND, class TB>
@@ -284,18 +292,40 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                                                              double* t_out, double* dt_out, long* na_out,
                                                              long* nr_out, int* st_out) {
     const double grow_floor = pow(5.0, -(double)TB::P);
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        double u = x[i];
-        const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
-        double t = t0, dt = dt0;
-        long long na = 0, nr = 0, consec = 0, att = 0;
-        int st = GS_OK;
-        while (t < t_end && (max_acc < 0 || na < max_acc)) {
-            if (++att > kMaxElementAttempts) {
-                st = GS_ERR_MAX_STEPS;
-                break;
+    const unsigned lane = threadIdx.x & 31u;
+    const long long nwarp = (long long)gridDim.x * (blockDim.x / 32);
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const long long chunk = (n + nwarp - 1) / nwarp;
+    long long cursor = gw * chunk;                        // next unclaimed element of this warp's chunk
+    const long long cend = cursor + chunk < n ? cursor + chunk : n;
+    long long i = -1;                                     // element in hand (-1: none)
+    double u = 0.0, cf = 0.0, t = 0.0, dt = 0.0;
+    long long na = 0, nr = 0, consec = 0, att = 0;
+    int st = GS_OK;
+    for (;;) {
+        const unsigned need = __ballot_sync(0xffffffffu, i < 0 && cursor < cend);
+        if (i < 0 && cursor < cend) {
+            const long long j = cursor + __popc(need & ((1u << lane) - 1u));
+            if (j < cend) {
+                i = j;
+                u = x[i];
+                cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
+                t = t0;
+                dt = dt0;
+                na = nr = consec = att = 0;
+                st = GS_OK;
             }
+        }
+        cursor += __popc(need);
+        if (__ballot_sync(0xffffffffu, i >= 0) == 0u) break;  // the chunk is done
+        if (i < 0) continue;
+        bool fin = false;
+        if (!(t < t_end && (max_acc < 0 || na < max_acc))) {
+            fin = true;
+        } else if (++att > kMaxElementAttempts) {
+            st = GS_ERR_MAX_STEPS;
+            fin = true;
+        } else {
             bool last = false;
             double h = dt;
             if (t + dt >= t_end) {
@@ -304,37 +334,48 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
             }
             if (!(h > 0.0) || t + h == t) {
                 st = GS_ERR_STEP_UNDERFLOW;
-                break;
-            }
-            double err, k1;
-            const double y = tab_step<KIND, TB, true>(u, t, h, cf, err, k1);
-            const double E = fabs(err) / (atol + rtol * (fabs(u) + h * fabs(k1)));
-            if (!isfinite(E)) {
-                st = GS_ERR_NONFINITE;
-                break;
-            }
-            if (E > 1.0) {
-                ++nr;
-                ++consec;
-                dt = h * fmax(0.9 * pow(E, -1.0 / (double)(TB::Q - 1)), 0.2);
-                if (consec >= max_rej) {
-                    st = GS_ERR_STEP_UNDERFLOW;
-                    break;
+                fin = true;
+            } else {
+                double err, k1;
+                const double y = tab_step<KIND, TB, true>(u, t, h, cf, err, k1);
+                const double E = fabs(err) / (atol + rtol * (fabs(u) + h * fabs(k1)));
+                if (!isfinite(E)) {
+                    st = GS_ERR_NONFINITE;
+                    fin = true;
+                } else {
+                    // one pow for the rejecting and the accepting lanes
+                    // alike (its arguments selected per lane), so a warp
+                    // holding both does not run the power twice
+                    const bool rej = E > 1.0;
+                    const double pw = pow(rej ? E : fmax(E, grow_floor),
+                                          rej ? -1.0 / (double)(TB::Q - 1) : -1.0 / (double)TB::P);
+                    if (rej) {
+                        ++nr;
+                        ++consec;
+                        dt = h * fmax(0.9 * pw, 0.2);
+                        if (consec >= max_rej) {
+                            st = GS_ERR_STEP_UNDERFLOW;
+                            fin = true;
+                        }
+                    } else {
+                        consec = 0;
+                        u = y;
+                        ++na;
+                        t = last ? t_end : t + h;
+                        dt = E < 0.5 ? h * 0.9 * pw : h;
+                    }
                 }
-                continue;
             }
-            consec = 0;
-            u = y;
-            ++na;
-            t = last ? t_end : t + h;
-            dt = E < 0.5 ? h * 0.9 * pow(fmax(E, grow_floor), -1.0 / (double)TB::P) : h;
         }
-        x[i] = u;
-        if (t_out) t_out[i] = t;
-        if (dt_out) dt_out[i] = dt;
-        if (na_out) na_out[i] = (long)na;
-        if (nr_out) nr_out[i] = (long)nr;
-        if (st_out) st_out[i] = st;
+        if (fin) {
+            x[i] = u;
+            if (t_out) t_out[i] = t;
+            if (dt_out) dt_out[i] = dt;
+            if (na_out) na_out[i] = (long)na;
+            if (nr_out) nr_out[i] = (long)nr;
+            if (st_out) st_out[i] = st;
+            i = -1;
+        }
     }
 }
 

@@ -5,6 +5,7 @@ so that a profiler sees each launch.
     python -m paper_2309_05331_b300.kernel_timing dp5 --n 1048576 --rhs 0
     python -m paper_2309_05331_b300.kernel_timing ab4 --n 16777216 --rhs 1 --steps 1000
     python -m paper_2309_05331_b300.kernel_timing batch --count 512
+    python -m paper_2309_05331_b300.kernel_timing each --n 16777216 --rhs 0
 
 dcpse: the Gray-Scott run with the DC-PSE Laplacian (Du = 2e-4, Dv = 1e-4,
 F = 0.053, k = 0.014, FP64, fixed steps of dt = 1).  dp5: error-controlled
@@ -13,6 +14,8 @@ point (whose attempts are launched one by one), atol = rtol = 1e-8, t: 0 -> 10.
 ab4: Adams-Bashforth 4, dt = 1e-3.  batch: the ensemble of `count` uneven
 Gray-Scott instances (FP32) and the batched integrator's autotuner, whose
 timing rounds launch every Dormand-Prince stage of the whole batch directly.
+each: Dormand-Prince with every element its own step size (one launch),
+atol = rtol = 1e-8, t: 0 -> 10.
 Seeded synthetic inputs; prints one JSON line with the wall time (after a
 warm-up run) of the call.
 """
@@ -32,7 +35,7 @@ def main(argv=None):
     from . import GS_DOPRI5, GS_FP64, GS_LAP_DCPSE, GS_RK4, GrayScott, gs_set_laplacian, lib, ode_integrate_ab4
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("what", choices=["dcpse", "dp5", "ab4", "batch"])
+    ap.add_argument("what", choices=["dcpse", "dp5", "ab4", "batch", "each"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--method", choices=["rk4", "dopri5"], default="rk4")
@@ -86,6 +89,20 @@ def main(argv=None):
         res.update(count=a.count, cells=int(sum(d["nx"] * d["ny"] * d["nz"] for d in insts)), tile=[ty, zc],
                    round_ms=ms, ms=(time.perf_counter() - t0) * 1e3)
         b.close()
+    elif a.what == "each":
+        from . import ODE_TAB_DOPRI5, ode_integrate_adaptive_each
+        x0 = torch.from_numpy(si.ode_initial_values(a.n, seed=1)).cuda()
+
+        def run():
+            x = x0.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ode_integrate_adaptive_each(a.rhs, ODE_TAB_DOPRI5, x, 0.0, 10.0, 1e-3, 1e-8, 1e-8)
+            torch.cuda.synchronize()
+            return (time.perf_counter() - t0) * 1e3, int(r["n_acc"].sum()), int(r["n_rej"].sum())
+        run()
+        ms, na, nr = run()
+        res.update(n=a.n, rhs=a.rhs, ms=ms, accepted=na, rejected=nr)
     else:
         x0 = torch.from_numpy(si.ode_initial_values(a.n, seed=1)).cuda()
 
