@@ -18,8 +18,11 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   Dopri5)                      polynomial exactness, observed orders
   dopri5 error estimate        pinned: local error order 5 (ratio ~32)
   integrate_adaptive           pinned: closed-form error within C*tol; tol
-                               scaling.  The controller formula itself is this
-                               build's reading (paper silent)
+                               scaling; every attempt (h, E, accept) of runs on
+                               dx/dt = -x against the stability polynomials of
+                               the tableau and the stated controller reading
+                               (paper silent on the formula), each constant of
+                               which a perturbed copy must fail to reproduce
   integrate_ab4                pinned: cubic exactness, observed order 4
   CK54 / RKF78 tableaux        pinned: Butcher order conditions (orders 5/4,
                                8/7) and observed orders
@@ -100,6 +103,9 @@ def lib():
                                                   C.c_double, C.c_double, C.c_long, C.c_long,
                                                   C.POINTER(C.c_long), C.POINTER(C.c_long), _dp, C.c_long]
         _lp = C.POINTER(C.c_long)
+        L.orc_pw_integrate_adaptive_trace.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, _dp, C.c_double, _dp,
+                                                      C.c_double, C.c_double, C.c_long, C.c_long, _lp, _lp, _dp,
+                                                      _dp, C.POINTER(C.c_int), C.c_long, _lp]
         L.orc_pw_integrate_adaptive_each.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, C.c_double,
                                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_long,
                                                      C.c_long, _dp, _dp, _lp, _lp, C.POINTER(C.c_int)]
@@ -325,6 +331,26 @@ def pw_integrate_adaptive(kind, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_r
                                            _p(log) if log_cap else None, log_cap)
     return {"x": x, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
             "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
+
+
+def pw_integrate_adaptive_trace(kind, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500, coef=None,
+                                method=DOPRI5, cap=100000):
+    """pw_integrate_adaptive plus the record of every attempt: arrays h, E
+    and accepted (bool), one entry per attempt in order."""
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    t = C.c_double(t0)
+    dt = C.c_double(dt0)
+    na, nr, natt = C.c_long(0), C.c_long(0), C.c_long(0)
+    th = np.zeros(cap)
+    tE = np.zeros(cap)
+    ta = np.zeros(cap, dtype=np.int32)
+    st = lib().orc_pw_integrate_adaptive_trace(method, kind, _p(c), x.size, _p(x), C.byref(t), t_end, C.byref(dt),
+                                               atol, rtol, max_acc, max_rej, C.byref(na), C.byref(nr), _p(th),
+                                               _p(tE), ta.ctypes.data_as(C.POINTER(C.c_int)), cap, C.byref(natt))
+    m = min(natt.value, cap)
+    return {"x": x, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
+            "h": th[:m].copy(), "E": tE[:m].copy(), "accepted": ta[:m].astype(bool)}
 
 
 def pw_integrate_ab4(kind, x, dt, nsteps, t0=0.0, coef=None):

@@ -529,11 +529,15 @@ enum { ORC_OK = 0, ORC_ERR_INVALID = 1, ORC_ERR_NOMEM = 3, ORC_ERR_STEP_UNDERFLO
  * On accept t += h (t = t_end exactly on a clipped step).  The loop ends when
  * t reaches t_end or after max_acc accepted steps (max_acc < 0: no limit).
  * If log_dt != NULL the accepted step sizes are written there (up to log_cap).
+ * The core also records every attempt (its size h, its norm E, whether it
+ * was accepted) when given trace arrays: the controller pins replay that
+ * record against the closed-form error of dx/dt = -x.
  */
-int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
+static int orc_adaptive_core(int method, orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
                              double t_end, double* dt_io, double atol, double rtol, long max_acc,
                              long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
-                             long log_cap) {
+                             long log_cap, double* trace_h, double* trace_E, int* trace_acc,
+                             long trace_cap, long* n_trace) {
     orc_tableau T;
     int po = 0, qo = 0;
     if (orc_get_tableau(method, &T) || orc_pair_orders(method, &po, &qo)) return ORC_ERR_INVALID;
@@ -544,7 +548,7 @@ int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, 
     double* err = (double*)malloc(sizeof(double) * (size_t)n);
     if (!k || !ytmp || !ynew || !err) { free(k); free(ytmp); free(ynew); free(err); return ORC_ERR_NOMEM; }
     double t = *t_io, dt = *dt_io;
-    long n_acc = 0, n_rej = 0, consec = 0;
+    long n_acc = 0, n_rej = 0, consec = 0, n_att = 0;
     int status = ORC_OK;
     while (t < t_end && (max_acc < 0 || n_acc < max_acc)) {
         int last = 0;
@@ -552,6 +556,12 @@ int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, 
         if (t + dt >= t_end) { h = t_end - t; last = 1; }
         if (!(h > 0.0) || t + h == t) { status = ORC_ERR_STEP_UNDERFLOW; break; }
         const double E = orc_error_attempt(&T, F, sys, n, t, h, y, ynew, atol, rtol, err, k, ytmp);
+        if (trace_h && n_att < trace_cap) {
+            trace_h[n_att] = h;
+            trace_E[n_att] = E;
+            trace_acc[n_att] = isfinite(E) && E <= 1.0;
+        }
+        ++n_att;
         if (!isfinite(E)) { status = ORC_ERR_NONFINITE; break; }
         if (E > 1.0) {
             ++n_rej; ++consec;
@@ -579,8 +589,17 @@ int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, 
     *dt_io = dt;
     if (n_acc_out) *n_acc_out = n_acc;
     if (n_rej_out) *n_rej_out = n_rej;
+    if (n_trace) *n_trace = n_att;
     free(k); free(ytmp); free(ynew); free(err);
     return status;
+}
+
+int orc_integrate_adaptive_m(int method, orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
+                             double t_end, double* dt_io, double atol, double rtol, long max_acc,
+                             long max_rej, long* n_acc_out, long* n_rej_out, double* log_dt,
+                             long log_cap) {
+    return orc_adaptive_core(method, F, sys, n, y, t_io, t_end, dt_io, atol, rtol, max_acc, max_rej, n_acc_out,
+                             n_rej_out, log_dt, log_cap, NULL, NULL, NULL, 0, NULL);
 }
 
 int orc_integrate_adaptive(orc_rhs_fn F, const void* sys, long n, double* y, double* t_io,
@@ -796,6 +815,16 @@ int orc_pw_integrate_adaptive_m(int method, int kind, const double* coef, long n
     orc_pointwise p = {kind, coef};
     return orc_integrate_adaptive_m(method, orc_pointwise_rhs, &p, n, y, t, t_end, dt, atol, rtol, max_acc,
                                     max_rej, n_acc, n_rej, log_dt, log_cap);
+}
+/* orc_pw_integrate_adaptive_m with the record of every attempt: trace_h[a],
+ * trace_E[a], trace_acc[a] for attempts a < min(*n_trace, trace_cap). */
+int orc_pw_integrate_adaptive_trace(int method, int kind, const double* coef, long n, double* y, double* t,
+                                    double t_end, double* dt, double atol, double rtol, long max_acc,
+                                    long max_rej, long* n_acc, long* n_rej, double* trace_h, double* trace_E,
+                                    int* trace_acc, long trace_cap, long* n_trace) {
+    orc_pointwise p = {kind, coef};
+    return orc_adaptive_core(method, orc_pointwise_rhs, &p, n, y, t, t_end, dt, atol, rtol, max_acc, max_rej,
+                             n_acc, n_rej, NULL, 0, trace_h, trace_E, trace_acc, trace_cap, n_trace);
 }
 /* Independent scalar ODEs, each with its own step size and controller: the
  * adaptive driver applied to each element alone (element e: a one-element
