@@ -14,7 +14,8 @@ L2, so no flush is needed between timed steps.
 N > 1 (torchrun): every rank integrates its own independent 256^3 problem
 (replicas; no data-path collective), value = all ranks' cell-steps / max time.
 --impl reference times the CPU FP64 oracle on the same workload, a bounded
-sample per step (one accepted step of the same grid), on the host cores.
+sample per step (one accepted step of the same grid), on every usable host
+core.
 """
 from __future__ import annotations
 
@@ -154,9 +155,24 @@ def _dist():
     return ws, rank, local
 
 
+def _host_cpu():
+    """Processor model and logical CPU count of the machine the bench runs on."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"cpu_model": model, "nproc": os.cpu_count(), "usable_cpus": len(os.sched_getaffinity(0))}
+
+
 def run_reference(args):
-    """The oracle (CPU FP64, single-threaded) on the same workload: each step
-    is one accepted Dormand-Prince step of the full 256^3 grid."""
+    """The oracle (CPU FP64, plain C, every usable host core) on the same
+    workload: each step is one accepted Dormand-Prince step of the full 256^3
+    grid."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -164,6 +180,8 @@ def run_reference(args):
 
     import oracle
     import synthetic_inputs as si
+    cores = oracle.max_threads()
+    oracle.set_threads(cores)
     u0, v0 = si.gs_initial_state(N, N, N, seed=2)
     u = u0.astype(np.float32).astype(np.float64)
     v = v0.astype(np.float32).astype(np.float64)
@@ -186,29 +204,67 @@ def run_reference(args):
             "config": {"workload": WORKLOAD.replace("10 accepted steps per bench step",
                                                      "1 accepted step per bench step (bounded CPU sample)"),
                        "grid": [N, N, N], "accepted_per_step": 1},
-            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": 1,
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores, "host": _host_cpu(),
                              "sample": f"one accepted Dormand-Prince step of the full {N}^3 grid per step, "
-                                       "FP64 oracle (plain C, single thread)"},
+                                       f"FP64 oracle (plain C, OpenMP over cells, {cores} threads)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def cpu_baseline_sample():
-    """Oracle time for one accepted Dormand-Prince step of the 256^3 grid."""
+def cpu_baseline_sample(torch, gs, si, replay_steps=20):
+    """The oracle on the headline workload, timed on the host cores, and the
+    FP32 path's error against it.
+
+    1. Single thread: one accepted Dormand-Prince step of the full 256^3 grid
+       from the initial state (adaptive, as the GPU runs it).
+    2. Every usable core: the FP64 oracle replays, as fixed Dormand-Prince
+       steps from the same FP32-rounded initial state, the first
+       `replay_steps` step sizes the FP32 GPU run accepted; the time is the
+       all-cores value, and the two states give the FP32 path's error against
+       the oracle (relative L2 over the full grid and over the 64^3
+       downsample, every 4th point per axis)."""
     import numpy as np
 
     import oracle
-    import synthetic_inputs as si
     u0, v0 = si.gs_initial_state(N, N, N, seed=2)
     u = u0.astype(np.float32).astype(np.float64)
     v = v0.astype(np.float32).astype(np.float64)
+    p = oracle.GSParams(N, N, N)
+    oracle.set_threads(1)
     t0 = time.perf_counter()
-    r = oracle.gs_integrate_adaptive(oracle.GSParams(N, N, N), u, v, 0.0, math.inf, DT0, TOL, TOL, max_acc=1)
-    el = time.perf_counter() - t0
-    return {"value": N ** 3 * r["n_acc"] / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"one accepted Dormand-Prince step of the full {N}^3 grid ({el:.1f} s, "
-                      f"{r['n_acc'] + r['n_rej']} attempt(s)), FP64 oracle, plain C, single thread"}
+    r = oracle.gs_integrate_adaptive(p, u, v, 0.0, math.inf, DT0, TOL, TOL, max_acc=1)
+    el1 = time.perf_counter() - t0
+    v1 = N ** 3 * r["n_acc"] / el1
+    # the FP32 GPU run whose accepted steps the oracle replays
+    g = gs.GrayScott(N, N, N, prec=gs.GS_FP32)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    gs.gs_set_step_log(g.ctx, replay_steps)
+    rg = g.integrate_adaptive(TOL, TOL, 0.0, math.inf, DT0, max_accepted=replay_steps)
+    dts, _ = gs.gs_get_step_log(g.ctx, replay_steps)
+    gu, gv = g.u.double().cpu().numpy(), g.v.double().cpu().numpy()
+    g.close()
+    cores = oracle.max_threads()
+    oracle.set_threads(cores)
+    t0 = time.perf_counter()
+    ou, ov = oracle.gs_integrate_replay(p, u, v, oracle.DOPRI5, dts)
+    elc = time.perf_counter() - t0
+    oracle.set_threads(1)
+    vc = N ** 3 * len(dts) / elc
+    sub = (slice(None, None, 4),) * 3
+    host = _host_cpu()
+    return {"value": vc, "unit": UNIT, "cores": cores, "kind": "oracle", "host": host,
+            "sample": f"{len(dts)} accepted Dormand-Prince steps of the full {N}^3 grid replayed from the FP32 GPU "
+                      f"run's step sizes ({elc:.1f} s), FP64 oracle, plain C, OpenMP over cells, {cores} threads on "
+                      f"{host['cpu_model']}",
+            "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                              "sample": f"one accepted Dormand-Prince step of the full {N}^3 grid ({el1:.1f} s, "
+                                        f"{r['n_acc'] + r['n_rej']} attempt(s)), adaptive"},
+            "fp32_vs_oracle": {"accepted_steps": len(dts), "t": rg["t"], "gpu_rejected": rg["n_rej"],
+                               "rel_l2_full": oracle.rel_l2([gu, gv], [ou, ov]),
+                               "rel_l2_64cubed_downsample": oracle.rel_l2([gu[sub], gv[sub]], [ou[sub], ov[sub]]),
+                               "max_abs_diff": max(oracle.linf(gu - ou), oracle.linf(gv - ov)),
+                               "reference": "FP64 oracle replaying the FP32 run's accepted step sizes"}}
 
 
 def extra_workloads(torch, gs, si):
@@ -444,8 +500,10 @@ def precision_workload(torch, gs, si, n=N, accepted=1000):
     out["gs_256cubed_fp32_vs_fp64_1000_accepted"] = {
         "t": r32["t"], "fp32_accepted": r32["n_acc"], "fp32_rejected": r32["n_rej"],
         "fp64_accepted": r64["n_acc"], "fp64_rejected": r64["n_rej"], "tolerance": TOL,
-        "rel_l2_full": rel(u32, v32, u64, v64),
-        "rel_l2_64cubed_downsample": rel(u32[s], v32[s], u64[s], v64[s])}
+        "rel_l2_full_vs_gpu_fp64": rel(u32, v32, u64, v64),
+        "rel_l2_64cubed_downsample_vs_gpu_fp64": rel(u32[s], v32[s], u64[s], v64[s]),
+        "reference": "the all-FP64 GPU path (oracle-pinned at <= 64^3 and on sampled 256^3 cells); the FP32 "
+                     "error against the oracle itself is cpu_baseline.fp32_vs_oracle"}
     g64.close()
     return out
 
@@ -700,7 +758,7 @@ def main():
             line["surrogate_speedup_at_matched_l2"] = sw.get("surrogate_speedup_at_matched_error")
             line["surrogate_heldout_rel_l2"] = sw["heldout_rel_l2_mean"]
         if ws == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline_sample()
+            line["cpu_baseline"] = cpu_baseline_sample(torch, gs, si)
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()

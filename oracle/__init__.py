@@ -76,6 +76,7 @@ def lib():
         path = _build.build()
         L = C.CDLL(path)
         L.orc_get_tableau.argtypes = [C.c_int, C.POINTER(_Tableau)]
+        L.orc_set_threads.argtypes = [C.c_int]
         L.orc_gs_laplacian.argtypes = [C.POINTER(_GS), _dp, _dp]
         L.orc_gs_rhs_full.argtypes = [C.POINTER(_GS), _dp, _dp]
         L.orc_gs_integrate_const.argtypes = [C.POINTER(_GS), C.c_int, _dp, C.c_double, C.c_double, C.c_long]
@@ -136,6 +137,23 @@ def _p(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def set_threads(n: int) -> None:
+    """Threads for the oracle's loops over cells and elements (default 1).
+    Each element's arithmetic is identical for every thread count.  Call it
+    only in a process that will not fork afterwards (OpenMP's thread pool does
+    not survive a fork)."""
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def max_threads() -> int:
+    """Processors available to this process."""
+    return int(lib().orc_max_threads())
 
 
 # --------------------------------------------------------------------------

@@ -2,7 +2,9 @@
 
 Flags: -O2 -ffp-contract=off (no FMA contraction, no fast-math) so every
 floating-point operation in oracle.c is one IEEE FP64 operation, in the order
-written.  Single-threaded.
+written.  -fopenmp: the loops over cells and elements can be shared among
+threads (oracle.set_threads; one thread unless set), without changing any
+element's operations or their order.
 """
 from __future__ import annotations
 
@@ -20,7 +22,7 @@ def build(force: bool = False) -> str:
         return LIB
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, SRC, "-lm"]
+           "-fopenmp", "-Wall", "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
     return LIB

@@ -6,9 +6,12 @@
  * load or call this file: only the tests, the smoke check and the benchmark's
  * CPU-baseline leg use it.  It shares no code with the CUDA library.
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fast-math, no FMA
- * contraction), so every operation below is one correctly rounded IEEE op in
- * the order written.
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no fast-math, no
+ * FMA contraction), so every operation below is one correctly rounded IEEE op
+ * in the order written.  The loops over cells and elements may be shared
+ * among threads (orc_set_threads; 1 by default): each element's operations
+ * and their order are the same whatever the thread count, and the only
+ * reduction (the error norm's maximum) stays sequential.
  *
  * Contents, each following the passage cited at its definition:
  *   - right-hand sides: the Gray-Scott system (Eq. 2, read with the System
@@ -38,8 +41,15 @@
  *     the learned surrogate, by their definitions (plain loops).
  */
 #include <math.h>
+#include <omp.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads for the cell / element loops (1 unless set). */
+static int orc_threads = 1;
+void orc_set_threads(int n) { orc_threads = n < 1 ? 1 : n; }
+int orc_get_threads(void) { return orc_threads; }
+int orc_max_threads(void) { return omp_get_num_procs(); }
 
 /* ------------------------------------------------------------------------ */
 /* Butcher tableaux (Table 1).  a is s x s row-major, strictly lower.        */
@@ -214,6 +224,7 @@ static double orc_lap(const orc_gs* p, const double* w, int x, int y, int z) {
 
 /* Lap(w) for a whole field (exported for the Laplacian pins). */
 void orc_gs_laplacian(const orc_gs* p, const double* w, double* out) {
+    #pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x)
@@ -227,6 +238,7 @@ void orc_gs_rhs(const void* sys, double t, long n, const double* y, double* f) {
     (void)n; /* n == 2N */
     const double* u = y;
     const double* v = y + N;
+    #pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int yy = 0; yy < p->ny; ++yy)
             for (int x = 0; x < p->nx; ++x) {
@@ -380,6 +392,7 @@ void orc_gs_rhs_dcpse(const void* sys, double t, long n, const double* y, double
     const long N = (long)p->nx * p->ny * p->nz;
     const double* u = y;
     const double* v = y + N;
+    #pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (int z = 0; z < p->nz; ++z)
         for (int yy = 0; yy < p->ny; ++yy)
             for (int x = 0; x < p->nx; ++x) {
@@ -435,6 +448,7 @@ void orc_rk_step(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, do
                  const double* y, double* yout, double* err, double* k, double* ytmp) {
     const int s = T->s;
     for (int i = 0; i < s; ++i) {
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
         for (long e = 0; e < n; ++e) {
             double acc = 0.0;
             for (int j = 0; j < i; ++j) acc += T->a[i * s + j] * k[(long)j * n + e];
@@ -443,12 +457,14 @@ void orc_rk_step(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, do
         F(sys, t + T->c[i] * dt, n, ytmp, k + (long)i * n);
     }
     if (err) {
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
         for (long e = 0; e < n; ++e) {
             double acc = 0.0;
             for (int i = 0; i < s; ++i) acc += (T->b[i] - T->bhat[i]) * k[(long)i * n + e];
             err[e] = dt * acc;
         }
     }
+#pragma omp parallel for num_threads(orc_threads) schedule(static)
     for (long e = 0; e < n; ++e) {
         double acc = 0.0;
         for (int i = 0; i < s; ++i) acc += T->b[i] * k[(long)i * n + e];

@@ -72,9 +72,6 @@ _SIGNATURES = {
     "gs_set_dopri5_fusion": ([_vp, C.c_int], C.c_int),
     "gs_get_dopri5_fusion": ([_vp], C.c_int),
     "gs_get_rk4_fusion": ([_vp], C.c_int),
-    "gs_set_pair_loader": ([_vp, C.c_int], C.c_int),
-    "gs_get_pair_loader": ([_vp], C.c_int),
-    "gs_pair_timeouts": ([C.POINTER(C.c_uint)], C.c_int),
     "gs_set_pair_config": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
     "gs_get_pair_configs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gs_time_pairs": ([_vp, C.c_int, _dp], C.c_int),
@@ -137,6 +134,7 @@ _SIGNATURES = {
     "sur_get_conv_engine": ([], C.c_int),
     "sur_conv_last_engine": ([], C.c_int),
     "sur_conv_tc_status": ([C.POINTER(C.c_uint)], C.c_int),
+    "sur_debug_set_timeout_word": ([_vp, C.c_uint], C.c_int),
     "sur_conv3d": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp, _vp, C.c_int, _vp],
                    C.c_int),
     "sur_wgrad_workspace_bytes": ([C.c_int, C.c_int], C.c_size_t),
@@ -296,20 +294,6 @@ def gs_get_dopri5_fusion(ctx):
 
 def gs_set_pair_config(ctx, pair, ty, depth):
     _check(lib().gs_set_pair_config(ctx, pair, ty, depth), ctx)
-
-
-def gs_set_pair_loader(ctx, bulk):
-    _check(lib().gs_set_pair_loader(ctx, bulk), ctx)
-
-
-def gs_get_pair_loader(ctx):
-    return lib().gs_get_pair_loader(ctx)
-
-
-def gs_pair_timeouts():
-    v = C.c_uint(0)
-    _check(lib().gs_pair_timeouts(C.byref(v)))
-    return v.value
 
 
 def gs_get_rk4_fusion(ctx):

@@ -9,6 +9,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "gs_internal.h"
 #include "host_util.h"
 
 namespace {

@@ -34,6 +34,7 @@
 #include "gs_tile.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
+#include "gs_internal.h"
 #include "host_util.h"
 
 using namespace gsk;

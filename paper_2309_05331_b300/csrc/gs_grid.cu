@@ -28,6 +28,7 @@
 #include "gs_persist.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
+#include "gs_internal.h"
 #include "host_util.h"
 
 using namespace gsk;
@@ -77,7 +78,6 @@ struct gs_ctx {
     int fuse = -1;          // Dormand-Prince stage pairs (2,3) (4,5) (6,7) in one launch each: -1 automatic, 0 off, 1 on
     bool fuse_auto = true;  // the automatic choice (the autotuner's verdict once tuned)
     bool rk4_fuse_auto = true;  // the automatic choice for RK4 (the autotuner's verdict once tuned)
-    int pair_bulk = 0;          // pair kernels' row loader: 0 per-thread cp.async, 1 TMA bulk copies (slower)
     // pair kernels (tile height, ring depth): Dormand-Prince stages 2+3, 4+5,
     // 6+7; RK4 stages 1+2, 3+4
     KCfg pc[5] = {{5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}, {5, 7, 0, 2}};
@@ -247,7 +247,7 @@ static int pair_depth_fit(int ty, int depth) {
 template <typename T, int NK, int MODE>
 static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
     const Geom<T> g = make_geom<T>(ctx->p);
-    auto kern = ctx->pair_bulk ? gs_pair_kernel<T, NK, MODE, true> : gs_pair_kernel<T, NK, MODE, false>;
+    auto kern = gs_pair_kernel<T, NK, MODE>;
     if (A.ty < 1 || A.ty > kPairMaxTY) return cudaErrorInvalidConfiguration;
     const int txw = 32 * pair_vx<T>();
     A.ntx = (ctx->p.nx + txw - 1) / txw;
@@ -1579,25 +1579,6 @@ gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth) {
 }
 
 int gs_get_rk4_fusion(const gs_ctx* ctx) { return ctx && rk4_pairs_on(ctx) ? 1 : 0; }
-
-gs_status gs_set_pair_loader(gs_ctx* ctx, int bulk) {
-    if (!ctx || bulk < 0 || bulk > 1) return GS_ERR_INVALID;
-    drop_graphs(ctx);
-    ctx->pair_bulk = bulk;
-    return GS_OK;
-}
-
-int gs_get_pair_loader(const gs_ctx* ctx) { return ctx ? ctx->pair_bulk : -1; }
-
-gs_status gs_pair_timeouts(unsigned* count) {
-    if (!count) return GS_ERR_INVALID;
-    cudaError_t e = cudaMemcpyFromSymbol(count, g_pair_timeouts, sizeof(unsigned));
-    if (e != cudaSuccess) {
-        set_global_error(e, "gs_pair_timeouts");
-        return GS_ERR_CUDA;
-    }
-    return GS_OK;
-}
 
 gs_status gs_get_pair_configs(const gs_ctx* ctx, int* ty, int* depth) {
     if (!ctx || !ty || !depth) return GS_ERR_INVALID;

@@ -36,15 +36,10 @@
 // it was filled, after the last iteration that reads another thread's cells
 // from it.  The upper z neighbour and the centre stay in registers.  The
 // inputs arrive through the staged form's per-thread cp.async ring, DEPTH
-// planes ahead (a slot is written and read only by the thread that copies
-// it).  Two loaders fill the ring: every thread copying its own 16-byte
-// vectors with cp.async (LSU path), or (BULK) lane 0 of each row warp issuing
-// one cp.async.bulk per input array of a plane (the row's 32*VX contiguous
-// cells) on the TMA engine, completion tracked by one mbarrier per (slot,
-// row warp) with the byte count; every mbarrier wait is bounded (a timeout is
-// counted in g_pair_timeouts and the kernel carries on, so it cannot hang).
-// The x-halo warp always uses cp.async (its 8-byte pairs are below the bulk
-// copy's 16-byte granule).
+// planes ahead: every thread copies its own 16-byte vectors (the halo warp
+// its 8-byte pairs) with cp.async, and a slot is written and read only by the
+// thread that copies it, so cp.async.wait_group is the only ordering the ring
+// needs.
 #pragma once
 
 #include <type_traits>
@@ -80,8 +75,6 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
     const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
     return (vec + halo + 15) / 16 * 16;
 }
-// mbarriers of the bulk loader: one per (ring slot, row warp), 8 bytes each
-constexpr size_t kPairMbarBytes = (size_t)3 * (kPairMaxTY + 4) * 8;
 // Dormand-Prince pair: the inverse error scale of the tile rows' cells for
 // the three planes between A and C (thread-private, 3 x 2 components)
 // (RK4 stages 3+4: the partial update u + dt (k1/6 + k2/3) between A and B)
@@ -92,38 +85,7 @@ __host__ __device__ inline size_t pair_isc_bytes(int ty) {
 template <typename T, int NK, int MODE>
 __host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
     return (pair_plane_bytes<T>(ty) + 15) / 16 * 16 + pair_isc_bytes<MODE>(ty) +
-           (size_t)depth * pair_slot_bytes<T, NK>(ty) + kPairMbarBytes;
-}
-
-__device__ unsigned int g_pair_timeouts = 0;  // bounded mbarrier waits that expired
-constexpr long kPairPolls = 1L << 20;
-
-__device__ __forceinline__ uint32_t smem_u32p(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void pair_mbar_init(uint32_t mb, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mb), "r"(count) : "memory");
-}
-__device__ __forceinline__ void pair_mbar_expect(uint32_t mb, uint32_t bytes) {
-    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(mb),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void pair_bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mb) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(mb)
-                 : "memory");
-}
-__device__ __forceinline__ bool pair_mbar_wait(uint32_t mb, uint32_t parity) {
-    for (long i = 0; i < kPairPolls; ++i) {
-        uint32_t ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(mb), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    atomicAdd(&g_pair_timeouts, 1u);
-    return false;
+           (size_t)depth * pair_slot_bytes<T, NK>(ty);
 }
 
 // Coefficients of one pair launch in T.
@@ -160,10 +122,10 @@ __device__ __forceinline__ int wrapm(int a, int n) {
 // One segment: column (tx, tyi), output planes [z0, z1).  Called by every
 // thread of the CTA (it contains barriers: (z1 - z0) + 4 per segment, the
 // same count in the row warps and in the halo warp).
-template <typename T, int NK, int MODE, bool BULK>
+template <typename T, int NK, int MODE>
 __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const PairCoef<T, NK>& C,
-                                             T* SA, T* SB, unsigned char* SI, unsigned char* R, uint64_t* MB,
-                                             uint32_t& ph, int depth, int TY, int tx, int tyi, int z0, int z1,
+                                             T* SA, T* SB, unsigned char* SI, unsigned char* R, int depth, int TY,
+                                             int tx, int tyi, int z0, int z1,
                                              typename ErrBits<T>::U& ebits) {
     constexpr int VX = pair_vx<T>();
     constexpr int TXW = 32 * VX;
@@ -222,31 +184,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
         return reinterpret_cast<V2*>(R + (size_t)s * slot_bytes + vec_bytes) + (size_t)a * 32 + lane;
     };
 
-    // BULK: the row's bytes per array, its mbarrier of slot s
-    const bool rowact = !hw && r < ah + 2;
-    const uint32_t rowbytes = (uint32_t)(aw * sizeof(T));
-    auto mbar = [&](int s) -> uint32_t { return smem_u32p(MB + (size_t)s * (kPairMaxTY + 4) + w); };
     // input plane q (z0 - 2 .. z1 + 1) into ring slot s
     auto fetch = [&](int q, int s) {
-        if (BULK && !hw) {
-            if (q <= z1 + 1 && rowact) {
-                __syncwarp();  // every lane has read the slot's previous plane
-                if (lane == 0) {
-                    const long long zo = plane * wrapm(q, nz);
-                    const uint32_t mb = mbar(s);
-                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    pair_mbar_expect(mb, (uint32_t)NA * rowbytes);
-#pragma unroll
-                    for (int c = 0; c < 2; ++c)
-#pragma unroll
-                        for (int f = 0; f <= NK; ++f) {
-                            const T* src = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]) + cbase + zo;
-                            pair_bulk_g2s(smem_u32p(rvec(s, c * (1 + NK) + f)), src, rowbytes, mb);
-                        }
-                }
-            }
-            return;
-        }
         if (q <= z1 + 1 && inA) {
             const long long zo = plane * wrapm(q, nz);
 #pragma unroll
@@ -360,14 +299,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             const int q = z0 - 2 + it;
             const int b1 = b == 0 ? 2 : b - 1, b2 = b == 2 ? 0 : b + 1;  // planes q - 1 and q - 2
             // ---- A(q)
-            if (BULK) {
-                if (rowact) {
-                    pair_mbar_wait(mbar(sA), (ph >> sA) & 1u);
-                    ph ^= 1u << sA;
-                }
-            } else {
-                cp_async_wait_pending(depth - 1);
-            }
+            cp_async_wait_pending(depth - 1);
             if (doA) {
                 auto ld = [&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(sA, a)), out); };
                 if (TILE)
@@ -581,22 +513,13 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     __syncthreads();           // the plane buffers are reused by the next segment
 }
 
-template <typename T, int NK, int MODE, bool BULK>
+template <typename T, int NK, int MODE>
 __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
     T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<pair_vx<T>()>();
     unsigned char* SI = smem_raw + (pair_plane_bytes<T>(A.ty) + 15) / 16 * 16;
     unsigned char* R = SI + pair_isc_bytes<MODE>(A.ty);
-    uint64_t* MB = reinterpret_cast<uint64_t*>(R + (size_t)depth * pair_slot_bytes<T, NK>(A.ty));
-    uint32_t ph = 0;  // BULK: phase parity of this row warp's mbarrier of each slot
-    if (BULK) {
-        const int w = threadIdx.y;
-        if (w < A.ty + 4 && threadIdx.x == 0)
-            for (int s = 0; s < depth; ++s) pair_mbar_init(smem_u32p(MB + (size_t)s * (kPairMaxTY + 4) + w), 1);
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();
-    }
     __shared__ T red[32];
     __shared__ int s_last;
 
@@ -617,8 +540,7 @@ __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> 
     typename ErrBits<T>::U ebits = 0;
     if (!skip) {
         for_each_segment(A, g.nz, [&](int col, int z0, int z1) {
-            pair_segment<T, NK, MODE, BULK>(g, P, C, SA, SB, SI, R, MB, ph, depth, A.ty, col % A.ntx, col / A.ntx, z0,
-                                            z1, ebits);
+            pair_segment<T, NK, MODE>(g, P, C, SA, SB, SI, R, depth, A.ty, col % A.ntx, col / A.ntx, z0, z1, ebits);
         });
     }
     const T emax = ErrBits<T>::value(ebits);

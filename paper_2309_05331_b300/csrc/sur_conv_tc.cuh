@@ -50,8 +50,10 @@
 // i+1 before the epilogue of tile i, so the MMAs of tile i+1 run while the
 // epilogue of tile i does, and the MMA warp never joins a block barrier.
 // Every mbarrier wait has an iteration limit and also watches a shared abort
-// flag: on expiry the kernel counts the event in g_tc_timeouts, all roles
-// leave their loops, and the TMEM is freed.
+// flag: on expiry the kernel sets the caller's timeout word (host-mapped
+// memory the host reads after the launch, so the call that owns the launch
+// reports an error instead of a result), all roles leave their loops, and
+// the TMEM is freed.
 #pragma once
 
 #include "sur_conv.cuh"
@@ -112,9 +114,6 @@ __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence
 // generic-proxy shared-memory writes -> visible to the tensor cores' reads
 __device__ __forceinline__ void fence_smem_to_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
-// mbarrier waits that gave up (read by sur_conv_tc_status)
-__device__ unsigned int g_tc_timeouts;
-
 __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(mbar) : "memory");
 }
@@ -132,13 +131,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
     return ok != 0;
 }
 // bounded wait for the phase with the given parity to complete; gives up
-// (false) after kMaxPolls tries or once *abort is set, and then sets *abort
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, volatile int* abort) {
+// (false) after kMaxPolls tries or once *abort is set, and then sets *abort;
+// the first thread of the CTA to give up also sets the launch's timeout
+// word (*timeouts = 1; a plain store: the word may live in host memory)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, volatile int* abort,
+                                                  unsigned int* timeouts) {
     for (long i = 0; i < kMaxPolls; ++i) {
         if (mbar_try_wait(mbar, parity)) return true;
         if ((i & 63) == 63 && *abort) return false;
     }
-    if (atomicExch((int*)abort, 1) == 0) atomicAdd(&g_tc_timeouts, 1u);
+    if (atomicExch((int*)abort, 1) == 0) {
+        *reinterpret_cast<volatile unsigned int*>(timeouts) = 1u;
+        __threadfence_system();
+    }
     return false;
 }
 
@@ -241,11 +246,12 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t xs_addr, uint32_t ws_ad
 
 // Same contract as conv_fwd_kernel<CIN, COUT, EPI> (sur_conv.cuh); D % 4 == 0,
 // H % 16 == 0, W % 8 == 0.  wp: the packed weights of sur_pack_weights.
+// timeouts: set to 1 if a wait gave up (the output is then invalid).
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(NTHREADS, 1)
     conv_tc_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ wp,
                    const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask, void* out, int out_ch,
-                   int D, int H, int W) {
+                   int D, int H, int W, unsigned int* timeouts) {
     using C = Cfg<CIN, COUT>;
     constexpr int CW = C::CW, NSTK = C::NSTK, SET_COLS = C::SET_COLS;
     constexpr size_t W_BYTES = C::W_BYTES, X_BYTES = C::X_BYTES;
@@ -323,8 +329,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             for (int i = 0; i < nmine; ++i) {
                 const int b = i & 1;
-                if (!mbar_wait_bounded(bar(HF + b), (uint32_t)((i >> 1) & 1), abort)) break;
-                if (i >= 2 && !mbar_wait_bounded(bar(AE + b), (uint32_t)(((i >> 1) - 1) & 1), abort)) break;
+                if (!mbar_wait_bounded(bar(HF + b), (uint32_t)((i >> 1) & 1), abort, timeouts)) break;
+                if (i >= 2 && !mbar_wait_bounded(bar(AE + b), (uint32_t)(((i >> 1) - 1) & 1), abort, timeouts)) break;
                 fence_after_sync();
                 issue_tile_mmas<CIN, COUT>(smem_u32(Xs[b]), ws_addr, tbase + (uint32_t)(b * SET_COLS));
                 mma_commit(bar(AF + b));  // accumulators full
@@ -356,12 +362,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                 // next halo is published before this tile's epilogue, so the
                 // MMAs of tile i+1 run while the epilogue of tile i does
                 if (i + 1 >= 2 && !mbar_wait_bounded(bar(HE + ((i + 1) & 1)), (uint32_t)((((i + 1) >> 1) - 1) & 1),
-                                                     abort))
+                                                     abort, timeouts))
                     break;
                 load(i + 1);
                 publish(i + 1);
             }
-            if (!mbar_wait_bounded(bar(AF + s), (uint32_t)((i >> 1) & 1), abort)) break;
+            if (!mbar_wait_bounded(bar(AF + s), (uint32_t)((i >> 1) & 1), abort, timeouts)) break;
             fence_after_sync();
             int x0, y0, z0;
             tile_origin(i, x0, y0, z0);

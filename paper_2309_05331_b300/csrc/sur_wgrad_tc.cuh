@@ -95,7 +95,7 @@ __device__ __forceinline__ void tile_async(unsigned char* buf, const __nv_bfloat
 // W % 8 == 0, any D.
 __global__ void __launch_bounds__(NTHREADS, 1)
     conv_wgrad_tc_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ dy,
-                         float* __restrict__ ws, int D, int H, int W) {
+                         float* __restrict__ ws, int D, int H, int W, unsigned int* timeouts) {
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char* buf[NBUF] = {smem, smem + BUF_BYTES};
     // mbarriers: tile full [0, 1], tile empty [2, 3], all MMAs done [4]
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (lane == 0) {
             for (int i = 0; i < nmine; ++i) {
                 const int b = i & 1;
-                if (!mbar_wait_bounded(bar(b), (uint32_t)((i >> 1) & 1), abort)) {
+                if (!mbar_wait_bounded(bar(b), (uint32_t)((i >> 1) & 1), abort, timeouts)) {
                     ok = false;
                     break;
                 }
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             mbar_arrive(bar(i & 1));
         };
         for (int i = 0; i < nmine; ++i) {
-            if (i >= 2 && !mbar_wait_bounded(bar(2 + (i & 1)), (uint32_t)(((i >> 1) - 1) & 1), abort)) {
+            if (i >= 2 && !mbar_wait_bounded(bar(2 + (i & 1)), (uint32_t)(((i >> 1) - 1) & 1), abort, timeouts)) {
                 ok = false;
                 break;
             }
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (warp < 4) {
             float* wsb = ws + (size_t)blockIdx.x * 27 * CH * CH;
             const int zp = lane >> 3, ich = 8 * warp + (lane & 7);
-            const bool have = ok && nmine > 0 && mbar_wait_bounded(bar(4), 0u, abort);
+            const bool have = ok && nmine > 0 && mbar_wait_bounded(bar(4), 0u, abort, timeouts);
             if (have) fence_after_sync();
 #pragma unroll 1
             for (int r = 0; r < 9; ++r) {

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/gs.h"
+#include "gs_internal.h"
 #include "host_util.h"
 #include "sur_conv_tc.cuh"
 #include "sur_wgrad_tc.cuh"
@@ -284,7 +285,7 @@ bool tc_applies(int cinp, int coutp, int epi, int D, int H, int W) {
 
 template <int CIN, int COUT, int EPI>
 cudaError_t launch_conv_tc_t(int D, int H, int W, const __nv_bfloat16* x, const __nv_bfloat16* wp, const float* bias,
-                             const __nv_bfloat16* mask, void* out, int out_ch, cudaStream_t s) {
+                             const __nv_bfloat16* mask, void* out, int out_ch, cudaStream_t s, unsigned int* tw) {
     auto kern = tc::conv_tc_kernel<CIN, COUT, EPI>;
     // one CTA per SM: a CTA allocates up to all 512 TMEM columns, and a second
     // one on the same SM would wait in tcgen05.alloc; asking for more shared
@@ -294,12 +295,15 @@ cudaError_t launch_conv_tc_t(int D, int H, int W, const __nv_bfloat16* x, const 
     if (e != cudaSuccess) return e;
     const int ntiles = (W / tc::TX) * (H / tc::TY) * (D / tc::TZ);
     const int grid = std::max(1, std::min(ntiles, nsm_now()));
-    kern<<<grid, tc::NTHREADS, smem, s>>>(x, wp, bias, mask, out, out_ch, D, H, W);
+    kern<<<grid, tc::NTHREADS, smem, s>>>(x, wp, bias, mask, out, out_ch, D, H, W, tw);
     return cudaGetLastError();
 }
 
+// tw: device address of the launch owner's timeout word (host-mapped; see
+// TimeoutWord), set by a tcgen05 kernel whose bounded wait gave up
 cudaError_t launch_conv(int cinp, int coutp, int epi, int D, int H, int W, const void* x, const void* wp,
-                        const float* bias, const void* mask, void* out, int out_ch, cudaStream_t s) {
+                        const float* bias, const void* mask, void* out, int out_ch, cudaStream_t s,
+                        unsigned int* tw) {
     const auto* xb = static_cast<const __nv_bfloat16*>(x);
     const auto* wb = static_cast<const __nv_bfloat16*>(wp);
     const auto* mb = static_cast<const __nv_bfloat16*>(mask);
@@ -307,7 +311,7 @@ cudaError_t launch_conv(int cinp, int coutp, int epi, int D, int H, int W, const
         g_conv_last_engine = 2;
 #define SUR_TC_CASE(CI, CO, EP)                   \
     if (cinp == CI && coutp == CO && epi == EP) \
-        return launch_conv_tc_t<CI, CO, EP>(D, H, W, xb, wb, bias, mb, out, out_ch, s);
+        return launch_conv_tc_t<CI, CO, EP>(D, H, W, xb, wb, bias, mb, out, out_ch, s, tw);
         SUR_TC_CASE(32, 32, EPI_BIAS_RELU_BF16)
         SUR_TC_CASE(32, 32, EPI_MASK_BF16)
         SUR_TC_CASE(32, 32, EPI_RAW_F32)
@@ -349,7 +353,7 @@ cudaError_t launch_wgrad_t(int D, int H, int W, const __nv_bfloat16* x, const __
 }
 
 cudaError_t launch_wgrad(int cinp, int coutp, int D, int H, int W, const void* x, const void* dy, float* ws,
-                         cudaStream_t s) {
+                         cudaStream_t s, unsigned int* tw) {
     const auto* xb = static_cast<const __nv_bfloat16*>(x);
     const auto* yb = static_cast<const __nv_bfloat16*>(dy);
     if (cinp == 8 && coutp == 32) return launch_wgrad_t<8, 32>(D, H, W, xb, yb, ws, s);
@@ -361,7 +365,7 @@ cudaError_t launch_wgrad(int cinp, int coutp, int D, int H, int W, const void* x
             cudaError_t e = cudaFuncSetAttribute(wtc::conv_wgrad_tc_kernel,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
-            wtc::conv_wgrad_tc_kernel<<<wgrad_grid(), wtc::NTHREADS, smem, s>>>(xb, yb, ws, D, H, W);
+            wtc::conv_wgrad_tc_kernel<<<wgrad_grid(), wtc::NTHREADS, smem, s>>>(xb, yb, ws, D, H, W, tw);
             return cudaGetLastError();
         }
         g_conv_last_engine = 1;
@@ -372,6 +376,39 @@ cudaError_t launch_wgrad(int cinp, int coutp, int D, int H, int W, const void* x
 }
 
 size_t wgrad_ws_bytes(int cinp, int coutp) { return (size_t)wgrad_grid() * 27 * cinp * coutp * sizeof(float); }
+
+// A word in pinned, device-mapped host memory that the tcgen05 kernels set
+// when a bounded wait gives up.  The host reads it without a device
+// round trip: after a stream synchronisation it reflects every launch that
+// preceded it; before one, every launch that has finished.
+struct TimeoutWord {
+    unsigned int* host = nullptr;
+    unsigned int* dev = nullptr;
+    cudaError_t alloc() {
+        cudaError_t e = cudaHostAlloc(&host, sizeof(unsigned int), cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e != cudaSuccess) {
+            host = nullptr;
+            return e;
+        }
+        *host = 0u;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&dev), host, 0);
+        if (e != cudaSuccess) release();
+        return e;
+    }
+    void release() {
+        if (host) cudaFreeHost(host);
+        host = dev = nullptr;
+    }
+    bool tripped() const { return host && *reinterpret_cast<volatile unsigned int*>(host) != 0u; }
+};
+
+// The layer primitives' word (process-wide), allocated at their first call.
+TimeoutWord* primitive_word(cudaError_t* err) {
+    static TimeoutWord w;
+    static cudaError_t e = w.alloc();
+    *err = e;
+    return e == cudaSuccess ? &w : nullptr;
+}
 
 bool shape_ok(int D, int H, int W) {
     return D >= TZ && H >= TY && W >= TX && D % TZ == 0 && H % TY == 0 && W % TX == 0;
@@ -405,6 +442,7 @@ struct sur_ctx {
     double* hacc = nullptr;  // pinned
     double mean[2] = {0, 0}, sd[2] = {1, 1}, scale[2] = {1, 1};
     int fallback = 0;      // set when the last judged call exceeded the threshold
+    TimeoutWord tcw;       // set by a tcgen05 launch of this context that gave up waiting
     char err[512] = {0};
 };
 
@@ -418,6 +456,23 @@ static void sset_err(sur_ctx* c, cudaError_t e, const char* where) {
             sset_err(ctx, e_, #call); \
             return GS_ERR_CUDA;       \
         }                             \
+    } while (0)
+
+// GS_ERR_CUDA once a tensor-core launch of ctx gave up waiting for its MMAs
+// (its output, and everything computed from it since, is invalid; the
+// context stays failed).  Checked on entry to every call and again after
+// every synchronisation, so a call whose own launches timed out never
+// reports success once it has synchronised.
+static gs_status tc_check(sur_ctx* ctx) {
+    if (!ctx->tcw.tripped()) return GS_OK;
+    snprintf(ctx->err, sizeof(ctx->err),
+             "a tcgen05 convolution gave up waiting for its tensor-core operations; results are invalid");
+    return GS_ERR_CUDA;
+}
+#define TCK()                                  \
+    do {                                       \
+        gs_status st_ = tc_check(ctx);         \
+        if (st_ != GS_OK) return st_;          \
     } while (0)
 
 static gs_status repack(sur_ctx* ctx) {
@@ -443,13 +498,13 @@ static gs_status forward(sur_ctx* ctx, const float* u, const float* v) {
                                                     static_cast<__nv_bfloat16*>(ctx->x0));
     SCK(cudaGetLastError());
     SCK(launch_conv(8, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->x0, ctx->wf[0], ctx->bpad[0], nullptr, ctx->a[0], 32,
-                    ctx->stream));
+                    ctx->stream, ctx->tcw.dev));
     SCK(launch_conv(32, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->a[0], ctx->wf[1], ctx->bpad[1], nullptr, ctx->a[1], 32,
-                    ctx->stream));
+                    ctx->stream, ctx->tcw.dev));
     SCK(launch_conv(32, 32, EPI_BIAS_RELU_BF16, D, H, W, ctx->a[1], ctx->wf[2], ctx->bpad[2], nullptr, ctx->a[2], 32,
-                    ctx->stream));
+                    ctx->stream, ctx->tcw.dev));
     SCK(launch_conv(32, 8, EPI_BIAS_F32, D, H, W, ctx->a[2], ctx->wf[3], ctx->bpad[3], nullptr, ctx->y, 2,
-                    ctx->stream));
+                    ctx->stream, ctx->tcw.dev));
     return GS_OK;
 }
 
@@ -497,6 +552,7 @@ gs_status sur_create(int nx, int ny, int nz, void* stream, sur_ctx** out) {
         ctx->iv = ctx->iu + ctx->N;
         if ((e = cudaMalloc(&ctx->dacc, sizeof(double) * 4)) != cudaSuccess) break;
         if ((e = cudaMallocHost(&ctx->hacc, sizeof(double) * 4)) != cudaSuccess) break;
+        if ((e = ctx->tcw.alloc()) != cudaSuccess) break;
     } while (0);
     if (e != cudaSuccess) {
         set_global_error(e, "sur_create");
@@ -528,12 +584,14 @@ gs_status sur_destroy(sur_ctx* ctx) {
     cudaFree(ctx->su);
     cudaFree(ctx->dacc);
     if (ctx->hacc) cudaFreeHost(ctx->hacc);
+    ctx->tcw.release();
     delete ctx;
     return GS_OK;
 }
 
 gs_status sur_set_params(sur_ctx* ctx, const float* host) {
     if (!ctx || !host) return GS_ERR_INVALID;
+    TCK();
     SCK(cudaMemcpyAsync(ctx->p, host, sizeof(float) * ctx->np, cudaMemcpyHostToDevice, ctx->stream));
     SCK(cudaMemsetAsync(ctx->m, 0, sizeof(float) * ctx->np * 2, ctx->stream));
     ctx->step = 0;
@@ -547,6 +605,7 @@ gs_status sur_get_params(sur_ctx* ctx, float* host) {
     if (!ctx || !host) return GS_ERR_INVALID;
     SCK(cudaMemcpyAsync(host, ctx->p, sizeof(float) * ctx->np, cudaMemcpyDeviceToHost, ctx->stream));
     SCK(cudaStreamSynchronize(ctx->stream));
+    TCK();
     return GS_OK;
 }
 
@@ -564,6 +623,7 @@ gs_status sur_set_normalization(sur_ctx* ctx, const double* mean, const double* 
 
 gs_status sur_forward(sur_ctx* ctx, const float* u, const float* v, float* uo, float* vo) {
     if (!ctx || !u || !v || !uo || !vo) return GS_ERR_INVALID;
+    TCK();
     gs_status st = forward(ctx, u, v);
     if (st != GS_OK) return st;
     residual_kernel<<<nsm_now() * 4, 256, 0, ctx->stream>>>(u, v, ctx->y, ctx->N, (float)ctx->scale[0],
@@ -575,6 +635,7 @@ gs_status sur_forward(sur_ctx* ctx, const float* u, const float* v, float* uo, f
 gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const float* ut, const float* vt, double lr,
                          double* loss) {
     if (!ctx || !u || !v || !ut || !vt || !(lr > 0)) return GS_ERR_INVALID;
+    TCK();
     const int D = ctx->nz, H = ctx->ny, W = ctx->nx;
     gs_status st = forward(ctx, u, v);
     if (st != GS_OK) return st;
@@ -591,7 +652,7 @@ gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const flo
     for (int l = 3; l >= 0; --l) {
         const LayerDims& L = kLayers[l];
         const void* xin = l == 0 ? ctx->x0 : ctx->a[l - 1];
-        SCK(launch_wgrad(L.cinp, L.coutp, D, H, W, xin, gin, ctx->ws, ctx->stream));
+        SCK(launch_wgrad(L.cinp, L.coutp, D, H, W, xin, gin, ctx->ws, ctx->stream, ctx->tcw.dev));
         wgrad_reduce_kernel<<<128, 256, 0, ctx->stream>>>(ctx->ws, wgrad_grid(), L.cinp, L.coutp, L.cin, L.cout,
                                                           ctx->g + layer_w_off(l));
         bias_grad_kernel<<<grid, 256, 0, ctx->stream>>>(static_cast<const __nv_bfloat16*>(gin), ctx->N, L.cout,
@@ -600,7 +661,7 @@ gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const flo
         if (l > 0) {
             void* gout = ctx->g32[l & 1];
             SCK(launch_conv(L.coutp, L.cinp, EPI_MASK_BF16, D, H, W, gin, ctx->wd[l], nullptr, ctx->a[l - 1], gout,
-                            L.cinp, ctx->stream));
+                            L.cinp, ctx->stream, ctx->tcw.dev));
             gin = gout;
         }
     }
@@ -614,6 +675,7 @@ gs_status sur_train_step(sur_ctx* ctx, const float* u, const float* v, const flo
     if (loss) {
         SCK(cudaMemcpyAsync(ctx->hacc, ctx->dacc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
         SCK(cudaStreamSynchronize(ctx->stream));
+        TCK();
         *loss = ctx->hacc[0];
     }
     return GS_OK;
@@ -623,12 +685,14 @@ gs_status sur_get_grad(sur_ctx* ctx, float* host) {
     if (!ctx || !host) return GS_ERR_INVALID;
     SCK(cudaMemcpyAsync(host, ctx->g, sizeof(float) * ctx->np, cudaMemcpyDeviceToHost, ctx->stream));
     SCK(cudaStreamSynchronize(ctx->stream));
+    TCK();
     return GS_OK;
 }
 
 gs_status sur_advance(sur_ctx* ctx, gs_ctx* integ, float* u, float* v, int judge, double threshold, double* rel_err,
                       int* fell_back) {
     if (!ctx || !u || !v || (judge && !integ)) return GS_ERR_INVALID;
+    TCK();
     if (fell_back) *fell_back = 0;
     if (rel_err) *rel_err = -1.0;
     const long long n = ctx->N;
@@ -644,11 +708,13 @@ gs_status sur_advance(sur_ctx* ctx, gs_ctx* integ, float* u, float* v, int judge
         SCK(cudaMemcpyAsync(u, ctx->su, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         SCK(cudaMemcpyAsync(v, ctx->sv, n * 4, cudaMemcpyDeviceToDevice, ctx->stream));
         SCK(cudaStreamSynchronize(ctx->stream));
+        TCK();
         return GS_OK;
     }
     // judge: 16 RK4 steps of dt = 0.1 on the same state (the integrator is
     // bound to u, v and updates them in place), then compare
     SCK(cudaStreamSynchronize(ctx->stream));
+    TCK();
     double t = 0.0;
     if ((st = gs_step(integ, GS_RK4, &t, 0.1, 16)) != GS_OK) return st;
     SCK(cudaMemsetAsync(ctx->dacc, 0, sizeof(double) * 2, ctx->stream));
@@ -693,8 +759,18 @@ gs_status sur_conv3d(int D, int H, int W, int cin_pad, int cout_pad, const void*
     if (!shape_ok(D, H, W) || !x || !packed || !out) return GS_ERR_INVALID;
     if (epi == EPI_MASK_BF16 && !mask) return GS_ERR_INVALID;
     if ((epi == EPI_BIAS_RELU_BF16 || epi == EPI_BIAS_F32) && !bias) return GS_ERR_INVALID;
-    cudaError_t e = launch_conv(cin_pad, cout_pad, epi, D, H, W, x, packed, bias, mask, out, out_ch,
-                                (cudaStream_t)stream);
+    cudaError_t e = cudaSuccess;
+    TimeoutWord* tw = primitive_word(&e);
+    if (!tw) {
+        set_global_error(e, "sur_conv3d (timeout word)");
+        return GS_ERR_CUDA;
+    }
+    if (tw->tripped()) {
+        set_global_error(cudaErrorLaunchTimeout, "sur_conv3d: an earlier tcgen05 launch gave up waiting");
+        return GS_ERR_CUDA;
+    }
+    e = launch_conv(cin_pad, cout_pad, epi, D, H, W, x, packed, bias, mask, out, out_ch, (cudaStream_t)stream,
+                    tw->dev);
     if (e == cudaErrorInvalidValue) return GS_ERR_INVALID;
     if (e != cudaSuccess) {
         set_global_error(e, "sur_conv3d");
@@ -715,11 +791,26 @@ int sur_conv_last_engine(void) { return g_conv_last_engine; }
 
 gs_status sur_conv_tc_status(unsigned int* timeouts) {
     if (!timeouts) return GS_ERR_INVALID;
-    cudaError_t e = cudaMemcpyFromSymbol(timeouts, tc::g_tc_timeouts, sizeof(unsigned int));
-    if (e != cudaSuccess) {
+    cudaError_t e = cudaSuccess;
+    TimeoutWord* tw = primitive_word(&e);
+    if (!tw) {
         set_global_error(e, "sur_conv_tc_status");
         return GS_ERR_CUDA;
     }
+    *timeouts = tw->tripped() ? 1u : 0u;
+    return GS_OK;
+}
+
+gs_status sur_debug_set_timeout_word(sur_ctx* ctx, unsigned int value) {
+    TimeoutWord* tw = nullptr;
+    if (ctx) {
+        tw = &ctx->tcw;
+    } else {
+        cudaError_t e = cudaSuccess;
+        tw = primitive_word(&e);
+    }
+    if (!tw || !tw->host) return GS_ERR_INVALID;
+    *reinterpret_cast<volatile unsigned int*>(tw->host) = value;
     return GS_OK;
 }
 
@@ -735,7 +826,17 @@ gs_status sur_conv3d_wgrad(int D, int H, int W, int cin_pad, int cout_pad, const
         cout < 1)
         return GS_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
-    cudaError_t e = launch_wgrad(cin_pad, cout_pad, D, H, W, x, dy, (float*)workspace, s);
+    cudaError_t e = cudaSuccess;
+    TimeoutWord* tw = primitive_word(&e);
+    if (!tw) {
+        set_global_error(e, "sur_conv3d_wgrad (timeout word)");
+        return GS_ERR_CUDA;
+    }
+    if (tw->tripped()) {
+        set_global_error(cudaErrorLaunchTimeout, "sur_conv3d_wgrad: an earlier tcgen05 launch gave up waiting");
+        return GS_ERR_CUDA;
+    }
+    e = launch_wgrad(cin_pad, cout_pad, D, H, W, x, dy, (float*)workspace, s, tw->dev);
     if (e == cudaSuccess) {
         wgrad_reduce_kernel<<<128, 256, 0, s>>>((const float*)workspace, wgrad_grid(), cin_pad, cout_pad, cin, cout,
                                                 dw);

@@ -236,8 +236,7 @@ def test_rk4_small_grid_path_matches_graph_path(prec, nsteps, ctas):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (8, 1, 1), (136, 13, 5)])
 @pytest.mark.parametrize("ty,depth", [(7, 2), (1, 1), (3, 3), (5, 1)])
-@pytest.mark.parametrize("bulk", [1, 0])
-def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, bulk):
+def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth):
     """Fixed Dopri5 steps with the stages in pairs (2+3, 4+5, 6+7 in one
     launch each, the first stage recomputed on a one-cell ring) against the
     oracle and against the single-stage kernels; ragged x tiles (132, 136,
@@ -257,8 +256,7 @@ def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, bulk):
         g = _gs(torch, dims, prec, u0, v0, **phys)
         gs.gs_set_dopri5_fusion(g.ctx, fusion)
         gs.gs_set_pair_config(g.ctx, -1, ty, depth)
-        gs.gs_set_pair_loader(g.ctx, bulk)
-        assert gs.gs_get_dopri5_fusion(g.ctx) == fusion and gs.gs_get_pair_loader(g.ctx) == bulk
+        assert gs.gs_get_dopri5_fusion(g.ctx) == fusion
         assert gs.gs_get_pair_configs(g.ctx) == [(ty, depth)] * 5
         t = g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
         assert abs(t - 0.75) < 1e-15
@@ -272,8 +270,7 @@ def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, bulk):
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(64, 20, 12), (132, 7, 9), (4, 4, 4), (260, 3, 2), (8, 1, 1), (136, 13, 5)])
 @pytest.mark.parametrize("ty,depth,nsteps", [(7, 2, 3), (1, 1, 2), (3, 3, 5)])
-@pytest.mark.parametrize("bulk", [1, 0])
-def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps, bulk):
+def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps):
     """Fixed-step RK4 as two pair launches (k1 and k2 from u; k3, k4 and the
     update without storing k3, k4) against the oracle and the four
     single-stage kernels; odd and even step counts (the state ends in either
@@ -293,7 +290,6 @@ def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps,
         gs.gs_set_small_grid_path(g.ctx, 0)
         gs.gs_set_dopri5_fusion(g.ctx, fusion)
         gs.gs_set_pair_config(g.ctx, -1, ty, depth)
-        gs.gs_set_pair_loader(g.ctx, bulk)
         assert gs.gs_get_rk4_fusion(g.ctx) == fusion
         t = g.step(gs.GS_RK4, 0.0, 0.2, nsteps)
         assert abs(t - 0.2 * nsteps) < 1e-12
@@ -302,26 +298,6 @@ def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps,
         g.close()
     if prec == 0:
         assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
-    assert gs.gs_pair_timeouts() == 0
-
-
-def test_pair_loaders_bit_identical():
-    """The TMA bulk-copy loader and the per-thread cp.async loader feed the
-    same values: bit-identical results (FP32 and FP64, ragged tiles)."""
-    torch = cuda_or_skip()
-    import paper_2309_05331_b300 as gs
-    for prec, dims in ((1, (136, 23, 9)), (0, (70, 13, 6))):
-        u0, v0 = si.gs_initial_state(*dims, seed=9)
-        res = []
-        for bulk in (1, 0):
-            g = _gs(torch, dims, prec, u0, v0, Du=2e-3, Dv=1e-3, L=3.0)
-            gs.gs_set_dopri5_fusion(g.ctx, 1)
-            gs.gs_set_pair_loader(g.ctx, bulk)
-            g.integrate_adaptive(1e-6, 1e-6, 0.0, 2.0, 0.05)
-            res.append((to_np(g.u), to_np(g.v)))
-            g.close()
-        assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
-    assert gs.gs_pair_timeouts() == 0
 
 
 def test_pairs_per_pair_configs_and_timing():

@@ -386,3 +386,47 @@ def test_network_gradient_tcgen05_matches_oracle_backprop(tc_engine):
     assert _rel(g.astype(np.float64), ref_g) < 2e-3
     s.close()
     assert _tc_timeouts(gs) == 0
+
+
+def test_timeout_mark_makes_every_call_fail():
+    """A tensor-core launch that gives up waiting marks its context failed;
+    the mark is set here from the host (no GPU fault or hang is provoked),
+    exactly as the kernel sets it.  Every later call on the context, and a
+    synchronising call, must return GS_ERR_CUDA instead of a result; the
+    layer primitives share one process-wide mark."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    L = gs.lib()
+    n = (16, 16, 4)
+    s = gs.Surrogate(*n)
+    u = torch.rand(n[::-1], dtype=torch.float32, device="cuda")
+    v = torch.rand(n[::-1], dtype=torch.float32, device="cuda")
+    uo, vo = torch.empty_like(u), torch.empty_like(v)
+    s.forward(u, v, uo, vo)
+    p0 = s.get_params()
+    assert L.sur_debug_set_timeout_word(s.ctx, 1) == 0
+    for call in (lambda: s.forward(u, v, uo, vo), s.get_params, s.get_grad,
+                 lambda: s.train_step(u, v, uo, vo, 1e-3)):
+        with pytest.raises(gs.GSError) as ei:
+            call()
+        assert ei.value.status == gs.GS_ERR_CUDA and "gave up" in str(ei.value)
+    assert L.sur_debug_set_timeout_word(s.ctx, 0) == 0
+    assert np.array_equal(s.get_params(), p0)
+    s.close()
+    # layer primitives: one process-wide mark
+    x = torch.zeros((4, 16, 16, 32), dtype=torch.bfloat16, device="cuda")
+    w = np.zeros((27, 32, 32))
+    packed, _ = _packed(torch, gs, w, 0)
+    out = torch.empty((4, 16, 16, 32), dtype=torch.float32, device="cuda")
+    args = (4, 16, 16, 32, 32, x.data_ptr(), packed.data_ptr(), None, 3, None, out.data_ptr(), 32, None)
+    assert L.sur_conv3d(*args) == 0
+    st = C.c_uint(7)
+    assert L.sur_conv_tc_status(C.byref(st)) == 0 and st.value == 0
+    assert L.sur_debug_set_timeout_word(None, 1) == 0
+    try:
+        assert L.sur_conv_tc_status(C.byref(st)) == 0 and st.value == 1
+        assert L.sur_conv3d(*args) == gs.GS_ERR_CUDA
+    finally:
+        assert L.sur_debug_set_timeout_word(None, 0) == 0
+    assert L.sur_conv3d(*args) == 0
+    torch.cuda.synchronize()

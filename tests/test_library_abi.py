@@ -1,5 +1,6 @@
 """The C-ABI library loads on a CPU-only host and exports every entry point
-declared in include/gs.h (no compute calls: there is no GPU here)."""
+declared in include/gs.h (the method's interface) and in the internal header
+of tuning, timing and test hooks (no compute calls: there is no GPU here)."""
 import os
 import re
 import subprocess
@@ -9,12 +10,16 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
+INTERNAL = os.path.join(ROOT, "paper_2309_05331_b300", "csrc", "gs_internal.h")
+
+
+def _declared(paths=None):
     names = set()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if not fn.endswith(".h"):
-            continue
-        src = open(os.path.join(ROOT, "include", fn)).read()
+    if paths is None:
+        paths = [os.path.join(ROOT, "include", fn) for fn in sorted(os.listdir(os.path.join(ROOT, "include")))
+                 if fn.endswith(".h")]
+    for path in paths:
+        src = open(path).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         # function declarations (a typedef of a function-pointer type declares no symbol)
         for m in re.finditer(r"^\s*(?!typedef\b)(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(",
@@ -35,10 +40,18 @@ def test_header_declares_the_named_boundary():
         assert name in d
 
 
+def test_public_header_holds_no_tuning_knobs():
+    pub, internal = _declared(), _declared([INTERNAL])
+    assert not (pub & internal)
+    for name in ("gs_set_tile", "gs_set_kernel_variant", "gs_set_pair_config", "gs_time_stages", "gs_time_pairs",
+                 "gsb_set_tile", "sur_set_conv_engine", "gs_measure_fp64_peak", "sur_debug_set_timeout_word"):
+        assert name in internal and name not in pub
+
+
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
     exported = {ln.split()[-1] for ln in out.splitlines() if " T " in ln}
-    missing = _declared() - exported
+    missing = (_declared() | _declared([INTERNAL])) - exported
     assert not missing, missing
 
 
@@ -47,7 +60,7 @@ def test_library_loads_through_the_binding(libpath):
     L = gs.lib()
     for name in gs.exported_names():
         assert hasattr(L, name)
-    assert set(gs.exported_names()) == _declared()
+    assert set(gs.exported_names()) == _declared() | _declared([INTERNAL])
     # a pure host query works without a GPU
     assert gs.ode_workspace_size(1000) >= 256 + 8000
 

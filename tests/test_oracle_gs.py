@@ -223,3 +223,32 @@ def test_dcpse_gs_fixed_point_and_reaction():
     fu, fv = oracle.gs_dcpse_rhs(p, u, v)
     assert np.allclose(fu, -0.4 * 0.09 + 0.053 * 0.6, rtol=1e-14, atol=1e-17)
     assert np.allclose(fv, 0.4 * 0.09 - 0.067 * 0.3, rtol=1e-14, atol=1e-17)
+
+
+def test_thread_count_does_not_change_results():
+    # the oracle's loops over cells may be shared among threads; every cell's
+    # operations and their order stay the same, so results are bit-identical.
+    # Run in a child process: OpenMP's thread pool must not meet a later fork.
+    import subprocess
+    import sys
+    code = r"""
+import numpy as np, oracle, synthetic_inputs as si
+p = oracle.GSParams(24, 20, 18, Du=2e-3, Dv=1e-3)
+u0, v0 = si.gs_initial_state(24, 20, 18, seed=3)
+out = []
+for th in (1, 4):
+    oracle.set_threads(th)
+    assert oracle.get_threads() == th
+    a = oracle.gs_integrate_const(p, u0, v0, oracle.DOPRI5, 0.2, 3)
+    b = oracle.gs_integrate_adaptive(p, u0, v0, 0.0, 2.0, 0.1, 1e-7, 1e-7, log_cap=100)
+    out.append((a, b))
+(a1, b1), (a4, b4) = out
+assert all(np.array_equal(x, y) for x, y in zip(a1, a4))
+assert np.array_equal(b1["u"], b4["u"]) and np.array_equal(b1["v"], b4["v"])
+assert np.array_equal(b1["dts"], b4["dts"]) and b1["n_rej"] == b4["n_rej"]
+print("ok")
+"""
+    import os
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stderr
