@@ -32,6 +32,10 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   ab_coefficients / AB 1..8    pinned: exactness on polynomials of degree
                                s - 1, the AB2/AB4 coefficients, observed
                                orders 1..8
+  am_coefficients / ABM 1..8   pinned: exactness on polynomials of degree
+                               s - 1 (not s), the trapezoidal and AM4
+                               weights, observed orders 1..8, exact
+                               quadrature of polynomial right-hand sides
   axpy                         pinned: exact small-integer sums
   dcpse_stencil / gs_dcpse_*   pinned: exact Laplacian of every polynomial of
                                degree <= 3 (not 4), second-order convergence
@@ -111,6 +115,10 @@ def lib():
                                                      C.c_double, C.c_double, C.c_double, C.c_double, C.c_long,
                                                      C.c_long, _dp, _dp, _lp, _lp, C.POINTER(C.c_int)]
         L.orc_ab_coefficients.argtypes = [C.c_int, _dp]
+        L.orc_am_coefficients.argtypes = [C.c_int, _dp]
+        L.orc_pw_integrate_abm.argtypes = [C.c_int, C.c_int, _dp, C.c_long, _dp, C.c_double, C.c_double,
+                                           C.c_long]
+        L.orc_gs_integrate_abm.argtypes = [C.POINTER(_GS), C.c_int, _dp, C.c_double, C.c_double, C.c_long]
         L.orc_pair_orders.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.orc_dcpse_stencil.argtypes = [C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int), _dp,
                                          C.c_int]
@@ -411,6 +419,30 @@ def pw_integrate_ab(steps, kind, x, dt, nsteps, t0=0.0, coef=None):
     if lib().orc_pw_integrate_ab(steps, kind, _p(c), x.size, _p(x), t0, dt, nsteps) != OK:
         raise ValueError(steps)
     return x
+
+
+def am_coefficients(steps):
+    """Adams-Moulton weights beta*_0..beta*_{s-1} (node t_{m+1} first)."""
+    beta = np.zeros(steps)
+    if lib().orc_am_coefficients(steps, _p(beta)) != OK:
+        raise ValueError(steps)
+    return beta
+
+
+def pw_integrate_abm(steps, kind, x, dt, nsteps, t0=0.0, coef=None):
+    """Adams-Bashforth-Moulton (PECE) with `steps` steps."""
+    x = _f64(x).copy()
+    c = _f64(coef) if coef is not None else None
+    if lib().orc_pw_integrate_abm(steps, kind, _p(c), x.size, _p(x), t0, dt, nsteps) != OK:
+        raise ValueError(steps)
+    return x
+
+
+def gs_integrate_abm(p: GSParams, u, v, steps, dt, nsteps, t0=0.0):
+    y = _pack(p, u, v)
+    if lib().orc_gs_integrate_abm(C.byref(p._c()), steps, _p(y), t0, dt, nsteps) != OK:
+        raise ValueError(steps)
+    return _unpack(p, y)
 
 
 def pair_orders(method):

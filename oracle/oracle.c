@@ -28,7 +28,9 @@
  *     used here is stated at orc_integrate_adaptive.
  *   - the Adams-Bashforth 4 multistep method (Table 1) started by RK4, and
  *     Adams-Bashforth with 1..8 steps (Table 1, Fig. 2c,d) with coefficients
- *     integrated from their definition.
+ *     integrated from their definition; Adams-Bashforth-Moulton with 1..8
+ *     steps (Table 1) as an Adams-Bashforth predictor and an Adams-Moulton
+ *     corrector (PECE), the weights likewise from their definition.
  *   - the further tableaux of Table 1: Cash-Karp 5(4) and Fehlberg 7(8), and
  *     the adaptive driver for any embedded pair; per-element adaptive
  *     integration of independent scalar ODEs (each its own step size).
@@ -224,7 +226,7 @@ static double orc_lap(const orc_gs* p, const double* w, int x, int y, int z) {
 
 /* Lap(w) for a whole field (exported for the Laplacian pins). */
 void orc_gs_laplacian(const orc_gs* p, const double* w, double* out) {
-    #pragma omp parallel for num_threads(orc_threads) schedule(static)
+    #pragma omp parallel for num_threads(orc_threads) schedule(static) if ((long)p->nx * p->ny * p->nz >= 4096)
     for (int z = 0; z < p->nz; ++z)
         for (int y = 0; y < p->ny; ++y)
             for (int x = 0; x < p->nx; ++x)
@@ -238,7 +240,7 @@ void orc_gs_rhs(const void* sys, double t, long n, const double* y, double* f) {
     (void)n; /* n == 2N */
     const double* u = y;
     const double* v = y + N;
-    #pragma omp parallel for num_threads(orc_threads) schedule(static)
+    #pragma omp parallel for num_threads(orc_threads) schedule(static) if ((long)p->nx * p->ny * p->nz >= 4096)
     for (int z = 0; z < p->nz; ++z)
         for (int yy = 0; yy < p->ny; ++yy)
             for (int x = 0; x < p->nx; ++x) {
@@ -392,7 +394,7 @@ void orc_gs_rhs_dcpse(const void* sys, double t, long n, const double* y, double
     const long N = (long)p->nx * p->ny * p->nz;
     const double* u = y;
     const double* v = y + N;
-    #pragma omp parallel for num_threads(orc_threads) schedule(static)
+    #pragma omp parallel for num_threads(orc_threads) schedule(static) if ((long)p->nx * p->ny * p->nz >= 4096)
     for (int z = 0; z < p->nz; ++z)
         for (int yy = 0; yy < p->ny; ++yy)
             for (int x = 0; x < p->nx; ++x) {
@@ -444,32 +446,62 @@ int orc_axpy(long n, int nterms, const double* a, const double* const* x, double
 /*   err  = dt * sum_i (b_i - bhat_i) k_i        (if err != NULL)             */
 /* k: s*n scratch (k_i at k + i*n), ytmp: n scratch.  yout may alias y.      */
 /* ------------------------------------------------------------------------ */
-void orc_rk_step(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, double t, double dt,
-                 const double* y, double* yout, double* err, double* k, double* ytmp) {
+/* The three element loops of a step, over elements [lo, hi). */
+static void orc_stage_input(const orc_tableau* T, int i, long n, double dt, const double* y, const double* k,
+                            double* ytmp, long lo, long hi) {
     const int s = T->s;
-    for (int i = 0; i < s; ++i) {
-#pragma omp parallel for num_threads(orc_threads) schedule(static)
-        for (long e = 0; e < n; ++e) {
-            double acc = 0.0;
-            for (int j = 0; j < i; ++j) acc += T->a[i * s + j] * k[(long)j * n + e];
-            ytmp[e] = y[e] + dt * acc;
-        }
-        F(sys, t + T->c[i] * dt, n, ytmp, k + (long)i * n);
+    for (long e = lo; e < hi; ++e) {
+        double acc = 0.0;
+        for (int j = 0; j < i; ++j) acc += T->a[i * s + j] * k[(long)j * n + e];
+        ytmp[e] = y[e] + dt * acc;
     }
-    if (err) {
-#pragma omp parallel for num_threads(orc_threads) schedule(static)
-        for (long e = 0; e < n; ++e) {
-            double acc = 0.0;
-            for (int i = 0; i < s; ++i) acc += (T->b[i] - T->bhat[i]) * k[(long)i * n + e];
-            err[e] = dt * acc;
-        }
+}
+static void orc_step_error(const orc_tableau* T, long n, double dt, const double* k, double* err, long lo,
+                           long hi) {
+    const int s = T->s;
+    for (long e = lo; e < hi; ++e) {
+        double acc = 0.0;
+        for (int i = 0; i < s; ++i) acc += (T->b[i] - T->bhat[i]) * k[(long)i * n + e];
+        err[e] = dt * acc;
     }
-#pragma omp parallel for num_threads(orc_threads) schedule(static)
-    for (long e = 0; e < n; ++e) {
+}
+static void orc_step_output(const orc_tableau* T, long n, double dt, const double* y, const double* k,
+                            double* yout, long lo, long hi) {
+    const int s = T->s;
+    for (long e = lo; e < hi; ++e) {
         double acc = 0.0;
         for (int i = 0; i < s; ++i) acc += T->b[i] * k[(long)i * n + e];
         yout[e] = y[e] + dt * acc;
     }
+}
+
+/* Runs body(lo, hi) over [0, n): on the calling thread for small n or one
+ * thread, else in contiguous blocks on orc_threads threads (each element is
+ * processed once, by the same operations, in any case). */
+#define ORC_FOR_ELEMENTS(n, CALL)                                                   \
+    do {                                                                            \
+        if ((n) < 4096 || orc_threads < 2) {                                        \
+            const long lo = 0, hi = (n);                                            \
+            CALL;                                                                   \
+        } else {                                                                    \
+            const long nb_ = 8L * orc_threads, sz_ = ((n) + nb_ - 1) / nb_;         \
+            _Pragma("omp parallel for num_threads(orc_threads) schedule(static)")  \
+            for (long b_ = 0; b_ < nb_; ++b_) {                                     \
+                const long lo = b_ * sz_, hi = lo + sz_ < (n) ? lo + sz_ : (n);     \
+                if (lo < hi) CALL;                                                  \
+            }                                                                       \
+        }                                                                           \
+    } while (0)
+
+void orc_rk_step(const orc_tableau* T, orc_rhs_fn F, const void* sys, long n, double t, double dt,
+                 const double* y, double* yout, double* err, double* k, double* ytmp) {
+    const int s = T->s;
+    for (int i = 0; i < s; ++i) {
+        ORC_FOR_ELEMENTS(n, orc_stage_input(T, i, n, dt, y, k, ytmp, lo, hi));
+        F(sys, t + T->c[i] * dt, n, ytmp, k + (long)i * n);
+    }
+    if (err) ORC_FOR_ELEMENTS(n, orc_step_error(T, n, dt, k, err, lo, hi));
+    ORC_FOR_ELEMENTS(n, orc_step_output(T, n, dt, y, k, yout, lo, hi));
 }
 
 /* integrate_const (Listing 3): nsteps fixed steps, t_m = t0 + m dt. */
@@ -691,6 +723,85 @@ int orc_integrate_ab(int s, orc_rhs_fn F, const void* sys, long n, double* y, do
     return ORC_OK;
 }
 
+/* Adams-Moulton weights with s nodes (the corrector of Table 1's
+ * Adams-Bashforth-Moulton, s = 1..8):
+ *   u_{m+1} = u_m + dt sum_{j<s} beta*_j f_{m+1-j},
+ * beta*_j = the integral over [t_m, t_m + dt] of the Lagrange basis
+ * polynomial of node t_{m+1-j} among t_{m+1}, t_m, ..., t_{m+2-s}, divided
+ * by dt.  In the unit variable tau (node m+1-j at tau = 1 - j):
+ *   beta*_j = int_0^1 prod_{i != j} (tau - 1 + i) / (i - j) dtau,
+ * expanded in powers of tau and integrated term by term. */
+int orc_am_coefficients(int s, double* beta) {
+    if (s < 1 || s > 8) return ORC_ERR_INVALID;
+    for (int j = 0; j < s; ++j) {
+        double poly[9] = {1.0, 0, 0, 0, 0, 0, 0, 0, 0}; /* coefficients of tau^0..tau^8 */
+        int deg = 0;
+        double denom = 1.0;
+        for (int i = 0; i < s; ++i) {
+            if (i == j) continue;
+            const double c = (double)(i - 1); /* multiply by (tau + c) */
+            for (int d = deg + 1; d >= 1; --d) poly[d] = poly[d - 1] + c * poly[d];
+            poly[0] = c * poly[0];
+            ++deg;
+            denom *= (double)(i - j);
+        }
+        double integral = 0.0;
+        for (int d = 0; d <= deg; ++d) integral += poly[d] / (double)(d + 1);
+        beta[j] = integral / denom;
+    }
+    return ORC_OK;
+}
+
+/* Adams-Bashforth-Moulton with s steps (Table 1: 1..8), as a
+ * predictor-corrector in PECE form (this build's reading; the paper names
+ * the method only): with f_m = F(t_m, u_m),
+ *   predict   u* = u_m + dt sum_{j<s} beta_j f_{m-j}        (Adams-Bashforth)
+ *   evaluate  f* = F(t_{m+1}, u*)
+ *   correct   u_{m+1} = u_m + dt (beta*_0 f* + sum_{1<=j<s} beta*_j f_{m+1-j})
+ *                                                            (Adams-Moulton)
+ *   evaluate  f_{m+1} = F(t_{m+1}, u_{m+1}) at the next step's start.
+ * t_m = t0 + m dt; the first s - 1 steps are one-step steps of order >= s,
+ * as for Adams-Bashforth (RK4 for s <= 4, the order-8 Fehlberg solution
+ * for s >= 5). */
+int orc_integrate_abm(int s, orc_rhs_fn F, const void* sys, long n, double* y, double t0, double dt,
+                      long nsteps) {
+    double beta[8], betas[8];
+    if (orc_ab_coefficients(s, beta) || orc_am_coefficients(s, betas)) return ORC_ERR_INVALID;
+    orc_tableau T;
+    orc_get_tableau(s <= 4 ? ORC_RK4 : ORC_RKF78, &T);
+    double* f = (double*)malloc(sizeof(double) * (size_t)n * (size_t)s);
+    double* k = (double*)malloc(sizeof(double) * (size_t)n * (size_t)T.s);
+    double* ytmp = (double*)malloc(sizeof(double) * (size_t)n);
+    double* fp = (double*)malloc(sizeof(double) * (size_t)n);
+    if (!f || !k || !ytmp || !fp) { free(f); free(k); free(ytmp); free(fp); return ORC_ERR_NOMEM; }
+    double* fm[8];
+    for (int j = 0; j < s; ++j) fm[j] = f + (long)j * n; /* fm[j] = f_{m-j} */
+    for (long m = 0; m < nsteps; ++m) {
+        const double t = t0 + (double)m * dt;
+        double* oldest = fm[s - 1];
+        for (int j = s - 1; j >= 1; --j) fm[j] = fm[j - 1];
+        fm[0] = oldest;
+        F(sys, t, n, y, fm[0]);
+        if (m < s - 1) {
+            orc_rk_step(&T, F, sys, n, t, dt, y, y, NULL, k, ytmp);
+            continue;
+        }
+        for (long e = 0; e < n; ++e) {
+            double acc = 0.0;
+            for (int j = 0; j < s; ++j) acc += beta[j] * fm[j][e];
+            ytmp[e] = y[e] + dt * acc;
+        }
+        F(sys, t0 + (double)(m + 1) * dt, n, ytmp, fp);
+        for (long e = 0; e < n; ++e) {
+            double acc = betas[0] * fp[e];
+            for (int j = 1; j < s; ++j) acc += betas[j] * fm[j - 1][e];
+            y[e] = y[e] + dt * acc;
+        }
+    }
+    free(f); free(k); free(ytmp); free(fp);
+    return ORC_OK;
+}
+
 /* Adams-Bashforth 4 (Table 1, multi-step), started with three RK4 steps:
  *   u_{m+1} = u_m + dt/24 (55 f_m - 59 f_{m-1} + 37 f_{m-2} - 9 f_{m-3}),
  * f_m = F(t_m, u_m), t_m = t0 + m dt.  nsteps counts all steps, the RK4
@@ -825,6 +936,14 @@ int orc_pw_integrate_ab(int steps, int kind, const double* coef, long n, double*
     orc_pointwise p = {kind, coef};
     return orc_integrate_ab(steps, orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
 }
+int orc_pw_integrate_abm(int steps, int kind, const double* coef, long n, double* y, double t0, double dt,
+                         long nsteps) {
+    orc_pointwise p = {kind, coef};
+    return orc_integrate_abm(steps, orc_pointwise_rhs, &p, n, y, t0, dt, nsteps);
+}
+int orc_gs_integrate_abm(const orc_gs* p, int steps, double* y, double t0, double dt, long nsteps) {
+    return orc_integrate_abm(steps, orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t0, dt, nsteps);
+}
 int orc_pw_integrate_adaptive_m(int method, int kind, const double* coef, long n, double* y, double* t,
                                 double t_end, double* dt, double atol, double rtol, long max_acc,
                                 long max_rej, long* n_acc, long* n_rej, double* log_dt, long log_cap) {
@@ -850,19 +969,21 @@ int orc_pw_integrate_adaptive_each(int method, int kind, const double* coef, lon
                                    double t_end, double dt0, double atol, double rtol, long max_acc,
                                    long max_rej, double* t_out, double* dt_out, long* n_acc, long* n_rej,
                                    int* status) {
+#pragma omp parallel for num_threads(orc_threads) schedule(dynamic, 64)
     for (long e = 0; e < n; ++e) {
         orc_pointwise p = {kind, coef ? coef + e : NULL};
         double t = t0, dt = dt0;
         long na = 0, nr = 0;
         const int st = orc_integrate_adaptive_m(method, orc_pointwise_rhs, &p, 1, y + e, &t, t_end, &dt, atol,
                                                 rtol, max_acc, max_rej, &na, &nr, NULL, 0);
-        if (st == ORC_ERR_INVALID || st == ORC_ERR_NOMEM) return st;
         t_out[e] = t;
         dt_out[e] = dt;
         n_acc[e] = na;
         n_rej[e] = nr;
         status[e] = st;
     }
+    for (long e = 0; e < n; ++e)
+        if (status[e] == ORC_ERR_INVALID || status[e] == ORC_ERR_NOMEM) return status[e];
     return ORC_OK;
 }
 /* One Dopri5 attempt on a pointwise system: yout, err, returns the norm. */

@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synthetic_inputs as si
-from tests._gpu_common import cuda_or_skip, to_np
+from tests._gpu_common import assert_parity, cuda_or_skip, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_batched_fp64_matches_oracle_per_instance():
         assert r["t"][i] == 5.0 and ref["t"] == 5.0
         assert (r["n_acc"][i], r["n_rej"][i]) == (ref["n_acc"], ref["n_rej"]), i
         gu, gv = b.view(i)
-        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-12, i
+        assert_parity([to_np(gu), to_np(gv)], [ref["u"], ref["v"]], 1e-12, i)
     b.close()
 
 
@@ -63,8 +63,7 @@ def test_batched_fp32_against_fp64_oracle():
         ref = _oracle_adaptive(d, *inits[i], 8.0, 1e-6)
         assert abs(int(r["n_acc"][i]) - ref["n_acc"]) <= 1
         gu, gv = b.view(i)
-        err = oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]])
-        assert err < 1e-5, (i, err)
+        assert_parity([to_np(gu), to_np(gv)], [ref["u"], ref["v"]], 1e-5, i)
     b.close()
 
 
@@ -83,7 +82,7 @@ def test_failure_of_one_instance_is_isolated():
         assert r["statuses"][i] == gs.GS_OK and r["t"][i] == 2.0
         ref = _oracle_adaptive(d, *inits[i], 2.0, 1e-8)
         gu, gv = b.view(i)
-        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-12, i
+        assert_parity([to_np(gu), to_np(gv)], [ref["u"], ref["v"]], 1e-12, i)
     b.close()
 
 
@@ -105,7 +104,7 @@ def test_batched_equals_single_grid_runs(depth):
         rs = g.integrate_adaptive(1e-8, 1e-8, 0.0, 3.0, 0.1)
         assert (rs["n_acc"], rs["n_rej"]) == (r["n_acc"][i], r["n_rej"][i])
         gu, gv = b.view(i)
-        assert oracle.rel_l2([to_np(gu), to_np(gv)], [to_np(g.u), to_np(g.v)]) < 1e-13
+        assert_parity([to_np(gu), to_np(gv)], [to_np(g.u), to_np(g.v)], 1e-13)
         g.close()
     b.close()
 
@@ -175,8 +174,12 @@ def test_batched_max_accepted_and_per_instance_times():
 
 def test_full_size_512_instance_ensemble():
     """512 instances, per-axis edges U{16..96}, F in [0.02,0.06], k in
-    [0.04,0.07], FP32 state / FP64 control, 3 accepted steps each; the three
-    smallest instances against the FP64 oracle."""
+    [0.04,0.07], FP32 state / FP64 control, 3 accepted steps each; EVERY
+    instance against the FP64 oracle's own adaptive run of it, cell by cell.
+    FP32 stages can flip an accept decision whose norm lies within rounding
+    of 1 against the FP64 oracle; such an instance (same accepted count,
+    different rejections or time) is a valid different run, not compared
+    cell by cell, and at most 2 % of the instances may be one."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     insts = si.batch_instances(512, seed=3)
@@ -189,15 +192,22 @@ def test_full_size_512_instance_ensemble():
     b.autotune()
     r = b.integrate_adaptive(1e-6, 1e-6, 0.0, np.inf, 0.1, max_accepted=3)
     assert np.all(r["statuses"] == 0) and np.all(r["n_acc"] == 3)
-    sizes = [d["nx"] * d["ny"] * d["nz"] for d in insts]
-    for i in np.argsort(sizes)[:3]:
-        d = insts[i]
-        u, v = (a.astype(np.float32).astype(np.float64) for a in inits[i])
-        p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], Du=2e-5, Dv=1e-5)
-        ref = oracle.gs_integrate_adaptive(p, u, v, 0.0, np.inf, 0.1, 1e-6, 1e-6, max_acc=3)
-        gu, gv = b.view(int(i))
-        assert abs(ref["t"] - r["t"][i]) < 1e-6 * max(1.0, ref["t"])
-        assert oracle.rel_l2([to_np(gu), to_np(gv)], [ref["u"], ref["v"]]) < 1e-5
+    diverged = []
+    oracle.set_threads(oracle.max_threads())
+    try:
+        for i, d in enumerate(insts):
+            u, v = (a.astype(np.float32).astype(np.float64) for a in inits[i])
+            p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], Du=2e-5, Dv=1e-5)
+            ref = oracle.gs_integrate_adaptive(p, u, v, 0.0, np.inf, 0.1, 1e-6, 1e-6, max_acc=3)
+            assert ref["status"] == oracle.OK and ref["n_acc"] == 3
+            if ref["n_rej"] != r["n_rej"][i] or abs(ref["t"] - r["t"][i]) > 1e-6 * max(1.0, ref["t"]):
+                diverged.append(i)
+                continue
+            gu, gv = b.view(i)
+            assert_parity([to_np(gu), to_np(gv)], [ref["u"], ref["v"]], 1e-5, i)
+    finally:
+        oracle.set_threads(1)
+    assert len(diverged) <= 0.02 * len(insts), diverged
     b.close()
 
 

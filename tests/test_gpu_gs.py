@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synthetic_inputs as si
-from tests._gpu_common import cuda_or_skip, periodic_box, to_np
+from tests._gpu_common import assert_parity, cuda_or_skip, periodic_box, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_rhs_fp64(dims):
     fu, fv = g.rhs()
     torch.cuda.synchronize()
     eu, ev = oracle.gs_rhs(oracle.GSParams(*dims, **phys), u0, v0)
-    assert oracle.rel_l2([to_np(fu), to_np(fv)], [eu, ev]) < 1e-14
+    assert_parity([to_np(fu), to_np(fv)], [eu, ev], 1e-14)
     g.close()
 
 
@@ -58,7 +58,7 @@ def test_rhs_fp32(dims):
     fu, fv = g.rhs()
     torch.cuda.synchronize()
     eu, ev = oracle.gs_rhs(oracle.GSParams(*dims), u0, v0)
-    assert oracle.rel_l2([to_np(fu), to_np(fv)], [eu, ev]) < 1e-6
+    assert_parity([to_np(fu), to_np(fv)], [eu, ev], 1e-6)
     g.close()
 
 
@@ -72,7 +72,7 @@ def test_rk4_32cubed_fp64_100_steps():
     t = g.step(gs.GS_RK4, 0.0, 0.1, 100)
     assert t == pytest.approx(10.0, abs=1e-12)
     ou, ov = oracle.gs_integrate_const(oracle.GSParams(n, n, n), u0, v0, oracle.RK4, 0.1, 100)
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL)
     g.close()
 
 
@@ -85,8 +85,7 @@ def test_rk4_32cubed_fp32():
     g = _gs(torch, (n, n, n), gs.GS_FP32, u0, v0)
     g.step(gs.GS_RK4, 0.0, 0.1, 100)
     ou, ov = oracle.gs_integrate_const(oracle.GSParams(n, n, n), u0, v0, oracle.RK4, 0.1, 100)
-    err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov])
-    assert err < FP32_TOL, err
+    err = assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP32_TOL)
     g.close()
 
 
@@ -108,7 +107,7 @@ def test_fixed_step_methods_fp64(dims, method, nsteps):
     else:
         om = {"euler": oracle.EULER, "rk4": oracle.RK4, "dopri5": oracle.DOPRI5}[method]
         ou, ov = oracle.gs_integrate_const(p, u0, v0, om, dt, nsteps)
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL)
     g.close()
 
 
@@ -167,9 +166,9 @@ def test_kernel_variants_match_oracle(prec, dims):
                 assert gs.gs_get_kernel_variant(g.ctx) == 4
                 assert gs.gs_get_stage_depths(g.ctx) == [depth] * 7
             g.step(method, 0.0, 0.25, 3)
-            err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov])
+            got = [to_np(g.u), to_np(g.v)]
             g.close()
-            assert err < tol, (variant, depth, method, err)
+            assert_parity(got, [ou, ov], tol, (variant, depth, method))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -195,10 +194,10 @@ def test_split_stages_match_unsplit_and_oracle(prec, dims):
         gs.gs_set_dopri5_split(g.ctx, split)
         g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
         res.append((to_np(g.u), to_np(g.v)))
-        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, split
+        assert_parity(list(res[-1]), [ou, ov], tol, split)
         g.close()
     if prec == 0:
-        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+        assert_parity(list(res[0]), list(res[1]), 1e-13)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -228,9 +227,9 @@ def test_rk4_small_grid_path_matches_graph_path(prec, nsteps, ctas):
     ou, ov = oracle.gs_integrate_const(oracle.GSParams(*dims, **phys), u0, v0, oracle.RK4, 0.2, nsteps)
     tol = FP64_TOL if prec == 0 else FP32_TOL
     for r in res:
-        assert oracle.rel_l2(list(r), [ou, ov]) < tol
+        assert_parity(list(r), [ou, ov], tol)
     if prec == 0:
-        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-14
+        assert_parity(list(res[0]), list(res[1]), 1e-14)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -261,10 +260,10 @@ def test_pairs_match_single_stages_and_oracle(prec, dims, ty, depth):
         t = g.step(gs.GS_DOPRI5, 0.0, 0.25, 3)
         assert abs(t - 0.75) < 1e-15
         res.append((to_np(g.u), to_np(g.v)))
-        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, fusion
+        assert_parity(list(res[-1]), [ou, ov], tol, fusion)
         g.close()
     if prec == 0:
-        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+        assert_parity(list(res[0]), list(res[1]), 1e-13)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -294,10 +293,10 @@ def test_rk4_pairs_match_single_stages_and_oracle(prec, dims, ty, depth, nsteps)
         t = g.step(gs.GS_RK4, 0.0, 0.2, nsteps)
         assert abs(t - 0.2 * nsteps) < 1e-12
         res.append((to_np(g.u), to_np(g.v)))
-        assert oracle.rel_l2(list(res[-1]), [ou, ov]) < tol, fusion
+        assert_parity(list(res[-1]), [ou, ov], tol, fusion)
         g.close()
     if prec == 0:
-        assert oracle.rel_l2(list(res[0]), list(res[1])) < 1e-13
+        assert_parity(list(res[0]), list(res[1]), 1e-13)
 
 
 def test_pairs_per_pair_configs_and_timing():
@@ -411,7 +410,7 @@ def test_adaptive_fp64_matches_oracle_run(fusion, split):
     assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"])
     # E is a cancelling sum: FMA vs non-FMA rounding moves it by ~1e-9 relative
     assert np.allclose(dts, ref["dts"], rtol=1e-7, atol=0), np.max(np.abs(dts / ref["dts"] - 1))
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]]) < FP64_TOL
+    assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP64_TOL)
     g.close()
 
 
@@ -427,8 +426,7 @@ def test_adaptive_fp32_against_fp64_oracle():
     ref = oracle.gs_integrate_adaptive(oracle.GSParams(n, n, n), u0, v0, 0.0, 50.0, 0.1, 1e-6, 1e-6)
     assert r["status"] == 0 and r["t"] == 50.0
     assert abs(r["n_acc"] - ref["n_acc"]) <= max(1, 0.01 * ref["n_acc"])
-    err = oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]])
-    assert err < FP32_TOL, err
+    err = assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP32_TOL)
     g.close()
 
 
@@ -496,29 +494,46 @@ def test_invalid_calls():
 
 def _light_cone_check(state_after, u0, v0, dims, method, dt, nsteps, radius, centers, tol):
     """Oracle values of sampled cells computed on periodic boxes around them
-    (the dependence cone of nsteps steps lies inside the box)."""
-    num, den = 0.0, 0.0
+    (the dependence cone of nsteps steps lies inside the box).  Each sampled
+    cell is checked on its own (|gpu - oracle| <= tol * max |oracle| over the
+    samples, per component) and the samples pooled by relative L2."""
     gu, gv = state_after
     h = [2.5 / n for n in dims]
     e = 2 * radius + 1
     p = oracle.GSParams(e, e, e, L=e * h[0], Ly=e * h[1], Lz=e * h[2])
+    got, ref = [], []
     for c in centers:
         bu, bv = periodic_box(u0, c, radius), periodic_box(v0, c, radius)
         ou, ov = oracle.gs_integrate_const(p, bu, bv, method, dt, nsteps)
-        ref = np.array([ou[radius, radius, radius], ov[radius, radius, radius]])
-        got = np.array([gu[c], gv[c]])
-        num += float(np.sum((got - ref) ** 2))
-        den += float(np.sum(ref ** 2))
-    err = math.sqrt(num / den)
-    assert err < tol, err
+        ref.append([ou[radius, radius, radius], ov[radius, radius, radius]])
+        got.append([gu[c], gv[c]])
+    got, ref = np.array(got), np.array(ref)
+    assert_parity([got[:, 0], got[:, 1]], [ref[:, 0], ref[:, 1]], tol, "sampled cells")
+
+
+def _seam_centers(n, ty, rng, count=64):
+    """Sample cells (z, y, x) of an n^3 grid on the places a tiling can get
+    wrong: x at the periodic seam and at the 128-cell row boundaries, y at the
+    periodic seam and at tile-height boundaries, z at the seam and at the
+    middle (where two z-bands of the column-split schedule meet), plus random
+    cells; count in total."""
+    xs = sorted({0, 1, 126, 127, 128, 129, n - 2, n - 1})
+    ys = sorted({0, ty - 1, ty, 2 * ty - 1, 2 * ty, (n // ty) * ty - 1, (n // ty) * ty, n - 1} - {n})
+    zs = sorted({0, n // 2 - 1, n // 2, n // 4, n - 1})
+    grid = [(z, y, x) for z in zs for y in ys for x in xs]
+    pick = rng.choice(len(grid), size=min(count - 16, len(grid)), replace=False)
+    centers = [grid[i] for i in sorted(pick)]
+    centers += [tuple(int(a) for a in rng.integers(0, n, 3)) for _ in range(count - len(centers))]
+    return centers
 
 
 @pytest.mark.parametrize("fusion", [1, 0])
 def test_full_size_256cubed_fp32_dopri5_sampled(fusion):
     """256^3 FP32 (the large adaptive workload's grid and kernels, autotuned
-    launch shapes; stage pairs and single stages): 3 fixed Dopri5 steps, 12
-    sampled cells against the oracle on their dependence cones (radius 6 per
-    step)."""
+    launch shapes; stage pairs and single stages): 3 fixed Dopri5 steps, 64
+    sampled cells -- on the periodic seams, the row and tile-height
+    boundaries and the z-band joins -- each against the oracle on its
+    dependence cone (radius 6 per step)."""
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
     n = 256
@@ -529,10 +544,14 @@ def test_full_size_256cubed_fp32_dopri5_sampled(fusion):
     gs.gs_set_dopri5_fusion(g.ctx, fusion)  # the tuned launch shapes of either path
     g.step(gs.GS_DOPRI5, 0.0, 0.5, 3)
     gu, gv = to_np(g.u), to_np(g.v)
-    rng = np.random.default_rng(0)
-    centers = [tuple(int(a) for a in rng.integers(0, n, 3)) for _ in range(8)]
-    centers += [(0, 0, 0), (255, 255, 255), (128, 100, 96), (96, 96, 159)]
-    _light_cone_check((gu, gv), u0, v0, (n, n, n), oracle.DOPRI5, 0.5, 3, 19, centers, FP32_TOL)
+    ty = gs.gs_get_pair_configs(g.ctx)[2][0] if fusion else gs.gs_get_stage_configs(g.ctx)[6][1]
+    centers = _seam_centers(n, ty, np.random.default_rng(0))
+    assert len(centers) == 64
+    oracle.set_threads(oracle.max_threads())
+    try:
+        _light_cone_check((gu, gv), u0, v0, (n, n, n), oracle.DOPRI5, 0.5, 3, 19, centers, FP32_TOL)
+    finally:
+        oracle.set_threads(1)
     g.close()
 
 
@@ -548,7 +567,28 @@ def test_full_size_256cubed_adaptive_properties():
     assert r["status"] == 0 and r["n_acc"] == 10 and cnt == 10
     assert r["t"] == pytest.approx(float(np.sum(dts)), rel=1e-14)
     assert bool(torch.isfinite(g.u).all()) and bool(torch.isfinite(g.v).all())
+    # the accepted steps replayed by the oracle (fixed Dormand-Prince steps of
+    # the logged sizes) on the dependence cones of sampled cells: radius 6 per
+    # step (y5 uses k1..k6), 10 steps
+    gu, gv = to_np(g.u), to_np(g.v)
     g.close()
+    u32, v32 = _round32(u0), _round32(v0)
+    radius = 61
+    e = 2 * radius + 1
+    p = oracle.GSParams(e, e, e, L=e * 2.5 / n)
+    centers = [(0, 0, 0), (255, 130, 127), (128, 7, 128), (96, 251, 255), (160, 160, 96), (31, 200, 64)]
+    oracle.set_threads(oracle.max_threads())
+    got, ref = [], []
+    try:
+        for c in centers:
+            bu, bv = periodic_box(u32, c, radius), periodic_box(v32, c, radius)
+            ou, ov = oracle.gs_integrate_replay(p, bu, bv, oracle.DOPRI5, dts)
+            ref.append([ou[radius, radius, radius], ov[radius, radius, radius]])
+            got.append([gu[c], gv[c]])
+    finally:
+        oracle.set_threads(1)
+    got, ref = np.array(got), np.array(ref)
+    assert_parity([got[:, 0], got[:, 1]], [ref[:, 0], ref[:, 1]], FP32_TOL, "adaptive 256^3 sampled cells")
 
 
 # ------------------------------------------------------------ DC-PSE Laplacian
@@ -587,7 +627,7 @@ def test_dcpse_rhs_matches_oracle(prec, dims):
     fu, fv = g.rhs()
     ou, ov = oracle.gs_dcpse_rhs(oracle.GSParams(*dims, **PAPER_GS), u0, v0)
     tol = FP64_TOL if prec == 0 else FP32_TOL
-    assert oracle.rel_l2([to_np(fu), to_np(fv)], [ou, ov]) < tol
+    assert_parity([to_np(fu), to_np(fv)], [ou, ov], tol)
     g.close()
 
 
@@ -607,7 +647,7 @@ def test_dcpse_fixed_steps_match_oracle(prec, method, omethod):
     assert t == 4.0
     ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, omethod, 1.0, 4)
     tol = FP64_TOL if prec == 0 else FP32_TOL
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < tol
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], tol)
     with pytest.raises(RuntimeError):
         g.step(gs.GS_AB4, 0.0, 1.0, 4)
     g.close()
@@ -644,11 +684,11 @@ def test_dcpse_tile_depths_agree(prec):
     p = oracle.GSParams(*dims, **PAPER_GS)
     ou, ov = oracle.gs_dcpse_integrate_const(p, u0, v0, oracle.RK4, 1.0, 3)
     bar = FP64_TOL if prec == 0 else FP32_TOL
-    assert oracle.rel_l2(list(runs[4][0]), [ou, ov]) < bar
+    assert_parity(list(runs[4][0]), [ou, ov], bar)
     if prec == 0:  # the FP64 run takes the oracle's steps
         ref = oracle.gs_dcpse_integrate_adaptive(p, ou, ov, 3.0, 6.0, 1.0, tol, tol)
         assert (ref["n_acc"], ref["n_rej"]) == runs[4][3:]
-        assert oracle.rel_l2([runs[4][1], runs[4][2]], [ref["u"], ref["v"]]) < bar
+        assert_parity([runs[4][1], runs[4][2]], [ref["u"], ref["v"]], bar)
 
 
 def test_dcpse_adaptive_fp64_matches_oracle_run():
@@ -668,7 +708,7 @@ def test_dcpse_adaptive_fp64_matches_oracle_run():
     assert r["status"] == 0 and ref["status"] == 0 and r["t"] == 20.0
     assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"]) and cnt == r["n_acc"]
     assert np.allclose(dts, ref["dts"], rtol=1e-7, atol=0)
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]]) < FP64_TOL
+    assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP64_TOL)
     g.close()
 
 
@@ -684,5 +724,5 @@ def test_dcpse_paper_workload_64cubed_rk4():
     gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
     g.step(gs.GS_RK4, 0.0, 1.0, 20)
     ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, oracle.RK4, 1.0, 20)
-    assert oracle.rel_l2([to_np(g.u), to_np(g.v)], [ou, ov]) < FP64_TOL
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL)
     g.close()

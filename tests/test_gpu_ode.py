@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synthetic_inputs as si
-from tests._gpu_common import cuda_or_skip, to_np
+from tests._gpu_common import assert_parity, cuda_or_skip, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -35,7 +35,7 @@ def test_adaptive_matches_oracle_run(kind, okind, n):
     # relative, and the step sequence carries that drift along
     d = to_np(log)[: r["n_acc"]]
     assert np.allclose(d, ref["dts"], rtol=1e-7, atol=0), np.max(np.abs(d / ref["dts"] - 1))
-    assert oracle.rel_l2(to_np(x), ref["x"]) < 1e-12
+    assert_parity(to_np(x), ref["x"], 1e-12)
 
 
 @pytest.mark.parametrize("kind,okind", KINDS)
@@ -48,7 +48,7 @@ def test_fixed_step_matches_oracle(kind, okind, method, omethod):
     gs.ode_integrate_const(kind, method, x, 0.0, 0.05, 200)
     torch.cuda.synchronize()
     ref = oracle.pw_integrate_const(okind, x0, omethod, 0.05, 200)
-    assert oracle.rel_l2(to_np(x), ref) < 1e-13
+    assert_parity(to_np(x), ref, 1e-13)
 
 
 @pytest.mark.parametrize("kind,okind", KINDS)
@@ -61,7 +61,7 @@ def test_ab4_matches_oracle(kind, okind, nsteps):
     gs.ode_integrate_ab4(kind, x, 0.0, 0.01, nsteps)
     torch.cuda.synchronize()
     ref = oracle.pw_integrate_ab4(okind, x0, 0.01, nsteps)
-    assert oracle.rel_l2(to_np(x), ref) < 1e-13
+    assert_parity(to_np(x), ref, 1e-13)
 
 
 @pytest.mark.parametrize("kind,okind", KINDS)
@@ -92,7 +92,7 @@ def test_full_size_ab4_sampled(kind, okind):
     got = to_np(x)
     idx = np.random.default_rng(3).choice(n, 2048, replace=False)
     ref = oracle.pw_integrate_ab4(okind, x0[idx], 1e-3, 10000)
-    assert oracle.rel_l2(got[idx], ref) < 1e-12
+    assert_parity(got[idx], ref, 1e-12)
     assert np.max(np.abs(got - _exact(kind, x0, 10.0))) < 1e-10
 
 
@@ -300,3 +300,34 @@ def test_adaptive_each_full_size_sampled():
     idx = np.random.default_rng(0).choice(n, 64, replace=False)
     ref = oracle.pw_integrate_adaptive_each(0, x0[idx], 0.0, 10.0, 1e-3, 1e-8, 1e-8)
     assert np.allclose(got[idx], ref["x"], rtol=1e-11, atol=0)
+
+
+def test_adaptive_each_lanes_refill_from_their_chunk():
+    """2,000,000 logistic elements, Dormand-Prince per element: every warp's
+    chunk holds several elements per lane, so lanes whose element stops take
+    the chunk's next one many times over (the refill path).  EVERY element
+    against the oracle's run of it alone: status, t, accepted / rejected
+    counts (identical for > 99.5 %; an FMA-rounded error ratio at E = 1
+    flips a decision only by chance) and the state."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    n = 2_000_000
+    x0 = si.ode_initial_values(n, seed=7)
+    x = _cuda(torch, x0)
+    r = gs.ode_integrate_adaptive_each(1, gs.ODE_TAB_DOPRI5, x, 0.0, 10.0, 1e-3, 1e-8, 1e-8)
+    torch.cuda.synchronize()
+    oracle.set_threads(oracle.max_threads())
+    try:
+        ref = oracle.pw_integrate_adaptive_each(oracle.PW_LOGISTIC, x0, 0.0, 10.0, 1e-3, 1e-8, 1e-8)
+    finally:
+        oracle.set_threads(1)
+    st, na, nr = to_np(r["status"]), to_np(r["n_acc"]), to_np(r["n_rej"])
+    assert np.all(st == 0) and np.all(ref["status"] == 0)
+    assert np.all(to_np(r["t"]) == 10.0) and np.all(ref["t"] == 10.0)
+    same = (na == ref["n_acc"]) & (nr == ref["n_rej"])
+    assert same.mean() > 0.995, np.sum(~same)
+    assert nr.sum() > 0 and len(set(na.tolist())) > 5  # rejections happen; elements take their own steps
+    got = to_np(x)
+    err = np.abs(got - ref["x"]) / (1.0 + np.abs(ref["x"]))
+    assert np.max(err[same]) < 1e-11
+    assert np.max(err) < 1e-7

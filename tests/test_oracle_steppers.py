@@ -349,3 +349,75 @@ def test_adaptive_global_norm_any_pair_closed_form(method):
     r = oracle.pw_integrate_adaptive(oracle.PW_PAPER_EXP, x0, t0, t1, 0.1, 1e-9, 1e-9, coef=coef, method=method)
     assert r["status"] == oracle.OK and r["t"] == t1
     assert np.max(np.abs(r["x"] - exact) / (1.0 + np.abs(exact))) < 5e-9
+
+
+# ------------------------------------------- Adams-Bashforth-Moulton (Table 1)
+@pytest.mark.parametrize("steps", range(1, 9))
+def test_am_coefficients_exact_on_polynomials(steps):
+    # the Adams-Moulton rule with s nodes t_{m+1}, ..., t_{m+2-s} integrates
+    # polynomials of degree < s over [t_m, t_{m+1}] exactly:
+    # sum_j beta*_j (1 - j)^k = 1 / (k + 1) for k = 0 .. s-1, not for k = s
+    beta = oracle.am_coefficients(steps)
+    node = 1.0 - np.arange(steps)
+    for k in range(steps):
+        lhs = float(np.sum(beta * node ** k))
+        assert abs(lhs - 1.0 / (k + 1)) < 1e-12 * max(1.0, float(np.sum(np.abs(beta * node ** k)))), (k, lhs)
+    assert abs(float(np.sum(beta * node ** steps)) - 1.0 / (steps + 1)) > 1e-6
+
+
+def test_am_coefficients_known_rules():
+    # implicit Euler, the trapezoidal rule and the 4-node Adams-Moulton rule
+    assert np.array_equal(oracle.am_coefficients(1), [1.0])
+    assert np.allclose(oracle.am_coefficients(2), [0.5, 0.5], rtol=1e-15, atol=0)
+    assert np.allclose(oracle.am_coefficients(3), np.array([5, 8, -1]) / 12, rtol=1e-14, atol=0)
+    assert np.allclose(oracle.am_coefficients(4), np.array([9, 19, -5, 1]) / 24, rtol=1e-14, atol=0)
+
+
+def test_abm_one_pece_step_by_hand():
+    # s = 2 on dx/dt = -x with the history seeded by one RK4 step: the
+    # predictor, the evaluation and the corrector written out
+    x0, dt = 0.8, 0.1
+    x1 = x0 * (1 - dt + dt ** 2 / 2 - dt ** 3 / 6 + dt ** 4 / 24)  # RK4 on -x
+    f0, f1 = -x0, -x1
+    xp = x1 + dt * (1.5 * f1 - 0.5 * f0)
+    x2 = x1 + dt * (0.5 * (-xp) + 0.5 * f1)
+    got = oracle.pw_integrate_abm(2, oracle.PW_EXP_DECAY, np.array([x0]), dt, 2)
+    assert abs(got[0] - x2) < 1e-15
+    # and differs from plain Adams-Bashforth 2 (the corrector acts)
+    ab = oracle.pw_integrate_ab(2, oracle.PW_EXP_DECAY, np.array([x0]), dt, 2)
+    assert abs(ab[0] - x2) > 1e-6
+
+
+@pytest.mark.parametrize("steps", range(1, 9))
+def test_abm_observed_order_exponential_family(steps):
+    # the exponential family (Eq. 1a) with 1..8 steps shows order s
+    x0, t0, t1, coef = _family(oracle.PW_PAPER_EXP)
+    exact = _closed_form(oracle.PW_PAPER_EXP, x0, t0, t1, coef)
+    errs = []
+    for m in (100, 200):
+        x = oracle.pw_integrate_abm(steps, oracle.PW_PAPER_EXP, x0, (t1 - t0) / m, m, t0=t0, coef=coef)
+        errs.append(oracle.linf(x - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - steps) < 0.4, errs
+
+
+@pytest.mark.parametrize("steps", range(1, 7))
+def test_abm_observed_order_decay(steps):
+    x0, t0, t1, coef = _family(oracle.PW_EXP_DECAY)
+    exact = _closed_form(oracle.PW_EXP_DECAY, x0, t0, t1, coef)
+    errs = []
+    for m in (200, 400):
+        x = oracle.pw_integrate_abm(steps, oracle.PW_EXP_DECAY, x0, (t1 - t0) / m, m, t0=t0)
+        errs.append(oracle.linf(x - exact))
+    assert abs(math.log2(errs[0] / errs[1]) - steps) < 0.45, errs
+
+
+@pytest.mark.parametrize("steps", [2, 4, 6])
+def test_abm_more_accurate_than_ab(steps):
+    # the corrector's error constant is smaller than the predictor's (e.g.
+    # 1/24 against 251/720 at s = 4): same order, smaller error
+    x0, t0, t1, coef = _family(oracle.PW_LOGISTIC)
+    exact = _closed_form(oracle.PW_LOGISTIC, x0, t0, t1, coef)
+    m = 200
+    e_ab = oracle.linf(oracle.pw_integrate_ab(steps, oracle.PW_LOGISTIC, x0, (t1 - t0) / m, m, t0=t0) - exact)
+    e_abm = oracle.linf(oracle.pw_integrate_abm(steps, oracle.PW_LOGISTIC, x0, (t1 - t0) / m, m, t0=t0) - exact)
+    assert e_abm < 0.5 * e_ab, (e_abm, e_ab)
