@@ -378,14 +378,17 @@ def extra_workloads(torch, gs, si):
             "roofline": fp64_roofline(m * 1e4 * ops, ms, {"element-step": ops})}
     # the paper's accuracy families (Eq. 1a: c = x y on a 4096 x 4096 grid of
     # (x, y) in [0,1]^2, from the closed form at t = -5 to t = 5), Table 1's
-    # Fehlberg 7(8) and Adams-Bashforth 8 with fixed steps
+    # Fehlberg 7(8), Adams-Bashforth 8 and Adams-Bashforth-Moulton 8 with
+    # fixed steps
     g1 = torch.linspace(0.0, 1.0, 4096, dtype=torch.float64, device="cuda")
     coef = torch.outer(g1, g1).reshape(-1).contiguous()
     xe0 = coef * math.exp(-5.0)
     for label, run, steps in (
             ("rkf78", lambda x: gs.ode_integrate_tableau(gs.ODE_PAPER_EXP, gs.ODE_TAB_RKF78, x, -5.0, 0.1, 100,
                                                          coef=coef), 100),
-            ("ab8", lambda x: gs.ode_integrate_ab_steps(gs.ODE_PAPER_EXP, 8, x, -5.0, 0.01, 1000, coef=coef), 1000)):
+            ("ab8", lambda x: gs.ode_integrate_ab_steps(gs.ODE_PAPER_EXP, 8, x, -5.0, 0.01, 1000, coef=coef), 1000),
+            ("abm8", lambda x: gs.ode_integrate_abm_steps(gs.ODE_PAPER_EXP, 8, x, -5.0, 0.01, 1000, coef=coef),
+             1000)):
         x = xe0.clone()
         run(x)  # warm-up
         x = xe0.clone()
@@ -415,8 +418,9 @@ def extra_workloads(torch, gs, si):
             "element_steps_per_s": acc / (ms * 1e-3)}
     # the paper's own Gray-Scott run: 64^3 on [0,2.5]^3, d1 = 2e-4, d2 = 1e-4,
     # F = 0.053, K = 0.014, DC-PSE Laplacian (122-point stencil), dt = 1 to
-    # t_f = 20, FP64: RK4 and Dormand-Prince with fixed steps, and adaptive
-    # Dormand-Prince (tolerance 1e-8)
+    # t_f = 20, FP64: RK4, Dormand-Prince and Fehlberg 7(8) (the paper's three
+    # Gray-Scott steppers) with fixed steps, and adaptive Dormand-Prince
+    # (tolerance 1e-8)
     n64 = 64
     u64, v64 = si.gs_initial_state(n64, n64, n64, seed=2)
     g = gs.GrayScott(n64, n64, n64, Du=2e-4, Dv=1e-4, F=0.053, k=0.014, prec=gs.GS_FP64)
@@ -425,6 +429,7 @@ def extra_workloads(torch, gs, si):
     for label, meth, run in (
             ("rk4_dt1_t20", "rk4", lambda: g.step(gs.GS_RK4, 0.0, 1.0, 20)),
             ("dopri5_dt1_t20", "dopri5_fixed", lambda: g.step(gs.GS_DOPRI5, 0.0, 1.0, 20)),
+            ("rkf78_dt1_t20", "rkf78_fixed", lambda: g.step(gs.GS_RKF78, 0.0, 1.0, 20)),
             ("dopri5_adaptive_tol1e-8_t20", "dopri5_adaptive",
              lambda: g.integrate_adaptive(1e-8, 1e-8, 0.0, 20.0, 1.0))):
         g.set_state(torch.from_numpy(u64), torch.from_numpy(v64))
@@ -468,7 +473,7 @@ def dcpse_fp64_ops_per_cell(method, npair):
     combination (s + 1 for s stages; the adaptive attempt adds the error
     terms and their scaling, s + 5)."""
     stage = 2 * npair + 1 + 5
-    s = {"rk4": 4, "dopri5_fixed": 6, "dopri5_adaptive": 7}[method]  # fixed steps skip stage 7 (b7 = 0)
+    s = {"rk4": 4, "dopri5_fixed": 6, "dopri5_adaptive": 7, "rkf78_fixed": 13}[method]  # fixed Dormand-Prince skips stage 7 (b7 = 0)
     inputs = sum(i + 1 for i in range(1, s))  # stage i reads k_1..k_i
     final = s + 1 + (s + 5 if method == "dopri5_adaptive" else 0)
     return 2 * (s * stage + inputs + final)

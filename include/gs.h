@@ -54,7 +54,9 @@ typedef enum {
     GS_RK4 = 0,    /* classical Runge-Kutta 4, fixed step */
     GS_DOPRI5 = 1, /* Dormand-Prince 5 (its 5th-order solution), fixed step */
     GS_AB4 = 2,    /* Adams-Bashforth 4; the first 3 steps of each call by RK4 */
-    GS_EULER = 3   /* explicit Euler */
+    GS_EULER = 3,  /* explicit Euler */
+    GS_CK54 = 4,   /* Cash-Karp 5(4) (its 5th-order solution), fixed step */
+    GS_RKF78 = 5   /* Fehlberg 7(8) (its 8th-order solution, 13 stages), fixed step */
 } gs_method;
 
 /* Gray-Scott problem (Eq. 2): periodic box [0,Lx)x[0,Ly)x[0,Lz), nx*ny*nz
@@ -107,7 +109,10 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u_dev, const void* v_dev, vo
 
 /* integrate_const / do_step (Listing 3): nsteps fixed steps of size dt from
  * *t on the bound state.  Step m is taken at time *t + m*dt; on return
- * *t = *t + nsteps*dt.  nsteps = 0 is a no-op.  Synchronises the stream. */
+ * *t = *t + nsteps*dt.  nsteps = 0 is a no-op.  GS_CK54 and GS_RKF78 run on
+ * the tableau path (see gs_set_laplacian; their stage fields k8..k13 and
+ * one more stage-input buffer are allocated at their first call, 7 fields x
+ * 2 components).  Synchronises the stream. */
 gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps);
 
 /* integrate_adaptive (section "Architecture and nomenclature of Boost
@@ -129,6 +134,20 @@ gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nste
 gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t, double t_end,
                                 double* dt, long max_accepted, long* n_accepted,
                                 long* n_rejected);
+
+/* integrate_adaptive with another error stepper of Table 1: pair =
+ * GS_DOPRI5 (the same as gs_integrate_adaptive), GS_CK54 (Cash-Karp 5(4),
+ * orders p = 5, q = 4) or GS_RKF78 (Fehlberg 7(8): the order-8 solution
+ * propagated, the order-7 one embedded, p = 8, q = 7).  Same norm,
+ * clipping, limits and results as gs_integrate_adaptive; the controller
+ * takes the pair's orders: E > 1 reject, dt *= max(0.9 E^(-1/(q-1)), 0.2);
+ * E < 0.5 accept, dt *= 0.9 max(E, 5^-p)^(-1/p); otherwise accept, dt
+ * kept.  Cash-Karp and Fehlberg run on the tableau path described at
+ * gs_set_laplacian (one tiled stage kernel per stage, the controller on
+ * the host), with either Laplacian.  INVALID: any other pair. */
+gs_status gs_integrate_adaptive_pair(gs_ctx* ctx, gs_method pair, double atol, double rtol, double* t,
+                                     double t_end, double* dt, long max_accepted, long* n_accepted,
+                                     long* n_rejected);
 
 /* Observer (the functor Odeint calls before each time step, e.g. to write
  * output; section "Architecture and nomenclature of Boost Odeint"):
@@ -179,14 +198,17 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty, int* zc, double* best_ms);
  * f_p), whose weights gs_set_laplacian computes once (Cholesky of the
  * moment system; the solved weights are even in the offset and are stored
  * exactly so, each pair {o, -o} taking the mean of its two values).  With
- * GS_LAP_DCPSE, gs_rhs, gs_step (GS_EULER, GS_RK4, GS_DOPRI5; GS_AB4 ->
- * INVALID) and gs_integrate_adaptive run a separate path: one tiled stage
- * kernel per stage (8 x 8 x 8 or 8 x 8 x 4 cells + a halo of 3 in shared
- * memory), each stage also forming the next stage's input at its own cells
- * and the last one the new state (and the attempt's error maximum), the
- * adaptive controller on the host with the formulas and limits of the
- * graph path; synchronous.  The FP64 kernel sums the stencil over the
- * offset pairs, sum_k w_k (f_{p+o_k} + f_{p-o_k}) - (sum_q w_q) f_p.
+ * GS_LAP_DCPSE, gs_rhs, gs_step (GS_EULER, GS_RK4, GS_DOPRI5, GS_CK54,
+ * GS_RKF78; GS_AB4 -> INVALID), gs_integrate_adaptive and
+ * gs_integrate_adaptive_pair run the tableau path: one tiled stage kernel
+ * per stage (8 x 8 x 8 or 8 x 8 x 4 cells + a halo of 3 in shared memory),
+ * each stage also forming the next stage's input at its own cells and the
+ * last one the new state (and the attempt's error maximum), the adaptive
+ * controller on the host with the formulas and limits of the graph path;
+ * synchronous.  The FP64 kernel sums the stencil over the offset pairs,
+ * sum_k w_k (f_{p+o_k} + f_{p-o_k}) - (sum_q w_q) f_p.  Cash-Karp and
+ * Fehlberg take the same path with the 7-point Laplacian too (as the
+ * stencil of the six neighbours, halo 1).
  * INVALID: unknown kind, rc_over_h outside [2, 4), a singular moment
  * system.  gs_get_dcpse_stencil: the offsets (3 ints each, in spacings)
  * and weights in use; capacity = 0 returns the count only.
@@ -259,6 +281,17 @@ gs_status gsb_autotune(gsb_ctx* ctx, int* ty, int* zc, double* best_ms);
  * set.  Synchronises; INVALID for t0 >= t_end, dt0 <= 0 or bad tolerances. */
 gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, double t_end, double dt0, int* ty_out,
                            int* zc_out, double* best_ms);
+
+/* Records the accepted step sizes of every instance in later
+ * gsb_integrate_adaptive calls (capacity per instance; 0 disables; device
+ * memory of count x capacity doubles allocated here).  gsb_get_step_log
+ * copies them to dts_host (count x capacity doubles, instance-major; the
+ * entries past an instance's count are untouched) and its accepted counts
+ * to counts (host array of count; a count may exceed capacity, only the
+ * first capacity sizes are kept).  capacity <= the logging capacity;
+ * synchronises.  With the sizes a run can be replayed step for step. */
+gs_status gsb_set_step_log(gsb_ctx* ctx, long capacity);
+gs_status gsb_get_step_log(gsb_ctx* ctx, double* dts_host, long capacity, long* counts);
 
 const char* gsb_last_error(const gsb_ctx* ctx);
 
@@ -461,6 +494,20 @@ gs_status ode_integrate_tableau(ode_rhs rhs, ode_tableau method, long n, double*
  * ode_integrate_tableau.  Enqueued on stream. */
 gs_status ode_integrate_ab_steps(ode_rhs rhs, int steps, long n, double* x_dev, const double* coef_dev,
                                  double t0, double dt, long nsteps, void* stream);
+
+/* Adams-Bashforth-Moulton with `steps` = 1..8 steps (Table 1), as a
+ * predictor-corrector in PECE form (the paper names the method only; this
+ * library's reading): with f_m = f(t_m, u_m),
+ *   u* = u_m + dt sum_{j<s} beta_j f_{m-j}                (Adams-Bashforth)
+ *   u_{m+1} = u_m + dt (beta*_0 f(t_{m+1}, u*) + sum_{1<=j<s} beta*_j f_{m+1-j})
+ *                                                          (Adams-Moulton),
+ * two evaluations of f per step, order s.  The first steps - 1 steps are
+ * one-step steps of order >= steps as for ode_integrate_ab_steps.  The
+ * Adams-Moulton weights are integrals of Lagrange basis polynomials,
+ * evaluated on the host by Gauss-Legendre quadrature.  Same arguments and
+ * errors as ode_integrate_ab_steps.  Enqueued on stream. */
+gs_status ode_integrate_abm_steps(ode_rhs rhs, int steps, long n, double* x_dev, const double* coef_dev,
+                                  double t0, double dt, long nsteps, void* stream);
 
 /* Error-controlled integration of n INDEPENDENT scalar ODEs, each with its
  * own step size and controller (no global norm), from t0 to t_end with the

@@ -89,6 +89,12 @@ def lib():
                                                 C.c_double, C.c_long, C.c_long, C.POINTER(C.c_long),
                                                 C.POINTER(C.c_long), _dp, C.c_long]
         L.orc_gs_integrate_ab4.argtypes = [C.POINTER(_GS), _dp, C.c_double, C.c_double, C.c_long]
+        L.orc_gs_integrate_adaptive_m.argtypes = [C.POINTER(_GS), C.c_int, _dp, _dp, C.c_double, _dp, C.c_double,
+                                                  C.c_double, C.c_long, C.c_long, C.POINTER(C.c_long),
+                                                  C.POINTER(C.c_long), _dp, C.c_long]
+        L.orc_gs_dcpse_integrate_adaptive_m.argtypes = [C.POINTER(_GS), C.c_double, C.c_int, _dp, _dp, C.c_double,
+                                                        _dp, C.c_double, C.c_double, C.c_long, C.c_long,
+                                                        C.POINTER(C.c_long), C.POINTER(C.c_long), _dp, C.c_long]
         L.orc_gs_dopri5_attempt.argtypes = [C.POINTER(_GS), C.c_double, C.c_double, _dp, _dp, _dp,
                                             C.c_double, C.c_double]
         L.orc_gs_dopri5_attempt.restype = C.c_double
@@ -243,15 +249,15 @@ def gs_integrate_replay(p: GSParams, u, v, method: int, dts, t0: float = 0.0):
 
 
 def gs_integrate_adaptive(p: GSParams, u, v, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500,
-                          log_cap=0):
+                          log_cap=0, method=DOPRI5):
     y = _pack(p, u, v)
     t = C.c_double(t0)
     dt = C.c_double(dt0)
     na, nr = C.c_long(0), C.c_long(0)
     log = np.zeros(max(log_cap, 1))
-    st = lib().orc_gs_integrate_adaptive(C.byref(p._c()), _p(y), C.byref(t), t_end, C.byref(dt), atol, rtol,
-                                         max_acc, max_rej, C.byref(na), C.byref(nr),
-                                         _p(log) if log_cap else None, log_cap)
+    st = lib().orc_gs_integrate_adaptive_m(C.byref(p._c()), method, _p(y), C.byref(t), t_end, C.byref(dt), atol,
+                                           rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
+                                           _p(log) if log_cap else None, log_cap)
     u1, v1 = _unpack(p, y)
     return {"u": u1, "v": v1, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value,
             "status": st, "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}
@@ -306,15 +312,15 @@ def gs_dcpse_integrate_const(p: GSParams, u, v, method: int, dt: float, nsteps: 
 
 
 def gs_dcpse_integrate_adaptive(p: GSParams, u, v, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500,
-                                rc_over_h=3.1, log_cap=0):
+                                rc_over_h=3.1, log_cap=0, method=DOPRI5):
     y = _pack(p, u, v)
     t = C.c_double(t0)
     dt = C.c_double(dt0)
     na, nr = C.c_long(0), C.c_long(0)
     log = np.zeros(max(log_cap, 1))
-    st = lib().orc_gs_dcpse_integrate_adaptive(C.byref(p._c()), rc_over_h, _p(y), C.byref(t), t_end, C.byref(dt),
-                                               atol, rtol, max_acc, max_rej, C.byref(na), C.byref(nr),
-                                               _p(log) if log_cap else None, log_cap)
+    st = lib().orc_gs_dcpse_integrate_adaptive_m(C.byref(p._c()), rc_over_h, method, _p(y), C.byref(t), t_end,
+                                                 C.byref(dt), atol, rtol, max_acc, max_rej, C.byref(na),
+                                                 C.byref(nr), _p(log) if log_cap else None, log_cap)
     u2, v2 = _unpack(p, y)
     return {"u": u2, "v": v2, "t": t.value, "dt": dt.value, "n_acc": na.value, "n_rej": nr.value, "status": st,
             "dts": log[: min(na.value, log_cap)].copy() if log_cap else None}

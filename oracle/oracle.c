@@ -852,6 +852,12 @@ int orc_gs_integrate_adaptive(const orc_gs* p, double* y, double* t, double t_en
     return orc_integrate_adaptive(orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t, t_end, dt, atol,
                                   rtol, max_acc, max_rej, n_acc, n_rej, log_dt, log_cap);
 }
+int orc_gs_integrate_adaptive_m(const orc_gs* p, int method, double* y, double* t, double t_end, double* dt,
+                                double atol, double rtol, long max_acc, long max_rej, long* n_acc, long* n_rej,
+                                double* log_dt, long log_cap) {
+    return orc_integrate_adaptive_m(method, orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t, t_end, dt, atol, rtol,
+                                    max_acc, max_rej, n_acc, n_rej, log_dt, log_cap);
+}
 int orc_gs_integrate_ab4(const orc_gs* p, double* y, double t0, double dt, long nsteps) {
     return orc_integrate_ab4(orc_gs_rhs, p, 2L * p->nx * p->ny * p->nz, y, t0, dt, nsteps);
 }
@@ -895,14 +901,20 @@ int orc_gs_dcpse_integrate_const(const orc_gs* p, double rc_over_h, int method, 
     return orc_integrate_const(method, orc_gs_rhs_dcpse, &P, 2L * p->nx * p->ny * p->nz, y, t0, dt, nsteps);
 }
 
-int orc_gs_dcpse_integrate_adaptive(const orc_gs* p, double rc_over_h, double* y, double* t, double t_end, double* dt,
-                                    double atol, double rtol, long max_acc, long max_rej, long* n_acc, long* n_rej,
-                                    double* log_dt, long log_cap) {
+int orc_gs_dcpse_integrate_adaptive_m(const orc_gs* p, double rc_over_h, int method, double* y, double* t,
+                                      double t_end, double* dt, double atol, double rtol, long max_acc, long max_rej,
+                                      long* n_acc, long* n_rej, double* log_dt, long log_cap) {
     static orc_dcpse S;
     if (orc_dcpse_laplacian(p->Lx / p->nx, p->Ly / p->ny, p->Lz / p->nz, rc_over_h, &S)) return ORC_ERR_INVALID;
     orc_gs_dcpse P = {*p, &S};
-    return orc_integrate_adaptive(orc_gs_rhs_dcpse, &P, 2L * p->nx * p->ny * p->nz, y, t, t_end, dt, atol, rtol,
-                                  max_acc, max_rej, n_acc, n_rej, log_dt, log_cap);
+    return orc_integrate_adaptive_m(method, orc_gs_rhs_dcpse, &P, 2L * p->nx * p->ny * p->nz, y, t, t_end, dt, atol,
+                                    rtol, max_acc, max_rej, n_acc, n_rej, log_dt, log_cap);
+}
+int orc_gs_dcpse_integrate_adaptive(const orc_gs* p, double rc_over_h, double* y, double* t, double t_end, double* dt,
+                                    double atol, double rtol, long max_acc, long max_rej, long* n_acc, long* n_rej,
+                                    double* log_dt, long log_cap) {
+    return orc_gs_dcpse_integrate_adaptive_m(p, rc_over_h, ORC_DOPRI5, y, t, t_end, dt, atol, rtol, max_acc, max_rej,
+                                             n_acc, n_rej, log_dt, log_cap);
 }
 
 void orc_pw_rhs(int kind, const double* coef, double t, long n, const double* y, double* f) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgs_b300.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_NOMEM = 0, 1, 2, 3
 GS_ERR_STEP_UNDERFLOW, GS_ERR_MAX_STEPS, GS_ERR_NONFINITE = 4, 5, 6
 GS_FP64, GS_FP32 = 0, 1
-GS_RK4, GS_DOPRI5, GS_AB4, GS_EULER = 0, 1, 2, 3
+GS_RK4, GS_DOPRI5, GS_AB4, GS_EULER, GS_CK54, GS_RKF78 = 0, 1, 2, 3, 4, 5
 ODE_EXP_DECAY, ODE_LOGISTIC = 0, 1
 
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID", 2: "GS_ERR_CUDA", 3: "GS_ERR_NOMEM",
@@ -58,6 +58,8 @@ _SIGNATURES = {
     "gs_rhs": ([_vp, C.c_double, _vp, _vp, _vp, _vp], C.c_int),
     "gs_step": ([_vp, C.c_int, _dp, C.c_double, C.c_long], C.c_int),
     "gs_integrate_adaptive": ([_vp, C.c_double, C.c_double, _dp, C.c_double, _dp, C.c_long, _lp, _lp], C.c_int),
+    "gs_integrate_adaptive_pair": ([_vp, C.c_int, C.c_double, C.c_double, _dp, C.c_double, _dp, C.c_long, _lp,
+                                    _lp], C.c_int),
     "gs_set_step_log": ([_vp, C.c_long], C.c_int),
     "gs_get_step_log": ([_vp, _dp, C.c_long, _lp], C.c_int),
     "gs_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
@@ -98,6 +100,9 @@ _SIGNATURES = {
                               C.c_int),
     "ode_integrate_ab_steps": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_long, _vp],
                                C.c_int),
+    "ode_integrate_abm_steps": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_long, _vp],
+                                C.c_int),
+    "ode_am_weights": ([C.c_int, _dp], C.c_int),
     "ode_integrate_adaptive_each": ([C.c_int, C.c_int, C.c_long, _vp, _vp, C.c_double, C.c_double, C.c_double,
                                      C.c_double, C.c_double, C.c_long, C.c_long, _vp, _vp, _vp, _vp, _vp, _vp],
                                     C.c_int),
@@ -117,6 +122,8 @@ _SIGNATURES = {
     "gsb_autotune_run": ([_vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_int),
                           C.POINTER(C.c_int), _dp], C.c_int),
     "gsb_last_error": ([_vp], C.c_char_p),
+    "gsb_set_step_log": ([_vp, C.c_long], C.c_int),
+    "gsb_get_step_log": ([_vp, _dp, C.c_long, _lp], C.c_int),
     "sur_param_count": ([], C.c_long),
     "sur_create": ([C.c_int, C.c_int, C.c_int, _vp, C.POINTER(_vp)], C.c_int),
     "sur_destroy": ([_vp], C.c_int),
@@ -230,6 +237,16 @@ def gs_integrate_adaptive(ctx, atol, rtol, t, t_end, dt, max_accepted=-1, check=
     na, nr = C.c_long(0), C.c_long(0)
     st = lib().gs_integrate_adaptive(ctx, atol, rtol, C.byref(tt), t_end, C.byref(dd), max_accepted,
                                      C.byref(na), C.byref(nr))
+    if check:
+        _check(st, ctx)
+    return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}
+
+
+def gs_integrate_adaptive_pair(ctx, pair, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
+    tt, dd = C.c_double(t), C.c_double(dt)
+    na, nr = C.c_long(0), C.c_long(0)
+    st = lib().gs_integrate_adaptive_pair(ctx, pair, atol, rtol, C.byref(tt), t_end, C.byref(dd), max_accepted,
+                                          C.byref(na), C.byref(nr))
     if check:
         _check(st, ctx)
     return {"status": st, "t": tt.value, "dt": dd.value, "n_acc": na.value, "n_rej": nr.value}
@@ -455,6 +472,18 @@ def ode_integrate_ab_steps(kind, steps, x, t0, dt, nsteps, coef=None, stream=Non
                                         _stream(stream)))
 
 
+def ode_integrate_abm_steps(kind, steps, x, t0, dt, nsteps, coef=None, stream=None):
+    _check(lib().ode_integrate_abm_steps(kind, steps, x.numel(), _ptr(x), _ptr(coef), t0, dt, nsteps,
+                                         _stream(stream)))
+
+
+def ode_am_weights(steps):
+    import numpy as np
+    w = np.zeros(max(steps, 1))
+    _check(lib().ode_am_weights(steps, w.ctypes.data_as(_dp)))
+    return w[:steps]
+
+
 def ode_integrate_adaptive_each(kind, method, x, t0, t_end, dt0, atol, rtol, max_acc=-1, max_rej=500, coef=None,
                                 outputs=True, stream=None):
     """Every element its own step size; returns per-element t, dt, counts, status (CUDA tensors)."""
@@ -512,7 +541,9 @@ class GrayScott:
     def step(self, method, t, dt, nsteps):
         return gs_step(self.ctx, method, t, dt, nsteps)
 
-    def integrate_adaptive(self, atol, rtol, t, t_end, dt, max_accepted=-1, check=True):
+    def integrate_adaptive(self, atol, rtol, t, t_end, dt, max_accepted=-1, check=True, pair=None):
+        if pair is not None:
+            return gs_integrate_adaptive_pair(self.ctx, pair, atol, rtol, t, t_end, dt, max_accepted, check)
         return gs_integrate_adaptive(self.ctx, atol, rtol, t, t_end, dt, max_accepted, check)
 
     def set_observer(self, fn):
@@ -589,6 +620,19 @@ class GrayScottBatch:
         if check:
             _bcheck(st, self.ctx)
         return {"status": st, "t": tt, "dt": dd, "n_acc": na, "n_rej": nr, "statuses": stv}
+
+    def set_step_log(self, capacity):
+        _bcheck(lib().gsb_set_step_log(self.ctx, capacity), self.ctx)
+        self._log_cap = capacity
+
+    def step_log(self):
+        """Per instance: the accepted step sizes of the last integration."""
+        import numpy as np
+        cap = getattr(self, "_log_cap", 0)
+        buf = np.zeros((len(self.instances), max(cap, 1)))
+        cnt = np.zeros(len(self.instances), dtype=np.int64)
+        _bcheck(lib().gsb_get_step_log(self.ctx, buf.ctypes.data_as(_dp), cap, cnt.ctypes.data_as(_lp)), self.ctx)
+        return [buf[i, :min(int(cnt[i]), cap)].copy() for i in range(len(self.instances))]
 
     def set_tile(self, ty, zc):
         _bcheck(lib().gsb_set_tile(self.ctx, ty, zc), self.ctx)

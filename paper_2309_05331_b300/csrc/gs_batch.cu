@@ -171,6 +171,8 @@ struct gsb_ctx {
     int ngroups = 1, nctr = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    double* dlog = nullptr;  // accepted step sizes: log_cap per instance (gsb_set_step_log)
+    long log_cap = 0;
     char err[512] = {0};
 };
 
@@ -483,6 +485,7 @@ gs_status gsb_destroy(gsb_ctx* ctx) {
     if (ctx->dinst) cudaFree(ctx->dinst);
     if (ctx->dctrl) cudaFree(ctx->dctrl);
     if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
+    if (ctx->dlog) cudaFree(ctx->dlog);
     if (ctx->counters) cudaFree(ctx->counters);
     for (int i = 0; i < 2; ++i)
         if (ctx->dseg[i]) cudaFree(ctx->dseg[i]);
@@ -538,6 +541,39 @@ gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* 
     return GS_OK;
 }
 
+gs_status gsb_set_step_log(gsb_ctx* ctx, long capacity) {
+    if (!ctx || capacity < 0) return GS_ERR_INVALID;
+    if (ctx->dlog) {
+        cudaFree(ctx->dlog);
+        ctx->dlog = nullptr;
+    }
+    ctx->log_cap = 0;
+    if (capacity == 0) return GS_OK;
+    cudaError_t e = cudaMalloc(&ctx->dlog, sizeof(double) * (size_t)capacity * ctx->count);
+    if (e != cudaSuccess) {
+        ctx->dlog = nullptr;
+        bset_err(ctx, e, "gsb_set_step_log");
+        return e == cudaErrorMemoryAllocation ? GS_ERR_NOMEM : GS_ERR_CUDA;
+    }
+    ctx->log_cap = capacity;
+    return GS_OK;
+}
+
+gs_status gsb_get_step_log(gsb_ctx* ctx, double* dts_host, long capacity, long* counts) {
+    if (!ctx || !dts_host || !counts || capacity < 0) return GS_ERR_INVALID;
+    if (!ctx->dlog || capacity > ctx->log_cap) return GS_ERR_INVALID;
+    for (int i = 0; i < ctx->count; ++i) {
+        const long n = (long)ctx->hctrl[i].n_acc;
+        counts[i] = n;
+        const long m = std::min(n, capacity);
+        if (m > 0)
+            BCK(cudaMemcpyAsync(dts_host + (size_t)i * capacity, ctx->dlog + (size_t)i * ctx->log_cap,
+                                sizeof(double) * (size_t)m, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    BCK(cudaStreamSynchronize(ctx->stream));
+    return GS_OK;
+}
+
 gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double* t, double t_end, double* dt,
                                  long max_accepted, long* n_acc, long* n_rej, int* status) {
     if (!ctx || !t || !dt || !ctx->state[0]) return GS_ERR_INVALID;
@@ -557,6 +593,10 @@ gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double*
         h->rtol = rtol;
         h->max_acc = max_accepted < 0 ? -1 : max_accepted;
         h->max_att = kMaxAttempts;
+        if (ctx->dlog) {
+            h->log_dt = ctx->dlog + (size_t)i * ctx->log_cap;
+            h->log_cap = ctx->log_cap;
+        }
         if (!(h->t < t_end) || max_accepted == 0) {
             h->done = 1;
             continue;

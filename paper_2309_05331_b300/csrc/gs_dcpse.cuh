@@ -19,17 +19,25 @@
 // u' = u + dt sum_j b_j k_j and, for an error-controlled attempt, the
 // maximum over cells of |dt sum_j e_j k_j| / (atol + rtol (|u| + dt |k1|)).
 // So every field value is formed once, and a step is s launches.
+//
+// The kernel takes any tableau (up to the 13 stages of Fehlberg 7(8)) and
+// any stencil of the form above; it also serves the Cash-Karp and Fehlberg
+// steppers with the 7-point Laplacian, written as the stencil of its six
+// neighbours (w = 1 / h_d^2) with a halo of R = 1.
 #pragma once
 
 #include "gs_tile.cuh"
 
 namespace gsk {
 
-constexpr int kDcpseMax = 256;  // stencil entries (r_c < 4 spacings)
-constexpr int kDcpseR = 3;      // halo of the tile (r_c < 4)
-constexpr int kDcpseT = 8;      // tile edge
-constexpr int kDcpseE = kDcpseT + 2 * kDcpseR;
-constexpr int kDcpseMaxNK = 6;  // stage inputs (Dormand-Prince stage 7 reads k1..k6)
+constexpr int kDcpseMax = 256;   // stencil entries (r_c < 4 spacings)
+constexpr int kDcpseR = 3;       // halo of the DC-PSE tile (r_c < 4)
+constexpr int kDcpseT = 8;       // tile edge
+constexpr int kDcpseMaxNK = 12;  // stage inputs (Fehlberg 7(8) stage 13 reads k1..k12)
+constexpr int kTabMaxS = kDcpseMaxNK + 1;
+
+// edge of the shared-memory tile of halo R
+__host__ __device__ constexpr int tile_edge(int R) { return kDcpseT + 2 * R; }
 
 // The weights are even in the offset (w_{-o} = w_o: the moment system is
 // symmetric under o -> -o, and the host averages the two solved values), so
@@ -46,7 +54,7 @@ struct DcpseStencil {
     signed char off[kDcpseMax][3];
     T w[kDcpseMax];
     int npair;
-    short pidx[kDcpseMax / 2];  // offset of pair k in the flattened Ys tile: (oz E + oy) E + ox
+    short pidx[kDcpseMax / 2];  // offset of pair k in the flattened Ys tile: (oz E + oy) E + ox, E = tile_edge(R)
     T pw[kDcpseMax / 2];
     T wsum;
 };
@@ -71,10 +79,11 @@ struct DcpseStageArgs {
     unsigned long long* emax;
 };
 
-template <typename T, int TZ>
+template <typename T, int TZ, int R>
 __global__ void __launch_bounds__(64 * TZ) dcpse_stage_kernel(const Geom<T> g, const DcpseStencil<T> S,
                                                               const DcpseStageArgs<T> A) {
-    constexpr int EZ = TZ + 2 * kDcpseR;
+    constexpr int kDcpseE = tile_edge(R);
+    constexpr int EZ = TZ + 2 * R;
     __shared__ T Ys[2][EZ][kDcpseE][kDcpseE];
     __shared__ double red[32];
     const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -85,7 +94,7 @@ __global__ void __launch_bounds__(64 * TZ) dcpse_stage_kernel(const Geom<T> g, c
     // Y_i on the tile and its halo (periodic)
     for (int e = tid; e < EZ * kDcpseE * kDcpseE; e += blockDim.x) {
         const int ex = e % kDcpseE, ey = (e / kDcpseE) % kDcpseE, ez = e / (kDcpseE * kDcpseE);
-        int x = x0 + ex - kDcpseR, y = y0 + ey - kDcpseR, z = z0 + ez - kDcpseR;
+        int x = x0 + ex - R, y = y0 + ey - R, z = z0 + ez - R;
         x = ((x % nx) + nx) % nx;
         y = ((y % ny) + ny) % ny;
         z = ((z % nz) + nz) % nz;
@@ -99,7 +108,7 @@ __global__ void __launch_bounds__(64 * TZ) dcpse_stage_kernel(const Geom<T> g, c
     const bool valid = x < nx && y < ny && z < nz;
     double emax = 0.0;
     if (valid) {
-        const int cx = lx + kDcpseR, cy = ly + kDcpseR, cz = lz + kDcpseR;
+        const int cx = lx + R, cy = ly + R, cz = lz + R;
         const T yu = Ys[0][cz][cy][cx], yv = Ys[1][cz][cy][cx];
         T lu = T(0), lv = T(0);
         if constexpr (sizeof(T) == 8) {
@@ -165,9 +174,9 @@ __global__ void __launch_bounds__(64 * TZ) dcpse_stage_kernel(const Geom<T> g, c
 template <typename T>
 struct DcpseCombineArgs {
     const T* u[2];
-    const T* k[7][2];
-    double b[7];
-    double e[7];  // error weights (if emax != nullptr)
+    const T* k[kTabMaxS][2];
+    double b[kTabMaxS];
+    double e[kTabMaxS];  // error weights (if emax != nullptr)
     int nk;
     double dt, atol, rtol;
     T* out[2];

@@ -28,6 +28,7 @@
 #include "gs_persist.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
+#include "tableaux.cuh"
 #include "gs_internal.h"
 #include "host_util.h"
 
@@ -90,7 +91,11 @@ struct gs_ctx {
     int dcpse_off[kDcpseMax][3] = {};
     double dcpse_w[kDcpseMax] = {};
     int dcpse_tz = 0;  // DC-PSE tile depth: 0 automatic, 4 or 8
-    unsigned long long* demax = nullptr;  // DC-PSE attempts: bits of the scaled error maximum
+    unsigned long long* demax = nullptr;  // tableau-path attempts: bits of the scaled error maximum
+    // tableau path (DC-PSE Laplacian, or Cash-Karp / Fehlberg): stage fields
+    // k8..k13 and a third stage-input buffer, allocated at first use
+    unsigned char* tab_scratch = nullptr;
+    void* tabx[7][2] = {};
     cudaGraph_t graph[G_COUNT] = {};
     cudaGraphExec_t exec[G_COUNT] = {};
     char err[512] = {0};
@@ -239,21 +244,22 @@ static cudaError_t launch_staged(gs_ctx* ctx, cudaStream_t s, StageArgs A, int d
 constexpr size_t kPairSmemCap = kMaxSmemPerCta - 1024;
 template <typename T, int NK, int MODE>
 static int pair_depth_fit(int ty, int depth) {
+    constexpr int VX = 16 / (int)sizeof(T);
     depth = std::max(1, std::min(depth, kMaxDepth));
-    while (depth > 1 && pair_smem_bytes<T, NK, MODE>(ty, depth) > kPairSmemCap) --depth;
+    while (depth > 1 && pair_smem_bytes<T, NK, MODE, VX>(ty, depth) > kPairSmemCap) --depth;
     return depth;
 }
 
-template <typename T, int NK, int MODE>
+template <typename T, int NK, int MODE, int VX>
 static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
     const Geom<T> g = make_geom<T>(ctx->p);
-    auto kern = gs_pair_kernel<T, NK, MODE>;
+    auto kern = gs_pair_kernel<T, NK, MODE, VX>;
     if (A.ty < 1 || A.ty > kPairMaxTY) return cudaErrorInvalidConfiguration;
-    const int txw = 32 * pair_vx<T>();
+    const int txw = 32 * VX;
     A.ntx = (ctx->p.nx + txw - 1) / txw;
     A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
     depth = pair_depth_fit<T, NK, MODE>(A.ty, depth);
-    const size_t smem = pair_smem_bytes<T, NK, MODE>(A.ty, depth);
+    const size_t smem = pair_smem_bytes<T, NK, MODE, VX>(A.ty, depth);
     if (smem > kPairSmemCap) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -268,8 +274,8 @@ static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int dep
 
 template <int NK, int MODE>
 static cudaError_t launch_pair_nk(gs_ctx* ctx, cudaStream_t s, const StageArgs& A, const KCfg& cfg) {
-    if (ctx->p.prec == GS_FP64) return launch_pair<double, NK, MODE>(ctx, s, A, cfg.depth);
-    return launch_pair<float, NK, MODE>(ctx, s, A, cfg.depth);
+    if (ctx->p.prec == GS_FP64) return launch_pair<double, NK, MODE, 2>(ctx, s, A, cfg.depth);
+    return launch_pair<float, NK, MODE, 4>(ctx, s, A, cfg.depth);
 }
 
 template <typename T, int NK, int MODE>
@@ -763,7 +769,7 @@ static DcpseStencil<T> dcpse_stencil(const gs_ctx* ctx) {
         // pairs {o, -o}: the representative has its last nonzero component positive
         const int lead = o[2] != 0 ? o[2] : (o[1] != 0 ? o[1] : o[0]);
         if (lead > 0) {
-            S.pidx[S.npair] = (short)((o[2] * kDcpseE + o[1]) * kDcpseE + o[0]);
+            S.pidx[S.npair] = (short)((o[2] * tile_edge(kDcpseR) + o[1]) * tile_edge(kDcpseR) + o[0]);
             S.pw[S.npair] = (T)ctx->dcpse_w[q];
             ++S.npair;
         }
@@ -772,22 +778,113 @@ static DcpseStencil<T> dcpse_stencil(const gs_ctx* ctx) {
     return S;
 }
 
-// one DC-PSE stage launch: tiles of 8 x 8 x 8 cells, or 8 x 8 x 4 where the
-// grid has fewer than 16 deep tiles per SM (more, smaller CTAs even out the
-// last wave; the deeper tile re-reads less halo)
+// The 7-point Laplacian as a stencil of the tableau path: the six
+// neighbours with w = 1 / h_d^2 (and the centre through -sum w), halo 1.
 template <typename T>
-static cudaError_t dcpse_launch(gs_ctx* ctx, const DcpseStageArgs<T>& A) {
+static DcpseStencil<T> seven_point_stencil(const gs_ctx* ctx) {
+    DcpseStencil<T> S;
+    memset(&S, 0, sizeof(S));
+    const double h[3] = {ctx->p.Lx / ctx->p.nx, ctx->p.Ly / ctx->p.ny, ctx->p.Lz / ctx->p.nz};
+    constexpr int E = tile_edge(1);
+    double wsum = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        const double w = 1.0 / (h[d] * h[d]);
+        for (int sgn = -1; sgn <= 1; sgn += 2) {
+            int o[3] = {0, 0, 0};
+            o[d] = sgn;
+            for (int k = 0; k < 3; ++k) S.off[S.count][k] = (signed char)o[k];
+            S.w[S.count] = (T)w;
+            ++S.count;
+            wsum += w;
+        }
+        int o[3] = {0, 0, 0};
+        o[d] = 1;
+        S.pidx[S.npair] = (short)((o[2] * E + o[1]) * E + o[0]);
+        S.pw[S.npair] = (T)w;
+        ++S.npair;
+    }
+    S.wsum = (T)wsum;
+    return S;
+}
+
+// one stage launch of the tableau path: tiles of 8 x 8 x 8 cells, or 8 x 8 x
+// 4 where the grid has fewer than 16 deep tiles per SM (more, smaller CTAs
+// even out the last wave; the deeper tile re-reads less halo); halo 3 for
+// the DC-PSE stencil, 1 for the 7-point one
+template <typename T, int R>
+static cudaError_t tab_launch_r(gs_ctx* ctx, const DcpseStencil<T>& S, const DcpseStageArgs<T>& A) {
     const Geom<T> g = make_geom<T>(ctx->p);
     const long long tx = (ctx->p.nx + kDcpseT - 1) / kDcpseT, ty = (ctx->p.ny + kDcpseT - 1) / kDcpseT;
     const long long t8 = tx * ty * ((ctx->p.nz + 7) / 8);
     const int tz = ctx->dcpse_tz ? ctx->dcpse_tz : (t8 < 16LL * ctx->nsm ? 4 : 8);
     if (tz == 4) {
         const long long tiles = tx * ty * ((ctx->p.nz + 3) / 4);
-        dcpse_stage_kernel<T, 4><<<(unsigned)tiles, 64 * 4, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
+        dcpse_stage_kernel<T, 4, R><<<(unsigned)tiles, 64 * 4, 0, ctx->stream>>>(g, S, A);
     } else {
-        dcpse_stage_kernel<T, 8><<<(unsigned)t8, 64 * 8, 0, ctx->stream>>>(g, dcpse_stencil<T>(ctx), A);
+        dcpse_stage_kernel<T, 8, R><<<(unsigned)t8, 64 * 8, 0, ctx->stream>>>(g, S, A);
     }
     return cudaGetLastError();
+}
+template <typename T>
+static cudaError_t dcpse_launch(gs_ctx* ctx, const DcpseStageArgs<T>& A) {
+    if (ctx->lap == 1) return tab_launch_r<T, kDcpseR>(ctx, dcpse_stencil<T>(ctx), A);
+    return tab_launch_r<T, 1>(ctx, seven_point_stencil<T>(ctx), A);
+}
+
+// Butcher rows of the tableau path (tableaux.cuh): s stages, the orders p,
+// q of the propagated / embedded solutions, error weights e = b - bhat.
+struct HostTab {
+    int s, p, q;
+    double a[kTabMaxS][kTabMaxS];
+    double b[kTabMaxS];
+    double e[kTabMaxS];
+};
+template <class TB>
+static HostTab tab_of() {
+    HostTab T;
+    memset(&T, 0, sizeof(T));
+    T.s = TB::S;
+    T.p = TB::P;
+    T.q = TB::Q;
+    for (int i = 0; i < TB::S; ++i) {
+        for (int j = 0; j < i; ++j) T.a[i][j] = TB::a(i, j);
+        T.b[i] = TB::b(i);
+        T.e[i] = TB::Q > 0 ? TB::b(i) - TB::bh(i) : 0.0;
+    }
+    return T;
+}
+static HostTab host_tab(gs_method m) {
+    switch (m) {
+        case GS_EULER: return tab_of<TabEuler>();
+        case GS_RK4: return tab_of<TabRK4>();
+        case GS_CK54: return tab_of<TabCK54>();
+        case GS_RKF78: return tab_of<TabRKF78>();
+        default: return tab_of<TabDP5>();
+    }
+}
+static bool tab_method(gs_method m) { return m == GS_CK54 || m == GS_RKF78; }
+
+// stage field k_j (1..13) and the third stage-input buffer (j = 14) of the
+// tableau path
+static void* tab_field(const gs_ctx* ctx, int j, int c) {
+    if (j <= 7) return ctx->field[j][c];
+    return ctx->tabx[j - 8][c];
+}
+static cudaError_t tab_ensure(gs_ctx* ctx) {
+    if (!ctx->demax) {
+        cudaError_t e = cudaMalloc(&ctx->demax, sizeof(unsigned long long));
+        if (e != cudaSuccess) return e;
+    }
+    if (ctx->tab_scratch) return cudaSuccess;
+    const size_t fbytes = ((size_t)ctx->N * ctx->esz + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&ctx->tab_scratch, fbytes * 2 * 7);
+    if (e != cudaSuccess) {
+        ctx->tab_scratch = nullptr;
+        return e;
+    }
+    for (int f = 0; f < 7; ++f)
+        for (int c = 0; c < 2; ++c) ctx->tabx[f][c] = ctx->tab_scratch + fbytes * (2 * f + c);
+    return cudaSuccess;
 }
 
 // k = F(y) at every cell (the right-hand side, no further output)
@@ -812,7 +909,7 @@ static cudaError_t dcpse_combine(gs_ctx* ctx, void* const u[2], int nk, const do
     for (int c = 0; c < 2; ++c) {
         A.u[c] = (const T*)u[c];
         A.out[c] = (T*)out[c];
-        for (int j = 0; j < nk; ++j) A.k[j][c] = (const T*)ctx->field[1 + j][c];
+        for (int j = 0; j < nk; ++j) A.k[j][c] = (const T*)tab_field(ctx, 1 + j, c);
     }
     for (int j = 0; j < nk; ++j) {
         A.b[j] = b[j];
@@ -828,44 +925,9 @@ static cudaError_t dcpse_combine(gs_ctx* ctx, void* const u[2], int nk, const do
     return cudaGetLastError();
 }
 
-// Butcher rows of the DC-PSE path: Euler, RK4, Dormand-Prince (7 stages)
-struct HostTab {
-    int s;
-    double a[7][7];
-    double b[7];
-    double e[7];
-};
-static HostTab host_tab(gs_method m) {
-    HostTab T;
-    memset(&T, 0, sizeof(T));
-    if (m == GS_EULER) {
-        T.s = 1;
-        T.b[0] = 1.0;
-    } else if (m == GS_RK4) {
-        T.s = 4;
-        T.a[1][0] = 0.5;
-        T.a[2][1] = 0.5;
-        T.a[3][2] = 1.0;
-        T.b[0] = 1.0 / 6.0;
-        T.b[1] = 1.0 / 3.0;
-        T.b[2] = 1.0 / 3.0;
-        T.b[3] = 1.0 / 6.0;
-    } else {
-        using namespace dp5;
-        T.s = 7;
-        const double A[7][7] = {{0}, {A21}, {A31, A32}, {A41, A42, A43}, {A51, A52, A53, A54},
-                                {A61, A62, A63, A64, A65}, {B1, 0, B3, B4, B5, B6}};
-        memcpy(T.a, A, sizeof(A));
-        const double b[7] = {B1, 0, B3, B4, B5, B6, 0};
-        const double e[7] = {E1, 0, E3, E4, E5, E6, E7};
-        memcpy(T.b, b, sizeof(b));
-        memcpy(T.e, e, sizeof(e));
-    }
-    return T;
-}
-
-// The stages of one step / attempt from state u: k_i into field i (1..s),
-// the stage inputs Y_2..Y_s alternating between fields 8 and 0 (Y_1 = u).
+// The stages of one step / attempt from state u: k_i into stage field i
+// (1..s), the stage inputs Y_2..Y_s alternating between fields 8 and 0
+// (Y_1 = u).
 // With fin, the last stage also writes u + dt sum_j b_j k_j there and, with
 // err, reduces the scaled error maximum into ctx->demax.  fin may be u
 // itself when s_used > 1 (the last stage reads u at its own cells only).
@@ -879,8 +941,8 @@ static cudaError_t dcpse_stages(gs_ctx* ctx, const HostTab& tab, int s_used, voi
         for (int c = 0; c < 2; ++c) {
             A.y[c] = (const T*)(i == 0 ? u[c] : ybuf[i % 2][c]);
             A.u[c] = (const T*)u[c];
-            A.out[c] = (T*)ctx->field[1 + i][c];
-            for (int j = 0; j < i; ++j) A.k[j][c] = (const T*)ctx->field[1 + j][c];
+            A.out[c] = (T*)tab_field(ctx, 1 + i, c);
+            for (int j = 0; j < i; ++j) A.k[j][c] = (const T*)tab_field(ctx, 1 + j, c);
         }
         A.nk = i;
         A.dt = dt;
@@ -906,8 +968,10 @@ static cudaError_t dcpse_stages(gs_ctx* ctx, const HostTab& tab, int s_used, voi
 template <typename T>
 static gs_status dcpse_step(gs_ctx* ctx, gs_method method, double t0, double dt, long nsteps) {
     const HostTab tab = host_tab(method);
-    // Dormand-Prince with fixed steps: stage 7 does not enter the solution
-    const int s_used = method == GS_DOPRI5 ? 6 : tab.s;
+    if (tab.s > 7) CK(tab_ensure(ctx));
+    // trailing stages with b = 0 (Dormand-Prince's stage 7) do not enter the solution
+    int s_used = tab.s;
+    while (s_used > 1 && tab.b[s_used - 1] == 0.0) --s_used;
     void* const u[2] = {ctx->state[0], ctx->state[1]};
     (void)t0;  // autonomous right-hand side
     for (long m = 0; m < nsteps; ++m) {
@@ -923,15 +987,23 @@ static gs_status dcpse_step(gs_ctx* ctx, gs_method method, double t0, double dt,
     return GS_OK;
 }
 
-// error-controlled Dormand-Prince on the DC-PSE path: the device computes the
-// attempt and its error maximum, the host runs the controller of the graph
-// path (same formulas and limits)
+// error-controlled integration with an embedded pair on the tableau path:
+// the device computes the attempt and its error maximum, the host runs the
+// controller of the graph path (same formulas and limits) with the pair's
+// orders: reject dt = h max(0.9 E^(-1/(q-1)), 0.2), grow dt = 0.9 h
+// max(E, 5^-p)^(-1/p)
 template <typename T>
-static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t_io, double t_end, double* dt_io,
-                                long max_acc, long* n_acc_out, long* n_rej_out) {
-    const HostTab tab = host_tab(GS_DOPRI5);
+static gs_status dcpse_adaptive(gs_ctx* ctx, gs_method method, double atol, double rtol, double* t_io, double t_end,
+                                double* dt_io, long max_acc, long* n_acc_out, long* n_rej_out) {
+    const HostTab tab = host_tab(method);
+    CK(tab_ensure(ctx));
     void* const u[2] = {ctx->state[0], ctx->state[1]};
-    void* const ynew[2] = {ctx->field[0][0], ctx->field[0][1]};
+    // the new state goes where the last stage does not read its input from
+    // (field 0 holds the inputs of odd stage indices)
+    const int flast = (tab.s - 1) % 2 == 1 ? 14 : 0;
+    void* const ynew[2] = {flast ? tab_field(ctx, flast, 0) : ctx->field[0][0],
+                           flast ? tab_field(ctx, flast, 1) : ctx->field[0][1]};
+    const double grow_floor = std::pow(5.0, -(double)tab.p);
     const size_t bytes = ctx->esz * (size_t)ctx->N;
     double t = *t_io, dt = *dt_io;
     long long n_acc = 0, n_rej = 0, consec = 0, att = 0;
@@ -955,7 +1027,7 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         }
         ++att;
         CK(cudaMemsetAsync(ctx->demax, 0, sizeof(unsigned long long), ctx->stream));
-        CK(dcpse_stages<T>(ctx, tab, 7, u, h, ynew, true, atol, rtol));
+        CK(dcpse_stages<T>(ctx, tab, tab.s, u, h, ynew, true, atol, rtol));
         unsigned long long bits = 0;
         CK(cudaMemcpyAsync(&bits, ctx->demax, sizeof(bits), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
@@ -968,7 +1040,7 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         if (E > 1.0) {
             ++n_rej;
             ++consec;
-            dt = h * std::max(0.9 * std::pow(E, -1.0 / 3.0), 0.2);
+            dt = h * std::max(0.9 * std::pow(E, -1.0 / (double)(tab.q - 1)), 0.2);
             if (consec >= kMaxConsecutiveRejects) {
                 status = GS_ERR_STEP_UNDERFLOW;
                 break;
@@ -981,7 +1053,7 @@ static gs_status dcpse_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
         log.push_back(h);
         ++n_acc;
         t = last ? t_end : t + h;
-        dt = E < 0.5 ? h * 0.9 * std::pow(std::max(E, 1.0 / 3125.0), -1.0 / 5.0) : h;
+        dt = E < 0.5 ? h * 0.9 * std::pow(std::max(E, grow_floor), -1.0 / (double)tab.p) : h;
         if (ctx->obs) stop = observe(ctx, t, &status);
     }
     // step log and counters where gs_get_step_log finds them
@@ -1211,6 +1283,7 @@ gs_status gs_destroy(gs_ctx* ctx) {
     if (ctx->hpatch) cudaFreeHost(ctx->hpatch);
     if (ctx->dlog) cudaFree(ctx->dlog);
     if (ctx->demax) cudaFree(ctx->demax);
+    if (ctx->tab_scratch) cudaFree(ctx->tab_scratch);
     delete ctx;
     return GS_OK;
 }
@@ -1322,7 +1395,7 @@ static gs_status step_observed(gs_ctx* ctx, gs_method method, double* t, double 
     const double t0 = *t;
     gs_status st = GS_OK;
     if (observe(ctx, t0, &st)) return st;
-    if (ctx->lap == 1) {
+    if (ctx->lap == 1 || tab_method(method)) {
         for (long n = 0; n < nsteps; ++n) {
             st = ctx->p.prec == GS_FP64 ? dcpse_step<double>(ctx, method, t0 + (double)n * dt, dt, 1)
                                         : dcpse_step<float>(ctx, method, t0 + (double)n * dt, dt, 1);
@@ -1360,14 +1433,14 @@ static gs_status step_observed(gs_ctx* ctx, gs_method method, double* t, double 
 
 gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps) {
     if (!ctx || !t || !ctx->state[0] || nsteps < 0 || !std::isfinite(dt)) return GS_ERR_INVALID;
-    if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER)
+    if (method != GS_RK4 && method != GS_DOPRI5 && method != GS_AB4 && method != GS_EULER && !tab_method(method))
         return GS_ERR_INVALID;
     if (ctx->lap == 1 && method == GS_AB4) return GS_ERR_INVALID;
     if (nsteps == 0) return GS_OK;
     if (ctx->obs) return step_observed(ctx, method, t, dt, nsteps);
     const double t0 = *t;
     gs_status st;
-    if (ctx->lap == 1) {
+    if (ctx->lap == 1 || tab_method(method)) {
         st = ctx->p.prec == GS_FP64 ? dcpse_step<double>(ctx, method, t0, dt, nsteps)
                                     : dcpse_step<float>(ctx, method, t0, dt, nsteps);
         if (st != GS_OK) return st;
@@ -1422,9 +1495,10 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     if (n_rejected) *n_rejected = 0;
     if (!(*t < t_end) || max_accepted == 0) return GS_OK;
     if (ctx->lap == 1)
-        return ctx->p.prec == GS_FP64
-                   ? dcpse_adaptive<double>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected)
-                   : dcpse_adaptive<float>(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
+        return ctx->p.prec == GS_FP64 ? dcpse_adaptive<double>(ctx, GS_DOPRI5, atol, rtol, t, t_end, dt, max_accepted,
+                                                               n_accepted, n_rejected)
+                                      : dcpse_adaptive<float>(ctx, GS_DOPRI5, atol, rtol, t, t_end, dt, max_accepted,
+                                                              n_accepted, n_rejected);
     const bool obs = ctx->obs != nullptr;
     gs_status st = GS_OK;
     if (obs && observe(ctx, *t, &st)) return st;
@@ -1486,6 +1560,21 @@ gs_status gs_integrate_adaptive(gs_ctx* ctx, double atol, double rtol, double* t
     if (n_accepted) *n_accepted = (long)h->n_acc;
     if (n_rejected) *n_rejected = (long)h->n_rej;
     return (gs_status)h->status;
+}
+
+gs_status gs_integrate_adaptive_pair(gs_ctx* ctx, gs_method pair, double atol, double rtol, double* t, double t_end,
+                                     double* dt, long max_accepted, long* n_accepted, long* n_rejected) {
+    if (pair == GS_DOPRI5)
+        return gs_integrate_adaptive(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
+    if (!ctx || !t || !dt || !ctx->state[0] || !tab_method(pair)) return GS_ERR_INVALID;
+    if (!(atol >= 0) || !(rtol >= 0) || !(atol > 0 || rtol > 0) || !(*dt > 0) || std::isnan(t_end))
+        return GS_ERR_INVALID;
+    if (n_accepted) *n_accepted = 0;
+    if (n_rejected) *n_rejected = 0;
+    if (!(*t < t_end) || max_accepted == 0) return GS_OK;
+    return ctx->p.prec == GS_FP64
+               ? dcpse_adaptive<double>(ctx, pair, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected)
+               : dcpse_adaptive<float>(ctx, pair, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
 }
 
 gs_status gs_set_step_log(gs_ctx* ctx, long capacity) {
@@ -1595,13 +1684,17 @@ gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth) {
     for (int pi = 0; pi < 5; ++pi) {
         const int ty = ctx->pc[pi].ty, d = ctx->pc[pi].depth;
         if (pi == 3)
-            depth[pi] = f64 ? pair_depth_fit<double, 0, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 0, MODE_PAIR_STAGE>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 0, MODE_PAIR_STAGE>(ty, d)
+                            : pair_depth_fit<float, 0, MODE_PAIR_STAGE>(ty, d);
         else if (pi == 4)
-            depth[pi] = f64 ? pair_depth_fit<double, 2, MODE_PAIR_RK4>(ty, d) : pair_depth_fit<float, 2, MODE_PAIR_RK4>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 2, MODE_PAIR_RK4>(ty, d)
+                            : pair_depth_fit<float, 2, MODE_PAIR_RK4>(ty, d);
         else if (pi == 0)
-            depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 1, MODE_PAIR_STAGE>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_STAGE>(ty, d)
+                            : pair_depth_fit<float, 1, MODE_PAIR_STAGE>(ty, d);
         else if (pi == 1)
-            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_STAGE>(ty, d) : pair_depth_fit<float, 3, MODE_PAIR_STAGE>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_STAGE>(ty, d)
+                            : pair_depth_fit<float, 3, MODE_PAIR_STAGE>(ty, d);
         else
             depth[pi] = f64 ? pair_depth_fit<double, 5, MODE_PAIR_DOPRI67>(ty, d)
                             : pair_depth_fit<float, 5, MODE_PAIR_DOPRI67>(ty, d);
@@ -1757,7 +1850,7 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
         for (int ty = 2; ty <= kPairMaxTY && st == GS_OK; ++ty)
             for (int depth = 1; depth <= kMaxDepth && st == GS_OK; ++depth) {
                 ctx->pc[pi] = KCfg{5, ty, 0, depth};
-                int used[3];
+                int used[5];
                 gs_get_pair_depths_in_use(ctx, used);
                 if (used[pi] < depth) break;  // shared memory holds no deeper ring
                 float ms = 0.f;

@@ -178,6 +178,11 @@ gs_status sur_conv_tc_status(unsigned int* timeouts);
  * GPU work is involved.  INVALID if the word was never allocated. */
 gs_status sur_debug_set_timeout_word(sur_ctx* ctx, unsigned int value);
 
+/* ---------------------------- pointwise ensembles ------------------------ */
+/* The Adams-Moulton weights ode_integrate_abm_steps passes to its kernel
+ * (host array of `steps` doubles, node t_{m+1} first), for the tests. */
+gs_status ode_am_weights(int steps, double* w);
+
 /* ---------------------------- measurement -------------------------------- */
 /* Measures this device's FP64 fused-multiply-add throughput (TFLOP/s,
  * 2 flops per FMA) with independent dependent-chains; used as the ALU

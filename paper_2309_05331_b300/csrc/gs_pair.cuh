@@ -18,7 +18,7 @@
 // k1, k2 without storing k3 or k4: 7 field passes per step instead of 13.
 //
 // Mapping (the staged form's, widened): a warp owns a row of 32*VX cells
-// (one 16-byte vector per lane).  The CTA has ty + 4 row warps for rows
+// (one 16-byte vector per lane, VX = 16 / sizeof(T)).  The CTA has ty + 4 row warps for rows
 // y0-2 .. y0+ty+1 and one halo warp whose lane 2(r+2)+s owns the two x-halo
 // columns of row y0+r on side s (s = 0: x0-2, x0-1; s = 1: x0+aw,
 // x0+aw+1).  Planes advance in z with three phases per iteration:
@@ -51,6 +51,7 @@ namespace gsk {
 constexpr int kPairMaxTY = 7;                        // rows per tile: ty + 5 warps (3 per SM sub-partition)
 constexpr int kPairThreads = 32 * (kPairMaxTY + 5);  // launch bound: 168 registers per thread
 
+
 template <typename T>
 __host__ __device__ constexpr int pair_vx() {
     return 16 / (int)sizeof(T);
@@ -62,30 +63,30 @@ __host__ __device__ constexpr int pair_pitch() {
     return 32 * VX + 2 * VX;
 }
 // Y_i: 3 buffers x (ty + 4) rows; Y_{i+1}: 3 buffers x (ty + 2) rows; 2 components
-template <typename T>
+template <typename T, int VX>
 __host__ __device__ inline size_t pair_plane_bytes(int ty) {
-    return sizeof(T) * 3 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<pair_vx<T>()>();
+    return sizeof(T) * 3 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<VX>();
 }
-// one ring slot: (ty + 4) rows x NA arrays x 32 lanes of 16-byte vectors,
+// one ring slot: (ty + 4) rows x NA arrays x 32 lanes of VX-cell vectors,
 // then the halo lanes' pairs: NA arrays x 32 lanes x 2 cells
-template <typename T, int NK>
+template <typename T, int NK, int VX>
 __host__ __device__ inline size_t pair_slot_bytes(int ty) {
     constexpr int NA = 2 * (1 + NK);
-    const size_t vec = (size_t)(ty + 4) * NA * 32 * 16;
+    const size_t vec = (size_t)(ty + 4) * NA * 32 * VX * sizeof(T);
     const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
     return (vec + halo + 15) / 16 * 16;
 }
 // Dormand-Prince pair: the inverse error scale of the tile rows' cells for
 // the three planes between A and C (thread-private, 3 x 2 components)
 // (RK4 stages 3+4: the partial update u + dt (k1/6 + k2/3) between A and B)
-template <int MODE>
+template <typename T, int MODE, int VX>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
-    return (MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? (size_t)3 * 2 * ty * 32 * 16 : 0;
+    return (MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? (size_t)3 * 2 * ty * 32 * VX * sizeof(T) : 0;
 }
-template <typename T, int NK, int MODE>
+template <typename T, int NK, int MODE, int VX>
 __host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
-    return (pair_plane_bytes<T>(ty) + 15) / 16 * 16 + pair_isc_bytes<MODE>(ty) +
-           (size_t)depth * pair_slot_bytes<T, NK>(ty);
+    return (pair_plane_bytes<T, VX>(ty) + 15) / 16 * 16 + pair_isc_bytes<T, MODE, VX>(ty) +
+           (size_t)depth * pair_slot_bytes<T, NK, VX>(ty);
 }
 
 // Coefficients of one pair launch in T.
@@ -122,12 +123,11 @@ __device__ __forceinline__ int wrapm(int a, int n) {
 // One segment: column (tx, tyi), output planes [z0, z1).  Called by every
 // thread of the CTA (it contains barriers: (z1 - z0) + 4 per segment, the
 // same count in the row warps and in the halo warp).
-template <typename T, int NK, int MODE>
+template <typename T, int NK, int MODE, int VX>
 __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T, NK>& P, const PairCoef<T, NK>& C,
                                              T* SA, T* SB, unsigned char* SI, unsigned char* R, int depth, int TY,
                                              int tx, int tyi, int z0, int z1,
                                              typename ErrBits<T>::U& ebits) {
-    constexpr int VX = pair_vx<T>();
     constexpr int TXW = 32 * VX;
     constexpr int PITCH = pair_pitch<VX>();
     constexpr int OFF = VX;
@@ -170,8 +170,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 
     auto ia = [&](int b, int row, int c, int cx) -> int { return ((b * RA + row + 2) * 2 + c) * PITCH + OFF + cx; };
     auto ib = [&](int b, int row, int c, int cx) -> int { return ((b * RB + row + 1) * 2 + c) * PITCH + OFF + cx; };
-    const size_t slot_bytes = pair_slot_bytes<T, NK>(TY);
-    const size_t vec_bytes = (size_t)RA * NA * 32 * 16;
+    const size_t slot_bytes = pair_slot_bytes<T, NK, VX>(TY);
+    const size_t vec_bytes = (size_t)RA * NA * 32 * sizeof(VTy);
     auto rvec = [&](int s, int a) -> VTy* {
         return reinterpret_cast<VTy*>(R + (size_t)s * slot_bytes) + ((size_t)w * NA + a) * 32 + lane;
     };
@@ -513,13 +513,13 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     __syncthreads();           // the plane buffers are reused by the next segment
 }
 
-template <typename T, int NK, int MODE>
+template <typename T, int NK, int MODE, int VX>
 __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
-    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<pair_vx<T>()>();
-    unsigned char* SI = smem_raw + (pair_plane_bytes<T>(A.ty) + 15) / 16 * 16;
-    unsigned char* R = SI + pair_isc_bytes<MODE>(A.ty);
+    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<VX>();
+    unsigned char* SI = smem_raw + (pair_plane_bytes<T, VX>(A.ty) + 15) / 16 * 16;
+    unsigned char* R = SI + pair_isc_bytes<T, MODE, VX>(A.ty);
     __shared__ T red[32];
     __shared__ int s_last;
 
@@ -540,7 +540,8 @@ __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> 
     typename ErrBits<T>::U ebits = 0;
     if (!skip) {
         for_each_segment(A, g.nz, [&](int col, int z0, int z1) {
-            pair_segment<T, NK, MODE>(g, P, C, SA, SB, SI, R, depth, A.ty, col % A.ntx, col / A.ntx, z0, z1, ebits);
+            pair_segment<T, NK, MODE, VX>(g, P, C, SA, SB, SI, R, depth, A.ty, col % A.ntx, col / A.ntx, z0, z1,
+                                          ebits);
         });
     }
     const T emax = ErrBits<T>::value(ebits);

@@ -10,6 +10,9 @@
 //   - Adams-Bashforth with 1..8 steps (Table 1; Fig. 2c,d), the history in
 //     registers, started by a one-step method of order >= s (RK4 for s <= 4,
 //     the order-8 Fehlberg solution for s >= 5);
+//   - Adams-Bashforth-Moulton with 1..8 steps (Table 1): the Adams-Bashforth
+//     predictor, one evaluation at the predicted value, the Adams-Moulton
+//     corrector (PECE), started like Adams-Bashforth;
 //   - error-controlled integration where EVERY element has its own step size
 //     and controller (no global norm: the elements are independent), with
 //     any embedded pair (Dormand-Prince, Cash-Karp, Fehlberg).
@@ -27,145 +30,13 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "gs_internal.h"
+#include "tableaux.cuh"
 #include "host_util.h"
 
 using namespace gsk;
 
 namespace {
-
-// ---------------------------------------------------------------------------
-// Tableaux (Table 1).  A strictly lower triangular, row i: stage i+1.
-// ---------------------------------------------------------------------------
-struct TabEuler {
-    static constexpr int S = 1, P = 1, Q = 0;
-    __host__ __device__ static constexpr double c(int i) {
-        constexpr double v[1] = {0.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double a(int i, int j) {
-        constexpr double v[1][1] = {{0.0}};
-        return v[i][j];
-    }
-    __host__ __device__ static constexpr double b(int i) {
-        constexpr double v[1] = {1.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double bh(int i) {
-        constexpr double v[1] = {0.0};
-        return v[i];
-    }
-};
-struct TabRK4 {
-    static constexpr int S = 4, P = 4, Q = 0;
-    __host__ __device__ static constexpr double c(int i) {
-        constexpr double v[4] = {0.0, 0.5, 0.5, 1.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double a(int i, int j) {
-        constexpr double v[4][4] = {{0, 0, 0, 0}, {0.5, 0, 0, 0}, {0, 0.5, 0, 0}, {0, 0, 1.0, 0}};
-        return v[i][j];
-    }
-    __host__ __device__ static constexpr double b(int i) {
-        constexpr double v[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double bh(int i) {
-        constexpr double v[4] = {0, 0, 0, 0};
-        return v[i];
-    }
-};
-struct TabDP5 {
-    static constexpr int S = 7, P = 5, Q = 4;
-    __host__ __device__ static constexpr double c(int i) {
-        constexpr double v[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double a(int i, int j) {
-        constexpr double v[7][7] = {
-        {0, 0, 0, 0, 0, 0, 0},
-        {dp5::A21, 0, 0, 0, 0, 0, 0},
-        {dp5::A31, dp5::A32, 0, 0, 0, 0, 0},
-        {dp5::A41, dp5::A42, dp5::A43, 0, 0, 0, 0},
-        {dp5::A51, dp5::A52, dp5::A53, dp5::A54, 0, 0, 0},
-        {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65, 0, 0},
-        {dp5::B1, 0, dp5::B3, dp5::B4, dp5::B5, dp5::B6, 0}};
-        return v[i][j];
-    }
-    __host__ __device__ static constexpr double b(int i) {
-        constexpr double v[7] = {dp5::B1, 0, dp5::B3, dp5::B4, dp5::B5, dp5::B6, 0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double bh(int i) {
-        constexpr double v[7] = {dp5::H1, 0, dp5::H3, dp5::H4, dp5::H5, dp5::H6, dp5::H7};
-        return v[i];
-    }
-};
-// Cash & Karp (1990): order-5 solution propagated, order-4 embedded.
-struct TabCK54 {
-    static constexpr int S = 6, P = 5, Q = 4;
-    __host__ __device__ static constexpr double c(int i) {
-        constexpr double v[6] = {0.0, 1.0 / 5, 3.0 / 10, 3.0 / 5, 1.0, 7.0 / 8};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double a(int i, int j) {
-        constexpr double v[6][6] = {{0, 0, 0, 0, 0, 0},
-                                       {1.0 / 5, 0, 0, 0, 0, 0},
-                                       {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-                                       {3.0 / 10, -9.0 / 10, 6.0 / 5, 0, 0, 0},
-                                       {-11.0 / 54, 5.0 / 2, -70.0 / 27, 35.0 / 27, 0, 0},
-                                       {1631.0 / 55296, 175.0 / 512, 575.0 / 13824, 44275.0 / 110592,
-                                        253.0 / 4096, 0}};
-        return v[i][j];
-    }
-    __host__ __device__ static constexpr double b(int i) {
-        constexpr double v[6] = {37.0 / 378, 0, 250.0 / 621, 125.0 / 594, 0, 512.0 / 1771};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double bh(int i) {
-        constexpr double v[6] = {2825.0 / 27648, 0, 18575.0 / 48384, 13525.0 / 55296, 277.0 / 14336,
-                                     1.0 / 4};
-        return v[i];
-    }
-};
-// Fehlberg (1968) 7(8), 13 stages; Table 1 lists it as order 8: the order-8
-// weights are propagated, the order-7 ones embedded.
-struct TabRKF78 {
-    static constexpr int S = 13, P = 8, Q = 7;
-    __host__ __device__ static constexpr double c(int i) {
-        constexpr double v[13] = {0.0,       2.0 / 27, 1.0 / 9, 1.0 / 6, 5.0 / 12, 1.0 / 2, 5.0 / 6,
-                                     1.0 / 6,   2.0 / 3,  1.0 / 3, 1.0,     0.0,      1.0};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double a(int i, int j) {
-        constexpr double v[13][13] = {
-        {0},
-        {2.0 / 27},
-        {1.0 / 36, 1.0 / 12},
-        {1.0 / 24, 0, 1.0 / 8},
-        {5.0 / 12, 0, -25.0 / 16, 25.0 / 16},
-        {1.0 / 20, 0, 0, 1.0 / 4, 1.0 / 5},
-        {-25.0 / 108, 0, 0, 125.0 / 108, -65.0 / 27, 125.0 / 54},
-        {31.0 / 300, 0, 0, 0, 61.0 / 225, -2.0 / 9, 13.0 / 900},
-        {2.0, 0, 0, -53.0 / 6, 704.0 / 45, -107.0 / 9, 67.0 / 90, 3.0},
-        {-91.0 / 108, 0, 0, 23.0 / 108, -976.0 / 135, 311.0 / 54, -19.0 / 60, 17.0 / 6, -1.0 / 12},
-        {2383.0 / 4100, 0, 0, -341.0 / 164, 4496.0 / 1025, -301.0 / 82, 2133.0 / 4100, 45.0 / 82, 45.0 / 164,
-         18.0 / 41},
-        {3.0 / 205, 0, 0, 0, 0, -6.0 / 41, -3.0 / 205, -3.0 / 41, 3.0 / 41, 6.0 / 41},
-        {-1777.0 / 4100, 0, 0, -341.0 / 164, 4496.0 / 1025, -289.0 / 82, 2193.0 / 4100, 51.0 / 82, 33.0 / 164,
-         12.0 / 41, 0, 1.0}};
-        return v[i][j];
-    }
-    __host__ __device__ static constexpr double b(int i) {
-        constexpr double v[13] = {0, 0, 0, 0, 0, 34.0 / 105, 9.0 / 35, 9.0 / 35, 9.0 / 280, 9.0 / 280, 0,
-                                     41.0 / 840, 41.0 / 840};
-        return v[i];
-    }
-    __host__ __device__ static constexpr double bh(int i) {
-        constexpr double v[13] = {41.0 / 840, 0, 0, 0, 0, 34.0 / 105, 9.0 / 35, 9.0 / 35, 9.0 / 280,
-                                      9.0 / 280, 41.0 / 840, 0, 0};
-        return v[i];
-    }
-};
 
 // Adams-Bashforth weights beta_j of f_{m-j} with s steps (published
 // rational values: numerators over a common denominator).
@@ -230,6 +101,50 @@ __global__ void __launch_bounds__(256) ode_tab_kernel(long long n, double* __res
         const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
         double e, k1;
         for (long long m = 0; m < nsteps; ++m) u = tab_step<KIND, TB, false>(u, t0 + (double)m * dt, dt, cf, e, k1);
+        x[i] = u;
+    }
+}
+
+// Adams-Moulton weights of the corrector (node t_{m+1} first), computed on
+// the host (am_weights) and passed by value.
+struct AmWeights {
+    double w[8];
+};
+
+// Adams-Bashforth-Moulton with S steps in PECE form: f[j] = f_{m-j} in
+// registers; predictor u* = u + dt sum_j ab_j f_{m-j}, f* = f(t_{m+1}, u*),
+// corrector u' = u + dt (am_0 f* + sum_{j>=1} am_j f_{m+1-j}).
+template <int KIND, int S>
+__global__ void __launch_bounds__(256) ode_abm_kernel(long long n, double* __restrict__ x,
+                                                      const double* __restrict__ coef, double t0, double dt,
+                                                      long long nsteps, const AmWeights am) {
+    using Start = typename std::conditional<(S <= 4), TabRK4, TabRKF78>::type;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double u = x[i];
+        const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
+        double f[S];
+#pragma unroll
+        for (int j = 0; j < S; ++j) f[j] = 0.0;
+        double e, k1;
+        for (long long m = 0; m < nsteps; ++m) {
+            const double t = t0 + (double)m * dt;
+#pragma unroll
+            for (int j = S - 1; j >= 1; --j) f[j] = f[j - 1];
+            f[0] = frhs<KIND>(t, u, cf);
+            if (m < S - 1) {
+                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1);
+            } else {
+                double acc = 0.0;
+#pragma unroll
+                for (int j = 0; j < S; ++j) acc += ab_weight(S, j) * f[j];
+                const double fp = frhs<KIND>(t0 + (double)(m + 1) * dt, u + dt * acc, cf);
+                double cor = am.w[0] * fp;
+#pragma unroll
+                for (int j = 1; j < S; ++j) cor += am.w[j] * f[j - 1];
+                u = u + dt * cor;
+            }
+        }
         x[i] = u;
     }
 }
@@ -464,6 +379,68 @@ cudaError_t launch_ab_k(int steps, cudaStream_t s, long long n, double* x, const
     }
 }
 
+// Adams-Moulton weights with s nodes tau_j = 1 - j (j = 0..s-1) on [0, 1]:
+// am_j = int_0^1 l_j(tau) dtau, l_j the Lagrange basis polynomial of node j,
+// by 8-point Gauss-Legendre quadrature in long double (exact for the
+// degree <= 7 integrands; nodes from Newton's method on the Legendre
+// recurrence).
+AmWeights am_weights(int s) {
+    constexpr int Q = 8;
+    long double xq[Q], wq[Q];
+    for (int q = 0; q < Q; ++q) {
+        long double z = cosl(3.14159265358979323846264338327950288L * (q + 0.75L) / (Q + 0.5L));
+        long double dp = 1.0L;
+        for (int it = 0; it < 100; ++it) {
+            long double p0 = 1.0L, p1 = z;  // P_0, P_1
+            for (int k = 2; k <= Q; ++k) {
+                const long double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = Q * (z * p1 - p0) / (z * z - 1.0L);  // P_Q'(z)
+            const long double dz = p1 / dp;
+            z -= dz;
+            if (fabsl(dz) < 1e-30L) break;
+        }
+        xq[q] = 0.5L * (1.0L - z);                       // node on [0, 1]
+        wq[q] = 1.0L / ((1.0L - z * z) * dp * dp);       // weight on [0, 1] (half of 2 / ((1 - z^2) P'^2))
+    }
+    AmWeights A{};
+    for (int j = 0; j < s; ++j) {
+        long double acc = 0.0L;
+        for (int q = 0; q < Q; ++q) {
+            long double l = 1.0L;
+            for (int i = 0; i < s; ++i)
+                if (i != j) l *= (xq[q] - (long double)(1 - i)) / (long double)((1 - j) - (1 - i));
+            acc += wq[q] * l;
+        }
+        A.w[j] = (double)acc;
+    }
+    return A;
+}
+
+template <int KIND, int S>
+cudaError_t launch_abm(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
+                       long long nsteps) {
+    auto k = ode_abm_kernel<KIND, S>;
+    k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps, am_weights(S));
+    return cudaGetLastError();
+}
+template <int KIND>
+cudaError_t launch_abm_k(int steps, cudaStream_t s, long long n, double* x, const double* coef, double t0,
+                         double dt, long long nsteps) {
+    switch (steps) {
+        case 1: return launch_abm<KIND, 1>(s, n, x, coef, t0, dt, nsteps);
+        case 2: return launch_abm<KIND, 2>(s, n, x, coef, t0, dt, nsteps);
+        case 3: return launch_abm<KIND, 3>(s, n, x, coef, t0, dt, nsteps);
+        case 4: return launch_abm<KIND, 4>(s, n, x, coef, t0, dt, nsteps);
+        case 5: return launch_abm<KIND, 5>(s, n, x, coef, t0, dt, nsteps);
+        case 6: return launch_abm<KIND, 6>(s, n, x, coef, t0, dt, nsteps);
+        case 7: return launch_abm<KIND, 7>(s, n, x, coef, t0, dt, nsteps);
+        default: return launch_abm<KIND, 8>(s, n, x, coef, t0, dt, nsteps);
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -503,6 +480,35 @@ gs_status ode_integrate_ab_steps(ode_rhs kind, int steps, long n, double* x, con
         set_global_error(e, "ode_integrate_ab_steps");
         return GS_ERR_CUDA;
     }
+    return GS_OK;
+}
+
+gs_status ode_integrate_abm_steps(ode_rhs kind, int steps, long n, double* x, const double* coef, double t0,
+                                  double dt, long nsteps, void* stream) {
+    if (!kind_ok(kind, coef) || steps < 1 || steps > 8 || n < 0 || nsteps < 0 || !std::isfinite(dt) ||
+        !std::isfinite(t0))
+        return GS_ERR_INVALID;
+    if (n > 0 && !x) return GS_ERR_INVALID;
+    if (n == 0 || nsteps == 0) return GS_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    switch (kind) {
+        case ODE_EXP_DECAY: e = launch_abm_k<ODE_EXP_DECAY>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        case ODE_LOGISTIC: e = launch_abm_k<ODE_LOGISTIC>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        case ODE_PAPER_EXP: e = launch_abm_k<ODE_PAPER_EXP>(steps, s, n, x, coef, t0, dt, nsteps); break;
+        default: e = launch_abm_k<ODE_PAPER_SIGMOID>(steps, s, n, x, coef, t0, dt, nsteps);
+    }
+    if (e != cudaSuccess) {
+        set_global_error(e, "ode_integrate_abm_steps");
+        return GS_ERR_CUDA;
+    }
+    return GS_OK;
+}
+
+gs_status ode_am_weights(int steps, double* w) {
+    if (steps < 1 || steps > 8 || !w) return GS_ERR_INVALID;
+    const AmWeights A = am_weights(steps);
+    for (int j = 0; j < steps; ++j) w[j] = A.w[j];
     return GS_OK;
 }
 

@@ -726,3 +726,120 @@ def test_dcpse_paper_workload_64cubed_rk4():
     ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, oracle.RK4, 1.0, 20)
     assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL)
     g.close()
+
+
+# ---------------------------------- Cash-Karp 5(4) and Fehlberg 7(8) (Table 1)
+TAB_METHODS = [("ck54", oracle.CK54), ("rkf78", oracle.RKF78)]
+
+
+def _tab_run_oracle(lap, dims, phys, u0, v0, omethod, dt, n):
+    p = oracle.GSParams(*dims, **phys)
+    if lap == "dcpse":
+        return oracle.gs_dcpse_integrate_const(p, u0, v0, omethod, dt, n)
+    return oracle.gs_integrate_const(p, u0, v0, omethod, dt, n)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("lap", ["7point", "dcpse"])
+@pytest.mark.parametrize("method,omethod", TAB_METHODS)
+@pytest.mark.parametrize("dims", [(16, 12, 10), (9, 5, 4), (20, 8, 1)])
+def test_tableau_path_fixed_steps_match_oracle(prec, lap, method, omethod, dims):
+    """Cash-Karp and Fehlberg fixed steps on the Gray-Scott grid (the tableau
+    path: one tiled stage kernel per stage, 13 stages for Fehlberg), with the
+    7-point and the DC-PSE Laplacian, ragged tiles and a single plane,
+    against the oracle's generic tableau step."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    phys = PAPER_GS if lap == "dcpse" else dict(Du=3e-3, Dv=1.5e-3)
+    dt = 1.0 if lap == "dcpse" else 0.25
+    u0, v0 = si.gs_initial_state(*dims, seed=71)
+    if prec == 1:
+        u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, dims, prec, u0, v0, **phys)
+    if lap == "dcpse":
+        gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    m = {"ck54": gs.GS_CK54, "rkf78": gs.GS_RKF78}[method]
+    t = g.step(m, 0.0, dt, 3)
+    assert t == 3 * dt
+    ou, ov = _tab_run_oracle(lap, dims, phys, u0, v0, omethod, dt, 3)
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL if prec == 0 else FP32_TOL, (lap, method))
+    g.close()
+
+
+@pytest.mark.parametrize("lap", ["7point", "dcpse"])
+@pytest.mark.parametrize("method,omethod", TAB_METHODS)
+def test_tableau_path_adaptive_fp64_matches_oracle_run(lap, method, omethod):
+    """Error-controlled Cash-Karp 5(4) and Fehlberg 7(8) (controller with the
+    pair's orders p, q): the oracle's accepted / rejected counts and step
+    sizes, the state within the FP64 bound."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (16, 12, 10)
+    phys = PAPER_GS if lap == "dcpse" else dict(Du=3e-3, Dv=1.5e-3)
+    u0, v0 = si.gs_initial_state(*dims, seed=72)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **phys)
+    if lap == "dcpse":
+        gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    gs.gs_set_step_log(g.ctx, 1000)
+    pair = {"ck54": gs.GS_CK54, "rkf78": gs.GS_RKF78}[method]
+    r = g.integrate_adaptive(1e-9, 1e-9, 0.0, 20.0, 1.0, pair=pair)
+    dts, cnt = gs.gs_get_step_log(g.ctx, 1000)
+    p = oracle.GSParams(*dims, **phys)
+    run = oracle.gs_dcpse_integrate_adaptive if lap == "dcpse" else oracle.gs_integrate_adaptive
+    ref = run(p, u0, v0, 0.0, 20.0, 1.0, 1e-9, 1e-9, log_cap=1000, method=omethod)
+    assert r["status"] == 0 and ref["status"] == 0 and r["t"] == 20.0
+    assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"]) and cnt == r["n_acc"]
+    assert ref["n_acc"] > 3  # the controller really worked
+    # Fehlberg's error estimate is dt 41/840 (k1 + k11 - k12 - k13), a
+    # difference of four nearly equal stage values (|k| ~ 1e-2, |err| ~ 1e-9
+    # here): stage values that differ by 1e-15 relative (FMA, the order of
+    # the stencil sums) move E by ~1e-5 relative, and dt follows E^(-1/8);
+    # the clipped last step inherits the accumulated difference of t.
+    # Cash-Karp's estimate cancels far less.
+    if method == "rkf78":
+        assert np.allclose(dts[:-1], ref["dts"][:-1], rtol=1e-4, atol=0)
+        assert abs(dts[-1] - ref["dts"][-1]) <= 1e-4 * 20.0
+    else:
+        assert np.allclose(dts, ref["dts"], rtol=1e-7, atol=0)
+    assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP64_TOL)
+    g.close()
+
+
+def test_tableau_path_adaptive_fp32_and_invalid():
+    """FP32 state with the FP64 controller against the FP64 oracle (1e-5);
+    pairs without an embedded solution are rejected."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (24, 16, 12)
+    u0, v0 = si.gs_initial_state(*dims, seed=73)
+    u0, v0 = _round32(u0), _round32(v0)
+    g = _gs(torch, dims, gs.GS_FP32, u0, v0, Du=3e-3, Dv=1.5e-3)
+    r = g.integrate_adaptive(1e-6, 1e-6, 0.0, 5.0, 0.2, pair=gs.GS_RKF78)
+    ref = oracle.gs_integrate_adaptive(oracle.GSParams(*dims, Du=3e-3, Dv=1.5e-3), u0, v0, 0.0, 5.0, 0.2, 1e-6, 1e-6,
+                                       method=oracle.RKF78)
+    assert r["t"] == 5.0 and abs(r["n_acc"] - ref["n_acc"]) <= 1
+    assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP32_TOL)
+    for bad in (gs.GS_RK4, gs.GS_EULER, gs.GS_AB4, 17):
+        with pytest.raises(RuntimeError):
+            g.integrate_adaptive(1e-6, 1e-6, 5.0, 6.0, 0.2, pair=bad)
+    g.close()
+
+
+def test_dcpse_paper_workload_64cubed_rkf78():
+    """The paper's Gray-Scott run with its third stepper: 64^3, d1 = 2e-4,
+    d2 = 1e-4, DC-PSE, Fehlberg 7(8) with dt = 1 to t_f = 20, FP64, against
+    the oracle."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (64, 64, 64)
+    u0, v0 = si.gs_initial_state(*dims, seed=2)
+    g = _gs(torch, dims, gs.GS_FP64, u0, v0, **PAPER_GS)
+    gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
+    g.step(gs.GS_RKF78, 0.0, 1.0, 20)
+    oracle.set_threads(oracle.max_threads())
+    try:
+        ou, ov = oracle.gs_dcpse_integrate_const(oracle.GSParams(*dims, **PAPER_GS), u0, v0, oracle.RKF78, 1.0, 20)
+    finally:
+        oracle.set_threads(1)
+    assert_parity([to_np(g.u), to_np(g.v)], [ou, ov], FP64_TOL)
+    g.close()

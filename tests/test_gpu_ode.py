@@ -212,6 +212,55 @@ def test_ab_convergence_order_on_gpu(steps):
     assert abs(np.log2(errs[0] / errs[1]) - steps) < 0.4, errs
 
 
+@pytest.mark.parametrize("okind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP,
+                                   oracle.PW_PAPER_SIGMOID])
+@pytest.mark.parametrize("steps", range(1, 9))
+@pytest.mark.parametrize("nsteps", [0, 1, 7, 50])
+def test_abm_steps_match_oracle(okind, steps, nsteps):
+    """Adams-Bashforth-Moulton (PECE) with 1..8 steps, every family, runs
+    shorter and longer than the start-up: element by element against the
+    oracle (1e-13 relative to 1 + |x|)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    x0, t0, t1, coef = _family(okind, 1031)
+    dt = (t1 - t0) / 400
+    x = _cuda(torch, x0)
+    gs.ode_integrate_abm_steps(okind, steps, x, t0, dt, nsteps, coef=_cuda(torch, coef))
+    torch.cuda.synchronize()
+    ref = oracle.pw_integrate_abm(steps, okind, x0, dt, nsteps, t0=t0, coef=coef)
+    got = to_np(x)
+    assert np.max(np.abs(got - ref) / (1.0 + np.abs(ref))) < 1e-13
+    if nsteps >= steps:  # past the start-up the corrector acts: not Adams-Bashforth's result
+        ab = oracle.pw_integrate_ab(steps, okind, x0, dt, nsteps, t0=t0, coef=coef)
+        assert np.max(np.abs(got - ab)) > 0.0 or okind == oracle.PW_PAPER_SIGMOID
+
+
+def test_abm_weights_match_oracle():
+    """The Adams-Moulton weights the library computes (Gauss-Legendre
+    quadrature of the Lagrange basis) against the oracle's (term-by-term
+    integration of the expanded basis)."""
+    import paper_2309_05331_b300 as gs
+    for s in range(1, 9):
+        assert np.allclose(gs.ode_am_weights(s), oracle.am_coefficients(s), rtol=1e-15, atol=1e-16)
+
+
+@pytest.mark.parametrize("steps", range(1, 9))
+def test_abm_convergence_order_on_gpu(steps):
+    """The exponential family (Eq. 1a) with Adams-Bashforth-Moulton 1..8
+    converges with order s on the GPU (error against u = c e^t at t = 5)."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    x0, t0, t1, coef = _family(oracle.PW_PAPER_EXP, 4096)
+    exact = coef * np.exp(t1)
+    errs = []
+    for m in (100, 200):
+        x = _cuda(torch, x0)
+        gs.ode_integrate_abm_steps(oracle.PW_PAPER_EXP, steps, x, t0, (t1 - t0) / m, m, coef=_cuda(torch, coef))
+        torch.cuda.synchronize()
+        errs.append(float(np.max(np.abs(to_np(x) - exact))))
+    assert abs(np.log2(errs[0] / errs[1]) - steps) < 0.4, errs
+
+
 @pytest.mark.parametrize("okind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP])
 @pytest.mark.parametrize("method,omethod", [(2, oracle.DOPRI5), (3, oracle.CK54), (4, oracle.RKF78)])
 @pytest.mark.parametrize("tol", [1e-6, 1e-10])
