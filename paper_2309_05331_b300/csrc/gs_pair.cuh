@@ -58,14 +58,18 @@ __host__ __device__ constexpr int pair_vx() {
 }
 // a plane row: 2 halo cells on each side of the 32*VX main cells, the main
 // cells starting at a whole vector (column c at OFF + c, OFF = VX)
-template <int VX>
+template <typename T>
+__host__ __device__ constexpr int pair_off() {
+    return 16 / (int)sizeof(T);
+}
+template <typename T, int VX>
 __host__ __device__ constexpr int pair_pitch() {
-    return 32 * VX + 2 * VX;
+    return 2 * pair_off<T>() + 32 * VX;
 }
 // Y_i: 3 buffers x (ty + 4) rows; Y_{i+1}: 3 buffers x (ty + 2) rows; 2 components
 template <typename T, int VX>
 __host__ __device__ inline size_t pair_plane_bytes(int ty) {
-    return sizeof(T) * 3 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<VX>();
+    return sizeof(T) * 3 * (size_t)((ty + 4) + (ty + 2)) * 2 * pair_pitch<T, VX>();
 }
 // one ring slot: (ty + 4) rows x NA arrays x 32 lanes of VX-cell vectors,
 // then the halo lanes' pairs: NA arrays x 32 lanes x 2 cells
@@ -74,7 +78,7 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
     constexpr int NA = 2 * (1 + NK);
     const size_t vec = (size_t)(ty + 4) * NA * 32 * VX * sizeof(T);
     const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
-    return (vec + halo + 15) / 16 * 16;
+    return (vec + halo + 127) / 128 * 128;
 }
 // Dormand-Prince pair: the inverse error scale of the tile rows' cells for
 // the three planes between A and C (thread-private, 3 x 2 components)
@@ -83,9 +87,12 @@ template <typename T, int MODE, int VX>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
     return (MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? (size_t)3 * 2 * ty * 32 * VX * sizeof(T) : 0;
 }
+// the input ring starts at a 128-byte boundary of the shared window (+ 128
+// bytes of room for that): a warp's 512 contiguous bytes of a slot then
+// cover four whole 128-byte lines instead of five
 template <typename T, int NK, int MODE, int VX>
 __host__ __device__ inline size_t pair_smem_bytes(int ty, int depth) {
-    return (pair_plane_bytes<T, VX>(ty) + 15) / 16 * 16 + pair_isc_bytes<T, MODE, VX>(ty) +
+    return (pair_plane_bytes<T, VX>(ty) + 15) / 16 * 16 + pair_isc_bytes<T, MODE, VX>(ty) + 128 +
            (size_t)depth * pair_slot_bytes<T, NK, VX>(ty);
 }
 
@@ -129,8 +136,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                                              int tx, int tyi, int z0, int z1,
                                              typename ErrBits<T>::U& ebits) {
     constexpr int TXW = 32 * VX;
-    constexpr int PITCH = pair_pitch<VX>();
-    constexpr int OFF = VX;
+    constexpr int PITCH = pair_pitch<T, VX>();
+    constexpr int OFF = pair_off<T>();
     constexpr int NA = 2 * (1 + NK);
     constexpr bool DP = MODE == MODE_PAIR_DOPRI67;
     constexpr bool RK = MODE == MODE_PAIR_RK4;
@@ -517,9 +524,12 @@ template <typename T, int NK, int MODE, int VX>
 __global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
-    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<VX>();
+    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, VX>();
     unsigned char* SI = smem_raw + (pair_plane_bytes<T, VX>(A.ty) + 15) / 16 * 16;
+    // the ring at the next 128-byte boundary of the shared window (an offset
+    // from smem_raw, so the compiler keeps shared-memory addressing)
     unsigned char* R = SI + pair_isc_bytes<T, MODE, VX>(A.ty);
+    R += (128u - ((uint32_t)__cvta_generic_to_shared(R) & 127u)) & 127u;
     __shared__ T red[32];
     __shared__ int s_last;
 
