@@ -55,8 +55,9 @@ typedef enum {
     GS_DOPRI5 = 1, /* Dormand-Prince 5 (its 5th-order solution), fixed step */
     GS_AB4 = 2,    /* Adams-Bashforth 4; the first 3 steps of each call by RK4 */
     GS_EULER = 3,  /* explicit Euler */
-    GS_CK54 = 4,   /* Cash-Karp 5(4) (its 5th-order solution), fixed step */
-    GS_RKF78 = 5   /* Fehlberg 7(8) (its 8th-order solution, 13 stages), fixed step */
+    GS_CK54 = 4,    /* Cash-Karp 5(4) (its 5th-order solution), fixed step */
+    GS_RKF78 = 5,   /* Fehlberg 7(8) (its 8th-order solution, 13 stages), fixed step */
+    GS_MIDPOINT = 6 /* modified midpoint, two substeps of dt/2 (order 2), fixed step */
 } gs_method;
 
 /* Gray-Scott problem (Eq. 2): periodic box [0,Lx)x[0,Ly)x[0,Lz), nx*ny*nz
@@ -109,10 +110,11 @@ gs_status gs_rhs(gs_ctx* ctx, double t, const void* u_dev, const void* v_dev, vo
 
 /* integrate_const / do_step (Listing 3): nsteps fixed steps of size dt from
  * *t on the bound state.  Step m is taken at time *t + m*dt; on return
- * *t = *t + nsteps*dt.  nsteps = 0 is a no-op.  GS_CK54 and GS_RKF78 run on
- * the tableau path (see gs_set_laplacian; their stage fields k8..k13 and
- * one more stage-input buffer are allocated at their first call, 7 fields x
- * 2 components).  Synchronises the stream. */
+ * *t = *t + nsteps*dt.  nsteps = 0 is a no-op.  GS_CK54, GS_RKF78 and
+ * GS_MIDPOINT run on the tableau path (see gs_set_laplacian; Fehlberg's
+ * stage fields k8..k13 and one more stage-input buffer are allocated at the
+ * first call that needs them, 7 fields x 2 components).  Synchronises the
+ * stream. */
 gs_status gs_step(gs_ctx* ctx, gs_method method, double* t, double dt, long nsteps);
 
 /* integrate_adaptive (section "Architecture and nomenclature of Boost
@@ -417,7 +419,9 @@ typedef enum {
     ODE_TAB_RK4 = 1,
     ODE_TAB_DOPRI5 = 2, /* Dormand-Prince 5(4), order 5 propagated */
     ODE_TAB_CK54 = 3,   /* Cash-Karp 5(4), order 5 propagated */
-    ODE_TAB_RKF78 = 4   /* Fehlberg 7(8), 13 stages, order 8 propagated */
+    ODE_TAB_RKF78 = 4,   /* Fehlberg 7(8), 13 stages, order 8 propagated */
+    ODE_TAB_MIDPOINT = 5 /* modified midpoint: z1 = x + h f(x), z2 = x + 2h f(z1),
+                            x' = (z1 + z2 + h f(z2)) / 2, h = dt / 2 (order 2) */
 } ode_tableau;
 
 /* Workspace bytes needed by ode_integrate_adaptive for n elements. */

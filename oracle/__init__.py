@@ -54,7 +54,7 @@ import numpy as np
 
 from . import build as _build
 
-EULER, RK4, DOPRI5, CK54, RKF78 = 0, 1, 2, 3, 4
+EULER, RK4, DOPRI5, CK54, RKF78, MIDPOINT = 0, 1, 2, 3, 4, 5
 PW_EXP_DECAY, PW_LOGISTIC, PW_PAPER_EXP, PW_PAPER_SIGMOID = 0, 1, 2, 3
 
 OK, ERR_INVALID, ERR_NOMEM, ERR_STEP_UNDERFLOW, ERR_MAX_STEPS, ERR_NONFINITE = 0, 1, 3, 4, 5, 6

@@ -18,8 +18,8 @@
  *     functor of Listing 2 for the v-equation) on a periodic grid with the
  *     7-point central Laplacian; pointwise ODEs dx/dt = -x and x(1-x); the
  *     paper's exponential (Eq. 1a) and sigmoidal (Eq. 1b) families.
- *   - explicit Runge-Kutta steppers of Table 1 (explicit Euler, RK4,
- *     Dormand-Prince 5 with its embedded order-4 solution), as one generic
+ *   - explicit Runge-Kutta steppers of Table 1 (explicit Euler, modified
+ *     midpoint, RK4, Dormand-Prince 5 with its embedded order-4 solution), as one generic
  *     Butcher-tableau step: k_i = F(t + c_i dt, u + dt sum_j a_ij k_j),
  *     u_new = u + dt sum_i b_i k_i, err = dt sum_i (b_i - bhat_i) k_i.
  *   - the error-controlled adaptive driver (section "Architecture and
@@ -66,7 +66,7 @@ typedef struct {
     int has_bhat;
 } orc_tableau;
 
-enum { ORC_EULER = 0, ORC_RK4 = 1, ORC_DOPRI5 = 2, ORC_CK54 = 3, ORC_RKF78 = 4 };
+enum { ORC_EULER = 0, ORC_RK4 = 1, ORC_DOPRI5 = 2, ORC_CK54 = 3, ORC_RKF78 = 4, ORC_MIDPOINT = 5 };
 
 /* Fills tableau T for method id; returns 0 on success. */
 int orc_get_tableau(int id, orc_tableau* T) {
@@ -76,6 +76,18 @@ int orc_get_tableau(int id, orc_tableau* T) {
         T->s = 1;
         T->b[0] = 1.0;
         T->c[0] = 0.0;
+        return 0;
+    }
+    if (id == ORC_MIDPOINT) {
+        /* modified midpoint (Table 1, order 2) with two substeps of h = dt/2
+         * (this build's reading of the substep count): z1 = y + h f(y),
+         * z2 = y + 2h f(z1), y_new = (z1 + z2 + h f(z2)) / 2, written as the
+         * tableau c = (0, 1/2, 1), a21 = 1/2, a32 = 1, b = (1/4, 1/2, 1/4) */
+        T->s = 3;
+        T->a[1 * 3 + 0] = 0.5;
+        T->a[2 * 3 + 1] = 1.0;
+        T->b[0] = 0.25; T->b[1] = 0.5; T->b[2] = 0.25;
+        T->c[0] = 0.0; T->c[1] = 0.5; T->c[2] = 1.0;
         return 0;
     }
     if (id == ORC_RK4) {

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libgs_b300.so")
 GS_OK, GS_ERR_INVALID, GS_ERR_CUDA, GS_ERR_NOMEM = 0, 1, 2, 3
 GS_ERR_STEP_UNDERFLOW, GS_ERR_MAX_STEPS, GS_ERR_NONFINITE = 4, 5, 6
 GS_FP64, GS_FP32 = 0, 1
-GS_RK4, GS_DOPRI5, GS_AB4, GS_EULER, GS_CK54, GS_RKF78 = 0, 1, 2, 3, 4, 5
+GS_RK4, GS_DOPRI5, GS_AB4, GS_EULER, GS_CK54, GS_RKF78, GS_MIDPOINT = 0, 1, 2, 3, 4, 5, 6
 ODE_EXP_DECAY, ODE_LOGISTIC = 0, 1
 
 STATUS_NAMES = {0: "GS_OK", 1: "GS_ERR_INVALID", 2: "GS_ERR_CUDA", 3: "GS_ERR_NOMEM",
@@ -457,7 +457,7 @@ def ode_integrate_const(kind, method, x, t0, dt, nsteps, stream=None):
 
 
 ODE_PAPER_EXP, ODE_PAPER_SIGMOID = 2, 3
-ODE_TAB_EULER, ODE_TAB_RK4, ODE_TAB_DOPRI5, ODE_TAB_CK54, ODE_TAB_RKF78 = 0, 1, 2, 3, 4
+ODE_TAB_EULER, ODE_TAB_RK4, ODE_TAB_DOPRI5, ODE_TAB_CK54, ODE_TAB_RKF78, ODE_TAB_MIDPOINT = 0, 1, 2, 3, 4, 5
 
 
 def ode_integrate_tableau(kind, method, x, t0, dt, nsteps, coef=None, stream=None):

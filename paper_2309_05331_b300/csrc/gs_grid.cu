@@ -859,10 +859,11 @@ static HostTab host_tab(gs_method m) {
         case GS_RK4: return tab_of<TabRK4>();
         case GS_CK54: return tab_of<TabCK54>();
         case GS_RKF78: return tab_of<TabRKF78>();
+        case GS_MIDPOINT: return tab_of<TabMidpoint>();
         default: return tab_of<TabDP5>();
     }
 }
-static bool tab_method(gs_method m) { return m == GS_CK54 || m == GS_RKF78; }
+static bool tab_method(gs_method m) { return m == GS_CK54 || m == GS_RKF78 || m == GS_MIDPOINT; }
 
 // stage field k_j (1..13) and the third stage-input buffer (j = 14) of the
 // tableau path
@@ -1566,7 +1567,7 @@ gs_status gs_integrate_adaptive_pair(gs_ctx* ctx, gs_method pair, double atol, d
                                      double* dt, long max_accepted, long* n_accepted, long* n_rejected) {
     if (pair == GS_DOPRI5)
         return gs_integrate_adaptive(ctx, atol, rtol, t, t_end, dt, max_accepted, n_accepted, n_rejected);
-    if (!ctx || !t || !dt || !ctx->state[0] || !tab_method(pair)) return GS_ERR_INVALID;
+    if (!ctx || !t || !dt || !ctx->state[0] || (pair != GS_CK54 && pair != GS_RKF78)) return GS_ERR_INVALID;
     if (!(atol >= 0) || !(rtol >= 0) || !(atol > 0 || rtol > 0) || !(*dt > 0) || std::isnan(t_end))
         return GS_ERR_INVALID;
     if (n_accepted) *n_accepted = 0;

@@ -6,7 +6,8 @@
 // e^-t) (Eq. 1b).
 //
 //   - fixed-step explicit Runge-Kutta with any tableau of Table 1 (Euler,
-//     RK4, Dormand-Prince 5, Cash-Karp 5(4), Fehlberg 7(8));
+//     modified midpoint, RK4, Dormand-Prince 5, Cash-Karp 5(4), Fehlberg
+//     7(8));
 //   - Adams-Bashforth with 1..8 steps (Table 1; Fig. 2c,d), the history in
 //     registers, started by a one-step method of order >= s (RK4 for s <= 4,
 //     the order-8 Fehlberg solution for s >= 5);
@@ -332,6 +333,7 @@ cudaError_t by_tab(int method, int kind, Args... args) {
         case ODE_TAB_RK4: return by_kind<Launch, TabRK4>(kind, args...);
         case ODE_TAB_DOPRI5: return by_kind<Launch, TabDP5>(kind, args...);
         case ODE_TAB_CK54: return by_kind<Launch, TabCK54>(kind, args...);
+        case ODE_TAB_MIDPOINT: return by_kind<Launch, TabMidpoint>(kind, args...);
         default: return by_kind<Launch, TabRKF78>(kind, args...);
     }
 }
@@ -447,7 +449,7 @@ extern "C" {
 
 gs_status ode_integrate_tableau(ode_rhs kind, ode_tableau method, long n, double* x, const double* coef,
                                 double t0, double dt, long nsteps, void* stream) {
-    if (!kind_ok(kind, coef) || method < ODE_TAB_EULER || method > ODE_TAB_RKF78 || n < 0 || nsteps < 0 ||
+    if (!kind_ok(kind, coef) || method < ODE_TAB_EULER || method > ODE_TAB_MIDPOINT || n < 0 || nsteps < 0 ||
         !std::isfinite(dt) || !std::isfinite(t0))
         return GS_ERR_INVALID;
     if (n > 0 && !x) return GS_ERR_INVALID;

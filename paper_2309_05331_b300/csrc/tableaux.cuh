@@ -1,6 +1,6 @@
 // tableaux.cuh -- Butcher tableaux of the explicit Runge-Kutta steppers of
-// Table 1 (explicit Euler, RK4, Dormand-Prince 5(4), Cash-Karp 5(4),
-// Fehlberg 7(8)) as compile-time constants for host and device code: the
+// Table 1 (explicit Euler, modified midpoint, RK4, Dormand-Prince 5(4),
+// Cash-Karp 5(4), Fehlberg 7(8)) as compile-time constants for host and device code: the
 // pointwise ensemble kernels (ode_tableau.cu) unroll them into FMA chains,
 // and the Gray-Scott tableau path (gs_grid.cu) reads them on the host.
 // Each struct: S stages, P / Q the orders of the propagated / embedded
@@ -26,6 +26,27 @@ struct TabEuler {
     }
     __host__ __device__ static constexpr double bh(int i) {
         constexpr double v[1] = {0.0};
+        return v[i];
+    }
+};
+// modified midpoint with two substeps (z1 = y + h f(y), z2 = y + 2h f(z1),
+// y' = (z1 + z2 + h f(z2)) / 2, h = dt / 2) as a 3-stage tableau; order 2.
+struct TabMidpoint {
+    static constexpr int S = 3, P = 2, Q = 0;
+    __host__ __device__ static constexpr double c(int i) {
+        constexpr double v[3] = {0.0, 0.5, 1.0};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double a(int i, int j) {
+        constexpr double v[3][3] = {{0, 0, 0}, {0.5, 0, 0}, {0, 1.0, 0}};
+        return v[i][j];
+    }
+    __host__ __device__ static constexpr double b(int i) {
+        constexpr double v[3] = {0.25, 0.5, 0.25};
+        return v[i];
+    }
+    __host__ __device__ static constexpr double bh(int i) {
+        constexpr double v[3] = {0.0, 0.0, 0.0};
         return v[i];
     }
 };

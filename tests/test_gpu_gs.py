@@ -741,7 +741,7 @@ def _tab_run_oracle(lap, dims, phys, u0, v0, omethod, dt, n):
 
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("lap", ["7point", "dcpse"])
-@pytest.mark.parametrize("method,omethod", TAB_METHODS)
+@pytest.mark.parametrize("method,omethod", TAB_METHODS + [("midpoint", oracle.MIDPOINT)])
 @pytest.mark.parametrize("dims", [(16, 12, 10), (9, 5, 4), (20, 8, 1)])
 def test_tableau_path_fixed_steps_match_oracle(prec, lap, method, omethod, dims):
     """Cash-Karp and Fehlberg fixed steps on the Gray-Scott grid (the tableau
@@ -758,7 +758,7 @@ def test_tableau_path_fixed_steps_match_oracle(prec, lap, method, omethod, dims)
     g = _gs(torch, dims, prec, u0, v0, **phys)
     if lap == "dcpse":
         gs.gs_set_laplacian(g.ctx, gs.GS_LAP_DCPSE, 3.1)
-    m = {"ck54": gs.GS_CK54, "rkf78": gs.GS_RKF78}[method]
+    m = {"ck54": gs.GS_CK54, "rkf78": gs.GS_RKF78, "midpoint": gs.GS_MIDPOINT}[method]
     t = g.step(m, 0.0, dt, 3)
     assert t == 3 * dt
     ou, ov = _tab_run_oracle(lap, dims, phys, u0, v0, omethod, dt, 3)
@@ -819,7 +819,7 @@ def test_tableau_path_adaptive_fp32_and_invalid():
                                        method=oracle.RKF78)
     assert r["t"] == 5.0 and abs(r["n_acc"] - ref["n_acc"]) <= 1
     assert_parity([to_np(g.u), to_np(g.v)], [ref["u"], ref["v"]], FP32_TOL)
-    for bad in (gs.GS_RK4, gs.GS_EULER, gs.GS_AB4, 17):
+    for bad in (gs.GS_RK4, gs.GS_EULER, gs.GS_AB4, gs.GS_MIDPOINT, 17):
         with pytest.raises(RuntimeError):
             g.integrate_adaptive(1e-6, 1e-6, 5.0, 6.0, 0.2, pair=bad)
     g.close()

@@ -155,7 +155,8 @@ def _family(okind, n, seed=11):
 
 
 ALL_KINDS = [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP, oracle.PW_PAPER_SIGMOID]
-TABS = [(0, oracle.EULER), (1, oracle.RK4), (2, oracle.DOPRI5), (3, oracle.CK54), (4, oracle.RKF78)]
+TABS = [(0, oracle.EULER), (1, oracle.RK4), (2, oracle.DOPRI5), (3, oracle.CK54), (4, oracle.RKF78),
+        (5, oracle.MIDPOINT)]
 
 
 def _cuda(torch, a):

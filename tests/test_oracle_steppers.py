@@ -74,6 +74,7 @@ def test_tree_enumeration_counts():
     (oracle.RK4, "b", 4),
     (oracle.DOPRI5, "b", 5),
     (oracle.DOPRI5, "bhat", 4),
+    (oracle.MIDPOINT, "b", 2),
 ])
 def test_order_conditions(method, weights, order):
     T = oracle.tableau(method)
@@ -104,8 +105,16 @@ def _R_dopri5(z):
     return sum(z ** k / math.factorial(k) for k in range(6)) + z ** 6 / 600.0
 
 
+def _R_midpoint(z):
+    # two substeps of h = dt/2 on x' = lambda x, written out: z1 = (1 + z/2) x,
+    # z2 = x + z z1, x' = (z1 + z2 + (z/2) z2) / 2  ->  1 + z + z^2/2 + z^3/8
+    z1 = 1 + z / 2
+    z2 = 1 + z * z1
+    return (z1 + z2 + z / 2 * z2) / 2
+
+
 @pytest.mark.parametrize("method,R", [(oracle.RK4, _R_rk4), (oracle.DOPRI5, _R_dopri5),
-                                      (oracle.EULER, lambda z: 1 + z)])
+                                      (oracle.EULER, lambda z: 1 + z), (oracle.MIDPOINT, _R_midpoint)])
 def test_exact_discrete_solution_decay(method, R):
     x0 = np.array([0.1, 0.5, 0.9, 1.7])
     for dt in (0.05, 0.3, 1.0):
@@ -146,7 +155,7 @@ def _family(kind):
 @pytest.mark.parametrize("kind", [oracle.PW_EXP_DECAY, oracle.PW_LOGISTIC, oracle.PW_PAPER_EXP,
                                   oracle.PW_PAPER_SIGMOID])
 @pytest.mark.parametrize("method,order,nbase", [(oracle.EULER, 1, 400), (oracle.RK4, 4, 40),
-                                                (oracle.DOPRI5, 5, 40)])
+                                                (oracle.DOPRI5, 5, 40), (oracle.MIDPOINT, 2, 200)])
 def test_observed_order(kind, method, order, nbase):
     x0, t0, t1, coef = _family(kind)
     exact = _closed_form(kind, x0, t0, t1, coef)
