@@ -59,6 +59,7 @@ PAIR_NAMES = ["k1", "stages2+3", "stages4+5", "stages6+7"]
 PAIR_FIELDS = [2, 4, 6, 8]
 BYTES_PER_FIELD_CELL = 8
 BATCH_BYTES_PER_CELL_ATTEMPT = 33 * BYTES_PER_FIELD_CELL  # batched path: single-stage schedule, FP32
+BATCH_PAIR_BYTES_PER_CELL_ATTEMPT = 18 * BYTES_PER_FIELD_CELL  # batched path: stage pairs, FP32
 NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside the measured copy peak)
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
@@ -527,8 +528,9 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
     for i, (u, v) in enumerate(inits):
         b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
     b.autotune()  # grouping (dense timing round)
-    tile = b.autotune_run(1e-6, 1e-6, 0.0, t_end, 0.1)  # tile: timed on this integration (state restored)
+    tile = b.autotune_run(1e-6, 1e-6, 0.0, t_end, 0.1)  # tile and pairs: timed on this integration (state restored)
     groups = b.grouping()
+    pairs = b.pairs()
     stream = torch.cuda.current_stream()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -562,17 +564,21 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
         g.close()
     b.close()
     # algorithmic bytes: every attempt of an instance moves its cells' 33
-    # field passes of the single-stage schedule (k1 reused)
+    # field passes of the single-stage schedule, or 18 with the stage pairs
+    # (k1 reused)
     attempts_cells = float(np.sum(cells * (rb["n_acc"] + rb["n_rej"])))
-    achieved = attempts_cells * BATCH_BYTES_PER_CELL_ATTEMPT / (ms_b * 1e-3) / 1e9
+    bpa = BATCH_PAIR_BYTES_PER_CELL_ATTEMPT if pairs[0] else BATCH_BYTES_PER_CELL_ATTEMPT
+    achieved = attempts_cells * bpa / (ms_b * 1e-3) / 1e9
     peak, peak_kind = _peaks()
     return {"gs_batched_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_b, "cell_steps_per_s": work_b / (ms_b * 1e-3), "accepted_total": int(rb["n_acc"].sum()),
         "rejected_total": int(rb["n_rej"].sum()), "cells_total": int(cells.sum()), "tile_ty_zc": [tile[0], tile[1]],
         "instance_groups": groups[1], "group_budget_cells": groups[0],
+        "kernels": ("stage pairs (one cell per lane), tile height %d, ring depth %d" % (pairs[1], pairs[2])
+                    if pairs[0] else "single stages"),
         "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                     "algorithmic_bytes_per_cell_attempt": BATCH_BYTES_PER_CELL_ATTEMPT,
+                     "algorithmic_bytes_per_cell_attempt": bpa,
                      "cell_attempts": attempts_cells}},
         "gs_per_instance_loop_512_uneven_dopri5_tol1e-6_t20": {
         "ms": ms_s, "cell_steps_per_s": work_s / (ms_s * 1e-3), "accepted_total": int(acc_s.sum())},

@@ -116,6 +116,8 @@ _SIGNATURES = {
                                 C.POINTER(C.c_int)], C.c_int),
     "gsb_set_tile": ([_vp, C.c_int, C.c_int], C.c_int),
     "gsb_set_grouping": ([_vp, C.c_longlong], C.c_int),
+    "gsb_set_pairs": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
+    "gsb_get_pairs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gsb_set_stage_depth": ([_vp, C.c_int], C.c_int),
     "gsb_get_grouping": ([_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
@@ -652,6 +654,14 @@ class GrayScottBatch:
     def set_stage_depth(self, depth):
         """Staged-form ring depth of the stage kernels (0: vectorised form)."""
         _bcheck(lib().gsb_set_stage_depth(self.ctx, depth), self.ctx)
+
+    def set_pairs(self, on, ty=7, depth=2):
+        _bcheck(lib().gsb_set_pairs(self.ctx, int(on), ty, depth), self.ctx)
+
+    def pairs(self):
+        on, ty, depth = C.c_int(0), C.c_int(0), C.c_int(0)
+        _bcheck(lib().gsb_get_pairs(self.ctx, C.byref(on), C.byref(ty), C.byref(depth)), self.ctx)
+        return on.value, ty.value, depth.value
 
     def set_grouping(self, cells_per_group):
         """Instance-group budget in cells (-1 automatic, 0 one group)."""

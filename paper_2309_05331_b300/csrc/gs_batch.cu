@@ -15,6 +15,13 @@
 // segment code is the staged form (each thread copies its inputs d planes
 // ahead into shared memory with cp.async), else the vectorised form.
 //
+// Stage pairs (gsb_set_pairs): stages 2+3, 4+5 and 6+7 each as one persistent
+// launch over the segments, running the single-grid pair segment
+// (gs_pair.cuh) with one cell per lane (any nx): k_i is recomputed on a
+// one-cell ring instead of being stored and read back, so an attempt moves
+// 18 field passes instead of 33; stages 6+7 fold each segment's error
+// maximum into its instance's accumulator.
+//
 // Cache blocking by instance group: a whole batch's stage fields are many
 // times the L2, but one instance's are small.  The instances are split into
 // consecutive groups whose working set (state, stage fields) fits a budget
@@ -31,6 +38,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "gs_pair.cuh"
 #include "gs_tile.cuh"
 #include "gs_staged.cuh"
 #include "gs_wide.cuh"
@@ -110,6 +118,68 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256,
     }
 }
 
+// One Dormand-Prince stage pair of every running instance (MODE_PAIR_STAGE:
+// stages 2+3 with NK = 1, 4+5 with NK = 3; MODE_PAIR_DOPRI67: stages 6+7,
+// y5, k7 and the instance's error maximum): CTAs take (instance, column of
+// A.ty rows x 32 cells, run of planes) segments from the counter and run the
+// pair segment with one cell per lane.
+// Tile heights of the batch's pair segments: up to 7 rows in a CTA compiled
+// for two per SM (384 threads, <= 85 registers), 8..12 rows in one compiled
+// for one per SM (544 threads, <= 120 registers).  12 is the most the pair
+// segment's halo warp covers (2 lanes per row for ty + 4 rows).
+constexpr int kBPairMaxTY = 12;
+template <bool TALL>
+__host__ __device__ constexpr int bpair_threads() {
+    return 32 * ((TALL ? kBPairMaxTY : kPairMaxTY) + 5);
+}
+
+template <typename T, int NK, int MODE, bool TALL>
+__global__ void __launch_bounds__(bpair_threads<TALL>(), TALL ? 1 : 2)
+    gsb_pair_kernel(const BInst* __restrict__ insts, DevCtrl* ctrls, const BSeg* __restrict__ segs, int nseg,
+                    unsigned int* counter, const StageArgs A, const int depth) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* SA = reinterpret_cast<T*>(smem_raw);
+    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, 1>();
+    unsigned char* SI = smem_raw + (pair_plane_bytes<T, 1>(A.ty) + 15) / 16 * 16;
+    unsigned char* R = SI + pair_isc_bytes<T, MODE, 1>(A.ty);
+    R += (128u - ((uint32_t)__cvta_generic_to_shared(R) & 127u)) & 127u;
+    __shared__ T red[32];
+    __shared__ int s_seg;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    for (;;) {
+        if (tid == 0) s_seg = (int)atomicAdd(counter, 1u);
+        __syncthreads();
+        const int sgi = s_seg;
+        __syncthreads();  // every thread has read s_seg before it is replaced
+        if (sgi >= nseg) break;
+        const BSeg sg = segs[sgi];
+        const DevCtrl* c = ctrls + sg.inst;
+        if (c->done) continue;  // block-uniform: control blocks are read-only here
+        const BInst in = insts[sg.inst];
+        Geom<T> g;
+        g.nx = in.nx;
+        g.ny = in.ny;
+        g.nz = in.nz;
+        g.cx = (T)in.cx;
+        g.cy = (T)in.cy;
+        g.cz = (T)in.cz;
+        g.Du = (T)in.Du;
+        g.Dv = (T)in.Dv;
+        g.F = (T)in.F;
+        g.k = (T)in.k;
+        const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, c->parity, 0, in.off);
+        const PairCoef<T, NK> C = pair_coef<T, NK>(A, c->dt_try, c->atol, c->rtol);
+        const int ntx = (in.nx + 31) / 32;
+        typename ErrBits<T>::U ebits = 0;
+        pair_segment<T, NK, MODE, 1>(g, P, C, SA, SB, SI, R, depth, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1,
+                                     ebits);
+        if (MODE == MODE_PAIR_DOPRI67) {
+            const T bmax = block_nanmax(ErrBits<T>::value(ebits), red);
+            if (tid == 0) atomic_max_nonneg(&ctrls[sg.inst].err_bits, (double)bmax);
+        }
+    }
+}
+
 // One thread per instance: accept / reject, next step, stop.  Resets the
 // stage segment counters (1 .. nctr-1) for the next attempt and sets the
 // loop condition.
@@ -162,12 +232,14 @@ struct gsb_ctx {
     DevCtrl* dctrl = nullptr;
     DevCtrl* hctrl = nullptr;  // pinned, count entries
     unsigned int* counters = nullptr;
-    BSeg* dseg[2] = {nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles
-    int nseg[2] = {0, 0};
+    BSeg* dseg[3] = {nullptr, nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles, [2]: pair tiles
+    int nseg[3] = {0, 0, 0};
     int ty = 6, zc = 16;
     int depth = 0;                        // staged-form ring depth (0: vectorised form)
+    int pairs = 0;                        // stage pairs (gsb_set_pairs)
+    int pty = 7, pdepth = 2;              // pair tile height and ring depth
     long long group_cells = 0;            // cells per group: -1 automatic (half the L2), 0 one group
-    std::vector<int> gseg0[2], gsegn[2];  // per group: first segment and count in each list
+    std::vector<int> gseg0[3], gsegn[3];  // per group: first segment and count in each list
     int ngroups = 1, nctr = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -203,9 +275,9 @@ static long long budget_cells(const gsb_ctx* ctx) {
     return std::max<long long>(1, (long long)l2 / 2 / ((long long)kCellFields * (long long)ctx->esz));
 }
 
-// segment lists for rows-per-CTA ty (stages) and min(ty, 6) (stage 7), and
-// the instance groups (consecutive instances, at most budget_cells cells,
-// at least one instance each)
+// segment lists for rows-per-CTA ty (stages), min(ty, 6) (stage 7) and pty
+// (stage pairs), and the instance groups (consecutive instances, at most
+// budget_cells cells, at least one instance each)
 static gs_status build_segments(gsb_ctx* ctx) {
     std::vector<int> first_inst;  // first instance of each group
     {
@@ -222,8 +294,8 @@ static gs_status build_segments(gsb_ctx* ctx) {
         }
     }
     ctx->ngroups = (int)first_inst.size();
-    for (int li = 0; li < 2; ++li) {
-        const int ty = li == 0 ? ctx->ty : std::min(ctx->ty, kMaxTYFinal);
+    for (int li = 0; li < 3; ++li) {
+        const int ty = li == 0 ? ctx->ty : (li == 1 ? std::min(ctx->ty, kMaxTYFinal) : ctx->pty);
         std::vector<BSeg> v;
         ctx->gseg0[li].assign(ctx->ngroups, 0);
         ctx->gsegn[li].assign(ctx->ngroups, 0);
@@ -365,8 +437,83 @@ static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st, in
     return blaunch(ctx, s, 5, MODE_DOPRI_FINAL, A, g, ctr);
 }
 
+template <typename T, int NK, int MODE>
+static cudaError_t bpair_launch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int group, int counter) {
+    const int seg0 = ctx->gseg0[2][group];
+    const int nseg = ctx->gsegn[2][group];
+    A.ty = ctx->pty;
+    auto kern = A.ty > kPairMaxTY ? gsb_pair_kernel<T, NK, MODE, true> : gsb_pair_kernel<T, NK, MODE, false>;
+    int depth = std::max(1, std::min(ctx->pdepth, kMaxDepth));
+    while (depth > 1 && pair_smem_bytes<T, NK, MODE, 1>(A.ty, depth) > kMaxSmemPerCta - 1024) --depth;
+    const size_t smem = pair_smem_bytes<T, NK, MODE, 1>(A.ty, depth);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (A.ty + 5), smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) occ = 1;
+    const int grid = std::max(1, std::min(nseg, ctx->nsm * occ));
+    kern<<<grid, dim3(32, A.ty + 5), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[2] + seg0, nseg,
+                                                ctx->counters + counter, A, depth);
+    return cudaGetLastError();
+}
+template <int NK, int MODE>
+static cudaError_t bpair_launch(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int group, int counter) {
+    if (ctx->prec == GS_FP64) return bpair_launch_t<double, NK, MODE>(ctx, s, A, group, counter);
+    return bpair_launch_t<float, NK, MODE>(ctx, s, A, group, counter);
+}
+
+// Dormand-Prince stage pair pi (0: stages 2+3, 1: 4+5, 2: 6+7 -> y5, k7 and
+// the error maxima) of instance group g: the buffers and coefficients of the
+// single-grid pairs
+static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int g) {
+    const int ctr = 1 + kStageCtrs * g + pi;
+    const Slot k1 = bpair(ctx, 1, 2, SEL_CUR);
+    const Slot k[6] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4), bfld(ctx, 5), bfld(ctx, 6)};  // k[i] = k_i
+    StageArgs A;
+    memset(&A, 0, sizeof(A));
+    A.u = bstate(ctx, SEL_CUR);
+    A.has_out1 = 1;
+    if (pi == 0) {
+        A.kin[0] = k[1];
+        A.a[0] = dp5::A21;
+        A.bk[0] = dp5::A31;
+        A.bk[1] = dp5::A32;
+        A.out0 = k[2];
+        A.out1 = k[3];
+        return bpair_launch<1, MODE_PAIR_STAGE>(ctx, s, A, g, ctr);
+    }
+    if (pi == 1) {
+        static const double a4[3] = {dp5::A41, dp5::A42, dp5::A43};
+        static const double a5[4] = {dp5::A51, dp5::A52, dp5::A53, dp5::A54};
+        for (int j = 0; j < 3; ++j) {
+            A.kin[j] = k[j + 1];
+            A.a[j] = a4[j];
+        }
+        for (int j = 0; j < 4; ++j) A.bk[j] = a5[j];
+        A.out0 = k[4];
+        A.out1 = k[5];
+        return bpair_launch<3, MODE_PAIR_STAGE>(ctx, s, A, g, ctr);
+    }
+    static const double a6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
+    for (int j = 0; j < 5; ++j) {
+        A.kin[j] = k[j + 1];
+        A.a[j] = a6[j];
+    }
+    A.out0 = bstate(ctx, SEL_NEXT);       // y5
+    A.out1 = bpair(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
+    return bpair_launch<5, MODE_PAIR_DOPRI67>(ctx, s, A, g, ctr);
+}
+
 static cudaError_t bbody(gsb_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond, bool with_ctrl) {
     for (int g = 0; g < ctx->ngroups; ++g) {
+        if (ctx->pairs) {
+            for (int pi = 0; pi < 3; ++pi) {
+                cudaError_t e = blaunch_dopri5_pair(ctx, s, pi, g);
+                if (e != cudaSuccess) return e;
+            }
+            continue;
+        }
         for (int st = 2; st <= 7; ++st) {
             cudaError_t e = blaunch_dopri5_stage(ctx, s, st, g);
             if (e != cudaSuccess) return e;
@@ -487,7 +634,7 @@ gs_status gsb_destroy(gsb_ctx* ctx) {
     if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
     if (ctx->dlog) cudaFree(ctx->dlog);
     if (ctx->counters) cudaFree(ctx->counters);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 3; ++i)
         if (ctx->dseg[i]) cudaFree(ctx->dseg[i]);
     delete ctx;
     return GS_OK;
@@ -516,6 +663,27 @@ gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc) {
     ctx->ty = ty;
     ctx->zc = zc;
     return build_segments(ctx);
+}
+
+gs_status gsb_set_pairs(gsb_ctx* ctx, int on, int ty, int depth) {
+    if (!ctx || on < 0 || on > 1 || ty < 1 || ty > kBPairMaxTY || depth < 1 || depth > kMaxDepth)
+        return GS_ERR_INVALID;
+    bdrop_graph(ctx);
+    ctx->pairs = on;
+    ctx->pdepth = depth;
+    if (ty != ctx->pty) {
+        ctx->pty = ty;
+        return build_segments(ctx);
+    }
+    return GS_OK;
+}
+
+gs_status gsb_get_pairs(const gsb_ctx* ctx, int* on, int* ty, int* depth) {
+    if (!ctx) return GS_ERR_INVALID;
+    if (on) *on = ctx->pairs;
+    if (ty) *ty = ctx->pty;
+    if (depth) *depth = ctx->pdepth;
+    return GS_OK;
 }
 
 gs_status gsb_set_stage_depth(gsb_ctx* ctx, int depth) {
@@ -751,7 +919,11 @@ gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, do
                            int* zc_out, double* best_ms) {
     if (!ctx || !ctx->state[0] || !(t0 < t_end) || !(dt0 > 0) || !(atol >= 0) || !(rtol >= 0) || !(atol + rtol > 0))
         return GS_ERR_INVALID;
-    static const int cand[][2] = {{4, 16}, {6, 16}, {6, 32}, {6, 64}, {8, 32}, {14, 16}, {14, 32}};
+    // (pairs, tile height, z-chunk): the single-stage tiles, then the stage
+    // pairs (one cell per lane) at two tile heights
+    static const int cand[][3] = {{0, 4, 16}, {0, 6, 16}, {0, 6, 32}, {0, 6, 64}, {0, 8, 32}, {0, 14, 16},
+                                  {0, 14, 32}, {1, 7, 32}, {1, 7, 64}, {1, 7, 128}, {1, 10, 64}, {1, 12, 64},
+                                  {1, 12, 128}};
     const size_t bytes = ctx->esz * (size_t)ctx->total;
     void* save[2] = {nullptr, nullptr};
     for (int c = 0; c < 2; ++c) {
@@ -770,7 +942,8 @@ gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, do
     gs_status st = GS_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = GS_ERR_CUDA;
     float best = 1e30f;
-    int bty = ctx->ty, bzc = ctx->zc;
+    int bty = ctx->ty, bzc = ctx->zc, bpairs = ctx->pairs, bpty = ctx->pty;
+    const int sty = ctx->ty;
     auto restore = [&]() -> gs_status {
         for (int c = 0; c < 2; ++c)
             if (cudaMemcpyAsync(ctx->state[c], save[c], bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
@@ -779,7 +952,13 @@ gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, do
     };
     for (const auto& c : cand) {
         if (st != GS_OK) break;
-        if ((st = gsb_set_tile(ctx, c[0], c[1])) != GS_OK) break;
+        if (c[0]) {
+            if ((st = gsb_set_tile(ctx, sty, c[2])) != GS_OK) break;
+            if ((st = gsb_set_pairs(ctx, 1, c[1], ctx->pdepth)) != GS_OK) break;
+        } else {
+            if ((st = gsb_set_pairs(ctx, 0, ctx->pty, ctx->pdepth)) != GS_OK) break;
+            if ((st = gsb_set_tile(ctx, c[1], c[2])) != GS_OK) break;
+        }
         for (int rep = 0; rep < 2 && st == GS_OK; ++rep) {  // the first run also builds the graph
             if ((st = restore()) != GS_OK) break;
             for (int i = 0; i < ctx->count; ++i) {
@@ -798,8 +977,12 @@ gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, do
             if (st == GS_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) st = GS_ERR_CUDA;
             if (st == GS_OK && rep == 1 && ms < best) {
                 best = ms;
-                bty = c[0];
-                bzc = c[1];
+                bpairs = c[0];
+                if (c[0])
+                    bpty = c[1];
+                else
+                    bty = c[1];
+                bzc = c[2];
             }
         }
     }
@@ -811,7 +994,8 @@ gs_status gsb_autotune_run(gsb_ctx* ctx, double atol, double rtol, double t0, do
     cudaFree(save[1]);
     if (st != GS_OK) return st;
     if ((st = gsb_set_tile(ctx, bty, bzc)) != GS_OK) return st;
-    if (ty_out) *ty_out = bty;
+    if ((st = gsb_set_pairs(ctx, bpairs, bpty, ctx->pdepth)) != GS_OK) return st;
+    if (ty_out) *ty_out = bpairs ? bpty : bty;
     if (zc_out) *zc_out = bzc;
     if (best_ms) *best_ms = best;
     return GS_OK;

@@ -149,6 +149,16 @@ gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group);
  * gsb_autotune tunes the tile of the depth in use. */
 gs_status gsb_set_stage_depth(gsb_ctx* ctx, int depth);
 gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* ngroups);
+/* Stage pairs for the batch: on = 1 runs each attempt as three launches
+ * (stages 2+3, 4+5, 6+7; the single-grid pair segment with one cell per lane,
+ * so any nx), 18 field passes per attempt instead of 33; ty = the pair
+ * segments' tile height (1..12; up to 7 in CTAs compiled for two per SM,
+ * 8..12 in CTAs compiled for one), depth = their input ring depth (1..3, cut
+ * to what shared memory holds).  The z-chunk is gsb_set_tile's.  Same
+ * formulas as the single stages (results agree to rounding).
+ * gsb_autotune_run tries both forms.  gsb_get_pairs: the setting in use. */
+gs_status gsb_set_pairs(gsb_ctx* ctx, int on, int ty, int depth);
+gs_status gsb_get_pairs(const gsb_ctx* ctx, int* on, int* ty, int* depth);
 
 /* ---------------------------- learned surrogate -------------------------- */
 /* Tensor-core engine of sur_conv3d (and of the network's convolutions),

@@ -49,6 +49,7 @@
 namespace gsk {
 
 constexpr int kPairMaxTY = 7;                        // rows per tile: ty + 5 warps (3 per SM sub-partition)
+// (the halo warp covers at most 12 rows: two lanes per row for ty + 4 rows)
 constexpr int kPairThreads = 32 * (kPairMaxTY + 5);  // launch bound: 168 registers per thread
 
 
@@ -171,6 +172,10 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     const bool inC = !hw && inA && r >= 0 && r < ah;
     const long long rowbase = (long long)nx * wrapm(y0 + r, ny);
     const long long cbase = rowbase + (hw ? (side == 0 ? wrapm(x0 - 2, nx) : wrapm(x0 + aw, nx)) : x0 + VX * lane);
+    // halo warp, one cell per lane in the rows (VX = 1, any nx): the pair's
+    // second cell wraps on its own and the pair is copied as two cells (an
+    // odd nx leaves it 8-byte unaligned)
+    const long long cbase1 = rowbase + (side == 0 ? wrapm(x0 - 1, nx) : wrapm(x0 + aw + 1, nx));
     const int col = hw ? (side == 0 ? -2 : aw) : VX * lane;  // shared-memory column of the first cell
     const int hin = side == 0 ? -1 : aw;                      // halo warp: its inner column
     const int hsel = side == 0 ? 1 : 0;                       // ... and its index in the pair
@@ -199,8 +204,13 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             for (int c = 0; c < 2; ++c) {
 #pragma unroll
                 for (int f = 0; f <= NK; ++f) {
-                    const T* src = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]) + cbase + zo;
-                    if (hw)
+                    const T* base = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]);
+                    const T* src = base + cbase + zo;
+                    if (hw && VX == 1) {
+                        T* dst = reinterpret_cast<T*>(rhal(s, c * (1 + NK) + f));
+                        cp_async_vec<sizeof(T)>(dst, src);
+                        cp_async_vec<sizeof(T)>(dst + 1, base + cbase1 + zo);
+                    } else if (hw)
                         cp_async_vec<2 * sizeof(T)>(rhal(s, c * (1 + NK) + f), src);
                     else
                         cp_async_vec<sizeof(VTy)>(rvec(s, c * (1 + NK) + f), src);
@@ -480,10 +490,15 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     Y, P2, Qd, Id, std::false_type{});
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
-                    V2 st;
-                    reinterpret_cast<T*>(&st)[0] = Y[c][0];
-                    reinterpret_cast<T*>(&st)[1] = Y[c][1];
-                    *reinterpret_cast<V2*>(SA + ia(b, r, c, col)) = st;
+                    if (VX == 1) {  // the pair's column may be odd
+                        SA[ia(b, r, c, col)] = Y[c][0];
+                        SA[ia(b, r, c, col) + 1] = Y[c][1];
+                    } else {
+                        V2 st;
+                        reinterpret_cast<T*>(&st)[0] = Y[c][0];
+                        reinterpret_cast<T*>(&st)[1] = Y[c][1];
+                        *reinterpret_cast<V2*>(SA + ia(b, r, c, col)) = st;
+                    }
                     h2[c] = Y[c][hsel];
                     hp2a[c] = P2[c][hsel];
                 }
@@ -520,8 +535,15 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     __syncthreads();           // the plane buffers are reused by the next segment
 }
 
+// CTAs per SM the pair kernel is compiled for: one with 16-byte rows (its
+// registers fill the SM at 384 threads), two with one cell per lane
+template <int VX>
+__host__ __device__ constexpr int pair_min_blocks() {
+    return VX == 1 ? 2 : 1;
+}
+
 template <typename T, int NK, int MODE, int VX>
-__global__ void __launch_bounds__(kPairThreads, 1) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
+__global__ void __launch_bounds__(kPairThreads, pair_min_blocks<VX>()) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
     T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, VX>();

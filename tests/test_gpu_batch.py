@@ -175,9 +175,60 @@ def test_batched_max_accepted_and_per_instance_times():
     b.close()
 
 
-def test_full_size_512_instance_ensemble():
+@pytest.mark.parametrize("ty,depth", [(7, 2), (3, 1), (1, 3), (12, 2), (9, 1)])
+def test_batched_pairs_fp64_match_oracle(ty, depth):
+    """The batch's stage pairs (stages 2+3, 4+5, 6+7 each one launch, one cell
+    per lane, any nx): every instance takes the oracle's accepted / rejected
+    steps and step sizes and matches its state element by element; odd and
+    tiny grids (1^3, nx = 5, 17, 33), tile heights above ny."""
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=300)
+    b = _batch(torch, SMALL, inits, 0)
+    b.set_pairs(1, ty, depth)
+    assert b.pairs() == (1, ty, depth)
+    b.set_step_log(200)
+    r = b.integrate_adaptive(1e-8, 1e-8, 0.0, 5.0, 0.1)
+    logs = b.step_log()
+    for i, d in enumerate(SMALL):
+        ref = _oracle_adaptive(d, *inits[i], 5.0, 1e-8, log_cap=200)
+        assert r["t"][i] == 5.0 and ref["t"] == 5.0
+        assert (r["n_acc"][i], r["n_rej"][i]) == (ref["n_acc"], ref["n_rej"]), i
+        assert np.allclose(logs[i], ref["dts"], rtol=1e-7, atol=0), i
+        gu, gv = b.view(i)
+        assert_parity([to_np(gu), to_np(gv)], [ref["u"], ref["v"]], 1e-12, i)
+    b.close()
+
+
+def test_batched_pairs_fp32_match_oracle_replay_and_single_stages():
+    """FP32 batch with the stage pairs: every instance against the FP64 oracle
+    replaying its logged step sizes (1e-5), and against the same batch run
+    with the single-stage kernels (the same formulas in another order)."""
+    torch = cuda_or_skip()
+    inits = _inits(SMALL, seed0=310, round32=True)
+    res = []
+    for pairs in (1, 0):
+        b = _batch(torch, SMALL, inits, 1)
+        b.set_pairs(pairs, 5, 2)
+        b.set_step_log(200)
+        r = b.integrate_adaptive(1e-6, 1e-6, 0.0, 4.0, 0.1)
+        assert np.all(r["statuses"] == 0) and np.all(r["t"] == 4.0)
+        logs = b.step_log()
+        states = [tuple(to_np(x) for x in b.view(i)) for i in range(len(SMALL))]
+        res.append((logs, states, r["n_acc"].copy()))
+        b.close()
+    for i, d in enumerate(SMALL):
+        p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], **PHYS)
+        ou, ov = oracle.gs_integrate_replay(p, *inits[i], oracle.DOPRI5, res[0][0][i])
+        assert_parity(list(res[0][1][i]), [ou, ov], 1e-5, i)
+        if res[0][2][i] == res[1][2][i] and np.allclose(res[0][0][i], res[1][0][i], rtol=1e-5):
+            assert_parity(list(res[0][1][i]), list(res[1][1][i]), 1e-5, ("pairs vs stages", i))
+
+
+@pytest.mark.parametrize("pairs", [0, 1])
+def test_full_size_512_instance_ensemble(pairs):
     """512 instances, per-axis edges U{16..96}, F in [0.02,0.06], k in
-    [0.04,0.07], FP32 state / FP64 control, 3 accepted steps each; EVERY
+    [0.04,0.07], FP32 state / FP64 control, 3 accepted steps each, single
+    stages and stage pairs; EVERY
     instance against the FP64 oracle replaying that instance's logged
     accepted step sizes, cell by cell (an FP32 run takes its own step sizes:
     its error norms carry FP32 rounding, so its own adaptive sequence is
@@ -192,6 +243,7 @@ def test_full_size_512_instance_ensemble():
         b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
         inits.append((u, v))
     b.autotune()
+    b.set_pairs(pairs, 7, 2)
     b.set_step_log(8)
     r = b.integrate_adaptive(1e-6, 1e-6, 0.0, np.inf, 0.1, max_accepted=3)
     assert np.all(r["statuses"] == 0) and np.all(r["n_acc"] == 3)
@@ -220,13 +272,18 @@ def test_autotune_run_restores_state_and_picks_a_candidate():
     b = _batch(torch, SMALL, inits, 0)
     before = [to_np(x).copy() for i in range(len(SMALL)) for x in b.view(i)]
     ty, zc, ms = b.autotune_run(1e-7, 1e-7, 0.0, 1.0, 0.1)
-    assert (ty, zc) in {(4, 16), (6, 16), (6, 32), (6, 64), (8, 32), (14, 16), (14, 32)} and ms > 0
+    pairs = b.pairs()
+    if pairs[0]:
+        assert (ty, zc) in {(7, 32), (7, 64), (7, 128), (10, 64), (12, 64), (12, 128)} and pairs[1] == ty and ms > 0
+    else:
+        assert (ty, zc) in {(4, 16), (6, 16), (6, 32), (6, 64), (8, 32), (14, 16), (14, 32)} and ms > 0
     after = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
     assert all(np.array_equal(p, q) for p, q in zip(before, after))
     b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
     tuned = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
     b.close()
     b = _batch(torch, SMALL, inits, 0)
+    b.set_pairs(*pairs)  # the same kernels on the default tile
     b.integrate_adaptive(1e-7, 1e-7, 0.0, 1.0, 0.1)
     ref = [to_np(x) for i in range(len(SMALL)) for x in b.view(i)]
     b.close()
