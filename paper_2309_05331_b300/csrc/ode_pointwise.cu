@@ -30,10 +30,11 @@ __device__ __forceinline__ double rhs(double x) {
     return x * (1.0 - x);
 }
 
-// One Dormand-Prince 5(4) attempt of element x with step h: returns y5 and
-// the scaled error ratio.
+// One Dormand-Prince 5(4) attempt of element x with step h: returns y5, the
+// error magnitude |err| and its scale atol + rtol (|x| + h |k1|).
 template <int KIND>
-__device__ __forceinline__ double dp5_attempt(double x, double h, double atol, double rtol, double& ratio) {
+__device__ __forceinline__ double dp5_attempt(double x, double h, double atol, double rtol, double& aerr,
+                                              double& scale) {
     using namespace dp5;
     const double k1 = rhs<KIND>(x);
     const double k2 = rhs<KIND>(x + h * (A21 * k1));
@@ -44,10 +45,36 @@ __device__ __forceinline__ double dp5_attempt(double x, double h, double atol, d
     const double y5 = x + h * (B1 * k1 + B3 * k3 + B4 * k4 + B5 * k5 + B6 * k6);
     const double k7 = rhs<KIND>(y5);
     const double err = h * (E1 * k1 + E3 * k3 + E4 * k4 + E5 * k5 + E6 * k6 + E7 * k7);
-    const double sc = atol + rtol * (fabs(x) + h * fabs(k1));
-    ratio = fabs(err) / sc;
+    aerr = fabs(err);
+    scale = atol + rtol * (fabs(x) + h * fabs(k1));
     return y5;
 }
+
+// Running maximum of the ratios a_i / s_i without a division per element:
+// the maximum is kept as the pair (num, den) of its element, and a_i / s_i
+// exceeds it iff a_i den > num s_i, both products exact up to one rounding
+// while every a_i and s_i lies in [2^-500, 2^500) (a_i = 0 included), so the
+// element chosen is the one with the largest ratio, up to a tie within an
+// ulp.  The thread divides once at the end.  Any value outside that range
+// (zero or subnormal scale, NaN, inf, extreme magnitudes) marks the thread,
+// which then recomputes its elements' ratios with one division each and the
+// NaN-propagating maximum: the result is the plain max_i a_i / s_i either
+// way.
+struct RatioMax {
+    double num = 0.0, den = 1.0;
+    bool odd = false;
+    __device__ __forceinline__ void add(double a, double sc) {
+        // biased exponents (a >= 0: |err|); integer tests, off the FP64 pipe
+        const long long ab = __double_as_longlong(a);
+        const unsigned ea = (unsigned)(ab >> 52) & 0x7ffu;
+        const unsigned es = ((unsigned)__double2hiint(sc) >> 20) & 0x7ffu;
+        odd |= !(ab == 0 || ea - 523u < 1000u) || !(es - 523u < 1000u);
+        if (a * den > num * sc) {
+            num = a;
+            den = sc;
+        }
+    }
+};
 
 template <int KIND>
 __device__ __forceinline__ double rk4_step(double x, double h) {
@@ -69,11 +96,22 @@ __global__ void __launch_bounds__(256) ode_dp5_attempt_kernel(long long n, doubl
     double* __restrict__ y = parity ? xa : xb;
     double emax = 0.0;
     if (!c->done) {
+        RatioMax m;
         for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
              i += (long long)gridDim.x * blockDim.x) {
-            double r;
-            y[i] = dp5_attempt<KIND>(x[i], h, atol, rtol, r);
-            emax = nanmax(emax, r);
+            double a, sc;
+            y[i] = dp5_attempt<KIND>(x[i], h, atol, rtol, a, sc);
+            m.add(a, sc);
+        }
+        emax = m.num / m.den;
+        if (m.odd) {  // exceptional values: the plain maximum of the ratios
+            emax = 0.0;
+            for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+                 i += (long long)gridDim.x * blockDim.x) {
+                double a, sc;
+                dp5_attempt<KIND>(x[i], h, atol, rtol, a, sc);
+                emax = nanmax(emax, a / sc);
+            }
         }
     }
     const double bmax = block_nanmax(emax, red);
@@ -141,8 +179,8 @@ __global__ void __launch_bounds__(256) ode_const_kernel(long long n, double* x, 
             } else if (METHOD == GS_RK4) {
                 u = rk4_step<KIND>(u, dt);
             } else {
-                double r;
-                u = dp5_attempt<KIND>(u, dt, 1.0, 1.0, r);
+                double a, sc;  // the error estimate is unused in fixed steps
+                u = dp5_attempt<KIND>(u, dt, 1.0, 1.0, a, sc);
             }
         }
         x[i] = u;

@@ -381,3 +381,44 @@ def test_adaptive_each_lanes_refill_from_their_chunk():
     err = np.abs(got - ref["x"]) / (1.0 + np.abs(ref["x"]))
     assert np.max(err[same]) < 1e-11
     assert np.max(err) < 1e-7
+
+
+def _exceptional_cases():
+    """Inputs whose error ratios leave the range where the attempt kernel
+    compares ratios by cross-multiplication (magnitudes outside 2^-500 ..
+    2^500, zero or subnormal scales, NaN): the kernel then takes the plain
+    maximum of the divided ratios, so the run must still match the oracle's."""
+    base = si.ode_initial_values(3000, seed=11)
+    wide = base.copy()
+    wide[::7] *= 1e250   # scales above 2^500
+    wide[3::7] *= 1e-290  # |err| below 2^-500
+    zero_scale = base.copy()
+    zero_scale[5] = 0.0   # atol = 0: 0 / 0 at this element
+    sub = base.copy()
+    sub[9] = 1e-300       # atol = 0: a subnormal scale, rtol |x| ~ 1e-308
+    nan = base.copy()
+    nan[1234] = np.nan
+    return [("wide", 0, oracle.PW_EXP_DECAY, wide, 1e-8, 1e-8),
+            ("wide_logistic", 1, oracle.PW_LOGISTIC, wide, 1e-8, 1e-8),
+            ("zero_scale", 0, oracle.PW_EXP_DECAY, zero_scale, 0.0, 1e-8),
+            ("subnormal_scale", 1, oracle.PW_LOGISTIC, sub, 0.0, 1e-8),
+            ("relative_only", 1, oracle.PW_LOGISTIC, base, 0.0, 1e-8),
+            ("nan", 0, oracle.PW_EXP_DECAY, nan, 1e-8, 1e-8)]
+
+
+@pytest.mark.parametrize("case", _exceptional_cases(), ids=lambda c: c[0])
+def test_adaptive_exceptional_ratios_match_oracle(case):
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    _, kind, okind, x0, atol, rtol = case
+    x = torch.from_numpy(x0.copy()).cuda()
+    log = torch.zeros(100000, dtype=torch.float64, device="cuda")
+    r = gs.ode_integrate_adaptive(kind, x, 0.0, 10.0, 1e-3, atol, rtol, dt_log=log, check=False)
+    ref = oracle.pw_integrate_adaptive(okind, x0, 0.0, 10.0, 1e-3, atol, rtol, log_cap=100000)
+    assert r["status"] == ref["status"]
+    assert (r["n_acc"], r["n_rej"]) == (ref["n_acc"], ref["n_rej"])
+    assert r["t"] == pytest.approx(ref["t"], rel=1e-12, abs=0)
+    d = to_np(log)[: r["n_acc"]]
+    assert np.allclose(d, ref["dts"], rtol=1e-7, atol=0)
+    if ref["status"] == oracle.OK:  # per element relative to its start value (magnitudes 1e-290 .. 1e250)
+        assert_parity(to_np(x) / x0, ref["x"] / x0, 1e-12)
