@@ -253,8 +253,10 @@ static int pair_depth_fit(int ty, int depth) {
 template <typename T, int NK, int MODE, int VX>
 static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int depth) {
     const Geom<T> g = make_geom<T>(ctx->p);
-    auto kern = gs_pair_kernel<T, NK, MODE, VX>;
-    if (A.ty < 1 || A.ty > kPairMaxTY) return cudaErrorInvalidConfiguration;
+    if (A.ty < 1 || A.ty > pair_max_ty(MODE)) return cudaErrorInvalidConfiguration;
+    auto kern = gs_pair_kernel<T, NK, MODE, VX, false>;
+    if constexpr (MODE != MODE_PAIR_DOPRI67)
+        if (A.ty > kPairMaxTY) kern = gs_pair_kernel<T, NK, MODE, VX, true>;
     const int txw = 32 * VX;
     A.ntx = (ctx->p.nx + txw - 1) / txw;
     A.nty = (ctx->p.ny + A.ty - 1) / A.ty;
@@ -1659,9 +1661,16 @@ gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode) {
 
 int gs_get_dopri5_fusion(const gs_ctx* ctx) { return ctx && pairs_on(ctx) ? 1 : 0; }
 
+// the launch mode of pair kernel pi (0..2: Dormand-Prince 2+3, 4+5, 6+7;
+// 3, 4: RK4 1+2, 3+4)
+static int pair_mode(int pi) {
+    return pi == 2 ? MODE_PAIR_DOPRI67 : (pi == 4 ? MODE_PAIR_RK4 : MODE_PAIR_STAGE);
+}
+
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth) {
-    if (!ctx || pair < -1 || pair > 4 || ty < 1 || ty > kPairMaxTY || depth < 1 || depth > kMaxDepth)
-        return GS_ERR_INVALID;
+    if (!ctx || pair < -1 || pair > 4 || ty < 1 || depth < 1 || depth > kMaxDepth) return GS_ERR_INVALID;
+    for (int pi = 0; pi < 5; ++pi)
+        if ((pair < 0 || pair == pi) && ty > pair_max_ty(pair_mode(pi))) return GS_ERR_INVALID;
     drop_graphs(ctx);
     for (int pi = 0; pi < 5; ++pi)
         if (pair < 0 || pair == pi) ctx->pc[pi] = KCfg{5, ty, 0, depth};
@@ -1848,7 +1857,7 @@ gs_status gs_autotune(gs_ctx* ctx, int* ty_out, int* zc_out, double* best_ms) {
     for (int pi = 0; pi < 5 && tune_pairs && st == GS_OK; ++pi) {
         float best = 1e30f;
         const KCfg saved = ctx->pc[pi];
-        for (int ty = 2; ty <= kPairMaxTY && st == GS_OK; ++ty)
+        for (int ty = 2; ty <= pair_max_ty(pair_mode(pi)) && st == GS_OK; ++ty)
             for (int depth = 1; depth <= kMaxDepth && st == GS_OK; ++depth) {
                 ctx->pc[pi] = KCfg{5, ty, 0, depth};
                 int used[5];

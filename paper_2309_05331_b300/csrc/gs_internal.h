@@ -102,7 +102,9 @@ int gs_get_dopri5_fusion(const gs_ctx* ctx);
 int gs_get_rk4_fusion(const gs_ctx* ctx);
 /* Launch shape of pair kernel `pair` (0: Dormand-Prince stages 2+3, 1: 4+5,
  * 2: 6+7; 3: RK4 stages 1+2, 4: RK4 stages 3+4 with the update; -1: all
- * five): tile height ty (1..7 rows; the CTA has ty + 5 warps) and input ring
+ * five): tile height ty (1..7 rows, 1..11 except for stages 6+7: the CTA
+ * has ty + 5 warps, compiled for 12 warps up to 7 rows and for 16 above; -1
+ * with ty > 7 is rejected) and input ring
  * depth (1..3 planes; cut back at launch to what shared memory holds).
  * gs_autotune overwrites it.  gs_get_pair_configs: host arrays of 5 ints. */
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth);

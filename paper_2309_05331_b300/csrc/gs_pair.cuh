@@ -48,9 +48,20 @@
 
 namespace gsk {
 
-constexpr int kPairMaxTY = 7;                        // rows per tile: ty + 5 warps (3 per SM sub-partition)
-// (the halo warp covers at most 12 rows: two lanes per row for ty + 4 rows)
-constexpr int kPairThreads = 32 * (kPairMaxTY + 5);  // launch bound: 168 registers per thread
+// Tile heights: up to 7 rows in a CTA of 12 warps (3 per SM sub-partition,
+// 168 registers per thread), 8..11 rows in a "tall" CTA of 16 warps (4 per
+// sub-partition, 128 registers) for the pairs whose state fits that budget
+// (not Dormand-Prince stages 6+7).  The halo warp covers at most 16 rows
+// (two lanes per row for ty + 4 rows).
+constexpr int kPairMaxTY = 7;
+constexpr int kPairMaxTYTall = 11;
+template <bool TALL>
+__host__ __device__ constexpr int pair_threads() {
+    return 32 * ((TALL ? kPairMaxTYTall : kPairMaxTY) + 5);
+}
+__host__ __device__ constexpr int pair_max_ty(int mode) {
+    return mode == MODE_PAIR_DOPRI67 ? kPairMaxTY : kPairMaxTYTall;
+}
 
 
 template <typename T>
@@ -542,8 +553,9 @@ __host__ __device__ constexpr int pair_min_blocks() {
     return VX == 1 ? 2 : 1;
 }
 
-template <typename T, int NK, int MODE, int VX>
-__global__ void __launch_bounds__(kPairThreads, pair_min_blocks<VX>()) gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
+template <typename T, int NK, int MODE, int VX, bool TALL>
+__global__ void __launch_bounds__(pair_threads<TALL>(), TALL ? 1 : pair_min_blocks<VX>())
+    gs_pair_kernel(const Geom<T> g, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
     T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, VX>();
