@@ -64,11 +64,11 @@ NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside 
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 832.0 MB read + 248.3 MB written), per cell so that other grids scale by
+# 832.7 MB read + 248.3 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "e8905a424f720b80",
-               "bytes_per_cell": (832034560 + 248319232) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "0d15f12579af01ed",
+               "bytes_per_cell": (832662016 + 248261120) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
