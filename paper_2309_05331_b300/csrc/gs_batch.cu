@@ -124,8 +124,10 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256,
 // A.ty rows x 32 cells, run of planes) segments from the counter and run the
 // pair segment with one cell per lane.
 // Tile heights of the batch's pair segments: up to 7 rows in a CTA compiled
-// for two per SM (384 threads, <= 85 registers), 8..12 rows in one compiled
-// for one per SM (544 threads, <= 120 registers).  12 is the most the pair
+// for two per SM (384 threads, <= 80 registers), 8..12 rows in one compiled
+// for one per SM (544 threads: 17 warps, 5 on one SM sub-partition, so <= 96
+// registers; stages 6+7 spill a little there, yet 12 rows measured faster
+// than 11 rows in 16 warps at 128 registers).  12 is the most the pair
 // segment's halo warp covers (2 lanes per row for ty + 4 rows).
 constexpr int kBPairMaxTY = 12;
 template <bool TALL>
