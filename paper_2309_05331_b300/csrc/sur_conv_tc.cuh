@@ -46,9 +46,11 @@
 // planes 2 (w / 4), 2 (w / 4) + 1).  Two halo buffers and two accumulator
 // sets (2 x 256 TMEM columns) flow between them through mbarriers: halo full
 // (256 loader arrivals) / halo empty (MMA commit), accumulators full (MMA
-// commit) / empty (8 epilogue warps).  The loaders publish the halo of tile
-// i+1 before the epilogue of tile i, so the MMAs of tile i+1 run while the
-// epilogue of tile i does, and the MMA warp never joins a block barrier.
+// commit) / empty (8 epilogue warps).  Once the MMAs of tile i complete, the
+// loaders publish the halo of tile i+1 (copied meanwhile) and start copying
+// that of tile i+2 into the buffer tile i used, then run the epilogue of
+// tile i: the MMAs of tile i+1 and the copies for tile i+2 both run while
+// the epilogue of tile i does, and the MMA warp never joins a block barrier.
 // Every mbarrier wait has an iteration limit and also watches a shared abort
 // flag: on expiry the kernel sets the caller's timeout word (host-mapped
 // memory the host reads after the launch, so the call that owns the launch
@@ -185,12 +187,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // Periodic halo of the tile at (x0, y0, z0), chunk-major: chunk q of halo
 // cell c at byte (q * HC + c) * 16; copied with cp.async (this thread's
-// copies only).  NCI chunks (CIN = 8 NCI channels) per cell.
+// copies only).  NCI chunks (CIN = 8 NCI channels) per cell.  Consecutive
+// threads take consecutive chunks of a cell, then of the next cell in x, so
+// a warp reads whole cells (contiguous runs of x) and every 32-byte sector
+// it touches is used whole.
 template <int NCI>
 __device__ __forceinline__ void halo_async(unsigned char* Xs, const __nv_bfloat16* __restrict__ x, int x0, int y0,
                                            int z0, int D, int H, int W) {
     for (int idx = threadIdx.x; idx < HC * NCI; idx += NLOAD) {
-        const int q = idx / HC, c = idx - q * HC;
+        const int q = idx % NCI, c = idx / NCI;
         const int hx = c % HX, rr = c / HX, hy = rr % HY, hz = rr / HY;
         // periodic wrap of a coordinate in [-1, n]
         int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;
@@ -198,7 +203,7 @@ __device__ __forceinline__ void halo_async(unsigned char* Xs, const __nv_bfloat1
         gy += gy < 0 ? H : (gy >= H ? -H : 0);
         gz += gz < 0 ? D : (gz >= D ? -D : 0);
         const size_t g = ((size_t)gx + (size_t)W * ((size_t)gy + (size_t)H * gz)) * (8 * NCI) + 8 * q;
-        const uint32_t dst = smem_u32(Xs + (size_t)idx * 16);
+        const uint32_t dst = smem_u32(Xs + (size_t)(q * HC + c) * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(x + g) : "memory");
     }
 }
@@ -350,25 +355,33 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             fence_smem_to_async();
             mbar_arrive(bar(HF + (i & 1)));
         };
+        // halo i + 1 is copied while tile i's MMAs and epilogue run: it is
+        // issued right after tile i - 1's MMAs complete (its buffer was last
+        // read by them) and published right after tile i's MMAs complete,
+        // before tile i's epilogue, so the MMAs of tile i + 1 also run while
+        // the epilogue of tile i does
         if (nmine > 0) {
             load(0);
             publish(0);
         }
+        if (nmine > 1) load(1);  // buffer 1: first use
         const int m = 32 * (warp & 3) + lane, mx = m % TX, my = m / TX;
+        // the bias in registers for the whole launch (per-plane loads of it
+        // would queue behind the halo copies)
+        constexpr bool HAS_BIAS = EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32 || EPI == EPI_RAW_F32;
+        float bv[COUT];
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) bv[o] = (HAS_BIAS && bias) ? __ldg(bias + o) : 0.f;
         for (int i = 0; i < nmine; ++i) {
             const int s = i & 1;
-            if (i + 1 < nmine) {
-                // buffer (i+1) % 2 was last read by the MMAs of tile i-1; the
-                // next halo is published before this tile's epilogue, so the
-                // MMAs of tile i+1 run while the epilogue of tile i does
-                if (i + 1 >= 2 && !mbar_wait_bounded(bar(HE + ((i + 1) & 1)), (uint32_t)((((i + 1) >> 1) - 1) & 1),
-                                                     abort, timeouts))
-                    break;
-                load(i + 1);
-                publish(i + 1);
-            }
             if (!mbar_wait_bounded(bar(AF + s), (uint32_t)((i >> 1) & 1), abort, timeouts)) break;
             fence_after_sync();
+            if (i + 1 < nmine) publish(i + 1);
+            if (i + 2 < nmine) {
+                // buffer s was last read by the MMAs of tile i (complete)
+                if (!mbar_wait_bounded(bar(HE + s), (uint32_t)((((i + 2) >> 1) - 1) & 1), abort, timeouts)) break;
+                load(i + 2);
+            }
             int x0, y0, z0;
             tile_origin(i, x0, y0, z0);
 #pragma unroll 1
@@ -387,9 +400,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
                     if (lane == 0) mbar_arrive(bar(AE + s));  // this warp's accumulator rows are read
                 }
                 const size_t cell = (size_t)(x0 + mx) + (size_t)W * ((size_t)(y0 + my) + (size_t)H * (z0 + p));
-                if (EPI == EPI_BIAS_RELU_BF16 || EPI == EPI_BIAS_F32 || (EPI == EPI_RAW_F32 && bias)) {
+                if (HAS_BIAS) {
 #pragma unroll
-                    for (int o = 0; o < COUT; ++o) v[o] += __ldg(bias + o);
+                    for (int o = 0; o < COUT; ++o) v[o] += bv[o];
                 }
                 if (EPI == EPI_BIAS_RELU_BF16) {
 #pragma unroll

@@ -63,12 +63,14 @@ constexpr uint32_t kIdescW = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (
 
 // x halo (chunk-major over 4 planes: chunk q of halo cell c at (q HC + c) 16)
 // and the dy tile (chunk q of tile cell t at (q 128 + t) 16) of the one-plane
-// tile at (x0, y0, z0); this thread's cp.async copies.
+// tile at (x0, y0, z0); this thread's cp.async copies.  Consecutive threads
+// take consecutive chunks of a cell, then of the next cell, so a warp reads
+// whole cells and every 32-byte sector it touches is used whole.
 __device__ __forceinline__ void tile_async(unsigned char* buf, const __nv_bfloat16* __restrict__ x,
                                            const __nv_bfloat16* __restrict__ dy, int x0, int y0, int z0, int D, int H,
                                            int W) {
     for (int idx = threadIdx.x; idx < HC * NCHUNK; idx += NLOAD) {
-        const int q = idx / HC, c = idx - q * HC;
+        const int q = idx % NCHUNK, c = idx / NCHUNK;
         const int hx = c % HX, rr = c / HX, hy = rr % HY, hz = rr / HY;
         int gx = x0 + hx - 1, gy = y0 + hy - 1, gz = z0 + hz - 1;  // gz in [-1, z0 + 2]
         gx += gx < 0 ? W : (gx >= W ? -W : 0);
@@ -77,15 +79,15 @@ __device__ __forceinline__ void tile_async(unsigned char* buf, const __nv_bfloat
         gz -= gz >= D ? D : 0;
         gz -= gz >= D ? D : 0;  // D == 1: z0 + 2 wraps twice
         const size_t g = ((size_t)gx + (size_t)W * ((size_t)gy + (size_t)H * gz)) * CH + 8 * q;
-        const uint32_t dst = smem_u32(buf + (size_t)idx * 16);
+        const uint32_t dst = smem_u32(buf + (size_t)(q * HC + c) * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(x + g) : "memory");
     }
     unsigned char* ybuf = buf + X_BYTES;
     for (int idx = threadIdx.x; idx < TX * TY * NCHUNK; idx += NLOAD) {
-        const int q = idx / (TX * TY), t = idx - q * (TX * TY);
+        const int q = idx % NCHUNK, t = idx / NCHUNK;
         const int tx = t % TX, ty = t / TX;
         const size_t g = ((size_t)(x0 + tx) + (size_t)W * ((size_t)(y0 + ty) + (size_t)H * z0)) * CH + 8 * q;
-        const uint32_t dst = smem_u32(ybuf + (size_t)idx * 16);
+        const uint32_t dst = smem_u32(ybuf + (size_t)(q * (TX * TY) + t) * 16);
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(dy + g) : "memory");
     }
 }
