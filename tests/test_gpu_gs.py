@@ -576,11 +576,14 @@ def _light_cone_check(state_after, u0, v0, dims, method, dt, nsteps, radius, cen
 def _seam_centers(n, ty, rng, count=64):
     """Sample cells (z, y, x) of an n^3 grid on the places a tiling can get
     wrong: x at the periodic seam and at the 128-cell row boundaries, y at the
-    periodic seam and at tile-height boundaries, z at the seam and at the
-    middle (where two z-bands of the column-split schedule meet), plus random
-    cells; count in total."""
+    periodic seam and at the tile-height boundaries of every height in ty (an
+    int or several), z at the seam and at the middle (where two z-bands of the
+    column-split schedule meet), plus random cells; count in total."""
     xs = sorted({0, 1, 126, 127, 128, 129, n - 2, n - 1})
-    ys = sorted({0, ty - 1, ty, 2 * ty - 1, 2 * ty, (n // ty) * ty - 1, (n // ty) * ty, n - 1} - {n})
+    ys = {0, n - 1}
+    for t in ([ty] if isinstance(ty, int) else ty):
+        ys |= {t - 1, t, 2 * t - 1, 2 * t, (n // t) * t - 1, (n // t) * t}
+    ys = sorted(ys - {n})
     zs = sorted({0, n // 2 - 1, n // 2, n // 4, n - 1})
     grid = [(z, y, x) for z in zs for y in ys for x in xs]
     pick = rng.choice(len(grid), size=min(count - 16, len(grid)), replace=False)
@@ -606,7 +609,8 @@ def test_full_size_256cubed_fp32_dopri5_sampled(fusion):
     gs.gs_set_dopri5_fusion(g.ctx, fusion)  # the tuned launch shapes of either path
     g.step(gs.GS_DOPRI5, 0.0, 0.5, 3)
     gu, gv = to_np(g.u), to_np(g.v)
-    ty = gs.gs_get_pair_configs(g.ctx)[2][0] if fusion else gs.gs_get_stage_configs(g.ctx)[6][1]
+    # the tile heights of all three pair kernels (2+3 and 4+5 may run 16-warp tiles)
+    ty = [c[0] for c in gs.gs_get_pair_configs(g.ctx)[:3]] if fusion else gs.gs_get_stage_configs(g.ctx)[6][1]
     centers = _seam_centers(n, ty, np.random.default_rng(0))
     assert len(centers) == 64
     oracle.set_threads(oracle.max_threads())
