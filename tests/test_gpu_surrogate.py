@@ -430,3 +430,68 @@ def test_timeout_mark_makes_every_call_fail():
         assert L.sur_debug_set_timeout_word(None, 0) == 0
     assert L.sur_conv3d(*args) == 0
     torch.cuda.synchronize()
+
+
+# more tiles than SMs: the persistent tcgen05 kernels then run several tiles
+# per CTA (halo buffers and accumulator sets reused, the next halo copied
+# while a tile's MMAs and epilogue run)
+MULTI_TILE_GRID = (32, 64, 96)  # 384 tiles of 8 x 16 x 4 for the forward kernel
+
+
+@pytest.mark.parametrize("cin,cout,epi", [(32, 32, 3), (2, 32, 0), (32, 2, 1)])
+def test_conv_forward_tcgen05_several_tiles_per_cta(tc_engine, cin, cout, epi):
+    torch, gs = tc_engine
+    D, H, W = MULTI_TILE_GRID
+    rng = np.random.default_rng(211 + 7 * cin + cout + epi)
+    x = _rand_bf16(rng, (D, H, W, cin))
+    w = _rand_bf16(rng, (27, cin, cout), 0.2)
+    b = rng.standard_normal(cout).astype(np.float32).astype(np.float64)
+    cip, cop = _pad(cin), _pad(cout)
+    xd = _dev_act(torch, x, cip)
+    wp, _ = _packed(torch, gs, w, 0)
+    bd = torch.zeros(cop, dtype=torch.float32, device="cuda")
+    bd[:cout] = torch.from_numpy(b.astype(np.float32))
+    if epi == 0:
+        out = torch.zeros((D, H, W, cop), dtype=torch.bfloat16, device="cuda")
+    elif epi == 1:
+        out = torch.zeros((D, H, W, cout), dtype=torch.float32, device="cuda")
+    else:
+        out = torch.zeros((D, H, W, cop), dtype=torch.float32, device="cuda")
+    before = _tc_timeouts(gs)
+    assert gs.lib().sur_conv3d(D, H, W, cip, cop, xd.data_ptr(), wp.data_ptr(), bd.data_ptr(), epi, None,
+                               out.data_ptr(), cout if epi == 1 else cop, None) == 0
+    torch.cuda.synchronize()
+    assert gs.lib().sur_conv_last_engine() == 2
+    assert _tc_timeouts(gs) == before
+    ref = oracle.conv3d_fwd(x, w, b)
+    got = to_np(out)
+    if epi in (1, 3):
+        assert _rel(got[..., :cout], ref) < ACC_TOL
+        # every cell, not only the pooled norm: one wrong tile would show here
+        assert np.max(np.abs(got[..., :cout] - ref)) <= ACC_TOL * np.max(np.abs(ref))
+    else:
+        refr = np.maximum(ref, 0.0)
+        assert np.all(np.abs(got[..., :cout] - refr) <= 2.0 ** -8 * np.abs(refr) + 1e-6 * np.max(np.abs(refr)))
+
+
+def test_conv_weight_gradient_tcgen05_several_tiles_per_cta(tc_engine):
+    """The weight gradient accumulates all of a CTA's one-plane tiles in TMEM
+    before writing its partial: 16 x 32 x 64 has 256 tiles (one or two per
+    CTA)."""
+    torch, gs = tc_engine
+    D, H, W = 16, 32, 64
+    rng = np.random.default_rng(307)
+    x = _rand_bf16(rng, (D, H, W, 32))
+    dy = _rand_bf16(rng, (D, H, W, 32))
+    xd, dyd = _dev_act(torch, x, 32), _dev_act(torch, dy, 32)
+    nb = gs.lib().sur_wgrad_workspace_bytes(32, 32)
+    ws = torch.empty(nb, dtype=torch.uint8, device="cuda")
+    dw = torch.zeros((27, 32, 32), dtype=torch.float32, device="cuda")
+    before = _tc_timeouts(gs)
+    assert gs.lib().sur_conv3d_wgrad(D, H, W, 32, 32, xd.data_ptr(), dyd.data_ptr(), 32, 32, dw.data_ptr(),
+                                     ws.data_ptr(), nb, None) == 0
+    torch.cuda.synchronize()
+    assert gs.lib().sur_conv_last_engine() == 2
+    assert _tc_timeouts(gs) == before
+    ref, _ = oracle.conv3d_wgrad(x, dy)
+    assert _rel(to_np(dw), ref) < ACC_TOL
