@@ -136,6 +136,32 @@ def test_tile_shape_does_not_change_results(dims, L, tile, variant):
         assert np.array_equal(res[0][0], r[0]) and np.array_equal(res[0][1], r[1])
 
 
+def test_pairs_more_columns_than_ctas_bit_identical():
+    """More tile columns than resident CTAs (256 x 160 x 8 FP64 at tile height
+    2: 4 x 80 columns): the pair kernels then take linear shares of the
+    (column, z) space, several partial columns per CTA, instead of the
+    column-split schedule; FP64 results are bit-identical to a run whose
+    columns fit the GPU (heights 7 and 11), for Dormand-Prince and RK4."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (256, 160, 8)
+    u0, v0 = si.gs_initial_state(*dims, seed=71)
+    res = []
+    for cfg in ([(2, 1)] * 5, [(11, 2), (11, 1), (7, 1), (11, 2), (11, 1)]):
+        g = _gs(torch, dims, gs.GS_FP64, u0, v0, Du=2e-5, Dv=1e-5)
+        gs.gs_set_small_grid_path(g.ctx, 0)
+        gs.gs_set_dopri5_fusion(g.ctx, 1)
+        for pi, (ty, d) in enumerate(cfg):
+            gs.gs_set_pair_config(g.ctx, pi, ty, d)
+        g.step(gs.GS_DOPRI5, 0.0, 0.2, 2)
+        g.step(gs.GS_RK4, 0.4, 0.2, 2)
+        res.append((to_np(g.u), to_np(g.v)))
+        g.close()
+    assert np.all(np.isfinite(res[0][0])) and np.all(np.isfinite(res[0][1]))
+    assert not np.array_equal(res[0][0], u0)
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims", [(64, 20, 12), (132, 23, 9), (136, 8, 5), (8, 1, 1)])
 @pytest.mark.parametrize("ty,depth", [(11, 3), (8, 1), (10, 2)])
@@ -354,6 +380,30 @@ def test_pairs_per_pair_configs_and_timing():
         g.close()
     for r in res[1:]:
         assert np.array_equal(res[0][0], r[0]) and np.array_equal(res[0][1], r[1])
+
+
+def test_pairs_more_columns_than_ctas_bit_identical():
+    """More tile columns than resident CTAs (256 x 160 x 8 FP64 at tile height
+    2: 4 x 80 columns): the pair kernels then take linear shares of the
+    (column, z) space, several partial columns per CTA, instead of the
+    column-split schedule; FP64 results are bit-identical to a run whose
+    columns fit the GPU (heights 7 and 11), for Dormand-Prince and RK4."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    dims = (256, 160, 8)
+    u0, v0 = si.gs_initial_state(*dims, seed=71)
+    res = []
+    for cfg in ([(2, 1)] * 5, [(11, 2), (11, 1), (7, 1), (11, 2), (11, 1)]):
+        g = _gs(torch, dims, gs.GS_FP64, u0, v0, Du=2e-5, Dv=1e-5)
+        gs.gs_set_small_grid_path(g.ctx, 0)
+        gs.gs_set_dopri5_fusion(g.ctx, 1)
+        for pi, (ty, d) in enumerate(cfg):
+            gs.gs_set_pair_config(g.ctx, pi, ty, d)
+        g.step(gs.GS_DOPRI5, 0.0, 0.2, 2)
+        g.step(gs.GS_RK4, 0.4, 0.2, 2)
+        res.append((to_np(g.u), to_np(g.v)))
+        g.close()
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
 
 
 @pytest.mark.parametrize("prec", [0, 1])
