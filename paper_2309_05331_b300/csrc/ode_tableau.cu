@@ -200,6 +200,39 @@ __global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __rest
 // in either order.
 constexpr long long kMaxElementAttempts = 1LL << 22;
 
+template <int K>
+__device__ __forceinline__ double ipow_pos(double y) {  // y^K, K in 1..8, by multiplication
+    const double y2 = y * y, y4 = y2 * y2;
+    if (K == 1) return y;
+    if (K == 2) return y2;
+    if (K == 3) return y2 * y;
+    if (K == 4) return y4;
+    if (K == 5) return y4 * y;
+    if (K == 6) return y4 * y2;
+    if (K == 7) return y4 * y2 * y;
+    return y4 * y4;
+}
+
+// The controller's power x^(-1/K), K = KR (a rejection) or KG (growth)
+// chosen per lane: an FP32 estimate, then two Newton steps on f(y) = y^-K -
+// x in FP64, y <- y ((K + 1) - x y^K) / K, each of which squares the
+// relative error (FP32's ~1e-7 -> ~1e-14 -> rounding): a few ulps from the
+// exact power, in a small fraction of the FP64 operations of pow.  x > 0
+// and finite; beyond FP32's range (a rejection with E > 3e38) the result
+// is 0, where the rejection factor is clamped to 0.2 anyway.
+template <int KR, int KG>
+__device__ __forceinline__ double ctrl_power(double x, bool rej) {
+    const double kp1 = rej ? (double)(KR + 1) : (double)(KG + 1);
+    const double rk = rej ? 1.0 / (double)KR : 1.0 / (double)KG;
+    double y = (double)powf((float)x, rej ? -1.0f / (float)KR : -1.0f / (float)KG);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double yk = rej ? ipow_pos<KR>(y) : ipow_pos<KG>(y);
+        y = y * fma(-x, yk, kp1) * rk;
+    }
+    return y;
+}
+
 template <int KIND, class TB>
 __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double* __restrict__ x,
                                                              const double* __restrict__ coef, double t0,
@@ -259,12 +292,11 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                     st = GS_ERR_NONFINITE;
                     fin = true;
                 } else {
-                    // one pow for the rejecting and the accepting lanes
+                    // one power for the rejecting and the accepting lanes
                     // alike (its arguments selected per lane), so a warp
-                    // holding both does not run the power twice
+                    // holding both does not run it twice
                     const bool rej = E > 1.0;
-                    const double pw = pow(rej ? E : fmax(E, grow_floor),
-                                          rej ? -1.0 / (double)(TB::Q - 1) : -1.0 / (double)TB::P);
+                    const double pw = ctrl_power<TB::Q - 1, TB::P>(rej ? E : fmax(E, grow_floor), rej);
                     if (rej) {
                         ++nr;
                         ++consec;
