@@ -486,7 +486,12 @@ gs_status ode_integrate_const(ode_rhs rhs, gs_method method, long n, double* x_d
  * stages and steps of an element in registers, one kernel.  coef: device
  * array of n coefficients c_i, required for ODE_PAPER_EXP, else ignored
  * (may be NULL).  INVALID: unknown kind or method, n < 0, nsteps < 0,
- * non-finite t0 or dt, coef missing for ODE_PAPER_EXP.  Enqueued on stream. */
+ * non-finite t0 or dt, coef missing for ODE_PAPER_EXP.  Enqueued on stream.
+ * ODE_PAPER_EXP / ODE_PAPER_SIGMOID depend on the element only through a
+ * factor of t shared by all elements, so the call first tabulates that
+ * factor at every stage time (a stream-ordered temporary allocation of 8
+ * bytes per step and stage, freed on the stream after the kernel);
+ * GS_ERR_CUDA if it cannot be allocated. */
 gs_status ode_integrate_tableau(ode_rhs rhs, ode_tableau method, long n, double* x_dev,
                                 const double* coef_dev, double t0, double dt, long nsteps,
                                 void* stream);
@@ -497,7 +502,8 @@ gs_status ode_integrate_tableau(ode_rhs rhs, ode_tableau method, long n, double*
  * call are one-step steps of order >= steps (RK4 for steps <= 4, the order-8
  * Fehlberg solution for 5..8), so the start-up does not limit the order; the
  * history lives in registers.  Same arguments and errors as
- * ode_integrate_tableau.  Enqueued on stream. */
+ * ode_integrate_tableau (the time-factor table: one value per step, plus the
+ * start-up steps' stage times).  Enqueued on stream. */
 gs_status ode_integrate_ab_steps(ode_rhs rhs, int steps, long n, double* x_dev, const double* coef_dev,
                                  double t0, double dt, long nsteps, void* stream);
 

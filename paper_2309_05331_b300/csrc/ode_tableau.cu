@@ -54,20 +54,64 @@ __host__ __device__ constexpr double ab_weight(int s, int j) {
          : s == 5 ? n5[j] / 720 : s == 6 ? n6[j] / 1440 : s == 7 ? n7[j] / 60480 : n8[j] / 120960;
 }
 
+// The paper's two families depend on x only through a factor of t shared
+// by every element: Eq. 1a f = c e^t (g(t) = e^t), Eq. 1b f = s (1 - s),
+// s = 1 / (1 + e^-t) (g(t) = f).
+template <int KIND>
+__host__ __device__ constexpr bool time_only() {
+    return KIND == ODE_PAPER_EXP || KIND == ODE_PAPER_SIGMOID;
+}
+template <int KIND>
+__device__ __forceinline__ double gtime(double t) {
+    if (KIND == ODE_PAPER_EXP) return exp(t);
+    const double s = 1.0 / (1.0 + exp(-t));
+    return s * (1.0 - s);
+}
+// f from g(t) (time_only kinds)
+template <int KIND>
+__device__ __forceinline__ double frhs_g(double g, double cf) {
+    return KIND == ODE_PAPER_EXP ? cf * g : g;
+}
+
 // f(t, x) of each family; cf: the element's coefficient (Eq. 1a)
 template <int KIND>
 __device__ __forceinline__ double frhs(double t, double x, double cf) {
     if (KIND == ODE_EXP_DECAY) return -x;
     if (KIND == ODE_LOGISTIC) return x * (1.0 - x);
-    if (KIND == ODE_PAPER_EXP) return cf * exp(t);
-    const double s = 1.0 / (1.0 + exp(-t));
-    return s * (1.0 - s);
+    return frhs_g<KIND>(gtime<KIND>(t), cf);
 }
+
+// Fixed steps of the time_only kinds evaluate g at the same times for every
+// element, so a call first tabulates them: G[m S + i] = g(t_m + c_i dt),
+// t_m = t0 + (mlo + m) dt, m < nm, for the S nodes c of tableau TB (S = 1,
+// c = 0: the step times).  Times are rounded as the oracle rounds them (the
+// product, then the sum); the kernels then read G (one cached load shared by
+// a warp) instead of evaluating exponentials per element.
+template <int KIND, class TB>
+__global__ void __launch_bounds__(256) ode_gtable_kernel(double t0, double dt, long long mlo, long long nm,
+                                                         double* __restrict__ G) {
+    const long long total = nm * TB::S;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long m = idx / TB::S;
+        const int i = (int)(idx - m * TB::S);
+        const double tm = __dadd_rn(t0, __dmul_rn((double)(mlo + m), dt));
+        G[idx] = gtime<KIND>(__dadd_rn(tm, __dmul_rn(TB::c(i), dt)));
+    }
+}
+// the step times alone (one node, c = 0)
+struct TabNode0 {
+    static constexpr int S = 1;
+    __host__ __device__ static constexpr double c(int) { return 0.0; }
+};
 
 // One step of tableau TB: returns the propagated solution; with ERR also
 // err = h sum_i (B_i - BH_i) k_i and k1 (for the error scale).
+// G: with a table (time_only kinds, fixed steps), g at this step's S stage
+// times, else null (g evaluated here)
 template <int KIND, class TB, bool ERR>
-__device__ __forceinline__ double tab_step(double u, double t, double h, double cf, double& err, double& k1) {
+__device__ __forceinline__ double tab_step(double u, double t, double h, double cf, double& err, double& k1,
+                                           const double* __restrict__ G = nullptr) {
     double k[TB::S];
 #pragma unroll
     for (int i = 0; i < TB::S; ++i) {
@@ -75,7 +119,10 @@ __device__ __forceinline__ double tab_step(double u, double t, double h, double 
 #pragma unroll
         for (int j = 0; j < i; ++j)
             if (TB::a(i, j) != 0.0) acc += TB::a(i, j) * k[j];
-        k[i] = frhs<KIND>(t + TB::c(i) * h, i == 0 ? u : u + h * acc, cf);
+        if (time_only<KIND>() && G)
+            k[i] = frhs_g<KIND>(__ldg(G + i), cf);
+        else
+            k[i] = frhs<KIND>(t + TB::c(i) * h, i == 0 ? u : u + h * acc, cf);
     }
     double acc = 0.0;
 #pragma unroll
@@ -92,16 +139,18 @@ __device__ __forceinline__ double tab_step(double u, double t, double h, double 
     return u + h * acc;
 }
 
+// G: the time_only kinds' table of g at every stage time (nsteps x TB::S)
 template <int KIND, class TB>
 __global__ void __launch_bounds__(256) ode_tab_kernel(long long n, double* __restrict__ x,
                                                       const double* __restrict__ coef, double t0, double dt,
-                                                      long long nsteps) {
+                                                      long long nsteps, const double* __restrict__ G) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double u = x[i];
         const double cf = KIND == ODE_PAPER_EXP ? coef[i] : 0.0;
         double e, k1;
-        for (long long m = 0; m < nsteps; ++m) u = tab_step<KIND, TB, false>(u, t0 + (double)m * dt, dt, cf, e, k1);
+        for (long long m = 0; m < nsteps; ++m)
+            u = tab_step<KIND, TB, false>(u, t0 + (double)m * dt, dt, cf, e, k1, G ? G + m * TB::S : nullptr);
         x[i] = u;
     }
 }
@@ -115,10 +164,13 @@ struct AmWeights {
 // Adams-Bashforth-Moulton with S steps in PECE form: f[j] = f_{m-j} in
 // registers; predictor u* = u + dt sum_j ab_j f_{m-j}, f* = f(t_{m+1}, u*),
 // corrector u' = u + dt (am_0 f* + sum_{j>=1} am_j f_{m+1-j}).
+// Gm, Gs (time_only kinds): g at the step times t_0..t_nsteps and at the
+// start-up steps' stage times ((S - 1) x Start::S), else null
 template <int KIND, int S>
 __global__ void __launch_bounds__(256) ode_abm_kernel(long long n, double* __restrict__ x,
                                                       const double* __restrict__ coef, double t0, double dt,
-                                                      long long nsteps, const AmWeights am) {
+                                                      long long nsteps, const AmWeights am,
+                                                      const double* __restrict__ Gm, const double* __restrict__ Gs) {
     using Start = typename std::conditional<(S <= 4), TabRK4, TabRKF78>::type;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -132,14 +184,16 @@ __global__ void __launch_bounds__(256) ode_abm_kernel(long long n, double* __res
             const double t = t0 + (double)m * dt;
 #pragma unroll
             for (int j = S - 1; j >= 1; --j) f[j] = f[j - 1];
-            f[0] = frhs<KIND>(t, u, cf);
+            f[0] = (time_only<KIND>() && Gm) ? frhs_g<KIND>(__ldg(Gm + m), cf) : frhs<KIND>(t, u, cf);
             if (m < S - 1) {
-                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1);
+                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1, Gs ? Gs + m * Start::S : nullptr);
             } else {
                 double acc = 0.0;
 #pragma unroll
                 for (int j = 0; j < S; ++j) acc += ab_weight(S, j) * f[j];
-                const double fp = frhs<KIND>(t0 + (double)(m + 1) * dt, u + dt * acc, cf);
+                const double fp = (time_only<KIND>() && Gm)
+                                      ? frhs_g<KIND>(__ldg(Gm + m + 1), cf)
+                                      : frhs<KIND>(t0 + (double)(m + 1) * dt, u + dt * acc, cf);
                 double cor = am.w[0] * fp;
 #pragma unroll
                 for (int j = 1; j < S; ++j) cor += am.w[j] * f[j - 1];
@@ -151,10 +205,12 @@ __global__ void __launch_bounds__(256) ode_abm_kernel(long long n, double* __res
 }
 
 // Adams-Bashforth with S steps: f[j] = f_{m-j} in registers.
+// Gm, Gs: as for ode_abm_kernel
 template <int KIND, int S>
 __global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __restrict__ x,
                                                      const double* __restrict__ coef, double t0, double dt,
-                                                     long long nsteps) {
+                                                     long long nsteps, const double* __restrict__ Gm,
+                                                     const double* __restrict__ Gs) {
     using Start = typename std::conditional<(S <= 4), TabRK4, TabRKF78>::type;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -168,9 +224,9 @@ __global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __rest
             const double t = t0 + (double)m * dt;
 #pragma unroll
             for (int j = S - 1; j >= 1; --j) f[j] = f[j - 1];
-            f[0] = frhs<KIND>(t, u, cf);
+            f[0] = (time_only<KIND>() && Gm) ? frhs_g<KIND>(__ldg(Gm + m), cf) : frhs<KIND>(t, u, cf);
             if (m < S - 1) {
-                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1);
+                u = tab_step<KIND, Start, false>(u, t, dt, cf, e, k1, Gs ? Gs + m * Start::S : nullptr);
             } else {
                 double acc = 0.0;
 #pragma unroll
@@ -370,13 +426,39 @@ cudaError_t by_tab(int method, int kind, Args... args) {
     }
 }
 
+// Stream-ordered table of g for a time_only kind (null for the others):
+// nm x TB::S values from step mlo; released with cudaFreeAsync after use.
+template <int KIND, class TB>
+cudaError_t make_gtable(cudaStream_t s, double t0, double dt, long long mlo, long long nm, double** out) {
+    *out = nullptr;
+    if (!time_only<KIND>() || nm <= 0) return cudaSuccess;
+    const long long total = nm * TB::S;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(out), sizeof(double) * (size_t)total, s);
+    if (e != cudaSuccess) {
+        *out = nullptr;
+        return e;
+    }
+    const int grid = (int)std::min<long long>((total + 255) / 256, 4096);
+    ode_gtable_kernel<KIND, TB><<<grid, 256, 0, s>>>(t0, dt, mlo, nm, *out);
+    return cudaGetLastError();
+}
+void free_gtable(cudaStream_t s, double* G) {
+    if (G) cudaFreeAsync(G, s);
+}
+
 template <int KIND, class TB>
 struct LaunchTab {
     static cudaError_t run(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
                            long long nsteps) {
-        auto k = ode_tab_kernel<KIND, TB>;
-        k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps);
-        return cudaGetLastError();
+        double* G = nullptr;
+        cudaError_t e = make_gtable<KIND, TB>(s, t0, dt, 0, nsteps, &G);
+        if (e == cudaSuccess) {
+            auto k = ode_tab_kernel<KIND, TB>;
+            k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps, G);
+            e = cudaGetLastError();
+        }
+        free_gtable(s, G);
+        return e;
     }
 };
 template <int KIND, class TB>
@@ -391,12 +473,30 @@ struct LaunchEach {
     }
 };
 
+// the tables of the multistep kernels: g at t_0..t_nsteps and at the
+// start-up steps' stage times
+template <int KIND, int S>
+cudaError_t make_ms_tables(cudaStream_t s, double t0, double dt, long long nsteps, double** Gm, double** Gs) {
+    using Start = typename std::conditional<(S <= 4), TabRK4, TabRKF78>::type;
+    *Gs = nullptr;
+    cudaError_t e = make_gtable<KIND, TabNode0>(s, t0, dt, 0, nsteps + 1, Gm);
+    if (e == cudaSuccess) e = make_gtable<KIND, Start>(s, t0, dt, 0, std::min<long long>(S - 1, nsteps), Gs);
+    return e;
+}
+
 template <int KIND, int S>
 cudaError_t launch_ab(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
                       long long nsteps) {
-    auto k = ode_ab_kernel<KIND, S>;
-    k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps);
-    return cudaGetLastError();
+    double *Gm = nullptr, *Gs = nullptr;
+    cudaError_t e = make_ms_tables<KIND, S>(s, t0, dt, nsteps, &Gm, &Gs);
+    if (e == cudaSuccess) {
+        auto k = ode_ab_kernel<KIND, S>;
+        k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps, Gm, Gs);
+        e = cudaGetLastError();
+    }
+    free_gtable(s, Gm);
+    free_gtable(s, Gs);
+    return e;
 }
 template <int KIND>
 cudaError_t launch_ab_k(int steps, cudaStream_t s, long long n, double* x, const double* coef, double t0,
@@ -456,9 +556,16 @@ AmWeights am_weights(int s) {
 template <int KIND, int S>
 cudaError_t launch_abm(cudaStream_t s, long long n, double* x, const double* coef, double t0, double dt,
                        long long nsteps) {
-    auto k = ode_abm_kernel<KIND, S>;
-    k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps, am_weights(S));
-    return cudaGetLastError();
+    double *Gm = nullptr, *Gs = nullptr;
+    cudaError_t e = make_ms_tables<KIND, S>(s, t0, dt, nsteps, &Gm, &Gs);
+    if (e == cudaSuccess) {
+        auto k = ode_abm_kernel<KIND, S>;
+        k<<<grid_for(k, n), 256, 0, s>>>(n, x, coef, t0, dt, nsteps, am_weights(S), Gm, Gs);
+        e = cudaGetLastError();
+    }
+    free_gtable(s, Gm);
+    free_gtable(s, Gs);
+    return e;
 }
 template <int KIND>
 cudaError_t launch_abm_k(int steps, cudaStream_t s, long long n, double* x, const double* coef, double t0,
