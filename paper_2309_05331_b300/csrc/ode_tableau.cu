@@ -350,9 +350,12 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                 } else {
                     // one power for the rejecting and the accepting lanes
                     // alike (its arguments selected per lane), so a warp
-                    // holding both does not run it twice
+                    // holding both does not run it twice; none when every
+                    // lane keeps its step (0.5 <= E <= 1, the steady state)
                     const bool rej = E > 1.0;
-                    const double pw = ctrl_power<TB::Q - 1, TB::P>(rej ? E : fmax(E, grow_floor), rej);
+                    double pw = 1.0;
+                    if (__any_sync(__activemask(), rej || E < 0.5))
+                        pw = ctrl_power<TB::Q - 1, TB::P>(rej ? E : fmax(E, grow_floor), rej);
                     if (rej) {
                         ++nr;
                         ++consec;
