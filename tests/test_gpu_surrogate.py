@@ -495,3 +495,47 @@ def test_conv_weight_gradient_tcgen05_several_tiles_per_cta(tc_engine):
     assert _tc_timeouts(gs) == before
     ref, _ = oracle.conv3d_wgrad(x, dy)
     assert _rel(to_np(dw), ref) < ACC_TOL
+
+
+def test_network_forward_128cubed_sampled_cones(tc_engine):
+    """The bench's size (128^3, the tcgen05 convolutions with ~28 tiles per
+    CTA): the GPU network forward against the oracle's on the dependence
+    cone of 40 sampled cells (radius 4: four 3^3 layers), cells on the
+    periodic seams and on the tiles' x, y and z boundaries among them."""
+    torch, gs = tc_engine
+    from tests._gpu_common import periodic_box
+    n = 128
+    params = si.surrogate_init_params(seed=5, last_layer_scale=0.5)
+    u, v = _state((n, n, n), 9)
+    u, v = u.astype(np.float32).astype(np.float64), v.astype(np.float32).astype(np.float64)
+    mean, sd, scale = _norm()
+    s = gs.Surrogate(n, n, n)
+    s.set_params(params)
+    s.set_normalization(mean, sd, scale)
+    du, dv = torch.from_numpy(u.astype(np.float32)).cuda(), torch.from_numpy(v.astype(np.float32)).cuda()
+    uo, vo = torch.empty_like(du), torch.empty_like(dv)
+    before = _tc_timeouts(gs)
+    s.forward(du, dv, uo, vo)
+    torch.cuda.synchronize()
+    assert _tc_timeouts(gs) == before
+    gu, gv = to_np(uo), to_np(vo)
+    s.close()
+    rng = np.random.default_rng(17)
+    seams = [(0, 0, 0), (127, 127, 127), (3, 15, 7), (4, 16, 8), (63, 64, 120), (64, 63, 121), (100, 31, 64),
+             (127, 0, 63), (0, 127, 64), (32, 48, 7)]
+    centers = seams + [tuple(int(a) for a in rng.integers(0, n, 3)) for _ in range(30)]
+    r = 4
+    got, ref = [], []
+    for c in centers:
+        bu, bv = periodic_box(u, c, r), periodic_box(v, c, r)
+        pu, pv = oracle.surrogate_forward(params.astype(np.float64), bu, bv, mean, sd, scale)
+        ref.append([pu[r, r, r] - u[c], pv[r, r, r] - v[c]])
+        got.append([gu[c] - u[c], gv[c] - v[c]])
+    got, ref = np.array(got), np.array(ref)
+    # BF16 hidden activations: a sum that lands on a rounding boundary may
+    # round the other way on one side, so the bound is the network's
+    # end-to-end tolerance (1e-3 of the update's scale), per cell
+    for comp in range(2):
+        scale_c = np.max(np.abs(ref[:, comp]))
+        assert scale_c > 0
+        assert np.max(np.abs(got[:, comp] - ref[:, comp])) <= 2e-3 * scale_c, comp
