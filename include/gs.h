@@ -528,7 +528,10 @@ gs_status ode_integrate_abm_steps(ode_rhs rhs, int steps, long n, double* x_dev,
  * shrinks dt = h max(0.9 E^(-1/(q-1)), 0.2); else accept, and if E < 0.5
  * grow dt = 0.9 h max(E, 5^-p)^(-1/p) (p, q = propagated / embedded order:
  * 5, 4 for Dormand-Prince and Cash-Karp, 8, 7 for Fehlberg); the last step
- * is clipped to t_end.  An element stops at t_end, after max_acc accepted
+ * is clipped to t_end.  The powers E^(-1/k) are computed to a few ulps (an
+ * FP32 estimate refined by two FP64 Newton steps), not by the correctly
+ * rounded pow: step sizes can differ from a pow-based controller in the
+ * last bits.  An element stops at t_end, after max_acc accepted
  * steps (< 0: no limit), after max_rej consecutive rejections or a step that
  * no longer advances t (GS_ERR_STEP_UNDERFLOW), on a non-finite error
  * (GS_ERR_NONFINITE) or after 2^22 attempts (GS_ERR_MAX_STEPS).  Optional
