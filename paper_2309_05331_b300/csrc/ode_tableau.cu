@@ -255,6 +255,9 @@ __global__ void __launch_bounds__(256) ode_ab_kernel(long long n, double* __rest
 // of whichever element each lane holds.  An element's arithmetic is the same
 // in either order.
 constexpr long long kMaxElementAttempts = 1LL << 22;
+// bit patterns of 1.0, 0.5 and 0.2 (IEEE binary64)
+constexpr long long kBits1 = 0x3FF0000000000000LL, kBitsHalf = 0x3FE0000000000000LL,
+                    kBitsFifth = 0x3FC999999999999ALL;
 
 template <int K>
 __device__ __forceinline__ double ipow_pos(double y) {  // y^K, K in 1..8, by multiplication
@@ -344,7 +347,11 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                 double err, k1;
                 const double y = tab_step<KIND, TB, true>(u, t, h, cf, err, k1);
                 const double E = fabs(err) / (atol + rtol * (fabs(u) + h * fabs(k1)));
-                if (!isfinite(E)) {
+                // E >= 0 (or NaN): the tests and maxima below compare its bit
+                // pattern as an integer, which orders non-negative doubles as
+                // their values, and leave the FP64 pipe to the arithmetic
+                const long long eb = __double_as_longlong(E);
+                if (((eb >> 52) & 0x7ff) == 0x7ff) {  // not finite
                     st = GS_ERR_NONFINITE;
                     fin = true;
                 } else {
@@ -352,14 +359,17 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                     // alike (its arguments selected per lane), so a warp
                     // holding both does not run it twice; none when every
                     // lane keeps its step (0.5 <= E <= 1, the steady state)
-                    const bool rej = E > 1.0;
+                    const bool rej = eb > kBits1;   // E > 1
+                    const bool grow = eb < kBitsHalf;  // E < 0.5
                     double pw = 1.0;
-                    if (__any_sync(__activemask(), rej || E < 0.5))
-                        pw = ctrl_power<TB::Q - 1, TB::P>(rej ? E : fmax(E, grow_floor), rej);
+                    if (__any_sync(__activemask(), rej || grow))
+                        pw = ctrl_power<TB::Q - 1, TB::P>(
+                            rej ? E : __longlong_as_double(max(eb, __double_as_longlong(grow_floor))), rej);
                     if (rej) {
                         ++nr;
                         ++consec;
-                        dt = h * fmax(0.9 * pw, 0.2);
+                        // max(0.9 pw, 0.2), pw >= 0
+                        dt = h * __longlong_as_double(max(__double_as_longlong(0.9 * pw), kBitsFifth));
                         if (consec >= max_rej) {
                             st = GS_ERR_STEP_UNDERFLOW;
                             fin = true;
@@ -369,7 +379,7 @@ __global__ void __launch_bounds__(256) ode_adapt_each_kernel(long long n, double
                         u = y;
                         ++na;
                         t = last ? t_end : t + h;
-                        dt = E < 0.5 ? h * 0.9 * pw : h;
+                        dt = grow ? h * 0.9 * pw : h;
                     }
                 }
             }
