@@ -53,10 +53,12 @@ STAGE_FIELDS = [2, 3, 4, 5, 6, 7, 8]
 # the scale and writes k7
 STAGE_FIELDS_SPLIT = [2, 3, 4, 5, 6, 9, 4]
 # with the stages in pairs (one launch each): stages 2+3 read u, k1 and write
-# k2, k3; stages 4+5 read u, k1..k3 and write k4, k5; stages 6+7 read u,
-# k1..k5 and write y5 and k7 (the error norm is reduced, not stored)
+# k2, k3 and the inverse error scale; stages 4+5 read u, k1..k3 and write
+# stage 6's input Y6, P (y5 without its k6 term) and the error terms through
+# k5; stages 6+7 read those four fields and write y5 and k7 (the error norm
+# is reduced, not stored)
 PAIR_NAMES = ["k1", "stages2+3", "stages4+5", "stages6+7"]
-PAIR_FIELDS = [2, 4, 6, 8]
+PAIR_FIELDS = [2, 5, 7, 6]
 BYTES_PER_FIELD_CELL = 8
 BATCH_BYTES_PER_CELL_ATTEMPT = 33 * BYTES_PER_FIELD_CELL  # batched path: single-stage schedule, FP32
 BATCH_PAIR_BYTES_PER_CELL_ATTEMPT = 18 * BYTES_PER_FIELD_CELL  # batched path: stage pairs, FP32

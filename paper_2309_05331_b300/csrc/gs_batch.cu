@@ -60,11 +60,11 @@ struct BSeg {
     int inst, col, z0, z1;
 };
 
-constexpr int kBFields = 8;    // 0: second state buffer; 1..7: stage fields
+constexpr int kBFields = 9;    // 0: second state buffer; 1..8: stage fields
 constexpr int kStageCtrs = 6;  // segment counters per group: stages 2..7 (counter 0: the k1 stage)
 // working set of a cell in units of the element size: state and second
 // buffer, k1..k7, two components each
-constexpr int kCellFields = 2 * 9;
+constexpr int kCellFields = 2 * (1 + kBFields);
 
 // FP32: registers capped for 4 CTAs of 256 threads per SM (stage kernels,
 // 64) or 3 (the final kernel, 85): the segment code prefetches a plane of
@@ -118,9 +118,10 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256,
     }
 }
 
-// One Dormand-Prince stage pair of every running instance (MODE_PAIR_STAGE:
-// stages 2+3 with NK = 1, 4+5 with NK = 3; MODE_PAIR_DOPRI67: stages 6+7,
-// y5, k7 and the instance's error maximum): CTAs take (instance, column of
+// One Dormand-Prince stage pair of every running instance (MODE_PAIR_DOPRI23:
+// stages 2+3 and the inverse error scale; MODE_PAIR_DOPRI45: stages 4+5 ->
+// stage 6's fields;
+// MODE_PAIR_DOPRI67: stages 6+7, y5, k7 and the instance's error maximum): CTAs take (instance, column of
 // A.ty rows x 32 cells, run of planes) segments from the counter and run the
 // pair segment with one cell per lane.
 // Tile heights of the batch's pair segments: up to 7 rows in a CTA compiled
@@ -465,13 +466,14 @@ static cudaError_t bpair_launch(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A
     return bpair_launch_t<float, NK, MODE>(ctx, s, A, group, counter);
 }
 
-// Dormand-Prince stage pair pi (0: stages 2+3, 1: 4+5, 2: 6+7 -> y5, k7 and
-// the error maxima) of instance group g: the buffers and coefficients of the
-// single-grid pairs
+// Dormand-Prince stage pair pi (0: stages 2+3 and the inverse error scale ->
+// field 8, 1: 4+5 -> Y6, P and the error terms in fields 5..7, 2: 6+7 from
+// fields 5..8 -> y5, k7 and the error maxima) of instance group g: the
+// buffers and coefficients of the single-grid pairs
 static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int g) {
     const int ctr = 1 + kStageCtrs * g + pi;
     const Slot k1 = bpair(ctx, 1, 2, SEL_CUR);
-    const Slot k[6] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4), bfld(ctx, 5), bfld(ctx, 6)};  // k[i] = k_i
+    const Slot k[4] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4)};  // k[i] = k_i
     StageArgs A;
     memset(&A, 0, sizeof(A));
     A.u = bstate(ctx, SEL_CUR);
@@ -483,7 +485,8 @@ static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int
         A.bk[1] = dp5::A32;
         A.out0 = k[2];
         A.out1 = k[3];
-        return bpair_launch<1, MODE_PAIR_STAGE>(ctx, s, A, g, ctr);
+        A.out2 = bfld(ctx, 8);  // inverse error scale
+        return bpair_launch<1, MODE_PAIR_DOPRI23>(ctx, s, A, g, ctr);
     }
     if (pi == 1) {
         static const double a4[3] = {dp5::A41, dp5::A42, dp5::A43};
@@ -493,18 +496,18 @@ static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int
             A.a[j] = a4[j];
         }
         for (int j = 0; j < 4; ++j) A.bk[j] = a5[j];
-        A.out0 = k[4];
-        A.out1 = k[5];
-        return bpair_launch<3, MODE_PAIR_STAGE>(ctx, s, A, g, ctr);
+        A.out0 = bfld(ctx, 5);  // Y6
+        A.out1 = bfld(ctx, 6);  // P
+        A.out2 = bfld(ctx, 7);  // error terms through k5
+        return bpair_launch<3, MODE_PAIR_DOPRI45>(ctx, s, A, g, ctr);
     }
-    static const double a6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
-    for (int j = 0; j < 5; ++j) {
-        A.kin[j] = k[j + 1];
-        A.a[j] = a6[j];
-    }
+    A.u = bfld(ctx, 5);
+    A.kin[0] = bfld(ctx, 6);
+    A.kin[1] = bfld(ctx, 7);
+    A.kin[2] = bfld(ctx, 8);
     A.out0 = bstate(ctx, SEL_NEXT);       // y5
     A.out1 = bpair(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
-    return bpair_launch<5, MODE_PAIR_DOPRI67>(ctx, s, A, g, ctr);
+    return bpair_launch<3, MODE_PAIR_DOPRI67>(ctx, s, A, g, ctr);
 }
 
 static cudaError_t bbody(gsb_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond, bool with_ctrl) {

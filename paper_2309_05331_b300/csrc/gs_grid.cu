@@ -255,7 +255,7 @@ static cudaError_t launch_pair(gs_ctx* ctx, cudaStream_t s, StageArgs A, int dep
     const Geom<T> g = make_geom<T>(ctx->p);
     if (A.ty < 1 || A.ty > pair_max_ty(MODE)) return cudaErrorInvalidConfiguration;
     auto kern = gs_pair_kernel<T, NK, MODE, VX, false>;
-    if constexpr (MODE != MODE_PAIR_DOPRI67)
+    if constexpr (MODE != MODE_PAIR_DOPRI45)
         if (A.ty > kPairMaxTY) kern = gs_pair_kernel<T, NK, MODE, VX, true>;
     const int txw = 32 * VX;
     A.ntx = (ctx->p.nx + txw - 1) / txw;
@@ -571,11 +571,14 @@ static cudaError_t launch_dopri5_stage(gs_ctx* ctx, cudaStream_t s, int st, unsi
     return launch_stage(ctx, s, 5, MODE_DOPRI_FINAL, A, cfg);
 }
 
-// Dormand-Prince stage pair pi (0: stages 2, 3; 1: stages 4, 5; 2: stages 6,
-// 7 with y5 -> next state, k7 -> next k1, the error norm and the controller)
+// Dormand-Prince stage pair pi (0: stages 2, 3 and the inverse error scale
+// -> field 8; 1: stages 4, 5 -> stage 6's input Y6, P = y5 without its k6
+// term and the error terms through k5 in fields 5..7; 2: stages 6, 7 from
+// fields 5..8 with y5 -> next state, k7 -> next k1, the error norm and the
+// controller)
 static cudaError_t launch_dopri5_pair(gs_ctx* ctx, cudaStream_t s, int pi, unsigned long long h, int use_cond) {
     const Slot k1 = pair_sel(ctx, 1, 2, SEL_CUR);
-    const Slot k[6] = {k1, k1, fld(ctx, 3), fld(ctx, 4), fld(ctx, 5), fld(ctx, 6)};  // k[i] = k_i
+    const Slot k[4] = {k1, k1, fld(ctx, 3), fld(ctx, 4)};  // k[i] = k_i
     const KCfg& cfg = ctx->pc[pi];
     StageArgs A = base_args(ctx, cfg);
     A.u = state_sel(ctx, SEL_CUR);
@@ -587,7 +590,8 @@ static cudaError_t launch_dopri5_pair(gs_ctx* ctx, cudaStream_t s, int pi, unsig
         A.bk[1] = dp5::A32;
         A.out0 = k[2];
         A.out1 = k[3];
-        return launch_pair_nk<1, MODE_PAIR_STAGE>(ctx, s, A, cfg);
+        A.out2 = fld(ctx, 8);  // inverse error scale
+        return launch_pair_nk<1, MODE_PAIR_DOPRI23>(ctx, s, A, cfg);
     }
     if (pi == 1) {
         static const double a4[3] = {dp5::A41, dp5::A42, dp5::A43};
@@ -597,21 +601,21 @@ static cudaError_t launch_dopri5_pair(gs_ctx* ctx, cudaStream_t s, int pi, unsig
             A.a[j] = a4[j];
         }
         for (int j = 0; j < 4; ++j) A.bk[j] = a5[j];
-        A.out0 = k[4];
-        A.out1 = k[5];
-        return launch_pair_nk<3, MODE_PAIR_STAGE>(ctx, s, A, cfg);
+        A.out0 = fld(ctx, 5);  // Y6
+        A.out1 = fld(ctx, 6);  // P
+        A.out2 = fld(ctx, 7);  // error terms through k5
+        return launch_pair_nk<3, MODE_PAIR_DOPRI45>(ctx, s, A, cfg);
     }
-    static const double a6[5] = {dp5::A61, dp5::A62, dp5::A63, dp5::A64, dp5::A65};
-    for (int j = 0; j < 5; ++j) {
-        A.kin[j] = k[j + 1];
-        A.a[j] = a6[j];
-    }
+    A.u = fld(ctx, 5);
+    A.kin[0] = fld(ctx, 6);
+    A.kin[1] = fld(ctx, 7);
+    A.kin[2] = fld(ctx, 8);
     A.out0 = state_sel(ctx, SEL_NEXT);       // y5
     A.out1 = pair_sel(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
     A.run_ctrl = 1;
     A.cond = h;
     A.use_cond = use_cond;
-    return launch_pair_nk<5, MODE_PAIR_DOPRI67>(ctx, s, A, cfg);
+    return launch_pair_nk<3, MODE_PAIR_DOPRI67>(ctx, s, A, cfg);
 }
 
 static cudaError_t body_dopri5(gs_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond) {
@@ -1664,7 +1668,13 @@ int gs_get_dopri5_fusion(const gs_ctx* ctx) { return ctx && pairs_on(ctx) ? 1 : 
 // the launch mode of pair kernel pi (0..2: Dormand-Prince 2+3, 4+5, 6+7;
 // 3, 4: RK4 1+2, 3+4)
 static int pair_mode(int pi) {
-    return pi == 2 ? MODE_PAIR_DOPRI67 : (pi == 4 ? MODE_PAIR_RK4 : MODE_PAIR_STAGE);
+    switch (pi) {
+        case 0: return MODE_PAIR_DOPRI23;
+        case 1: return MODE_PAIR_DOPRI45;
+        case 2: return MODE_PAIR_DOPRI67;
+        case 4: return MODE_PAIR_RK4;
+        default: return MODE_PAIR_STAGE;
+    }
 }
 
 gs_status gs_set_pair_config(gs_ctx* ctx, int pair, int ty, int depth) {
@@ -1700,14 +1710,14 @@ gs_status gs_get_pair_depths_in_use(const gs_ctx* ctx, int* depth) {
             depth[pi] = f64 ? pair_depth_fit<double, 2, MODE_PAIR_RK4>(ty, d)
                             : pair_depth_fit<float, 2, MODE_PAIR_RK4>(ty, d);
         else if (pi == 0)
-            depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_STAGE>(ty, d)
-                            : pair_depth_fit<float, 1, MODE_PAIR_STAGE>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 1, MODE_PAIR_DOPRI23>(ty, d)
+                            : pair_depth_fit<float, 1, MODE_PAIR_DOPRI23>(ty, d);
         else if (pi == 1)
-            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_STAGE>(ty, d)
-                            : pair_depth_fit<float, 3, MODE_PAIR_STAGE>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_DOPRI45>(ty, d)
+                            : pair_depth_fit<float, 3, MODE_PAIR_DOPRI45>(ty, d);
         else
-            depth[pi] = f64 ? pair_depth_fit<double, 5, MODE_PAIR_DOPRI67>(ty, d)
-                            : pair_depth_fit<float, 5, MODE_PAIR_DOPRI67>(ty, d);
+            depth[pi] = f64 ? pair_depth_fit<double, 3, MODE_PAIR_DOPRI67>(ty, d)
+                            : pair_depth_fit<float, 3, MODE_PAIR_DOPRI67>(ty, d);
     }
     return GS_OK;
 }

@@ -80,15 +80,19 @@ int gs_get_dopri5_split(const gs_ctx* ctx);
  * stages 2+3, 4+5 and 6+7 each run as ONE launch that computes the first
  * stage's k on the tile plus a one-cell ring (recomputed by neighbouring
  * tiles) and the second stage from it, so k2, k4 and k6 are never read back
- * and k6 is never stored: an attempt moves 18 field passes instead of 31.
- * Stages 6+7 write y5 (the next state) and k7 (the next k1), reduce the
- * scaled error norm and run the controller.  Requires the staged form (x
+ * and k6 is never stored.  Stages 2+3 also write the inverse error scale;
+ * stages 4+5 write, instead of k4 and k5, stage 6's input Y6, y5 without
+ * its k6 term and the error terms through k5 (the only combinations of k4
+ * and k5 the later stages use); stages 6+7 read those and the scale, write y5 (the next state) and
+ * k7 (the next k1), reduce the scaled error norm and run the controller: an
+ * attempt moves 18 field passes instead of 31.  Requires the staged form (x
  * extent a multiple of the vector width); any ny, nz.  mode: -1 automatic
  * (on when the staged form applies and no other kernel form is forced;
  * gs_autotune keeps it on only if the pairs' summed kernel time beats the
  * single stages'), 0 off, 1 on (INVALID if the staged form does not apply).
  * The stage formulas are those of the single stages; Y_{i+1} is summed as
- * (u + dt sum_{j<i} a_{i+1,j} k_j) + dt a_{i+1,i} k_i.
+ * (u + dt sum_{j<i} a_{i+1,j} k_j) + dt a_{i+1,i} k_i, and Y6, y5 and the
+ * error terms as (the k1..k3 part) + dt (w4 k4 + w5 k5) + dt w6 k6 + ...
  * gs_get_dopri5_fusion: 1 if the pairs are in use. */
 gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode);
 int gs_get_dopri5_fusion(const gs_ctx* ctx);
@@ -102,7 +106,7 @@ int gs_get_dopri5_fusion(const gs_ctx* ctx);
 int gs_get_rk4_fusion(const gs_ctx* ctx);
 /* Launch shape of pair kernel `pair` (0: Dormand-Prince stages 2+3, 1: 4+5,
  * 2: 6+7; 3: RK4 stages 1+2, 4: RK4 stages 3+4 with the update; -1: all
- * five): tile height ty (1..7 rows, 1..11 except for stages 6+7: the CTA
+ * five): tile height ty (1..7 rows, 1..11 except for stages 4+5: the CTA
  * has ty + 5 warps, compiled for 12 warps up to 7 rows and for 16 above; -1
  * with ty > 7 is rejected) and input ring
  * depth (1..3 planes; cut back at launch to what shared memory holds).
@@ -141,7 +145,7 @@ gs_status gsb_set_tile(gsb_ctx* ctx, int ty, int zc);
  * group of consecutive instances at a time, so a group's stage fields are
  * re-read from L2 instead of HBM.  cells_per_group: the group budget (a
  * group holds at least one instance); -1 = half the L2 over the working set
- * of a cell (state and stage fields, 18 values); 0 (the default) = one group
+ * of a cell (state and stage fields, 20 values); 0 (the default) = one group
  * (every stage over all instances).  gsb_get_grouping: the budget in
  * use and the number of groups.  gsb_autotune also chooses the grouping. */
 gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group);

@@ -10,10 +10,19 @@
 // and reading it back with a halo in a second launch: the pair reads u and
 // k_1..k_{i-1} once and writes k_i and k_{i+1}, i + 3 field passes instead
 // of 2i + 3.  Dormand-Prince stages 6 and 7 fuse the same way: stage 7's
-// input is y5 = u + dt sum_j b_j k_j (b7 = 0), so that pair reads u, k1..k5,
-// writes y5 and k7 (the next k1) and reduces the scaled error norm, with
-// the arithmetic of the split stages 6/7 (gs_staged.cuh): 8 field passes
-// instead of 13.  RK4 runs as two pairs: k1, k2 from u (stage 1 is F(u)),
+// input is y5 = u + dt sum_j b_j k_j (b7 = 0).  Nothing after stage 7 needs
+// k4 or k5 themselves, only their pointwise combinations, so the 4+5 pair
+// writes, instead of k4 and k5, the three fields stage 6 onwards uses at a
+// cell: Y6 = u + dt sum_{j<=5} a_6j k_j, P = u + dt sum_{j<=5} b_j k_j (y5
+// without its k6 term) and the error terms through k5; the 2+3 pair, which
+// reads u and k1, also writes the inverse error scale 1 / (atol + rtol (|u|
+// + dt |k1|)).  The 6+7 pair reads those four fields (Y6 on every row of the
+// tile's two-cell ring, P on the one-cell ring, the other two on the tile),
+// writes y5 and k7 (the next k1) and reduces the scaled error norm.  An
+// attempt still moves 18 field passes (stages 2+3: 5, 4+5: 7, 6+7: 6), but
+// the six-array formation of Y6 and P, which the halo rows of the 6+7 tiles
+// would repeat, runs once per cell in the 4+5 pair's tile rows.  RK4
+// runs as two pairs: k1, k2 from u (stage 1 is F(u)),
 // then k3, k4 and the update u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) from u,
 // k1, k2 without storing k3 or k4: 7 field passes per step instead of 13.
 //
@@ -51,8 +60,9 @@ namespace gsk {
 // Tile heights: up to 7 rows in a CTA of 12 warps (3 per SM sub-partition,
 // 168 registers per thread), 8..11 rows in a "tall" CTA of 16 warps (4 per
 // sub-partition, 128 registers) for the pairs whose state fits that budget
-// (not Dormand-Prince stages 6+7).  The halo warp covers at most 16 rows
-// (two lanes per row for ty + 4 rows).
+// and whose per-row shared memory allows it (not Dormand-Prince stages
+// 4+5).  The halo warp covers at most 16 rows (two lanes per row for ty + 4
+// rows).
 constexpr int kPairMaxTY = 7;
 constexpr int kPairMaxTYTall = 11;
 template <bool TALL>
@@ -60,7 +70,7 @@ __host__ __device__ constexpr int pair_threads() {
     return 32 * ((TALL ? kPairMaxTYTall : kPairMaxTY) + 5);
 }
 __host__ __device__ constexpr int pair_max_ty(int mode) {
-    return mode == MODE_PAIR_DOPRI67 ? kPairMaxTY : kPairMaxTYTall;
+    return mode == MODE_PAIR_DOPRI45 ? kPairMaxTY : kPairMaxTYTall;
 }
 
 
@@ -92,12 +102,18 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
     const size_t halo = (size_t)NA * 32 * 2 * sizeof(T);
     return (vec + halo + 127) / 128 * 128;
 }
-// Dormand-Prince pair: the inverse error scale of the tile rows' cells for
-// the three planes between A and C (thread-private, 3 x 2 components)
-// (RK4 stages 3+4: the partial update u + dt (k1/6 + k2/3) between A and B)
+// Values the tile rows' threads keep from phase A to phase C in shared
+// memory (thread-private, 3 planes x fields x 2 components): Dormand-Prince
+// stages 6+7 the inverse error scale; stages 4+5 the parts of Y6, P and the
+// error terms formed from u and k1..k3; RK4 stages 3+4 the partial update
+// u + dt (k1/6 + k2/3).
+template <int MODE>
+__host__ __device__ constexpr int pair_stash_fields() {
+    return MODE == MODE_PAIR_DOPRI45 ? 3 : ((MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? 1 : 0);
+}
 template <typename T, int MODE, int VX>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
-    return (MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? (size_t)3 * 2 * ty * 32 * VX * sizeof(T) : 0;
+    return (size_t)pair_stash_fields<MODE>() * 3 * 2 * ty * 32 * VX * sizeof(T);
 }
 // the input ring starts at a 128-byte boundary of the shared window (+ 128
 // bytes of room for that): a warp's 512 contiguous bytes of a slot then
@@ -152,8 +168,13 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     constexpr int OFF = pair_off<T>();
     constexpr int NA = 2 * (1 + NK);
     constexpr bool DP = MODE == MODE_PAIR_DOPRI67;
+    constexpr bool D45 = MODE == MODE_PAIR_DOPRI45;
+    constexpr bool D23 = MODE == MODE_PAIR_DOPRI23;
     constexpr bool RK = MODE == MODE_PAIR_RK4;
-    static_assert(!DP || NK == 5, "Dormand-Prince stages 6/7 take k1..k5");
+    constexpr int NS = pair_stash_fields<MODE>();
+    static_assert(!DP || NK == 3, "Dormand-Prince stages 6/7 take Y6, P, the error terms and the inverse scale");
+    static_assert(!D45 || NK == 3, "Dormand-Prince stages 4/5 take k1..k3");
+    static_assert(!D23 || NK == 1, "Dormand-Prince stages 2/3 take k1");
     static_assert(!RK || NK == 2, "RK4 stages 3/4 take k1, k2");
     using VTy = typename VecT<T, VX>::type;
     using V2 = typename VecT<T, 2>::type;
@@ -163,13 +184,14 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     const int nx = g.nx, ny = g.ny, nz = g.nz;
     const long long plane = (long long)nx * ny;
     const T dt = C.dt;
-    // weight of k_i in Y_{i+1} (Dormand-Prince: y5 = ... + dt b6 k6) and the
-    // split stage-6/7 error constants
+    // weight of k_i in Y_{i+1} (Dormand-Prince: y5 = P + dt b6 k6) and the
+    // stage-6/7 error constants
     const T dta2 = DP ? dt * (T)dp5::B6 : dt * C.a2[NK];
     const T dte6 = dt * (T)dp5::E6, dte7 = dt * (T)dp5::E7;
-    const T e67 = (T)(dp5::E6 + dp5::E7);
-    const T bw[4] = {(T)dp5::B1, (T)dp5::B3, (T)dp5::B4, (T)dp5::B5};
-    const T ew[3] = {(T)dp5::E3, (T)dp5::E4, (T)dp5::E5};
+    // stages 4+5: the k4, k5 weights of Y6, P and the error terms, times dt
+    const T d64 = dt * (T)dp5::A64, d65 = dt * (T)dp5::A65;
+    const T db4 = dt * (T)dp5::B4, db5 = dt * (T)dp5::B5;
+    const T de4 = dt * (T)dp5::E4, de5 = dt * (T)dp5::E5;
 
     const int x0 = tx * TXW, y0 = tyi * TY;
     const int aw = min(TXW, nx - x0);
@@ -198,10 +220,10 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     auto rvec = [&](int s, int a) -> VTy* {
         return reinterpret_cast<VTy*>(R + (size_t)s * slot_bytes) + ((size_t)w * NA + a) * 32 + lane;
     };
-    // this thread's inverse-scale vector of component c in plane buffer k
+    // this thread's stash vector of field f, component c in plane buffer k
     // (0..2); tile rows only
-    auto siv = [&](int k, int c) -> VTy* {
-        return reinterpret_cast<VTy*>(SI) + ((size_t)(k * 2 + c) * TY + r) * 32 + lane;
+    auto siv = [&](int k, int f, int c) -> VTy* {
+        return reinterpret_cast<VTy*>(SI) + ((size_t)((k * NS + f) * 2 + c) * TY + r) * 32 + lane;
     };
     auto rhal = [&](int s, int a) -> V2* {
         return reinterpret_cast<V2*>(R + (size_t)s * slot_bytes + vec_bytes) + (size_t)a * 32 + lane;
@@ -215,6 +237,9 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             for (int c = 0; c < 2; ++c) {
 #pragma unroll
                 for (int f = 0; f <= NK; ++f) {
+                    // stages 6+7: Y6 on every row, P on rows -1..ty, the
+                    // error terms and the inverse scale on the tile rows
+                    if (DP && f > 0 && !(f == 1 ? inB : inC)) continue;
                     const T* base = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]);
                     const T* src = base + cbase + zo;
                     if (hw && VX == 1) {
@@ -232,25 +257,37 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     };
 
     // Y_i of NV consecutive cells from the slot (ld(a, v) loads array a) and
-    // the second-stage partial P2 = u + dt sum_{j<i} a2_j k_j (Dormand-Prince:
-    // u + dt sum_{j=1,3,4,5} b_j k_j); with E (Dormand-Prince tile rows) also
-    // the error terms Q = dt (sum_{j=3,4,5} e_j (k_j - k1) - (e6 + e7) k1) and
-    // the inverse error scale I = 1 / (atol + rtol (|u| + dt |k1|)).  RK4
-    // stages 3+4 with E: I = u + dt (k1/6 + k2/3), the update so far.
-    auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I, auto E) {
+    // the second-stage partial P2 = u + dt sum_{j<i} a2_j k_j.  Dormand-Prince
+    // stages 6+7 load them (Y6 and P) and, with E (tile rows), the error terms
+    // Q and the inverse error scale I.  With E (tile rows), stages 4+5 also
+    // form the parts of stage 6's fields that u and k1..k3 give and stages
+    // 2+3 the inverse error scale, and hand them, one component at a time,
+    // to sink(c, S6, S7, Q, I): S6 = u + dt (a61 k1 + a62 k2 + a63 k3), S7 =
+    // u + dt (b1 k1 + b3 k3), Q = dt (e1 k1 + e3 k3) (b2 = e2 = 0); I = 1 /
+    // (atol + rtol (|u| + dt |k1|)).  RK4 stages 3+4 with E: I = u + dt
+    // (k1/6 + k2/3), the update so far.
+    auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I, auto E, auto&& sink) {
         constexpr int NV = sizeof(Y[0]) / sizeof(T);
         constexpr bool WE = DP && decltype(E)::value;
+        constexpr bool W45 = D45 && decltype(E)::value;
+        constexpr bool W23 = D23 && decltype(E)::value;
         constexpr bool WR = RK && decltype(E)::value;
 #pragma unroll
         for (int c = 0; c < 2; ++c) {
-            T uu[NV], s1[NV], s2[NV], k1v[NV], q[NV];
+            if (DP) {
+                ld(c * (1 + NK), Y[c]);
+                ld(c * (1 + NK) + 1, P2[c]);
+                if (WE) {
+                    ld(c * (1 + NK) + 2, Q[c]);
+                    ld(c * (1 + NK) + 3, I[c]);
+                }
+                continue;
+            }
+            T uu[NV], s1[NV], s2[NV], k1v[NV], q[NV], s6[NV], s7[NV];
             ld(c * (1 + NK), uu);
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                s1[v] = T(0);
-                s2[v] = T(0);
-                k1v[v] = T(0);
-                q[v] = T(0);
+                s1[v] = s2[v] = k1v[v] = q[v] = s6[v] = s7[v] = T(0);
             }
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
@@ -259,15 +296,21 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     s1[v] = (j == 0) ? C.a1[0] * kk[v] : s1[v] + C.a1[j] * kk[v];
+                    s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
                     if (WR) q[v] = (j == 0) ? C.rb[0] * kk[v] : q[v] + C.rb[j] * kk[v];
-                    if (!DP) {
-                        s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
-                    } else if (j == 0) {
-                        k1v[v] = kk[v];
-                        s2[v] = bw[0] * kk[v];
-                    } else if (j >= 2) {
-                        s2[v] += bw[j - 1] * kk[v];
-                        if (WE) q[v] += ew[j - 2] * (kk[v] - k1v[v]);
+                    if (W23 && j == 0) k1v[v] = kk[v];
+                    if (W45) {
+                        if (j == 0) {
+                            s6[v] = (T)dp5::A61 * kk[v];
+                            s7[v] = (T)dp5::B1 * kk[v];
+                            q[v] = (T)dp5::E1 * kk[v];
+                        } else if (j == 1) {
+                            s6[v] += (T)dp5::A62 * kk[v];
+                        } else {
+                            s6[v] += (T)dp5::A63 * kk[v];
+                            s7[v] += (T)dp5::B3 * kk[v];
+                            q[v] += (T)dp5::E3 * kk[v];
+                        }
                     }
                 }
             }
@@ -275,18 +318,51 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             for (int v = 0; v < NV; ++v) {
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s1[v];
                 P2[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s2[v];
-                if (WE) {
-                    Q[c][v] = dt * (q[v] - e67 * k1v[v]);
-                    I[c][v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
+                if (W45) {
+                    s6[v] = uu[v] + dt * s6[v];
+                    s7[v] = uu[v] + dt * s7[v];
+                    q[v] = dt * q[v];
                 }
+                if (W23) k1v[v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
                 if (WR) I[c][v] = uu[v] + dt * q[v];
             }
+            if (W45 || W23) sink(c, s6, s7, q, k1v);
         }
     };
+    auto nosink = [](int, const T*, const T*, const T*, const T*) {};
     auto react = [&](T yu, T yv, T lu, T lv, T& fu, T& fv) {
         const T uvv = yu * yv * yv;
         fu = g.Du * lu - uvv + g.F * (T(1) - yu);
         fv = g.Dv * lv + uvv - (g.F + g.k) * yv;
+    };
+    // k = F(Y) (Eq. 2) at this thread's VX cells of a plane: centre Yc and
+    // upper z neighbour Yu in registers, the y neighbours and the lower z
+    // neighbour from plane buffer S (index function ix; bc: this plane's
+    // buffer, bz: the plane below), x neighbours across lanes (xl, xr: the
+    // shuffled values of the neighbouring lanes, read from S at the row's
+    // ends)
+    auto cell_rhs = [&](const T* S, auto&& ix, int bc, int bz, const T(&Yc)[2][VX], const T(&Yu)[2][VX], T xl[2],
+                        T xr[2], T(&f)[2][VX]) {
+        T lap[2][VX];
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            if (lane == 0) xl[c] = S[ix(bc, r, c, -1)];
+            if (lane == nl - 1) xr[c] = S[ix(bc, r, c, aw)];
+            T ys[VX], yn[VX], zm[VX];
+            lds_v<T, VX>(S + ix(bc, r - 1, c, col), ys);
+            lds_v<T, VX>(S + ix(bc, r + 1, c, col), yn);
+            lds_v<T, VX>(S + ix(bz, r, c, col), zm);
+#pragma unroll
+            for (int v = 0; v < VX; ++v) {
+                const T xm = (v == 0) ? xl[c] : Yc[c][v - 1];
+                const T xp = (v == VX - 1) ? xr[c] : Yc[c][v + 1];
+                const T yy = Yc[c][v];
+                lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
+                            (zm[v] - T(2) * yy + Yu[c][v]) * g.cz;
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < VX; ++v) react(Yc[0][v], Yc[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
     };
 
     for (int i = 0; i < depth; ++i) fetch(z0 - 2 + i, i);
@@ -323,24 +399,36 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         const T(&qC)[2][VX], T(&epN)[2][VX], const T(&epC)[2][VX]) {
             const bool doA = TILE || inA, doB = TILE ? act : (it >= 2 && inB), doC = TILE ? act : (it >= 4 && inC);
             // rows whose error terms (RK4: partial update) are needed
-            const bool wide = (DP || RK) && (TILE || inC);
+            const bool wide = (DP || D45 || D23 || RK) && (TILE || inC);
             const int q = z0 - 2 + it;
             const int b1 = b == 0 ? 2 : b - 1, b2 = b == 2 ? 0 : b + 1;  // planes q - 1 and q - 2
             // ---- A(q)
             cp_async_wait_pending(depth - 1);
             if (doA) {
                 auto ld = [&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(sA, a)), out); };
+                // tile rows: stages 4+5 S6, S7 and Q to the stash; stages
+                // 2+3 I straight to its field (no later phase needs it)
+                auto sink = [&](int c, const T* s6, const T* s7, const T* qa, const T* ic) {
+                    if (!(TILE ? act : true)) return;
+                    if (D45) {
+                        stv<T, VX>(reinterpret_cast<T*>(siv(b, 0, c)), s6);
+                        stv<T, VX>(reinterpret_cast<T*>(siv(b, 1, c)), s7);
+                        stv<T, VX>(reinterpret_cast<T*>(siv(b, 2, c)), qa);
+                    } else if (q >= z0 && q < z1) {
+                        stv<T, VX>(P.o2[c] + cbase + plane * q, ic);
+                    }
+                };
                 if (TILE)
-                    formA(ld, yaN, p2N, qN, isc, std::true_type{});
+                    formA(ld, yaN, p2N, qN, isc, std::true_type{}, sink);
                 else if (wide)
-                    formA(ld, yaN, p2N, qN, isc, std::true_type{});
+                    formA(ld, yaN, p2N, qN, isc, std::true_type{}, sink);
                 else
-                    formA(ld, yaN, p2N, qN, isc, std::false_type{});
+                    formA(ld, yaN, p2N, qN, isc, std::false_type{}, nosink);
                 if (TILE ? act : true) {
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
                         stv<T, VX>(SA + ia(b, r, c, col), yaN[c]);
-                        if (wide) stv<T, VX>(reinterpret_cast<T*>(siv(b, c)), isc[c]);
+                        if (wide && !D45 && NS > 0) stv<T, VX>(reinterpret_cast<T*>(siv(b, 0, c)), isc[c]);
                     }
                 }
             }
@@ -355,33 +443,14 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     xr[c] = __shfl_down_sync(0xffffffffu, yaC[c][0], 1);
                 }
                 if (doB) {
-                    T lap[2][VX];
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (lane == 0) xl[c] = SA[ia(b1, r, c, -1)];
-                        if (lane == nl - 1) xr[c] = SA[ia(b1, r, c, aw)];
-                        T ys[VX], yn[VX], zm[VX];
-                        lds_v<T, VX>(SA + ia(b1, r - 1, c, col), ys);
-                        lds_v<T, VX>(SA + ia(b1, r + 1, c, col), yn);
-                        lds_v<T, VX>(SA + ia(b2, r, c, col), zm);
-#pragma unroll
-                        for (int v = 0; v < VX; ++v) {
-                            const T xm = (v == 0) ? xl[c] : yaC[c][v - 1];
-                            const T xp = (v == VX - 1) ? xr[c] : yaC[c][v + 1];
-                            const T yy = yaC[c][v];
-                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
-                                        (zm[v] - T(2) * yy + yaN[c][v]) * g.cz;
-                        }
-                    }
                     T f[2][VX];
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) react(yaC[0][v], yaC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    cell_rhs(SA, ia, b1, b2, yaC, yaN, xl, xr, f);
                     const bool own = TILE ? p < z1 : (r >= 0 && r < ah && p >= z0 && p < z1);
                     const long long gi = cbase + plane * p;
                     T tu[2][VX] = {};  // RK4: the partial update of plane p (tile rows)
                     if (RK && (TILE || (r >= 0 && r < ah))) {
 #pragma unroll
-                        for (int c = 0; c < 2; ++c) lds_v<T, VX>(reinterpret_cast<const T*>(siv(b1, c)), tu[c]);
+                        for (int c = 0; c < 2; ++c) lds_v<T, VX>(reinterpret_cast<const T*>(siv(b1, 0, c)), tu[c]);
                     }
 #pragma unroll
                     for (int c = 0; c < 2; ++c)
@@ -389,9 +458,10 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         for (int v = 0; v < VX; ++v) {
                             ybN[c][v] = p2C[c][v] + dta2 * f[c][v];
                             if (DP) epN[c][v] = qC[c][v] + dte6 * f[c][v];
+                            if (D45) epN[c][v] = f[c][v];  // k4, to phase C
                             if (RK) epN[c][v] = tu[c][v] + dt * C.rb[2] * f[c][v];
                         }
-                    if (own && !RK) {
+                    if (own && !RK && !D45) {
 #pragma unroll
                         for (int c = 0; c < 2; ++c) stv<T, VX>(P.o0[c] + gi, DP ? ybN[c] : f[c]);
                     }
@@ -409,27 +479,8 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                     xr[c] = __shfl_down_sync(0xffffffffu, ybC[c][0], 1);
                 }
                 if (doC) {
-                    T lap[2][VX];
-#pragma unroll
-                    for (int c = 0; c < 2; ++c) {
-                        if (lane == 0) xl[c] = SB[ib(b1, r, c, -1)];
-                        if (lane == nl - 1) xr[c] = SB[ib(b1, r, c, aw)];
-                        T ys[VX], yn[VX], zm[VX];
-                        lds_v<T, VX>(SB + ib(b1, r - 1, c, col), ys);
-                        lds_v<T, VX>(SB + ib(b1, r + 1, c, col), yn);
-                        lds_v<T, VX>(SB + ib(b2, r, c, col), zm);
-#pragma unroll
-                        for (int v = 0; v < VX; ++v) {
-                            const T xm = (v == 0) ? xl[c] : ybC[c][v - 1];
-                            const T xp = (v == VX - 1) ? xr[c] : ybC[c][v + 1];
-                            const T yy = ybC[c][v];
-                            lap[c][v] = (xm - T(2) * yy + xp) * g.cx + (ys[v] - T(2) * yy + yn[v]) * g.cy +
-                                        (zm[v] - T(2) * yy + ybN[c][v]) * g.cz;
-                        }
-                    }
                     T f[2][VX];
-#pragma unroll
-                    for (int v = 0; v < VX; ++v) react(ybC[0][v], ybC[1][v], lap[0][v], lap[1][v], f[0][v], f[1][v]);
+                    cell_rhs(SB, ib, b1, b2, ybC, ybN, xl, xr, f);
                     const long long gi = cbase + plane * o;
 #pragma unroll
                     for (int c = 0; c < 2; ++c) {
@@ -438,12 +489,29 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 #pragma unroll
                             for (int v = 0; v < VX; ++v) un[v] = epC[c][v] + dt * C.rb[3] * f[c][v];
                             stv<T, VX>(P.o0[c] + gi, un);
+                        } else if (D45) {
+                            // stage 6's fields: the stashed parts plus the
+                            // k4 (epC) and k5 (f) terms
+                            T s6[VX], s7[VX], qa[VX];
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 0, c)), s6);  // plane q - 2
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 1, c)), s7);
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 2, c)), qa);
+#pragma unroll
+                            for (int v = 0; v < VX; ++v) {
+                                const T k4 = epC[c][v], k5 = f[c][v];
+                                s6[v] = d65 * k5 + (d64 * k4 + s6[v]);
+                                s7[v] = db5 * k5 + (db4 * k4 + s7[v]);
+                                qa[v] = de5 * k5 + (de4 * k4 + qa[v]);
+                            }
+                            stv<T, VX>(P.o0[c] + gi, s6);
+                            stv<T, VX>(P.o1[c] + gi, s7);
+                            stv<T, VX>(P.o2[c] + gi, qa);
                         } else {
                             stv<T, VX>(P.o1[c] + gi, f[c]);
                         }
                         if (DP) {
                             T sc[VX];
-                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, c)), sc);  // plane q - 2
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 0, c)), sc);  // plane q - 2
 #pragma unroll
                             for (int v = 0; v < VX; ++v) {
                                 const T err = epC[c][v] + dte7 * f[c][v];
@@ -498,7 +566,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         out[0] = reinterpret_cast<const T*>(&q2)[0];
                         out[1] = reinterpret_cast<const T*>(&q2)[1];
                     },
-                    Y, P2, Qd, Id, std::false_type{});
+                    Y, P2, Qd, Id, std::false_type{}, nosink);
 #pragma unroll
                 for (int c = 0; c < 2; ++c) {
                     if (VX == 1) {  // the pair's column may be odd

@@ -35,9 +35,13 @@ namespace gsk {
 // differently (staged form only): stage 6 also forms y5 (b7 = 0, so y5 needs
 // k1..k6 only), the error terms of k1..k6 and the inverse error scale, and
 // never stores k6; stage 7 evaluates k7 = F(y5) and adds its error term.
-// MODE_PAIR_STAGE / MODE_PAIR_DOPRI67 / MODE_PAIR_RK4: two consecutive
-// stages in one launch (gs_pair.cuh): stages i and i+1; Dormand-Prince stages
-// 6 and 7 with y5, k7 and the error norm; RK4 stages 3 and 4 with the update.
+// MODE_PAIR_STAGE / MODE_PAIR_DOPRI23 / MODE_PAIR_DOPRI45 /
+// MODE_PAIR_DOPRI67 / MODE_PAIR_RK4: two consecutive stages in one launch
+// (gs_pair.cuh): stages i and i+1; Dormand-Prince stages 2 and 3 that also
+// write the inverse error scale; stages 4 and 5 writing stage 6's input, the
+// partial y5 and the error terms through k5 instead of k4 and k5; stages 6
+// and 7 from those fields with y5, k7 and the error norm; RK4 stages 3 and 4
+// with the update.
 enum StageMode : int {
     MODE_STAGE = 0,
     MODE_FINAL = 1,
@@ -46,7 +50,9 @@ enum StageMode : int {
     MODE_DOPRI_S7 = 4,
     MODE_PAIR_STAGE = 5,
     MODE_PAIR_DOPRI67 = 6,
-    MODE_PAIR_RK4 = 7
+    MODE_PAIR_RK4 = 7,
+    MODE_PAIR_DOPRI45 = 8,
+    MODE_PAIR_DOPRI23 = 9
 };
 
 template <typename T>
@@ -71,7 +77,7 @@ struct StageArgs {
     double be[kMaxNE];
     double bf;
     Slot out0, out1;
-    Slot out2;              // MODE_DOPRI_S6: inverse error scale
+    Slot out2;              // MODE_DOPRI_S6, MODE_PAIR_DOPRI23: inverse error scale; MODE_PAIR_DOPRI45: error terms
     int n_ex;
     int has_out1;
     int ty, zc;             // tile shape

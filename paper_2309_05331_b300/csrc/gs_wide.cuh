@@ -139,7 +139,9 @@ __device__ __forceinline__ StagePtrs<T, NK> resolve_stage(const StageArgs& A, in
         for (int j = 0; j < NK; ++j) P.k[j][c] = resolve<T>(A.kin[j], c, parity, step) + off;
         P.o0[c] = resolve<T>(A.out0, c, parity, step) + off;
         P.o1[c] = (MODE != MODE_STAGE && A.has_out1) ? resolve<T>(A.out1, c, parity, step) + off : nullptr;
-        P.o2[c] = MODE == MODE_DOPRI_S6 ? resolve<T>(A.out2, c, parity, step) + off : nullptr;
+        P.o2[c] = (MODE == MODE_DOPRI_S6 || MODE == MODE_PAIR_DOPRI23 || MODE == MODE_PAIR_DOPRI45)
+                      ? resolve<T>(A.out2, c, parity, step) + off
+                      : nullptr;
 #pragma unroll
         for (int j = 0; j < kMaxNE; ++j)
             P.ex[j][c] = ((MODE == MODE_FINAL || MODE == MODE_DOPRI_S7) && j < A.n_ex)
