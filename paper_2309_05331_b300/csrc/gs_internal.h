@@ -91,8 +91,9 @@ int gs_get_dopri5_split(const gs_ctx* ctx);
  * gs_autotune keeps it on only if the pairs' summed kernel time beats the
  * single stages'), 0 off, 1 on (INVALID if the staged form does not apply).
  * The stage formulas are those of the single stages; Y_{i+1} is summed as
- * (u + dt sum_{j<i} a_{i+1,j} k_j) + dt a_{i+1,i} k_i, and Y6, y5 and the
- * error terms as (the k1..k3 part) + dt (w4 k4 + w5 k5) + dt w6 k6 + ...
+ * (u + dt sum_{j<i} a_{i+1,j} k_j) + dt a_{i+1,i} k_i; Y6 as u + ((the
+ * k1..k3 part) + dt a64 k4 + dt a65 k5), y5 likewise plus dt b6 k6, and the
+ * error terms as (the k1..k5 part) + dt e6 k6 + dt e7 k7.
  * gs_get_dopri5_fusion: 1 if the pairs are in use. */
 gs_status gs_set_dopri5_fusion(gs_ctx* ctx, int mode);
 int gs_get_dopri5_fusion(const gs_ctx* ctx);

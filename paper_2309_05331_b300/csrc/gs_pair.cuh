@@ -104,12 +104,12 @@ __host__ __device__ inline size_t pair_slot_bytes(int ty) {
 }
 // Values the tile rows' threads keep from phase A to phase C in shared
 // memory (thread-private, 3 planes x fields x 2 components): Dormand-Prince
-// stages 6+7 the inverse error scale; stages 4+5 the parts of Y6, P and the
-// error terms formed from u and k1..k3; RK4 stages 3+4 the partial update
-// u + dt (k1/6 + k2/3).
+// stages 6+7 the inverse error scale; stages 4+5 the k1..k3 parts of Y6 - u,
+// P - u and the error terms, and u (so that Y6 and P add u once, to the
+// whole small sum); RK4 stages 3+4 the partial update u + dt (k1/6 + k2/3).
 template <int MODE>
 __host__ __device__ constexpr int pair_stash_fields() {
-    return MODE == MODE_PAIR_DOPRI45 ? 3 : ((MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? 1 : 0);
+    return MODE == MODE_PAIR_DOPRI45 ? 4 : ((MODE == MODE_PAIR_DOPRI67 || MODE == MODE_PAIR_RK4) ? 1 : 0);
 }
 template <typename T, int MODE, int VX>
 __host__ __device__ inline size_t pair_isc_bytes(int ty) {
@@ -262,9 +262,9 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
     // Q and the inverse error scale I.  With E (tile rows), stages 4+5 also
     // form the parts of stage 6's fields that u and k1..k3 give and stages
     // 2+3 the inverse error scale, and hand them, one component at a time,
-    // to sink(c, S6, S7, Q, I): S6 = u + dt (a61 k1 + a62 k2 + a63 k3), S7 =
-    // u + dt (b1 k1 + b3 k3), Q = dt (e1 k1 + e3 k3) (b2 = e2 = 0); I = 1 /
-    // (atol + rtol (|u| + dt |k1|)).  RK4 stages 3+4 with E: I = u + dt
+    // to sink(c, S6, S7, Q, X): S6 = dt (a61 k1 + a62 k2 + a63 k3), S7 = dt
+    // (b1 k1 + b3 k3), Q = dt (e1 k1 + e3 k3) (b2 = e2 = 0) and X = u; X = I
+    // = 1 / (atol + rtol (|u| + dt |k1|)).  RK4 stages 3+4 with E: I = u + dt
     // (k1/6 + k2/3), the update so far.
     auto formA = [&](auto&& ld, auto& Y, auto& P2, auto& Q, auto& I, auto E, auto&& sink) {
         constexpr int NV = sizeof(Y[0]) / sizeof(T);
@@ -319,14 +319,15 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s1[v];
                 P2[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s2[v];
                 if (W45) {
-                    s6[v] = uu[v] + dt * s6[v];
-                    s7[v] = uu[v] + dt * s7[v];
+                    s6[v] = dt * s6[v];
+                    s7[v] = dt * s7[v];
                     q[v] = dt * q[v];
                 }
                 if (W23) k1v[v] = ErrBits<T>::recip(C.ta + C.tr * (fabs(uu[v]) + dt * fabs(k1v[v])));
                 if (WR) I[c][v] = uu[v] + dt * q[v];
             }
-            if (W45 || W23) sink(c, s6, s7, q, k1v);
+            if (W45) sink(c, s6, s7, q, uu);
+            if (W23) sink(c, s6, s7, q, k1v);
         }
     };
     auto nosink = [](int, const T*, const T*, const T*, const T*) {};
@@ -406,14 +407,15 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             cp_async_wait_pending(depth - 1);
             if (doA) {
                 auto ld = [&](int a, T* out) { lds_v<T, VX>(reinterpret_cast<const T*>(rvec(sA, a)), out); };
-                // tile rows: stages 4+5 S6, S7 and Q to the stash; stages
-                // 2+3 I straight to its field (no later phase needs it)
+                // tile rows: stages 4+5 S6, S7, Q and u to the stash;
+                // stages 2+3 I straight to its field (no later phase needs it)
                 auto sink = [&](int c, const T* s6, const T* s7, const T* qa, const T* ic) {
                     if (!(TILE ? act : true)) return;
                     if (D45) {
                         stv<T, VX>(reinterpret_cast<T*>(siv(b, 0, c)), s6);
                         stv<T, VX>(reinterpret_cast<T*>(siv(b, 1, c)), s7);
                         stv<T, VX>(reinterpret_cast<T*>(siv(b, 2, c)), qa);
+                        stv<T, VX>(reinterpret_cast<T*>(siv(b, 3, c)), ic);
                     } else if (q >= z0 && q < z1) {
                         stv<T, VX>(P.o2[c] + cbase + plane * q, ic);
                     }
@@ -492,15 +494,16 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
                         } else if (D45) {
                             // stage 6's fields: the stashed parts plus the
                             // k4 (epC) and k5 (f) terms
-                            T s6[VX], s7[VX], qa[VX];
+                            T s6[VX], s7[VX], qa[VX], uo[VX];
                             lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 0, c)), s6);  // plane q - 2
                             lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 1, c)), s7);
                             lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 2, c)), qa);
+                            lds_v<T, VX>(reinterpret_cast<const T*>(siv(b2, 3, c)), uo);
 #pragma unroll
                             for (int v = 0; v < VX; ++v) {
                                 const T k4 = epC[c][v], k5 = f[c][v];
-                                s6[v] = d65 * k5 + (d64 * k4 + s6[v]);
-                                s7[v] = db5 * k5 + (db4 * k4 + s7[v]);
+                                s6[v] = uo[v] + (d65 * k5 + (d64 * k4 + s6[v]));
+                                s7[v] = uo[v] + (db5 * k5 + (db4 * k4 + s7[v]));
                                 qa[v] = de5 * k5 + (de4 * k4 + qa[v]);
                             }
                             stv<T, VX>(P.o0[c] + gi, s6);
