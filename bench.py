@@ -65,12 +65,12 @@ BATCH_PAIR_BYTES_PER_CELL_ATTEMPT = 18 * BYTES_PER_FIELD_CELL  # batched path: s
 NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside the measured copy peak)
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
-# stages 6+7 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 832.7 MB read + 248.3 MB written), per cell so that other grids scale by
+# stages 4+5 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
+# 554.4 MB read + 365.9 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages6+7", "path": "pairs", "source_sha": "0d15f12579af01ed",
-               "bytes_per_cell": (832662016 + 248261120) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages4+5", "path": "pairs", "source_sha": "cce42abadfb2dc82",
+               "bytes_per_cell": (554367232 + 365880320) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
