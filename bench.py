@@ -533,6 +533,7 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
     tile = b.autotune_run(1e-6, 1e-6, 0.0, t_end, 0.1)  # tile and pairs: timed on this integration (state restored)
     groups = b.grouping()
     pairs = b.pairs()
+    lanes = b.pair_lanes()
     stream = torch.cuda.current_stream()
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -576,8 +577,9 @@ def batched_workload(torch, gs, si, count=512, t_end=20.0):
         "ms": ms_b, "cell_steps_per_s": work_b / (ms_b * 1e-3), "accepted_total": int(rb["n_acc"].sum()),
         "rejected_total": int(rb["n_rej"].sum()), "cells_total": int(cells.sum()), "tile_ty_zc": [tile[0], tile[1]],
         "instance_groups": groups[1], "group_budget_cells": groups[0],
-        "kernels": ("stage pairs (one cell per lane), tile height %d, ring depth %d" % (pairs[1], pairs[2])
-                    if pairs[0] else "single stages"),
+        "kernels": ("stage pairs, ring depth %d; instances with 1 / 2 / 4 cells per lane: %d / %d / %d "
+                    "(tile height %d for one cell per lane, %d for the wider lanes)"
+                    % (pairs[2], *lanes[2], pairs[1], lanes[1]) if pairs[0] else "single stages"),
         "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                      "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                      "algorithmic_bytes_per_cell_attempt": bpa,

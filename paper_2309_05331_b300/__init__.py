@@ -118,6 +118,8 @@ _SIGNATURES = {
     "gsb_set_grouping": ([_vp, C.c_longlong], C.c_int),
     "gsb_set_pairs": ([_vp, C.c_int, C.c_int, C.c_int], C.c_int),
     "gsb_get_pairs": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
+    "gsb_set_pair_lanes": ([_vp, C.c_int, C.c_int], C.c_int),
+    "gsb_get_pair_lanes": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)], C.c_int),
     "gsb_set_stage_depth": ([_vp, C.c_int], C.c_int),
     "gsb_get_grouping": ([_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_int)], C.c_int),
     "gsb_autotune": ([_vp, C.POINTER(C.c_int), C.POINTER(C.c_int), _dp], C.c_int),
@@ -662,6 +664,16 @@ class GrayScottBatch:
         on, ty, depth = C.c_int(0), C.c_int(0), C.c_int(0)
         _bcheck(lib().gsb_get_pairs(self.ctx, C.byref(on), C.byref(ty), C.byref(depth)), self.ctx)
         return on.value, ty.value, depth.value
+
+    def set_pair_lanes(self, mode, ty_wide=7):
+        """1: 2 or 4 cells per lane where an instance's rows allow; 0: one."""
+        _bcheck(lib().gsb_set_pair_lanes(self.ctx, int(mode), ty_wide), self.ctx)
+
+    def pair_lanes(self):
+        """(mode, ty_wide, [instances with 1, 2, 4 cells per lane])."""
+        mode, tyw, counts = C.c_int(0), C.c_int(0), (C.c_int * 3)()
+        _bcheck(lib().gsb_get_pair_lanes(self.ctx, C.byref(mode), C.byref(tyw), counts), self.ctx)
+        return mode.value, tyw.value, list(counts)
 
     def set_grouping(self, cells_per_group):
         """Instance-group budget in cells (-1 automatic, 0 one group)."""

@@ -51,7 +51,7 @@ namespace {
 
 struct BInst {
     int nx, ny, nz;
-    int pad;
+    int vx;         // stage pairs: cells per lane (1, 2 or 4; the row alignment allows it)
     long long off;  // element offset in the concatenated fields
     double cx, cy, cz, Du, Dv, F, k;
 };
@@ -61,7 +61,12 @@ struct BSeg {
 };
 
 constexpr int kBFields = 9;    // 0: second state buffer; 1..8: stage fields
-constexpr int kStageCtrs = 6;  // segment counters per group: stages 2..7 (counter 0: the k1 stage)
+// segment counters per group: stages 2..7, or the three stage pairs for each
+// lane width (counter 0: the k1 stage)
+constexpr int kStageCtrs = 9;
+// segment lists: stage tiles, final-kernel tiles, pair tiles for 1, 2 and 4
+// cells per lane
+constexpr int kLists = 5;
 // working set of a cell in units of the element size: state and second
 // buffer, k1..k7, two components each
 constexpr int kCellFields = 2 * (1 + kBFields);
@@ -124,27 +129,32 @@ __global__ void __launch_bounds__(MODE == MODE_STAGE ? 512 : 256,
 // MODE_PAIR_DOPRI67: stages 6+7, y5, k7 and the instance's error maximum): CTAs take (instance, column of
 // A.ty rows x 32 cells, run of planes) segments from the counter and run the
 // pair segment with one cell per lane.
-// Tile heights of the batch's pair segments: up to 7 rows in a CTA compiled
-// for two per SM (384 threads, <= 80 registers), 8..12 rows in one compiled
-// for one per SM (544 threads: 17 warps, 5 on one SM sub-partition, so <= 96
-// registers; stages 6+7 spill a little there, yet 12 rows measured faster
-// than 11 rows in 16 warps at 128 registers).  12 is the most the pair
-// segment's halo warp covers (2 lanes per row for ty + 4 rows).
+// Tile heights of the batch's pair segments: with one cell per lane, up to 7
+// rows in a CTA compiled for two per SM (384 threads, <= 80 registers),
+// 8..12 rows in one compiled for one per SM (544 threads: 17 warps, 5 on one
+// SM sub-partition, so <= 96 registers; 12 rows measured faster than 11 rows
+// in 16 warps at 128 registers).  12 is the most the pair segment's halo
+// warp covers (2 lanes per row for ty + 4 rows).  Wider lanes (2 or 4 cells)
+// run in the single grid's 12-warp CTA, one per SM, up to 7 rows.
 constexpr int kBPairMaxTY = 12;
-template <bool TALL>
+template <int VX, bool TALL>
 __host__ __device__ constexpr int bpair_threads() {
     return 32 * ((TALL ? kBPairMaxTY : kPairMaxTY) + 5);
 }
+template <int VX, bool TALL>
+__host__ __device__ constexpr int bpair_min_blocks() {
+    return TALL ? 1 : pair_min_blocks<VX>();
+}
 
-template <typename T, int NK, int MODE, bool TALL>
-__global__ void __launch_bounds__(bpair_threads<TALL>(), TALL ? 1 : 2)
+template <typename T, int NK, int MODE, int VX, bool TALL>
+__global__ void __launch_bounds__(bpair_threads<VX, TALL>(), (bpair_min_blocks<VX, TALL>()))
     gsb_pair_kernel(const BInst* __restrict__ insts, DevCtrl* ctrls, const BSeg* __restrict__ segs, int nseg,
                     unsigned int* counter, const StageArgs A, const int depth) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* SA = reinterpret_cast<T*>(smem_raw);
-    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, 1>();
-    unsigned char* SI = smem_raw + (pair_plane_bytes<T, 1>(A.ty) + 15) / 16 * 16;
-    unsigned char* R = SI + pair_isc_bytes<T, MODE, 1>(A.ty);
+    T* SB = SA + 3 * (size_t)(A.ty + 4) * 2 * pair_pitch<T, VX>();
+    unsigned char* SI = smem_raw + (pair_plane_bytes<T, VX>(A.ty) + 15) / 16 * 16;
+    unsigned char* R = SI + pair_isc_bytes<T, MODE, VX>(A.ty);
     R += (128u - ((uint32_t)__cvta_generic_to_shared(R) & 127u)) & 127u;
     __shared__ T red[32];
     __shared__ int s_seg;
@@ -172,10 +182,10 @@ __global__ void __launch_bounds__(bpair_threads<TALL>(), TALL ? 1 : 2)
         g.k = (T)in.k;
         const StagePtrs<T, NK> P = resolve_stage<T, NK, MODE>(A, c->parity, 0, in.off);
         const PairCoef<T, NK> C = pair_coef<T, NK>(A, c->dt_try, c->atol, c->rtol);
-        const int ntx = (in.nx + 31) / 32;
+        const int ntx = (in.nx + 32 * VX - 1) / (32 * VX);
         typename ErrBits<T>::U ebits = 0;
-        pair_segment<T, NK, MODE, 1>(g, P, C, SA, SB, SI, R, depth, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1,
-                                     ebits);
+        pair_segment<T, NK, MODE, VX>(g, P, C, SA, SB, SI, R, depth, A.ty, sg.col % ntx, sg.col / ntx, sg.z0, sg.z1,
+                                      ebits);
         if (MODE == MODE_PAIR_DOPRI67) {
             const T bmax = block_nanmax(ErrBits<T>::value(ebits), red);
             if (tid == 0) atomic_max_nonneg(&ctrls[sg.inst].err_bits, (double)bmax);
@@ -235,14 +245,15 @@ struct gsb_ctx {
     DevCtrl* dctrl = nullptr;
     DevCtrl* hctrl = nullptr;  // pinned, count entries
     unsigned int* counters = nullptr;
-    BSeg* dseg[3] = {nullptr, nullptr, nullptr};  // [0]: stage tiles, [1]: final-kernel tiles, [2]: pair tiles
-    int nseg[3] = {0, 0, 0};
+    BSeg* dseg[kLists] = {};  // [0]: stage tiles, [1]: final-kernel tiles, [2 + c]: pair tiles, 2^c cells per lane
+    int nseg[kLists] = {};
     int ty = 6, zc = 16;
     int depth = 0;                        // staged-form ring depth (0: vectorised form)
     int pairs = 0;                        // stage pairs (gsb_set_pairs)
-    int pty = 7, pdepth = 2;              // pair tile height and ring depth
+    int pty = 7, pdepth = 2;              // pair tile height and ring depth (one cell per lane)
+    int plane = 1, ptyw = kPairMaxTY;     // wider pair lanes where rows allow (gsb_set_pair_lanes), their tile height
     long long group_cells = 0;            // cells per group: -1 automatic (half the L2), 0 one group
-    std::vector<int> gseg0[3], gsegn[3];  // per group: first segment and count in each list
+    std::vector<int> gseg0[kLists], gsegn[kLists];  // per group: first segment and count in each list
     int ngroups = 1, nctr = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -278,6 +289,19 @@ static long long budget_cells(const gsb_ctx* ctx) {
     return std::max<long long>(1, (long long)l2 / 2 / ((long long)kCellFields * (long long)ctx->esz));
 }
 
+// Cells per lane of an instance's stage pairs: lanes own 4 (FP32) or 2
+// consecutive cells of a row when every row of the instance starts on that
+// boundary (instances start 16-byte aligned, so nx a multiple of 4 or 2)
+// and the row is long enough for the wider column (32 x 4 or 32 x 2 cells)
+// not to leave most lanes idle: FP32 nx > 64 and a multiple of 4 -> 4
+// cells, nx > 32 and even -> 2; FP64 (16-byte pairs) nx > 32 and even -> 2;
+// otherwise (or with gsb_set_pair_lanes(ctx, 0, ...)) one cell per lane.
+static int pair_lane_width(const gsb_ctx* ctx, int nx) {
+    if (!ctx->plane) return 1;
+    if (ctx->prec == GS_FP32 && nx > 64 && nx % 4 == 0) return 4;
+    return (nx > 32 && nx % 2 == 0) ? 2 : 1;
+}
+
 // segment lists for rows-per-CTA ty (stages), min(ty, 6) (stage 7) and pty
 // (stage pairs), and the instance groups (consecutive instances, at most
 // budget_cells cells, at least one instance each)
@@ -297,8 +321,10 @@ static gs_status build_segments(gsb_ctx* ctx) {
         }
     }
     ctx->ngroups = (int)first_inst.size();
-    for (int li = 0; li < 3; ++li) {
-        const int ty = li == 0 ? ctx->ty : (li == 1 ? std::min(ctx->ty, kMaxTYFinal) : ctx->pty);
+    for (int i = 0; i < ctx->count; ++i) ctx->hinst[i].vx = pair_lane_width(ctx, ctx->hinst[i].nx);
+    for (int li = 0; li < kLists; ++li) {
+        const int vx = li < 2 ? 1 : 1 << (li - 2);
+        const int ty = li == 0 ? ctx->ty : (li == 1 ? std::min(ctx->ty, kMaxTYFinal) : (vx == 1 ? ctx->pty : ctx->ptyw));
         std::vector<BSeg> v;
         ctx->gseg0[li].assign(ctx->ngroups, 0);
         ctx->gsegn[li].assign(ctx->ngroups, 0);
@@ -307,7 +333,8 @@ static gs_status build_segments(gsb_ctx* ctx) {
             if (g + 1 < ctx->ngroups && i == first_inst[g + 1]) ++g;
             if (i == first_inst[g]) ctx->gseg0[li][g] = (int)v.size();
             const BInst& in = ctx->hinst[i];
-            const int ncol = ((in.nx + 31) / 32) * ((in.ny + ty - 1) / ty);
+            if (li >= 2 && in.vx != vx) continue;  // pair lists: the instances of this lane width
+            const int ncol = ((in.nx + 32 * vx - 1) / (32 * vx)) * ((in.ny + ty - 1) / ty);
             // z-chunk major: segments taken one after another cover the same
             // planes of neighbouring columns, so their halos meet in L2
             for (int z0 = 0; z0 < in.nz; z0 += ctx->zc)
@@ -316,6 +343,8 @@ static gs_status build_segments(gsb_ctx* ctx) {
         }
         if (ctx->dseg[li]) cudaFree(ctx->dseg[li]);
         ctx->dseg[li] = nullptr;
+        ctx->nseg[li] = 0;
+        if (v.empty()) continue;  // no instance of this lane width
         BCK(cudaMalloc(&ctx->dseg[li], sizeof(BSeg) * v.size()));
         BCK(cudaMemcpy(ctx->dseg[li], v.data(), sizeof(BSeg) * v.size(), cudaMemcpyHostToDevice));
         ctx->nseg[li] = (int)v.size();
@@ -440,15 +469,23 @@ static cudaError_t blaunch_dopri5_stage(gsb_ctx* ctx, cudaStream_t s, int st, in
     return blaunch(ctx, s, 5, MODE_DOPRI_FINAL, A, g, ctr);
 }
 
-template <typename T, int NK, int MODE>
+// one pair launch over group `group`'s instances of lane width VX (their
+// own segment list), taken from the segment counter `counter`; nothing when
+// the group has none
+template <typename T, int NK, int MODE, int VX>
 static cudaError_t bpair_launch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int group, int counter) {
-    const int seg0 = ctx->gseg0[2][group];
-    const int nseg = ctx->gsegn[2][group];
-    A.ty = ctx->pty;
-    auto kern = A.ty > kPairMaxTY ? gsb_pair_kernel<T, NK, MODE, true> : gsb_pair_kernel<T, NK, MODE, false>;
+    const int li = 2 + (VX == 4 ? 2 : VX - 1);
+    const int seg0 = ctx->gseg0[li][group];
+    const int nseg = ctx->gsegn[li][group];
+    if (nseg == 0) return cudaSuccess;
+    A.ty = VX == 1 ? ctx->pty : ctx->ptyw;
+    auto kern = gsb_pair_kernel<T, NK, MODE, VX, false>;
+    if constexpr (VX == 1)
+        if (A.ty > kPairMaxTY) kern = gsb_pair_kernel<T, NK, MODE, VX, true>;
     int depth = std::max(1, std::min(ctx->pdepth, kMaxDepth));
-    while (depth > 1 && pair_smem_bytes<T, NK, MODE, 1>(A.ty, depth) > kMaxSmemPerCta - 1024) --depth;
-    const size_t smem = pair_smem_bytes<T, NK, MODE, 1>(A.ty, depth);
+    while (depth > 1 && pair_smem_bytes<T, NK, MODE, VX>(A.ty, depth) > kMaxSmemPerCta - 1024) --depth;
+    const size_t smem = pair_smem_bytes<T, NK, MODE, VX>(A.ty, depth);
+    if (smem > kMaxSmemPerCta - 1024) return cudaErrorInvalidConfiguration;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -456,14 +493,24 @@ static cudaError_t bpair_launch_t(gsb_ctx* ctx, cudaStream_t s, StageArgs A, int
     if (e != cudaSuccess) return e;
     if (occ < 1) occ = 1;
     const int grid = std::max(1, std::min(nseg, ctx->nsm * occ));
-    kern<<<grid, dim3(32, A.ty + 5), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[2] + seg0, nseg,
+    kern<<<grid, dim3(32, A.ty + 5), smem, s>>>(ctx->dinst, ctx->dctrl, ctx->dseg[li] + seg0, nseg,
                                                 ctx->counters + counter, A, depth);
     return cudaGetLastError();
 }
+// pair pi of group g for every lane width (counters 3 per width apart)
 template <int NK, int MODE>
-static cudaError_t bpair_launch(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int group, int counter) {
-    if (ctx->prec == GS_FP64) return bpair_launch_t<double, NK, MODE>(ctx, s, A, group, counter);
-    return bpair_launch_t<float, NK, MODE>(ctx, s, A, group, counter);
+static cudaError_t bpair_launch(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A, int g, int pi) {
+    const int ctr = 1 + kStageCtrs * g + pi;
+    cudaError_t e = cudaSuccess;
+    if (ctx->prec == GS_FP64) {
+        e = bpair_launch_t<double, NK, MODE, 1>(ctx, s, A, g, ctr);
+        if (e == cudaSuccess) e = bpair_launch_t<double, NK, MODE, 2>(ctx, s, A, g, ctr + 3);
+        return e;
+    }
+    e = bpair_launch_t<float, NK, MODE, 1>(ctx, s, A, g, ctr);
+    if (e == cudaSuccess) e = bpair_launch_t<float, NK, MODE, 2>(ctx, s, A, g, ctr + 3);
+    if (e == cudaSuccess) e = bpair_launch_t<float, NK, MODE, 4>(ctx, s, A, g, ctr + 6);
+    return e;
 }
 
 // Dormand-Prince stage pair pi (0: stages 2+3 and the inverse error scale ->
@@ -471,7 +518,6 @@ static cudaError_t bpair_launch(gsb_ctx* ctx, cudaStream_t s, const StageArgs& A
 // fields 5..8 -> y5, k7 and the error maxima) of instance group g: the
 // buffers and coefficients of the single-grid pairs
 static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int g) {
-    const int ctr = 1 + kStageCtrs * g + pi;
     const Slot k1 = bpair(ctx, 1, 2, SEL_CUR);
     const Slot k[4] = {k1, k1, bfld(ctx, 3), bfld(ctx, 4)};  // k[i] = k_i
     StageArgs A;
@@ -486,7 +532,7 @@ static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int
         A.out0 = k[2];
         A.out1 = k[3];
         A.out2 = bfld(ctx, 8);  // inverse error scale
-        return bpair_launch<1, MODE_PAIR_DOPRI23>(ctx, s, A, g, ctr);
+        return bpair_launch<1, MODE_PAIR_DOPRI23>(ctx, s, A, g, pi);
     }
     if (pi == 1) {
         static const double a4[3] = {dp5::A41, dp5::A42, dp5::A43};
@@ -499,7 +545,7 @@ static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int
         A.out0 = bfld(ctx, 5);  // Y6
         A.out1 = bfld(ctx, 6);  // P
         A.out2 = bfld(ctx, 7);  // error terms through k5
-        return bpair_launch<3, MODE_PAIR_DOPRI45>(ctx, s, A, g, ctr);
+        return bpair_launch<3, MODE_PAIR_DOPRI45>(ctx, s, A, g, pi);
     }
     A.u = bfld(ctx, 5);
     A.kin[0] = bfld(ctx, 6);
@@ -507,7 +553,7 @@ static cudaError_t blaunch_dopri5_pair(gsb_ctx* ctx, cudaStream_t s, int pi, int
     A.kin[2] = bfld(ctx, 8);
     A.out0 = bstate(ctx, SEL_NEXT);       // y5
     A.out1 = bpair(ctx, 1, 2, SEL_NEXT);  // k7 = next k1
-    return bpair_launch<3, MODE_PAIR_DOPRI67>(ctx, s, A, g, ctr);
+    return bpair_launch<3, MODE_PAIR_DOPRI67>(ctx, s, A, g, pi);
 }
 
 static cudaError_t bbody(gsb_ctx* ctx, cudaStream_t s, unsigned long long h, int use_cond, bool with_ctrl) {
@@ -584,7 +630,7 @@ gs_status gsb_create(int count, const gsb_instance* inst, double L, double Du, d
         b.nx = inst[i].nx;
         b.ny = inst[i].ny;
         b.nz = inst[i].nz;
-        b.pad = 0;
+        b.vx = 1;
         b.off = off;
         const double hx = L / b.nx, hy = L / b.ny, hz = L / b.nz;
         b.cx = 1.0 / (hx * hx);
@@ -639,7 +685,7 @@ gs_status gsb_destroy(gsb_ctx* ctx) {
     if (ctx->hctrl) cudaFreeHost(ctx->hctrl);
     if (ctx->dlog) cudaFree(ctx->dlog);
     if (ctx->counters) cudaFree(ctx->counters);
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < kLists; ++i)
         if (ctx->dseg[i]) cudaFree(ctx->dseg[i]);
     delete ctx;
     return GS_OK;
@@ -679,6 +725,26 @@ gs_status gsb_set_pairs(gsb_ctx* ctx, int on, int ty, int depth) {
     if (ty != ctx->pty) {
         ctx->pty = ty;
         return build_segments(ctx);
+    }
+    return GS_OK;
+}
+
+gs_status gsb_set_pair_lanes(gsb_ctx* ctx, int mode, int ty_wide) {
+    if (!ctx || mode < 0 || mode > 1 || ty_wide < 1 || ty_wide > kPairMaxTY) return GS_ERR_INVALID;
+    if (mode == ctx->plane && ty_wide == ctx->ptyw) return GS_OK;
+    bdrop_graph(ctx);
+    ctx->plane = mode;
+    ctx->ptyw = ty_wide;
+    return build_segments(ctx);
+}
+
+gs_status gsb_get_pair_lanes(const gsb_ctx* ctx, int* mode, int* ty_wide, int* counts) {
+    if (!ctx) return GS_ERR_INVALID;
+    if (mode) *mode = ctx->plane;
+    if (ty_wide) *ty_wide = ctx->ptyw;
+    if (counts) {
+        counts[0] = counts[1] = counts[2] = 0;
+        for (const BInst& in : ctx->hinst) ++counts[in.vx == 4 ? 2 : in.vx - 1];
     }
     return GS_OK;
 }

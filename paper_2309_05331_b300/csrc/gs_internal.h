@@ -156,16 +156,27 @@ gs_status gsb_set_grouping(gsb_ctx* ctx, long long cells_per_group);
  * gsb_autotune tunes the tile of the depth in use. */
 gs_status gsb_set_stage_depth(gsb_ctx* ctx, int depth);
 gs_status gsb_get_grouping(const gsb_ctx* ctx, long long* cells_per_group, int* ngroups);
-/* Stage pairs for the batch: on = 1 runs each attempt as three launches
- * (stages 2+3, 4+5, 6+7; the single-grid pair segment with one cell per lane,
- * so any nx), 18 field passes per attempt instead of 33; ty = the pair
- * segments' tile height (1..12; up to 7 in CTAs compiled for two per SM,
- * 8..12 in CTAs compiled for one), depth = their input ring depth (1..3, cut
- * to what shared memory holds).  The z-chunk is gsb_set_tile's.  Same
- * formulas as the single stages (results agree to rounding).
- * gsb_autotune_run tries both forms.  gsb_get_pairs: the setting in use. */
+/* Stage pairs for the batch: on = 1 runs each attempt as three pair steps
+ * (stages 2+3, 4+5, 6+7; the single-grid pair segment), 18 field passes per
+ * attempt instead of 33; ty = the tile height of the instances run with one
+ * cell per lane (1..12; up to 7 in CTAs compiled for two per SM, 8..12 in
+ * CTAs compiled for one), depth = the input ring depth (1..3, cut to what
+ * shared memory holds).  The z-chunk is gsb_set_tile's.  Same formulas as
+ * the single stages (results agree to rounding).  gsb_autotune_run tries
+ * both forms.  gsb_get_pairs: the setting in use. */
 gs_status gsb_set_pairs(gsb_ctx* ctx, int on, int ty, int depth);
 gs_status gsb_get_pairs(const gsb_ctx* ctx, int* on, int* ty, int* depth);
+/* Lane width of the stage pairs per instance: mode 1 (the default) gives
+ * an instance 4 consecutive cells per lane (FP32, 16-byte rows: nx > 64 and
+ * a multiple of 4) or 2 (8-byte FP32 / 16-byte FP64 rows: nx > 32 and even)
+ * where every row starts on that boundary, one cell per lane otherwise; each
+ * width runs its own launch per pair step over its instances, the wider
+ * ones in 12-warp CTAs of tile height ty_wide (1..7).  mode 0: one cell per
+ * lane for every instance.  Per-cell arithmetic is the same for every width
+ * (FP64 results are identical).  gsb_get_pair_lanes: the setting and the
+ * number of instances of width 1, 2 and 4 (host array of 3 ints). */
+gs_status gsb_set_pair_lanes(gsb_ctx* ctx, int mode, int ty_wide);
+gs_status gsb_get_pair_lanes(const gsb_ctx* ctx, int* mode, int* ty_wide, int* counts);
 
 /* ---------------------------- learned surrogate -------------------------- */
 /* Tensor-core engine of sur_conv3d (and of the network's convolutions),

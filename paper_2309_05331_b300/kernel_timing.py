@@ -4,7 +4,7 @@ so that a profiler sees each launch.
     python -m paper_2309_05331_b300.kernel_timing dcpse --grid 64 --method rk4 --steps 20
     python -m paper_2309_05331_b300.kernel_timing dp5 --n 1048576 --rhs 0
     python -m paper_2309_05331_b300.kernel_timing ab4 --n 16777216 --rhs 1 --steps 1000
-    python -m paper_2309_05331_b300.kernel_timing batch --count 512 [--pairs 12]
+    python -m paper_2309_05331_b300.kernel_timing batch --count 512 [--pairs 12 [--lanes 0]]
     python -m paper_2309_05331_b300.kernel_timing each --n 16777216 --rhs 0
 
 dcpse: the Gray-Scott run with the DC-PSE Laplacian (Du = 2e-4, Dv = 1e-4,
@@ -14,8 +14,10 @@ point (whose attempts are launched one by one), atol = rtol = 1e-8, t: 0 -> 10.
 ab4: Adams-Bashforth 4, dt = 1e-3.  batch: the ensemble of `count` uneven
 Gray-Scott instances (FP32) and the batched integrator's autotuner, whose
 timing rounds launch every Dormand-Prince stage of the whole batch directly
-(with --pairs TY: the k1 stage and the three stage-pair kernels, tile height
-TY, ring depth 2).
+(with --pairs TY: the k1 stage and the three stage-pair steps, ring depth 2,
+tile height TY for the instances with one cell per lane; --lanes 1, the
+default: 2 or 4 cells per lane where an instance's rows allow, tile height 7
+for those; --lanes 0: one cell per lane for every instance).
 each: Dormand-Prince with every element its own step size (one launch),
 atol = rtol = 1e-8, t: 0 -> 10.
 Seeded synthetic inputs; prints one JSON line with the wall time (after a
@@ -45,6 +47,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=1 << 20)
     ap.add_argument("--rhs", type=int, default=0, help="0: dx/dt = -x, 1: x (1 - x)")
     ap.add_argument("--pairs", type=int, default=0, help="batch: stage pairs of this tile height (0: single stages)")
+    ap.add_argument("--lanes", type=int, default=1, help="batch pairs: 1 = 2 or 4 cells per lane where rows allow, 0 = one")
     a = ap.parse_args(argv)
     res = {"what": a.what}
     if a.what == "dcpse":
@@ -89,11 +92,12 @@ def main(argv=None):
             b.set_instance(i, torch.from_numpy(u), torch.from_numpy(v))
         if a.pairs:
             b.set_pairs(True, a.pairs, 2)
+            b.set_pair_lanes(a.lanes)
         t0 = time.perf_counter()
         ty, zc, ms = b.autotune()
         if a.pairs:
             ty = a.pairs
-        res.update(pairs=bool(a.pairs), count=a.count, cells=int(sum(d["nx"] * d["ny"] * d["nz"] for d in insts)), tile=[ty, zc],
+        res.update(pairs=bool(a.pairs), lanes=b.pair_lanes()[2] if a.pairs else None, count=a.count, cells=int(sum(d["nx"] * d["ny"] * d["nz"] for d in insts)), tile=[ty, zc],
                    round_ms=ms, ms=(time.perf_counter() - t0) * 1e3)
         b.close()
     elif a.what == "each":

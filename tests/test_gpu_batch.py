@@ -224,6 +224,88 @@ def test_batched_pairs_fp32_match_oracle_replay_and_single_stages():
             assert_parity(list(res[0][1][i]), list(res[1][1][i]), 1e-5, ("pairs vs stages", i))
 
 
+# instances whose rows allow 4 (FP32: nx > 64, a multiple of 4) or 2 (nx > 32,
+# even) cells per lane in the stage pairs, with partial last columns (100 of
+# 128 cells; 130 = 64 + 64 + 2), and two that keep one cell per lane
+WIDE = [dict(nx=96, ny=9, nz=5, F=0.03, k=0.05), dict(nx=68, ny=13, nz=3, F=0.045, k=0.061),
+        dict(nx=100, ny=4, nz=6, F=0.053, k=0.014), dict(nx=130, ny=5, nz=4, F=0.04, k=0.06),
+        dict(nx=66, ny=7, nz=5, F=0.025, k=0.055), dict(nx=34, ny=3, nz=9, F=0.058, k=0.065),
+        dict(nx=35, ny=6, nz=4, F=0.035, k=0.045), dict(nx=12, ny=9, nz=7, F=0.05, k=0.06)]
+
+
+@pytest.mark.parametrize("tyw,depth", [(7, 2), (3, 1), (5, 3)])
+def test_batched_pairs_wide_lanes_fp64_match_oracle_and_one_cell_lanes(tyw, depth):
+    """FP64 batch with the stage pairs at 2 cells (16 bytes) per lane where nx
+    is even and above 32: every instance takes the oracle's accepted /
+    rejected steps and step sizes and matches its state element by element,
+    and the run is bit-identical to the one with one cell per lane
+    everywhere (the per-cell arithmetic does not depend on the lane width)."""
+    torch = cuda_or_skip()
+    inits = _inits(WIDE, seed0=400)
+    res = []
+    for mode in (1, 0):
+        b = _batch(torch, WIDE, inits, 0)
+        b.set_pairs(1, 7, depth)
+        b.set_pair_lanes(mode, tyw)
+        assert b.pair_lanes() == (mode, tyw, [2, 6, 0] if mode else [8, 0, 0])
+        b.set_step_log(1000)
+        r = b.integrate_adaptive(1e-8, 1e-8, 0.0, 1.0, 0.1)
+        res.append((b.step_log(), [tuple(to_np(x) for x in b.view(i)) for i in range(len(WIDE))],
+                    r["n_acc"].copy(), r["n_rej"].copy()))
+        b.close()
+    logs, states, nacc, nrej = res[0]
+    for i, d in enumerate(WIDE):
+        ref = _oracle_adaptive(d, *inits[i], 1.0, 1e-8, log_cap=1000)
+        assert (nacc[i], nrej[i]) == (ref["n_acc"], ref["n_rej"]) and nacc[i] <= 1000, i
+        assert np.allclose(logs[i], ref["dts"], rtol=1e-7, atol=0), i
+        assert_parity(list(states[i]), [ref["u"], ref["v"]], 1e-12, i)
+        assert np.array_equal(logs[i], res[1][0][i]), i
+        assert np.array_equal(states[i][0], res[1][1][i][0]) and np.array_equal(states[i][1], res[1][1][i][1]), i
+
+
+@pytest.mark.parametrize("tyw,depth", [(7, 1), (4, 2)])
+def test_batched_pairs_wide_lanes_fp32_match_oracle_replay(tyw, depth):
+    """FP32 batch with the stage pairs at 4 cells per lane (nx > 64, a multiple
+    of 4), 2 (nx > 32, even) and 1 (the rest): every instance against the
+    FP64 oracle replaying its logged step sizes, cell by cell (1e-5), and
+    against the run with one cell per lane everywhere."""
+    torch = cuda_or_skip()
+    inits = _inits(WIDE, seed0=410, round32=True)
+    res = []
+    for mode in (1, 0):
+        b = _batch(torch, WIDE, inits, 1)
+        b.set_pairs(1, 9, depth)
+        b.set_pair_lanes(mode, tyw)
+        assert b.pair_lanes()[2] == ([2, 3, 3] if mode else [8, 0, 0])
+        b.set_step_log(1000)
+        r = b.integrate_adaptive(1e-6, 1e-6, 0.0, 1.0, 0.1)
+        assert np.all(r["statuses"] == 0) and np.all(r["t"] == 1.0)
+        assert np.all(r["n_acc"] <= 1000)
+        res.append((b.step_log(), [tuple(to_np(x) for x in b.view(i)) for i in range(len(WIDE))],
+                    r["n_acc"].copy()))
+        b.close()
+    for i, d in enumerate(WIDE):
+        p = oracle.GSParams(d["nx"], d["ny"], d["nz"], F=d["F"], k=d["k"], **PHYS)
+        ou, ov = oracle.gs_integrate_replay(p, *inits[i], oracle.DOPRI5, res[0][0][i])
+        gu, gv = res[0][1][i]
+        assert_parity([gu, gv], [ou, ov], 1e-5, i)
+        for a, o in ((gu, ou), (gv, ov)):
+            assert np.max(np.abs(a - o)) <= 1e-5 * np.max(np.abs(o)), i
+        if res[0][2][i] == res[1][2][i] and np.allclose(res[0][0][i], res[1][0][i], rtol=1e-5):
+            assert_parity(list(res[0][1][i]), list(res[1][1][i]), 1e-5, ("4/2 vs 1 cells per lane", i))
+
+
+def test_pair_lanes_reject_invalid_settings():
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    b = _batch(torch, WIDE[:2], _inits(WIDE[:2]), 1)
+    for bad in ((2, 7), (-1, 7), (1, 0), (1, 8)):
+        with pytest.raises(gs.GSError):
+            b.set_pair_lanes(*bad)
+    assert b.pair_lanes() == (1, 7, [0, 0, 2])
+    b.close()
+
+
 @pytest.mark.parametrize("pairs", [0, 1])
 def test_full_size_512_instance_ensemble(pairs):
     """512 instances, per-axis edges U{16..96}, F in [0.02,0.06], k in
