@@ -69,7 +69,7 @@ NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside 
 # 554.4 MB read + 365.9 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages4+5", "path": "pairs", "source_sha": "cce42abadfb2dc82",
+NCU_TRAFFIC = {"kernel": "stages4+5", "path": "pairs", "source_sha": "c21c09cc5669b45b",
                "bytes_per_cell": (554367232 + 365880320) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]

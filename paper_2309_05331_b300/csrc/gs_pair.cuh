@@ -26,8 +26,10 @@
 // then k3, k4 and the update u' = u + dt (k1/6 + k2/3 + k3/3 + k4/6) from u,
 // k1, k2 without storing k3 or k4: 7 field passes per step instead of 13.
 //
-// Mapping (the staged form's, widened): a warp owns a row of 32*VX cells
-// (one 16-byte vector per lane, VX = 16 / sizeof(T)).  The CTA has ty + 4 row warps for rows
+// Mapping (the staged form's, widened): a warp owns a row of 32*VX cells, a
+// vector of VX consecutive cells per lane (16 bytes on the single grid, VX =
+// 16 / sizeof(T); the batched ensemble also runs one cell or 8 bytes per
+// lane, as its instances' rows allow).  The CTA has ty + 4 row warps for rows
 // y0-2 .. y0+ty+1 and one halo warp whose lane 2(r+2)+s owns the two x-halo
 // columns of row y0+r on side s (s = 0: x0-2, x0-1; s = 1: x0+aw,
 // x0+aw+1).  Planes advance in z with three phases per iteration:
@@ -35,9 +37,11 @@
 //           stored in the Y_i plane buffer;
 //   B(z+1): k_i of plane z+1 on rows -1..ty and the two inner halo columns
 //           (7-point stencil on the Y_i planes z, z+1, z+2), stored for the
-//           tile rows; Y_{i+1} of plane z+1 formed and stored in the Y_{i+1}
+//           tile rows (Dormand-Prince 4+5: kept for C; 6+7: y5 stored
+//           instead); Y_{i+1} of plane z+1 formed and stored in the Y_{i+1}
 //           plane buffer;
-//   C(z):   k_{i+1} of plane z on the tile rows, stored.
+//   C(z):   k_{i+1} of plane z on the tile rows, stored (4+5: stage 6's
+//           fields instead; 6+7: k7 and the scaled error).
 // B reads the Y_i plane that A wrote one iteration earlier (neighbours) and
 // its own cells of the plane before (lower z neighbour); C likewise on the
 // Y_{i+1} planes.  Three buffers of each and one barrier per iteration order
