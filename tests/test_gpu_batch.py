@@ -295,6 +295,29 @@ def test_batched_pairs_wide_lanes_fp32_match_oracle_replay(tyw, depth):
             assert_parity(list(res[0][1][i]), list(res[1][1][i]), 1e-5, ("4/2 vs 1 cells per lane", i))
 
 
+@pytest.mark.parametrize("group_cells", [1, 6000, 0])
+def test_pair_lanes_with_instance_groups_bit_identical(group_cells):
+    """Stage pairs at every lane width, run group by group (one launch per
+    lane width and group, each from its own counter): the same bits as one
+    group, in FP64."""
+    torch = cuda_or_skip()
+    inits = _inits(WIDE, seed0=420)
+    res = []
+    for gc in (0, group_cells):
+        b = _batch(torch, WIDE, inits, 0)
+        b.set_pairs(1, 5, 2)
+        b.set_grouping(gc)
+        if gc == 1:
+            assert b.grouping()[1] == len(WIDE)
+        r = b.integrate_adaptive(1e-7, 1e-7, 0.0, 0.5, 0.1)
+        res.append(([to_np(x) for i in range(len(WIDE)) for x in b.view(i)], r["n_acc"].copy(), r["n_rej"].copy()))
+        b.close()
+    (a0, acc0, rej0), (a1, acc1, rej1) = res
+    assert np.array_equal(acc0, acc1) and np.array_equal(rej0, rej1)
+    for a, c in zip(a0, a1):
+        assert np.array_equal(a, c)
+
+
 def test_pair_lanes_reject_invalid_settings():
     torch = cuda_or_skip()
     import paper_2309_05331_b300 as gs
