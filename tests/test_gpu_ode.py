@@ -422,3 +422,23 @@ def test_adaptive_exceptional_ratios_match_oracle(case):
     assert np.allclose(d, ref["dts"], rtol=1e-7, atol=0)
     if ref["status"] == oracle.OK:  # per element relative to its start value (magnitudes 1e-290 .. 1e250)
         assert_parity(to_np(x) / x0, ref["x"] / x0, 1e-12)
+
+
+def test_zero_elements_are_accepted_by_every_pointwise_call():
+    """n = 0 is a valid ensemble: every pointwise entry point returns OK and
+    leaves t where it was (nothing to integrate), without touching memory."""
+    torch = cuda_or_skip()
+    import paper_2309_05331_b300 as gs
+    x = torch.empty(0, dtype=torch.float64, device="cuda")
+    r = gs.ode_integrate_adaptive(0, x, 0.0, 1.0, 0.1, 1e-8, 1e-8)
+    assert r["n_acc"] == 0 and r["n_rej"] == 0 and r["t"] == 0.0
+    gs.ode_integrate_ab4(0, x, 0.0, 0.1, 10)
+    gs.ode_integrate_const(0, 0, x, 0.0, 0.1, 10)
+    gs.ode_integrate_tableau(0, gs.ODE_TAB_RKF78, x, 0.0, 0.1, 10)
+    gs.ode_integrate_ab_steps(0, 8, x, 0.0, 0.1, 10)
+    gs.ode_integrate_abm_steps(0, 8, x, 0.0, 0.1, 10)
+    e = gs.ode_integrate_adaptive_each(0, gs.ODE_TAB_DOPRI5, x, 0.0, 1.0, 0.1, 1e-8, 1e-8)
+    assert all(v.numel() == 0 for v in e.values() if hasattr(v, "numel"))
+    ys = torch.empty(0, dtype=torch.float32, device="cuda")
+    gs.ode_axpy_stage([1.0, 2.0], [ys, ys], ys)
+    torch.cuda.synchronize()
