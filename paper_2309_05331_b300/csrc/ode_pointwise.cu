@@ -147,22 +147,29 @@ __global__ void __launch_bounds__(256) ode_ab4_kernel(long long n, double* x, do
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         double u = x[i];
-        double f0 = 0, f1 = 0, f2 = 0, f3 = 0;  // f_m, f_{m-1}, f_{m-2}, f_{m-3}
+        // history h_j of the last four steps: f_{m-j} itself, or for dx/dt =
+        // -x the state x_{m-j} with the sign folded into the update (x' = x -
+        // dt sum c_j x_j: the same values as x + dt sum c_j f_j, negation
+        // being exact, without an instruction to form -x)
+        constexpr bool NEG = KIND == ODE_EXP_DECAY;
+        auto hist = [](double v) { return NEG ? v : rhs<KIND>(v); };
+        double h0 = 0, h1 = 0, h2 = 0, h3 = 0;
         const long long ns = nsteps < 3 ? nsteps : 3;
         for (long long m = 0; m < ns; ++m) {
-            f3 = f2;
-            f2 = f1;
-            f1 = f0;
-            f0 = rhs<KIND>(u);
+            h3 = h2;
+            h2 = h1;
+            h1 = h0;
+            h0 = hist(u);
             u = rk4_step<KIND>(u, dt);
         }
         const double c0 = 55.0 / 24.0, c1 = -59.0 / 24.0, c2 = 37.0 / 24.0, c3 = -9.0 / 24.0;
         for (long long m = ns; m < nsteps; ++m) {
-            f3 = f2;
-            f2 = f1;
-            f1 = f0;
-            f0 = rhs<KIND>(u);
-            u = u + dt * (c0 * f0 + c1 * f1 + c2 * f2 + c3 * f3);
+            h3 = h2;
+            h2 = h1;
+            h1 = h0;
+            h0 = hist(u);
+            const double sum = c0 * h0 + c1 * h1 + c2 * h2 + c3 * h3;
+            u = NEG ? u - dt * sum : u + dt * sum;
         }
         x[i] = u;
     }
