@@ -320,6 +320,33 @@ def extra_workloads(torch, gs, si):
     gs.gs_set_small_grid_path(g.ctx, -1, 0)
     out["gs_32cubed_fp64_rk4_dt0.1_x100"]["launch_paths"] = paths
     g.close()
+
+    # Gray-Scott 256^3 FP32 RK4 dt=0.1 x 50 steps: two stage-pair launches per
+    # step (k1, k2 from u; then k3, k4 and the update), 7 field passes of 8 B
+    # per cell-step (read u; write k1, k2; read u, k1, k2; write u')
+    n = 256
+    u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+    g = gs.GrayScott(n, n, n, prec=gs.GS_FP32)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    gs.gs_autotune(g.ctx)
+    g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+    g.step(gs.GS_RK4, 0.0, 0.1, 5)
+    a, b = ev(), ev()
+    a.record(stream)
+    g.step(gs.GS_RK4, 0.5, 0.1, 50)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    peak_hbm, peak_kind = _peaks()
+    rk4_bytes = 7 * BYTES_PER_FIELD_CELL * n ** 3 * 50
+    gbs = rk4_bytes / (ms * 1e-3) / 1e9
+    out["gs_256cubed_fp32_rk4_dt0.1_x50"] = {
+        "ms": ms, "cell_steps_per_s": n ** 3 * 50 / (ms * 1e-3),
+        "path": "stage pairs" if gs.gs_get_rk4_fusion(g.ctx) else "single stages",
+        "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": gbs, "peak": peak_hbm, "frac": gbs / peak_hbm,
+                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_cell_step": 7 * BYTES_PER_FIELD_CELL}}
+    g.close()
     # the Algebra's linear combination y = sum_j a_j x_j (ode_axpy_stage),
     # 128 MB per operand (2^25 FP32 / 2^24 FP64 elements, so every call
     # streams from HBM): nterms + 1 arrays moved per call.  In FP64 each
