@@ -275,7 +275,10 @@ gs_status gsb_integrate_adaptive(gsb_ctx* ctx, double atol, double rtol, double*
 gs_status gsb_autotune(gsb_ctx* ctx, int* ty, int* zc, double* best_ms);
 /* Tile choice by timing the caller's integration itself: each candidate
  * (the single-stage kernels at 7 tile shapes; the stage pairs, stages 2+3,
- * 4+5 and 6+7 each in one launch, at 6 tile shapes)
+ * 4+5 and 6+7 each one step, at 6 tile shapes for the instances run with
+ * one cell per lane; the instances whose rows allow 2 or 4 cells per lane
+ * run so at tile height 7 in their own launches, as gsb_set_pair_lanes in
+ * the internal header describes)
  * runs gsb_integrate_adaptive(atol, rtol, t0 -> t_end, dt0 for every
  * instance) twice (the first run builds its graph) from the bound state,
  * which is saved (a temporary copy of the state, allocated and freed here)
