@@ -6,6 +6,7 @@ so that a profiler sees each launch.
     python -m paper_2309_05331_b300.kernel_timing ab4 --n 16777216 --rhs 1 --steps 1000
     python -m paper_2309_05331_b300.kernel_timing batch --count 512 [--pairs 12 [--lanes 0]]
     python -m paper_2309_05331_b300.kernel_timing each --n 16777216 --rhs 0
+    python -m paper_2309_05331_b300.kernel_timing rk4 --grid 256 --steps 50
 
 dcpse: the Gray-Scott run with the DC-PSE Laplacian (Du = 2e-4, Dv = 1e-4,
 F = 0.053, k = 0.014, FP64, fixed steps of dt = 1).  dp5: error-controlled
@@ -20,6 +21,10 @@ default: 2 or 4 cells per lane where an instance's rows allow, tile height 7
 for those; --lanes 0: one cell per lane for every instance).
 each: Dormand-Prince with every element its own step size (one launch),
 atol = rtol = 1e-8, t: 0 -> 10.
+rk4: the Gray-Scott grid (Du = 2e-5, Dv = 1e-5, FP32) autotuned (its timing
+launches every stage and stage-pair kernel directly, the RK4 pairs among
+them), then `steps` fixed RK4 steps of dt = 0.1; reports the pair shapes
+chosen and the steps' time.
 Seeded synthetic inputs; prints one JSON line with the wall time (after a
 warm-up run) of the call.
 """
@@ -39,7 +44,7 @@ def main(argv=None):
     from . import GS_DOPRI5, GS_FP64, GS_LAP_DCPSE, GS_RK4, GrayScott, gs_set_laplacian, lib, ode_integrate_ab4
 
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("what", choices=["dcpse", "dp5", "ab4", "batch", "each"])
+    ap.add_argument("what", choices=["dcpse", "dp5", "ab4", "batch", "each", "rk4"])
     ap.add_argument("--count", type=int, default=512)
     ap.add_argument("--grid", type=int, default=64)
     ap.add_argument("--method", choices=["rk4", "dopri5"], default="rk4")
@@ -100,6 +105,22 @@ def main(argv=None):
         res.update(pairs=bool(a.pairs), lanes=b.pair_lanes()[2] if a.pairs else None, count=a.count, cells=int(sum(d["nx"] * d["ny"] * d["nz"] for d in insts)), tile=[ty, zc],
                    round_ms=ms, ms=(time.perf_counter() - t0) * 1e3)
         b.close()
+    elif a.what == "rk4":
+        from . import GS_FP32, GS_RK4, GrayScott, gs_autotune, gs_get_pair_configs, gs_get_rk4_fusion
+        n = a.grid
+        u0, v0 = si.gs_initial_state(n, n, n, seed=2)
+        g = GrayScott(n, n, n, prec=GS_FP32)
+        g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+        gs_autotune(g.ctx)
+        g.set_state(torch.from_numpy(u0), torch.from_numpy(v0))
+        g.step(GS_RK4, 0.0, 0.1, 2)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.step(GS_RK4, 0.2, 0.1, a.steps)
+        torch.cuda.synchronize()
+        res.update(grid=n, steps=a.steps, ms=(time.perf_counter() - t0) * 1e3, rk4_pairs=gs_get_rk4_fusion(g.ctx),
+                   pair_configs=gs_get_pair_configs(g.ctx))
+        g.close()
     elif a.what == "each":
         from . import ODE_TAB_DOPRI5, ode_integrate_adaptive_each
         x0 = torch.from_numpy(si.ode_initial_values(a.n, seed=1)).cuda()
