@@ -242,8 +242,10 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 #pragma unroll
                 for (int f = 0; f <= NK; ++f) {
                     // stages 6+7: Y6 on every row, P on rows -1..ty, the
-                    // error terms and the inverse scale on the tile rows
+                    // error terms and the inverse scale on the tile rows;
+                    // RK4 stages 3+4: k1 only on the tile rows (the update)
                     if (DP && f > 0 && !(f == 1 ? inB : inC)) continue;
+                    if (RK && f == 1 && !inC) continue;
                     const T* base = (f == 0 ? P.u[c] : P.k[f > 0 ? f - 1 : 0][c]);
                     const T* src = base + cbase + zo;
                     if (hw && VX == 1) {
@@ -295,12 +297,19 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
             }
 #pragma unroll
             for (int j = 0; j < NK; ++j) {
+                // RK4 stages 3+4: Y3 = u + dt/2 k2 and Y4 = u + dt k3, so k1
+                // enters only the update (tile rows)
+                if (RK && j == 0 && !WR) continue;
                 T kk[NV];
                 ld(c * (1 + NK) + 1 + j, kk);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    s1[v] = (j == 0) ? C.a1[0] * kk[v] : s1[v] + C.a1[j] * kk[v];
-                    s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
+                    if (RK) {
+                        if (j == 1) s1[v] = C.a1[j] * kk[v];
+                    } else {
+                        s1[v] = (j == 0) ? C.a1[0] * kk[v] : s1[v] + C.a1[j] * kk[v];
+                        s2[v] = (j == 0) ? C.a2[0] * kk[v] : s2[v] + C.a2[j] * kk[v];
+                    }
                     if (WR) q[v] = (j == 0) ? C.rb[0] * kk[v] : q[v] + C.rb[j] * kk[v];
                     if (W23 && j == 0) k1v[v] = kk[v];
                     if (W45) {
@@ -321,7 +330,7 @@ __device__ __forceinline__ void pair_segment(const Geom<T>& g, const StagePtrs<T
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
                 Y[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s1[v];
-                P2[c][v] = (NK == 0) ? uu[v] : uu[v] + dt * s2[v];
+                P2[c][v] = (NK == 0 || RK) ? uu[v] : uu[v] + dt * s2[v];
                 if (W45) {
                     s6[v] = dt * s6[v];
                     s7[v] = dt * s7[v];
