@@ -66,11 +66,11 @@ NOMINAL_HBM_GBS = 7700.0  # HBM3e nominal bandwidth of one B300 (context beside 
 
 # DRAM traffic of the dominant kernel from one ncu capture of the standalone
 # stages 4+5 pair launch at 256^3 (profiles/gs_dopri5_pairs_fp32_256cubed_full.md:
-# 554.4 MB read + 365.9 MB written), per cell so that other grids scale by
+# 554.3 MB read + 365.8 MB written), per cell so that other grids scale by
 # cells; valid only for that kernel on that path while the stage-kernel
 # sources are unchanged.
-NCU_TRAFFIC = {"kernel": "stages4+5", "path": "pairs", "source_sha": "c21c09cc5669b45b",
-               "bytes_per_cell": (554367232 + 365880320) / 256 ** 3}
+NCU_TRAFFIC = {"kernel": "stages4+5", "path": "pairs", "source_sha": "19c0d030dd0de6dd",
+               "bytes_per_cell": (554307328 + 365822720) / 256 ** 3}
 KERNEL_SOURCES = ("common.cuh", "gs_tile.cuh", "gs_wide.cuh", "gs_staged.cuh", "gs_pair.cuh", "gs_grid.cu")
 FORM_NAMES = ["", "generic", "vec16B", "vec8B", "staged16B"]
 
